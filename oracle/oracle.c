@@ -1,0 +1,661 @@
+/*
+ * CPU ORACLE -- TEST INFRASTRUCTURE ONLY.
+ *
+ * Plain, slow, literal implementation of what the RP-Tuning hot path computes:
+ *   - RobustPrune, sorted and unsorted (Algorithm 1; unsorted variant in §3,
+ *     "RP-Tuning" paragraph),
+ *   - RP-Tuning = RobustPrune(p, N_out(p), alpha2, R) for every node (§3),
+ *   - the slow-preprocessing construction RobustPrune(p, P \ {p}, alpha, R)
+ *     (§2.1, Lemma 2.2),
+ *   - GreedySearch (Algorithm 2) from the medoid start vertex (§4.1),
+ *   - brute-force exact k nearest neighbours (ground truth for recall, §4),
+ *   - alpha-reachability alpha* of a graph (Definition 2.1).
+ *
+ * Only the test-suite, the package smoke check and the benchmark's CPU
+ * baseline leg use this file.  It shares no code, header or constant with the
+ * CUDA library and never calls it.
+ *
+ * Canonical arithmetic (the paper says "Euclidean distance", §4.1; it fixes no
+ * precision, so these readings are ours):
+ *   - uint8 vectors: d2 is the exact int64 sum of (x_i - y_i)^2; the domination
+ *     test alpha * D(p*,p') <= D(p,p') is evaluated exactly as
+ *     A*A*d2(p*,p') <= 1e6 * d2(p,p') in int64, alpha = A / 1000.
+ *   - float32 vectors: t = (double)x_i - (double)y_i; s = s + t*t in index order,
+ *     round-to-nearest binary64, no fused multiply-add (built with
+ *     -ffp-contract=off).  Decision: (double)(A*A) * d2a <= 1e6 * d2b, each
+ *     product rounded to binary64.
+ *   - Squared distances stand in for distances: alpha*D(a,b) <= D(c,e) iff
+ *     alpha^2 * d2(a,b) <= d2(c,e) over the reals.
+ *   - argmin ties go to the smaller id; candidate sets are deduplicated and p
+ *     itself is dropped (Algorithm 1 first step: V <- (V u N_out(p)) \ {p}).
+ *   - R = INT32_MAX means "no degree bound" (RP-Tuning passes infinity, §3).
+ */
+#include <math.h>
+#include <pthread.h>
+#include <stdatomic.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#include <unistd.h>
+
+#define ORC_U8 1
+#define ORC_F32 2
+#define ORC_SORTED 0
+#define ORC_UNSORTED 1
+
+/* ------------------------------------------------------------------ */
+/* distances                                                           */
+/* ------------------------------------------------------------------ */
+
+static int64_t d2_u8(const uint8_t *a, const uint8_t *b, int d) {
+  int64_t s = 0;
+  for (int i = 0; i < d; i++) {
+    int64_t t = (int64_t)a[i] - (int64_t)b[i];
+    s += t * t;
+  }
+  return s;
+}
+
+static double d2_f32(const float *a, const float *b, int d) {
+  double s = 0.0;
+  for (int i = 0; i < d; i++) {
+    double t = (double)a[i] - (double)b[i];
+    s = s + t * t;
+  }
+  return s;
+}
+
+/* d2 between two base points as a double (exact for uint8: < 2^53). */
+static double d2_pts(const void *X, int dtype, int d, int64_t a, int64_t b) {
+  if (dtype == ORC_U8) {
+    const uint8_t *U = (const uint8_t *)X;
+    return (double)d2_u8(U + a * d, U + b * d, d);
+  }
+  const float *F = (const float *)X;
+  return d2_f32(F + a * d, F + b * d, d);
+}
+
+/* d2 between a free vector q (same dtype as X) and base point b. */
+static double d2_vec(const void *X, int dtype, int d, const void *q, int64_t b) {
+  if (dtype == ORC_U8)
+    return (double)d2_u8((const uint8_t *)q, (const uint8_t *)X + b * d, d);
+  return d2_f32((const float *)q, (const float *)X + b * d, d);
+}
+
+/* ------------------------------------------------------------------ */
+/* a tiny thread pool over independent items                           */
+/* ------------------------------------------------------------------ */
+
+typedef void (*item_fn)(void *arg, int64_t item, int tid);
+typedef struct {
+  atomic_llong next;
+  int64_t total;
+  item_fn fn;
+  void *arg;
+} pool_t;
+typedef struct {
+  pool_t *pool;
+  int tid;
+} worker_arg;
+
+static void *pool_worker(void *a) {
+  worker_arg *w = (worker_arg *)a;
+  for (;;) {
+    int64_t i = atomic_fetch_add(&w->pool->next, 1);
+    if (i >= w->pool->total) break;
+    w->pool->fn(w->pool->arg, i, w->tid);
+  }
+  return NULL;
+}
+
+static int resolve_threads(int nthreads) {
+  if (nthreads > 0) return nthreads;
+  long c = sysconf(_SC_NPROCESSORS_ONLN);
+  return c > 0 ? (int)c : 1;
+}
+
+static void parallel_for(int64_t total, int nthreads, item_fn fn, void *arg) {
+  pool_t pool;
+  atomic_init(&pool.next, 0);
+  pool.total = total;
+  pool.fn = fn;
+  pool.arg = arg;
+  if (nthreads <= 1 || total <= 1) {
+    worker_arg w = {&pool, 0};
+    pool_worker(&w);
+    return;
+  }
+  pthread_t *th = (pthread_t *)malloc(sizeof(pthread_t) * (size_t)nthreads);
+  worker_arg *wa = (worker_arg *)malloc(sizeof(worker_arg) * (size_t)nthreads);
+  for (int t = 0; t < nthreads; t++) {
+    wa[t].pool = &pool;
+    wa[t].tid = t;
+    pthread_create(&th[t], NULL, pool_worker, &wa[t]);
+  }
+  for (int t = 0; t < nthreads; t++) pthread_join(th[t], NULL);
+  free(th);
+  free(wa);
+}
+
+int orc_num_threads(int nthreads) { return resolve_threads(nthreads); }
+
+/* ------------------------------------------------------------------ */
+/* Algorithm 1, RobustPrune(p, V, alpha, R), written once over an      */
+/* abstract distance oracle so that the Euclidean form (vectors) and  */
+/* the general-metric form (an explicit distance matrix) share the    */
+/* same loop.                                                          */
+/* ------------------------------------------------------------------ */
+
+typedef struct {
+  /* vector form */
+  const void *X;
+  int dtype;
+  int d;
+  int32_t A; /* alpha in milli-units */
+  /* matrix form */
+  const double *D;
+  int64_t n;
+  double alpha;
+  /* common */
+  int64_t p;
+} prune_env;
+
+/* key(p, v): D(p, v) as used for the argmin (squared for vectors). */
+static double piv_key(const prune_env *e, int64_t v) {
+  if (e->D) return e->D[e->p * e->n + v];
+  return d2_pts(e->X, e->dtype, e->d, e->p, v);
+}
+
+/* Does the newly kept point a remove candidate v?  alpha * D(a, v) <= D(p, v),
+   where key_v = D(p, v) as returned by piv_key. */
+static int dominates(const prune_env *e, int64_t a, int64_t v, double key_v) {
+  if (e->D) return e->alpha * e->D[a * e->n + v] <= key_v;
+  if (e->dtype == ORC_U8) {
+    const uint8_t *U = (const uint8_t *)e->X;
+    int64_t d2a = d2_u8(U + a * e->d, U + v * e->d, e->d);
+    int64_t d2b = (int64_t)key_v; /* exact: an integer below 2^53 */
+    return (int64_t)e->A * (int64_t)e->A * d2a <= (int64_t)1000000 * d2b;
+  }
+  const float *F = (const float *)e->X;
+  double d2a = d2_f32(F + a * e->d, F + v * e->d, e->d);
+  double A2 = (double)((int64_t)e->A * (int64_t)e->A);
+  return A2 * d2a <= 1e6 * key_v;
+}
+
+typedef struct {
+  int32_t id;
+  int64_t pos;
+} id_pos;
+
+static int by_id_then_pos(const void *a, const void *b) {
+  const id_pos *x = (const id_pos *)a, *y = (const id_pos *)b;
+  if (x->id != y->id) return (x->id > y->id) - (x->id < y->id);
+  return (x->pos > y->pos) - (x->pos < y->pos);
+}
+
+static int by_pos(const void *a, const void *b) {
+  const id_pos *x = (const id_pos *)a, *y = (const id_pos *)b;
+  return (x->pos > y->pos) - (x->pos < y->pos);
+}
+
+/*
+ * The loop of Algorithm 1.  cand[0..m) is V in stored order (may hold
+ * duplicates and p itself); out receives the new N_out(p) in the order points
+ * were added.  Returns |N_out(p)|.
+ */
+static int64_t robust_prune_env(const prune_env *e, const int32_t *cand, int64_t m,
+                                int32_t R, int variant, int32_t *out) {
+  /* V <- (V u N_out(p)) \ {p}, as a set; first occurrence keeps its place. */
+  int32_t *V = (int32_t *)malloc(sizeof(int32_t) * (size_t)(m > 0 ? m : 1));
+  double *key = (double *)malloc(sizeof(double) * (size_t)(m > 0 ? m : 1));
+  char *alive = (char *)malloc((size_t)(m > 0 ? m : 1));
+  id_pos *ip = (id_pos *)malloc(sizeof(id_pos) * (size_t)(m > 0 ? m : 1));
+  int64_t nip = 0, nv = 0;
+  for (int64_t j = 0; j < m; j++)
+    if ((int64_t)cand[j] != e->p) {
+      ip[nip].id = cand[j];
+      ip[nip].pos = j;
+      nip++;
+    }
+  qsort(ip, (size_t)nip, sizeof(id_pos), by_id_then_pos);
+  int64_t nu = 0;
+  for (int64_t j = 0; j < nip; j++)
+    if (j == 0 || ip[j].id != ip[j - 1].id) ip[nu++] = ip[j];
+  qsort(ip, (size_t)nu, sizeof(id_pos), by_pos);
+  for (int64_t j = 0; j < nu; j++) V[nv++] = ip[j].id;
+  free(ip);
+  for (int64_t j = 0; j < nv; j++) {
+    key[j] = piv_key(e, V[j]);
+    alive[j] = 1;
+  }
+  int64_t remaining = nv, kept = 0;
+  while (remaining > 0) {
+    /* p* <- argmin_{p' in V} D(p, p')  (sorted), or an arbitrary member of V:
+       the first one still present in stored order (unsorted). */
+    int64_t best = -1;
+    for (int64_t j = 0; j < nv; j++) {
+      if (!alive[j]) continue;
+      if (best < 0) { best = j; if (variant == ORC_UNSORTED) break; continue; }
+      if (key[j] < key[best] || (key[j] == key[best] && V[j] < V[best])) best = j;
+    }
+    int64_t ps = V[best];
+    out[kept++] = (int32_t)ps;
+    alive[best] = 0;
+    remaining--;
+    if (kept == (int64_t)R) break;
+    for (int64_t j = 0; j < nv; j++) {
+      if (!alive[j]) continue;
+      if (dominates(e, ps, V[j], key[j])) { alive[j] = 0; remaining--; }
+    }
+  }
+  free(V);
+  free(key);
+  free(alive);
+  return kept;
+}
+
+int64_t orc_robust_prune(const void *X, int dtype, int64_t n, int d, int64_t p,
+                         const int32_t *cand, int64_t m, int32_t A, int32_t R, int variant,
+                         int32_t *out) {
+  (void)n;
+  prune_env e;
+  memset(&e, 0, sizeof e);
+  e.X = X; e.dtype = dtype; e.d = d; e.A = A; e.p = p;
+  return robust_prune_env(&e, cand, m, R, variant, out);
+}
+
+int64_t orc_robust_prune_dmat(const double *D, int64_t n, int64_t p, const int32_t *cand,
+                              int64_t m, double alpha, int32_t R, int variant, int32_t *out) {
+  prune_env e;
+  memset(&e, 0, sizeof e);
+  e.D = D; e.n = n; e.alpha = alpha; e.p = p;
+  return robust_prune_env(&e, cand, m, R, variant, out);
+}
+
+/* ------------------------------------------------------------------ */
+/* RP-Tuning over a whole graph (§3), or over a list of nodes          */
+/* ------------------------------------------------------------------ */
+
+typedef struct {
+  const void *X;
+  int dtype, d;
+  int64_t n;
+  const int64_t *row_ptr;
+  const int32_t *col;
+  int32_t A, R;
+  int variant;
+  const int64_t *nodes;
+  int32_t *out_cnt;
+  int32_t *out_col;
+  int64_t cap;
+  int slow; /* 1: V = P \ {p} (slow preprocessing) */
+  int32_t **scratch;
+} tune_job;
+
+static void tune_item(void *arg, int64_t i, int tid) {
+  tune_job *J = (tune_job *)arg;
+  int64_t p = J->nodes ? J->nodes[i] : i;
+  int32_t *tmp = J->scratch[tid];
+  int64_t kept;
+  if (J->slow) {
+    int32_t *all = tmp + J->n; /* second half of the scratch */
+    int64_t m = 0;
+    for (int64_t v = 0; v < J->n; v++)
+      if (v != p) all[m++] = (int32_t)v;
+    kept = orc_robust_prune(J->X, J->dtype, J->n, J->d, p, all, m, J->A, J->R, J->variant, tmp);
+  } else {
+    int64_t a = J->row_ptr[p], b = J->row_ptr[p + 1];
+    kept = orc_robust_prune(J->X, J->dtype, J->n, J->d, p, J->col + a, b - a, J->A, J->R,
+                            J->variant, tmp);
+  }
+  if (kept > J->cap) kept = J->cap; /* caller sized cap >= max possible; never hit */
+  J->out_cnt[i] = (int32_t)kept;
+  memcpy(J->out_col + i * J->cap, tmp, sizeof(int32_t) * (size_t)kept);
+}
+
+static int run_tune(tune_job *J, int64_t count, int nthreads, int64_t scratch_len) {
+  int T = resolve_threads(nthreads);
+  J->scratch = (int32_t **)malloc(sizeof(int32_t *) * (size_t)T);
+  for (int t = 0; t < T; t++)
+    J->scratch[t] = (int32_t *)malloc(sizeof(int32_t) * (size_t)(scratch_len > 0 ? scratch_len : 1));
+  parallel_for(count, T, tune_item, J);
+  for (int t = 0; t < T; t++) free(J->scratch[t]);
+  free(J->scratch);
+  return 0;
+}
+
+/* out_cnt[i], out_col[i*cap ..] for node nodes[i] (or i when nodes == NULL). */
+int orc_rp_tune(const void *X, int dtype, int64_t n, int d, const int64_t *row_ptr,
+                const int32_t *col, int32_t A, int32_t R, int variant, const int64_t *nodes,
+                int64_t n_nodes, int nthreads, int32_t *out_cnt, int32_t *out_col, int64_t cap) {
+  tune_job J;
+  memset(&J, 0, sizeof J);
+  J.X = X; J.dtype = dtype; J.d = d; J.n = n; J.row_ptr = row_ptr; J.col = col;
+  J.A = A; J.R = R; J.variant = variant; J.nodes = nodes; J.out_cnt = out_cnt;
+  J.out_col = out_col; J.cap = cap;
+  int64_t maxdeg = 0;
+  for (int64_t p = 0; p < n; p++)
+    if (row_ptr[p + 1] - row_ptr[p] > maxdeg) maxdeg = row_ptr[p + 1] - row_ptr[p];
+  return run_tune(&J, nodes ? n_nodes : n, nthreads, maxdeg);
+}
+
+/* Slow preprocessing (§2.1, Lemma 2.2): RobustPrune(p, P \ {p}, alpha, R). */
+int orc_slow_base(const void *X, int dtype, int64_t n, int d, int32_t A, int32_t R, int variant,
+                  const int64_t *nodes, int64_t n_nodes, int nthreads, int32_t *out_cnt,
+                  int32_t *out_col, int64_t cap) {
+  tune_job J;
+  memset(&J, 0, sizeof J);
+  J.X = X; J.dtype = dtype; J.d = d; J.n = n; J.A = A; J.R = R; J.variant = variant;
+  J.nodes = nodes; J.out_cnt = out_cnt; J.out_col = out_col; J.cap = cap; J.slow = 1;
+  return run_tune(&J, nodes ? n_nodes : n, nthreads, 2 * n);
+}
+
+/* ------------------------------------------------------------------ */
+/* exact k nearest neighbours, ordered by (d2, id)                     */
+/* ------------------------------------------------------------------ */
+
+typedef struct {
+  const void *X;
+  int dtype, d;
+  int64_t n;
+  const void *Q;
+  const int64_t *qid;
+  int k;
+  int32_t *out_ids;
+  double *out_d2;
+} knn_job;
+
+static void knn_item(void *arg, int64_t i, int tid) {
+  (void)tid;
+  knn_job *J = (knn_job *)arg;
+  int32_t *ids = J->out_ids + i * J->k;
+  double *dd = J->out_d2 + i * J->k;
+  int cnt = 0;
+  size_t esz = J->dtype == ORC_U8 ? 1 : 4;
+  const void *q = J->qid ? (const char *)J->X + (size_t)J->qid[i] * (size_t)J->d * esz
+                         : (const char *)J->Q + (size_t)i * (size_t)J->d * esz;
+  int64_t self = J->qid ? J->qid[i] : -1;
+  for (int64_t v = 0; v < J->n; v++) {
+    if (v == self) continue;
+    double x = d2_vec(J->X, J->dtype, J->d, q, v);
+    /* keep the k smallest (d2, id) pairs seen so far, in order */
+    if (cnt == J->k) {
+      if (!(x < dd[cnt - 1])) continue; /* equal d2: larger id loses */
+      cnt--;
+    }
+    int pos = cnt;
+    while (pos > 0 && x < dd[pos - 1]) {
+      dd[pos] = dd[pos - 1];
+      ids[pos] = ids[pos - 1];
+      pos--;
+    }
+    dd[pos] = x;
+    ids[pos] = (int32_t)v;
+    cnt++;
+  }
+  for (int j = cnt; j < J->k; j++) {
+    ids[j] = -1;
+    dd[j] = INFINITY;
+  }
+}
+
+/* Queries are Q[i] (qid == NULL) or base points qid[i] with themselves excluded. */
+int orc_knn(const void *X, int dtype, int64_t n, int d, const void *Q, const int64_t *qid,
+            int64_t nq, int k, int nthreads, int32_t *out_ids, double *out_d2) {
+  knn_job J = {X, dtype, d, n, Q, qid, k, out_ids, out_d2};
+  parallel_for(nq, resolve_threads(nthreads), knn_item, &J);
+  return 0;
+}
+
+/* ------------------------------------------------------------------ */
+/* start vertex: the point nearest to the mean (§4.1 "medoid")         */
+/* ------------------------------------------------------------------ */
+
+int64_t orc_medoid(const void *X, int dtype, int64_t n, int d) {
+  if (n <= 0) return -1;
+  double *mean = (double *)calloc((size_t)d, sizeof(double));
+  for (int j = 0; j < d; j++) {
+    double s = 0.0;
+    for (int64_t i = 0; i < n; i++)
+      s = s + (dtype == ORC_U8 ? (double)((const uint8_t *)X)[i * d + j]
+                               : (double)((const float *)X)[i * d + j]);
+    mean[j] = s / (double)n;
+  }
+  int64_t best = -1;
+  double bd = 0.0;
+  for (int64_t i = 0; i < n; i++) {
+    double s = 0.0;
+    for (int j = 0; j < d; j++) {
+      double x = dtype == ORC_U8 ? (double)((const uint8_t *)X)[i * d + j]
+                                 : (double)((const float *)X)[i * d + j];
+      double t = x - mean[j];
+      s = s + t * t;
+    }
+    if (best < 0 || s < bd) { best = i; bd = s; }
+  }
+  free(mean);
+  return best;
+}
+
+/* ------------------------------------------------------------------ */
+/* Algorithm 2, GreedySearch(s, q, k, L)                               */
+/* ------------------------------------------------------------------ */
+
+typedef struct {
+  const void *X;
+  int dtype, d;
+  int64_t n;
+  const int64_t *row_ptr;
+  const int32_t *col;
+  int64_t start;
+  const void *Q;
+  int L, k;
+  int32_t *out_ids;
+  double *out_d2;
+  int64_t *out_expansions;
+  int64_t maxdeg;
+  /* per-thread scratch */
+  char **seen;
+  char **in_list;
+  char **visited;
+  int64_t **touched;
+} search_job;
+
+typedef struct {
+  double dist;
+  int32_t id;
+} entry;
+
+static int entry_cmp(const void *a, const void *b) {
+  const entry *x = (const entry *)a, *y = (const entry *)b;
+  if (x->dist < y->dist) return -1;
+  if (x->dist > y->dist) return 1;
+  return (x->id > y->id) - (x->id < y->id);
+}
+
+static void search_item(void *arg, int64_t qi, int tid) {
+  search_job *J = (search_job *)arg;
+  size_t esz = J->dtype == ORC_U8 ? 1 : 4;
+  const void *q = (const char *)J->Q + (size_t)qi * (size_t)J->d * esz;
+  char *seen = J->seen[tid];
+  char *inL = J->in_list[tid];
+  char *vis = J->visited[tid];
+  int64_t *touched = J->touched[tid]; /* every node marked during this query, once */
+  int64_t ntouched = 0;
+  entry *Lst = (entry *)malloc(sizeof(entry) * (size_t)(J->L + J->maxdeg + 1));
+  int64_t ls = 0, expansions = 0;
+  /* L <- {s}, V <- {} */
+  Lst[ls].dist = d2_vec(J->X, J->dtype, J->d, q, J->start);
+  Lst[ls].id = (int32_t)J->start;
+  ls++;
+  inL[J->start] = 1;
+  seen[J->start] = 1;
+  touched[ntouched++] = J->start;
+  for (;;) {
+    /* p* <- argmin over L \ V of D(p, q); ties to the smaller id */
+    int64_t best = -1;
+    for (int64_t j = 0; j < ls; j++) {
+      if (vis[Lst[j].id]) continue;
+      if (best < 0 || entry_cmp(&Lst[j], &Lst[best]) < 0) best = j;
+    }
+    if (best < 0) break; /* L \ V is empty */
+    int32_t ps = Lst[best].id;
+    expansions++;
+    /* L <- L u N_out(p*), V <- V u {p*} */
+    vis[ps] = 1;
+    for (int64_t e = J->row_ptr[ps]; e < J->row_ptr[ps + 1]; e++) {
+      int32_t v = J->col[e];
+      if (inL[v]) continue;
+      inL[v] = 1;
+      if (!seen[v]) { seen[v] = 1; touched[ntouched++] = v; }
+      Lst[ls].dist = d2_vec(J->X, J->dtype, J->d, q, v);
+      Lst[ls].id = v;
+      ls++;
+    }
+    /* if |L| > L, keep the L closest to q */
+    if (ls > J->L) {
+      qsort(Lst, (size_t)ls, sizeof(entry), entry_cmp);
+      for (int64_t j = J->L; j < ls; j++) inL[Lst[j].id] = 0;
+      ls = J->L;
+    }
+  }
+  qsort(Lst, (size_t)ls, sizeof(entry), entry_cmp);
+  for (int j = 0; j < J->k; j++) {
+    J->out_ids[qi * J->k + j] = j < ls ? Lst[j].id : -1;
+    J->out_d2[qi * J->k + j] = j < ls ? Lst[j].dist : INFINITY;
+  }
+  if (J->out_expansions) J->out_expansions[qi] = expansions;
+  /* reset this thread's marks for the next query */
+  for (int64_t j = 0; j < ntouched; j++) {
+    seen[touched[j]] = 0;
+    inL[touched[j]] = 0;
+    vis[touched[j]] = 0;
+  }
+  free(Lst);
+}
+
+int orc_greedy_search(const void *X, int dtype, int64_t n, int d, const int64_t *row_ptr,
+                      const int32_t *col, int64_t start, const void *Q, int64_t nq, int L, int k,
+                      int nthreads, int32_t *out_ids, double *out_d2, int64_t *out_expansions) {
+  if (L < k || k <= 0 || start < 0 || start >= n) return -1;
+  int T = resolve_threads(nthreads);
+  search_job J;
+  memset(&J, 0, sizeof J);
+  J.X = X; J.dtype = dtype; J.d = d; J.n = n; J.row_ptr = row_ptr; J.col = col;
+  J.start = start; J.Q = Q; J.L = L; J.k = k; J.out_ids = out_ids; J.out_d2 = out_d2;
+  J.out_expansions = out_expansions;
+  for (int64_t p = 0; p < n; p++)
+    if (row_ptr[p + 1] - row_ptr[p] > J.maxdeg) J.maxdeg = row_ptr[p + 1] - row_ptr[p];
+  J.seen = (char **)malloc(sizeof(char *) * (size_t)T);
+  J.in_list = (char **)malloc(sizeof(char *) * (size_t)T);
+  J.visited = (char **)malloc(sizeof(char *) * (size_t)T);
+  J.touched = (int64_t **)malloc(sizeof(int64_t *) * (size_t)T);
+  for (int t = 0; t < T; t++) {
+    J.seen[t] = (char *)calloc((size_t)n, 1);
+    J.in_list[t] = (char *)calloc((size_t)n, 1);
+    J.visited[t] = (char *)calloc((size_t)n, 1);
+    J.touched[t] = (int64_t *)malloc(sizeof(int64_t) * (size_t)n);
+  }
+  parallel_for(nq, T, search_item, &J);
+  for (int t = 0; t < T; t++) {
+    free(J.seen[t]);
+    free(J.in_list[t]);
+    free(J.visited[t]);
+    free(J.touched[t]);
+  }
+  free(J.seen);
+  free(J.in_list);
+  free(J.visited);
+  free(J.touched);
+  return 0;
+}
+
+/* ------------------------------------------------------------------ */
+/* reachability alpha*(G) (Definition 2.1)                             */
+/* ------------------------------------------------------------------ */
+/* alpha*(G) = min over ordered pairs (p, q), q != p, (p, q) not an edge, of
+   max over p' in N_out(p) of D(p, q) / D(p', q); D(p', q) = 0 makes q reachable
+   at every alpha (ratio +inf); a node with no out-neighbour gives ratio 0. */
+
+typedef struct {
+  const double *D2; /* n x n squared distances, or NULL */
+  const double *Dm; /* n x n distances (general metric), or NULL */
+  int64_t n;
+  const int64_t *row_ptr;
+  const int32_t *col;
+  double *per_node;
+} reach_job;
+
+static double rj_dist(const reach_job *J, int64_t a, int64_t b) {
+  return J->Dm ? J->Dm[a * J->n + b] : sqrt(J->D2[a * J->n + b]);
+}
+
+static void reach_item(void *arg, int64_t p, int tid) {
+  (void)tid;
+  reach_job *J = (reach_job *)arg;
+  double worst = INFINITY;
+  int64_t a = J->row_ptr[p], b = J->row_ptr[p + 1];
+  for (int64_t q = 0; q < J->n; q++) {
+    if (q == p) continue;
+    int edge = 0;
+    for (int64_t e = a; e < b; e++)
+      if (J->col[e] == q) { edge = 1; break; }
+    if (edge) continue;
+    double best = 0.0;
+    double dpq = rj_dist(J, p, q);
+    for (int64_t e = a; e < b; e++) {
+      double dd = rj_dist(J, J->col[e], q);
+      double r = dd == 0.0 ? INFINITY : dpq / dd;
+      if (r > best) best = r;
+    }
+    if (best < worst) worst = best;
+  }
+  J->per_node[p] = worst;
+}
+
+static double reach_run(reach_job *J, int nthreads) {
+  J->per_node = (double *)malloc(sizeof(double) * (size_t)(J->n > 0 ? J->n : 1));
+  parallel_for(J->n, resolve_threads(nthreads), reach_item, J);
+  double w = INFINITY;
+  for (int64_t p = 0; p < J->n; p++)
+    if (J->per_node[p] < w) w = J->per_node[p];
+  free(J->per_node);
+  return w;
+}
+
+double orc_reachability(const void *X, int dtype, int64_t n, int d, const int64_t *row_ptr,
+                        const int32_t *col, int nthreads) {
+  double *D2 = (double *)malloc(sizeof(double) * (size_t)(n * n > 0 ? n * n : 1));
+  for (int64_t a = 0; a < n; a++)
+    for (int64_t b = 0; b < n; b++) D2[a * n + b] = d2_pts(X, dtype, d, a, b);
+  reach_job J = {D2, NULL, n, row_ptr, col, NULL};
+  double r = reach_run(&J, nthreads);
+  free(D2);
+  return r;
+}
+
+double orc_reachability_dmat(const double *D, int64_t n, const int64_t *row_ptr,
+                             const int32_t *col) {
+  reach_job J = {NULL, D, n, row_ptr, col, NULL};
+  return reach_run(&J, 1);
+}
+
+/* canonical squared distances for a list of (a, b) base-point pairs */
+int orc_d2_pairs(const void *X, int dtype, int d, const int64_t *a, const int64_t *b,
+                 int64_t npairs, double *out) {
+  for (int64_t i = 0; i < npairs; i++) out[i] = d2_pts(X, dtype, d, a[i], b[i]);
+  return 0;
+}
+
+/* canonical squared distances from free vectors Q[i] to base points ids[i*k + j] */
+int orc_d2_query(const void *X, int dtype, int d, const void *Q, int64_t nq,
+                 const int32_t *ids, int k, double *out) {
+  size_t esz = dtype == ORC_U8 ? 1 : 4;
+  for (int64_t i = 0; i < nq; i++)
+    for (int j = 0; j < k; j++) {
+      int32_t v = ids[i * k + j];
+      out[i * k + j] = v < 0 ? INFINITY
+                             : d2_vec(X, dtype, d, (const char *)Q + (size_t)i * d * esz, v);
+    }
+  return 0;
+}

@@ -1,0 +1,374 @@
+"""Pins for the CPU oracle: what the paper and plain mathematics fix, independent
+of the oracle's own code.
+
+* Lemma 3.5 (collinear construction, unsorted) and the sorted counterpart,
+* Lemma 3.7 (general-metric distance matrix, sorted),
+* Appendix A (Euclidean construction of Lemma 3.8) and the worked numbers
+  printed after Table 1 (tests/golden/worked_example_alpha3_alpha2.json),
+* Lemma 2.2 (slow preprocessing gives an alpha-reachable graph),
+* Theorems 3.1 / 3.2 (reachability after RP-Tuning is at least the worst case),
+* Algorithm 1 invariants (characterisation of the kept set, subgraph,
+  idempotence, R-prefix, duplicate handling),
+* Algorithm 2 traced by hand (tests/golden/greedy_search_line.json) and its
+  reduction to exact kNN on a complete graph,
+* exact kNN against scipy's brute-force distances.
+"""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+
+import datagen
+import oracle
+from closed_forms import (appendix_a_points, beta_euc, sorted_euclid_bound,
+                          sorted_general_bound, unsorted_bound,
+                          unsorted_bound_as_printed)
+
+GOLD = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _gold(name):
+    with open(os.path.join(GOLD, name)) as f:
+        return json.load(f)
+
+
+def _csr(rows):
+    row_ptr = np.zeros(len(rows) + 1, dtype=np.int64)
+    np.cumsum([len(r) for r in rows], out=row_ptr[1:])
+    col = np.concatenate([np.asarray(r, dtype=np.int32) for r in rows]) if rows else np.zeros(0, np.int32)
+    return row_ptr, col.astype(np.int32)
+
+
+def _canon_d2_matrix(X):
+    """Exact squared distances: int64 for uint8; for float32 the binary64 sum
+    in index order, which is the canonical reading of the Euclidean distance."""
+    if X.dtype == np.uint8:
+        Y = X.astype(np.int64)
+        return ((Y[:, None, :] - Y[None, :, :]) ** 2).sum(-1)
+    Y = X.astype(np.float64)
+    s = np.zeros((X.shape[0], X.shape[0]))
+    for i in range(X.shape[1]):
+        t = Y[:, None, i] - Y[None, :, i]
+        s = s + t * t
+    return s
+
+
+def _dominated(D2, A, u, v, p):
+    if D2.dtype == np.int64:
+        return A * A * int(D2[u, v]) <= 1_000_000 * int(D2[p, v])
+    return float(A * A) * D2[u, v] <= 1e6 * D2[p, v]
+
+
+# ---------------------------------------------------------------- Lemma 3.5
+
+@pytest.mark.parametrize("dtype", [np.uint8, np.float32])
+def test_lemma_3_5_collinear_unsorted_is_tight(dtype):
+    # alpha1 = alpha2 = 2: p=0, z=1*4, y=z+z/alpha1=6, x=y+y/alpha2=9 on a line.
+    a1 = a2 = 2.0
+    X = np.array([[0], [4], [6], [9]], dtype=dtype)  # ids: p=0, z=1, y=2, x=3
+    p, z, y, x = 0, 1, 2, 3
+    # N_out(p) = {x, y} with x stored first; every other node links to all others.
+    assert oracle.robust_prune(X, p, [x, y], a2, variant="unsorted").tolist() == [x]
+    assert oracle.robust_prune(X, p, [x, y], a2, variant="sorted").tolist() == [y]
+    base = [[x, y], [0, 2, 3], [0, 1, 3], [0, 1, 2]]
+    rp, col = _csr(base)
+    # G is alpha1-reachable: z is reached from p through y with equality.
+    assert oracle.reachability(X, rp, col) == pytest.approx(a1, rel=1e-12)
+    after = [oracle.robust_prune(X, p, [x, y], a2, variant="unsorted").tolist()] + base[1:]
+    rp2, col2 = _csr(after)
+    # Theorem 3.1 is attained: alpha* = alpha1 alpha2 / (alpha1 + alpha2 + 1) = 0.8.
+    assert oracle.reachability(X, rp2, col2) == pytest.approx(unsorted_bound(a1, a2), rel=1e-12)
+    assert unsorted_bound(a1, a2) == pytest.approx(0.8)
+    assert unsorted_bound_as_printed(a1, a2) <= unsorted_bound(a1, a2)
+    after_s = [oracle.robust_prune(X, p, [x, y], a2, variant="sorted").tolist()] + base[1:]
+    rp3, col3 = _csr(after_s)
+    # Sorted processing keeps y, the witness for z: the pattern is ruled out (§3.2).
+    assert oracle.reachability(X, rp3, col3) >= a2 - 1e-12
+
+
+# ---------------------------------------------------------------- Lemma 3.7
+
+def _lemma37_matrix(a1, a2):
+    # ids: p=0, x=1, y=2, z=3; D(p,.)=1, D(y,z)=1/a1, D(x,y)=1/a2,
+    # D(x,z)=(a1+a2)/(a1 a2).  (The printed matrix swaps the labels x and z;
+    # this labelling is the one that satisfies the constraints of Lemma 3.6.)
+    D = np.zeros((4, 4))
+    D[0, 1:] = D[1:, 0] = 1.0
+    D[2, 3] = D[3, 2] = 1.0 / a1
+    D[1, 2] = D[2, 1] = 1.0 / a2
+    D[1, 3] = D[3, 1] = (a1 + a2) / (a1 * a2)
+    return D
+
+
+@pytest.mark.parametrize("a1,a2", [(4.0, 2.0), (2.0, 2.0)])
+def test_lemma_3_7_general_metric_sorted_is_tight(a1, a2):
+    D = _lemma37_matrix(a1, a2)
+    p, x, y, z = 0, 1, 2, 3
+    # Equal distances from p: the tie goes to the smaller id, so x is taken first
+    # and prunes y (alpha2 * D(x, y) = 1 <= D(p, y) = 1).
+    assert oracle.robust_prune_dmat(D, p, [y, x], a2, variant="sorted").tolist() == [x]
+    base = [[x, y], [0, 2, 3], [0, 1, 3], [0, 1, 2]]
+    rp, col = _csr(base)
+    assert oracle.reachability_dmat(D, rp, col) == pytest.approx(a1, rel=1e-12)
+    after = [oracle.robust_prune_dmat(D, p, [y, x], a2).tolist()] + base[1:]
+    rp2, col2 = _csr(after)
+    assert oracle.reachability_dmat(D, rp2, col2) == pytest.approx(sorted_general_bound(a1, a2), rel=1e-12)
+
+
+def test_worked_example_general_metric_value():
+    g = _gold("worked_example_alpha3_alpha2.json")
+    a1, a2 = g["alpha1"], g["alpha2"]
+    D = _lemma37_matrix(a1, a2)
+    kept = oracle.robust_prune_dmat(D, 0, [2, 1], a2)
+    assert kept.tolist() == [1]
+    ratio = D[0, 3] / D[kept[0], 3]
+    assert round(ratio, g["printed_digits"]) == g["general_sorted"]
+
+
+# ---------------------------------------------------------------- Appendix A
+
+@pytest.mark.parametrize("a1,a2", [(3.0, 2.0), (1.5, 1.2), (1.5, 1.1), (2.0, 1.5)])
+def test_appendix_a_euclidean_construction(a1, a2):
+    pts = appendix_a_points(a1, a2)  # p, x, y, z
+    P = np.array(pts, dtype=np.float64)
+    D = np.sqrt(((P[:, None, :] - P[None, :, :]) ** 2).sum(-1))
+    D[0, 1:] = D[1:, 0] = 1.0  # x, y, z lie on the unit circle around p
+    # The constraints of Lemma 3.8 hold with equality in the reals ...
+    assert D[2, 3] == pytest.approx(1.0 / a1, rel=1e-12)
+    assert D[1, 2] == pytest.approx(1.0 / a2, rel=1e-12)
+    # ... so prune with alpha2 a hair below its value to stay on the pruning side.
+    kept = oracle.robust_prune_dmat(D, 0, [2, 1], a2 * (1 - 1e-9))
+    assert kept.tolist() == [1]
+    ratio = D[0, 3] / D[1, 3]
+    assert ratio == pytest.approx(1.0 / beta_euc(a1, a2), rel=1e-12)
+    assert ratio >= sorted_general_bound(a1, a2)  # the Euclidean case is better (Table 1)
+
+
+def test_worked_example_euclidean_value():
+    g = _gold("worked_example_alpha3_alpha2.json")
+    a1, a2 = g["alpha1"], g["alpha2"]
+    P = np.array(appendix_a_points(a1, a2))
+    D = np.sqrt(((P[:, None, :] - P[None, :, :]) ** 2).sum(-1))
+    D[0, 1:] = D[1:, 0] = 1.0
+    kept = oracle.robust_prune_dmat(D, 0, [2, 1], a2 * (1 - 1e-9))
+    ratio = D[0, 3] / D[kept[0], 3]
+    assert round(ratio, g["printed_digits"]) == g["euclidean_sorted_approx"]
+    assert round(sorted_euclid_bound(a1, a2), 3) == g["euclidean_sorted_approx"]
+
+
+def test_appendix_a_vector_form_float32():
+    # The same construction as float32 vectors, nudged off the equality
+    # boundaries (x moved towards y and inwards) so the decisions are strict.
+    a1, a2 = 3.0, 2.0
+    t1 = math.asin(1 / (2 * a1))
+    t2 = math.asin(1 / (2 * a2)) * (1 - 1e-3)
+    y = (math.cos(2 * t1), math.sin(2 * t1))
+    x = tuple((1 - 1e-3) * c for c in (math.cos(2 * (t1 + t2)), math.sin(2 * (t1 + t2))))
+    X = np.array([(0, 0), x, y, (1, 0)], dtype=np.float32)
+    assert oracle.robust_prune(X, 0, [2, 1], a2).tolist() == [1]
+    d = lambda a, b: math.dist(X[a].astype(float), X[b].astype(float))
+    assert d(0, 3) / d(1, 3) == pytest.approx(1 / beta_euc(a1, a2), rel=5e-3)
+
+
+# ---------------------------------------------------------------- Algorithm 1 invariants
+
+def _check_prune_invariants(X, D2, p, cand, A, R, variant, kept):
+    V = []
+    for v in cand:
+        if v != p and v not in V:
+            V.append(int(v))
+    kept = [int(v) for v in kept]
+    assert set(kept) <= set(V), "output must be a subset of the candidates"
+    assert len(set(kept)) == len(kept)
+    assert len(kept) <= R
+    if variant == "sorted":
+        order = sorted(V, key=lambda v: (D2[p, v], v))
+    else:
+        order = V
+    pos = {v: i for i, v in enumerate(order)}
+    assert [pos[v] for v in kept] == sorted(pos[v] for v in kept), "kept in processing order"
+    # every kept point is not dominated by an earlier kept point
+    for i, v in enumerate(kept):
+        for u in kept[:i]:
+            assert not _dominated(D2, A, u, v, p)
+    # every dropped point is dominated by a kept point processed before it,
+    # unless the degree bound was reached before it came up
+    last = pos[kept[-1]] if kept else -1
+    for v in V:
+        if v in kept:
+            continue
+        dom = any(_dominated(D2, A, u, v, p) for u in kept if pos[u] < pos[v])
+        assert dom or (len(kept) == R and pos[v] > last)
+    # the set is uniquely determined by those two facts: rebuild it greedily
+    K = []
+    for v in order:
+        if len(K) == R:
+            break
+        if not any(_dominated(D2, A, u, v, p) for u in K):
+            K.append(v)
+    assert K == kept
+
+
+@pytest.mark.parametrize("dtype", [np.uint8, np.float32])
+@pytest.mark.parametrize("variant", ["sorted", "unsorted"])
+def test_robust_prune_characterisation(dtype, variant):
+    rng = np.random.default_rng(7)
+    for trial in range(40):
+        n = int(rng.integers(5, 40))
+        d = int(rng.choice([1, 2, 3, 8, 17]))
+        if dtype == np.uint8:
+            X = rng.integers(0, 6 if trial % 3 == 0 else 256, size=(n, d)).astype(np.uint8)
+        else:
+            X = rng.normal(size=(n, d)).astype(np.float32)
+            if trial % 4 == 0:
+                X[1] = X[2]  # identical vectors: distance 0
+        D2 = _canon_d2_matrix(X)
+        p = int(rng.integers(0, n))
+        cand = rng.integers(0, n, size=int(rng.integers(0, 2 * n))).tolist() + [p]
+        rng.shuffle(cand)
+        for alpha in (1.0, 1.05, 1.2, 1.5, 2.0):
+            A = int(round(alpha * 1000))
+            for R in (1, 3, oracle.R_INF):
+                kept = oracle.robust_prune(X, p, cand, alpha, R, variant)
+                _check_prune_invariants(X, D2, p, cand, A, R, variant, kept)
+
+
+def test_duplicates_and_self_loops_are_ignored():
+    X = datagen.dataset("tiny", 50)
+    cand = [3, 7, 3, 0, 12, 7, 0, 40, 12]
+    ref = oracle.robust_prune(X, 0, [3, 7, 12, 40], 1.1)
+    assert oracle.robust_prune(X, 0, cand, 1.1).tolist() == ref.tolist()
+    # unsorted: first occurrences keep their positions
+    assert oracle.robust_prune(X, 0, cand, 1.1, variant="unsorted").tolist() == \
+        oracle.robust_prune(X, 0, [3, 7, 12, 40], 1.1, variant="unsorted").tolist()
+
+
+@pytest.fixture(scope="module")
+def tiny_base():
+    X = datagen.dataset("tiny")
+    rp, col = oracle.slow_base(X, 1.5)
+    return X, rp, col
+
+
+def test_lemma_2_2_slow_preprocessing_is_alpha_reachable(tiny_base):
+    X, rp, col = tiny_base
+    assert oracle.reachability(X, rp, col) >= 1.5
+    # and on integer data
+    U = datagen.dataset("sift", 300)
+    rpu, colu = oracle.slow_base(U, 1.2)
+    assert oracle.reachability(U, rpu, colu) >= 1.2
+
+
+@pytest.mark.parametrize("a2", [1.2, 1.1])
+def test_theorems_3_1_3_2_reachability_after_tuning(tiny_base, a2):
+    X, rp, col = tiny_base
+    a1 = 1.5
+    rps, cols = oracle.rp_tune(X, rp, col, a2, oracle.R_INF, "sorted")
+    assert oracle.reachability(X, rps, cols) >= sorted_euclid_bound(a1, a2)
+    rpu, colu = oracle.rp_tune(X, rp, col, a2, oracle.R_INF, "unsorted")
+    assert oracle.reachability(X, rpu, colu) >= unsorted_bound(a1, a2)
+
+
+def _rows(rp, col):
+    return [col[rp[i]:rp[i + 1]].tolist() for i in range(rp.shape[0] - 1)]
+
+
+def test_subgraph_idempotence_and_r_prefix(tiny_base):
+    X, rp, col = tiny_base
+    base_rows = _rows(rp, col)
+    # identity: re-pruning the base at its own alpha with no bound changes nothing
+    rpi, coli = oracle.rp_tune(X, rp, col, 1.5, oracle.R_INF)
+    assert _rows(rpi, coli) == base_rows
+    for a in (1.2, 1.0):
+        rpa, cola = oracle.rp_tune(X, rp, col, a, 32)
+        rows = _rows(rpa, cola)
+        assert all(set(r) <= set(b) for r, b in zip(rows, base_rows))
+        rpb, colb = oracle.rp_tune(X, rpa, cola, a, 32)
+        assert _rows(rpb, colb) == rows
+        rpc, colc = oracle.rp_tune(X, rp, col, a, 8)
+        assert _rows(rpc, colc) == [r[:8] for r in rows]
+
+
+# ---------------------------------------------------------------- Algorithm 2
+
+def test_greedy_search_hand_trace():
+    g = _gold("greedy_search_line.json")
+    X = np.array(g["points_1d_u8"], dtype=np.uint8)[:, None]
+    n = X.shape[0]
+    rows = [[v for v in (i - 1, i + 1) if 0 <= v < n] for i in range(n)]
+    rp, col = _csr(rows)
+    Q = np.array([[g["query_1d_u8"]]], dtype=np.uint8)
+    ids, d2, exp = oracle.greedy_search(X, rp, col, g["start"], Q, g["L"], g["k"])
+    assert ids[0].tolist() == g["expected_ids"]
+    assert d2[0].tolist() == g["expected_d2"]
+    assert int(exp[0]) == g["expected_expansions"]
+
+
+@pytest.mark.parametrize("dtype", [np.uint8, np.float32])
+def test_greedy_search_complete_graph_is_exact(dtype):
+    scipy_dist = pytest.importorskip("scipy.spatial.distance")
+    rng = np.random.default_rng(3)
+    n, d = 120, 6
+    X = (rng.integers(0, 4, size=(n, d)) if dtype == np.uint8 else rng.normal(size=(n, d))).astype(dtype)
+    Q = (rng.integers(0, 4, size=(9, d)) if dtype == np.uint8 else rng.normal(size=(9, d))).astype(dtype)
+    rows = [[v for v in range(n) if v != i] for i in range(n)]
+    rp, col = _csr(rows)
+    for L, k in ((10, 10), (40, 7)):
+        ids, _, _ = oracle.greedy_search(X, rp, col, 5, Q, L, k)
+        D = scipy_dist.cdist(Q.astype(np.float64), X.astype(np.float64), "sqeuclidean")
+        for i in range(Q.shape[0]):
+            ref = np.lexsort((np.arange(n), D[i]))[:k]
+            assert ids[i].tolist() == ref.tolist()
+
+
+def test_greedy_search_pads_unreachable():
+    X = np.arange(6, dtype=np.uint8)[:, None]
+    rows = [[1], [0], [3], [2], [5], [4]]  # three components
+    rp, col = _csr(rows)
+    ids, d2, _ = oracle.greedy_search(X, rp, col, 0, np.array([[5]], np.uint8), 4, 4)
+    assert ids[0].tolist() == [1, 0, -1, -1]
+    assert np.isinf(d2[0, 2:]).all()
+
+
+# ---------------------------------------------------------------- kNN and medoid
+
+@pytest.mark.parametrize("dtype", [np.uint8, np.float32])
+def test_knn_matches_library_brute_force(dtype):
+    scipy_dist = pytest.importorskip("scipy.spatial.distance")
+    rng = np.random.default_rng(11)
+    n, d, k = 500, 12, 25
+    X = (rng.integers(0, 3, size=(n, d)) if dtype == np.uint8 else rng.normal(size=(n, d))).astype(dtype)
+    Q = X[:30] if dtype == np.uint8 else rng.normal(size=(30, d)).astype(dtype)
+    ids, d2 = oracle.knn(X, k, Q=Q)
+    D = scipy_dist.cdist(Q.astype(np.float64), X.astype(np.float64), "sqeuclidean")
+    for i in range(Q.shape[0]):
+        ref = np.lexsort((np.arange(n), D[i]))[:k]  # many exact ties for uint8
+        assert ids[i].tolist() == ref.tolist()
+        np.testing.assert_allclose(d2[i], D[i, ref], rtol=1e-12)
+    # base points as queries exclude themselves
+    ids2, _ = oracle.knn(X, k, qid=np.arange(10))
+    for i in range(10):
+        Di = scipy_dist.cdist(X[i:i + 1].astype(np.float64), X.astype(np.float64), "sqeuclidean")[0]
+        order = [v for v in np.lexsort((np.arange(n), Di)) if v != i][:k]
+        assert ids2[i].tolist() == order
+
+
+def test_medoid_is_nearest_to_mean():
+    X = datagen.dataset("tiny")
+    m = X.astype(np.float64).mean(0)
+    d = ((X.astype(np.float64) - m) ** 2).sum(1)
+    assert oracle.medoid(X) == int(np.argmin(d))
+    U = datagen.dataset("sift", 3000)
+    mu = U.astype(np.float64).mean(0)
+    du = ((U.astype(np.float64) - mu) ** 2).sum(1)
+    assert oracle.medoid(U) == int(np.argmin(du))
+
+
+def test_reachability_small_line():
+    # points 0, 1, 3 on a line; edges 0->1, 1->2, 2->1
+    X = np.array([[0], [1], [3]], dtype=np.uint8)
+    rp, col = _csr([[1], [2], [1]])
+    # non-edges: (0,2): D(0,2)/D(1,2) = 3/2; (1,0): D(1,0)/D(2,0) = 1/3; (2,0): D(2,0)/D(1,0) = 3
+    assert oracle.reachability(X, rp, col) == pytest.approx(1 / 3, rel=1e-12)
