@@ -1,0 +1,466 @@
+#!/usr/bin/env python
+"""Benchmark of the RP-Tuning hot path on one GB300 (per rank under torchrun).
+
+Workload (SIFT-shaped, uint8): n = 1,000,000 points, d = 128, values
+rint(min(255, Gamma(0.6, 40))); base graph = RobustPrune(1.2, 64) over each
+point's exact 128 nearest neighbours, built once by the library (not timed);
+targets (alpha, R) = (1.1, 64), (1.05, 48), (1.0, 32); 10,000 queries,
+L = 128, k = 100.
+
+One timed step = the whole hot path over that input: RP-Tuning of every node
+for the three targets in one batched launch (gather, keys, Gram, sort,
+domination bits, scans, CSR emit), GreedySearch of the 10,000 queries on each
+tuned graph and recall@100 of each against the exact kNN ground truth.
+`value` = nodes x targets / second over the timed steps (inputs resident in
+HBM, L2 flushed before every step).  `e2e` repeats the step through the C ABI
+with host buffers: vectors, base CSR and queries copied in, tuned graphs and
+search results copied out, every step.
+
+`--impl reference` times the CPU oracle (the reference arm of this build) on
+a bounded sample of the same workload and prints the same JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import datagen  # noqa: E402
+
+METRIC = "RP-Tuning nodes/s per α (batched vs plain, same GPU); query p50/p99 at recall@100"
+UNIT = "nodes/s per alpha"
+TARGETS = [(1.1, 64), (1.05, 48), (1.0, 32)]
+BASE_ALPHA, BASE_R, KCAND = 1.2, 64, 128
+L_SEARCH, K_SEARCH = 128, 100
+
+
+def workload_name(n, nq):
+    return (f"sift-shaped uint8 n={n:,} d=128; base RobustPrune(1.2,64) over exact kNN-128; "
+            f"tune (1.1,64),(1.05,48),(1.0,32); {nq:,} queries L=128 k=100")
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def load_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[5:9]):
+                if val.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ---------------------------------------------------------------- reference arm / CPU baseline
+
+def oracle_sample(n_sample, rank_seed=0):
+    """The oracle's own base rows over a prefix of the same dataset (no GPU input)."""
+    import oracle
+    X = datagen.dataset("sift", n_sample)
+    t0 = time.perf_counter()
+    base_rp, base_col = oracle.knn_base(X, KCAND, BASE_ALPHA, BASE_R)
+    return X, base_rp, base_col, time.perf_counter() - t0
+
+
+def time_oracle_tune(X, base_rp, base_col):
+    import oracle
+    t0 = time.perf_counter()
+    for a, r in TARGETS:
+        oracle.rp_tune(X, base_rp, base_col, a, r)
+    return time.perf_counter() - t0
+
+
+def cpu_baseline(n_sample=20000):
+    import oracle
+    X, brp, bcol, build_s = oracle_sample(n_sample)
+    secs, reps = 0.0, 0
+    while secs < 10.0 or reps < 1:  # about ten seconds of CPU work
+        secs += time_oracle_tune(X, brp, bcol)
+        reps += 1
+    Q = datagen.queries("sift", 200)
+    start = oracle.medoid(X)
+    t0 = time.perf_counter()
+    oracle.greedy_search(X, brp, bcol, start, Q, L_SEARCH, K_SEARCH)
+    qs = time.perf_counter() - t0
+    return {"value": reps * n_sample * len(TARGETS) / secs, "unit": UNIT, "cores": oracle.num_threads(0),
+            "kind": "oracle",
+            "sample": (f"oracle RP-Tuning of all {n_sample:,} nodes of a {n_sample:,}-point prefix of the same "
+                       f"dataset (its own kNN-128 -> RobustPrune(1.2,64) base), 3 targets, repeated {reps}x "
+                       f"({secs:.1f} s); GreedySearch of 200 queries {200 / qs:.1f} QPS"),
+            "search_qps": 200 / qs}
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    import oracle
+    n_sample = args.ref_sample
+    X, brp, bcol, _ = oracle_sample(n_sample)
+    for _ in range(args.warmup):
+        time_oracle_tune(X, brp, bcol)
+    times = [time_oracle_tune(X, brp, bcol) for _ in range(args.steps)]
+    tot = sum(times)
+    value = n_sample * len(TARGETS) * args.steps / tot
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * tot / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u8",
+            "data": "synthetic", "config": {"workload": workload_name(args.n, args.nq),
+                                            "reference_sample_nodes": n_sample},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": oracle.num_threads(0), "kind": "oracle",
+                             "sample": f"RP-Tuning of a {n_sample:,}-point prefix (its own base), 3 targets per step"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------- our arm
+
+def run_ours(args):
+    import torch
+    import paper_2602_08097_gb300 as rp
+    from paper_2602_08097_gb300 import build as b
+
+    ws, rank, local = dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    b.build()
+    n, nq, k = args.n, args.nq, K_SEARCH
+    X = datagen.dataset("sift", n)
+    Q = datagen.queries("sift", nq)
+    stream = torch.cuda.Stream(device=dev)
+    ctx = rp.rp_create(local, stream=stream)
+    alphas = [a for a, _ in TARGETS]
+    Rs = [r for _, r in TARGETS]
+    T = len(TARGETS)
+
+    # ---- fixture (not timed): vectors, base graph, ground truth
+    t0 = time.perf_counter()
+    data = rp.rp_load_graph(ctx, X)
+    base = rp.rp_build_knn_base(ctx, data, KCAND, BASE_ALPHA, BASE_R)
+    base_rp, base_col = rp.rp_graph_export(ctx, base)
+    gt, _ = rp.rp_knn(ctx, data, Q, k)
+    fixture_s = time.perf_counter() - t0
+    deg = np.diff(base_rp)
+    Qd = torch.from_numpy(Q).to(dev)
+    gtd = torch.from_numpy(gt).to(dev)
+    ids_d = [torch.empty((nq, k), dtype=torch.int32, device=dev) for _ in range(T)]
+    dist_d = [torch.empty((nq, k), dtype=torch.float32, device=dev) for _ in range(T)]
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
+
+    stats_acc = {"prune_ms": [], "emit_ms": [], "search_ms": []}
+
+    def step(record):
+        outs = rp.rp_tune_batch(ctx, base, alphas, Rs)
+        if record:
+            st = rp.rp_stats(ctx)
+            stats_acc["prune_ms"].append(st["last_prune_ms"])
+            stats_acc["emit_ms"].append(st["last_emit_ms"])
+        sms = 0.0
+        for i, g in enumerate(outs):
+            rp.rp_search(ctx, g, Qd, L_SEARCH, k, ids=ids_d[i], dists=dist_d[i])
+            if record:
+                sms += rp.rp_stats(ctx)["last_search_ms"]
+        if record:
+            stats_acc["search_ms"].append(sms)
+        hits = [rp.rp_recall(ctx, ids_d[i], gtd, k) for i in range(T)]
+        return outs, hits
+
+    def free(outs):
+        for g in outs:
+            rp.rp_graph_free(ctx, g)
+
+    nnz = None
+    for _ in range(args.warmup):
+        outs, hits = step(False)
+        if nnz is None:
+            nnz = [rp.rp_graph_info(ctx, g)["nnz"] for g in outs]
+        free(outs)
+    torch.cuda.synchronize(dev)
+    if ws > 1:
+        torch.distributed.barrier()
+    l0 = rp.rp_stats(ctx)["kernel_launches"]
+    times = []
+    recalls = None
+    with ClockSampler(local) as clocks:
+        for _ in range(args.steps):
+            with torch.cuda.stream(stream):
+                flush.zero_()  # evict L2 (129 MB) before every timed step
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            outs, hits = step(False)
+            e1.record(stream)
+            stream.synchronize()
+            times.append(e0.elapsed_time(e1))
+            recalls = [h / (nq * k) for h in hits]
+            if nnz is None:
+                nnz = [rp.rp_graph_info(ctx, g)["nnz"] for g in outs]
+            free(outs)
+    launches = rp.rp_stats(ctx)["kernel_launches"] - l0
+    torch.cuda.synchronize(dev)
+    tot_ms = sum(times)
+    if ws > 1:
+        t = torch.tensor([tot_ms], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        torch.distributed.barrier()
+        tot_ms = float(t.item())
+    value = ws * n * T * args.steps / (tot_ms / 1000.0)
+
+    # ---- per-kernel timing pass (same step, phase events read between calls)
+    for _ in range(max(2, args.steps)):
+        with torch.cuda.stream(stream):
+            flush.zero_()
+        outs, _ = step(True)
+        free(outs)
+    prune_ms = statistics.mean(stats_acc["prune_ms"])
+    emit_ms = statistics.mean(stats_acc["emit_ms"])
+    search_ms = statistics.mean(stats_acc["search_ms"])
+    alg_bytes = float(((deg + 1) * 128 + 4 * deg + 8).sum() + 4 * sum(nnz))
+    hbm_peak, peak_kind = load_peaks()
+    achieved = alg_bytes / (prune_ms / 1000.0) / 1e9
+    traffic = None
+    prof = os.path.join(ROOT, "profiles", "prune_fast_u8_sift1m_traffic.json")
+    if os.path.exists(prof):
+        with open(prof) as f:
+            pj = json.load(f)
+        if pj.get("kernel_source_hash") == kernel_hash():
+            traffic = pj.get("traffic_bytes_per_launch")
+
+    # ---- plain vs batched tuning alone
+    def time_tune(batched, reps):
+        ts = []
+        for r in range(reps + 2):
+            with torch.cuda.stream(stream):
+                flush.zero_()
+            a0 = torch.cuda.Event(enable_timing=True)
+            a1 = torch.cuda.Event(enable_timing=True)
+            a0.record(stream)
+            if batched:
+                outs = rp.rp_tune_batch(ctx, base, alphas, Rs)
+            else:
+                outs = [rp.rp_tune(ctx, base, a, R) for a, R in TARGETS]
+            a1.record(stream)
+            stream.synchronize()
+            if r >= 2:
+                ts.append(a0.elapsed_time(a1))
+            free(outs)
+        return statistics.median(ts)
+
+    tb = time_tune(True, args.steps)
+    tp = time_tune(False, args.steps)
+
+    # ---- single-query latency (batch size 1), on the (1.05, 48) graph
+    outs = rp.rp_tune_batch(ctx, base, alphas, Rs)
+    g1 = outs[1]
+    lat = []
+    q1 = [Qd[i:i + 1] for i in range(min(300, nq))]
+    i1 = torch.empty((1, k), dtype=torch.int32, device=dev)
+    d1 = torch.empty((1, k), dtype=torch.float32, device=dev)
+    for i, q in enumerate(q1):
+        a0 = torch.cuda.Event(enable_timing=True)
+        a1 = torch.cuda.Event(enable_timing=True)
+        a0.record(stream)
+        rp.rp_search(ctx, g1, q, L_SEARCH, k, ids=i1, dists=d1)
+        a1.record(stream)
+        stream.synchronize()
+        if i >= 20:
+            lat.append(a0.elapsed_time(a1))
+    free(outs)
+    lat.sort()
+    p50 = lat[len(lat) // 2]
+    p99 = lat[min(len(lat) - 1, int(0.99 * len(lat)))]
+
+    # ---- end to end through the C ABI with host buffers
+    e2e = None
+    if not args.no_e2e:
+        Xh = torch.from_numpy(X).pin_memory()
+        rph = torch.from_numpy(base_rp).pin_memory()
+        colh = torch.from_numpy(base_col).pin_memory()
+        Qh = torch.from_numpy(Q).pin_memory()
+        gth = torch.from_numpy(gt).pin_memory()
+        idh = [torch.empty((nq, k), dtype=torch.int32).pin_memory() for _ in range(T)]
+        dh = [torch.empty((nq, k), dtype=torch.float32).pin_memory() for _ in range(T)]
+        out_rp = [torch.empty(n + 1, dtype=torch.int64).pin_memory() for _ in range(T)]
+        out_col = [torch.empty(base_col.shape[0], dtype=torch.int32).pin_memory() for _ in range(T)]
+        lib = rp.load_library()
+        import ctypes
+
+        def e2e_step():
+            g = rp.rp_load_graph(ctx, Xh, rph, colh)
+            outs = rp.rp_tune_batch(ctx, g, alphas, Rs)
+            h2d = X.nbytes + base_rp.nbytes + base_col.nbytes
+            d2h = 0
+            hits = []
+            for i, t in enumerate(outs):
+                rp.rp_search(ctx, t, Qh, L_SEARCH, k, ids=idh[i], dists=dh[i])
+                h2d += Q.nbytes
+                d2h += idh[i].numel() * 4 + dh[i].numel() * 4
+                hits.append(rp.rp_recall(ctx, idh[i], gth, k))
+                h2d += idh[i].numel() * 4 + gth.numel() * 4
+                rc = lib.rp_graph_export(ctx, int(t), ctypes.c_void_p(out_rp[i].data_ptr()),
+                                         ctypes.c_void_p(out_col[i].data_ptr()), int(out_col[i].numel()),
+                                         rp.RP_MEM_HOST)
+                if rc != 0:
+                    raise rp.RPError(rc, rp.rp_last_error(ctx))
+                d2h += (n + 1) * 8 + nnz[i] * 4
+            for t in outs:
+                rp.rp_graph_free(ctx, t)
+            rp.rp_graph_free(ctx, g)
+            return h2d, d2h
+
+        for _ in range(1):
+            e2e_step()
+        torch.cuda.synchronize(dev)
+        et = []
+        for _ in range(max(2, min(args.steps, 5))):
+            t1 = time.perf_counter()
+            h2d, d2h = e2e_step()
+            torch.cuda.synchronize(dev)
+            et.append(time.perf_counter() - t1)
+        e2e_s = statistics.mean(et)
+        e2e = {"value": ws * n * T / e2e_s, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+               "d2h_bytes_per_step": int(d2h), "ms_per_step": 1000 * e2e_s}
+
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(args.cpu_sample)
+
+    rp.rp_destroy(ctx)
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": tot_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "u8", "data": "synthetic",
+            "config": {"workload": workload_name(n, nq), "n": n, "d": 128, "targets": TARGETS,
+                       "queries": nq, "L": L_SEARCH, "k": k, "l2": "flushed (512 MB write) before every timed step",
+                       "parallelism": f"replicas x{ws}" if ws > 1 else "1 GPU"},
+            "roofline": {"bound": "hbm", "kernel": "prune_fast_kernel<u8,64>", "achieved": achieved,
+                         "peak": hbm_peak, "unit": "GB/s", "frac": achieved / hbm_peak, "traffic": traffic,
+                         "peak_kind": peak_kind, "algorithmic_bytes_per_launch": alg_bytes,
+                         "launch_ms": prune_ms},
+            "cpu_baseline": cpu,
+            "e2e": e2e,
+            "gpu_launches": int(launches),
+            "clocks": clocks.summary(),
+            "tune_batched_nodes_per_s_per_alpha": n * T / (tb / 1000.0),
+            "tune_plain_nodes_per_s_per_alpha": n * T / (tp / 1000.0),
+            "batched_over_plain": tp / tb,
+            "phase_ms": {"prune": prune_ms, "emit": emit_ms, "search_3x": search_ms},
+            "search_qps": 3 * nq / (search_ms / 1000.0),
+            "query_latency_ms_bs1": {"p50": p50, "p99": p99},
+            "recall_at_100": dict(zip([f"{a},{r}" for a, r in TARGETS], recalls)),
+            "avg_degree": {"base": float(deg.mean()), **{f"{a},{r}": nz / n for (a, r), nz in zip(TARGETS, nnz)}},
+            "fixture_s": fixture_s,
+        }
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+def kernel_hash():
+    import hashlib
+    h = hashlib.sha256()
+    for f in ("prune.cu", "common.cuh"):
+        with open(os.path.join(ROOT, "paper_2602_08097_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--n", type=int, default=1_000_000)
+    ap.add_argument("--nq", type=int, default=10_000)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-sample", type=int, default=20000)
+    ap.add_argument("--ref-sample", type=int, default=20000)
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl == "ours":
+        print("note: timing rules ask for >= 3 warm-up steps", file=sys.stderr)
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,247 @@
+/*
+ * rp.h -- C ABI of the GB300 RP-Tuning library (librp.so).
+ *
+ * RP-Tuning (§3, "RP-Tuning" paragraph) re-runs RobustPrune (Algorithm 1) on
+ * every node of an existing graph, each node reading only its own input
+ * out-neighbour list, to lower alpha and/or the degree bound R without
+ * rebuilding the index.  GreedySearch (Algorithm 2) from the medoid (§4.1)
+ * queries the tuned graph.  Everything below runs in this library's own CUDA
+ * kernels on one GPU.
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ * - Every call returns an rp_status.  RP_OK is 0; errors are negative.  On an
+ *   error, rp_last_error(ctx) returns a message owned by the context and valid
+ *   until the next call on that context.  No C++ exception and no abort ever
+ *   crosses this boundary.  A device-side problem found by a kernel (a bad
+ *   index in an input graph, a canonical-tie run that could not be resolved)
+ *   is reported as RP_EDEVICE with the first offending index in the message;
+ *   kernels never trap.
+ * - Vectors are row-major, n rows of d elements, element type RP_U8 (uint8)
+ *   or RP_F32 (IEEE binary32).  Distances are squared Euclidean (the paper
+ *   uses Euclidean distance for every dataset, §4.1); ordering by squared
+ *   distance equals ordering by distance.
+ * - Graphs are CSR: row_ptr int64[n+1] (row_ptr[0] = 0, non-decreasing),
+ *   col int32[row_ptr[n]], ids in [0, n).  N_out(p) = col[row_ptr[p] ..
+ *   row_ptr[p+1]).
+ * - mem_flags = RP_MEM_HOST: pointers are host memory; the call copies inputs
+ *   in, and copies outputs back before returning.  RP_MEM_DEVICE: pointers
+ *   are device memory on the context's device; the call reads and writes them
+ *   in order on the context's stream and may return before the work is done
+ *   (rp_sync waits).  Input buffers are borrowed only for the duration of the
+ *   call (until the stream reaches it, for device pointers).
+ * - Graph handles (rp_graph) name device-resident graphs owned by the
+ *   context.  They stay resident until rp_graph_free or rp_destroy.  A tuned
+ *   graph shares the vectors of the graph it was tuned from.
+ * - alpha must be >= 1 and a multiple of 0.001 (|1000 alpha - round(1000
+ *   alpha)| < 1e-6); it is carried exactly as A = round(1000 alpha).  The
+ *   domination test alpha * D(p*, v) <= D(p, v) of Algorithm 1 is evaluated
+ *   as A^2 * d2(p*, v) <= 10^6 * d2(p, v): exactly in integers for RP_U8, and
+ *   for RP_F32 with the same decision as the binary64 expression
+ *   fl(A^2 * d2a) <= fl(1e6 * d2b) where d2 is summed in index order in
+ *   binary64 without fused multiply-add (decisions whose single-precision
+ *   margin is below a rigorous error bound are recomputed that way on the GPU).
+ * - R >= 1; RP_R_INF (INT32_MAX) means no degree bound, as RP-Tuning is
+ *   stated in §3.
+ * - Calls on one context are serialised by the context; use one context per
+ *   host thread for concurrency.
+ */
+#ifndef RP_H_
+#define RP_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct rp_ctx rp_ctx;
+typedef int32_t rp_status;
+typedef int64_t rp_graph;
+
+enum {
+  RP_OK = 0,
+  RP_EINVAL = -1,    /* bad argument or malformed input */
+  RP_ENOMEM = -2,    /* the request would exceed the context's HBM budget */
+  RP_ECUDA = -3,     /* a CUDA runtime call failed */
+  RP_ETIMEOUT = -4,  /* a bounded wait ran out */
+  RP_ENOTFOUND = -5, /* unknown graph handle */
+  RP_EDEVICE = -6    /* a kernel reported a problem through its status word */
+};
+
+enum { RP_U8 = 1, RP_F32 = 2 };
+enum { RP_SORTED = 0, RP_UNSORTED = 1 };
+enum { RP_MEM_HOST = 0, RP_MEM_DEVICE = 1 };
+
+#define RP_R_INF INT32_MAX
+/* Largest out-degree a graph may have after cleaning (rp_load_graph). */
+#define RP_MAX_DEGREE 8192
+/* Largest beam width L accepted by rp_search. */
+#define RP_MAX_L 1024
+
+/*
+ * rp_create: make a context on CUDA device `device`.
+ *   hbm_budget_bytes: cap on the device memory the context may hold at once
+ *     (vectors, graphs and scratch); 0 means "no cap beyond the device".
+ *   cuda_stream: a cudaStream_t to order all work on (e.g. PyTorch's current
+ *     stream), or NULL for a stream the context creates and owns.
+ * Errors: RP_EINVAL (no such device, out == NULL), RP_ECUDA.
+ */
+rp_status rp_create(rp_ctx **out, int32_t device, uint64_t hbm_budget_bytes, void *cuda_stream);
+
+/* rp_destroy: wait for outstanding work, free every graph and the context. */
+rp_status rp_destroy(rp_ctx *ctx);
+
+/* rp_last_error: message for the last failed call on ctx ("" if none). */
+const char *rp_last_error(const rp_ctx *ctx);
+
+/* rp_sync: block until all work enqueued on the context's stream is done,
+ * then report any device status word raised since the last check. */
+rp_status rp_sync(rp_ctx *ctx);
+
+/*
+ * rp_load_graph: make vectors and a graph resident (§2, a graph index
+ * G = (P, E) over the dataset P; Algorithm 1's first step drops p from its
+ * own candidate set and treats N_out(p) as a set).
+ *   vectors: n x d elements of `dtype`, row-major.
+ *   row_ptr, col: the graph in CSR; row_ptr == NULL loads the vectors with
+ *     an empty graph (every out-degree 0), e.g. as the data source of
+ *     rp_build_knn_base.
+ *   start: the GreedySearch start vertex, or -1 for the medoid, read as the
+ *     data point nearest (binary64, index-order sums) to the binary64 mean
+ *     vector, ties to the smaller id (§4.1 names the medoid; this reading
+ *     keeps it computable at n = 10^7).
+ * Cleaning: self loops are dropped and repeated ids keep their first
+ * occurrence; the cleaned graph is what every later call sees.  Counts of
+ * dropped entries are available through rp_stats.
+ * Errors: RP_EINVAL (n < 1, d < 1, bad dtype, row_ptr not monotone, an id
+ *   outside [0, n), a cleaned out-degree above RP_MAX_DEGREE, start >= n);
+ *   RP_ENOMEM (over budget); RP_ECUDA.
+ */
+rp_status rp_load_graph(rp_ctx *ctx, const void *vectors, int32_t dtype, int64_t n, int32_t d,
+                        const int64_t *row_ptr, const int32_t *col, int32_t start,
+                        int32_t mem_flags, rp_graph *base_out);
+
+/*
+ * rp_tune: RP-Tuning (§3) of graph `src` to one target: for every node p,
+ * N_out'(p) = RobustPrune(p, N_out(p), alpha, R) (Algorithm 1), computed from
+ * src's lists only.  variant RP_SORTED takes p* = argmin D(p, .) with ties to
+ * the smaller id; RP_UNSORTED (UnsortedRobustPrune, §3) takes the first
+ * remaining candidate in src's stored order.  The new list of p holds the
+ * kept points in the order they were added.  The result is a new graph
+ * sharing src's vectors; *out receives its handle.
+ * Errors: RP_ENOTFOUND, RP_EINVAL (alpha off the 0.001 grid or < 1, R < 1,
+ *   bad variant), RP_ENOMEM, RP_ECUDA, RP_EDEVICE.
+ */
+rp_status rp_tune(rp_ctx *ctx, rp_graph src, double alpha, int32_t R, int32_t variant,
+                  rp_graph *out);
+
+/*
+ * rp_tune_batch: T targets (alphas[t], Rs[t]) of the same source in one
+ * persistent launch; each node's sort, pairwise distances and margins are
+ * computed once and shared by all targets.  outs[t] receives the graph that
+ * rp_tune(src, alphas[t], Rs[t], variant) would return (identical edges and
+ * order).  1 <= T <= 16.  Repeated calls with the same (src, targets,
+ * variant) replay a captured CUDA graph.
+ * Errors: as rp_tune; RP_EINVAL for T outside [1, 16].
+ */
+rp_status rp_tune_batch(rp_ctx *ctx, rp_graph src, const double *alphas, const int32_t *Rs,
+                        int32_t T, int32_t variant, rp_graph *outs);
+
+/*
+ * rp_graph_info: n, number of edges, largest out-degree and start vertex of
+ * a graph (waits for the graph to be complete).  Any output pointer may be
+ * NULL.  Errors: RP_ENOTFOUND, RP_ECUDA.
+ */
+rp_status rp_graph_info(rp_ctx *ctx, rp_graph g, int64_t *n, int64_t *nnz, int32_t *max_deg,
+                        int64_t *start);
+
+/*
+ * rp_graph_export: copy a graph out as CSR (row_ptr int64[n+1], col
+ * int32[nnz]) into caller buffers; col_cap is the capacity of col in
+ * elements.  Errors: RP_ENOTFOUND, RP_EINVAL (col_cap < nnz; call
+ * rp_graph_info for nnz), RP_ECUDA.
+ */
+rp_status rp_graph_export(rp_ctx *ctx, rp_graph g, int64_t *row_ptr, int32_t *col,
+                          int64_t col_cap, int32_t mem_flags);
+
+/*
+ * rp_search: GreedySearch(s, q, k, L) (Algorithm 2) on graph g for each of
+ * the nq query rows (nq x d, the graph's dtype), s = the graph's start
+ * vertex.  L is the search list size, L >= k (Algorithm 2's input condition).
+ * The list is ordered by (distance, id); the loop ends when every member has
+ * been expanded; the k closest members are returned.
+ *   ids: int32[nq * k]; -1 where fewer than k points were reached.
+ *   dists: float[nq * k] squared distances (exact integers for RP_U8; for
+ *     RP_F32 single precision, with orderings decided as in binary64), +inf
+ *     where ids is -1.  dists may be NULL.
+ * Errors: RP_ENOTFOUND, RP_EINVAL (nq < 0, k < 1, L < k, L > RP_MAX_L),
+ *   RP_ENOMEM, RP_ECUDA.
+ */
+rp_status rp_search(rp_ctx *ctx, rp_graph g, const void *queries, int64_t nq, int32_t L,
+                    int32_t k, int32_t *ids, float *dists, int32_t mem_flags);
+
+/*
+ * rp_knn: exact k nearest neighbours by brute force over the vectors of
+ * graph g, ordered by (distance, id) -- the ground truth of k-recall@k (§4).
+ *   queries: nq x d rows of g's dtype, or NULL to use the base points
+ *     0 .. nq-1 themselves, each excluded from its own list.
+ *   ids int32[nq * k], dists float[nq * k] (dists may be NULL); -1 / +inf pad.
+ * Errors: RP_ENOTFOUND, RP_EINVAL (k < 1 or k > 1024, nq > n when queries
+ *   is NULL), RP_ENOMEM, RP_ECUDA, RP_EDEVICE.
+ */
+rp_status rp_knn(rp_ctx *ctx, rp_graph g, const void *queries, int64_t nq, int32_t k,
+                 int32_t *ids, float *dists, int32_t mem_flags);
+
+/*
+ * rp_recall: k-recall@k (§4: the share of the true k nearest neighbours
+ * found among the k returned).  found: int32[nq * ld_found], truth:
+ * int32[nq * ld_truth]; the first k entries of each row are compared;
+ * negative ids never match.  *hits receives the total number of matches,
+ * so recall = hits / (nq * k).
+ * Errors: RP_EINVAL (k < 1, ld < k), RP_ECUDA.
+ */
+rp_status rp_recall(rp_ctx *ctx, const int32_t *found, int32_t ld_found, const int32_t *truth,
+                    int32_t ld_truth, int64_t nq, int32_t k, int64_t *hits, int32_t mem_flags);
+
+/*
+ * rp_build_knn_base: a base graph for tuning, built as RobustPrune(p, kNN(p),
+ * alpha, R) for every p (Algorithm 1 over each point's exact `kcand` nearest
+ * neighbours, excluding p).  The paper's base graphs are Vamana graphs
+ * (§4.1); this kNN-candidate form stands in for them.  Uses the vectors of
+ * graph `data`; *out shares them.  1 <= kcand <= 128.
+ * Errors: as rp_knn and rp_tune.
+ */
+rp_status rp_build_knn_base(rp_ctx *ctx, rp_graph data, int32_t kcand, double alpha, int32_t R,
+                            rp_graph *out);
+
+/* rp_graph_free: release a graph (its vectors are freed with the last graph
+ * that uses them).  Errors: RP_ENOTFOUND. */
+rp_status rp_graph_free(rp_ctx *ctx, rp_graph g);
+
+/* Counters of the context since rp_create (or the last reset). */
+typedef struct {
+  int64_t nodes_pruned;        /* node x target pairs processed by the prune kernels */
+  int64_t fp64_decisions;      /* domination tests settled by the binary64 recheck */
+  int64_t fp64_sort_keys;      /* pivot keys recomputed in binary64 to order near-ties */
+  int64_t fp64_search_dists;   /* search distances recomputed in binary64 for ordering */
+  int64_t self_loops_dropped;  /* rp_load_graph cleaning */
+  int64_t duplicates_dropped;  /* rp_load_graph cleaning */
+  int64_t generic_nodes;       /* nodes handled by the large-degree path */
+  int64_t graph_replays;       /* rp_tune_batch calls served from a captured CUDA graph */
+  uint64_t bytes_in_use;       /* device bytes held by the context */
+  uint64_t bytes_peak;
+  int64_t kernel_launches;     /* kernels of this library launched (graph replays included) */
+  float last_prune_ms;         /* device time of the prune kernels of the last tuning call */
+  float last_emit_ms;          /* device time of its CSR emit (scan + compaction) */
+  float last_search_ms;        /* device time of the last rp_search kernel */
+} rp_stats_t;
+
+rp_status rp_stats(rp_ctx *ctx, rp_stats_t *out, int32_t reset);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* RP_H_ */

@@ -1,0 +1,245 @@
+"""Python binding of librp.so (the C ABI in include/rp.h), argument marshalling only.
+
+Every function here has the name of the C entry point it calls and does no
+computation of its own: numpy arrays are passed as host memory
+(RP_MEM_HOST), CUDA torch tensors as device memory (RP_MEM_DEVICE), and all
+work runs in the library's kernels.  There is no fallback: if librp.so is
+missing or cannot be loaded, :func:`load_library` raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "librp.so")
+
+RP_OK, RP_EINVAL, RP_ENOMEM, RP_ECUDA, RP_ETIMEOUT, RP_ENOTFOUND, RP_EDEVICE = 0, -1, -2, -3, -4, -5, -6
+RP_U8, RP_F32 = 1, 2
+RP_SORTED, RP_UNSORTED = 0, 1
+RP_MEM_HOST, RP_MEM_DEVICE = 0, 1
+RP_R_INF = 2**31 - 1
+RP_MAX_DEGREE = 8192
+RP_MAX_L = 1024
+
+_NAMES = {RP_EINVAL: "RP_EINVAL", RP_ENOMEM: "RP_ENOMEM", RP_ECUDA: "RP_ECUDA", RP_ETIMEOUT: "RP_ETIMEOUT",
+          RP_ENOTFOUND: "RP_ENOTFOUND", RP_EDEVICE: "RP_EDEVICE"}
+
+
+class RPError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{_NAMES.get(code, code)}: {msg}")
+        self.code = code
+
+
+class rp_stats_t(ctypes.Structure):
+    _fields_ = [("nodes_pruned", ctypes.c_int64), ("fp64_decisions", ctypes.c_int64),
+                ("fp64_sort_keys", ctypes.c_int64), ("fp64_search_dists", ctypes.c_int64),
+                ("self_loops_dropped", ctypes.c_int64), ("duplicates_dropped", ctypes.c_int64),
+                ("generic_nodes", ctypes.c_int64), ("graph_replays", ctypes.c_int64),
+                ("bytes_in_use", ctypes.c_uint64), ("bytes_peak", ctypes.c_uint64),
+                ("kernel_launches", ctypes.c_int64), ("last_prune_ms", ctypes.c_float),
+                ("last_emit_ms", ctypes.c_float), ("last_search_ms", ctypes.c_float)]
+
+
+_lib = None
+
+
+def load_library(path: str = LIB_PATH):
+    """Load librp.so (built by ``paper_2602_08097_gb300.build.build()``); raises if absent."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise ImportError(f"librp.so not found at {path}: build it with __graft_entry__.build()")
+    lib = ctypes.CDLL(path)
+    P, i32, i64, u64, dbl = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_uint64, ctypes.c_double
+    sig = {
+        "rp_create": [ctypes.POINTER(P), i32, u64, P],
+        "rp_destroy": [P],
+        "rp_sync": [P],
+        "rp_load_graph": [P, P, i32, i64, i32, P, P, i32, i32, ctypes.POINTER(i64)],
+        "rp_tune": [P, i64, dbl, i32, i32, ctypes.POINTER(i64)],
+        "rp_tune_batch": [P, i64, P, P, i32, i32, P],
+        "rp_graph_info": [P, i64, ctypes.POINTER(i64), ctypes.POINTER(i64), ctypes.POINTER(i32), ctypes.POINTER(i64)],
+        "rp_graph_export": [P, i64, P, P, i64, i32],
+        "rp_search": [P, i64, P, i64, i32, i32, P, P, i32],
+        "rp_knn": [P, i64, P, i64, i32, P, P, i32],
+        "rp_recall": [P, P, i32, P, i32, i64, i32, ctypes.POINTER(i64), i32],
+        "rp_build_knn_base": [P, i64, i32, dbl, i32, ctypes.POINTER(i64)],
+        "rp_graph_free": [P, i64],
+        "rp_stats": [P, ctypes.POINTER(rp_stats_t), i32],
+    }
+    for name, args in sig.items():
+        fn = getattr(lib, name)
+        fn.argtypes = args
+        fn.restype = i32
+    lib.rp_last_error.argtypes = [P]
+    lib.rp_last_error.restype = ctypes.c_char_p
+    _lib = lib
+    return lib
+
+
+def _check(ctx, rc):
+    if rc != RP_OK:
+        msg = load_library().rp_last_error(ctx).decode(errors="replace") if ctx else ""
+        raise RPError(rc, msg)
+
+
+def _is_torch(x):
+    return type(x).__module__.split(".")[0] == "torch"
+
+
+def _mem(*arrays):
+    kinds = {("dev" if (_is_torch(a) and a.is_cuda) else "host") for a in arrays if a is not None}
+    if len(kinds) > 1:
+        raise TypeError("mix of host and device buffers in one call")
+    return RP_MEM_DEVICE if kinds == {"dev"} else RP_MEM_HOST
+
+
+def _ptr(a):
+    if a is None:
+        return None
+    if _is_torch(a):
+        if not a.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return ctypes.c_void_p(a.data_ptr())
+    if not a.flags["C_CONTIGUOUS"]:
+        raise ValueError("array must be C-contiguous")
+    return ctypes.c_void_p(a.ctypes.data)
+
+
+def _dtype_code(x):
+    name = str(x.dtype).split(".")[-1]
+    if name == "uint8":
+        return RP_U8
+    if name == "float32":
+        return RP_F32
+    raise TypeError(f"vectors must be uint8 or float32, got {x.dtype}")
+
+
+def _empty_like_mem(mem, shape, np_dtype, device=None):
+    if mem == RP_MEM_HOST:
+        return np.empty(shape, dtype=np_dtype)
+    import torch
+    tdt = {np.int32: torch.int32, np.float32: torch.float32, np.int64: torch.int64}[np_dtype]
+    return torch.empty(shape, dtype=tdt, device=device)
+
+
+def rp_create(device: int = 0, hbm_budget_bytes: int = 0, stream=None):
+    """Returns an opaque context handle.  ``stream``: a torch.cuda.Stream, a raw handle or None."""
+    lib = load_library()
+    h = stream.cuda_stream if hasattr(stream, "cuda_stream") else stream
+    out = ctypes.c_void_p()
+    rc = lib.rp_create(ctypes.byref(out), int(device), int(hbm_budget_bytes), ctypes.c_void_p(h) if h else None)
+    _check(None, rc)
+    return out
+
+
+def rp_destroy(ctx):
+    _check(None, load_library().rp_destroy(ctx))
+
+
+def rp_last_error(ctx) -> str:
+    return load_library().rp_last_error(ctx).decode(errors="replace")
+
+
+def rp_sync(ctx):
+    _check(ctx, load_library().rp_sync(ctx))
+
+
+def rp_load_graph(ctx, vectors, row_ptr=None, col=None, start: int = -1) -> int:
+    mem = _mem(vectors, row_ptr, col)
+    n, d = int(vectors.shape[0]), int(vectors.shape[1])
+    out = ctypes.c_int64()
+    _check(ctx, load_library().rp_load_graph(ctx, _ptr(vectors), _dtype_code(vectors), n, d, _ptr(row_ptr),
+                                             _ptr(col), int(start), mem, ctypes.byref(out)))
+    return out.value
+
+
+def rp_tune(ctx, src: int, alpha: float, R: int = RP_R_INF, variant: int = RP_SORTED) -> int:
+    out = ctypes.c_int64()
+    _check(ctx, load_library().rp_tune(ctx, int(src), float(alpha), int(R), int(variant), ctypes.byref(out)))
+    return out.value
+
+
+def rp_tune_batch(ctx, src: int, alphas, Rs, variant: int = RP_SORTED):
+    T = len(alphas)
+    a = (ctypes.c_double * T)(*[float(x) for x in alphas])
+    r = (ctypes.c_int32 * T)(*[int(x) for x in Rs])
+    outs = (ctypes.c_int64 * T)()
+    _check(ctx, load_library().rp_tune_batch(ctx, int(src), a, r, T, int(variant), outs))
+    return list(outs)
+
+
+def rp_graph_info(ctx, g: int):
+    n, nnz, start = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+    md = ctypes.c_int32()
+    _check(ctx, load_library().rp_graph_info(ctx, int(g), ctypes.byref(n), ctypes.byref(nnz), ctypes.byref(md),
+                                             ctypes.byref(start)))
+    return dict(n=n.value, nnz=nnz.value, max_degree=md.value, start=start.value)
+
+
+def rp_graph_export(ctx, g: int, device=None):
+    """Returns (row_ptr int64[n+1], col int32[nnz]) as numpy arrays, or torch tensors on ``device``."""
+    info = rp_graph_info(ctx, g)
+    mem = RP_MEM_DEVICE if device is not None else RP_MEM_HOST
+    rp = _empty_like_mem(mem, (info["n"] + 1,), np.int64, device)
+    col = _empty_like_mem(mem, (max(info["nnz"], 1),), np.int32, device)
+    _check(ctx, load_library().rp_graph_export(ctx, int(g), _ptr(rp), _ptr(col), int(col.shape[0]), mem))
+    if mem == RP_MEM_DEVICE:
+        rp_sync(ctx)
+    return rp, col[:info["nnz"]]
+
+
+def rp_search(ctx, g: int, queries, L: int, k: int, ids=None, dists=None):
+    """GreedySearch for every row of ``queries``; returns (ids[nq,k], dists[nq,k])."""
+    mem = _mem(queries, ids, dists)
+    nq = int(queries.shape[0])
+    dev = queries.device if mem == RP_MEM_DEVICE else None
+    if ids is None:
+        ids = _empty_like_mem(mem, (nq, k), np.int32, dev)
+    if dists is None:
+        dists = _empty_like_mem(mem, (nq, k), np.float32, dev)
+    _check(ctx, load_library().rp_search(ctx, int(g), _ptr(queries), nq, int(L), int(k), _ptr(ids), _ptr(dists), mem))
+    return ids, dists
+
+
+def rp_knn(ctx, g: int, queries, k: int, nq: int | None = None, ids=None, dists=None):
+    """Exact kNN of ``queries`` (or of base points 0..nq-1 when queries is None)."""
+    mem = _mem(queries, ids, dists) if queries is not None else (_mem(ids) if ids is not None else RP_MEM_HOST)
+    nq = int(queries.shape[0]) if queries is not None else int(nq)
+    dev = (queries.device if queries is not None else ids.device) if mem == RP_MEM_DEVICE else None
+    if ids is None:
+        ids = _empty_like_mem(mem, (nq, k), np.int32, dev)
+    if dists is None:
+        dists = _empty_like_mem(mem, (nq, k), np.float32, dev)
+    _check(ctx, load_library().rp_knn(ctx, int(g), _ptr(queries), nq, int(k), _ptr(ids), _ptr(dists), mem))
+    return ids, dists
+
+
+def rp_recall(ctx, found, truth, k: int) -> int:
+    """Total matches between the first k ids of each row of found and truth."""
+    mem = _mem(found, truth)
+    hits = ctypes.c_int64()
+    _check(ctx, load_library().rp_recall(ctx, _ptr(found), int(found.shape[1]), _ptr(truth), int(truth.shape[1]),
+                                         int(found.shape[0]), int(k), ctypes.byref(hits), mem))
+    return hits.value
+
+
+def rp_build_knn_base(ctx, data: int, kcand: int, alpha: float, R: int) -> int:
+    out = ctypes.c_int64()
+    _check(ctx, load_library().rp_build_knn_base(ctx, int(data), int(kcand), float(alpha), int(R), ctypes.byref(out)))
+    return out.value
+
+
+def rp_graph_free(ctx, g: int):
+    _check(ctx, load_library().rp_graph_free(ctx, int(g)))
+
+
+def rp_stats(ctx, reset: bool = False) -> dict:
+    s = rp_stats_t()
+    _check(ctx, load_library().rp_stats(ctx, ctypes.byref(s), int(bool(reset))))
+    return {name: getattr(s, name) for name, _ in rp_stats_t._fields_}

@@ -1,0 +1,109 @@
+// Internal host-side declarations shared by the library's translation units.
+#pragma once
+
+#include <algorithm>
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "common.cuh"
+
+namespace rpk {
+
+// Vectors on the device: rows padded to a multiple of 128 bytes with zeros
+// (padding changes no distance).
+struct DevData {
+  const uint8_t* X = nullptr;
+  int64_t row_bytes = 0;
+  int64_t n = 0;
+  int d = 0;
+  int dtype = 0;
+};
+
+// A source graph for the prune kernels.
+struct PruneLaunch {
+  DevData data;
+  const int64_t* row_ptr = nullptr;
+  const int32_t* col = nullptr;
+  const int32_t* bucket_nodes[3] = {nullptr, nullptr, nullptr};  // deg<=64, <=128, >128
+  const int32_t* bucket_count = nullptr;                          // device int[3]
+  int64_t host_bucket_count[3] = {0, 0, 0};
+  int host_max_degree = 0;
+  int T = 0;
+  int variant = 0;
+  int32_t A[kMaxTargets];
+  int32_t R[kMaxTargets];
+  int32_t* out_col[kMaxTargets];  // scratch, same offsets as row_ptr
+  int32_t* out_cnt[kMaxTargets];  // per node
+  unsigned int* work = nullptr;   // device unsigned[3], zeroed before the launch
+  DevStatus* status = nullptr;
+  int num_sms = 0;
+};
+
+// prune.cu
+cudaError_t launch_bucket_nodes(const int64_t* row_ptr, int64_t n, int32_t* lists /* 3*n */,
+                                int32_t* counts /* 3 */, cudaStream_t s);
+cudaError_t launch_prune(const PruneLaunch& L, cudaStream_t s);
+// counts -> row_ptr (per target) and compaction of kept ids into col.
+cudaError_t launch_emit_csr(int64_t n, int T, const int64_t* src_row_ptr,
+                            int32_t* const* scratch_col, int32_t* const* cnt,
+                            int64_t* const* dst_row_ptr, int32_t* const* dst_col,
+                            int64_t* block_sums /* T * nblk */, cudaStream_t s);
+int64_t emit_csr_blocks(int64_t n);
+
+// prep.cu
+cudaError_t launch_pad_rows(const void* src, int64_t n, int64_t src_row_bytes, uint8_t* dst,
+                            int64_t dst_row_bytes, cudaStream_t s);
+cudaError_t launch_check_finite(const DevData& D, DevStatus* st, cudaStream_t s);
+cudaError_t launch_validate_csr(const int64_t* row_ptr, const int32_t* col, int64_t n,
+                                int64_t nnz, DevStatus* st, cudaStream_t s);
+cudaError_t launch_clean_count(const int64_t* row_ptr, const int32_t* col, int64_t n,
+                               int32_t* cnt, unsigned long long* dropped /* [2] */,
+                               cudaStream_t s);
+cudaError_t launch_clean_write(const int64_t* row_ptr, const int32_t* col, int64_t n,
+                               const int64_t* new_row_ptr, int32_t* new_col, cudaStream_t s);
+cudaError_t launch_scan_counts(const int32_t* cnt, int64_t n, int64_t* row_ptr,
+                               int64_t* block_sums, int32_t* max_deg, cudaStream_t s);
+cudaError_t launch_medoid(const DevData& D, double* mean /* d */, double* block_best /* 2*nb */,
+                          int64_t* medoid, cudaStream_t s);
+int64_t medoid_blocks(int64_t n);
+
+// search.cu
+struct SearchLaunch {
+  DevData data;
+  const int64_t* row_ptr = nullptr;
+  const int32_t* col = nullptr;
+  int64_t start = 0;
+  const uint8_t* Q = nullptr;  // padded rows like data
+  int64_t nq = 0;
+  int L = 0;
+  int k = 0;
+  int32_t* out_ids = nullptr;
+  float* out_dists = nullptr;
+  uint32_t* seen_bits = nullptr;  // per slot: n bits (words)
+  int64_t seen_words = 0;         // words per slot
+  int32_t* seen_list = nullptr;   // per slot: list of set ids, for clearing
+  int64_t seen_list_cap = 0;
+  int slots = 0;
+  unsigned int* work = nullptr;   // zeroed
+  DevStatus* status = nullptr;
+  int max_degree = 0;
+};
+cudaError_t launch_search(const SearchLaunch& S, cudaStream_t s);
+int search_slots(int num_sms);
+cudaError_t launch_recall(const int32_t* found, int ld_found, const int32_t* truth, int ld_truth,
+                          int64_t nq, int k, unsigned long long* hits, cudaStream_t s);
+
+// knn.cu
+struct KnnLaunch {
+  DevData data;
+  const uint8_t* Q = nullptr;  // padded query rows, or nullptr for base points 0..nq-1
+  int64_t nq = 0;
+  int k = 0;
+  int32_t* out_ids = nullptr;
+  float* out_dists = nullptr;
+  DevStatus* status = nullptr;
+  int num_sms = 0;
+};
+cudaError_t launch_knn(const KnnLaunch& K, cudaStream_t s);
+
+}  // namespace rpk

@@ -1,0 +1,784 @@
+// RP-Tuning prune kernels (§3, "RP-Tuning": RobustPrune(p, N_out(p), alpha, R)
+// for every node p, each reading only the input graph) and the CSR emit.
+//
+// Per node p with m = |N_out(p)| candidates (Algorithm 1):
+//   a2 gather    the rows of p and of its m candidates, 128-byte slices at a
+//                time, into shared memory (cp.async, 16-byte copies);
+//   a3 keys      d2(p, v) for every candidate v;
+//   a5 Gram      d2(u, v) for every candidate pair (difference form);
+//   a4 sort      processing order = ascending (d2(p, v), id) -- the argmin of
+//                Algorithm 1 taken in one go, ties to the smaller id -- or the
+//                stored order for UnsortedRobustPrune;
+//   a6 decide    for every target t and every pair u before v in that order,
+//                bit "u removes v": alpha_t * D(u, v) <= D(p, v);
+//   a7 scan      per target: keep the first live candidate, stop at R_t, drop
+//                every candidate the kept one removes (warp-free bit scan);
+//   a8 emit      kept ids in kept order into per-target scratch, then counts
+//                -> row_ptr (scan) -> compacted col.
+// Because removal is only ever done by kept points, "take the argmin of the
+// live set" (Algorithm 1) and "walk the sorted order, skipping removed
+// points" pick the same sequence; the bit scan is the latter.
+//
+// Fast path: m <= 64 (two nodes per 128-thread CTA, 64 threads each) and
+// 64 < m <= 128 (one node per CTA).  Larger degrees take the generic path
+// (one node per 256-thread CTA, lazy distances, no Gram in shared memory).
+#include "internal.h"
+
+namespace rpk {
+
+namespace {
+
+constexpr int kSlice = 128;  // bytes of every row staged per slice
+constexpr int kPitch = 144;  // shared-memory row pitch (16 bytes of padding)
+
+struct PruneArgs {
+  const uint8_t* X;
+  int64_t row_bytes;
+  int d;
+  const int64_t* row_ptr;
+  const int32_t* col;
+  const int32_t* nodes;
+  const int32_t* count;
+  unsigned int* work;
+  int T;
+  int variant;
+  int32_t A[kMaxTargets];
+  int32_t R[kMaxTargets];
+  int32_t* out_col[kMaxTargets];
+  int32_t* out_cnt[kMaxTargets];
+  DevStatus* status;
+};
+
+template <int MAXM>
+struct FastLayout {
+  static constexpr int MW = MAXM / 64;
+  static constexpr size_t off_D = 0;
+  static constexpr size_t off_slice = off_D + size_t(MAXM) * MAXM * 4;
+  static constexpr size_t off_skey = off_slice + size_t(MAXM + 1) * kPitch;
+  static constexpr size_t off_key64 = off_skey + size_t(MAXM) * 8;
+  static constexpr size_t off_masks = off_key64 + size_t(MAXM) * 8;
+  __host__ __device__ static size_t off_ids(int T) { return off_masks + size_t(T) * MW * MAXM * 8; }
+  __host__ __device__ static size_t off_perm(int T) { return off_ids(T) + size_t(MAXM) * 4; }
+  __host__ __device__ static size_t off_key(int T) { return off_perm(T) + size_t(MAXM) * 4; }
+  __host__ __device__ static size_t off_lnk(int T) { return off_key(T) + size_t(MAXM) * 4; }
+  __host__ __device__ static size_t off_misc(int T) { return off_lnk(T) + size_t(MAXM); }
+  __host__ __device__ static size_t bytes(int T) { return (off_misc(T) + 32 + 127) & ~size_t(127); }
+};
+
+template <int DT>
+struct Acc;
+template <>
+struct Acc<kU8> {
+  using T = unsigned;
+  __device__ static __forceinline__ T step(uint2 x, uint2 y, T acc) {
+    acc = sqdiff4_u8(x.x, y.x, acc);
+    return sqdiff4_u8(x.y, y.y, acc);
+  }
+  __device__ static __forceinline__ T step4(uint4 x, uint4 y, T acc) {
+    acc = sqdiff4_u8(x.x, y.x, acc);
+    acc = sqdiff4_u8(x.y, y.y, acc);
+    acc = sqdiff4_u8(x.z, y.z, acc);
+    return sqdiff4_u8(x.w, y.w, acc);
+  }
+  __device__ static __forceinline__ unsigned long long bits(T v) { return v; }
+};
+template <>
+struct Acc<kF32> {
+  using T = float;
+  __device__ static __forceinline__ float sq(unsigned a, unsigned b, float acc) {
+    float t = __uint_as_float(a) - __uint_as_float(b);
+    return fmaf(t, t, acc);
+  }
+  __device__ static __forceinline__ T step(uint2 x, uint2 y, T acc) {
+    acc = sq(x.x, y.x, acc);
+    return sq(x.y, y.y, acc);
+  }
+  __device__ static __forceinline__ T step4(uint4 x, uint4 y, T acc) {
+    acc = sq(x.x, y.x, acc);
+    acc = sq(x.y, y.y, acc);
+    acc = sq(x.z, y.z, acc);
+    return sq(x.w, y.w, acc);
+  }
+  __device__ static __forceinline__ unsigned long long bits(T v) { return __float_as_uint(v); }
+};
+
+// Full single-precision difference-form d2 between two global rows.
+template <int DT>
+__device__ __forceinline__ typename Acc<DT>::T row_d2(const uint8_t* a, const uint8_t* b,
+                                                       int64_t row_bytes) {
+  typename Acc<DT>::T acc = 0;
+  const uint4* pa = reinterpret_cast<const uint4*>(a);
+  const uint4* pb = reinterpret_cast<const uint4*>(b);
+  for (int64_t c = 0; c < row_bytes / 16; ++c) acc = Acc<DT>::step4(__ldg(pa + c), __ldg(pb + c), acc);
+  return acc;
+}
+
+// The canonical binary64 decision for float rows (tier 3).
+__device__ __forceinline__ bool tier3_dominates(const PruneArgs& a, int32_t u, int32_t v, int32_t p,
+                                                double* key64_v, double A2) {
+  const float* X = reinterpret_cast<const float*>(a.X);
+  const int64_t stride = a.row_bytes / 4;
+  double d2a = canon_d2_f32(X + int64_t(u) * stride, X + int64_t(v) * stride, a.d);
+  double d2b = *key64_v;
+  if (isnan(d2b)) {
+    d2b = canon_d2_f32(X + int64_t(p) * stride, X + int64_t(v) * stride, a.d);
+    *key64_v = d2b;  // every writer stores the same value
+  }
+  atomicAdd(&a.status->fp64_decisions, 1ull);
+  return canon_dominates(A2, d2a, d2b);
+}
+
+template <int DT, int MAXM>
+__global__ void __launch_bounds__(128) prune_fast_kernel(PruneArgs a) {
+  using L = FastLayout<MAXM>;
+  using AT = typename Acc<DT>::T;
+  constexpr int GT = MAXM;        // threads per node group
+  constexpr int NG = 128 / MAXM;  // node groups per CTA
+  constexpr int S = MAXM / 8;     // tile stride: a thread's tile rows are a, a+S, ..., a+7S
+  constexpr int TPT = (S * S) / GT;
+  constexpr int MW = L::MW;
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  const int T = a.T;
+  const int g = threadIdx.x / GT;
+  const int t = threadIdx.x % GT;
+  unsigned char* sb = smem_raw + size_t(g) * L::bytes(T);
+  AT* D = reinterpret_cast<AT*>(sb + L::off_D);
+  unsigned char* slice = sb + L::off_slice;
+  unsigned long long* skey = reinterpret_cast<unsigned long long*>(sb + L::off_skey);
+  double* key64 = reinterpret_cast<double*>(sb + L::off_key64);
+  unsigned long long* masks = reinterpret_cast<unsigned long long*>(sb + L::off_masks);
+  int32_t* ids = reinterpret_cast<int32_t*>(sb + L::off_ids(T));
+  int32_t* perm = reinterpret_cast<int32_t*>(sb + L::off_perm(T));
+  AT* key = reinterpret_cast<AT*>(sb + L::off_key(T));
+  unsigned char* lnk = sb + L::off_lnk(T);
+  int* misc = reinterpret_cast<int*>(sb + L::off_misc(T));
+
+  auto gsync = [&]() {
+    if constexpr (NG == 1) __syncthreads();
+    else named_sync(1 + g, GT);
+  };
+
+  const int count = *a.count;
+  const int nslices = int(a.row_bytes / kSlice);
+  const float E = rel_bound(a.d), Eabs = abs_bound(a.d);
+  long long done = 0;
+
+  for (;;) {
+    if (t == 0) {
+      unsigned idx = atomicAdd(a.work, 1u);
+      misc[0] = idx < unsigned(count) ? a.nodes[idx] : -1;
+    }
+    gsync();
+    const int p = misc[0];
+    if (p < 0) break;
+    const int64_t e0 = a.row_ptr[p];
+    const int m = int(a.row_ptr[p + 1] - e0);
+    if (m > MAXM) {  // bucketing never sends such a node here; refuse rather than overrun
+      if (t == 0) raise_status(a.status, kDevBadDegree, p);
+      gsync();
+      continue;
+    }
+    if (t < m) {
+      ids[t] = a.col[e0 + t];
+      key64[t] = __longlong_as_double(0x7ff8000000000000ll);  // not computed yet
+    }
+    if (t == 0) misc[1] = 0;
+    gsync();
+
+    // ---- a2 gather + a3 keys + a5 Gram, one 128-byte slice of every row at a time
+    const int nr = (m + S - 1) / S;  // tile rows/cols that touch live candidates
+    AT acc[TPT][8][8];
+#pragma unroll
+    for (int q = 0; q < TPT; ++q)
+#pragma unroll
+      for (int r = 0; r < 8; ++r)
+#pragma unroll
+        for (int c = 0; c < 8; ++c) acc[q][r][c] = 0;
+    AT kacc = 0;
+    for (int s = 0; s < nslices; ++s) {
+      for (int c = t; c < (m + 1) * 8; c += GT) {
+        const int r = c >> 3, part = c & 7;
+        const int64_t src = r == 0 ? int64_t(p) : int64_t(ids[r - 1]);
+        cp_async16(slice + r * kPitch + part * 16, a.X + src * a.row_bytes + s * kSlice + part * 16, 16);
+      }
+      cp_async_commit();
+      cp_async_wait<0>();
+      gsync();
+      if (t < m) {
+        const unsigned char* r0 = slice;
+        const unsigned char* r1 = slice + (t + 1) * kPitch;
+#pragma unroll
+        for (int part = 0; part < 8; ++part)
+          kacc = Acc<DT>::step4(*reinterpret_cast<const uint4*>(r0 + part * 16),
+                                *reinterpret_cast<const uint4*>(r1 + part * 16), kacc);
+      }
+#pragma unroll
+      for (int q = 0; q < TPT; ++q) {
+        const int tile = t + q * GT;
+        const int ta = tile / S, tb = tile % S;
+        const unsigned char* rbase = slice + (1 + ta) * kPitch;
+        const unsigned char* cbase = slice + (1 + tb) * kPitch;
+#pragma unroll 2
+        for (int w = 0; w < kSlice / 8; ++w) {
+          uint2 rv[8], cv[8];
+#pragma unroll
+          for (int r = 0; r < 8; ++r)
+            if (r < nr) rv[r] = *reinterpret_cast<const uint2*>(rbase + r * S * kPitch + w * 8);
+#pragma unroll
+          for (int c = 0; c < 8; ++c)
+            if (c < nr) cv[c] = *reinterpret_cast<const uint2*>(cbase + c * S * kPitch + w * 8);
+#pragma unroll
+          for (int r = 0; r < 8; ++r)
+            if (r < nr)
+#pragma unroll
+              for (int c = 0; c < 8; ++c)
+                if (c < nr) acc[q][r][c] = Acc<DT>::step(rv[r], cv[c], acc[q][r][c]);
+        }
+      }
+      gsync();  // the slice buffer is rewritten next
+    }
+#pragma unroll
+    for (int q = 0; q < TPT; ++q) {
+      const int tile = t + q * GT;
+      const int ta = tile / S, tb = tile % S;
+#pragma unroll
+      for (int r = 0; r < 8; ++r)
+#pragma unroll
+        for (int c = 0; c < 8; ++c) {
+          const int i = ta + r * S, j = tb + c * S;
+          if (r < nr && c < nr && i < m && j < m) D[i * MAXM + j] = acc[q][r][c];
+        }
+    }
+    if (t < m) key[t] = kacc;
+
+    // ---- a4 processing order
+    if (a.variant == 0) {
+      skey[t] = t < m ? (Acc<DT>::bits(kacc) << 32) | unsigned(ids[t]) : ~0ull;
+      perm[t] = t;
+      gsync();
+      for (int k = 2; k <= MAXM; k <<= 1) {
+        for (int j = k >> 1; j > 0; j >>= 1) {
+          const int pt = t ^ j;
+          const unsigned long long x = skey[t], y = skey[pt];
+          const int vx = perm[t], vy = perm[pt];
+          const bool up = (t & k) == 0;
+          const bool keep_min = (t < pt) == up;
+          const bool swap = keep_min ? (y < x) : (x < y);
+          gsync();
+          if (swap) {
+            skey[t] = y;
+            perm[t] = vy;
+          }
+          gsync();
+        }
+      }
+      if constexpr (DT == kF32) {
+        // near-ties of single-precision keys: order them by the binary64 keys
+        lnk[t] = 0;
+        if (t + 1 < m && !sure_less(key[perm[t]], key[perm[t + 1]], E, Eabs)) {
+          lnk[t] = 1;
+          misc[1] = 1;
+        }
+        gsync();
+        if (misc[1]) {
+          const bool member = t < m && (lnk[t] || (t > 0 && lnk[t - 1]));
+          if (member) {
+            const float* X = reinterpret_cast<const float*>(a.X);
+            const int64_t stride = a.row_bytes / 4;
+            key64[perm[t]] = canon_d2_f32(X + int64_t(p) * stride, X + int64_t(ids[perm[t]]) * stride, a.d);
+            atomicAdd(&a.status->fp64_sort_keys, 1ull);
+          }
+          gsync();
+          if (member && !(t > 0 && lnk[t - 1])) {
+            int end = t;
+            while (end + 1 < m && lnk[end]) ++end;
+            for (int i = t + 1; i <= end; ++i) {  // insertion sort of the run by (key64, id)
+              const int v = perm[i];
+              int j = i - 1;
+              while (j >= t && (key64[perm[j]] > key64[v] ||
+                                (key64[perm[j]] == key64[v] && ids[perm[j]] > ids[v]))) {
+                perm[j + 1] = perm[j];
+                --j;
+              }
+              perm[j + 1] = v;
+            }
+          }
+        }
+      }
+    } else {
+      perm[t] = t;
+    }
+    gsync();
+
+    // ---- a6 domination bits: row i (processing order) marks the later v it removes
+    if (t < m) {
+      const int i = t, pi = perm[i];
+      const AT* Drow = D + pi * MAXM;
+      for (int tt = 0; tt < T; ++tt) {
+        const int64_t A2 = int64_t(a.A[tt]) * a.A[tt];
+#pragma unroll
+        for (int w = 0; w < MW; ++w) {
+          unsigned long long bits = 0;
+          const int jlo = max(i + 1, 64 * w), jhi = min(m, 64 * w + 64);
+          for (int j = jlo; j < jhi; ++j) {
+            const int pj = perm[j];
+            bool dom;
+            if constexpr (DT == kU8) {
+              dom = static_cast<unsigned long long>(A2) * Drow[pj] <=
+                    1000000ull * static_cast<unsigned long long>(key[pj]);
+            } else {
+              const int r = sure_dominates(float(A2), Drow[pj], key[pj], E, Eabs);
+              dom = r >= 0 ? (r == 1) : tier3_dominates(a, ids[pi], ids[pj], p, &key64[pj], double(A2));
+            }
+            if (dom) bits |= 1ull << (j & 63);
+          }
+          masks[(tt * MW + w) * MAXM + i] = bits;
+        }
+      }
+    }
+    gsync();
+
+    // ---- a7 greedy scan per target, a8 kept ids into scratch
+    if (t < T) {
+      unsigned long long al0, al1 = 0;
+      al0 = m >= 64 ? ~0ull : ((1ull << m) - 1);
+      if (MW == 2) al1 = m >= 128 ? ~0ull : (m > 64 ? ((1ull << (m - 64)) - 1) : 0ull);
+      int32_t* out = a.out_col[t] + e0;
+      const int R = a.R[t];
+      int kept = 0;
+      for (;;) {
+        int i;
+        if (al0) i = __ffsll(static_cast<long long>(al0)) - 1;
+        else if (MW == 2 && al1) i = 64 + __ffsll(static_cast<long long>(al1)) - 1;
+        else break;
+        out[kept++] = ids[perm[i]];
+        if (i < 64) al0 &= ~(1ull << i);
+        else al1 &= ~(1ull << (i - 64));
+        if (kept == R) break;
+        al0 &= ~masks[(t * MW + 0) * MAXM + i];
+        if (MW == 2) al1 &= ~masks[(t * MW + 1) * MAXM + i];
+      }
+      a.out_cnt[t][p] = kept;
+    }
+    ++done;
+    gsync();
+  }
+  if (t == 0 && done) atomicAdd(&a.status->nodes_pruned, static_cast<unsigned long long>(done) * T);
+}
+
+// ---------------------------------------------------------------------------
+// generic path: one node per CTA, any degree up to RP_MAX_DEGREE
+// ---------------------------------------------------------------------------
+struct GenericLayout {
+  // sort keys and, once sorted, the binary64 pivot-key cache share one array
+  __host__ __device__ static size_t bytes(int M2) { return size_t(M2) * 22 + 64; }
+};
+
+template <int DT>
+__global__ void __launch_bounds__(256) prune_generic_kernel(PruneArgs a, int M2) {
+  using AT = typename Acc<DT>::T;
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  unsigned long long* skey = reinterpret_cast<unsigned long long*>(smem_raw);
+  double* key64 = reinterpret_cast<double*>(smem_raw);  // valid after the sort
+  int32_t* ids = reinterpret_cast<int32_t*>(smem_raw + size_t(M2) * 8);
+  int32_t* perm = reinterpret_cast<int32_t*>(smem_raw + size_t(M2) * 12);
+  AT* key = reinterpret_cast<AT*>(smem_raw + size_t(M2) * 16);
+  unsigned char* alive = smem_raw + size_t(M2) * 20;
+  unsigned char* lnk = smem_raw + size_t(M2) * 21;
+  int* misc = reinterpret_cast<int*>(smem_raw + size_t(M2) * 22);
+  const int t = threadIdx.x, NT = blockDim.x;
+  const int count = *a.count;
+  const float E = rel_bound(a.d), Eabs = abs_bound(a.d);
+  long long done = 0;
+
+  for (;;) {
+    if (t == 0) {
+      unsigned idx = atomicAdd(a.work, 1u);
+      misc[0] = idx < unsigned(count) ? a.nodes[idx] : -1;
+      misc[2] = 0;
+    }
+    __syncthreads();
+    const int p = misc[0];
+    if (p < 0) break;
+    const int64_t e0 = a.row_ptr[p];
+    const int m = int(a.row_ptr[p + 1] - e0);
+    if (m > M2) {  // bucketing guarantees m <= M2; keep the kernel safe regardless
+      if (t == 0) raise_status(a.status, kDevBadDegree, p);
+      __syncthreads();
+      continue;
+    }
+    const uint8_t* xp = a.X + int64_t(p) * a.row_bytes;
+    for (int j = t; j < M2; j += NT) {
+      if (j < m) {
+        const int32_t v = a.col[e0 + j];
+        ids[j] = v;
+        const AT kv = row_d2<DT>(xp, a.X + int64_t(v) * a.row_bytes, a.row_bytes);
+        key[j] = kv;
+        skey[j] = a.variant == 0 ? (Acc<DT>::bits(kv) << 32) | unsigned(v) : (unsigned long long)j;
+      } else {
+        skey[j] = ~0ull;
+      }
+      perm[j] = j;
+    }
+    __syncthreads();
+    if (a.variant == 0) {
+      for (int k = 2; k <= M2; k <<= 1) {
+        for (int j = k >> 1; j > 0; j >>= 1) {
+          for (int idx = t; idx < M2 / 2; idx += NT) {
+            const int i = (idx / j) * 2 * j + (idx % j);
+            const int l = i + j;
+            const bool up = (i & k) == 0;
+            const unsigned long long x = skey[i], y = skey[l];
+            if ((x > y) == up) {
+              skey[i] = y;
+              skey[l] = x;
+              const int tmp = perm[i];
+              perm[i] = perm[l];
+              perm[l] = tmp;
+            }
+          }
+          __syncthreads();
+        }
+      }
+      for (int j = t; j < M2; j += NT) key64[j] = __longlong_as_double(0x7ff8000000000000ll);
+      __syncthreads();
+      if constexpr (DT == kF32) {
+        for (int i = t; i < m; i += NT) {
+          lnk[i] = 0;
+          if (i + 1 < m && !sure_less(key[perm[i]], key[perm[i + 1]], E, Eabs)) {
+            lnk[i] = 1;
+            misc[2] = 1;
+          }
+        }
+        __syncthreads();
+        if (misc[2]) {
+          const float* X = reinterpret_cast<const float*>(a.X);
+          const int64_t stride = a.row_bytes / 4;
+          for (int i = t; i < m; i += NT) {
+            if (lnk[i] || (i > 0 && lnk[i - 1])) {
+              key64[perm[i]] = canon_d2_f32(X + int64_t(p) * stride, X + int64_t(ids[perm[i]]) * stride, a.d);
+              atomicAdd(&a.status->fp64_sort_keys, 1ull);
+            }
+          }
+          __syncthreads();
+          for (int s0 = t; s0 < m; s0 += NT) {
+            const bool head = (lnk[s0] || (s0 > 0 && lnk[s0 - 1])) && !(s0 > 0 && lnk[s0 - 1]);
+            if (!head) continue;
+            int end = s0;
+            while (end + 1 < m && lnk[end]) ++end;
+            for (int i = s0 + 1; i <= end; ++i) {
+              const int v = perm[i];
+              int j = i - 1;
+              while (j >= s0 && (key64[perm[j]] > key64[v] ||
+                                 (key64[perm[j]] == key64[v] && ids[perm[j]] > ids[v]))) {
+                perm[j + 1] = perm[j];
+                --j;
+              }
+              perm[j + 1] = v;
+            }
+          }
+        }
+      }
+    } else {
+      for (int j = t; j < M2; j += NT) key64[j] = __longlong_as_double(0x7ff8000000000000ll);
+    }
+    __syncthreads();
+
+    for (int tt = 0; tt < a.T; ++tt) {
+      const int64_t A2 = int64_t(a.A[tt]) * a.A[tt];
+      const int R = a.R[tt];
+      int32_t* out = a.out_col[tt] + e0;
+      for (int j = t; j < m; j += NT) alive[j] = 1;
+      if (t == 0) misc[1] = 0;  // cursor
+      __syncthreads();
+      int kept = 0;
+      for (;;) {
+        if (t == 0) {
+          int c = misc[1];
+          while (c < m && !alive[c]) ++c;
+          misc[1] = c;
+          misc[3] = c;
+          if (c < m) {
+            out[kept] = ids[perm[c]];
+            alive[c] = 0;
+          }
+        }
+        __syncthreads();
+        const int i = misc[3];
+        if (i >= m) break;
+        ++kept;
+        if (kept == R) break;
+        const int32_t ui = ids[perm[i]];
+        const uint8_t* xu = a.X + int64_t(ui) * a.row_bytes;
+        for (int j = i + 1 + t; j < m; j += NT) {
+          if (!alive[j]) continue;
+          const int pj = perm[j];
+          const AT d2a = row_d2<DT>(xu, a.X + int64_t(ids[pj]) * a.row_bytes, a.row_bytes);
+          bool dom;
+          if constexpr (DT == kU8) {
+            dom = static_cast<unsigned long long>(A2) * d2a <= 1000000ull * static_cast<unsigned long long>(key[pj]);
+          } else {
+            const int r = sure_dominates(float(A2), d2a, key[pj], E, Eabs);
+            dom = r >= 0 ? (r == 1) : tier3_dominates(a, ui, ids[pj], p, &key64[pj], double(A2));
+          }
+          if (dom) alive[j] = 0;
+        }
+        __syncthreads();
+      }
+      if (t == 0) a.out_cnt[tt][p] = kept;
+      __syncthreads();
+    }
+    ++done;
+  }
+  if (t == 0 && done) {
+    atomicAdd(&a.status->nodes_pruned, static_cast<unsigned long long>(done) * a.T);
+    atomicAdd(&a.status->generic_nodes, static_cast<unsigned long long>(done));
+  }
+}
+
+__global__ void bucket_nodes_kernel(const int64_t* __restrict__ row_ptr, int64_t n,
+                                    int32_t* __restrict__ lists, int32_t* __restrict__ counts) {
+  const int lane = threadIdx.x & 31;
+  for (int64_t base = int64_t(blockIdx.x) * blockDim.x; base < n; base += int64_t(gridDim.x) * blockDim.x) {
+    const int64_t p = base + threadIdx.x;
+    const bool valid = p < n;
+    int b = -1;
+    if (valid) {
+      const int64_t deg = row_ptr[p + 1] - row_ptr[p];
+      b = deg <= 64 ? 0 : (deg <= 128 ? 1 : 2);
+    }
+#pragma unroll
+    for (int bb = 0; bb < 3; ++bb) {
+      const unsigned msk = __ballot_sync(0xffffffffu, b == bb);
+      if (!msk) continue;
+      const int leader = __ffs(msk) - 1;
+      int off = 0;
+      if (lane == leader) off = atomicAdd(&counts[bb], __popc(msk));
+      off = __shfl_sync(0xffffffffu, off, leader);
+      if (b == bb) lists[int64_t(bb) * n + off + __popc(msk & ((1u << lane) - 1))] = int32_t(p);
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// counts -> row_ptr -> compacted col (a8)
+// ---------------------------------------------------------------------------
+constexpr int kScanChunk = 4096;  // nodes per block
+constexpr int kScanThreads = 256;
+constexpr int kPerThread = kScanChunk / kScanThreads;
+
+struct EmitArgs {
+  int64_t n;
+  int64_t nblk;
+  const int64_t* src_row_ptr;
+  int32_t* scratch[kMaxTargets];
+  int32_t* cnt[kMaxTargets];
+  int64_t* dst_row_ptr[kMaxTargets];
+  int32_t* dst_col[kMaxTargets];
+  int64_t* bsum;
+};
+
+__device__ __forceinline__ int64_t block_excl_scan(int64_t v, int64_t* warp_tot, int64_t* total) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  int64_t x = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int64_t y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) warp_tot[w] = x;
+  __syncthreads();
+  if (w == 0) {
+    int64_t s = lane < int(blockDim.x >> 5) ? warp_tot[lane] : 0;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int64_t y = __shfl_up_sync(0xffffffffu, s, o);
+      if (lane >= o) s += y;
+    }
+    if (lane < int(blockDim.x >> 5)) warp_tot[lane] = s;  // inclusive per warp
+    if (lane == int(blockDim.x >> 5) - 1) *total = s;
+  }
+  __syncthreads();
+  const int64_t before = w > 0 ? warp_tot[w - 1] : 0;
+  return before + x - v;
+}
+
+__global__ void __launch_bounds__(kScanThreads) emit_block_sums(EmitArgs e) {
+  const int tt = blockIdx.y;
+  const int64_t b0 = int64_t(blockIdx.x) * kScanChunk;
+  int64_t s = 0;
+  for (int i = threadIdx.x; i < kScanChunk; i += kScanThreads) {
+    const int64_t p = b0 + i;
+    if (p < e.n) s += e.cnt[tt][p];
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+  __shared__ int64_t ws[kScanThreads / 32];
+  if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int64_t tot = 0;
+    for (int w = 0; w < kScanThreads / 32; ++w) tot += ws[w];
+    e.bsum[int64_t(tt) * e.nblk + blockIdx.x] = tot;
+  }
+}
+
+__global__ void __launch_bounds__(1024) emit_scan_sums(EmitArgs e) {
+  const int tt = blockIdx.x;
+  __shared__ int64_t warp_tot[32];
+  __shared__ int64_t total;
+  int64_t carry = 0;
+  for (int64_t base = 0; base < e.nblk; base += blockDim.x) {
+    const int64_t i = base + threadIdx.x;
+    const int64_t v = i < e.nblk ? e.bsum[int64_t(tt) * e.nblk + i] : 0;
+    const int64_t ex = block_excl_scan(v, warp_tot, &total);
+    if (i < e.nblk) e.bsum[int64_t(tt) * e.nblk + i] = carry + ex;
+    carry += total;
+    __syncthreads();
+  }
+}
+
+__global__ void __launch_bounds__(kScanThreads) emit_write(EmitArgs e) {
+  const int tt = blockIdx.y;
+  const int64_t b0 = int64_t(blockIdx.x) * kScanChunk;
+  __shared__ int64_t warp_tot[32];
+  __shared__ int64_t total;
+  __shared__ int64_t off[kScanChunk];
+  int local[kPerThread];
+  int64_t mine = 0;
+#pragma unroll
+  for (int i = 0; i < kPerThread; ++i) {
+    const int64_t p = b0 + int64_t(threadIdx.x) * kPerThread + i;
+    local[i] = p < e.n ? e.cnt[tt][p] : 0;
+    mine += local[i];
+  }
+  int64_t run = block_excl_scan(mine, warp_tot, &total) + e.bsum[int64_t(tt) * e.nblk + blockIdx.x];
+#pragma unroll
+  for (int i = 0; i < kPerThread; ++i) {
+    const int li = threadIdx.x * kPerThread + i;
+    const int64_t p = b0 + li;
+    off[li] = run;
+    run += local[i];
+    if (p < e.n) e.dst_row_ptr[tt][p + 1] = run;
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) e.dst_row_ptr[tt][0] = 0;
+  __syncthreads();
+  if (e.dst_col[tt] == nullptr) return;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  for (int li = w; li < kScanChunk; li += kScanThreads / 32) {
+    const int64_t p = b0 + li;
+    if (p >= e.n) break;
+    const int c = e.cnt[tt][p];
+    const int32_t* src = e.scratch[tt] + e.src_row_ptr[p];
+    int32_t* dst = e.dst_col[tt] + off[li];
+    for (int j = lane; j < c; j += 32) dst[j] = src[j];
+  }
+}
+
+}  // namespace
+
+int64_t emit_csr_blocks(int64_t n) { return (n + kScanChunk - 1) / kScanChunk; }
+
+cudaError_t launch_emit_csr(int64_t n, int T, const int64_t* src_row_ptr, int32_t* const* scratch_col,
+                            int32_t* const* cnt, int64_t* const* dst_row_ptr, int32_t* const* dst_col,
+                            int64_t* block_sums, cudaStream_t s) {
+  EmitArgs e{};
+  e.n = n;
+  e.nblk = emit_csr_blocks(n);
+  e.src_row_ptr = src_row_ptr;
+  e.bsum = block_sums;
+  for (int t = 0; t < T; ++t) {
+    e.scratch[t] = scratch_col ? scratch_col[t] : nullptr;
+    e.cnt[t] = cnt[t];
+    e.dst_row_ptr[t] = dst_row_ptr[t];
+    e.dst_col[t] = dst_col ? dst_col[t] : nullptr;
+  }
+  const dim3 grid(unsigned(e.nblk), unsigned(T));
+  emit_block_sums<<<grid, kScanThreads, 0, s>>>(e);
+  emit_scan_sums<<<T, 1024, 0, s>>>(e);
+  emit_write<<<grid, kScanThreads, 0, s>>>(e);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_bucket_nodes(const int64_t* row_ptr, int64_t n, int32_t* lists, int32_t* counts,
+                                cudaStream_t s) {
+  cudaError_t err = cudaMemsetAsync(counts, 0, 3 * sizeof(int32_t), s);
+  if (err != cudaSuccess) return err;
+  const int64_t blocks = std::min<int64_t>((n + 255) / 256, 65535 * 4);
+  bucket_nodes_kernel<<<unsigned(std::max<int64_t>(blocks, 1)), 256, 0, s>>>(row_ptr, n, lists, counts);
+  return cudaGetLastError();
+}
+
+template <int DT, int MAXM>
+static cudaError_t run_fast(const PruneArgs& args, int num_sms, int64_t host_count, cudaStream_t s) {
+  if (host_count <= 0) return cudaSuccess;
+  const size_t per_group = FastLayout<MAXM>::bytes(args.T);
+  const size_t bytes = per_group * (128 / MAXM);
+  auto kern = prune_fast_kernel<DT, MAXM>;
+  cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(bytes));
+  if (err != cudaSuccess) return err;
+  int per_sm = 0;
+  err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 128, bytes);
+  if (err != cudaSuccess) return err;
+  if (per_sm < 1) per_sm = 1;
+  const int64_t groups_needed = (host_count + (128 / MAXM) - 1) / (128 / MAXM);
+  const int64_t grid = std::min<int64_t>(int64_t(num_sms) * per_sm, groups_needed);
+  kern<<<unsigned(grid), 128, bytes, s>>>(args);
+  return cudaGetLastError();
+}
+
+template <int DT>
+static cudaError_t run_generic(const PruneArgs& args, int num_sms, int64_t host_count, int max_degree,
+                               cudaStream_t s) {
+  if (host_count <= 0) return cudaSuccess;
+  int M2 = 256;
+  while (M2 < max_degree) M2 <<= 1;
+  const size_t bytes = GenericLayout::bytes(M2);
+  auto kern = prune_generic_kernel<DT>;
+  cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(bytes));
+  if (err != cudaSuccess) return err;
+  int per_sm = 0;
+  err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 256, bytes);
+  if (err != cudaSuccess) return err;
+  if (per_sm < 1) return cudaErrorInvalidConfiguration;
+  const int64_t grid = std::min<int64_t>(int64_t(num_sms) * per_sm, host_count);
+  kern<<<unsigned(grid), 256, bytes, s>>>(args, M2);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_prune(const PruneLaunch& L, cudaStream_t s) {
+  PruneArgs a{};
+  a.X = L.data.X;
+  a.row_bytes = L.data.row_bytes;
+  a.d = L.data.d;
+  a.row_ptr = L.row_ptr;
+  a.col = L.col;
+  a.T = L.T;
+  a.variant = L.variant;
+  a.status = L.status;
+  for (int t = 0; t < L.T; ++t) {
+    a.A[t] = L.A[t];
+    a.R[t] = L.R[t];
+    a.out_col[t] = L.out_col[t];
+    a.out_cnt[t] = L.out_cnt[t];
+  }
+  cudaError_t err = cudaSuccess;
+  for (int b = 0; b < 3 && err == cudaSuccess; ++b) {
+    a.nodes = L.bucket_nodes[b];
+    a.count = L.bucket_count + b;
+    a.work = L.work + b;
+    const int64_t hc = L.host_bucket_count[b];
+    if (L.data.dtype == kU8) {
+      if (b == 0) err = run_fast<kU8, 64>(a, L.num_sms, hc, s);
+      else if (b == 1) err = run_fast<kU8, 128>(a, L.num_sms, hc, s);
+      else err = run_generic<kU8>(a, L.num_sms, hc, L.host_max_degree, s);
+    } else {
+      if (b == 0) err = run_fast<kF32, 64>(a, L.num_sms, hc, s);
+      else if (b == 1) err = run_fast<kF32, 128>(a, L.num_sms, hc, s);
+      else err = run_generic<kF32>(a, L.num_sms, hc, L.host_max_degree, s);
+    }
+  }
+  return err;
+}
+
+}  // namespace rpk

@@ -1,0 +1,937 @@
+// C ABI and host runtime of librp.so: contexts, resident graphs, the HBM
+// budget, stream-ordered allocation and CUDA-graph replay of batched tuning.
+// The public contract of every function is documented in include/rp.h.
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "internal.h"
+#include "rp.h"
+
+using namespace rpk;
+
+namespace {
+
+struct Dataset {
+  uint8_t* X = nullptr;
+  int64_t row_bytes = 0;
+  int64_t n = 0;
+  int d = 0;
+  int dtype = 0;
+  size_t bytes = 0;
+  DevData dev() const {
+    DevData D;
+    D.X = X;
+    D.row_bytes = row_bytes;
+    D.n = n;
+    D.d = d;
+    D.dtype = dtype;
+    return D;
+  }
+};
+
+struct Graph {
+  std::shared_ptr<Dataset> data;
+  int64_t* row_ptr = nullptr;
+  int32_t* col = nullptr;
+  int64_t n = 0;
+  int64_t col_cap = 0;
+  int64_t nnz = -1;         // known on the host after a sync, else -1
+  int max_deg_bound = 0;    // an upper bound of the largest out-degree
+  int64_t start = 0;
+  int32_t* buckets = nullptr;  // 3 * n node lists + 3 counts, built on first use as a source
+  size_t bytes = 0;
+  size_t bucket_bytes = 0;
+};
+
+struct BatchPlan {
+  rp_graph src = 0;
+  int64_t kernels = 0;  // kernels in the captured graph
+  int T = 0;
+  int variant = 0;
+  int32_t A[kMaxTargets];
+  int32_t R[kMaxTargets];
+  cudaGraphExec_t exec = nullptr;
+};
+
+}  // namespace
+
+struct rp_ctx {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  int num_sms = 0;
+  uint64_t budget = 0;
+  uint64_t used = 0;
+  uint64_t peak = 0;
+  std::map<rp_graph, Graph*> graphs;
+  rp_graph next_id = 1;
+  std::string err;
+  std::mutex mu;
+  DevStatus* status = nullptr;        // device
+  unsigned long long* dropped = nullptr;  // device [2]
+  // prune scratch, grown on demand
+  int32_t* scratch_col = nullptr;
+  int64_t scratch_col_elems = 0;
+  int32_t* scratch_cnt = nullptr;
+  int64_t scratch_cnt_elems = 0;
+  int64_t* scratch_bsum = nullptr;
+  int64_t scratch_bsum_elems = 0;
+  unsigned int* work = nullptr;       // device [8]
+  // search scratch
+  uint32_t* seen_bits = nullptr;
+  int64_t seen_bits_words = 0;
+  int32_t* seen_list = nullptr;
+  int64_t seen_list_elems = 0;
+  uint8_t* qbuf = nullptr;
+  int64_t qbuf_bytes = 0;
+  unsigned long long* hits = nullptr;  // device [1]
+  std::vector<BatchPlan> plans;
+  int64_t graph_replays = 0;
+  int64_t kernel_launches = 0;
+  // phase timing: 0/1 prune, 1/2 emit, 3/4 search
+  cudaEvent_t ev[5] = {};
+  bool ev_tune = false, ev_search = false;
+};
+
+namespace {
+
+rp_status fail(rp_ctx* c, rp_status code, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  if (c) c->err = buf;
+  return code;
+}
+
+#define CUDA_TRY(ctx, expr)                                                                   \
+  do {                                                                                        \
+    cudaError_t e_ = (expr);                                                                  \
+    if (e_ != cudaSuccess)                                                                    \
+      return fail(ctx, RP_ECUDA, "%s failed: %s (%s:%d)", #expr, cudaGetErrorString(e_),      \
+                  __FILE__, __LINE__);                                                        \
+  } while (0)
+
+size_t elem_size(int dtype) { return dtype == RP_U8 ? 1 : 4; }
+int64_t padded_row_bytes(int d, int dtype) {
+  const int64_t raw = int64_t(d) * int64_t(elem_size(dtype));
+  return (raw + 127) / 128 * 128;
+}
+
+// Stream-ordered allocation against the context budget.
+rp_status dalloc(rp_ctx* c, void** p, size_t bytes) {
+  *p = nullptr;
+  if (bytes == 0) bytes = 16;
+  if (c->budget && c->used + bytes > c->budget)
+    return fail(c, RP_ENOMEM, "allocation of %zu bytes exceeds the HBM budget (%llu of %llu in use)", bytes,
+                (unsigned long long)c->used, (unsigned long long)c->budget);
+  cudaError_t e = cudaMallocAsync(p, bytes, c->stream);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return fail(c, e == cudaErrorMemoryAllocation ? RP_ENOMEM : RP_ECUDA, "cudaMallocAsync(%zu): %s", bytes,
+                cudaGetErrorString(e));
+  }
+  c->used += bytes;
+  c->peak = std::max(c->peak, c->used);
+  return RP_OK;
+}
+
+void dfree(rp_ctx* c, void* p, size_t bytes) {
+  if (!p) return;
+  if (bytes == 0) bytes = 16;
+  cudaFreeAsync(p, c->stream);
+  c->used -= std::min<uint64_t>(c->used, bytes);
+}
+
+template <typename T>
+rp_status grow(rp_ctx* c, T** buf, int64_t* have, int64_t need) {
+  if (*have >= need) return RP_OK;
+  dfree(c, *buf, size_t(*have) * sizeof(T));
+  *buf = nullptr;
+  *have = 0;
+  const int64_t want = std::max<int64_t>(need, 1);
+  rp_status s = dalloc(c, reinterpret_cast<void**>(buf), size_t(want) * sizeof(T));
+  if (s != RP_OK) return s;
+  *have = want;
+  return RP_OK;
+}
+
+rp_status check_device_status(rp_ctx* c) {
+  DevStatus h;
+  CUDA_TRY(c, cudaMemcpyAsync(&h, c->status, sizeof h, cudaMemcpyDeviceToHost, c->stream));
+  CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  if (h.code != 0) {
+    const int zero = 0;
+    CUDA_TRY(c, cudaMemcpyAsync(&c->status->code, &zero, sizeof zero, cudaMemcpyHostToDevice, c->stream));
+    CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    const char* what = h.code == kDevBadId        ? "an id outside [0, n), a malformed row_ptr or a non-finite value"
+                       : h.code == kDevTieUnresolved ? "a near-tie run longer than the kept candidates"
+                       : h.code == kDevOverflow      ? "a per-query scratch structure ran out of room"
+                       : h.code == kDevBadDegree     ? "a degree above the kernel's limit"
+                                                     : "unknown";
+    return fail(c, RP_EDEVICE, "device status %d (%s) at index %lld", h.code, what, (long long)h.info);
+  }
+  return RP_OK;
+}
+
+Graph* find_graph(rp_ctx* c, rp_graph g) {
+  auto it = c->graphs.find(g);
+  return it == c->graphs.end() ? nullptr : it->second;
+}
+
+rp_graph add_graph(rp_ctx* c, Graph* G) {
+  const rp_graph id = c->next_id++;
+  c->graphs[id] = G;
+  return id;
+}
+
+void free_graph_mem(rp_ctx* c, Graph* G) {
+  dfree(c, G->row_ptr, size_t(G->n + 1) * 8);
+  dfree(c, G->col, size_t(std::max<int64_t>(G->col_cap, 1)) * 4);
+  if (G->buckets) dfree(c, G->buckets, G->bucket_bytes);
+  if (G->data && G->data.use_count() == 1) dfree(c, G->data->X, G->data->bytes);
+  G->data.reset();
+  delete G;
+}
+
+bool alpha_to_milli(double alpha, int32_t* A) {
+  if (!(alpha >= 1.0) || !(alpha <= 100.0)) return false;
+  const double m = alpha * 1000.0;
+  const double r = std::nearbyint(m);
+  if (std::fabs(m - r) > 1e-6) return false;
+  *A = int32_t(r);
+  return true;
+}
+
+// Copy rows (packed, d * esz bytes each) into a padded device buffer.
+rp_status upload_rows(rp_ctx* c, uint8_t* dst, int64_t dst_rb, const void* src, int64_t n, int d, int dtype,
+                      int mem_flags) {
+  const size_t w = size_t(d) * elem_size(dtype);
+  CUDA_TRY(c, cudaMemsetAsync(dst, 0, size_t(n * dst_rb), c->stream));
+  if (n == 0) return RP_OK;
+  CUDA_TRY(c, cudaMemcpy2DAsync(dst, size_t(dst_rb), src, w, w, size_t(n),
+                                mem_flags == RP_MEM_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice,
+                                c->stream));
+  return RP_OK;
+}
+
+rp_status ensure_buckets(rp_ctx* c, Graph* G) {
+  if (G->buckets) return RP_OK;
+  G->bucket_bytes = size_t(3 * G->n + 4) * 4;
+  rp_status s = dalloc(c, reinterpret_cast<void**>(&G->buckets), G->bucket_bytes);
+  if (s != RP_OK) return s;
+  CUDA_TRY(c, launch_bucket_nodes(G->row_ptr, G->n, G->buckets, G->buckets + 3 * G->n, c->stream));
+  return RP_OK;
+}
+
+// Enqueue the whole tuning pipeline for `T` targets of `src` into `outs`.
+rp_status enqueue_tune(rp_ctx* c, Graph* S, int T, const int32_t* A, const int32_t* R, int variant,
+                       Graph* const* outs, int64_t* kernels) {
+  PruneLaunch L;
+  L.data = S->data->dev();
+  L.row_ptr = S->row_ptr;
+  L.col = S->col;
+  for (int b = 0; b < 3; ++b) {
+    L.bucket_nodes[b] = S->buckets + int64_t(b) * S->n;
+    L.host_bucket_count[b] = S->n;  // upper bound; kernels stop at the device count
+  }
+  if (S->max_deg_bound <= 128) L.host_bucket_count[2] = 0;
+  if (S->max_deg_bound <= 64) L.host_bucket_count[1] = 0;
+  L.bucket_count = S->buckets + 3 * S->n;
+  L.host_max_degree = S->max_deg_bound;
+  L.T = T;
+  L.variant = variant;
+  L.work = c->work;
+  L.status = c->status;
+  L.num_sms = c->num_sms;
+  int32_t* dst_col[kMaxTargets];
+  int64_t* dst_rp[kMaxTargets];
+  int32_t* scr[kMaxTargets];
+  int32_t* cnt[kMaxTargets];
+  for (int t = 0; t < T; ++t) {
+    L.A[t] = A[t];
+    L.R[t] = R[t];
+    scr[t] = c->scratch_col + int64_t(t) * std::max<int64_t>(S->col_cap, 1);
+    cnt[t] = c->scratch_cnt + int64_t(t) * S->n;
+    L.out_col[t] = scr[t];
+    L.out_cnt[t] = cnt[t];
+    dst_col[t] = outs[t]->col;
+    dst_rp[t] = outs[t]->row_ptr;
+  }
+  CUDA_TRY(c, cudaMemsetAsync(c->work, 0, 8 * sizeof(unsigned), c->stream));
+  CUDA_TRY(c, cudaEventRecord(c->ev[0], c->stream));
+  CUDA_TRY(c, launch_prune(L, c->stream));
+  CUDA_TRY(c, cudaEventRecord(c->ev[1], c->stream));
+  CUDA_TRY(c, launch_emit_csr(S->n, T, S->row_ptr, scr, cnt, dst_rp, dst_col, c->scratch_bsum, c->stream));
+  CUDA_TRY(c, cudaEventRecord(c->ev[2], c->stream));
+  c->ev_tune = true;
+  int64_t k = 3;
+  for (int b = 0; b < 3; ++b) k += L.host_bucket_count[b] > 0;
+  *kernels = k;
+  return RP_OK;
+}
+
+rp_status tune_impl(rp_ctx* c, rp_graph src, const double* alphas, const int32_t* Rs, int32_t T, int32_t variant,
+                    rp_graph* outs, bool use_graph) {
+  if (!outs || !alphas || !Rs) return fail(c, RP_EINVAL, "null argument");
+  if (T < 1 || T > kMaxTargets) return fail(c, RP_EINVAL, "T=%d outside [1, %d]", T, kMaxTargets);
+  if (variant != RP_SORTED && variant != RP_UNSORTED) return fail(c, RP_EINVAL, "bad variant %d", variant);
+  Graph* S = find_graph(c, src);
+  if (!S) return fail(c, RP_ENOTFOUND, "unknown graph %lld", (long long)src);
+  int32_t A[kMaxTargets], R[kMaxTargets];
+  for (int t = 0; t < T; ++t) {
+    if (!alpha_to_milli(alphas[t], &A[t]))
+      return fail(c, RP_EINVAL, "alpha=%.17g must lie in [1, 100] on the 0.001 grid", alphas[t]);
+    if (Rs[t] < 1) return fail(c, RP_EINVAL, "R=%d must be >= 1", Rs[t]);
+    R[t] = Rs[t];
+  }
+  rp_status s = ensure_buckets(c, S);
+  if (s != RP_OK) return s;
+  const int64_t cap = std::max<int64_t>(S->col_cap, 1);
+  if ((s = grow(c, &c->scratch_col, &c->scratch_col_elems, cap * T)) != RP_OK) return s;
+  if ((s = grow(c, &c->scratch_cnt, &c->scratch_cnt_elems, S->n * T)) != RP_OK) return s;
+  if ((s = grow(c, &c->scratch_bsum, &c->scratch_bsum_elems, emit_csr_blocks(S->n) * T)) != RP_OK) return s;
+  Graph* G[kMaxTargets] = {};
+  for (int t = 0; t < T; ++t) {
+    G[t] = new Graph;
+    G[t]->data = S->data;
+    G[t]->n = S->n;
+    G[t]->col_cap = S->col_cap;
+    G[t]->start = S->start;
+    G[t]->max_deg_bound = std::min(S->max_deg_bound, R[t]);
+    G[t]->bytes = size_t(S->n + 1) * 8 + size_t(cap) * 4;
+    s = dalloc(c, reinterpret_cast<void**>(&G[t]->row_ptr), size_t(S->n + 1) * 8);
+    if (s == RP_OK) s = dalloc(c, reinterpret_cast<void**>(&G[t]->col), size_t(cap) * 4);
+    if (s != RP_OK) {
+      for (int u = 0; u <= t; ++u) free_graph_mem(c, G[u]);
+      return s;
+    }
+  }
+  int64_t nk = 0;
+  if (!use_graph) {
+    s = enqueue_tune(c, S, T, A, R, variant, G, &nk);
+    c->kernel_launches += nk;
+  } else {
+    // Replay: capture this call's launches and update the cached executable
+    // graph of the same (source, targets, variant) in place.
+    BatchPlan* plan = nullptr;
+    for (auto& pl : c->plans)
+      if (pl.src == src && pl.T == T && pl.variant == variant && !memcmp(pl.A, A, 4 * T) && !memcmp(pl.R, R, 4 * T))
+        plan = &pl;
+    cudaGraph_t graph = nullptr;
+    cudaError_t ce = cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal);
+    if (ce != cudaSuccess) s = fail(c, RP_ECUDA, "begin capture: %s", cudaGetErrorString(ce));
+    if (s == RP_OK) {
+      s = enqueue_tune(c, S, T, A, R, variant, G, &nk);
+      ce = cudaStreamEndCapture(c->stream, &graph);
+      if (s == RP_OK && ce != cudaSuccess) s = fail(c, RP_ECUDA, "end capture: %s", cudaGetErrorString(ce));
+    }
+    if (s == RP_OK) {
+      bool ok = false;
+      if (plan && plan->exec) {
+        cudaGraphExecUpdateResultInfo info;
+        ok = cudaGraphExecUpdate(plan->exec, graph, &info) == cudaSuccess;
+        if (!ok) cudaGetLastError();
+        else ++c->graph_replays;
+      }
+      if (!ok) {
+        cudaGraphExec_t exec = nullptr;
+        ce = cudaGraphInstantiate(&exec, graph, 0);
+        if (ce != cudaSuccess) s = fail(c, RP_ECUDA, "instantiate: %s", cudaGetErrorString(ce));
+        else {
+          if (!plan) {
+            c->plans.push_back(BatchPlan{});
+            plan = &c->plans.back();
+            plan->src = src;
+            plan->T = T;
+            plan->variant = variant;
+            memcpy(plan->A, A, 4 * T);
+            memcpy(plan->R, R, 4 * T);
+          } else if (plan->exec) {
+            cudaGraphExecDestroy(plan->exec);
+          }
+          plan->exec = exec;
+        }
+      }
+      if (s == RP_OK) {
+        plan->kernels = nk;
+        ce = cudaGraphLaunch(plan->exec, c->stream);
+        if (ce != cudaSuccess) s = fail(c, RP_ECUDA, "graph launch: %s", cudaGetErrorString(ce));
+        else c->kernel_launches += nk;
+      }
+    }
+    if (graph) cudaGraphDestroy(graph);
+  }
+  if (s != RP_OK) {
+    for (int t = 0; t < T; ++t) free_graph_mem(c, G[t]);
+    return s;
+  }
+  for (int t = 0; t < T; ++t) outs[t] = add_graph(c, G[t]);
+  return RP_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+rp_status rp_create(rp_ctx** out, int32_t device, uint64_t hbm_budget_bytes, void* cuda_stream) {
+  if (!out) return RP_EINVAL;
+  *out = nullptr;
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) {
+    cudaGetLastError();
+    return RP_EINVAL;
+  }
+  std::unique_ptr<rp_ctx> c(new rp_ctx);
+  c->device = device;
+  c->budget = hbm_budget_bytes;
+  if (cudaSetDevice(device) != cudaSuccess) return RP_ECUDA;
+  if (cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess) return RP_ECUDA;
+  if (cuda_stream) {
+    c->stream = static_cast<cudaStream_t>(cuda_stream);
+  } else {
+    if (cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking) != cudaSuccess) return RP_ECUDA;
+    c->own_stream = true;
+  }
+  cudaMemPool_t pool;
+  if (cudaDeviceGetDefaultMemPool(&pool, device) == cudaSuccess) {
+    uint64_t thr = UINT64_MAX;  // keep freed blocks cached in this process
+    cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+  }
+  if (dalloc(c.get(), reinterpret_cast<void**>(&c->status), sizeof(DevStatus)) != RP_OK) return RP_ECUDA;
+  if (dalloc(c.get(), reinterpret_cast<void**>(&c->dropped), 2 * sizeof(unsigned long long)) != RP_OK)
+    return RP_ECUDA;
+  if (dalloc(c.get(), reinterpret_cast<void**>(&c->work), 8 * sizeof(unsigned)) != RP_OK) return RP_ECUDA;
+  if (dalloc(c.get(), reinterpret_cast<void**>(&c->hits), sizeof(unsigned long long)) != RP_OK) return RP_ECUDA;
+  if (cudaMemsetAsync(c->status, 0, sizeof(DevStatus), c->stream) != cudaSuccess) return RP_ECUDA;
+  if (cudaMemsetAsync(c->dropped, 0, 2 * sizeof(unsigned long long), c->stream) != cudaSuccess) return RP_ECUDA;
+  for (auto& e : c->ev)
+    if (cudaEventCreate(&e) != cudaSuccess) return RP_ECUDA;
+  if (cudaStreamSynchronize(c->stream) != cudaSuccess) return RP_ECUDA;
+  *out = c.release();
+  return RP_OK;
+}
+
+rp_status rp_destroy(rp_ctx* c) {
+  if (!c) return RP_EINVAL;
+  {
+    std::lock_guard<std::mutex> lk(c->mu);
+    cudaSetDevice(c->device);
+    cudaStreamSynchronize(c->stream);
+    for (auto& kv : c->graphs) free_graph_mem(c, kv.second);
+    c->graphs.clear();
+    for (auto& pl : c->plans)
+      if (pl.exec) cudaGraphExecDestroy(pl.exec);
+    dfree(c, c->scratch_col, size_t(c->scratch_col_elems) * 4);
+    dfree(c, c->scratch_cnt, size_t(c->scratch_cnt_elems) * 4);
+    dfree(c, c->scratch_bsum, size_t(c->scratch_bsum_elems) * 8);
+    dfree(c, c->seen_bits, size_t(c->seen_bits_words) * 4);
+    dfree(c, c->seen_list, size_t(c->seen_list_elems) * 4);
+    dfree(c, c->qbuf, size_t(c->qbuf_bytes));
+    dfree(c, c->status, sizeof(DevStatus));
+    dfree(c, c->dropped, 16);
+    dfree(c, c->work, 32);
+    dfree(c, c->hits, 8);
+    cudaStreamSynchronize(c->stream);
+    for (auto& e : c->ev)
+      if (e) cudaEventDestroy(e);
+    if (c->own_stream) cudaStreamDestroy(c->stream);
+  }
+  delete c;
+  return RP_OK;
+}
+
+const char* rp_last_error(const rp_ctx* c) { return c ? c->err.c_str() : "null context"; }
+
+rp_status rp_sync(rp_ctx* c) {
+  if (!c) return RP_EINVAL;
+  std::lock_guard<std::mutex> lk(c->mu);
+  cudaSetDevice(c->device);
+  CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  return check_device_status(c);
+}
+
+rp_status rp_load_graph(rp_ctx* c, const void* vectors, int32_t dtype, int64_t n, int32_t d, const int64_t* row_ptr,
+                        const int32_t* col, int32_t start, int32_t mem_flags, rp_graph* base_out) {
+  if (!c) return RP_EINVAL;
+  std::lock_guard<std::mutex> lk(c->mu);
+  cudaSetDevice(c->device);
+  if (!base_out || !vectors) return fail(c, RP_EINVAL, "null argument");
+  if (dtype != RP_U8 && dtype != RP_F32) return fail(c, RP_EINVAL, "bad dtype %d", dtype);
+  if (n < 1 || n > INT32_MAX || d < 1 || d > 65536) return fail(c, RP_EINVAL, "bad shape n=%lld d=%d", (long long)n, d);
+  if (start < -1 || start >= n) return fail(c, RP_EINVAL, "start=%d outside [-1, n)", start);
+  if (mem_flags != RP_MEM_HOST && mem_flags != RP_MEM_DEVICE) return fail(c, RP_EINVAL, "bad mem_flags");
+  if (dtype == RP_U8 && d > 4096) return fail(c, RP_EINVAL, "uint8 vectors are limited to d <= 4096");
+
+  auto D = std::make_shared<Dataset>();
+  D->n = n;
+  D->d = d;
+  D->dtype = dtype;
+  D->row_bytes = padded_row_bytes(d, dtype);
+  D->bytes = size_t(n * D->row_bytes);
+  rp_status s = dalloc(c, reinterpret_cast<void**>(&D->X), D->bytes);
+  if (s != RP_OK) return s;
+  auto fail_free = [&](rp_status st) {
+    dfree(c, D->X, D->bytes);
+    D->X = nullptr;
+    return st;
+  };
+  if ((s = upload_rows(c, D->X, D->row_bytes, vectors, n, d, dtype, mem_flags)) != RP_OK) return fail_free(s);
+  if (launch_check_finite(D->dev(), c->status, c->stream) != cudaSuccess)
+    return fail_free(fail(c, RP_ECUDA, "check_finite launch failed"));
+
+  Graph* G = new Graph;
+  G->data = D;
+  G->n = n;
+  int64_t nnz_in = 0;
+  if (row_ptr) {
+    if (mem_flags == RP_MEM_HOST) {
+      nnz_in = row_ptr[n];
+      if (row_ptr[0] != 0 || nnz_in < 0) {
+        delete G;
+        return fail_free(fail(c, RP_EINVAL, "row_ptr[0] must be 0 and row_ptr[n] >= 0"));
+      }
+    } else {
+      int64_t ends[2];
+      cudaMemcpyAsync(&ends[0], row_ptr, 8, cudaMemcpyDeviceToHost, c->stream);
+      cudaMemcpyAsync(&ends[1], row_ptr + n, 8, cudaMemcpyDeviceToHost, c->stream);
+      if (cudaStreamSynchronize(c->stream) != cudaSuccess || ends[0] != 0 || ends[1] < 0) {
+        delete G;
+        return fail_free(fail(c, RP_EINVAL, "row_ptr[0] must be 0 and row_ptr[n] >= 0"));
+      }
+      nnz_in = ends[1];
+    }
+  }
+  // device copies of the input CSR
+  int64_t* rp_in = nullptr;
+  int32_t* col_in = nullptr;
+  int32_t* cnt = nullptr;
+  int64_t* bsum = nullptr;
+  int32_t* maxd = nullptr;
+  int64_t* med = nullptr;
+  double* mean = nullptr;
+  double* best = nullptr;
+  const int64_t nblk = (n + 4095) / 4096;
+  auto cleanup = [&]() {
+    dfree(c, rp_in, size_t(n + 1) * 8);
+    dfree(c, col_in, size_t(std::max<int64_t>(nnz_in, 1)) * 4);
+    dfree(c, cnt, size_t(n) * 4);
+    dfree(c, bsum, size_t(nblk) * 8);
+    dfree(c, maxd, 8);
+    dfree(c, med, 8);
+    dfree(c, mean, size_t(d) * 8);
+    dfree(c, best, size_t(2 * medoid_blocks(n)) * 8);
+  };
+  G->col_cap = std::max<int64_t>(nnz_in, 1);
+  s = dalloc(c, reinterpret_cast<void**>(&G->row_ptr), size_t(n + 1) * 8);
+  if (s == RP_OK) s = dalloc(c, reinterpret_cast<void**>(&G->col), size_t(G->col_cap) * 4);
+  if (s == RP_OK) s = dalloc(c, reinterpret_cast<void**>(&rp_in), size_t(n + 1) * 8);
+  if (s == RP_OK) s = dalloc(c, reinterpret_cast<void**>(&col_in), size_t(std::max<int64_t>(nnz_in, 1)) * 4);
+  if (s == RP_OK) s = dalloc(c, reinterpret_cast<void**>(&cnt), size_t(n) * 4);
+  if (s == RP_OK) s = dalloc(c, reinterpret_cast<void**>(&bsum), size_t(nblk) * 8);
+  if (s == RP_OK) s = dalloc(c, reinterpret_cast<void**>(&maxd), 8);
+  if (s == RP_OK) s = dalloc(c, reinterpret_cast<void**>(&med), 8);
+  if (s == RP_OK) s = dalloc(c, reinterpret_cast<void**>(&mean), size_t(d) * 8);
+  if (s == RP_OK) s = dalloc(c, reinterpret_cast<void**>(&best), size_t(2 * medoid_blocks(n)) * 8);
+  if (s != RP_OK) {
+    cleanup();
+    free_graph_mem(c, G);
+    return s;
+  }
+  const cudaMemcpyKind kind = mem_flags == RP_MEM_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
+  cudaError_t ce = cudaSuccess;
+  if (row_ptr) {
+    ce = cudaMemcpyAsync(rp_in, row_ptr, size_t(n + 1) * 8, kind, c->stream);
+    if (ce == cudaSuccess && nnz_in > 0) ce = cudaMemcpyAsync(col_in, col, size_t(nnz_in) * 4, kind, c->stream);
+  } else {
+    ce = cudaMemsetAsync(rp_in, 0, size_t(n + 1) * 8, c->stream);
+  }
+  const unsigned long long zero2[2] = {0, 0};
+  if (ce == cudaSuccess) ce = cudaMemcpyAsync(c->dropped, zero2, 16, cudaMemcpyHostToDevice, c->stream);
+  if (ce == cudaSuccess) ce = launch_validate_csr(rp_in, col_in, n, nnz_in, c->status, c->stream);
+  if (ce == cudaSuccess) ce = cudaStreamSynchronize(c->stream);
+  if (ce != cudaSuccess) {
+    cleanup();
+    free_graph_mem(c, G);
+    return fail(c, RP_ECUDA, "graph upload/validate: %s", cudaGetErrorString(ce));
+  }
+  if ((s = check_device_status(c)) != RP_OK) {
+    cleanup();
+    free_graph_mem(c, G);
+    return fail(c, RP_EINVAL, "invalid input: %s", c->err.c_str());
+  }
+  ce = launch_clean_count(rp_in, col_in, n, cnt, c->dropped, c->stream);
+  if (ce == cudaSuccess) ce = launch_scan_counts(cnt, n, G->row_ptr, bsum, maxd, c->stream);
+  if (ce == cudaSuccess) ce = launch_clean_write(rp_in, col_in, n, G->row_ptr, G->col, c->stream);
+  if (ce == cudaSuccess && start < 0) ce = launch_medoid(D->dev(), mean, best, med, c->stream);
+  int64_t nnz = 0, medoid = start;
+  int32_t maxdeg = 0;
+  unsigned long long dropped[2] = {0, 0};
+  if (ce == cudaSuccess) ce = cudaMemcpyAsync(&nnz, G->row_ptr + n, 8, cudaMemcpyDeviceToHost, c->stream);
+  if (ce == cudaSuccess) ce = cudaMemcpyAsync(&maxdeg, maxd, 4, cudaMemcpyDeviceToHost, c->stream);
+  if (ce == cudaSuccess && start < 0) ce = cudaMemcpyAsync(&medoid, med, 8, cudaMemcpyDeviceToHost, c->stream);
+  if (ce == cudaSuccess) ce = cudaMemcpyAsync(dropped, c->dropped, 16, cudaMemcpyDeviceToHost, c->stream);
+  if (ce == cudaSuccess) ce = cudaStreamSynchronize(c->stream);
+  cleanup();
+  if (ce != cudaSuccess) {
+    free_graph_mem(c, G);
+    return fail(c, RP_ECUDA, "graph cleaning: %s", cudaGetErrorString(ce));
+  }
+  if ((s = check_device_status(c)) != RP_OK) {
+    free_graph_mem(c, G);
+    return s;
+  }
+  if (maxdeg > RP_MAX_DEGREE) {
+    free_graph_mem(c, G);
+    return fail(c, RP_EINVAL, "out-degree %d after cleaning exceeds RP_MAX_DEGREE=%d", maxdeg, RP_MAX_DEGREE);
+  }
+  G->nnz = nnz;
+  G->max_deg_bound = maxdeg;
+  G->start = medoid;
+  G->bytes = size_t(n + 1) * 8 + size_t(G->col_cap) * 4;
+  static_assert(sizeof(unsigned long long) == 8, "");
+  // stats carry the cleaning counters in the spare slots of the status word
+  unsigned long long add[2] = {dropped[0], dropped[1]};
+  DevStatus hs;
+  cudaMemcpyAsync(&hs, c->status, sizeof hs, cudaMemcpyDeviceToHost, c->stream);
+  cudaStreamSynchronize(c->stream);
+  hs.spare[0] += add[0];
+  hs.spare[1] += add[1];
+  cudaMemcpyAsync(c->status, &hs, sizeof hs, cudaMemcpyHostToDevice, c->stream);
+  cudaStreamSynchronize(c->stream);
+  *base_out = add_graph(c, G);
+  return RP_OK;
+}
+
+rp_status rp_tune(rp_ctx* c, rp_graph src, double alpha, int32_t R, int32_t variant, rp_graph* out) {
+  if (!c) return RP_EINVAL;
+  std::lock_guard<std::mutex> lk(c->mu);
+  cudaSetDevice(c->device);
+  return tune_impl(c, src, &alpha, &R, 1, variant, out, false);
+}
+
+rp_status rp_tune_batch(rp_ctx* c, rp_graph src, const double* alphas, const int32_t* Rs, int32_t T,
+                        int32_t variant, rp_graph* outs) {
+  if (!c) return RP_EINVAL;
+  std::lock_guard<std::mutex> lk(c->mu);
+  cudaSetDevice(c->device);
+  return tune_impl(c, src, alphas, Rs, T, variant, outs, true);
+}
+
+rp_status rp_graph_info(rp_ctx* c, rp_graph g, int64_t* n, int64_t* nnz, int32_t* max_deg, int64_t* start) {
+  if (!c) return RP_EINVAL;
+  std::lock_guard<std::mutex> lk(c->mu);
+  cudaSetDevice(c->device);
+  Graph* G = find_graph(c, g);
+  if (!G) return fail(c, RP_ENOTFOUND, "unknown graph %lld", (long long)g);
+  if (G->nnz < 0 || max_deg) {
+    int64_t* rp = nullptr;
+    std::vector<int64_t> h(size_t(G->n + 1));
+    CUDA_TRY(c, cudaMemcpyAsync(h.data(), G->row_ptr, size_t(G->n + 1) * 8, cudaMemcpyDeviceToHost, c->stream));
+    CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    (void)rp;
+    G->nnz = h[size_t(G->n)];
+    int64_t mx = 0;
+    for (int64_t p = 0; p < G->n; ++p) mx = std::max(mx, h[size_t(p + 1)] - h[size_t(p)]);
+    G->max_deg_bound = int(mx);
+    if (max_deg) *max_deg = int32_t(mx);
+  }
+  if (n) *n = G->n;
+  if (nnz) *nnz = G->nnz;
+  if (start) *start = G->start;
+  return check_device_status(c);
+}
+
+rp_status rp_graph_export(rp_ctx* c, rp_graph g, int64_t* row_ptr, int32_t* col, int64_t col_cap,
+                          int32_t mem_flags) {
+  if (!c) return RP_EINVAL;
+  std::lock_guard<std::mutex> lk(c->mu);
+  cudaSetDevice(c->device);
+  Graph* G = find_graph(c, g);
+  if (!G) return fail(c, RP_ENOTFOUND, "unknown graph %lld", (long long)g);
+  if (!row_ptr || (!col && col_cap > 0)) return fail(c, RP_EINVAL, "null argument");
+  if (G->nnz < 0) {
+    CUDA_TRY(c, cudaMemcpyAsync(&G->nnz, G->row_ptr + G->n, 8, cudaMemcpyDeviceToHost, c->stream));
+    CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  }
+  if (col_cap < G->nnz) return fail(c, RP_EINVAL, "col_cap=%lld < nnz=%lld", (long long)col_cap, (long long)G->nnz);
+  const cudaMemcpyKind kind = mem_flags == RP_MEM_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
+  CUDA_TRY(c, cudaMemcpyAsync(row_ptr, G->row_ptr, size_t(G->n + 1) * 8, kind, c->stream));
+  if (G->nnz > 0) CUDA_TRY(c, cudaMemcpyAsync(col, G->col, size_t(G->nnz) * 4, kind, c->stream));
+  if (mem_flags == RP_MEM_HOST) {
+    CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    return check_device_status(c);
+  }
+  return RP_OK;
+}
+
+rp_status rp_graph_free(rp_ctx* c, rp_graph g) {
+  if (!c) return RP_EINVAL;
+  std::lock_guard<std::mutex> lk(c->mu);
+  cudaSetDevice(c->device);
+  auto it = c->graphs.find(g);
+  if (it == c->graphs.end()) return fail(c, RP_ENOTFOUND, "unknown graph %lld", (long long)g);
+  for (auto pl = c->plans.begin(); pl != c->plans.end();) {
+    if (pl->src == g) {
+      if (pl->exec) cudaGraphExecDestroy(pl->exec);
+      pl = c->plans.erase(pl);
+    } else {
+      ++pl;
+    }
+  }
+  free_graph_mem(c, it->second);
+  c->graphs.erase(it);
+  return RP_OK;
+}
+
+rp_status rp_search(rp_ctx* c, rp_graph g, const void* queries, int64_t nq, int32_t L, int32_t k, int32_t* ids,
+                    float* dists, int32_t mem_flags) {
+  if (!c) return RP_EINVAL;
+  std::lock_guard<std::mutex> lk(c->mu);
+  cudaSetDevice(c->device);
+  Graph* G = find_graph(c, g);
+  if (!G) return fail(c, RP_ENOTFOUND, "unknown graph %lld", (long long)g);
+  if (nq < 0 || k < 1 || L < k || L > RP_MAX_L)
+    return fail(c, RP_EINVAL, "need nq >= 0 and 1 <= k <= L <= %d (nq=%lld L=%d k=%d)", RP_MAX_L, (long long)nq, L, k);
+  if (nq == 0) return RP_OK;
+  if (!queries || !ids) return fail(c, RP_EINVAL, "null argument");
+  const Dataset& D = *G->data;
+  rp_status s;
+  const int64_t qbytes = nq * D.row_bytes;
+  const int64_t out_bytes = nq * k * 8;
+  if ((s = grow(c, &c->qbuf, &c->qbuf_bytes, qbytes + (mem_flags == RP_MEM_HOST ? out_bytes : 0))) != RP_OK) return s;
+  if ((s = upload_rows(c, c->qbuf, D.row_bytes, queries, nq, D.d, D.dtype, mem_flags)) != RP_OK) return s;
+  const int slots = search_slots(c->num_sms);
+  const int64_t words = (D.n + 31) / 32;
+  if (c->seen_bits_words < words * slots) {
+    if ((s = grow(c, &c->seen_bits, &c->seen_bits_words, words * slots)) != RP_OK) return s;
+    CUDA_TRY(c, cudaMemsetAsync(c->seen_bits, 0, size_t(c->seen_bits_words) * 4, c->stream));
+  }
+  const int64_t list_cap = 16384;
+  if ((s = grow(c, &c->seen_list, &c->seen_list_elems, list_cap * slots)) != RP_OK) return s;
+  SearchLaunch S;
+  S.data = D.dev();
+  S.row_ptr = G->row_ptr;
+  S.col = G->col;
+  S.start = G->start;
+  S.Q = c->qbuf;
+  S.nq = nq;
+  S.L = L;
+  S.k = k;
+  int32_t* dev_ids = ids;
+  float* dev_d = dists;
+  if (mem_flags == RP_MEM_HOST) {
+    dev_ids = reinterpret_cast<int32_t*>(c->qbuf + qbytes);
+    dev_d = reinterpret_cast<float*>(c->qbuf + qbytes + nq * k * 4);
+  }
+  S.out_ids = dev_ids;
+  S.out_dists = dev_d;
+  S.seen_bits = c->seen_bits;
+  S.seen_words = words;
+  S.seen_list = c->seen_list;
+  S.seen_list_cap = list_cap;
+  S.slots = slots;
+  S.work = c->work;
+  S.status = c->status;
+  S.max_degree = G->max_deg_bound;
+  CUDA_TRY(c, cudaMemsetAsync(c->work, 0, 8 * sizeof(unsigned), c->stream));
+  CUDA_TRY(c, cudaEventRecord(c->ev[3], c->stream));
+  CUDA_TRY(c, launch_search(S, c->stream));
+  CUDA_TRY(c, cudaEventRecord(c->ev[4], c->stream));
+  c->ev_search = true;
+  c->kernel_launches += 1;
+  if (mem_flags == RP_MEM_HOST) {
+    CUDA_TRY(c, cudaMemcpyAsync(ids, dev_ids, size_t(nq * k) * 4, cudaMemcpyDeviceToHost, c->stream));
+    if (dists) CUDA_TRY(c, cudaMemcpyAsync(dists, dev_d, size_t(nq * k) * 4, cudaMemcpyDeviceToHost, c->stream));
+    CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    return check_device_status(c);
+  }
+  return RP_OK;
+}
+
+rp_status rp_knn(rp_ctx* c, rp_graph g, const void* queries, int64_t nq, int32_t k, int32_t* ids, float* dists,
+                 int32_t mem_flags) {
+  if (!c) return RP_EINVAL;
+  std::lock_guard<std::mutex> lk(c->mu);
+  cudaSetDevice(c->device);
+  Graph* G = find_graph(c, g);
+  if (!G) return fail(c, RP_ENOTFOUND, "unknown graph %lld", (long long)g);
+  const Dataset& D = *G->data;
+  if (k < 1 || k > 1024 || nq < 0 || (!queries && nq > D.n))
+    return fail(c, RP_EINVAL, "need 1 <= k <= 1024, nq >= 0 (nq <= n without queries)");
+  if (nq == 0) return RP_OK;
+  if (!ids) return fail(c, RP_EINVAL, "null ids");
+  rp_status s;
+  const int64_t qbytes = queries ? nq * D.row_bytes : 0;
+  const int64_t out_bytes = nq * k * 8;
+  if ((s = grow(c, &c->qbuf, &c->qbuf_bytes, qbytes + (mem_flags == RP_MEM_HOST ? out_bytes : 0))) != RP_OK) return s;
+  if (queries && (s = upload_rows(c, c->qbuf, D.row_bytes, queries, nq, D.d, D.dtype, mem_flags)) != RP_OK) return s;
+  int32_t* dev_ids = ids;
+  float* dev_d = dists;
+  if (mem_flags == RP_MEM_HOST) {
+    dev_ids = reinterpret_cast<int32_t*>(c->qbuf + qbytes);
+    dev_d = reinterpret_cast<float*>(c->qbuf + qbytes + nq * k * 4);
+  }
+  KnnLaunch K;
+  K.data = D.dev();
+  K.Q = queries ? c->qbuf : nullptr;
+  K.nq = nq;
+  K.k = k;
+  K.out_ids = dev_ids;
+  K.out_dists = dev_d;
+  K.status = c->status;
+  K.num_sms = c->num_sms;
+  CUDA_TRY(c, launch_knn(K, c->stream));
+  c->kernel_launches += 1;
+  if (mem_flags == RP_MEM_HOST) {
+    CUDA_TRY(c, cudaMemcpyAsync(ids, dev_ids, size_t(nq * k) * 4, cudaMemcpyDeviceToHost, c->stream));
+    if (dists) CUDA_TRY(c, cudaMemcpyAsync(dists, dev_d, size_t(nq * k) * 4, cudaMemcpyDeviceToHost, c->stream));
+    CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    return check_device_status(c);
+  }
+  return RP_OK;
+}
+
+rp_status rp_recall(rp_ctx* c, const int32_t* found, int32_t ld_found, const int32_t* truth, int32_t ld_truth,
+                    int64_t nq, int32_t k, int64_t* hits, int32_t mem_flags) {
+  if (!c) return RP_EINVAL;
+  std::lock_guard<std::mutex> lk(c->mu);
+  cudaSetDevice(c->device);
+  if (!hits || k < 1 || ld_found < k || ld_truth < k || nq < 0 || k > 1024)
+    return fail(c, RP_EINVAL, "need 1 <= k <= min(ld_found, ld_truth, 1024)");
+  *hits = 0;
+  if (nq == 0) return RP_OK;
+  const int32_t* df = found;
+  const int32_t* dt = truth;
+  rp_status s;
+  if (mem_flags == RP_MEM_HOST) {
+    const int64_t need = nq * (int64_t(ld_found) + ld_truth) * 4;
+    if ((s = grow(c, &c->qbuf, &c->qbuf_bytes, need)) != RP_OK) return s;
+    int32_t* a = reinterpret_cast<int32_t*>(c->qbuf);
+    int32_t* b = a + nq * ld_found;
+    CUDA_TRY(c, cudaMemcpyAsync(a, found, size_t(nq * ld_found) * 4, cudaMemcpyHostToDevice, c->stream));
+    CUDA_TRY(c, cudaMemcpyAsync(b, truth, size_t(nq * ld_truth) * 4, cudaMemcpyHostToDevice, c->stream));
+    df = a;
+    dt = b;
+  }
+  CUDA_TRY(c, cudaMemsetAsync(c->hits, 0, 8, c->stream));
+  CUDA_TRY(c, launch_recall(df, ld_found, dt, ld_truth, nq, k, c->hits, c->stream));
+  c->kernel_launches += 1;
+  unsigned long long h = 0;
+  CUDA_TRY(c, cudaMemcpyAsync(&h, c->hits, 8, cudaMemcpyDeviceToHost, c->stream));
+  CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  *hits = int64_t(h);
+  return check_device_status(c);
+}
+
+rp_status rp_build_knn_base(rp_ctx* c, rp_graph data, int32_t kcand, double alpha, int32_t R, rp_graph* out) {
+  if (!c) return RP_EINVAL;
+  std::lock_guard<std::mutex> lk(c->mu);
+  cudaSetDevice(c->device);
+  Graph* G = find_graph(c, data);
+  if (!G) return fail(c, RP_ENOTFOUND, "unknown graph %lld", (long long)data);
+  if (!out) return fail(c, RP_EINVAL, "null out");
+  if (kcand < 1 || kcand > 128) return fail(c, RP_EINVAL, "kcand=%d outside [1, 128]", kcand);
+  const int64_t n = G->n;
+  const int kk = int(std::min<int64_t>(kcand, n - 1));
+  Graph* K = new Graph;
+  K->data = G->data;
+  K->n = n;
+  K->col_cap = std::max<int64_t>(n * kk, 1);
+  K->start = G->start;
+  K->max_deg_bound = kk;
+  K->nnz = n * kk;
+  rp_status s = dalloc(c, reinterpret_cast<void**>(&K->row_ptr), size_t(n + 1) * 8);
+  if (s == RP_OK) s = dalloc(c, reinterpret_cast<void**>(&K->col), size_t(K->col_cap) * 4);
+  if (s != RP_OK) {
+    free_graph_mem(c, K);
+    return s;
+  }
+  if (kk > 0) {
+    KnnLaunch L;
+    L.data = G->data->dev();
+    L.Q = nullptr;
+    L.nq = n;
+    L.k = kk;
+    L.out_ids = K->col;
+    L.out_dists = nullptr;
+    L.status = c->status;
+    L.num_sms = c->num_sms;
+    cudaError_t ce = launch_knn(L, c->stream);
+    if (ce != cudaSuccess) {
+      free_graph_mem(c, K);
+      return fail(c, RP_ECUDA, "knn: %s", cudaGetErrorString(ce));
+    }
+  }
+  std::vector<int64_t> hrp(size_t(n + 1));
+  for (int64_t p = 0; p <= n; ++p) hrp[size_t(p)] = p * kk;
+  cudaError_t ce = cudaMemcpyAsync(K->row_ptr, hrp.data(), size_t(n + 1) * 8, cudaMemcpyHostToDevice, c->stream);
+  if (ce == cudaSuccess) ce = cudaStreamSynchronize(c->stream);
+  if (ce != cudaSuccess) {
+    free_graph_mem(c, K);
+    return fail(c, RP_ECUDA, "knn graph: %s", cudaGetErrorString(ce));
+  }
+  if ((s = check_device_status(c)) != RP_OK) {
+    free_graph_mem(c, K);
+    return s;
+  }
+  const rp_graph kid = add_graph(c, K);
+  rp_graph res = 0;
+  s = tune_impl(c, kid, &alpha, &R, 1, RP_SORTED, &res, false);
+  auto it = c->graphs.find(kid);
+  free_graph_mem(c, it->second);
+  c->graphs.erase(it);
+  if (s != RP_OK) return s;
+  *out = res;
+  return RP_OK;
+}
+
+rp_status rp_stats(rp_ctx* c, rp_stats_t* out, int32_t reset) {
+  if (!c || !out) return RP_EINVAL;
+  std::lock_guard<std::mutex> lk(c->mu);
+  cudaSetDevice(c->device);
+  DevStatus h;
+  CUDA_TRY(c, cudaMemcpyAsync(&h, c->status, sizeof h, cudaMemcpyDeviceToHost, c->stream));
+  CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  memset(out, 0, sizeof *out);
+  out->nodes_pruned = int64_t(h.nodes_pruned);
+  out->fp64_decisions = int64_t(h.fp64_decisions);
+  out->fp64_sort_keys = int64_t(h.fp64_sort_keys);
+  out->fp64_search_dists = int64_t(h.fp64_search);
+  out->generic_nodes = int64_t(h.generic_nodes);
+  out->self_loops_dropped = int64_t(h.spare[0]);
+  out->duplicates_dropped = int64_t(h.spare[1]);
+  out->graph_replays = c->graph_replays;
+  out->bytes_in_use = c->used;
+  out->bytes_peak = c->peak;
+  out->kernel_launches = c->kernel_launches;
+  if (c->ev_tune) {
+    cudaEventElapsedTime(&out->last_prune_ms, c->ev[0], c->ev[1]);
+    cudaEventElapsedTime(&out->last_emit_ms, c->ev[1], c->ev[2]);
+  }
+  if (c->ev_search) cudaEventElapsedTime(&out->last_search_ms, c->ev[3], c->ev[4]);
+  cudaGetLastError();
+  if (reset) {
+    DevStatus z;
+    memset(&z, 0, sizeof z);
+    z.code = h.code;
+    z.info = h.info;
+    CUDA_TRY(c, cudaMemcpyAsync(c->status, &z, sizeof z, cudaMemcpyHostToDevice, c->stream));
+    CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    c->graph_replays = 0;
+    c->kernel_launches = 0;
+    c->peak = c->used;
+  }
+  return RP_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,444 @@
+// Batched GreedySearch (Algorithm 2) and k-recall@k (§4).
+//
+// One warp runs one query at a time; warps take queries from an atomic
+// counter.  The search list is kept sorted by (distance, id) in shared
+// memory, so "the closest unexpanded member" of Algorithm 2 is the first
+// member without its visited bit, and "retain the closest L" is a cut after
+// a merge.
+//
+// A per-warp bitmap over all n points remembers every point that ever
+// entered the list.  Skipping such points when a neighbour list is added is
+// exactly Algorithm 2: a point still in the list must not be added twice (the
+// list is a set), and a point that was cut can never come back -- once the
+// list has been cut to L members its L-th (distance, id) only decreases, and
+// the cut point was already behind an earlier L-th.
+//
+// Neighbours are added 32 at a time, each batch merged and cut to L before the
+// next; the L closest of a union are the L closest of the L closest of its
+// parts, so this equals adding the whole list and cutting once.
+//
+// Ordering: uint8 distances are exact integers.  float32 distances carry a
+// rigorous single-precision error bound; when two intervals overlap, both
+// distances are recomputed in binary64 (index order, no fused multiply-add)
+// and compared there, so every comparison agrees with the binary64 reading.
+#include <cfloat>
+
+#include "internal.h"
+
+namespace rpk {
+
+namespace {
+
+constexpr int kWarps = 4;  // warps (queries in flight) per CTA
+constexpr unsigned kVisited = 0x80000000u;
+constexpr unsigned kIdMask = 0x7fffffffu;
+
+struct SearchArgs {
+  const uint8_t* X;
+  int64_t row_bytes;
+  int d;
+  int64_t n;
+  const int64_t* row_ptr;
+  const int32_t* col;
+  int64_t start;
+  const uint8_t* Q;
+  int64_t nq;
+  int L;
+  int k;
+  int32_t* out_ids;
+  float* out_dists;
+  uint32_t* seen_bits;
+  int64_t seen_words;
+  int32_t* seen_list;
+  int64_t seen_list_cap;
+  unsigned int* work;
+  DevStatus* status;
+};
+
+struct WarpSmem {
+  unsigned* key[2];
+  unsigned* idv[2];
+  double* d64[2];
+  unsigned* ckey;  // sorted candidates of the current batch
+  unsigned* cid;
+  double* cd64;
+  uint8_t* q;
+};
+
+__host__ __device__ inline size_t warp_bytes(int L, int64_t row_bytes, bool f32) {
+  const size_t cap = size_t(L) + 32;
+  size_t b = 2 * cap * 8 + 32 * 8;  // keys + ids for both buffers, candidate keys + ids
+  if (f32) b += 2 * cap * 8 + 32 * 8;
+  b += size_t(row_bytes);
+  return (b + 127) & ~size_t(127);
+}
+
+__device__ inline WarpSmem carve(unsigned char* base, int L, int64_t row_bytes, bool f32) {
+  WarpSmem w;
+  const size_t cap = size_t(L) + 32;
+  unsigned char* p = base;
+  if (f32) {
+    w.d64[0] = reinterpret_cast<double*>(p);
+    p += cap * 8;
+    w.d64[1] = reinterpret_cast<double*>(p);
+    p += cap * 8;
+    w.cd64 = reinterpret_cast<double*>(p);
+    p += 32 * 8;
+  } else {
+    w.d64[0] = w.d64[1] = w.cd64 = nullptr;
+  }
+  w.q = p;
+  p += row_bytes;
+  w.key[0] = reinterpret_cast<unsigned*>(p);
+  p += cap * 4;
+  w.key[1] = reinterpret_cast<unsigned*>(p);
+  p += cap * 4;
+  w.idv[0] = reinterpret_cast<unsigned*>(p);
+  p += cap * 4;
+  w.idv[1] = reinterpret_cast<unsigned*>(p);
+  p += cap * 4;
+  w.ckey = reinterpret_cast<unsigned*>(p);
+  p += 32 * 4;
+  w.cid = reinterpret_cast<unsigned*>(p);
+  return w;
+}
+
+// d2(q, v) in the search's working precision, as order-preserving bits.
+template <int DT>
+__device__ __forceinline__ unsigned dist_bits(const uint8_t* __restrict__ q, const uint8_t* __restrict__ x,
+                                              int64_t row_bytes) {
+  const uint4* pq = reinterpret_cast<const uint4*>(q);
+  const uint4* px = reinterpret_cast<const uint4*>(x);
+  if constexpr (DT == kU8) {
+    unsigned acc = 0;
+    for (int64_t c = 0; c < row_bytes / 16; ++c) {
+      const uint4 a = pq[c], b = __ldg(px + c);
+      acc = sqdiff4_u8(a.x, b.x, acc);
+      acc = sqdiff4_u8(a.y, b.y, acc);
+      acc = sqdiff4_u8(a.z, b.z, acc);
+      acc = sqdiff4_u8(a.w, b.w, acc);
+    }
+    return acc;
+  } else {
+    float acc = 0.f;
+    for (int64_t c = 0; c < row_bytes / 16; ++c) {
+      const uint4 a = pq[c], b = __ldg(px + c);
+      float t;
+      t = __uint_as_float(a.x) - __uint_as_float(b.x); acc = fmaf(t, t, acc);
+      t = __uint_as_float(a.y) - __uint_as_float(b.y); acc = fmaf(t, t, acc);
+      t = __uint_as_float(a.z) - __uint_as_float(b.z); acc = fmaf(t, t, acc);
+      t = __uint_as_float(a.w) - __uint_as_float(b.w); acc = fmaf(t, t, acc);
+    }
+    return __float_as_uint(acc);
+  }
+}
+
+// Total order on (distance, id) entries.  For float data `d64a`/`d64b` point to
+// the slots caching the binary64 distances (NaN until computed).
+template <int DT>
+__device__ __forceinline__ bool entry_less(unsigned ka, unsigned ia, double* d64a, unsigned kb, unsigned ib,
+                                           double* d64b, const SearchArgs& a, const uint8_t* q, float E,
+                                           float Eabs) {
+  if constexpr (DT == kU8) {
+    return ka < kb || (ka == kb && ia < ib);
+  } else {
+    const float fa = __uint_as_float(ka), fb = __uint_as_float(kb);
+    if (sure_less(fa, fb, E, Eabs)) return true;
+    if (sure_less(fb, fa, E, Eabs)) return false;
+    const float* qf = reinterpret_cast<const float*>(q);
+    const int64_t stride = a.row_bytes / 4;
+    const float* X = reinterpret_cast<const float*>(a.X);
+    double xa = *d64a, xb = *d64b;
+    if (isnan(xa)) {
+      xa = canon_d2_f32(qf, X + int64_t(ia) * stride, a.d);
+      *d64a = xa;
+      atomicAdd(&a.status->fp64_search, 1ull);
+    }
+    if (isnan(xb)) {
+      xb = canon_d2_f32(qf, X + int64_t(ib) * stride, a.d);
+      *d64b = xb;
+      atomicAdd(&a.status->fp64_search, 1ull);
+    }
+    return xa < xb || (xa == xb && ia < ib);
+  }
+}
+
+template <int DT>
+__global__ void __launch_bounds__(kWarps * 32) search_kernel(SearchArgs a) {
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const bool f32 = DT == kF32;
+  WarpSmem S = carve(smem_raw + size_t(w) * warp_bytes(a.L, a.row_bytes, f32), a.L, a.row_bytes, f32);
+  const int64_t slot = int64_t(blockIdx.x) * kWarps + w;
+  uint32_t* bits = a.seen_bits + slot * a.seen_words;
+  int32_t* list = a.seen_list + slot * a.seen_list_cap;
+  const float E = rel_bound(a.d), Eabs = abs_bound(a.d);
+  const double qnan = __longlong_as_double(0x7ff8000000000000ll);
+
+  for (;;) {
+    unsigned qi = 0;
+    if (lane == 0) qi = atomicAdd(a.work, 1u);
+    qi = __shfl_sync(0xffffffffu, qi, 0);
+    if (qi >= a.nq) break;
+    // stage the query row
+    const uint4* src = reinterpret_cast<const uint4*>(a.Q + int64_t(qi) * a.row_bytes);
+    for (int c = lane; c < a.row_bytes / 16; c += 32) reinterpret_cast<uint4*>(S.q)[c] = src[c];
+    __syncwarp();
+
+    int cur = 0;  // which buffer holds the list
+    int size = 1;
+    int64_t nseen = 0;
+    if (lane == 0) {
+      const unsigned s = unsigned(a.start);
+      S.key[0][0] = dist_bits<DT>(S.q, a.X + int64_t(s) * a.row_bytes, a.row_bytes);
+      S.idv[0][0] = s;
+      if (f32) S.d64[0][0] = qnan;
+      bits[s >> 5] |= 1u << (s & 31);
+      list[0] = int32_t(s);
+    }
+    nseen = 1;
+    __syncwarp();
+
+    int64_t iters = 0;
+    for (;;) {
+      // the closest member not yet expanded
+      int pos = -1;
+      for (int c0 = 0; c0 < size; c0 += 32) {
+        const int i = c0 + lane;
+        const bool open = i < size && !(S.idv[cur][i] & kVisited);
+        const unsigned b = __ballot_sync(0xffffffffu, open);
+        if (b) {
+          pos = c0 + __ffs(b) - 1;
+          break;
+        }
+      }
+      if (pos < 0) break;
+      if (++iters > a.n + 1) {  // cannot happen: each point is expanded at most once
+        if (lane == 0) raise_status(a.status, kDevOverflow, qi);
+        break;
+      }
+      const unsigned ps = S.idv[cur][pos] & kIdMask;
+      __syncwarp();
+      if (lane == 0) S.idv[cur][pos] |= kVisited;
+      __syncwarp();
+      const int64_t e0 = a.row_ptr[ps], e1 = a.row_ptr[ps + 1];
+      for (int64_t eb = e0; eb < e1; eb += 32) {
+        // ---- new neighbours of this batch
+        const int64_t e = eb + lane;
+        bool fresh = false;
+        unsigned v = 0;
+        if (e < e1) {
+          v = unsigned(a.col[e]);
+          const unsigned bit = 1u << (v & 31);
+          const unsigned old = atomicOr(&bits[v >> 5], bit);
+          fresh = !(old & bit);
+        }
+        const unsigned fm = __ballot_sync(0xffffffffu, fresh);
+        const int nf = __popc(fm);
+        if (nf == 0) continue;
+        const int rank = __popc(fm & ((1u << lane) - 1));
+        if (fresh && nseen + rank < a.seen_list_cap) list[nseen + rank] = int32_t(v);
+        nseen += nf;
+        unsigned kv = 0xffffffffu;
+        if (fresh) kv = dist_bits<DT>(S.q, a.X + int64_t(v) * a.row_bytes, a.row_bytes);
+        // compact the fresh ones into lanes 0..nf-1
+        unsigned myk = 0xffffffffu, myid = 0xffffffffu;
+        {
+          // lane j takes the j-th fresh entry
+          int srcl = -1;
+          unsigned m = fm;
+          for (int j = 0; j < 32 && m; ++j) {
+            const int l = __ffs(m) - 1;
+            if (j == lane) srcl = l;
+            m &= m - 1;
+          }
+          const unsigned k2 = __shfl_sync(0xffffffffu, kv, srcl < 0 ? 0 : srcl);
+          const unsigned i2 = __shfl_sync(0xffffffffu, v, srcl < 0 ? 0 : srcl);
+          if (srcl >= 0) {
+            myk = k2;
+            myid = i2;
+          }
+        }
+        // ---- sort the batch (bitonic over the warp); empty lanes sort last
+        double myd = qnan;
+        if (f32) S.cd64[lane] = qnan;
+        for (int kk = 2; kk <= 32; kk <<= 1) {
+          for (int j = kk >> 1; j > 0; j >>= 1) {
+            const unsigned ok = __shfl_xor_sync(0xffffffffu, myk, j);
+            const unsigned oi = __shfl_xor_sync(0xffffffffu, myid, j);
+            // dec: 1 = my entry comes first, 0 = the partner's, -1 = undecided
+            int dec;
+            const bool me_empty = myid == 0xffffffffu, o_empty = oi == 0xffffffffu;
+            if (me_empty && o_empty) dec = lane < (lane ^ j) ? 1 : 0;
+            else if (me_empty) dec = 0;
+            else if (o_empty) dec = 1;
+            else if (DT == kU8) dec = (myk < ok || (myk == ok && myid < oi)) ? 1 : 0;
+            else {
+              const float fa = __uint_as_float(myk), fb = __uint_as_float(ok);
+              dec = sure_less(fa, fb, E, Eabs) ? 1 : (sure_less(fb, fa, E, Eabs) ? 0 : -1);
+            }
+            double od = 0.0;
+            if constexpr (DT == kF32) {
+              // an undecided pair is undecided for both lanes: each brings its
+              // own binary64 distance, then both compare there
+              if (dec < 0 && isnan(myd)) {
+                myd = canon_d2_f32(reinterpret_cast<const float*>(S.q),
+                                   reinterpret_cast<const float*>(a.X + int64_t(myid) * a.row_bytes), a.d);
+                atomicAdd(&a.status->fp64_search, 1ull);
+              }
+              od = __shfl_xor_sync(0xffffffffu, myd, j);
+              if (dec < 0) dec = (myd < od || (myd == od && myid < oi)) ? 1 : 0;
+            }
+            const bool less_me = dec == 1;
+            const bool up = (lane & kk) == 0;
+            const bool lower = (lane & j) == 0;
+            const bool take_partner = (lower == up) ? !less_me : less_me;
+            if (take_partner) {
+              myk = ok;
+              myid = oi;
+              myd = od;
+            }
+          }
+        }
+        if (lane < nf) {
+          S.ckey[lane] = myk;
+          S.cid[lane] = myid;
+          if (f32) S.cd64[lane] = myd;
+        }
+        __syncwarp();
+        // ---- merge the sorted batch into the list, keep the first L
+        const int nxt = cur ^ 1;
+        for (int i = lane; i < size; i += 32) {
+          const unsigned bk = S.key[cur][i], bi = S.idv[cur][i];
+          int lo = 0, hi = nf;  // number of candidates before list entry i
+          while (lo < hi) {
+            const int mid = (lo + hi) >> 1;
+            const bool cl = entry_less<DT>(S.ckey[mid], S.cid[mid], f32 ? &S.cd64[mid] : nullptr, bk, bi & kIdMask,
+                                           f32 ? &S.d64[cur][i] : nullptr, a, S.q, E, Eabs);
+            if (cl) lo = mid + 1;
+            else hi = mid;
+          }
+          const int np = i + lo;
+          if (np < a.L) {
+            S.key[nxt][np] = bk;
+            S.idv[nxt][np] = bi;
+            if (f32) S.d64[nxt][np] = S.d64[cur][i];
+          }
+        }
+        if (lane < nf) {
+          const unsigned ck = S.ckey[lane], ci = S.cid[lane];
+          int lo = 0, hi = size;  // number of list entries before candidate lane
+          while (lo < hi) {
+            const int mid = (lo + hi) >> 1;
+            const bool bl = entry_less<DT>(S.key[cur][mid], S.idv[cur][mid] & kIdMask,
+                                           f32 ? &S.d64[cur][mid] : nullptr, ck, ci,
+                                           f32 ? &S.cd64[lane] : nullptr, a, S.q, E, Eabs);
+            if (bl) lo = mid + 1;
+            else hi = mid;
+          }
+          const int np = lane + lo;
+          if (np < a.L) {
+            S.key[nxt][np] = ck;
+            S.idv[nxt][np] = ci;
+            if (f32) S.d64[nxt][np] = S.cd64[lane];
+          }
+        }
+        __syncwarp();
+        size = min(a.L, size + nf);
+        cur = nxt;
+      }
+    }
+    // ---- the k closest members
+    for (int j = lane; j < a.k; j += 32) {
+      const bool have = j < size;
+      a.out_ids[int64_t(qi) * a.k + j] = have ? int32_t(S.idv[cur][j] & kIdMask) : -1;
+      if (a.out_dists) {
+        float dv;
+        if (!have) dv = __int_as_float(0x7f800000);
+        else if (DT == kU8) dv = float(S.key[cur][j]);
+        else dv = __uint_as_float(S.key[cur][j]);
+        a.out_dists[int64_t(qi) * a.k + j] = dv;
+      }
+    }
+    // ---- forget this query's marks
+    if (nseen <= a.seen_list_cap) {
+      for (int64_t j = lane; j < nseen; j += 32) bits[unsigned(list[j]) >> 5] = 0u;
+    } else {
+      for (int64_t j = lane; j < a.seen_words; j += 32) bits[j] = 0u;
+    }
+    __syncwarp();
+  }
+}
+
+__global__ void recall_kernel(const int32_t* __restrict__ found, int ld_found, const int32_t* __restrict__ truth,
+                              int ld_truth, int64_t nq, int k, unsigned long long* hits) {
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t q = int64_t(blockIdx.x) * (blockDim.x >> 5) + w;
+  if (q >= nq) return;
+  const int32_t* f = found + q * ld_found;
+  const int32_t* t = truth + q * ld_truth;
+  unsigned long long h = 0;
+  for (int i = lane; i < k; i += 32) {
+    const int32_t v = f[i];
+    if (v < 0) continue;
+    for (int j = 0; j < k; ++j)
+      if (t[j] == v) {
+        ++h;
+        break;
+      }
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) h += __shfl_down_sync(0xffffffffu, h, o);
+  if (lane == 0 && h) atomicAdd(hits, h);
+}
+
+}  // namespace
+
+int search_slots(int num_sms) { return num_sms * 2 * kWarps; }
+
+cudaError_t launch_search(const SearchLaunch& L, cudaStream_t s) {
+  SearchArgs a{};
+  a.X = L.data.X;
+  a.row_bytes = L.data.row_bytes;
+  a.d = L.data.d;
+  a.n = L.data.n;
+  a.row_ptr = L.row_ptr;
+  a.col = L.col;
+  a.start = L.start;
+  a.Q = L.Q;
+  a.nq = L.nq;
+  a.L = L.L;
+  a.k = L.k;
+  a.out_ids = L.out_ids;
+  a.out_dists = L.out_dists;
+  a.seen_bits = L.seen_bits;
+  a.seen_words = L.seen_words;
+  a.seen_list = L.seen_list;
+  a.seen_list_cap = L.seen_list_cap;
+  a.work = L.work;
+  a.status = L.status;
+  const bool f32 = L.data.dtype == kF32;
+  const size_t bytes = warp_bytes(L.L, L.data.row_bytes, f32) * kWarps;
+  const int grid = L.slots / kWarps;
+  cudaError_t err;
+  if (f32) {
+    err = cudaFuncSetAttribute(search_kernel<kF32>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(bytes));
+    if (err != cudaSuccess) return err;
+    search_kernel<kF32><<<grid, kWarps * 32, bytes, s>>>(a);
+  } else {
+    err = cudaFuncSetAttribute(search_kernel<kU8>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(bytes));
+    if (err != cudaSuccess) return err;
+    search_kernel<kU8><<<grid, kWarps * 32, bytes, s>>>(a);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_recall(const int32_t* found, int ld_found, const int32_t* truth, int ld_truth, int64_t nq, int k,
+                          unsigned long long* hits, cudaStream_t s) {
+  const int per = 8;
+  const int64_t blocks = (nq + per - 1) / per;
+  recall_kernel<<<unsigned(blocks), per * 32, 0, s>>>(found, ld_found, truth, ld_truth, nq, k, hits);
+  return cudaGetLastError();
+}
+
+}  // namespace rpk
