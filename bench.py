@@ -288,6 +288,8 @@ def run_ours(args):
         outs, _ = step(True)
         free(outs)
     prune_ms = statistics.mean(stats_acc["prune_ms"])
+    if not prune_ms > 0:
+        raise RuntimeError(f"prune kernel time not measured: {stats_acc}")
     emit_ms = statistics.mean(stats_acc["emit_ms"])
     search_ms = statistics.mean(stats_acc["search_ms"])
     alg_bytes = float(((deg + 1) * 128 + 4 * deg + 8).sum() + 4 * sum(nnz))
@@ -321,14 +323,14 @@ def run_ours(args):
             free(outs)
         return statistics.median(ts)
 
-    tb = time_tune(True, args.steps)
-    tp = time_tune(False, args.steps)
+    tb = time_tune(True, args.steps) if not args.quick else float("nan")
+    tp = time_tune(False, args.steps) if not args.quick else float("nan")
 
     # ---- single-query latency (batch size 1), on the (1.05, 48) graph
     outs = rp.rp_tune_batch(ctx, base, alphas, Rs)
     g1 = outs[1]
     lat = []
-    q1 = [Qd[i:i + 1] for i in range(min(300, nq))]
+    q1 = [Qd[i:i + 1] for i in range(min(300 if not args.quick else 22, nq))]
     i1 = torch.empty((1, k), dtype=torch.int32, device=dev)
     d1 = torch.empty((1, k), dtype=torch.float32, device=dev)
     for i, q in enumerate(q1):
@@ -347,7 +349,7 @@ def run_ours(args):
 
     # ---- end to end through the C ABI with host buffers
     e2e = None
-    if not args.no_e2e:
+    if not args.no_e2e and not args.quick:
         Xh = torch.from_numpy(X).pin_memory()
         rph = torch.from_numpy(base_rp).pin_memory()
         colh = torch.from_numpy(base_col).pin_memory()
@@ -397,7 +399,7 @@ def run_ours(args):
                "d2h_bytes_per_step": int(d2h), "ms_per_step": 1000 * e2e_s}
 
     cpu = None
-    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline and not args.quick:
         cpu = cpu_baseline(args.cpu_sample)
 
     rp.rp_destroy(ctx)
@@ -454,6 +456,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample", type=int, default=20000)
     ap.add_argument("--ref-sample", type=int, default=20000)
+    ap.add_argument("--quick", action="store_true",
+                    help="timed steps and the per-kernel pass only (for profiler runs)")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         print("note: timing rules ask for >= 3 warm-up steps", file=sys.stderr)

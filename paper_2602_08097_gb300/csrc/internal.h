@@ -89,7 +89,7 @@ struct SearchLaunch {
   int max_degree = 0;
 };
 cudaError_t launch_search(const SearchLaunch& S, cudaStream_t s);
-int search_slots(int num_sms);
+int search_slots(int num_sms, int64_t n);
 cudaError_t launch_recall(const int32_t* found, int ld_found, const int32_t* truth, int ld_truth,
                           int64_t nq, int k, unsigned long long* hits, cudaStream_t s);
 

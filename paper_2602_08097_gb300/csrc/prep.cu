@@ -212,17 +212,43 @@ __global__ void count_write(const int32_t* __restrict__ cnt, int64_t n, const in
 }
 
 // ---- medoid -----------------------------------------------------------------
-__global__ void mean_kernel(const uint8_t* __restrict__ X, int64_t n, int64_t row_bytes, int d, int dtype,
-                            double* __restrict__ mean) {
+// uint8: exact integer column sums in any order (they equal the index-order
+// binary64 sums, which are exact below 2^53).
+__global__ void mean_u8_sum_kernel(const uint8_t* __restrict__ X, int64_t n, int64_t row_bytes, int d,
+                                   unsigned long long* __restrict__ sums) {
+  const int64_t rows_per_block = 4096;
+  const int64_t r0 = int64_t(blockIdx.y) * rows_per_block;
+  const int64_t r1 = min(n, r0 + rows_per_block);
+  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < d; j += gridDim.x * blockDim.x) {
+    unsigned long long s = 0;
+    for (int64_t i = r0; i < r1; ++i) s += X[i * row_bytes + j];
+    atomicAdd(&sums[j], s);
+  }
+}
+
+__global__ void mean_u8_finish_kernel(const unsigned long long* __restrict__ sums, int64_t n, int d,
+                                      double* __restrict__ mean) {
+  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < d; j += gridDim.x * blockDim.x)
+    mean[j] = __ddiv_rn(double(sums[j]), double(n));
+}
+
+// float32: one thread per column adds the rows in index order in binary64;
+// loads are issued eight rows ahead of the dependent additions.
+__global__ void mean_f32_kernel(const uint8_t* __restrict__ X, int64_t n, int64_t row_bytes, int d,
+                                double* __restrict__ mean) {
+  const float* F = reinterpret_cast<const float*>(X);
+  const int64_t stride = row_bytes / 4;
   for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < d; j += gridDim.x * blockDim.x) {
     double s = 0.0;
-    if (dtype == kU8) {
-      for (int64_t i = 0; i < n; ++i) s = __dadd_rn(s, double(X[i * row_bytes + j]));
-    } else {
-      const float* F = reinterpret_cast<const float*>(X);
-      const int64_t stride = row_bytes / 4;
-      for (int64_t i = 0; i < n; ++i) s = __dadd_rn(s, double(F[i * stride + j]));
+    int64_t i = 0;
+    for (; i + 8 <= n; i += 8) {
+      float v[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) v[u] = __ldg(F + (i + u) * stride + j);
+#pragma unroll
+      for (int u = 0; u < 8; ++u) s = __dadd_rn(s, double(v[u]));
     }
+    for (; i < n; ++i) s = __dadd_rn(s, double(F[i * stride + j]));
     mean[j] = __ddiv_rn(s, double(n));
   }
 }
@@ -337,7 +363,18 @@ int64_t medoid_blocks(int64_t n) { return std::min<int64_t>((n + 255) / 256, 204
 
 cudaError_t launch_medoid(const DevData& D, double* mean, double* block_best, int64_t* medoid,
                           cudaStream_t s) {
-  mean_kernel<<<unsigned((D.d + 127) / 128), 128, 0, s>>>(D.X, D.n, D.row_bytes, D.d, D.dtype, mean);
+  if (D.dtype == kU8) {
+    // block_best has room for 2 * medoid_blocks(n) >= d doubles of scratch only when n is
+    // large; the column sums live in `mean` reinterpreted, finished in place.
+    unsigned long long* sums = reinterpret_cast<unsigned long long*>(mean);
+    cudaError_t err = cudaMemsetAsync(sums, 0, size_t(D.d) * 8, s);
+    if (err != cudaSuccess) return err;
+    const dim3 grid(unsigned((D.d + 127) / 128), unsigned((D.n + 4095) / 4096));
+    mean_u8_sum_kernel<<<grid, 128, 0, s>>>(D.X, D.n, D.row_bytes, D.d, sums);
+    mean_u8_finish_kernel<<<unsigned((D.d + 127) / 128), 128, 0, s>>>(sums, D.n, D.d, mean);
+  } else {
+    mean_f32_kernel<<<unsigned((D.d + 31) / 32), 32, 0, s>>>(D.X, D.n, D.row_bytes, D.d, mean);
+  }
   const int64_t nb = medoid_blocks(D.n);
   nearest_mean_kernel<<<unsigned(nb), 256, 0, s>>>(D.X, D.n, D.row_bytes, D.d, D.dtype, mean, block_best);
   pick_medoid_kernel<<<1, 32, 0, s>>>(block_best, nb, medoid);

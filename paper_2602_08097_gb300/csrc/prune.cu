@@ -51,18 +51,16 @@ struct PruneArgs {
 
 template <int MAXM>
 struct FastLayout {
-  static constexpr int MW = MAXM / 64;
-  static constexpr size_t off_D = 0;
-  static constexpr size_t off_slice = off_D + size_t(MAXM) * MAXM * 4;
-  static constexpr size_t off_skey = off_slice + size_t(MAXM + 1) * kPitch;
-  static constexpr size_t off_key64 = off_skey + size_t(MAXM) * 8;
-  static constexpr size_t off_masks = off_key64 + size_t(MAXM) * 8;
-  __host__ __device__ static size_t off_ids(int T) { return off_masks + size_t(T) * MW * MAXM * 8; }
-  __host__ __device__ static size_t off_perm(int T) { return off_ids(T) + size_t(MAXM) * 4; }
-  __host__ __device__ static size_t off_key(int T) { return off_perm(T) + size_t(MAXM) * 4; }
-  __host__ __device__ static size_t off_lnk(int T) { return off_key(T) + size_t(MAXM) * 4; }
-  __host__ __device__ static size_t off_misc(int T) { return off_lnk(T) + size_t(MAXM); }
-  __host__ __device__ static size_t bytes(int T) { return (off_misc(T) + 32 + 127) & ~size_t(127); }
+  static constexpr int MW = MAXM / 64;  // 64-bit mask words per row
+  static constexpr size_t off_D = 0;                                         // MAXM x MAXM d2
+  static constexpr size_t off_slice = off_D + size_t(MAXM) * MAXM * 4;       // (MAXM+1) rows
+  static constexpr size_t off_key64 = off_slice + size_t(MAXM + 1) * kPitch;  // binary64 pivot keys
+  static constexpr size_t off_ids = off_key64 + size_t(MAXM) * 8;
+  static constexpr size_t off_perm = off_ids + size_t(MAXM) * 4;
+  static constexpr size_t off_key = off_perm + size_t(MAXM) * 4;
+  static constexpr size_t off_norm = off_key + size_t(MAXM) * 4;
+  static constexpr size_t off_misc = off_norm + size_t(MAXM) * 4;
+  __host__ __device__ static size_t bytes() { return (off_misc + 32 + 127) & ~size_t(127); }
 };
 
 template <int DT>
@@ -81,6 +79,16 @@ struct Acc<kU8> {
     return sqdiff4_u8(x.w, y.w, acc);
   }
   __device__ static __forceinline__ unsigned long long bits(T v) { return v; }
+  // inner product of 8 bytes (exact): the u8 Gram is built from <x, y>
+  __device__ static __forceinline__ T gram(uint2 x, uint2 y, T acc) {
+    return __dp4a(x.y, y.y, __dp4a(x.x, y.x, acc));
+  }
+  __device__ static __forceinline__ T dot4(uint4 x, uint4 y, T acc) {
+    acc = __dp4a(x.x, y.x, acc);
+    acc = __dp4a(x.y, y.y, acc);
+    acc = __dp4a(x.z, y.z, acc);
+    return __dp4a(x.w, y.w, acc);
+  }
 };
 template <>
 struct Acc<kF32> {
@@ -100,6 +108,9 @@ struct Acc<kF32> {
     return sq(x.w, y.w, acc);
   }
   __device__ static __forceinline__ unsigned long long bits(T v) { return __float_as_uint(v); }
+  // float Gram entries stay in difference form (rigorous relative bound)
+  __device__ static __forceinline__ T gram(uint2 x, uint2 y, T acc) { return step(x, y, acc); }
+  __device__ static __forceinline__ T dot4(uint4, uint4, T acc) { return acc; }
 };
 
 // Full single-precision difference-form d2 between two global rows.
@@ -128,30 +139,78 @@ __device__ __forceinline__ bool tier3_dominates(const PruneArgs& a, int32_t u, i
   return canon_dominates(A2, d2a, d2b);
 }
 
-template <int DT, int MAXM>
-__global__ void __launch_bounds__(128) prune_fast_kernel(PruneArgs a) {
+// Sort MAXM (key, position) pairs held by one warp, E = MAXM / 32 per lane
+// (element index lane + 32 e), ascending by key.  Keys are unique.
+template <int E>
+__device__ __forceinline__ void warp_bitonic(unsigned long long (&key)[E], int (&pos)[E]) {
+  const int lane = threadIdx.x & 31;
+  constexpr int N = 32 * E;
+#pragma unroll
+  for (int k = 2; k <= N; k <<= 1) {
+#pragma unroll
+    for (int j = k >> 1; j > 0; j >>= 1) {
+      if (j >= 32) {
+        const int je = j / 32;
+#pragma unroll
+        for (int e = 0; e < E; ++e) {
+          if (e & je) continue;
+          const int idx = lane + 32 * e;
+          const bool up = (idx & k) == 0;
+          const unsigned long long a = key[e], b = key[e + je];
+          const int pa = pos[e], pb = pos[e + je];
+          const bool sw = up ? (b < a) : (a < b);
+          if (sw) {
+            key[e] = b; key[e + je] = a;
+            pos[e] = pb; pos[e + je] = pa;
+          }
+        }
+      } else {
+#pragma unroll
+        for (int e = 0; e < E; ++e) {
+          const int idx = lane + 32 * e;
+          const unsigned long long o = __shfl_xor_sync(0xffffffffu, key[e], j);
+          const int op = __shfl_xor_sync(0xffffffffu, pos[e], j);
+          const bool lower = (idx & j) == 0;
+          const bool up = (idx & k) == 0;
+          const bool want_min = lower == up;
+          const bool take = want_min ? (o < key[e]) : (key[e] < o);
+          if (take) {
+            key[e] = o;
+            pos[e] = op;
+          }
+        }
+      }
+    }
+  }
+}
+
+template <int DT, int MAXM, int TPW>
+__global__ void __launch_bounds__(128, MAXM == 64 ? 4 : 2) prune_fast_kernel(PruneArgs a) {
   using L = FastLayout<MAXM>;
   using AT = typename Acc<DT>::T;
   constexpr int GT = MAXM;        // threads per node group
   constexpr int NG = 128 / MAXM;  // node groups per CTA
+  constexpr int NW = MAXM / 32;   // warps per group
+  constexpr int E = MAXM / 32;    // columns (and sort elements) per lane
   constexpr int S = MAXM / 8;     // tile stride: a thread's tile rows are a, a+S, ..., a+7S
   constexpr int TPT = (S * S) / GT;
   constexpr int MW = L::MW;
+  // TPW: targets handled per warp at most (warp w takes targets w, w + NW, ...)
   extern __shared__ __align__(128) unsigned char smem_raw[];
   const int T = a.T;
   const int g = threadIdx.x / GT;
   const int t = threadIdx.x % GT;
-  unsigned char* sb = smem_raw + size_t(g) * L::bytes(T);
+  const int wg = t >> 5;  // warp within the group
+  const int lane = threadIdx.x & 31;
+  unsigned char* sb = smem_raw + size_t(g) * L::bytes();
   AT* D = reinterpret_cast<AT*>(sb + L::off_D);
   unsigned char* slice = sb + L::off_slice;
-  unsigned long long* skey = reinterpret_cast<unsigned long long*>(sb + L::off_skey);
   double* key64 = reinterpret_cast<double*>(sb + L::off_key64);
-  unsigned long long* masks = reinterpret_cast<unsigned long long*>(sb + L::off_masks);
-  int32_t* ids = reinterpret_cast<int32_t*>(sb + L::off_ids(T));
-  int32_t* perm = reinterpret_cast<int32_t*>(sb + L::off_perm(T));
-  AT* key = reinterpret_cast<AT*>(sb + L::off_key(T));
-  unsigned char* lnk = sb + L::off_lnk(T);
-  int* misc = reinterpret_cast<int*>(sb + L::off_misc(T));
+  int32_t* ids = reinterpret_cast<int32_t*>(sb + L::off_ids);
+  int32_t* perm = reinterpret_cast<int32_t*>(sb + L::off_perm);
+  AT* key = reinterpret_cast<AT*>(sb + L::off_key);
+  AT* norm = reinterpret_cast<AT*>(sb + L::off_norm);
+  int* misc = reinterpret_cast<int*>(sb + L::off_misc);
 
   auto gsync = [&]() {
     if constexpr (NG == 1) __syncthreads();
@@ -160,7 +219,7 @@ __global__ void __launch_bounds__(128) prune_fast_kernel(PruneArgs a) {
 
   const int count = *a.count;
   const int nslices = int(a.row_bytes / kSlice);
-  const float E = rel_bound(a.d), Eabs = abs_bound(a.d);
+  const float E_rel = rel_bound(a.d), E_abs = abs_bound(a.d);
   long long done = 0;
 
   for (;;) {
@@ -182,7 +241,6 @@ __global__ void __launch_bounds__(128) prune_fast_kernel(PruneArgs a) {
       ids[t] = a.col[e0 + t];
       key64[t] = __longlong_as_double(0x7ff8000000000000ll);  // not computed yet
     }
-    if (t == 0) misc[1] = 0;
     gsync();
 
     // ---- a2 gather + a3 keys + a5 Gram, one 128-byte slice of every row at a time
@@ -194,7 +252,7 @@ __global__ void __launch_bounds__(128) prune_fast_kernel(PruneArgs a) {
       for (int r = 0; r < 8; ++r)
 #pragma unroll
         for (int c = 0; c < 8; ++c) acc[q][r][c] = 0;
-    AT kacc = 0;
+    AT kacc = 0, nacc = 0;
     for (int s = 0; s < nslices; ++s) {
       for (int c = t; c < (m + 1) * 8; c += GT) {
         const int r = c >> 3, part = c & 7;
@@ -208,9 +266,11 @@ __global__ void __launch_bounds__(128) prune_fast_kernel(PruneArgs a) {
         const unsigned char* r0 = slice;
         const unsigned char* r1 = slice + (t + 1) * kPitch;
 #pragma unroll
-        for (int part = 0; part < 8; ++part)
-          kacc = Acc<DT>::step4(*reinterpret_cast<const uint4*>(r0 + part * 16),
-                                *reinterpret_cast<const uint4*>(r1 + part * 16), kacc);
+        for (int part = 0; part < 8; ++part) {
+          const uint4 y = *reinterpret_cast<const uint4*>(r1 + part * 16);
+          kacc = Acc<DT>::step4(*reinterpret_cast<const uint4*>(r0 + part * 16), y, kacc);
+          if constexpr (DT == kU8) nacc = Acc<DT>::dot4(y, y, nacc);
+        }
       }
 #pragma unroll
       for (int q = 0; q < TPT; ++q) {
@@ -232,11 +292,16 @@ __global__ void __launch_bounds__(128) prune_fast_kernel(PruneArgs a) {
             if (r < nr)
 #pragma unroll
               for (int c = 0; c < 8; ++c)
-                if (c < nr) acc[q][r][c] = Acc<DT>::step(rv[r], cv[c], acc[q][r][c]);
+                if (c < nr) acc[q][r][c] = Acc<DT>::gram(rv[r], cv[c], acc[q][r][c]);
         }
       }
       gsync();  // the slice buffer is rewritten next
     }
+    if (t < m) {
+      key[t] = kacc;
+      if constexpr (DT == kU8) norm[t] = nacc;
+    }
+    gsync();
 #pragma unroll
     for (int q = 0; q < TPT; ++q) {
       const int tile = t + q * GT;
@@ -246,119 +311,170 @@ __global__ void __launch_bounds__(128) prune_fast_kernel(PruneArgs a) {
 #pragma unroll
         for (int c = 0; c < 8; ++c) {
           const int i = ta + r * S, j = tb + c * S;
-          if (r < nr && c < nr && i < m && j < m) D[i * MAXM + j] = acc[q][r][c];
+          if (r < nr && c < nr && i < m && j < m) {
+            if constexpr (DT == kU8) D[i * MAXM + j] = norm[i] + norm[j] - 2u * acc[q][r][c];  // exact
+            else D[i * MAXM + j] = acc[q][r][c];
+          }
         }
     }
-    if (t < m) key[t] = kacc;
 
-    // ---- a4 processing order
-    if (a.variant == 0) {
-      skey[t] = t < m ? (Acc<DT>::bits(kacc) << 32) | unsigned(ids[t]) : ~0ull;
-      perm[t] = t;
-      gsync();
-      for (int k = 2; k <= MAXM; k <<= 1) {
-        for (int j = k >> 1; j > 0; j >>= 1) {
-          const int pt = t ^ j;
-          const unsigned long long x = skey[t], y = skey[pt];
-          const int vx = perm[t], vy = perm[pt];
-          const bool up = (t & k) == 0;
-          const bool keep_min = (t < pt) == up;
-          const bool swap = keep_min ? (y < x) : (x < y);
-          gsync();
-          if (swap) {
-            skey[t] = y;
-            perm[t] = vy;
+    // ---- a4 processing order: warp 0 of the group sorts by (key, id)
+    if (wg == 0) {
+      if (a.variant == 0) {
+        unsigned long long sk[E];
+        int sp[E];
+#pragma unroll
+        for (int e = 0; e < E; ++e) {
+          const int j = lane + 32 * e;
+          sk[e] = j < m ? (Acc<DT>::bits(key[j]) << 32) | unsigned(ids[j]) : ~0ull;
+          sp[e] = j;
+        }
+        warp_bitonic<E>(sk, sp);
+#pragma unroll
+        for (int e = 0; e < E; ++e) perm[lane + 32 * e] = sp[e];
+        if constexpr (DT == kF32) {
+          // near-ties of single-precision keys: order them by the binary64 keys
+          __syncwarp();
+          bool link = false;
+#pragma unroll
+          for (int e = 0; e < E; ++e) {
+            const int i = lane + 32 * e;
+            if (i + 1 < m && !sure_less(key[perm[i]], key[perm[i + 1]], E_rel, E_abs)) link = true;
           }
-          gsync();
-        }
-      }
-      if constexpr (DT == kF32) {
-        // near-ties of single-precision keys: order them by the binary64 keys
-        lnk[t] = 0;
-        if (t + 1 < m && !sure_less(key[perm[t]], key[perm[t + 1]], E, Eabs)) {
-          lnk[t] = 1;
-          misc[1] = 1;
-        }
-        gsync();
-        if (misc[1]) {
-          const bool member = t < m && (lnk[t] || (t > 0 && lnk[t - 1]));
-          if (member) {
+          if (__any_sync(0xffffffffu, link) && lane == 0) {
             const float* X = reinterpret_cast<const float*>(a.X);
             const int64_t stride = a.row_bytes / 4;
-            key64[perm[t]] = canon_d2_f32(X + int64_t(p) * stride, X + int64_t(ids[perm[t]]) * stride, a.d);
-            atomicAdd(&a.status->fp64_sort_keys, 1ull);
-          }
-          gsync();
-          if (member && !(t > 0 && lnk[t - 1])) {
-            int end = t;
-            while (end + 1 < m && lnk[end]) ++end;
-            for (int i = t + 1; i <= end; ++i) {  // insertion sort of the run by (key64, id)
-              const int v = perm[i];
-              int j = i - 1;
-              while (j >= t && (key64[perm[j]] > key64[v] ||
-                                (key64[perm[j]] == key64[v] && ids[perm[j]] > ids[v]))) {
-                perm[j + 1] = perm[j];
-                --j;
+            int i = 0;
+            while (i < m) {
+              int end = i;
+              while (end + 1 < m && !sure_less(key[perm[end]], key[perm[end + 1]], E_rel, E_abs)) ++end;
+              if (end > i) {
+                for (int r = i; r <= end; ++r)
+                  key64[perm[r]] = canon_d2_f32(X + int64_t(p) * stride, X + int64_t(ids[perm[r]]) * stride, a.d);
+                atomicAdd(&a.status->fp64_sort_keys, static_cast<unsigned long long>(end - i + 1));
+                for (int r = i + 1; r <= end; ++r) {  // insertion sort of the run by (key64, id)
+                  const int v = perm[r];
+                  int z = r - 1;
+                  while (z >= i && (key64[perm[z]] > key64[v] || (key64[perm[z]] == key64[v] && ids[perm[z]] > ids[v]))) {
+                    perm[z + 1] = perm[z];
+                    --z;
+                  }
+                  perm[z + 1] = v;
+                }
               }
-              perm[j + 1] = v;
+              i = end + 1;
             }
           }
         }
+      } else {
+#pragma unroll
+        for (int e = 0; e < E; ++e) perm[lane + 32 * e] = lane + 32 * e;
       }
-    } else {
-      perm[t] = t;
     }
     gsync();
 
-    // ---- a6 domination bits: row i (processing order) marks the later v it removes
-    if (t < m) {
-      const int i = t, pi = perm[i];
-      const AT* Drow = D + pi * MAXM;
-      for (int tt = 0; tt < T; ++tt) {
-        const int64_t A2 = int64_t(a.A[tt]) * a.A[tt];
+    // ---- a6 domination bits + a7 greedy scan, fused and lazy: walk the
+    // processing order once; a row is evaluated only when it is kept by at
+    // least one of this warp's targets.  Lane l owns columns l + 32 e.
+    {
+      int pj[E];
+      AT kj[E];
+#pragma unroll
+      for (int e = 0; e < E; ++e) {
+        const int j = lane + 32 * e;
+        pj[e] = j < m ? perm[j] : 0;
+        kj[e] = j < m ? key[pj[e]] : AT(0);
+      }
+      unsigned long long al[TPW][MW];
+      int kept[TPW];
+      int Rt[TPW];
+      float A2f[TPW];
+      double A2d[TPW];
+      // uint8: u removes v  <=>  A^2 d2(u, v) <= 1e6 d2(p, v)  <=>  d2(u, v) <= floor(1e6 d2(p, v) / A^2)
+      unsigned thr[TPW][E];
+      unsigned long long live[MW];  // rows still live for at least one of this warp's targets
+#pragma unroll
+      for (int w = 0; w < MW; ++w) live[w] = 0;
+#pragma unroll
+      for (int u = 0; u < TPW; ++u) {
+        const int tt = wg + NW * u;
+        const bool mine = tt < T;
+        const int64_t A2 = mine ? int64_t(a.A[tt]) * a.A[tt] : 1;
+        kept[u] = 0;
+        Rt[u] = mine ? a.R[tt] : 0;
+        A2f[u] = float(A2);
+        A2d[u] = double(A2);
+#pragma unroll
+        for (int e = 0; e < E; ++e) {
+          if constexpr (DT == kU8) thr[u][e] = unsigned((1000000ull * static_cast<unsigned long long>(kj[e])) / A2);
+          else thr[u][e] = 0;
+        }
 #pragma unroll
         for (int w = 0; w < MW; ++w) {
+          const int lo = 64 * w;
           unsigned long long bits = 0;
-          const int jlo = max(i + 1, 64 * w), jhi = min(m, 64 * w + 64);
-          for (int j = jlo; j < jhi; ++j) {
-            const int pj = perm[j];
-            bool dom;
-            if constexpr (DT == kU8) {
-              dom = static_cast<unsigned long long>(A2) * Drow[pj] <=
-                    1000000ull * static_cast<unsigned long long>(key[pj]);
-            } else {
-              const int r = sure_dominates(float(A2), Drow[pj], key[pj], E, Eabs);
-              dom = r >= 0 ? (r == 1) : tier3_dominates(a, ids[pi], ids[pj], p, &key64[pj], double(A2));
-            }
-            if (dom) bits |= 1ull << (j & 63);
-          }
-          masks[(tt * MW + w) * MAXM + i] = bits;
+          if (mine && m > lo) bits = (m - lo >= 64) ? ~0ull : ((1ull << (m - lo)) - 1);
+          al[u][w] = bits;
+          live[w] |= bits;
         }
       }
-    }
-    gsync();
-
-    // ---- a7 greedy scan per target, a8 kept ids into scratch
-    if (t < T) {
-      unsigned long long al0, al1 = 0;
-      al0 = m >= 64 ? ~0ull : ((1ull << m) - 1);
-      if (MW == 2) al1 = m >= 128 ? ~0ull : (m > 64 ? ((1ull << (m - 64)) - 1) : 0ull);
-      int32_t* out = a.out_col[t] + e0;
-      const int R = a.R[t];
-      int kept = 0;
       for (;;) {
         int i;
-        if (al0) i = __ffsll(static_cast<long long>(al0)) - 1;
-        else if (MW == 2 && al1) i = 64 + __ffsll(static_cast<long long>(al1)) - 1;
+        if (live[0]) i = __ffsll(static_cast<long long>(live[0])) - 1;
+        else if (MW == 2 && live[MW - 1]) i = 64 + __ffsll(static_cast<long long>(live[MW - 1])) - 1;
         else break;
-        out[kept++] = ids[perm[i]];
-        if (i < 64) al0 &= ~(1ull << i);
-        else al1 &= ~(1ull << (i - 64));
-        if (kept == R) break;
-        al0 &= ~masks[(t * MW + 0) * MAXM + i];
-        if (MW == 2) al1 &= ~masks[(t * MW + 1) * MAXM + i];
+        const int wi = i >> 6;
+        const unsigned long long bit = 1ull << (i & 63);
+        const int pi = perm[i];
+        AT dv[E];
+#pragma unroll
+        for (int e = 0; e < E; ++e) dv[e] = D[pi * MAXM + pj[e]];
+#pragma unroll
+        for (int u = 0; u < TPW; ++u) {
+          if (!(al[u][wi] & bit)) continue;
+          const int tt = wg + NW * u;
+          if (lane == 0) a.out_col[tt][e0 + kept[u]] = ids[pi];
+          ++kept[u];
+          al[u][wi] &= ~bit;
+          if (kept[u] == Rt[u]) {
+#pragma unroll
+            for (int w = 0; w < MW; ++w) al[u][w] = 0;
+            continue;
+          }
+          unsigned bal[E];
+#pragma unroll
+          for (int e = 0; e < E; ++e) {
+            const int j = lane + 32 * e;
+            bool dom = false;
+            if (j > i && j < m) {
+              if constexpr (DT == kU8) {
+                dom = dv[e] <= thr[u][e];
+              } else {
+                const int r = sure_dominates(A2f[u], dv[e], kj[e], E_rel, E_abs);
+                dom = r >= 0 ? (r == 1) : tier3_dominates(a, ids[pi], ids[pj[e]], p, &key64[pj[e]], A2d[u]);
+              }
+            }
+            bal[e] = __ballot_sync(0xffffffffu, dom);
+          }
+#pragma unroll
+          for (int w = 0; w < MW; ++w)
+            al[u][w] &= ~((static_cast<unsigned long long>(bal[2 * w + 1]) << 32) | bal[2 * w]);
+        }
+#pragma unroll
+        for (int w = 0; w < MW; ++w) {
+          unsigned long long lv = 0;
+#pragma unroll
+          for (int u = 0; u < TPW; ++u) lv |= al[u][w];
+          live[w] = lv;
+        }
       }
-      a.out_cnt[t][p] = kept;
+      if (lane == 0) {
+#pragma unroll
+        for (int u = 0; u < TPW; ++u) {
+          const int tt = wg + NW * u;
+          if (tt < T) a.out_cnt[tt][p] = kept[u];
+        }
+      }
     }
     ++done;
     gsync();
@@ -709,12 +825,11 @@ cudaError_t launch_bucket_nodes(const int64_t* row_ptr, int64_t n, int32_t* list
   return cudaGetLastError();
 }
 
-template <int DT, int MAXM>
-static cudaError_t run_fast(const PruneArgs& args, int num_sms, int64_t host_count, cudaStream_t s) {
-  if (host_count <= 0) return cudaSuccess;
-  const size_t per_group = FastLayout<MAXM>::bytes(args.T);
+template <int DT, int MAXM, int TPW>
+static cudaError_t run_fast_t(const PruneArgs& args, int num_sms, int64_t host_count, cudaStream_t s) {
+  const size_t per_group = FastLayout<MAXM>::bytes();
   const size_t bytes = per_group * (128 / MAXM);
-  auto kern = prune_fast_kernel<DT, MAXM>;
+  auto kern = prune_fast_kernel<DT, MAXM, TPW>;
   cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(bytes));
   if (err != cudaSuccess) return err;
   int per_sm = 0;
@@ -725,6 +840,19 @@ static cudaError_t run_fast(const PruneArgs& args, int num_sms, int64_t host_cou
   const int64_t grid = std::min<int64_t>(int64_t(num_sms) * per_sm, groups_needed);
   kern<<<unsigned(grid), 128, bytes, s>>>(args);
   return cudaGetLastError();
+}
+
+// Picks the kernel instance whose per-warp target slots cover T (targets are
+// dealt to the MAXM/32 warps of a node group round-robin).
+template <int DT, int MAXM>
+static cudaError_t run_fast(const PruneArgs& args, int num_sms, int64_t host_count, cudaStream_t s) {
+  if (host_count <= 0) return cudaSuccess;
+  constexpr int NW = MAXM / 32;
+  const int tpw = (args.T + NW - 1) / NW;
+  if (tpw <= 1) return run_fast_t<DT, MAXM, 1>(args, num_sms, host_count, s);
+  if (tpw <= 2) return run_fast_t<DT, MAXM, 2>(args, num_sms, host_count, s);
+  if (tpw <= 4) return run_fast_t<DT, MAXM, 4>(args, num_sms, host_count, s);
+  return run_fast_t<DT, MAXM, kMaxTargets / NW>(args, num_sms, host_count, s);
 }
 
 template <int DT>

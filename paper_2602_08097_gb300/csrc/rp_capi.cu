@@ -183,6 +183,16 @@ rp_status check_device_status(rp_ctx* c) {
   return RP_OK;
 }
 
+// Records a timing event; inside a stream capture it becomes an event-record
+// node of the graph (cudaEventRecordExternal), so replays time themselves.
+cudaError_t record(cudaEvent_t e, cudaStream_t s) {
+  cudaStreamCaptureStatus st = cudaStreamCaptureStatusNone;
+  cudaError_t err = cudaStreamIsCapturing(s, &st);
+  if (err != cudaSuccess) return err;
+  return st == cudaStreamCaptureStatusActive ? cudaEventRecordWithFlags(e, s, cudaEventRecordExternal)
+                                             : cudaEventRecord(e, s);
+}
+
 Graph* find_graph(rp_ctx* c, rp_graph g) {
   auto it = c->graphs.find(g);
   return it == c->graphs.end() ? nullptr : it->second;
@@ -268,11 +278,11 @@ rp_status enqueue_tune(rp_ctx* c, Graph* S, int T, const int32_t* A, const int32
     dst_rp[t] = outs[t]->row_ptr;
   }
   CUDA_TRY(c, cudaMemsetAsync(c->work, 0, 8 * sizeof(unsigned), c->stream));
-  CUDA_TRY(c, cudaEventRecord(c->ev[0], c->stream));
+  CUDA_TRY(c, record(c->ev[0], c->stream));
   CUDA_TRY(c, launch_prune(L, c->stream));
-  CUDA_TRY(c, cudaEventRecord(c->ev[1], c->stream));
+  CUDA_TRY(c, record(c->ev[1], c->stream));
   CUDA_TRY(c, launch_emit_csr(S->n, T, S->row_ptr, scr, cnt, dst_rp, dst_col, c->scratch_bsum, c->stream));
-  CUDA_TRY(c, cudaEventRecord(c->ev[2], c->stream));
+  CUDA_TRY(c, record(c->ev[2], c->stream));
   c->ev_tune = true;
   int64_t k = 3;
   for (int b = 0; b < 3; ++b) k += L.host_bucket_count[b] > 0;
@@ -710,7 +720,7 @@ rp_status rp_search(rp_ctx* c, rp_graph g, const void* queries, int64_t nq, int3
   const int64_t out_bytes = nq * k * 8;
   if ((s = grow(c, &c->qbuf, &c->qbuf_bytes, qbytes + (mem_flags == RP_MEM_HOST ? out_bytes : 0))) != RP_OK) return s;
   if ((s = upload_rows(c, c->qbuf, D.row_bytes, queries, nq, D.d, D.dtype, mem_flags)) != RP_OK) return s;
-  const int slots = search_slots(c->num_sms);
+  const int slots = search_slots(c->num_sms, D.n);
   const int64_t words = (D.n + 31) / 32;
   if (c->seen_bits_words < words * slots) {
     if ((s = grow(c, &c->seen_bits, &c->seen_bits_words, words * slots)) != RP_OK) return s;
@@ -744,9 +754,9 @@ rp_status rp_search(rp_ctx* c, rp_graph g, const void* queries, int64_t nq, int3
   S.status = c->status;
   S.max_degree = G->max_deg_bound;
   CUDA_TRY(c, cudaMemsetAsync(c->work, 0, 8 * sizeof(unsigned), c->stream));
-  CUDA_TRY(c, cudaEventRecord(c->ev[3], c->stream));
+  CUDA_TRY(c, record(c->ev[3], c->stream));
   CUDA_TRY(c, launch_search(S, c->stream));
-  CUDA_TRY(c, cudaEventRecord(c->ev[4], c->stream));
+  CUDA_TRY(c, record(c->ev[4], c->stream));
   c->ev_search = true;
   c->kernel_launches += 1;
   if (mem_flags == RP_MEM_HOST) {

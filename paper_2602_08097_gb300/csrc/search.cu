@@ -394,7 +394,16 @@ __global__ void recall_kernel(const int32_t* __restrict__ found, int ld_found, c
 
 }  // namespace
 
-int search_slots(int num_sms) { return num_sms * 2 * kWarps; }
+// Queries in flight: enough warps to hide the latency of each expansion (32
+// per SM), fewer if the per-warp membership bitmaps (n bits each) would pass
+// 4 GB.
+int search_slots(int num_sms, int64_t n) {
+  const int64_t bitmap_bytes = ((n + 31) / 32) * 4;
+  int64_t slots = int64_t(num_sms) * 32;
+  const int64_t cap = (int64_t(4) << 30) / std::max<int64_t>(bitmap_bytes, 1);
+  slots = std::min(slots, std::max<int64_t>(cap, int64_t(num_sms) * kWarps));
+  return int(slots / kWarps * kWarps);
+}
 
 cudaError_t launch_search(const SearchLaunch& L, cudaStream_t s) {
   SearchArgs a{};
