@@ -411,7 +411,7 @@ def run_ours(args):
             "config": {"workload": workload_name(n, nq), "n": n, "d": 128, "targets": TARGETS,
                        "queries": nq, "L": L_SEARCH, "k": k, "l2": "flushed (512 MB write) before every timed step",
                        "parallelism": f"replicas x{ws}" if ws > 1 else "1 GPU"},
-            "roofline": {"bound": "hbm", "kernel": "prune_fast_kernel<u8,64>", "achieved": achieved,
+            "roofline": {"bound": "hbm", "kernel": "prune_tc_kernel<u8,64> (tcgen05 Gram)", "achieved": achieved,
                          "peak": hbm_peak, "unit": "GB/s", "frac": achieved / hbm_peak, "traffic": traffic,
                          "peak_kind": peak_kind, "algorithmic_bytes_per_launch": alg_bytes,
                          "launch_ms": prune_ms},
@@ -438,7 +438,7 @@ def run_ours(args):
 def kernel_hash():
     import hashlib
     h = hashlib.sha256()
-    for f in ("prune.cu", "common.cuh"):
+    for f in ("prune.cu", "common.cuh", "tc.cuh"):
         with open(os.path.join(ROOT, "paper_2602_08097_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]

@@ -33,7 +33,7 @@ struct DevStatus {
   unsigned long long fp64_search;
   unsigned long long generic_nodes;
   unsigned long long nodes_pruned;
-  unsigned long long spare[3];
+  unsigned long long spare[3];  // [0] self loops, [1] duplicates, [2] single-precision rechecks
 };
 
 enum DevCode : int {

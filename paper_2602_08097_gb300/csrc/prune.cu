@@ -2,34 +2,36 @@
 // for every node p, each reading only the input graph) and the CSR emit.
 //
 // Per node p with m = |N_out(p)| candidates (Algorithm 1):
-//   a2 gather    the rows of p and of its m candidates, 128-byte slices at a
-//                time, into shared memory (cp.async, 16-byte copies);
-//   a3 keys      d2(p, v) for every candidate v;
-//   a5 Gram      d2(u, v) for every candidate pair (difference form);
+//   a2 gather    each thread loads its candidate's row (and p's row) with
+//                16-byte vector loads and writes it as a bf16 MMA operand;
+//   a3 keys      d2(p, v) for every candidate v, exactly / single precision;
+//   a5 Gram      G = A A^T for the candidates on the tensor cores (tcgen05,
+//                accumulator in TMEM), d2(u, v) = |u|^2 + |v|^2 - 2 G(u, v);
 //   a4 sort      processing order = ascending (d2(p, v), id) -- the argmin of
 //                Algorithm 1 taken in one go, ties to the smaller id -- or the
 //                stored order for UnsortedRobustPrune;
 //   a6 decide    for every target t and every pair u before v in that order,
 //                bit "u removes v": alpha_t * D(u, v) <= D(p, v);
 //   a7 scan      per target: keep the first live candidate, stop at R_t, drop
-//                every candidate the kept one removes (warp-free bit scan);
+//                every candidate the kept one removes (warp ballots over
+//                64-bit live masks; a6 is evaluated lazily inside this loop,
+//                only for rows some target keeps);
 //   a8 emit      kept ids in kept order into per-target scratch, then counts
 //                -> row_ptr (scan) -> compacted col.
 // Because removal is only ever done by kept points, "take the argmin of the
 // live set" (Algorithm 1) and "walk the sorted order, skipping removed
 // points" pick the same sequence; the bit scan is the latter.
 //
-// Fast path: m <= 64 (two nodes per 128-thread CTA, 64 threads each) and
-// 64 < m <= 128 (one node per CTA).  Larger degrees take the generic path
-// (one node per 256-thread CTA, lazy distances, no Gram in shared memory).
+// Tensor-core path: m <= 64 (two nodes per 128-thread CTA, one 128 x 128
+// MMA) and 64 < m <= 128 (one node per CTA).  Larger degrees take the generic
+// path (one node per 256-thread CTA, lazy CUDA-core distances).
 #include "internal.h"
+#include "tc.cuh"
 
 namespace rpk {
 
 namespace {
 
-constexpr int kSlice = 128;  // bytes of every row staged per slice
-constexpr int kPitch = 144;  // shared-memory row pitch (16 bytes of padding)
 
 struct PruneArgs {
   const uint8_t* X;
@@ -47,20 +49,6 @@ struct PruneArgs {
   int32_t* out_col[kMaxTargets];
   int32_t* out_cnt[kMaxTargets];
   DevStatus* status;
-};
-
-template <int MAXM>
-struct FastLayout {
-  static constexpr int MW = MAXM / 64;  // 64-bit mask words per row
-  static constexpr size_t off_D = 0;                                         // MAXM x MAXM d2
-  static constexpr size_t off_slice = off_D + size_t(MAXM) * MAXM * 4;       // (MAXM+1) rows
-  static constexpr size_t off_key64 = off_slice + size_t(MAXM + 1) * kPitch;  // binary64 pivot keys
-  static constexpr size_t off_ids = off_key64 + size_t(MAXM) * 8;
-  static constexpr size_t off_perm = off_ids + size_t(MAXM) * 4;
-  static constexpr size_t off_key = off_perm + size_t(MAXM) * 4;
-  static constexpr size_t off_norm = off_key + size_t(MAXM) * 4;
-  static constexpr size_t off_misc = off_norm + size_t(MAXM) * 4;
-  __host__ __device__ static size_t bytes() { return (off_misc + 32 + 127) & ~size_t(127); }
 };
 
 template <int DT>
@@ -184,156 +172,283 @@ __device__ __forceinline__ void warp_bitonic(unsigned long long (&key)[E], int (
   }
 }
 
-template <int DT, int MAXM, int TPW>
-__global__ void __launch_bounds__(128, MAXM == 64 ? 4 : 2) prune_fast_kernel(PruneArgs a) {
-  using L = FastLayout<MAXM>;
-  using AT = typename Acc<DT>::T;
-  constexpr int GT = MAXM;        // threads per node group
-  constexpr int NG = 128 / MAXM;  // node groups per CTA
-  constexpr int NW = MAXM / 32;   // warps per group
-  constexpr int E = MAXM / 32;    // columns (and sort elements) per lane
-  constexpr int S = MAXM / 8;     // tile stride: a thread's tile rows are a, a+S, ..., a+7S
-  constexpr int TPT = (S * S) / GT;
-  constexpr int MW = L::MW;
-  // TPW: targets handled per warp at most (warp w takes targets w, w + NW, ...)
-  extern __shared__ __align__(128) unsigned char smem_raw[];
-  const int T = a.T;
-  const int g = threadIdx.x / GT;
-  const int t = threadIdx.x % GT;
-  const int wg = t >> 5;  // warp within the group
-  const int lane = threadIdx.x & 31;
-  unsigned char* sb = smem_raw + size_t(g) * L::bytes();
-  AT* D = reinterpret_cast<AT*>(sb + L::off_D);
-  unsigned char* slice = sb + L::off_slice;
-  double* key64 = reinterpret_cast<double*>(sb + L::off_key64);
-  int32_t* ids = reinterpret_cast<int32_t*>(sb + L::off_ids);
-  int32_t* perm = reinterpret_cast<int32_t*>(sb + L::off_perm);
-  AT* key = reinterpret_cast<AT*>(sb + L::off_key);
-  AT* norm = reinterpret_cast<AT*>(sb + L::off_norm);
-  int* misc = reinterpret_cast<int*>(sb + L::off_misc);
+// ---------------------------------------------------------------------------
+// tensor-core path: the candidate Gram on tcgen05
+// ---------------------------------------------------------------------------
+// One CTA of 128 threads stacks the candidates of NG = 128 / MAXM nodes as the
+// 128 rows of one MMA (M = N = 128): D = A A^T, A = candidates x dims in bf16,
+// accumulated in f32 in TMEM.  Row r of the CTA is candidate r % MAXM of node
+// group r / MAXM, and TMEM lane r holds its Gram row; the diagonal MAXM x MAXM
+// blocks are the nodes' Grams.
+//   uint8: values 0..255 are exact in bf16, products exact in f32, and every
+//          partial sum is an integer below 2^24, so G is exact and
+//          d2(u, v) = |u|^2 + |v|^2 - 2 G(u, v) is the exact integer.
+//   float: d2~ = |u|^2 + |v|^2 - 2 G~ with |d2~ - d2| <= err(u, v) =
+//          2 eps_ip |u||v| + (d + 12) 2^-24 (|u|^2 + |v|^2) + tiny, eps_ip =
+//          2^-7 + 2^-16 + d 2^-22 (bf16 rounding of both operands plus f32
+//          accumulation with a factor 2 allowance).  A domination test whose
+//          margin is inside that bound is redone in single-precision
+//          difference form from the rows (rigorous relative bound), and if
+//          still inside, in binary64.
+template <int MAXM>
+struct TcLayout {
+  static constexpr int NG = 128 / MAXM;
+  // The MMA operand (128 rows x 128 dims bf16, 32 KB) is dead once the MMA has
+  // completed, so the d2 matrices of the node groups reuse its space.
+  static constexpr size_t opnd_bytes = 128 * 128 * 2;
+  static constexpr size_t g_D = size_t(MAXM) * MAXM * 4;
+  static constexpr size_t big = opnd_bytes > NG * g_D ? opnd_bytes : NG * g_D;
+  static constexpr size_t off_opnd = 0;
+  static constexpr size_t off_D = 0;
+  static constexpr size_t off_grp = big;
+  static constexpr size_t g_key64 = 0;
+  static constexpr size_t g_ids = g_key64 + size_t(MAXM) * 8;
+  static constexpr size_t g_perm = g_ids + size_t(MAXM) * 4;
+  static constexpr size_t g_key = g_perm + size_t(MAXM) * 4;
+  static constexpr size_t g_norm = g_key + size_t(MAXM) * 4;
+  static constexpr size_t g_sn = g_norm + size_t(MAXM) * 4;
+  static constexpr size_t g_bytes = g_sn + size_t(MAXM) * 4;
+  static constexpr size_t off_misc = off_grp + NG * g_bytes;  // node / degree (current, next), mbar, tmem
+  static constexpr size_t bytes = (off_misc + 64 + 127) & ~size_t(127);
+};
 
-  auto gsync = [&]() {
-    if constexpr (NG == 1) __syncthreads();
-    else named_sync(1 + g, GT);
+// d2 matrix element (row, col) of one node group, columns XOR-swizzled by the
+// row so that row writes and row reads are both free of bank conflicts.
+template <int MAXM>
+__device__ __forceinline__ int dix(int row, int col) {
+  return row * MAXM + (col ^ (row & 31));
+}
+
+template <int DT, int MAXM, int TPW>
+__global__ void __launch_bounds__(128) prune_tc_kernel(PruneArgs a) {
+  using L = TcLayout<MAXM>;
+  using AT = typename Acc<DT>::T;
+  constexpr int NG = L::NG;
+  constexpr int GT = MAXM;       // threads per node group
+  constexpr int NW = MAXM / 32;  // warps per group
+  constexpr int E = MAXM / 32;   // columns per lane in the scan
+  constexpr int MW = MAXM / 64;
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  const int T = a.T;
+  const int r = threadIdx.x;  // CTA row = TMEM lane
+  const int g = r / GT;
+  const int t = r % GT;
+  const int wg = t >> 5;
+  const int lane = r & 31;
+  const int warp = r >> 5;
+  unsigned char* opnd = smem_raw + L::off_opnd;
+  float* D = reinterpret_cast<float*>(smem_raw + L::off_D + g * L::g_D);
+  unsigned char* gb = smem_raw + L::off_grp + g * L::g_bytes;
+  double* key64 = reinterpret_cast<double*>(gb + L::g_key64);
+  int32_t* ids = reinterpret_cast<int32_t*>(gb + L::g_ids);
+  int32_t* perm = reinterpret_cast<int32_t*>(gb + L::g_perm);
+  AT* key = reinterpret_cast<AT*>(gb + L::g_key);
+  AT* norm = reinterpret_cast<AT*>(gb + L::g_norm);
+  float* sn = reinterpret_cast<float*>(gb + L::g_sn);
+  int* misc = reinterpret_cast<int*>(smem_raw + L::off_misc);  // [g] node, [2+g] degree, [4+g] next node
+  uint64_t* mbar = reinterpret_cast<uint64_t*>(smem_raw + L::off_misc + 32);
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem_raw + L::off_misc + 48);
+
+  auto gsync = [&]() {  // constant barrier ids keep the per-block barrier count low
+    if constexpr (NG == 1) {
+      __syncthreads();
+    } else {
+      if (g == 0) named_sync(1, GT);
+      else named_sync(2, GT);
+    }
+  };
+  const int count = *a.count;
+  auto claim = [&]() -> int {  // next node of this group's share of the bucket list
+    const unsigned idx = atomicAdd(a.work, 1u);
+    return idx < unsigned(count) ? a.nodes[idx] : -1;
   };
 
-  const int count = *a.count;
-  const int nslices = int(a.row_bytes / kSlice);
+  if (warp == 0) tmem_alloc(tmem_slot, 128);
+  if (r == 0) mbar_init(mbar, 1);
+  if (t == 0) misc[4 + g] = claim();
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+  constexpr uint32_t idesc = umma_idesc_bf16(128, 128);
+  const int64_t elems = a.row_bytes / (DT == kU8 ? 1 : 4);  // padded dims per row
+  const int nslices = int((elems + 127) / 128);
   const float E_rel = rel_bound(a.d), E_abs = abs_bound(a.d);
+  const float eps_ip = 0.0078125f + 1.52587890625e-05f + float(a.d) * 2.384185791015625e-07f;
+  const float eps_n = float(a.d + 12) * 5.9604645e-08f;
+  const float err_abs = float(a.d) * 2.3509887e-38f;  // underflowed products, 2^-125 each
+  uint32_t phase = 0;
   long long done = 0;
+  bool dead = false;
 
   for (;;) {
     if (t == 0) {
-      unsigned idx = atomicAdd(a.work, 1u);
-      misc[0] = idx < unsigned(count) ? a.nodes[idx] : -1;
+      const int p = misc[4 + g];
+      int deg = p >= 0 ? int(a.row_ptr[p + 1] - a.row_ptr[p]) : 0;
+      if (deg > MAXM) {  // bucketing never sends such a node here; skip it, report it
+        raise_status(a.status, kDevBadDegree, p);
+        deg = 0;
+      }
+      misc[g] = p;
+      misc[2 + g] = deg;
     }
-    gsync();
-    const int p = misc[0];
-    if (p < 0) break;
-    const int64_t e0 = a.row_ptr[p];
-    const int m = int(a.row_ptr[p + 1] - e0);
-    if (m > MAXM) {  // bucketing never sends such a node here; refuse rather than overrun
-      if (t == 0) raise_status(a.status, kDevBadDegree, p);
-      gsync();
-      continue;
+    __syncthreads();
+    bool any = false;
+#pragma unroll
+    for (int q = 0; q < NG; ++q) any |= misc[q] >= 0;
+    if (!any || dead) break;  // both are the same for every thread of the CTA
+    const int p = misc[g];
+    const int m = misc[2 + g];
+    const int64_t e0 = p >= 0 ? a.row_ptr[p] : 0;
+    const bool live_row = t < m;
+    int32_t my_id = 0;
+    if (live_row) {
+      my_id = a.col[e0 + t];
+      ids[t] = my_id;
+      key64[t] = __longlong_as_double(0x7ff8000000000000ll);
     }
-    if (t < m) {
-      ids[t] = a.col[e0 + t];
-      key64[t] = __longlong_as_double(0x7ff8000000000000ll);  // not computed yet
-    }
-    gsync();
-
-    // ---- a2 gather + a3 keys + a5 Gram, one 128-byte slice of every row at a time
-    const int nr = (m + S - 1) / S;  // tile rows/cols that touch live candidates
-    AT acc[TPT][8][8];
-#pragma unroll
-    for (int q = 0; q < TPT; ++q)
-#pragma unroll
-      for (int r = 0; r < 8; ++r)
-#pragma unroll
-        for (int c = 0; c < 8; ++c) acc[q][r][c] = 0;
+    // ---- a2 gather, a3 pivot keys, norms, bf16 operand rows; a5 Gram on tcgen05
     AT kacc = 0, nacc = 0;
+    const uint8_t* xrow = a.X + int64_t(my_id) * a.row_bytes;
+    const uint8_t* prow = a.X + int64_t(p >= 0 ? p : 0) * a.row_bytes;
     for (int s = 0; s < nslices; ++s) {
-      for (int c = t; c < (m + 1) * 8; c += GT) {
-        const int r = c >> 3, part = c & 7;
-        const int64_t src = r == 0 ? int64_t(p) : int64_t(ids[r - 1]);
-        cp_async16(slice + r * kPitch + part * 16, a.X + src * a.row_bytes + s * kSlice + part * 16, 16);
-      }
-      cp_async_commit();
-      cp_async_wait<0>();
-      gsync();
-      if (t < m) {
-        const unsigned char* r0 = slice;
-        const unsigned char* r1 = slice + (t + 1) * kPitch;
-#pragma unroll
-        for (int part = 0; part < 8; ++part) {
-          const uint4 y = *reinterpret_cast<const uint4*>(r1 + part * 16);
-          kacc = Acc<DT>::step4(*reinterpret_cast<const uint4*>(r0 + part * 16), y, kacc);
-          if constexpr (DT == kU8) nacc = Acc<DT>::dot4(y, y, nacc);
-        }
-      }
-#pragma unroll
-      for (int q = 0; q < TPT; ++q) {
-        const int tile = t + q * GT;
-        const int ta = tile / S, tb = tile % S;
-        const unsigned char* rbase = slice + (1 + ta) * kPitch;
-        const unsigned char* cbase = slice + (1 + tb) * kPitch;
-#pragma unroll 2
-        for (int w = 0; w < kSlice / 8; ++w) {
-          uint2 rv[8], cv[8];
-#pragma unroll
-          for (int r = 0; r < 8; ++r)
-            if (r < nr) rv[r] = *reinterpret_cast<const uint2*>(rbase + r * S * kPitch + w * 8);
-#pragma unroll
-          for (int c = 0; c < 8; ++c)
-            if (c < nr) cv[c] = *reinterpret_cast<const uint2*>(cbase + c * S * kPitch + w * 8);
-#pragma unroll
-          for (int r = 0; r < 8; ++r)
-            if (r < nr)
-#pragma unroll
-              for (int c = 0; c < 8; ++c)
-                if (c < nr) acc[q][r][c] = Acc<DT>::gram(rv[r], cv[c], acc[q][r][c]);
-        }
-      }
-      gsync();  // the slice buffer is rewritten next
-    }
-    if (t < m) {
-      key[t] = kacc;
-      if constexpr (DT == kU8) norm[t] = nacc;
-    }
-    gsync();
-#pragma unroll
-    for (int q = 0; q < TPT; ++q) {
-      const int tile = t + q * GT;
-      const int ta = tile / S, tb = tile % S;
-#pragma unroll
-      for (int r = 0; r < 8; ++r)
+      const int64_t rem = elems - int64_t(s) * 128;
+      const int kd = int(rem < 128 ? rem : 128);  // a multiple of 16 here
+      if constexpr (DT == kU8) {
+        // all loads of the slice first, then the arithmetic
+        uint4 xs[8], ys[8];
 #pragma unroll
         for (int c = 0; c < 8; ++c) {
-          const int i = ta + r * S, j = tb + c * S;
-          if (r < nr && c < nr && i < m && j < m) {
-            if constexpr (DT == kU8) D[i * MAXM + j] = norm[i] + norm[j] - 2u * acc[q][r][c];  // exact
-            else D[i * MAXM + j] = acc[q][r][c];
+          xs[c] = make_uint4(0, 0, 0, 0);
+          ys[c] = make_uint4(0, 0, 0, 0);
+          if (live_row && c < kd / 16) {
+            xs[c] = __ldg(reinterpret_cast<const uint4*>(xrow + s * 128) + c);
+            ys[c] = __ldg(reinterpret_cast<const uint4*>(prow + s * 128) + c);
           }
         }
+#pragma unroll
+        for (int c = 0; c < 8; ++c) {
+          if (c >= kd / 16) break;
+          const uint4 x = xs[c];
+          kacc = Acc<kU8>::step4(x, ys[c], kacc);
+          nacc = Acc<kU8>::dot4(x, x, nacc);
+          const unsigned w4[4] = {x.x, x.y, x.z, x.w};
+          uint32_t o[8];
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            o[2 * q] = pack_bf16x2(float(w4[q] & 0xff), float((w4[q] >> 8) & 0xff));
+            o[2 * q + 1] = pack_bf16x2(float((w4[q] >> 16) & 0xff), float(w4[q] >> 24));
+          }
+          const int kc0 = 2 * c;
+          *reinterpret_cast<uint4*>(opnd + (kc0 * 16 + r / 8) * 128 + (r % 8) * 16) = make_uint4(o[0], o[1], o[2], o[3]);
+          *reinterpret_cast<uint4*>(opnd + ((kc0 + 1) * 16 + r / 8) * 128 + (r % 8) * 16) = make_uint4(o[4], o[5], o[6], o[7]);
+        }
+      } else {
+#pragma unroll 4
+        for (int c = 0; c < kd / 8; ++c) {
+          float xv[8];
+          if (live_row) {
+            const uint4* xs = reinterpret_cast<const uint4*>(xrow + int64_t(s) * 512) + 2 * c;
+            const uint4* ps = reinterpret_cast<const uint4*>(prow + int64_t(s) * 512) + 2 * c;
+            const uint4 x0 = __ldg(xs), x1 = __ldg(xs + 1), y0 = __ldg(ps), y1 = __ldg(ps + 1);
+            kacc = Acc<kF32>::step4(x0, y0, kacc);
+            kacc = Acc<kF32>::step4(x1, y1, kacc);
+            xv[0] = __uint_as_float(x0.x); xv[1] = __uint_as_float(x0.y);
+            xv[2] = __uint_as_float(x0.z); xv[3] = __uint_as_float(x0.w);
+            xv[4] = __uint_as_float(x1.x); xv[5] = __uint_as_float(x1.y);
+            xv[6] = __uint_as_float(x1.z); xv[7] = __uint_as_float(x1.w);
+#pragma unroll
+            for (int q = 0; q < 8; ++q) nacc = fmaf(xv[q], xv[q], nacc);
+          } else {
+#pragma unroll
+            for (int q = 0; q < 8; ++q) xv[q] = 0.f;
+          }
+          *reinterpret_cast<uint4*>(opnd + (c * 16 + r / 8) * 128 + (r % 8) * 16) =
+              make_uint4(pack_bf16x2(xv[0], xv[1]), pack_bf16x2(xv[2], xv[3]), pack_bf16x2(xv[4], xv[5]),
+                         pack_bf16x2(xv[6], xv[7]));
+        }
+      }
+      fence_async_smem();
+      tc_fence_before();
+      __syncthreads();
+      tc_fence_after();
+      if (r == 0) {
+#pragma unroll 1
+        for (int k = 0; k < kd / 16; ++k) {
+          const uint64_t dsc = umma_desc(smem_addr(opnd) + uint32_t(k) * 2u * 16u * 128u, 16u * 128u, 128u);
+          umma_bf16(tmem, dsc, dsc, idesc, s > 0 || k > 0);
+        }
+        umma_commit(mbar);
+      }
+      const bool ok = mbar_wait(mbar, phase, 1 << 24);
+      if (__syncthreads_or(!ok)) {  // the MMA never completed: report and stop (uniform)
+        if (r == 0) raise_status(a.status, kDevOverflow, -2);
+        dead = true;
+      }
+      phase ^= 1u;
+      tc_fence_after();
     }
+    if (live_row) {
+      key[t] = kacc;
+      norm[t] = nacc;
+      if constexpr (DT == kF32) sn[t] = sqrtf(nacc);
+    }
+    if (t == 0 && p >= 0) misc[4 + g] = claim();  // the next node, fetched while this one is scanned
+    __syncthreads();
+    // ---- Gram row of this thread's candidate -> d2 row (over the dead operand).
+    // tcgen05.ld is warp-collective: every lane issues it, live rows use it.
+    if (!dead) {
+      const AT nr_ = live_row ? norm[t] : AT(0);
+#pragma unroll 1
+      for (int c0 = 0; c0 < MAXM; c0 += 32) {
+        uint32_t v[32];
+        tmem_ld32(tmem + (uint32_t(32 * warp) << 16) + uint32_t(g * MAXM + c0), v);
+        tmem_ld_wait();
+        if (live_row) {
+#pragma unroll
+          for (int j = 0; j < 32; ++j) {
+            const int c = c0 + j;
+            if (c < m) {
+              const float G = __uint_as_float(v[j]);
+              if constexpr (DT == kU8) {
+                const unsigned d2 = nr_ + norm[c] - 2u * unsigned(G);
+                D[dix<MAXM>(t, c)] = __uint_as_float(d2);
+              } else {
+                D[dix<MAXM>(t, c)] = (nr_ + norm[c]) - 2.f * G;
+              }
+            }
+          }
+        }
+      }
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (p < 0 || dead) continue;
 
-    // ---- a4 processing order: warp 0 of the group sorts by (key, id)
+    // ---- a4 processing order: rank of every key among the m keys (warp 0 of the group)
     if (wg == 0) {
       if (a.variant == 0) {
-        unsigned long long sk[E];
-        int sp[E];
+        unsigned long long mk[E];
+        int rank[E];
 #pragma unroll
         for (int e = 0; e < E; ++e) {
           const int j = lane + 32 * e;
-          sk[e] = j < m ? (Acc<DT>::bits(key[j]) << 32) | unsigned(ids[j]) : ~0ull;
-          sp[e] = j;
+          mk[e] = j < m ? (Acc<DT>::bits(key[j]) << 32) | unsigned(ids[j]) : ~0ull;
+          rank[e] = 0;
         }
-        warp_bitonic<E>(sk, sp);
+#pragma unroll 4
+        for (int q = 0; q < m; ++q) {
+          const unsigned long long kq = (Acc<DT>::bits(key[q]) << 32) | unsigned(ids[q]);
 #pragma unroll
-        for (int e = 0; e < E; ++e) perm[lane + 32 * e] = sp[e];
+          for (int e = 0; e < E; ++e) rank[e] += kq < mk[e];
+        }
+#pragma unroll
+        for (int e = 0; e < E; ++e) {
+          const int j = lane + 32 * e;
+          if (j < m) perm[rank[e]] = j;
+        }
         if constexpr (DT == kF32) {
-          // near-ties of single-precision keys: order them by the binary64 keys
           __syncwarp();
           bool link = false;
 #pragma unroll
@@ -349,12 +464,12 @@ __global__ void __launch_bounds__(128, MAXM == 64 ? 4 : 2) prune_fast_kernel(Pru
               int end = i;
               while (end + 1 < m && !sure_less(key[perm[end]], key[perm[end + 1]], E_rel, E_abs)) ++end;
               if (end > i) {
-                for (int r = i; r <= end; ++r)
-                  key64[perm[r]] = canon_d2_f32(X + int64_t(p) * stride, X + int64_t(ids[perm[r]]) * stride, a.d);
+                for (int q = i; q <= end; ++q)
+                  key64[perm[q]] = canon_d2_f32(X + int64_t(p) * stride, X + int64_t(ids[perm[q]]) * stride, a.d);
                 atomicAdd(&a.status->fp64_sort_keys, static_cast<unsigned long long>(end - i + 1));
-                for (int r = i + 1; r <= end; ++r) {  // insertion sort of the run by (key64, id)
-                  const int v = perm[r];
-                  int z = r - 1;
+                for (int q = i + 1; q <= end; ++q) {
+                  const int v = perm[q];
+                  int z = q - 1;
                   while (z >= i && (key64[perm[z]] > key64[v] || (key64[perm[z]] == key64[v] && ids[perm[z]] > ids[v]))) {
                     perm[z + 1] = perm[z];
                     --z;
@@ -373,26 +488,26 @@ __global__ void __launch_bounds__(128, MAXM == 64 ? 4 : 2) prune_fast_kernel(Pru
     }
     gsync();
 
-    // ---- a6 domination bits + a7 greedy scan, fused and lazy: walk the
-    // processing order once; a row is evaluated only when it is kept by at
-    // least one of this warp's targets.  Lane l owns columns l + 32 e.
+    // ---- a6 + a7: fused lazy domination / greedy scan (warp wg takes targets wg, wg + NW, ...)
     {
       int pj[E];
       AT kj[E];
+      float nj[E], sj[E];
 #pragma unroll
       for (int e = 0; e < E; ++e) {
         const int j = lane + 32 * e;
         pj[e] = j < m ? perm[j] : 0;
         kj[e] = j < m ? key[pj[e]] : AT(0);
+        nj[e] = DT == kF32 && j < m ? float(norm[pj[e]]) : 0.f;
+        sj[e] = DT == kF32 && j < m ? sn[pj[e]] : 0.f;
       }
       unsigned long long al[TPW][MW];
       int kept[TPW];
       int Rt[TPW];
       float A2f[TPW];
       double A2d[TPW];
-      // uint8: u removes v  <=>  A^2 d2(u, v) <= 1e6 d2(p, v)  <=>  d2(u, v) <= floor(1e6 d2(p, v) / A^2)
       unsigned thr[TPW][E];
-      unsigned long long live[MW];  // rows still live for at least one of this warp's targets
+      unsigned long long live[MW];
 #pragma unroll
       for (int w = 0; w < MW; ++w) live[w] = 0;
 #pragma unroll
@@ -426,9 +541,11 @@ __global__ void __launch_bounds__(128, MAXM == 64 ? 4 : 2) prune_fast_kernel(Pru
         const int wi = i >> 6;
         const unsigned long long bit = 1ull << (i & 63);
         const int pi = perm[i];
-        AT dv[E];
+        float dv[E];
 #pragma unroll
-        for (int e = 0; e < E; ++e) dv[e] = D[pi * MAXM + pj[e]];
+        for (int e = 0; e < E; ++e) dv[e] = D[dix<MAXM>(pi, pj[e])];
+        const float ni = DT == kF32 ? float(norm[pi]) : 0.f;
+        const float si = DT == kF32 ? sn[pi] : 0.f;
 #pragma unroll
         for (int u = 0; u < TPW; ++u) {
           if (!(al[u][wi] & bit)) continue;
@@ -448,10 +565,26 @@ __global__ void __launch_bounds__(128, MAXM == 64 ? 4 : 2) prune_fast_kernel(Pru
             bool dom = false;
             if (j > i && j < m) {
               if constexpr (DT == kU8) {
-                dom = dv[e] <= thr[u][e];
+                dom = __float_as_uint(dv[e]) <= thr[u][e];
               } else {
-                const int r = sure_dominates(A2f[u], dv[e], kj[e], E_rel, E_abs);
-                dom = r >= 0 ? (r == 1) : tier3_dominates(a, ids[pi], ids[pj[e]], p, &key64[pj[e]], A2d[u]);
+                // Gram tier: d2~ with its error bound against the pivot key interval
+                const float err = 2.f * eps_ip * si * sj[e] * 1.0009765625f + eps_n * (ni + nj[e]) + err_abs;
+                const float lhs_hi = A2f[u] * (dv[e] + err) * 1.0000005f;
+                const float lhs_lo = A2f[u] * (dv[e] - err) * 0.9999995f;
+                const float rhs_lo = 1.0e6f * (kj[e] * (1.0f - E_rel) - E_abs) * 0.9999995f;
+                const float rhs_hi = 1.0e6f * (kj[e] * (1.0f + E_rel) + E_abs) * 1.0000005f;
+                if (lhs_hi < rhs_lo) {
+                  dom = true;
+                } else if (lhs_lo > rhs_hi) {
+                  dom = false;
+                } else {
+                  // difference-form single precision from the rows, then binary64
+                  const float d2a = row_d2<kF32>(a.X + int64_t(ids[pi]) * a.row_bytes,
+                                                 a.X + int64_t(ids[pj[e]]) * a.row_bytes, a.row_bytes);
+                  atomicAdd(&a.status->spare[2], 1ull);
+                  const int rr = sure_dominates(A2f[u], d2a, kj[e], E_rel, E_abs);
+                  dom = rr >= 0 ? (rr == 1) : tier3_dominates(a, ids[pi], ids[pj[e]], p, &key64[pj[e]], A2d[u]);
+                }
               }
             }
             bal[e] = __ballot_sync(0xffffffffu, dom);
@@ -477,8 +610,11 @@ __global__ void __launch_bounds__(128, MAXM == 64 ? 4 : 2) prune_fast_kernel(Pru
       }
     }
     ++done;
-    gsync();
   }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  if (warp == 0) tmem_dealloc(tmem, 128);
   if (t == 0 && done) atomicAdd(&a.status->nodes_pruned, static_cast<unsigned long long>(done) * T);
 }
 
@@ -493,7 +629,7 @@ struct GenericLayout {
 template <int DT>
 __global__ void __launch_bounds__(256) prune_generic_kernel(PruneArgs a, int M2) {
   using AT = typename Acc<DT>::T;
-  extern __shared__ __align__(128) unsigned char smem_raw[];
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned long long* skey = reinterpret_cast<unsigned long long*>(smem_raw);
   double* key64 = reinterpret_cast<double*>(smem_raw);  // valid after the sort
   int32_t* ids = reinterpret_cast<int32_t*>(smem_raw + size_t(M2) * 8);
@@ -825,17 +961,41 @@ cudaError_t launch_bucket_nodes(const int64_t* row_ptr, int64_t n, int32_t* list
   return cudaGetLastError();
 }
 
+// CTAs of `kern` that fit on one SM, from its registers and dynamic shared
+// memory (computed directly: the occupancy query under-reports it for these
+// kernels when called while a stream is being captured).
+template <typename K>
+static cudaError_t resident_ctas(K kern, int threads, size_t dyn_smem, int cap, int* out) {
+  cudaFuncAttributes fa;
+  cudaError_t err = cudaFuncGetAttributes(&fa, kern);
+  if (err != cudaSuccess) return err;
+  int dev = 0, smem_sm = 0, regs_sm = 0;
+  if ((err = cudaGetDevice(&dev)) != cudaSuccess) return err;
+  if ((err = cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev)) != cudaSuccess)
+    return err;
+  if ((err = cudaDeviceGetAttribute(&regs_sm, cudaDevAttrMaxRegistersPerMultiprocessor, dev)) != cudaSuccess)
+    return err;
+  const size_t per_cta_smem = dyn_smem + fa.sharedSizeBytes + 1024;  // 1 KB reserved per CTA
+  const int regs_per_warp = ((std::max(fa.numRegs, 1) * 32 + 255) / 256) * 256;
+  const int by_smem = int(size_t(smem_sm) / per_cta_smem);
+  const int by_regs = regs_sm / (regs_per_warp * ((threads + 31) / 32));
+  *out = std::max(1, std::min({cap, by_smem, by_regs}));
+  return cudaSuccess;
+}
+
 template <int DT, int MAXM, int TPW>
 static cudaError_t run_fast_t(const PruneArgs& args, int num_sms, int64_t host_count, cudaStream_t s) {
-  const size_t per_group = FastLayout<MAXM>::bytes();
-  const size_t bytes = per_group * (128 / MAXM);
-  auto kern = prune_fast_kernel<DT, MAXM, TPW>;
+  const size_t bytes = TcLayout<MAXM>::bytes;
+  auto kern = prune_tc_kernel<DT, MAXM, TPW>;
   cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(bytes));
   if (err != cudaSuccess) return err;
-  int per_sm = 0;
-  err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 128, bytes);
+  // ask for the largest shared-memory carveout so the occupancy query (and the
+  // launch) see the whole 228 KB per SM
+  err = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
   if (err != cudaSuccess) return err;
-  if (per_sm < 1) per_sm = 1;
+  int per_sm = 0;
+  err = resident_ctas(kern, 128, bytes, 4 /* 128 of the 512 TMEM columns per CTA */, &per_sm);
+  if (err != cudaSuccess) return err;
   const int64_t groups_needed = (host_count + (128 / MAXM) - 1) / (128 / MAXM);
   const int64_t grid = std::min<int64_t>(int64_t(num_sms) * per_sm, groups_needed);
   kern<<<unsigned(grid), 128, bytes, s>>>(args);
@@ -865,10 +1025,11 @@ static cudaError_t run_generic(const PruneArgs& args, int num_sms, int64_t host_
   auto kern = prune_generic_kernel<DT>;
   cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(bytes));
   if (err != cudaSuccess) return err;
-  int per_sm = 0;
-  err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 256, bytes);
+  err = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
   if (err != cudaSuccess) return err;
-  if (per_sm < 1) return cudaErrorInvalidConfiguration;
+  int per_sm = 0;
+  err = resident_ctas(kern, 256, bytes, 8, &per_sm);
+  if (err != cudaSuccess) return err;
   const int64_t grid = std::min<int64_t>(int64_t(num_sms) * per_sm, host_count);
   kern<<<unsigned(grid), 256, bytes, s>>>(args, M2);
   return cudaGetLastError();
