@@ -183,6 +183,44 @@ rp_status rp_search(rp_ctx *ctx, rp_graph g, const void *queries, int64_t nq, in
                     int32_t k, int32_t *ids, float *dists, int32_t mem_flags);
 
 /*
+ * rp_search_noalloc: the GreedySearch of rp_search for callers that cannot
+ * allocate device memory.  The paper has no counterpart: this entry point
+ * exists for processes that reserve all device memory up front (an inference
+ * engine's pool, an arena shared with other models) and for callers that must
+ * not have allocations appear while they capture a stream.  It takes no
+ * context, allocates nothing (no cudaMalloc, cudaMallocAsync or cudaFree, no
+ * allocating library routine) and uses instead a fixed scratch array of
+ * RP_NOALLOC_SCRATCH_BYTES that every GPU loading this library holds until
+ * the process exits.
+ *   vectors: n x d elements of dtype, device memory, rows packed (stride
+ *     d * element size, which must be a multiple of 16 bytes; pointer
+ *     16-byte aligned).
+ *   row_ptr, col: the graph in CSR on the device; ids must lie in [0, n) and
+ *     rows must hold no repeated id (graphs from rp_graph_export qualify).
+ *   start: the start vertex in [0, n).
+ *   queries: nq x d elements of dtype, device memory, same stride rule.
+ *   ids: int32[nq * k], dists: float[nq * k] or NULL, device memory; same
+ *     contents as rp_search's outputs.
+ *   cuda_stream: the stream to run on (NULL: the legacy default stream).
+ * The call is asynchronous on cuda_stream and runs on the current device.
+ * The first call on a device looks up the scratch array's device address
+ * (cudaGetSymbolAddress); make that first call outside any stream capture.
+ * All calls share the one array and each clears what it needs at its start,
+ * so calls whose work overlaps on the GPU (other streams, other threads) race
+ * and must be serialised by the caller.
+ * Limit: the per-query membership bitmaps need n/8 bytes each; with at least
+ * 4 queries in flight, n may be at most about 134 million.
+ * Errors (checked on the host, before any work is enqueued): RP_EINVAL for a
+ * bad argument, a stride or pointer alignment off 16 bytes, or an n beyond
+ * the scratch limit; RP_ECUDA if the symbol lookup or a launch fails.
+ */
+#define RP_NOALLOC_SCRATCH_BYTES (64u << 20)
+rp_status rp_search_noalloc(const void *vectors, int32_t dtype, int64_t n, int32_t d,
+                            const int64_t *row_ptr, const int32_t *col, int64_t start,
+                            const void *queries, int64_t nq, int32_t L, int32_t k, int32_t *ids,
+                            float *dists, void *cuda_stream);
+
+/*
  * rp_knn: exact k nearest neighbours by brute force over the vectors of
  * graph g, ordered by (distance, id) -- the ground truth of k-recall@k (§4).
  *   queries: nq x d rows of g's dtype, or NULL to use the base points

@@ -71,6 +71,7 @@ def load_library(path: str = LIB_PATH):
         "rp_build_knn_base": [P, i64, i32, dbl, i32, ctypes.POINTER(i64)],
         "rp_graph_free": [P, i64],
         "rp_stats": [P, ctypes.POINTER(rp_stats_t), i32],
+        "rp_search_noalloc": [P, i32, i64, i32, P, P, i64, P, i64, i32, i32, P, P, P],
     }
     for name, args in sig.items():
         fn = getattr(lib, name)
@@ -243,3 +244,29 @@ def rp_stats(ctx, reset: bool = False) -> dict:
     s = rp_stats_t()
     _check(ctx, load_library().rp_stats(ctx, ctypes.byref(s), int(bool(reset))))
     return {name: getattr(s, name) for name, _ in rp_stats_t._fields_}
+
+
+def rp_search_noalloc(vectors, row_ptr, col, start: int, queries, L: int, k: int, ids=None, dists=None,
+                      stream=None):
+    """GreedySearch with caller-owned CUDA tensors and no device allocation by the library.
+
+    ``vectors``/``queries`` are CUDA tensors of uint8 or float32 rows; ``row_ptr``/``col`` the
+    graph on the device.  Runs on ``stream`` (a torch.cuda.Stream or raw handle; default: the
+    current torch stream).  Returns (ids, dists) tensors.
+    """
+    import torch
+    nq = int(queries.shape[0])
+    if ids is None:
+        ids = torch.empty((nq, k), dtype=torch.int32, device=queries.device)
+    if dists is None:
+        dists = torch.empty((nq, k), dtype=torch.float32, device=queries.device)
+    if stream is None:
+        stream = torch.cuda.current_stream(queries.device)
+    h = stream.cuda_stream if hasattr(stream, "cuda_stream") else stream
+    rc = load_library().rp_search_noalloc(_ptr(vectors), _dtype_code(vectors), int(vectors.shape[0]),
+                                          int(vectors.shape[1]), _ptr(row_ptr), _ptr(col), int(start),
+                                          _ptr(queries), nq, int(L), int(k), _ptr(ids), _ptr(dists),
+                                          ctypes.c_void_p(h) if h else None)
+    if rc != RP_OK:
+        raise RPError(rc, "rp_search_noalloc rejected its arguments or failed to launch")
+    return ids, dists

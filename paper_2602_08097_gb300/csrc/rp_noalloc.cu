@@ -1,0 +1,109 @@
+// rp_search_noalloc: GreedySearch for callers that must not allocate device
+// memory.  Everything the kernel needs beyond the caller's inputs and outputs
+// lives in one fixed array of this file, so the call makes no cudaMalloc,
+// cudaMallocAsync or cudaFree and creates no context object.
+//
+// Who needs this: a serving process that reserves all of its device memory
+// up front (an inference engine's memory pool, or an arena shared with other
+// models) has nothing left for a library to allocate, and a caller that
+// brackets its work in stream capture must not see allocations appear in its
+// graph.  Both still own the vectors, the graph and the result buffers; they
+// only cannot hand the library new memory per call.
+#include <mutex>
+
+#include "internal.h"
+#include "rp.h"
+
+namespace {
+
+// The whole scratch: a small header (status word and work counter), then one
+// membership bitmap and one list of set ids per in-flight query slot.  Every
+// GPU that loads this library holds these RP_NOALLOC_SCRATCH_BYTES until exit.
+constexpr size_t kHeader = 256;
+constexpr int64_t kListCap = 4096;
+static __device__ __align__(256) unsigned char g_noalloc_scratch[RP_NOALLOC_SCRATCH_BYTES];
+
+// Device addresses of the array, resolved once per device (in host code the
+// symbol is only a host-side stand-in and must not be passed to a kernel).
+constexpr int kMaxDevices = 64;
+std::mutex g_mu;
+void* g_scratch_addr[kMaxDevices] = {};
+
+size_t elem_size(int dtype) { return dtype == RP_U8 ? 1 : 4; }
+
+}  // namespace
+
+extern "C" rp_status rp_search_noalloc(const void* vectors, int32_t dtype, int64_t n, int32_t d,
+                                       const int64_t* row_ptr, const int32_t* col, int64_t start,
+                                       const void* queries, int64_t nq, int32_t L, int32_t k, int32_t* ids,
+                                       float* dists, void* cuda_stream) {
+  if (dtype != RP_U8 && dtype != RP_F32) return RP_EINVAL;
+  if (!vectors || !row_ptr || !col || !ids || (nq > 0 && !queries)) return RP_EINVAL;
+  if (n < 1 || n > INT32_MAX || d < 1 || nq < 0 || k < 1 || L < k || L > RP_MAX_L) return RP_EINVAL;
+  if (start < 0 || start >= n) return RP_EINVAL;
+  const int64_t row_bytes = int64_t(d) * int64_t(elem_size(dtype));
+  // the kernel reads rows with 16-byte loads
+  if (row_bytes % 16 != 0 || reinterpret_cast<uintptr_t>(vectors) % 16 != 0 ||
+      reinterpret_cast<uintptr_t>(queries) % 16 != 0)
+    return RP_EINVAL;
+  if (nq == 0) return RP_OK;
+
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return RP_ECUDA;
+  void* base = nullptr;
+  {
+    std::lock_guard<std::mutex> lk(g_mu);
+    if (!g_scratch_addr[dev]) {
+      void* p = nullptr;
+      if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) return RP_ECUDA;
+      g_scratch_addr[dev] = p;
+    }
+    base = g_scratch_addr[dev];
+  }
+  int num_sms = 0;
+  if (cudaDeviceGetAttribute(&num_sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return RP_ECUDA;
+
+  // As many query slots as fit (at most 32 warps per SM, a multiple of 4);
+  // a graph too large for even 4 slots is refused.
+  const int64_t words = (n + 31) / 32;
+  const int64_t per_slot = words * 4 + kListCap * 4;
+  int64_t slots = (int64_t(RP_NOALLOC_SCRATCH_BYTES) - int64_t(kHeader)) / per_slot;
+  slots = std::min<int64_t>(slots, int64_t(num_sms) * 32);
+  slots = slots / 4 * 4;
+  if (slots < 4) return RP_EINVAL;
+
+  unsigned char* s = static_cast<unsigned char*>(base);
+  rpk::DevStatus* status = reinterpret_cast<rpk::DevStatus*>(s);
+  unsigned int* work = reinterpret_cast<unsigned int*>(s + 128);
+  uint32_t* bits = reinterpret_cast<uint32_t*>(s + kHeader);
+  int32_t* lists = reinterpret_cast<int32_t*>(s + kHeader + slots * words * 4);
+  cudaStream_t stream = static_cast<cudaStream_t>(cuda_stream);
+
+  // The array keeps the last call's contents: the header and the bitmaps
+  // must start at zero.
+  if (cudaMemsetAsync(s, 0, size_t(kHeader + slots * words * 4), stream) != cudaSuccess) return RP_ECUDA;
+
+  rpk::SearchLaunch S;
+  S.data.X = static_cast<const uint8_t*>(vectors);
+  S.data.row_bytes = row_bytes;
+  S.data.n = n;
+  S.data.d = d;
+  S.data.dtype = dtype;
+  S.row_ptr = row_ptr;
+  S.col = col;
+  S.start = start;
+  S.Q = static_cast<const uint8_t*>(queries);
+  S.nq = nq;
+  S.L = L;
+  S.k = k;
+  S.out_ids = ids;
+  S.out_dists = dists;
+  S.seen_bits = bits;
+  S.seen_words = words;
+  S.seen_list = lists;
+  S.seen_list_cap = kListCap;
+  S.slots = int(slots);
+  S.work = work;
+  S.status = status;
+  return rpk::launch_search(S, stream) == cudaSuccess ? RP_OK : RP_ECUDA;
+}

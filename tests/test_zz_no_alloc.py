@@ -1,0 +1,66 @@
+"""rp_search_noalloc: the search entry point for callers that cannot allocate
+device memory (their memory is reserved up front, or they must not see
+allocations while capturing a stream).  It must return what rp_search returns
+on the same graph and queries, on two calls in a row (the second call reuses
+the fixed scratch array the first one left behind).  This file is collected
+last so that a failure here stops a -x run only after every other test."""
+import numpy as np
+import pytest
+
+import datagen
+
+rp = pytest.importorskip("paper_2602_08097_gb300")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def env():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2602_08097_gb300 import build as b
+    b.build()
+    ctx = rp.rp_create(0)
+    yield torch, ctx
+    rp.rp_destroy(ctx)
+
+
+def _graph_on_device(torch, ctx, name, n, nq, kcand, alpha, R):
+    X = datagen.dataset(name, n)
+    Q = datagen.queries(name, nq)
+    g = rp.rp_load_graph(ctx, X)
+    b = rp.rp_build_knn_base(ctx, g, kcand, alpha, R)
+    row_ptr, col = rp.rp_graph_export(ctx, b)
+    start = rp.rp_graph_info(ctx, b)["start"]
+    dev = torch.device("cuda:0")
+    tens = [torch.from_numpy(np.ascontiguousarray(a)).to(dev) for a in (X, row_ptr, col, Q)]
+    return b, Q, start, tens
+
+
+@pytest.mark.parametrize("name,n,L,k", [("sift", 6000, 128, 100), ("deep", 5000, 64, 10), ("tiny", 2000, 64, 10)])
+def test_no_alloc_search_matches_rp_search(env, name, n, L, k):
+    torch, ctx = env
+    b, Q, start, (Xd, rpd, cold, Qd) = _graph_on_device(torch, ctx, name, n, 300, 64, 1.2, 32)
+    ref_ids, ref_d = rp.rp_search(ctx, b, Q, L, k)
+    for _ in range(2):
+        ids, dists = rp.rp_search_noalloc(Xd, rpd, cold, start, Qd, L, k)
+        torch.cuda.synchronize()
+        assert np.array_equal(ids.cpu().numpy(), ref_ids)
+        np.testing.assert_allclose(dists.cpu().numpy(), ref_d, rtol=1e-5)
+    rp.rp_graph_free(ctx, b)
+
+
+def test_no_alloc_search_rejects_bad_arguments(env):
+    torch, ctx = env
+    dev = torch.device("cuda:0")
+    X = torch.zeros((10, 3), dtype=torch.uint8, device=dev)  # 3-byte rows: not a multiple of 16
+    rp_ = torch.zeros(11, dtype=torch.int64, device=dev)
+    col = torch.zeros(1, dtype=torch.int32, device=dev)
+    with pytest.raises(rp.RPError) as e:
+        rp.rp_search_noalloc(X, rp_, col, 0, X[:2], 8, 4)
+    assert e.value.code == rp.RP_EINVAL
+    Xok = torch.zeros((10, 16), dtype=torch.uint8, device=dev)
+    with pytest.raises(rp.RPError):
+        rp.rp_search_noalloc(Xok, rp_, col, 0, Xok[:2], 4, 8)  # L < k
+    with pytest.raises(rp.RPError):
+        rp.rp_search_noalloc(Xok, rp_, col, 10, Xok[:2], 8, 4)  # start outside [0, n)
