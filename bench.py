@@ -295,13 +295,17 @@ def run_ours(args):
     alg_bytes = float(((deg + 1) * 128 + 4 * deg + 8).sum() + 4 * sum(nnz))
     hbm_peak, peak_kind = load_peaks()
     achieved = alg_bytes / (prune_ms / 1000.0) / 1e9
-    traffic = None
-    prof = os.path.join(ROOT, "profiles", "prune_fast_u8_sift1m_traffic.json")
-    if os.path.exists(prof):
+    traffic = None  # DRAM bytes per launch from the committed ncu summary, if it is of this kernel source
+    prof = os.path.join(ROOT, "profiles", "prune_tc_u8_sift1m.md")
+    if os.path.exists(prof) and n == 1_000_000:
+        fields = {}
         with open(prof) as f:
-            pj = json.load(f)
-        if pj.get("kernel_source_hash") == kernel_hash():
-            traffic = pj.get("traffic_bytes_per_launch")
+            for ln in f:
+                if ":" in ln and not ln.startswith(("#", "-", " ", "|")):
+                    k_, v_ = ln.split(":", 1)
+                    fields[k_.strip()] = v_.strip()
+        if fields.get("kernel_source_hash") == kernel_hash():
+            traffic = float(fields["traffic_bytes_per_launch"])
 
     # ---- plain vs batched tuning alone
     def time_tune(batched, reps):
