@@ -233,14 +233,27 @@ __global__ void __launch_bounds__(kWarps * 32) search_kernel(SearchArgs a) {
           const unsigned old = atomicOr(&bits[v >> 5], bit);
           fresh = !(old & bit);
         }
-        const unsigned fm = __ballot_sync(0xffffffffu, fresh);
-        const int nf = __popc(fm);
-        if (nf == 0) continue;
-        const int rank = __popc(fm & ((1u << lane) - 1));
+        const unsigned seen_m = __ballot_sync(0xffffffffu, fresh);
+        const int nseen_b = __popc(seen_m);
+        if (nseen_b == 0) continue;
+        const int rank = __popc(seen_m & ((1u << lane) - 1));
         if (fresh && nseen + rank < a.seen_list_cap) list[nseen + rank] = int32_t(v);
-        nseen += nf;
+        nseen += nseen_b;
         unsigned kv = 0xffffffffu;
         if (fresh) kv = dist_bits<DT>(S.q, a.X + int64_t(v) * a.row_bytes, a.row_bytes);
+        // A full list keeps only entries before its L-th: a new point behind it
+        // would be cut right after the merge, so it skips the merge (it stays
+        // marked as seen, which is all Algorithm 2 retains of it).
+        bool enters = fresh;
+        if (enters && size == a.L) {
+          double cand_d64 = qnan;
+          enters = entry_less<DT>(kv, v, f32 ? &cand_d64 : nullptr, S.key[cur][a.L - 1],
+                                  S.idv[cur][a.L - 1] & kIdMask, f32 ? &S.d64[cur][a.L - 1] : nullptr, a, S.q,
+                                  E, Eabs);
+        }
+        const unsigned fm = __ballot_sync(0xffffffffu, enters);
+        const int nf = __popc(fm);
+        if (nf == 0) continue;
         // compact the fresh ones into lanes 0..nf-1
         unsigned myk = 0xffffffffu, myid = 0xffffffffu;
         {
