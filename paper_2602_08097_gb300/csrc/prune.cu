@@ -190,44 +190,45 @@ __device__ __forceinline__ void warp_bitonic(unsigned long long (&key)[E], int (
 //          margin is inside that bound is redone in single-precision
 //          difference form from the rows (rigorous relative bound), and if
 //          still inside, in binary64.
-template <int MAXM>
+template <int MAXM, int TB>
 struct TcLayout {
   static constexpr int NG = 128 / MAXM;
-  // The MMA operand (128 rows x 128 dims bf16, 32 KB) is dead once the MMA has
-  // completed, so the d2 matrices of the node groups reuse its space.
-  static constexpr size_t opnd_bytes = 128 * 128 * 2;
-  static constexpr size_t g_D = size_t(MAXM) * MAXM * 4;
-  static constexpr size_t big = opnd_bytes > NG * g_D ? opnd_bytes : NG * g_D;
-  static constexpr size_t off_opnd = 0;
-  static constexpr size_t off_D = 0;
-  static constexpr size_t off_grp = big;
+  static constexpr int MW = MAXM / 64;
+  static constexpr size_t off_opnd = 0;  // 128 rows x 128 dims bf16 = 32 KB
+  static constexpr size_t off_grp = 128 * 128 * 2;
   static constexpr size_t g_key64 = 0;
-  static constexpr size_t g_ids = g_key64 + size_t(MAXM) * 8;
+  static constexpr size_t g_masks = g_key64 + size_t(MAXM) * 8;          // [TB][MAXM][MW] u64
+  static constexpr size_t g_ids = g_masks + size_t(TB) * MAXM * MW * 8;
   static constexpr size_t g_perm = g_ids + size_t(MAXM) * 4;
   static constexpr size_t g_key = g_perm + size_t(MAXM) * 4;
   static constexpr size_t g_norm = g_key + size_t(MAXM) * 4;
   static constexpr size_t g_sn = g_norm + size_t(MAXM) * 4;
-  static constexpr size_t g_bytes = g_sn + size_t(MAXM) * 4;
-  static constexpr size_t off_misc = off_grp + NG * g_bytes;  // node / degree (current, next), mbar, tmem
-  static constexpr size_t bytes = (off_misc + 64 + 127) & ~size_t(127);
+  static constexpr size_t g_qlo = g_sn + size_t(MAXM) * 4;                 // [TB][MAXM] thresholds
+  static constexpr size_t g_qhi = g_qlo + size_t(TB) * MAXM * 4;
+  static constexpr size_t g_bytes = g_qhi + size_t(TB) * MAXM * 4;
+  static constexpr size_t off_misc = off_grp + NG * g_bytes;  // nodes, degrees, row starts, mbar, tmem
+  static constexpr size_t bytes = (off_misc + 128 + 127) & ~size_t(127);
 };
 
-// d2 matrix element (row, col) of one node group, columns XOR-swizzled by the
-// row so that row writes and row reads are both free of bank conflicts.
-template <int MAXM>
-__device__ __forceinline__ int dix(int row, int col) {
-  return row * MAXM + (col ^ (row & 31));
+// floor(1e6 k / A2) for integers, exactly: a single-precision estimate
+// corrected with 64-bit products.
+__device__ __forceinline__ unsigned exact_threshold(unsigned k, unsigned long long A2) {
+  const unsigned long long num = 1000000ull * k;
+  long long q = static_cast<long long>(floorf(__fdiv_rn(1.0e6f * float(k), float(A2))));
+  if (q < 0) q = 0;
+  while (static_cast<unsigned long long>(q) * A2 > num) --q;
+  while (static_cast<unsigned long long>(q + 1) * A2 <= num) ++q;
+  return static_cast<unsigned>(q);
 }
 
-template <int DT, int MAXM, int TPW>
+template <int DT, int MAXM, int TB>
 __global__ void __launch_bounds__(128) prune_tc_kernel(PruneArgs a) {
-  using L = TcLayout<MAXM>;
+  using L = TcLayout<MAXM, TB>;
   using AT = typename Acc<DT>::T;
   constexpr int NG = L::NG;
-  constexpr int GT = MAXM;       // threads per node group
-  constexpr int NW = MAXM / 32;  // warps per group
-  constexpr int E = MAXM / 32;   // columns per lane in the scan
-  constexpr int MW = MAXM / 64;
+  constexpr int GT = MAXM;      // threads per node group
+  constexpr int E = MAXM / 32;  // sort elements per lane
+  constexpr int MW = L::MW;
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   const int T = a.T;
   const int r = threadIdx.x;  // CTA row = TMEM lane
@@ -237,17 +238,21 @@ __global__ void __launch_bounds__(128) prune_tc_kernel(PruneArgs a) {
   const int lane = r & 31;
   const int warp = r >> 5;
   unsigned char* opnd = smem_raw + L::off_opnd;
-  float* D = reinterpret_cast<float*>(smem_raw + L::off_D + g * L::g_D);
   unsigned char* gb = smem_raw + L::off_grp + g * L::g_bytes;
   double* key64 = reinterpret_cast<double*>(gb + L::g_key64);
+  unsigned long long* masks = reinterpret_cast<unsigned long long*>(gb + L::g_masks);
   int32_t* ids = reinterpret_cast<int32_t*>(gb + L::g_ids);
   int32_t* perm = reinterpret_cast<int32_t*>(gb + L::g_perm);
   AT* key = reinterpret_cast<AT*>(gb + L::g_key);
   AT* norm = reinterpret_cast<AT*>(gb + L::g_norm);
   float* sn = reinterpret_cast<float*>(gb + L::g_sn);
-  int* misc = reinterpret_cast<int*>(smem_raw + L::off_misc);  // [g] node, [2+g] degree, [4+g] next node
+  float* qlo = reinterpret_cast<float*>(gb + L::g_qlo);
+  float* qhi = reinterpret_cast<float*>(gb + L::g_qhi);
+  // misc: [g] node, [2+g] degree, [4+g] next node, [6+g] next degree; row starts at +64
+  int* misc = reinterpret_cast<int*>(smem_raw + L::off_misc);
   uint64_t* mbar = reinterpret_cast<uint64_t*>(smem_raw + L::off_misc + 32);
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem_raw + L::off_misc + 48);
+  int64_t* rows = reinterpret_cast<int64_t*>(smem_raw + L::off_misc + 64);  // [g] row start, [2+g] next
 
   auto gsync = [&]() {  // constant barrier ids keep the per-block barrier count low
     if constexpr (NG == 1) {
@@ -258,14 +263,28 @@ __global__ void __launch_bounds__(128) prune_tc_kernel(PruneArgs a) {
     }
   };
   const int count = *a.count;
-  auto claim = [&]() -> int {  // next node of this group's share of the bucket list
+  // claim the next node of the bucket list for this group, with its row bounds
+  auto claim = [&]() {
     const unsigned idx = atomicAdd(a.work, 1u);
-    return idx < unsigned(count) ? a.nodes[idx] : -1;
+    const int p = idx < unsigned(count) ? a.nodes[idx] : -1;
+    int deg = 0;
+    int64_t e0 = 0;
+    if (p >= 0) {
+      e0 = a.row_ptr[p];
+      deg = int(a.row_ptr[p + 1] - e0);
+    }
+    if (deg > MAXM) {  // bucketing never sends such a node here; skip it, report it
+      raise_status(a.status, kDevBadDegree, p);
+      deg = 0;
+    }
+    misc[4 + g] = p;
+    misc[6 + g] = deg;
+    rows[2 + g] = e0;
   };
 
-  if (warp == 0) tmem_alloc(tmem_slot, 128);
+  if (warp == 0) tmem_alloc(tmem_slot, 128);  // 128 of the SM's 512 TMEM columns, for the kernel's life
   if (r == 0) mbar_init(mbar, 1);
-  if (t == 0) misc[4 + g] = claim();
+  if (t == 0) claim();
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
@@ -283,14 +302,9 @@ __global__ void __launch_bounds__(128) prune_tc_kernel(PruneArgs a) {
 
   for (;;) {
     if (t == 0) {
-      const int p = misc[4 + g];
-      int deg = p >= 0 ? int(a.row_ptr[p + 1] - a.row_ptr[p]) : 0;
-      if (deg > MAXM) {  // bucketing never sends such a node here; skip it, report it
-        raise_status(a.status, kDevBadDegree, p);
-        deg = 0;
-      }
-      misc[g] = p;
-      misc[2 + g] = deg;
+      misc[g] = misc[4 + g];
+      misc[2 + g] = misc[6 + g];
+      rows[g] = rows[2 + g];
     }
     __syncthreads();
     bool any = false;
@@ -299,7 +313,7 @@ __global__ void __launch_bounds__(128) prune_tc_kernel(PruneArgs a) {
     if (!any || dead) break;  // both are the same for every thread of the CTA
     const int p = misc[g];
     const int m = misc[2 + g];
-    const int64_t e0 = p >= 0 ? a.row_ptr[p] : 0;
+    const int64_t e0 = rows[g];
     const bool live_row = t < m;
     int32_t my_id = 0;
     if (live_row) {
@@ -315,7 +329,6 @@ __global__ void __launch_bounds__(128) prune_tc_kernel(PruneArgs a) {
       const int64_t rem = elems - int64_t(s) * 128;
       const int kd = int(rem < 128 ? rem : 128);  // a multiple of 16 here
       if constexpr (DT == kU8) {
-        // all loads of the slice first, then the arithmetic
         uint4 xs[8], ys[8];
 #pragma unroll
         for (int c = 0; c < 8; ++c) {
@@ -368,6 +381,12 @@ __global__ void __launch_bounds__(128) prune_tc_kernel(PruneArgs a) {
                          pack_bf16x2(xv[6], xv[7]));
         }
       }
+      const bool last = s == nslices - 1;
+      if (last && live_row) {
+        key[t] = kacc;
+        norm[t] = nacc;
+        if constexpr (DT == kF32) sn[t] = sqrtf(nacc);
+      }
       fence_async_smem();
       tc_fence_before();
       __syncthreads();
@@ -380,6 +399,89 @@ __global__ void __launch_bounds__(128) prune_tc_kernel(PruneArgs a) {
         }
         umma_commit(mbar);
       }
+      if (last && p >= 0) {
+        // While the MMA runs: per-column domination thresholds of every target
+        // (a6), the processing order (a4), the next node.
+        if (live_row) {
+#pragma unroll
+          for (int u = 0; u < TB; ++u) {
+            if (u >= T) break;
+            const unsigned long long A2 = static_cast<unsigned long long>(a.A[u]) * a.A[u];
+            if constexpr (DT == kU8) {
+              // v is removed by row u'  <=>  A2 d2(u', v) <= 1e6 d2(p, v)
+              //                         <=>  2 G(u', v) - |u'|^2 >= |v|^2 - floor(1e6 d2(p, v) / A2)
+              // (every quantity an integer below 2^24, exact in f32)
+              const unsigned thr = exact_threshold(kacc, A2);
+              qlo[u * MAXM + t] = float(int(nacc) - int(thr));
+            } else {
+              const float A2f = float(A2);
+              qlo[u * MAXM + t] = 1.0e6f * (kacc * (1.0f - E_rel) - E_abs) * 0.9999995f / A2f * 0.9999995f;
+              qhi[u * MAXM + t] = 1.0e6f * (kacc * (1.0f + E_rel) + E_abs) * 1.0000005f / A2f * 1.0000005f;
+            }
+          }
+        }
+        if (wg == 0) {
+          if (a.variant == 0) {
+            unsigned long long mk[E];
+            int rank[E];
+#pragma unroll
+            for (int e = 0; e < E; ++e) {
+              const int j = lane + 32 * e;
+              mk[e] = j < m ? (Acc<DT>::bits(key[j]) << 32) | unsigned(ids[j]) : ~0ull;
+              rank[e] = 0;
+            }
+#pragma unroll 4
+            for (int q = 0; q < m; ++q) {
+              const unsigned long long kq = (Acc<DT>::bits(key[q]) << 32) | unsigned(ids[q]);
+#pragma unroll
+              for (int e = 0; e < E; ++e) rank[e] += kq < mk[e];
+            }
+#pragma unroll
+            for (int e = 0; e < E; ++e) {
+              const int j = lane + 32 * e;
+              if (j < m) perm[rank[e]] = j;
+            }
+            if constexpr (DT == kF32) {
+              // near-ties of single-precision keys: order them by the binary64 keys
+              __syncwarp();
+              bool link = false;
+#pragma unroll
+              for (int e = 0; e < E; ++e) {
+                const int i = lane + 32 * e;
+                if (i + 1 < m && !sure_less(key[perm[i]], key[perm[i + 1]], E_rel, E_abs)) link = true;
+              }
+              if (__any_sync(0xffffffffu, link) && lane == 0) {
+                const float* X = reinterpret_cast<const float*>(a.X);
+                const int64_t stride = a.row_bytes / 4;
+                int i = 0;
+                while (i < m) {
+                  int end = i;
+                  while (end + 1 < m && !sure_less(key[perm[end]], key[perm[end + 1]], E_rel, E_abs)) ++end;
+                  if (end > i) {
+                    for (int q = i; q <= end; ++q)
+                      key64[perm[q]] = canon_d2_f32(X + int64_t(p) * stride, X + int64_t(ids[perm[q]]) * stride, a.d);
+                    atomicAdd(&a.status->fp64_sort_keys, static_cast<unsigned long long>(end - i + 1));
+                    for (int q = i + 1; q <= end; ++q) {
+                      const int v = perm[q];
+                      int z = q - 1;
+                      while (z >= i && (key64[perm[z]] > key64[v] || (key64[perm[z]] == key64[v] && ids[perm[z]] > ids[v]))) {
+                        perm[z + 1] = perm[z];
+                        --z;
+                      }
+                      perm[z + 1] = v;
+                    }
+                  }
+                  i = end + 1;
+                }
+              }
+            }
+          } else {
+#pragma unroll
+            for (int e = 0; e < E; ++e) perm[lane + 32 * e] = lane + 32 * e;
+          }
+        }
+        if (t == 0) claim();  // the next node, fetched while this one is finished
+      }
       const bool ok = mbar_wait(mbar, phase, 1 << 24);
       if (__syncthreads_or(!ok)) {  // the MMA never completed: report and stop (uniform)
         if (r == 0) raise_status(a.status, kDevOverflow, -2);
@@ -388,17 +490,18 @@ __global__ void __launch_bounds__(128) prune_tc_kernel(PruneArgs a) {
       phase ^= 1u;
       tc_fence_after();
     }
-    if (live_row) {
-      key[t] = kacc;
-      norm[t] = nacc;
-      if constexpr (DT == kF32) sn[t] = sqrtf(nacc);
-    }
-    if (t == 0 && p >= 0) misc[4 + g] = claim();  // the next node, fetched while this one is scanned
-    __syncthreads();
-    // ---- Gram row of this thread's candidate -> d2 row (over the dead operand).
+
+    // ---- a6: each thread reads its candidate's Gram row from TMEM and builds,
+    // per target, the mask of candidates (by stored position) it would remove.
     // tcgen05.ld is warp-collective: every lane issues it, live rows use it.
     if (!dead) {
-      const AT nr_ = live_row ? norm[t] : AT(0);
+      unsigned long long mk[TB][MW];
+#pragma unroll
+      for (int u = 0; u < TB; ++u)
+#pragma unroll
+        for (int w = 0; w < MW; ++w) mk[u][w] = 0;
+      const float nt = live_row ? float(norm[t]) : 0.f;
+      const float st = DT == kF32 && live_row ? sn[t] : 0.f;
 #pragma unroll 1
       for (int c0 = 0; c0 < MAXM; c0 += 32) {
         uint32_t v[32];
@@ -408,16 +511,51 @@ __global__ void __launch_bounds__(128) prune_tc_kernel(PruneArgs a) {
 #pragma unroll
           for (int j = 0; j < 32; ++j) {
             const int c = c0 + j;
-            if (c < m) {
-              const float G = __uint_as_float(v[j]);
-              if constexpr (DT == kU8) {
-                const unsigned d2 = nr_ + norm[c] - 2u * unsigned(G);
-                D[dix<MAXM>(t, c)] = __uint_as_float(d2);
-              } else {
-                D[dix<MAXM>(t, c)] = (nr_ + norm[c]) - 2.f * G;
+            if (c >= m) break;
+            const float G = __uint_as_float(v[j]);
+            const unsigned long long bit = 1ull << (c & 63);
+            const int w = c >> 6;
+            if constexpr (DT == kU8) {
+              const float x = fmaf(2.f, G, -nt);  // exact integer
+#pragma unroll
+              for (int u = 0; u < TB; ++u) {
+                if (u >= T) break;
+                if (x >= qlo[u * MAXM + c]) mk[u][w] |= bit;
+              }
+            } else {
+              const float nc = float(norm[c]);
+              const float dv = (nt + nc) - 2.f * G;
+              const float err = 2.f * eps_ip * st * sn[c] * 1.0009765625f + eps_n * (nt + nc) + err_abs;
+              const float hi = (dv + err) * 1.0000005f, lo = (dv - err) * 0.9999995f;
+#pragma unroll
+              for (int u = 0; u < TB; ++u) {
+                if (u >= T) break;
+                bool dom;
+                if (hi < qlo[u * MAXM + c]) {
+                  dom = true;
+                } else if (lo > qhi[u * MAXM + c]) {
+                  dom = false;
+                } else {
+                  // difference-form single precision from the rows, then binary64
+                  const int64_t A2 = int64_t(a.A[u]) * a.A[u];
+                  const float d2a = row_d2<kF32>(a.X + int64_t(ids[t]) * a.row_bytes,
+                                                 a.X + int64_t(ids[c]) * a.row_bytes, a.row_bytes);
+                  atomicAdd(&a.status->spare[2], 1ull);
+                  const int rr = sure_dominates(float(A2), d2a, key[c], E_rel, E_abs);
+                  dom = rr >= 0 ? (rr == 1) : tier3_dominates(a, ids[t], ids[c], p, &key64[c], double(A2));
+                }
+                if (dom) mk[u][w] |= bit;
               }
             }
           }
+        }
+      }
+      if (live_row) {
+#pragma unroll
+        for (int u = 0; u < TB; ++u) {
+          if (u >= T) break;
+#pragma unroll
+          for (int w = 0; w < MW; ++w) masks[(u * MAXM + t) * MW + w] = mk[u][w];
         }
       }
     }
@@ -426,188 +564,35 @@ __global__ void __launch_bounds__(128) prune_tc_kernel(PruneArgs a) {
     tc_fence_after();
     if (p < 0 || dead) continue;
 
-    // ---- a4 processing order: rank of every key among the m keys (warp 0 of the group)
-    if (wg == 0) {
-      if (a.variant == 0) {
-        unsigned long long mk[E];
-        int rank[E];
+    // ---- a7 greedy scan: lane u of the group's first warp walks the
+    // processing order for target u; a kept row clears what it removes.
+    if (wg == 0 && lane < T) {
+      unsigned long long al[MW];
 #pragma unroll
-        for (int e = 0; e < E; ++e) {
-          const int j = lane + 32 * e;
-          mk[e] = j < m ? (Acc<DT>::bits(key[j]) << 32) | unsigned(ids[j]) : ~0ull;
-          rank[e] = 0;
-        }
-#pragma unroll 4
-        for (int q = 0; q < m; ++q) {
-          const unsigned long long kq = (Acc<DT>::bits(key[q]) << 32) | unsigned(ids[q]);
-#pragma unroll
-          for (int e = 0; e < E; ++e) rank[e] += kq < mk[e];
-        }
-#pragma unroll
-        for (int e = 0; e < E; ++e) {
-          const int j = lane + 32 * e;
-          if (j < m) perm[rank[e]] = j;
-        }
-        if constexpr (DT == kF32) {
-          __syncwarp();
-          bool link = false;
-#pragma unroll
-          for (int e = 0; e < E; ++e) {
-            const int i = lane + 32 * e;
-            if (i + 1 < m && !sure_less(key[perm[i]], key[perm[i + 1]], E_rel, E_abs)) link = true;
-          }
-          if (__any_sync(0xffffffffu, link) && lane == 0) {
-            const float* X = reinterpret_cast<const float*>(a.X);
-            const int64_t stride = a.row_bytes / 4;
-            int i = 0;
-            while (i < m) {
-              int end = i;
-              while (end + 1 < m && !sure_less(key[perm[end]], key[perm[end + 1]], E_rel, E_abs)) ++end;
-              if (end > i) {
-                for (int q = i; q <= end; ++q)
-                  key64[perm[q]] = canon_d2_f32(X + int64_t(p) * stride, X + int64_t(ids[perm[q]]) * stride, a.d);
-                atomicAdd(&a.status->fp64_sort_keys, static_cast<unsigned long long>(end - i + 1));
-                for (int q = i + 1; q <= end; ++q) {
-                  const int v = perm[q];
-                  int z = q - 1;
-                  while (z >= i && (key64[perm[z]] > key64[v] || (key64[perm[z]] == key64[v] && ids[perm[z]] > ids[v]))) {
-                    perm[z + 1] = perm[z];
-                    --z;
-                  }
-                  perm[z + 1] = v;
-                }
-              }
-              i = end + 1;
-            }
-          }
-        }
-      } else {
-#pragma unroll
-        for (int e = 0; e < E; ++e) perm[lane + 32 * e] = lane + 32 * e;
+      for (int w = 0; w < MW; ++w) {
+        const int lo = 64 * w;
+        al[w] = m > lo ? ((m - lo >= 64) ? ~0ull : ((1ull << (m - lo)) - 1)) : 0ull;
       }
-    }
-    gsync();
-
-    // ---- a6 + a7: fused lazy domination / greedy scan (warp wg takes targets wg, wg + NW, ...)
-    {
-      int pj[E];
-      AT kj[E];
-      float nj[E], sj[E];
+      const int R = a.R[lane];
+      int32_t* out = a.out_col[lane] + e0;
+      int kept = 0;
+      for (int i = 0; i < m; ++i) {
+        const int pos = perm[i];
+        const int w = pos >> 6;
+        const unsigned long long bit = 1ull << (pos & 63);
+        if (!(al[w] & bit)) continue;
+        out[kept++] = ids[pos];
+        if (kept == R) break;
+        bool left = false;
 #pragma unroll
-      for (int e = 0; e < E; ++e) {
-        const int j = lane + 32 * e;
-        pj[e] = j < m ? perm[j] : 0;
-        kj[e] = j < m ? key[pj[e]] : AT(0);
-        nj[e] = DT == kF32 && j < m ? float(norm[pj[e]]) : 0.f;
-        sj[e] = DT == kF32 && j < m ? sn[pj[e]] : 0.f;
+        for (int q = 0; q < MW; ++q) {
+          al[q] &= ~masks[(lane * MAXM + pos) * MW + q];
+          left |= al[q] != 0;
+        }
+        al[w] &= ~bit;
+        if (!left) break;
       }
-      unsigned long long al[TPW][MW];
-      int kept[TPW];
-      int Rt[TPW];
-      float A2f[TPW];
-      double A2d[TPW];
-      unsigned thr[TPW][E];
-      unsigned long long live[MW];
-#pragma unroll
-      for (int w = 0; w < MW; ++w) live[w] = 0;
-#pragma unroll
-      for (int u = 0; u < TPW; ++u) {
-        const int tt = wg + NW * u;
-        const bool mine = tt < T;
-        const int64_t A2 = mine ? int64_t(a.A[tt]) * a.A[tt] : 1;
-        kept[u] = 0;
-        Rt[u] = mine ? a.R[tt] : 0;
-        A2f[u] = float(A2);
-        A2d[u] = double(A2);
-#pragma unroll
-        for (int e = 0; e < E; ++e) {
-          if constexpr (DT == kU8) thr[u][e] = unsigned((1000000ull * static_cast<unsigned long long>(kj[e])) / A2);
-          else thr[u][e] = 0;
-        }
-#pragma unroll
-        for (int w = 0; w < MW; ++w) {
-          const int lo = 64 * w;
-          unsigned long long bits = 0;
-          if (mine && m > lo) bits = (m - lo >= 64) ? ~0ull : ((1ull << (m - lo)) - 1);
-          al[u][w] = bits;
-          live[w] |= bits;
-        }
-      }
-      for (;;) {
-        int i;
-        if (live[0]) i = __ffsll(static_cast<long long>(live[0])) - 1;
-        else if (MW == 2 && live[MW - 1]) i = 64 + __ffsll(static_cast<long long>(live[MW - 1])) - 1;
-        else break;
-        const int wi = i >> 6;
-        const unsigned long long bit = 1ull << (i & 63);
-        const int pi = perm[i];
-        float dv[E];
-#pragma unroll
-        for (int e = 0; e < E; ++e) dv[e] = D[dix<MAXM>(pi, pj[e])];
-        const float ni = DT == kF32 ? float(norm[pi]) : 0.f;
-        const float si = DT == kF32 ? sn[pi] : 0.f;
-#pragma unroll
-        for (int u = 0; u < TPW; ++u) {
-          if (!(al[u][wi] & bit)) continue;
-          const int tt = wg + NW * u;
-          if (lane == 0) a.out_col[tt][e0 + kept[u]] = ids[pi];
-          ++kept[u];
-          al[u][wi] &= ~bit;
-          if (kept[u] == Rt[u]) {
-#pragma unroll
-            for (int w = 0; w < MW; ++w) al[u][w] = 0;
-            continue;
-          }
-          unsigned bal[E];
-#pragma unroll
-          for (int e = 0; e < E; ++e) {
-            const int j = lane + 32 * e;
-            bool dom = false;
-            if (j > i && j < m) {
-              if constexpr (DT == kU8) {
-                dom = __float_as_uint(dv[e]) <= thr[u][e];
-              } else {
-                // Gram tier: d2~ with its error bound against the pivot key interval
-                const float err = 2.f * eps_ip * si * sj[e] * 1.0009765625f + eps_n * (ni + nj[e]) + err_abs;
-                const float lhs_hi = A2f[u] * (dv[e] + err) * 1.0000005f;
-                const float lhs_lo = A2f[u] * (dv[e] - err) * 0.9999995f;
-                const float rhs_lo = 1.0e6f * (kj[e] * (1.0f - E_rel) - E_abs) * 0.9999995f;
-                const float rhs_hi = 1.0e6f * (kj[e] * (1.0f + E_rel) + E_abs) * 1.0000005f;
-                if (lhs_hi < rhs_lo) {
-                  dom = true;
-                } else if (lhs_lo > rhs_hi) {
-                  dom = false;
-                } else {
-                  // difference-form single precision from the rows, then binary64
-                  const float d2a = row_d2<kF32>(a.X + int64_t(ids[pi]) * a.row_bytes,
-                                                 a.X + int64_t(ids[pj[e]]) * a.row_bytes, a.row_bytes);
-                  atomicAdd(&a.status->spare[2], 1ull);
-                  const int rr = sure_dominates(A2f[u], d2a, kj[e], E_rel, E_abs);
-                  dom = rr >= 0 ? (rr == 1) : tier3_dominates(a, ids[pi], ids[pj[e]], p, &key64[pj[e]], A2d[u]);
-                }
-              }
-            }
-            bal[e] = __ballot_sync(0xffffffffu, dom);
-          }
-#pragma unroll
-          for (int w = 0; w < MW; ++w)
-            al[u][w] &= ~((static_cast<unsigned long long>(bal[2 * w + 1]) << 32) | bal[2 * w]);
-        }
-#pragma unroll
-        for (int w = 0; w < MW; ++w) {
-          unsigned long long lv = 0;
-#pragma unroll
-          for (int u = 0; u < TPW; ++u) lv |= al[u][w];
-          live[w] = lv;
-        }
-      }
-      if (lane == 0) {
-#pragma unroll
-        for (int u = 0; u < TPW; ++u) {
-          const int tt = wg + NW * u;
-          if (tt < T) a.out_cnt[tt][p] = kept[u];
-        }
-      }
+      a.out_cnt[lane][p] = kept;
     }
     ++done;
   }
@@ -983,14 +968,13 @@ static cudaError_t resident_ctas(K kern, int threads, size_t dyn_smem, int cap, 
   return cudaSuccess;
 }
 
-template <int DT, int MAXM, int TPW>
+template <int DT, int MAXM, int TB>
 static cudaError_t run_fast_t(const PruneArgs& args, int num_sms, int64_t host_count, cudaStream_t s) {
-  const size_t bytes = TcLayout<MAXM>::bytes;
-  auto kern = prune_tc_kernel<DT, MAXM, TPW>;
+  const size_t bytes = TcLayout<MAXM, TB>::bytes;
+  auto kern = prune_tc_kernel<DT, MAXM, TB>;
   cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(bytes));
   if (err != cudaSuccess) return err;
-  // ask for the largest shared-memory carveout so the occupancy query (and the
-  // launch) see the whole 228 KB per SM
+  // ask for the largest shared-memory carveout so the launch sees the whole 228 KB per SM
   err = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
   if (err != cudaSuccess) return err;
   int per_sm = 0;
@@ -1002,17 +986,15 @@ static cudaError_t run_fast_t(const PruneArgs& args, int num_sms, int64_t host_c
   return cudaGetLastError();
 }
 
-// Picks the kernel instance whose per-warp target slots cover T (targets are
-// dealt to the MAXM/32 warps of a node group round-robin).
+// Picks the kernel instance whose per-node target slots cover T.
 template <int DT, int MAXM>
 static cudaError_t run_fast(const PruneArgs& args, int num_sms, int64_t host_count, cudaStream_t s) {
   if (host_count <= 0) return cudaSuccess;
-  constexpr int NW = MAXM / 32;
-  const int tpw = (args.T + NW - 1) / NW;
-  if (tpw <= 1) return run_fast_t<DT, MAXM, 1>(args, num_sms, host_count, s);
-  if (tpw <= 2) return run_fast_t<DT, MAXM, 2>(args, num_sms, host_count, s);
-  if (tpw <= 4) return run_fast_t<DT, MAXM, 4>(args, num_sms, host_count, s);
-  return run_fast_t<DT, MAXM, kMaxTargets / NW>(args, num_sms, host_count, s);
+  if (args.T <= 1) return run_fast_t<DT, MAXM, 1>(args, num_sms, host_count, s);
+  if (args.T <= 2) return run_fast_t<DT, MAXM, 2>(args, num_sms, host_count, s);
+  if (args.T <= 4) return run_fast_t<DT, MAXM, 4>(args, num_sms, host_count, s);
+  if (args.T <= 8) return run_fast_t<DT, MAXM, 8>(args, num_sms, host_count, s);
+  return run_fast_t<DT, MAXM, kMaxTargets>(args, num_sms, host_count, s);
 }
 
 template <int DT>
@@ -1058,8 +1040,11 @@ cudaError_t launch_prune(const PruneLaunch& L, cudaStream_t s) {
     a.work = L.work + b;
     const int64_t hc = L.host_bucket_count[b];
     if (L.data.dtype == kU8) {
-      if (b == 0) err = run_fast<kU8, 64>(a, L.num_sms, hc, s);
-      else if (b == 1) err = run_fast<kU8, 128>(a, L.num_sms, hc, s);
+      // The bf16 Gram is exact for uint8 only while every partial sum stays
+      // below 2^24 (d <= 256 here); wider rows take the exact CUDA-core path.
+      const bool exact_tc = L.data.d <= 256;
+      if (b == 0 && exact_tc) err = run_fast<kU8, 64>(a, L.num_sms, hc, s);
+      else if (b == 1 && exact_tc) err = run_fast<kU8, 128>(a, L.num_sms, hc, s);
       else err = run_generic<kU8>(a, L.num_sms, hc, L.host_max_degree, s);
     } else {
       if (b == 0) err = run_fast<kF32, 64>(a, L.num_sms, hc, s);

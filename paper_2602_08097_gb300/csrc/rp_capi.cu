@@ -254,7 +254,8 @@ rp_status enqueue_tune(rp_ctx* c, Graph* S, int T, const int32_t* A, const int32
     L.bucket_nodes[b] = S->buckets + int64_t(b) * S->n;
     L.host_bucket_count[b] = S->n;  // upper bound; kernels stop at the device count
   }
-  if (S->max_deg_bound <= 128) L.host_bucket_count[2] = 0;
+  const bool generic_all = S->data->dtype == RP_U8 && S->data->d > 256;  // see launch_prune
+  if (S->max_deg_bound <= 128 && !generic_all) L.host_bucket_count[2] = 0;
   if (S->max_deg_bound <= 64) L.host_bucket_count[1] = 0;
   L.bucket_count = S->buckets + 3 * S->n;
   L.host_max_degree = S->max_deg_bound;

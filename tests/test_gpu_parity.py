@@ -305,3 +305,33 @@ def test_device_buffers(ctx, tiny):
     ref, _, _ = oracle.greedy_search(X, r.cpu().numpy(), c.cpu().numpy(), rp.rp_graph_info(ctx, t)["start"],
                                      Q.cpu().numpy(), 40, 10)
     assert np.array_equal(ids.cpu().numpy(), ref)
+
+
+def test_uint8_wide_rows_take_the_exact_path(ctx):
+    # d = 384: bf16 partial sums could pass 2^24, so these rows must be pruned
+    # on the exact integer path
+    rng = np.random.default_rng(21)
+    X = rng.integers(0, 256, size=(700, 384)).astype(np.uint8)
+    row_ptr, col = datagen.random_graph(700, 10, 100, seed=4)
+    g = rp.rp_load_graph(ctx, X, row_ptr, col)
+    for alpha, R in ((1.0, 16), (1.2, rp.RP_R_INF)):
+        t = rp.rp_tune(ctx, g, alpha, R)
+        _same_csr(rp.rp_graph_export(ctx, t), oracle.rp_tune(X, row_ptr, col, alpha, R), f"u8 d=384 a={alpha}")
+        rp.rp_graph_free(ctx, t)
+
+
+@pytest.mark.parametrize("dtype", ["u8", "f32"])
+def test_sixteen_targets_in_one_launch(ctx, dtype):
+    n = 3000
+    X = datagen.dataset("sift" if dtype == "u8" else "deep", n)
+    row_ptr, col = datagen.random_graph(n, 0, 128, seed=16)
+    g = rp.rp_load_graph(ctx, X, row_ptr, col)
+    alphas = [1.0 + 0.013 * i for i in range(16)]
+    Rs = [8 + 4 * i for i in range(16)]
+    for variant in (rp.RP_SORTED, rp.RP_UNSORTED):
+        outs = rp.rp_tune_batch(ctx, g, alphas, Rs, variant)
+        for t, a, r in zip(outs, alphas, Rs):
+            _same_csr(rp.rp_graph_export(ctx, t),
+                      oracle.rp_tune(X, row_ptr, col, a, r, "sorted" if variant == rp.RP_SORTED else "unsorted"),
+                      f"{dtype} 16 targets a={a} R={r}")
+            rp.rp_graph_free(ctx, t)
