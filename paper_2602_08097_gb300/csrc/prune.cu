@@ -190,24 +190,34 @@ __device__ __forceinline__ void warp_bitonic(unsigned long long (&key)[E], int (
 //          margin is inside that bound is redone in single-precision
 //          difference form from the rows (rigorous relative bound), and if
 //          still inside, in binary64.
+// Shared-memory plan of prune_tc_kernel.  Per node group the producer warps
+// keep norms and thresholds; per pipeline slot (2) and group they hand the
+// consumer warp the candidate ids, keys, binary64 key cache and masks.
 template <int MAXM, int TB>
 struct TcLayout {
   static constexpr int NG = 128 / MAXM;
   static constexpr int MW = MAXM / 64;
   static constexpr size_t off_opnd = 0;  // 128 rows x 128 dims bf16 = 32 KB
-  static constexpr size_t off_grp = 128 * 128 * 2;
-  static constexpr size_t g_key64 = 0;
-  static constexpr size_t g_masks = g_key64 + size_t(MAXM) * 8;          // [TB][MAXM][MW] u64
-  static constexpr size_t g_ids = g_masks + size_t(TB) * MAXM * MW * 8;
-  static constexpr size_t g_perm = g_ids + size_t(MAXM) * 4;
-  static constexpr size_t g_key = g_perm + size_t(MAXM) * 4;
-  static constexpr size_t g_norm = g_key + size_t(MAXM) * 4;
-  static constexpr size_t g_sn = g_norm + size_t(MAXM) * 4;
-  static constexpr size_t g_qlo = g_sn + size_t(MAXM) * 4;                 // [TB][MAXM] thresholds
-  static constexpr size_t g_qhi = g_qlo + size_t(TB) * MAXM * 4;
-  static constexpr size_t g_bytes = g_qhi + size_t(TB) * MAXM * 4;
-  static constexpr size_t off_misc = off_grp + NG * g_bytes;  // nodes, degrees, row starts, mbar, tmem
-  static constexpr size_t bytes = (off_misc + 128 + 127) & ~size_t(127);
+  // per (slot, group)
+  static constexpr size_t s_key64 = 0;
+  static constexpr size_t s_masks = s_key64 + size_t(MAXM) * 8;  // [TB][MAXM][MW] u64
+  static constexpr size_t s_ids = s_masks + size_t(TB) * MAXM * MW * 8;
+  static constexpr size_t s_key = s_ids + size_t(MAXM) * 4;
+  static constexpr size_t s_bytes = s_key + size_t(MAXM) * 4;
+  static constexpr size_t off_slots = 128 * 128 * 2;
+  // per group, producer side
+  static constexpr size_t p_norm = 0;
+  static constexpr size_t p_sn = p_norm + size_t(MAXM) * 4;
+  static constexpr size_t p_qlo = p_sn + size_t(MAXM) * 4;  // [TB][MAXM]
+  static constexpr size_t p_qhi = p_qlo + size_t(TB) * MAXM * 4;
+  static constexpr size_t p_bytes = p_qhi + size_t(TB) * MAXM * 4;
+  static constexpr size_t off_prod = off_slots + 2 * NG * s_bytes;
+  // per group, consumer side
+  static constexpr size_t off_perm = off_prod + NG * p_bytes;
+  // small words: node/degree/row start per (slot, group) and the next claim, mbarrier, TMEM address
+  static constexpr size_t off_misc = off_perm + NG * size_t(MAXM) * 4;
+  static constexpr size_t misc_bytes = 256;
+  static constexpr size_t bytes = (off_misc + misc_bytes + 127) & ~size_t(127);
 };
 
 // floor(1e6 k / A2) for integers, exactly: a single-precision estimate
@@ -221,386 +231,447 @@ __device__ __forceinline__ unsigned exact_threshold(unsigned k, unsigned long lo
   return static_cast<unsigned>(q);
 }
 
+// Named barriers of prune_tc_kernel (0 is __syncthreads, unused in the loop).
+constexpr int kBarProd = 1;       // the 128 producer threads
+constexpr int kBarFull = 2;       // + slot: producers arrive, the consumer waits (160)
+constexpr int kBarFree = 4;       // + slot: the consumer arrives, producers wait (160)
+
+__device__ __forceinline__ void bar_arrive(int id, int count) {
+  asm volatile("bar.arrive %0, %1;" ::"r"(id), "r"(count) : "memory");
+}
+// Producer barrier that also ORs a flag over the 128 producer threads.
+__device__ __forceinline__ bool prod_sync_or(bool flag) {
+  uint32_t res;
+  asm volatile(
+      "{\n.reg .pred p;\nsetp.ne.u32 p, %1, 0;\nbar.red.or.pred p, 1, 128, p;\nselp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(res)
+      : "r"(static_cast<uint32_t>(flag))
+      : "memory");
+  return res != 0;
+}
+
+// One CTA = 4 producer warps + 1 consumer warp.  The producers (warps 0-3,
+// CTA row r = TMEM lane r) handle NG = 128 / MAXM nodes at a time: gather,
+// keys, bf16 operands, the tcgen05 Gram, per-column thresholds and, from the
+// Gram rows read back from TMEM, one domination mask per target for every
+// candidate.  They hand the masks over through one of two slots; the consumer
+// warp sorts each node's candidates (a4) and walks the processing order per
+// target (a7) while the producers already work on the next nodes.
 template <int DT, int MAXM, int TB>
-__global__ void __launch_bounds__(128) prune_tc_kernel(PruneArgs a) {
+__global__ void __launch_bounds__(160) prune_tc_kernel(PruneArgs a) {
   using L = TcLayout<MAXM, TB>;
   using AT = typename Acc<DT>::T;
   constexpr int NG = L::NG;
-  constexpr int GT = MAXM;      // threads per node group
   constexpr int E = MAXM / 32;  // sort elements per lane
   constexpr int MW = L::MW;
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   const int T = a.T;
-  const int r = threadIdx.x;  // CTA row = TMEM lane
-  const int g = r / GT;
-  const int t = r % GT;
-  const int wg = t >> 5;
-  const int lane = r & 31;
+  const int r = threadIdx.x;
   const int warp = r >> 5;
+  const int lane = r & 31;
   unsigned char* opnd = smem_raw + L::off_opnd;
-  unsigned char* gb = smem_raw + L::off_grp + g * L::g_bytes;
-  double* key64 = reinterpret_cast<double*>(gb + L::g_key64);
-  unsigned long long* masks = reinterpret_cast<unsigned long long*>(gb + L::g_masks);
-  int32_t* ids = reinterpret_cast<int32_t*>(gb + L::g_ids);
-  int32_t* perm = reinterpret_cast<int32_t*>(gb + L::g_perm);
-  AT* key = reinterpret_cast<AT*>(gb + L::g_key);
-  AT* norm = reinterpret_cast<AT*>(gb + L::g_norm);
-  float* sn = reinterpret_cast<float*>(gb + L::g_sn);
-  float* qlo = reinterpret_cast<float*>(gb + L::g_qlo);
-  float* qhi = reinterpret_cast<float*>(gb + L::g_qhi);
-  // misc: [g] node, [2+g] degree, [4+g] next node, [6+g] next degree; row starts at +64
   int* misc = reinterpret_cast<int*>(smem_raw + L::off_misc);
-  uint64_t* mbar = reinterpret_cast<uint64_t*>(smem_raw + L::off_misc + 32);
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem_raw + L::off_misc + 48);
-  int64_t* rows = reinterpret_cast<int64_t*>(smem_raw + L::off_misc + 64);  // [g] row start, [2+g] next
-
-  auto gsync = [&]() {  // constant barrier ids keep the per-block barrier count low
-    if constexpr (NG == 1) {
-      __syncthreads();
-    } else {
-      if (g == 0) named_sync(1, GT);
-      else named_sync(2, GT);
-    }
-  };
+  // misc ints: [0..3] slot node (s*2+g), [4..7] slot degree, [8..9] next node, [10..11] next degree
+  int64_t* misc64 = reinterpret_cast<int64_t*>(smem_raw + L::off_misc + 64);  // [0..3] slot row start, [4..5] next
+  uint64_t* mbar = reinterpret_cast<uint64_t*>(smem_raw + L::off_misc + 128);
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem_raw + L::off_misc + 144);
+  auto slot_base = [&](int s, int g) { return smem_raw + L::off_slots + (size_t(s) * NG + g) * L::s_bytes; };
+  const float E_rel = rel_bound(a.d), E_abs = abs_bound(a.d);
   const int count = *a.count;
-  // claim the next node of the bucket list for this group, with its row bounds
-  auto claim = [&]() {
-    const unsigned idx = atomicAdd(a.work, 1u);
-    const int p = idx < unsigned(count) ? a.nodes[idx] : -1;
-    int deg = 0;
-    int64_t e0 = 0;
-    if (p >= 0) {
-      e0 = a.row_ptr[p];
-      deg = int(a.row_ptr[p + 1] - e0);
-    }
-    if (deg > MAXM) {  // bucketing never sends such a node here; skip it, report it
-      raise_status(a.status, kDevBadDegree, p);
-      deg = 0;
-    }
-    misc[4 + g] = p;
-    misc[6 + g] = deg;
-    rows[2 + g] = e0;
-  };
 
   if (warp == 0) tmem_alloc(tmem_slot, 128);  // 128 of the SM's 512 TMEM columns, for the kernel's life
   if (r == 0) mbar_init(mbar, 1);
-  if (t == 0) claim();
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
-  const uint32_t tmem = *tmem_slot;
-  constexpr uint32_t idesc = umma_idesc_bf16(128, 128);
-  const int64_t elems = a.row_bytes / (DT == kU8 ? 1 : 4);  // padded dims per row
-  const int nslices = int((elems + 127) / 128);
-  const float E_rel = rel_bound(a.d), E_abs = abs_bound(a.d);
-  const float eps_ip = 0.0078125f + 1.52587890625e-05f + float(a.d) * 2.384185791015625e-07f;
-  const float eps_n = float(a.d + 12) * 5.9604645e-08f;
-  const float err_abs = float(a.d) * 2.3509887e-38f;  // underflowed products, 2^-125 each
-  uint32_t phase = 0;
-  long long done = 0;
-  bool dead = false;
 
-  for (;;) {
-    if (t == 0) {
-      misc[g] = misc[4 + g];
-      misc[2 + g] = misc[6 + g];
-      rows[g] = rows[2 + g];
-    }
-    __syncthreads();
-    bool any = false;
+  if (warp < 4) {
+    // =========================== producers ===========================
+    const int g = r / MAXM;
+    const int t = r % MAXM;
+    unsigned char* pb = smem_raw + L::off_prod + g * L::p_bytes;
+    AT* norm = reinterpret_cast<AT*>(pb + L::p_norm);
+    float* sn = reinterpret_cast<float*>(pb + L::p_sn);
+    float* qlo = reinterpret_cast<float*>(pb + L::p_qlo);
+    float* qhi = reinterpret_cast<float*>(pb + L::p_qhi);
+    const uint32_t tmem = *tmem_slot;
+    constexpr uint32_t idesc = umma_idesc_bf16(128, 128);
+    const int64_t elems = a.row_bytes / (DT == kU8 ? 1 : 4);  // padded dims per row
+    const int nslices = int((elems + 127) / 128);
+    const float eps_ip = 0.0078125f + 1.52587890625e-05f + float(a.d) * 2.384185791015625e-07f;
+    const float eps_n = float(a.d + 12) * 5.9604645e-08f;
+    const float err_abs = float(a.d) * 2.3509887e-38f;  // underflowed products, 2^-125 each
+    auto claim = [&]() {  // next node of the bucket list for group g, with its row bounds
+      const unsigned idx = atomicAdd(a.work, 1u);
+      const int p = idx < unsigned(count) ? a.nodes[idx] : -1;
+      int deg = 0;
+      int64_t e0 = 0;
+      if (p >= 0) {
+        e0 = a.row_ptr[p];
+        deg = int(a.row_ptr[p + 1] - e0);
+      }
+      if (deg > MAXM) {  // bucketing never sends such a node here; skip it, report it
+        raise_status(a.status, kDevBadDegree, p);
+        deg = 0;
+      }
+      misc[8 + g] = p;
+      misc[10 + g] = deg;
+      misc64[4 + g] = e0;
+    };
+    if (t == 0) claim();
+    named_sync(kBarProd, 128);
+    uint32_t phase = 0;
+    bool dead = false;
+    for (int k = 0;; ++k) {
+      const int s = k & 1;
+      named_sync(kBarFree + s, 160);  // the consumer is done with this slot
+      if (t == 0) {
+        misc[s * 2 + g] = dead ? -1 : misc[8 + g];
+        misc[4 + s * 2 + g] = dead ? 0 : misc[10 + g];
+        misc64[s * 2 + g] = misc64[4 + g];
+      }
+      named_sync(kBarProd, 128);
+      bool any = false;
 #pragma unroll
-    for (int q = 0; q < NG; ++q) any |= misc[q] >= 0;
-    if (!any || dead) break;  // both are the same for every thread of the CTA
-    const int p = misc[g];
-    const int m = misc[2 + g];
-    const int64_t e0 = rows[g];
-    const bool live_row = t < m;
-    int32_t my_id = 0;
-    if (live_row) {
-      my_id = a.col[e0 + t];
-      ids[t] = my_id;
-      key64[t] = __longlong_as_double(0x7ff8000000000000ll);
-    }
-    // ---- a2 gather, a3 pivot keys, norms, bf16 operand rows; a5 Gram on tcgen05
-    AT kacc = 0, nacc = 0;
-    const uint8_t* xrow = a.X + int64_t(my_id) * a.row_bytes;
-    const uint8_t* prow = a.X + int64_t(p >= 0 ? p : 0) * a.row_bytes;
-    for (int s = 0; s < nslices; ++s) {
-      const int64_t rem = elems - int64_t(s) * 128;
-      const int kd = int(rem < 128 ? rem : 128);  // a multiple of 16 here
-      if constexpr (DT == kU8) {
-        uint4 xs[8], ys[8];
+      for (int q = 0; q < NG; ++q) any |= misc[s * 2 + q] >= 0;
+      if (!any) {  // tell the consumer there is nothing more, and stop
+        bar_arrive(kBarFull + s, 160);
+        break;
+      }
+      unsigned char* sb = slot_base(s, g);
+      double* key64 = reinterpret_cast<double*>(sb + L::s_key64);
+      unsigned long long* masks = reinterpret_cast<unsigned long long*>(sb + L::s_masks);
+      int32_t* ids = reinterpret_cast<int32_t*>(sb + L::s_ids);
+      AT* key = reinterpret_cast<AT*>(sb + L::s_key);
+      const int p = misc[s * 2 + g];
+      const int m = misc[4 + s * 2 + g];
+      const int64_t e0 = misc64[s * 2 + g];
+      const bool live_row = t < m;
+      int32_t my_id = 0;
+      if (live_row) {
+        my_id = a.col[e0 + t];
+        ids[t] = my_id;
+        key64[t] = __longlong_as_double(0x7ff8000000000000ll);
+      }
+      // ---- a2 gather, a3 pivot keys, norms, bf16 operand rows; a5 Gram on tcgen05
+      AT kacc = 0, nacc = 0;
+      const uint8_t* xrow = a.X + int64_t(my_id) * a.row_bytes;
+      const uint8_t* prow = a.X + int64_t(p >= 0 ? p : 0) * a.row_bytes;
+      for (int sl = 0; sl < nslices; ++sl) {
+        const int64_t rem = elems - int64_t(sl) * 128;
+        const int kd = int(rem < 128 ? rem : 128);  // a multiple of 16 here
+        if constexpr (DT == kU8) {
+          uint4 xs[8], ys[8];
 #pragma unroll
-        for (int c = 0; c < 8; ++c) {
-          xs[c] = make_uint4(0, 0, 0, 0);
-          ys[c] = make_uint4(0, 0, 0, 0);
-          if (live_row && c < kd / 16) {
-            xs[c] = __ldg(reinterpret_cast<const uint4*>(xrow + s * 128) + c);
-            ys[c] = __ldg(reinterpret_cast<const uint4*>(prow + s * 128) + c);
+          for (int c = 0; c < 8; ++c) {
+            xs[c] = make_uint4(0, 0, 0, 0);
+            ys[c] = make_uint4(0, 0, 0, 0);
+            if (live_row && c < kd / 16) {
+              xs[c] = __ldg(reinterpret_cast<const uint4*>(xrow + sl * 128) + c);
+              ys[c] = __ldg(reinterpret_cast<const uint4*>(prow + sl * 128) + c);
+            }
           }
-        }
 #pragma unroll
-        for (int c = 0; c < 8; ++c) {
-          if (c >= kd / 16) break;
-          const uint4 x = xs[c];
-          kacc = Acc<kU8>::step4(x, ys[c], kacc);
-          nacc = Acc<kU8>::dot4(x, x, nacc);
-          const unsigned w4[4] = {x.x, x.y, x.z, x.w};
-          uint32_t o[8];
+          for (int c = 0; c < 8; ++c) {
+            if (c >= kd / 16) break;
+            const uint4 x = xs[c];
+            kacc = Acc<kU8>::step4(x, ys[c], kacc);
+            nacc = Acc<kU8>::dot4(x, x, nacc);
+            const unsigned w4[4] = {x.x, x.y, x.z, x.w};
+            uint32_t o[8];
 #pragma unroll
-          for (int q = 0; q < 4; ++q) {
-            o[2 * q] = pack_bf16x2(float(w4[q] & 0xff), float((w4[q] >> 8) & 0xff));
-            o[2 * q + 1] = pack_bf16x2(float((w4[q] >> 16) & 0xff), float(w4[q] >> 24));
+            for (int q = 0; q < 4; ++q) {
+              o[2 * q] = pack_bf16x2(float(w4[q] & 0xff), float((w4[q] >> 8) & 0xff));
+              o[2 * q + 1] = pack_bf16x2(float((w4[q] >> 16) & 0xff), float(w4[q] >> 24));
+            }
+            const int kc0 = 2 * c;
+            *reinterpret_cast<uint4*>(opnd + (kc0 * 16 + r / 8) * 128 + (r % 8) * 16) = make_uint4(o[0], o[1], o[2], o[3]);
+            *reinterpret_cast<uint4*>(opnd + ((kc0 + 1) * 16 + r / 8) * 128 + (r % 8) * 16) =
+                make_uint4(o[4], o[5], o[6], o[7]);
           }
-          const int kc0 = 2 * c;
-          *reinterpret_cast<uint4*>(opnd + (kc0 * 16 + r / 8) * 128 + (r % 8) * 16) = make_uint4(o[0], o[1], o[2], o[3]);
-          *reinterpret_cast<uint4*>(opnd + ((kc0 + 1) * 16 + r / 8) * 128 + (r % 8) * 16) = make_uint4(o[4], o[5], o[6], o[7]);
-        }
-      } else {
+        } else {
 #pragma unroll 4
-        for (int c = 0; c < kd / 8; ++c) {
-          float xv[8];
-          if (live_row) {
-            const uint4* xs = reinterpret_cast<const uint4*>(xrow + int64_t(s) * 512) + 2 * c;
-            const uint4* ps = reinterpret_cast<const uint4*>(prow + int64_t(s) * 512) + 2 * c;
-            const uint4 x0 = __ldg(xs), x1 = __ldg(xs + 1), y0 = __ldg(ps), y1 = __ldg(ps + 1);
-            kacc = Acc<kF32>::step4(x0, y0, kacc);
-            kacc = Acc<kF32>::step4(x1, y1, kacc);
-            xv[0] = __uint_as_float(x0.x); xv[1] = __uint_as_float(x0.y);
-            xv[2] = __uint_as_float(x0.z); xv[3] = __uint_as_float(x0.w);
-            xv[4] = __uint_as_float(x1.x); xv[5] = __uint_as_float(x1.y);
-            xv[6] = __uint_as_float(x1.z); xv[7] = __uint_as_float(x1.w);
+          for (int c = 0; c < kd / 8; ++c) {
+            float xv[8];
+            if (live_row) {
+              const uint4* xs = reinterpret_cast<const uint4*>(xrow + int64_t(sl) * 512) + 2 * c;
+              const uint4* ps = reinterpret_cast<const uint4*>(prow + int64_t(sl) * 512) + 2 * c;
+              const uint4 x0 = __ldg(xs), x1 = __ldg(xs + 1), y0 = __ldg(ps), y1 = __ldg(ps + 1);
+              kacc = Acc<kF32>::step4(x0, y0, kacc);
+              kacc = Acc<kF32>::step4(x1, y1, kacc);
+              xv[0] = __uint_as_float(x0.x); xv[1] = __uint_as_float(x0.y);
+              xv[2] = __uint_as_float(x0.z); xv[3] = __uint_as_float(x0.w);
+              xv[4] = __uint_as_float(x1.x); xv[5] = __uint_as_float(x1.y);
+              xv[6] = __uint_as_float(x1.z); xv[7] = __uint_as_float(x1.w);
 #pragma unroll
-            for (int q = 0; q < 8; ++q) nacc = fmaf(xv[q], xv[q], nacc);
-          } else {
+              for (int q = 0; q < 8; ++q) nacc = fmaf(xv[q], xv[q], nacc);
+            } else {
 #pragma unroll
-            for (int q = 0; q < 8; ++q) xv[q] = 0.f;
+              for (int q = 0; q < 8; ++q) xv[q] = 0.f;
+            }
+            *reinterpret_cast<uint4*>(opnd + (c * 16 + r / 8) * 128 + (r % 8) * 16) =
+                make_uint4(pack_bf16x2(xv[0], xv[1]), pack_bf16x2(xv[2], xv[3]), pack_bf16x2(xv[4], xv[5]),
+                           pack_bf16x2(xv[6], xv[7]));
           }
-          *reinterpret_cast<uint4*>(opnd + (c * 16 + r / 8) * 128 + (r % 8) * 16) =
-              make_uint4(pack_bf16x2(xv[0], xv[1]), pack_bf16x2(xv[2], xv[3]), pack_bf16x2(xv[4], xv[5]),
-                         pack_bf16x2(xv[6], xv[7]));
         }
-      }
-      const bool last = s == nslices - 1;
-      if (last && live_row) {
-        key[t] = kacc;
-        norm[t] = nacc;
-        if constexpr (DT == kF32) sn[t] = sqrtf(nacc);
-      }
-      fence_async_smem();
-      tc_fence_before();
-      __syncthreads();
-      tc_fence_after();
-      if (r == 0) {
+        const bool last = sl == nslices - 1;
+        if (last && live_row) {
+          key[t] = kacc;
+          norm[t] = nacc;
+          if constexpr (DT == kF32) sn[t] = sqrtf(nacc);
+        }
+        fence_async_smem();
+        tc_fence_before();
+        named_sync(kBarProd, 128);
+        tc_fence_after();
+        if (r == 0) {
 #pragma unroll 1
-        for (int k = 0; k < kd / 16; ++k) {
-          const uint64_t dsc = umma_desc(smem_addr(opnd) + uint32_t(k) * 2u * 16u * 128u, 16u * 128u, 128u);
-          umma_bf16(tmem, dsc, dsc, idesc, s > 0 || k > 0);
+          for (int kk = 0; kk < kd / 16; ++kk) {
+            const uint64_t dsc = umma_desc(smem_addr(opnd) + uint32_t(kk) * 2u * 16u * 128u, 16u * 128u, 128u);
+            umma_bf16(tmem, dsc, dsc, idesc, sl > 0 || kk > 0);
+          }
+          umma_commit(mbar);
         }
-        umma_commit(mbar);
+        if (last) {
+          // while the MMA runs: per-column thresholds of every target (a6), the next node
+          if (live_row) {
+#pragma unroll
+            for (int u = 0; u < TB; ++u) {
+              if (u >= T) break;
+              const unsigned long long A2 = static_cast<unsigned long long>(a.A[u]) * a.A[u];
+              if constexpr (DT == kU8) {
+                // v is removed by row u'  <=>  A2 d2(u', v) <= 1e6 d2(p, v)
+                //   <=>  2 G(u', v) - |u'|^2 >= |v|^2 - floor(1e6 d2(p, v) / A2)
+                // (every quantity an integer below 2^24, exact in f32)
+                const unsigned thr = exact_threshold(kacc, A2);
+                qlo[u * MAXM + t] = float(int(nacc) - int(thr));
+              } else {
+                const float A2f = float(A2);
+                qlo[u * MAXM + t] = 1.0e6f * (kacc * (1.0f - E_rel) - E_abs) * 0.9999995f / A2f * 0.9999995f;
+                qhi[u * MAXM + t] = 1.0e6f * (kacc * (1.0f + E_rel) + E_abs) * 1.0000005f / A2f * 1.0000005f;
+              }
+            }
+          }
+          if (t == 0 && p >= 0) claim();
+        }
+        const bool ok = mbar_wait(mbar, phase, 1 << 24);
+        if (prod_sync_or(!ok)) {  // the MMA never completed: report, stop after this slot (uniform)
+          if (r == 0) raise_status(a.status, kDevOverflow, -2);
+          dead = true;
+        }
+        phase ^= 1u;
+        tc_fence_after();
       }
-      if (last && p >= 0) {
-        // While the MMA runs: per-column domination thresholds of every target
-        // (a6), the processing order (a4), the next node.
+
+      // ---- a6: each thread turns its candidate's Gram row (TMEM) into one
+      // mask per target of the candidates (stored positions) it would remove.
+      // tcgen05.ld is warp-collective: every lane issues it, live rows use it.
+      if (!dead) {
+        unsigned long long mk[TB][MW];
+#pragma unroll
+        for (int u = 0; u < TB; ++u)
+#pragma unroll
+          for (int w = 0; w < MW; ++w) mk[u][w] = 0;
+        const float nt = live_row ? float(norm[t]) : 0.f;
+        const float st = DT == kF32 && live_row ? sn[t] : 0.f;
+#pragma unroll 1
+        for (int c0 = 0; c0 < MAXM; c0 += 32) {
+          uint32_t v[32];
+          tmem_ld32(tmem + (uint32_t(32 * warp) << 16) + uint32_t(g * MAXM + c0), v);
+          tmem_ld_wait();
+          if (live_row) {
+#pragma unroll
+            for (int j = 0; j < 32; ++j) {
+              const int c = c0 + j;
+              if (c >= m) break;
+              const float G = __uint_as_float(v[j]);
+              const unsigned long long bit = 1ull << (c & 63);
+              const int w = c >> 6;
+              if constexpr (DT == kU8) {
+                const float x = fmaf(2.f, G, -nt);  // exact integer
+#pragma unroll
+                for (int u = 0; u < TB; ++u) {
+                  if (u >= T) break;
+                  if (x >= qlo[u * MAXM + c]) mk[u][w] |= bit;
+                }
+              } else {
+                const float nc = float(norm[c]);
+                const float dv = (nt + nc) - 2.f * G;
+                const float err = 2.f * eps_ip * st * sn[c] * 1.0009765625f + eps_n * (nt + nc) + err_abs;
+                const float hi = (dv + err) * 1.0000005f, lo = (dv - err) * 0.9999995f;
+#pragma unroll
+                for (int u = 0; u < TB; ++u) {
+                  if (u >= T) break;
+                  bool dom;
+                  if (hi < qlo[u * MAXM + c]) {
+                    dom = true;
+                  } else if (lo > qhi[u * MAXM + c]) {
+                    dom = false;
+                  } else {
+                    // difference-form single precision from the rows, then binary64
+                    const int64_t A2 = int64_t(a.A[u]) * a.A[u];
+                    const float d2a = row_d2<kF32>(a.X + int64_t(ids[t]) * a.row_bytes,
+                                                   a.X + int64_t(ids[c]) * a.row_bytes, a.row_bytes);
+                    atomicAdd(&a.status->spare[2], 1ull);
+                    const int rr = sure_dominates(float(A2), d2a, key[c], E_rel, E_abs);
+                    dom = rr >= 0 ? (rr == 1) : tier3_dominates(a, ids[t], ids[c], p, &key64[c], double(A2));
+                  }
+                  if (dom) mk[u][w] |= bit;
+                }
+              }
+            }
+          }
+        }
         if (live_row) {
 #pragma unroll
           for (int u = 0; u < TB; ++u) {
             if (u >= T) break;
-            const unsigned long long A2 = static_cast<unsigned long long>(a.A[u]) * a.A[u];
-            if constexpr (DT == kU8) {
-              // v is removed by row u'  <=>  A2 d2(u', v) <= 1e6 d2(p, v)
-              //                         <=>  2 G(u', v) - |u'|^2 >= |v|^2 - floor(1e6 d2(p, v) / A2)
-              // (every quantity an integer below 2^24, exact in f32)
-              const unsigned thr = exact_threshold(kacc, A2);
-              qlo[u * MAXM + t] = float(int(nacc) - int(thr));
-            } else {
-              const float A2f = float(A2);
-              qlo[u * MAXM + t] = 1.0e6f * (kacc * (1.0f - E_rel) - E_abs) * 0.9999995f / A2f * 0.9999995f;
-              qhi[u * MAXM + t] = 1.0e6f * (kacc * (1.0f + E_rel) + E_abs) * 1.0000005f / A2f * 1.0000005f;
-            }
+#pragma unroll
+            for (int w = 0; w < MW; ++w) masks[(u * MAXM + t) * MW + w] = mk[u][w];
           }
         }
-        if (wg == 0) {
-          if (a.variant == 0) {
-            unsigned long long mk[E];
-            int rank[E];
-#pragma unroll
-            for (int e = 0; e < E; ++e) {
-              const int j = lane + 32 * e;
-              mk[e] = j < m ? (Acc<DT>::bits(key[j]) << 32) | unsigned(ids[j]) : ~0ull;
-              rank[e] = 0;
-            }
-#pragma unroll 4
-            for (int q = 0; q < m; ++q) {
-              const unsigned long long kq = (Acc<DT>::bits(key[q]) << 32) | unsigned(ids[q]);
-#pragma unroll
-              for (int e = 0; e < E; ++e) rank[e] += kq < mk[e];
-            }
-#pragma unroll
-            for (int e = 0; e < E; ++e) {
-              const int j = lane + 32 * e;
-              if (j < m) perm[rank[e]] = j;
-            }
-            if constexpr (DT == kF32) {
-              // near-ties of single-precision keys: order them by the binary64 keys
-              __syncwarp();
-              bool link = false;
-#pragma unroll
-              for (int e = 0; e < E; ++e) {
-                const int i = lane + 32 * e;
-                if (i + 1 < m && !sure_less(key[perm[i]], key[perm[i + 1]], E_rel, E_abs)) link = true;
-              }
-              if (__any_sync(0xffffffffu, link) && lane == 0) {
-                const float* X = reinterpret_cast<const float*>(a.X);
-                const int64_t stride = a.row_bytes / 4;
-                int i = 0;
-                while (i < m) {
-                  int end = i;
-                  while (end + 1 < m && !sure_less(key[perm[end]], key[perm[end + 1]], E_rel, E_abs)) ++end;
-                  if (end > i) {
-                    for (int q = i; q <= end; ++q)
-                      key64[perm[q]] = canon_d2_f32(X + int64_t(p) * stride, X + int64_t(ids[perm[q]]) * stride, a.d);
-                    atomicAdd(&a.status->fp64_sort_keys, static_cast<unsigned long long>(end - i + 1));
-                    for (int q = i + 1; q <= end; ++q) {
-                      const int v = perm[q];
-                      int z = q - 1;
-                      while (z >= i && (key64[perm[z]] > key64[v] || (key64[perm[z]] == key64[v] && ids[perm[z]] > ids[v]))) {
-                        perm[z + 1] = perm[z];
-                        --z;
-                      }
-                      perm[z + 1] = v;
-                    }
-                  }
-                  i = end + 1;
-                }
-              }
-            }
-          } else {
-#pragma unroll
-            for (int e = 0; e < E; ++e) perm[lane + 32 * e] = lane + 32 * e;
-          }
-        }
-        if (t == 0) claim();  // the next node, fetched while this one is finished
       }
-      const bool ok = mbar_wait(mbar, phase, 1 << 24);
-      if (__syncthreads_or(!ok)) {  // the MMA never completed: report and stop (uniform)
-        if (r == 0) raise_status(a.status, kDevOverflow, -2);
-        dead = true;
-      }
-      phase ^= 1u;
+      if (dead && t == 0) misc[s * 2 + g] = -1;  // nothing valid in this slot
+      tc_fence_before();
+      named_sync(kBarProd, 128);  // every producer's masks and TMEM reads are done
       tc_fence_after();
+      bar_arrive(kBarFull + s, 160);
     }
-
-    // ---- a6: each thread reads its candidate's Gram row from TMEM and builds,
-    // per target, the mask of candidates (by stored position) it would remove.
-    // tcgen05.ld is warp-collective: every lane issues it, live rows use it.
-    if (!dead) {
-      unsigned long long mk[TB][MW];
+  } else {
+    // =========================== consumer warp ===========================
+    bar_arrive(kBarFree + 0, 160);  // both slots start free
+    bar_arrive(kBarFree + 1, 160);
+    long long done = 0;
+    for (int k = 0;; ++k) {
+      const int s = k & 1;
+      named_sync(kBarFull + s, 160);
+      bool any = false;
 #pragma unroll
-      for (int u = 0; u < TB; ++u)
-#pragma unroll
-        for (int w = 0; w < MW; ++w) mk[u][w] = 0;
-      const float nt = live_row ? float(norm[t]) : 0.f;
-      const float st = DT == kF32 && live_row ? sn[t] : 0.f;
+      for (int q = 0; q < NG; ++q) any |= misc[s * 2 + q] >= 0;
+      if (!any) break;
 #pragma unroll 1
-      for (int c0 = 0; c0 < MAXM; c0 += 32) {
-        uint32_t v[32];
-        tmem_ld32(tmem + (uint32_t(32 * warp) << 16) + uint32_t(g * MAXM + c0), v);
-        tmem_ld_wait();
-        if (live_row) {
+      for (int g = 0; g < NG; ++g) {
+        const int p = misc[s * 2 + g];
+        if (p < 0) continue;
+        const int m = misc[4 + s * 2 + g];
+        unsigned char* sb = slot_base(s, g);
+        double* key64 = reinterpret_cast<double*>(sb + L::s_key64);
+        int32_t* ids = reinterpret_cast<int32_t*>(sb + L::s_ids);
+        AT* key = reinterpret_cast<AT*>(sb + L::s_key);
+        int32_t* perm = reinterpret_cast<int32_t*>(smem_raw + L::off_perm + size_t(g) * MAXM * 4);
+        // ---- a4 processing order: rank of each (key, id) among the m candidates
+        if (a.variant == 0) {
+          unsigned long long mkey[E];
+          int rank[E];
 #pragma unroll
-          for (int j = 0; j < 32; ++j) {
-            const int c = c0 + j;
-            if (c >= m) break;
-            const float G = __uint_as_float(v[j]);
-            const unsigned long long bit = 1ull << (c & 63);
-            const int w = c >> 6;
-            if constexpr (DT == kU8) {
-              const float x = fmaf(2.f, G, -nt);  // exact integer
+          for (int e = 0; e < E; ++e) {
+            const int j = lane + 32 * e;
+            mkey[e] = j < m ? (Acc<DT>::bits(key[j]) << 32) | unsigned(ids[j]) : ~0ull;
+            rank[e] = 0;
+          }
+#pragma unroll 4
+          for (int q = 0; q < m; ++q) {
+            const unsigned long long kq = (Acc<DT>::bits(key[q]) << 32) | unsigned(ids[q]);
 #pragma unroll
-              for (int u = 0; u < TB; ++u) {
-                if (u >= T) break;
-                if (x >= qlo[u * MAXM + c]) mk[u][w] |= bit;
-              }
-            } else {
-              const float nc = float(norm[c]);
-              const float dv = (nt + nc) - 2.f * G;
-              const float err = 2.f * eps_ip * st * sn[c] * 1.0009765625f + eps_n * (nt + nc) + err_abs;
-              const float hi = (dv + err) * 1.0000005f, lo = (dv - err) * 0.9999995f;
+            for (int e = 0; e < E; ++e) rank[e] += kq < mkey[e];
+          }
 #pragma unroll
-              for (int u = 0; u < TB; ++u) {
-                if (u >= T) break;
-                bool dom;
-                if (hi < qlo[u * MAXM + c]) {
-                  dom = true;
-                } else if (lo > qhi[u * MAXM + c]) {
-                  dom = false;
-                } else {
-                  // difference-form single precision from the rows, then binary64
-                  const int64_t A2 = int64_t(a.A[u]) * a.A[u];
-                  const float d2a = row_d2<kF32>(a.X + int64_t(ids[t]) * a.row_bytes,
-                                                 a.X + int64_t(ids[c]) * a.row_bytes, a.row_bytes);
-                  atomicAdd(&a.status->spare[2], 1ull);
-                  const int rr = sure_dominates(float(A2), d2a, key[c], E_rel, E_abs);
-                  dom = rr >= 0 ? (rr == 1) : tier3_dominates(a, ids[t], ids[c], p, &key64[c], double(A2));
+          for (int e = 0; e < E; ++e) {
+            const int j = lane + 32 * e;
+            if (j < m) perm[rank[e]] = j;
+          }
+          if constexpr (DT == kF32) {
+            // near-ties of single-precision keys: order them by the binary64 keys
+            __syncwarp();
+            bool link = false;
+#pragma unroll
+            for (int e = 0; e < E; ++e) {
+              const int i = lane + 32 * e;
+              if (i + 1 < m && !sure_less(key[perm[i]], key[perm[i + 1]], E_rel, E_abs)) link = true;
+            }
+            if (__any_sync(0xffffffffu, link) && lane == 0) {
+              const float* X = reinterpret_cast<const float*>(a.X);
+              const int64_t stride = a.row_bytes / 4;
+              int i = 0;
+              while (i < m) {
+                int end = i;
+                while (end + 1 < m && !sure_less(key[perm[end]], key[perm[end + 1]], E_rel, E_abs)) ++end;
+                if (end > i) {
+                  for (int q = i; q <= end; ++q)
+                    key64[perm[q]] = canon_d2_f32(X + int64_t(p) * stride, X + int64_t(ids[perm[q]]) * stride, a.d);
+                  atomicAdd(&a.status->fp64_sort_keys, static_cast<unsigned long long>(end - i + 1));
+                  for (int q = i + 1; q <= end; ++q) {
+                    const int v = perm[q];
+                    int z = q - 1;
+                    while (z >= i && (key64[perm[z]] > key64[v] || (key64[perm[z]] == key64[v] && ids[perm[z]] > ids[v]))) {
+                      perm[z + 1] = perm[z];
+                      --z;
+                    }
+                    perm[z + 1] = v;
+                  }
                 }
-                if (dom) mk[u][w] |= bit;
+                i = end + 1;
               }
             }
           }
+        } else {
+#pragma unroll
+          for (int e = 0; e < E; ++e) perm[lane + 32 * e] = lane + 32 * e;
+        }
+        __syncwarp();
+        ++done;
+      }
+      // ---- a7 greedy scan: lane (g * 16 + u) walks node g's processing order for target u
+      {
+        const int g = NG == 2 ? lane >> 4 : 0;
+        const int u = NG == 2 ? (lane & 15) : lane;
+        const int p = misc[s * 2 + g];
+        if (p >= 0 && u < T) {
+          const int m = misc[4 + s * 2 + g];
+          const int64_t e0 = misc64[s * 2 + g];
+          unsigned char* sb = slot_base(s, g);
+          const unsigned long long* masks = reinterpret_cast<const unsigned long long*>(sb + L::s_masks);
+          const int32_t* ids = reinterpret_cast<const int32_t*>(sb + L::s_ids);
+          const int32_t* perm = reinterpret_cast<const int32_t*>(smem_raw + L::off_perm + size_t(g) * MAXM * 4);
+          unsigned long long al[MW];
+#pragma unroll
+          for (int w = 0; w < MW; ++w) {
+            const int lo = 64 * w;
+            al[w] = m > lo ? ((m - lo >= 64) ? ~0ull : ((1ull << (m - lo)) - 1)) : 0ull;
+          }
+          const int R = a.R[u];
+          int32_t* out = a.out_col[u] + e0;
+          int kept = 0;
+          for (int i = 0; i < m; ++i) {
+            const int pos = perm[i];
+            const int w = pos >> 6;
+            const unsigned long long bit = 1ull << (pos & 63);
+            if (!(al[w] & bit)) continue;
+            out[kept++] = ids[pos];
+            if (kept == R) break;
+            bool left = false;
+#pragma unroll
+            for (int q = 0; q < MW; ++q) {
+              al[q] &= ~masks[(u * MAXM + pos) * MW + q];
+              left |= al[q] != 0;
+            }
+            if (!left) break;
+          }
+          a.out_cnt[u][p] = kept;
         }
       }
-      if (live_row) {
-#pragma unroll
-        for (int u = 0; u < TB; ++u) {
-          if (u >= T) break;
-#pragma unroll
-          for (int w = 0; w < MW; ++w) masks[(u * MAXM + t) * MW + w] = mk[u][w];
-        }
-      }
+      __syncwarp();
+      bar_arrive(kBarFree + s, 160);
     }
-    tc_fence_before();
-    __syncthreads();
-    tc_fence_after();
-    if (p < 0 || dead) continue;
-
-    // ---- a7 greedy scan: lane u of the group's first warp walks the
-    // processing order for target u; a kept row clears what it removes.
-    if (wg == 0 && lane < T) {
-      unsigned long long al[MW];
-#pragma unroll
-      for (int w = 0; w < MW; ++w) {
-        const int lo = 64 * w;
-        al[w] = m > lo ? ((m - lo >= 64) ? ~0ull : ((1ull << (m - lo)) - 1)) : 0ull;
-      }
-      const int R = a.R[lane];
-      int32_t* out = a.out_col[lane] + e0;
-      int kept = 0;
-      for (int i = 0; i < m; ++i) {
-        const int pos = perm[i];
-        const int w = pos >> 6;
-        const unsigned long long bit = 1ull << (pos & 63);
-        if (!(al[w] & bit)) continue;
-        out[kept++] = ids[pos];
-        if (kept == R) break;
-        bool left = false;
-#pragma unroll
-        for (int q = 0; q < MW; ++q) {
-          al[q] &= ~masks[(lane * MAXM + pos) * MW + q];
-          left |= al[q] != 0;
-        }
-        al[w] &= ~bit;
-        if (!left) break;
-      }
-      a.out_cnt[lane][p] = kept;
-    }
-    ++done;
+    if (lane == 0 && done) atomicAdd(&a.status->nodes_pruned, static_cast<unsigned long long>(done) * T);
   }
-  tc_fence_before();
-  __syncthreads();
-  tc_fence_after();
-  if (warp == 0) tmem_dealloc(tmem, 128);
-  if (t == 0 && done) atomicAdd(&a.status->nodes_pruned, static_cast<unsigned long long>(done) * T);
+  // the TMEM columns go back once the producers are finished with them
+  if (warp < 4) {
+    tc_fence_before();
+    named_sync(kBarProd, 128);
+    tc_fence_after();
+    if (warp == 0) tmem_dealloc(*tmem_slot, 128);
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -972,17 +1043,18 @@ template <int DT, int MAXM, int TB>
 static cudaError_t run_fast_t(const PruneArgs& args, int num_sms, int64_t host_count, cudaStream_t s) {
   const size_t bytes = TcLayout<MAXM, TB>::bytes;
   auto kern = prune_tc_kernel<DT, MAXM, TB>;
+  constexpr int kThreadsTc = 160;  // 4 producer warps + 1 consumer warp
   cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(bytes));
   if (err != cudaSuccess) return err;
   // ask for the largest shared-memory carveout so the launch sees the whole 228 KB per SM
   err = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
   if (err != cudaSuccess) return err;
   int per_sm = 0;
-  err = resident_ctas(kern, 128, bytes, 4 /* 128 of the 512 TMEM columns per CTA */, &per_sm);
+  err = resident_ctas(kern, kThreadsTc, bytes, 4 /* 128 of the 512 TMEM columns per CTA */, &per_sm);
   if (err != cudaSuccess) return err;
   const int64_t groups_needed = (host_count + (128 / MAXM) - 1) / (128 / MAXM);
   const int64_t grid = std::min<int64_t>(int64_t(num_sms) * per_sm, groups_needed);
-  kern<<<unsigned(grid), 128, bytes, s>>>(args);
+  kern<<<unsigned(grid), kThreadsTc, bytes, s>>>(args);
   return cudaGetLastError();
 }
 
