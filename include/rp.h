@@ -183,6 +183,24 @@ rp_status rp_search(rp_ctx *ctx, rp_graph g, const void *queries, int64_t nq, in
                     int32_t k, int32_t *ids, float *dists, int32_t mem_flags);
 
 /*
+ * rp_search_multi: one launch of GreedySearch (Algorithm 2) over queries that
+ * address different graphs and list sizes -- the mixed batch a serving loop
+ * collects.  The paper has no counterpart; each query's result is exactly what
+ * rp_search(ctx, graphs[q_graph[i]], query i, q_L[i], k) returns, since every
+ * query is searched on its own.
+ *   graphs: ngraphs >= 1 resident graphs that share their vectors (tuned
+ *     from one base, or the base itself).
+ *   q_graph, q_L: int32[nq] host arrays: the graph index (in [0, ngraphs))
+ *     and the list size (k <= q_L[i] <= RP_MAX_L) of each query.
+ *   queries, ids, dists, mem_flags: as rp_search.
+ * Errors: RP_ENOTFOUND, RP_EINVAL (an index or list size out of range, graphs
+ *   with different vectors, k < 1), RP_ENOMEM, RP_ECUDA, RP_EDEVICE.
+ */
+rp_status rp_search_multi(rp_ctx *ctx, const rp_graph *graphs, int32_t ngraphs,
+                          const int32_t *q_graph, const int32_t *q_L, const void *queries,
+                          int64_t nq, int32_t k, int32_t *ids, float *dists, int32_t mem_flags);
+
+/*
  * rp_search_noalloc: the GreedySearch of rp_search for callers that cannot
  * allocate device memory.  The paper has no counterpart: this entry point
  * exists for processes that reserve all device memory up front (an inference
@@ -254,6 +272,14 @@ rp_status rp_recall(rp_ctx *ctx, const int32_t *found, int32_t ld_found, const i
 rp_status rp_build_knn_base(rp_ctx *ctx, rp_graph data, int32_t kcand, double alpha, int32_t R,
                             rp_graph *out);
 
+/*
+ * rp_graph_shape: the vectors behind graph g (d and dtype) and the device
+ * bytes of g's own adjacency (row_ptr and col capacity, vectors excluded).  A
+ * graph tuned from g holds the same number of adjacency bytes.  Any output
+ * pointer may be NULL.  Errors: RP_ENOTFOUND.
+ */
+rp_status rp_graph_shape(rp_ctx *ctx, rp_graph g, int32_t *d, int32_t *dtype, uint64_t *adj_bytes);
+
 /* rp_graph_free: release a graph (its vectors are freed with the last graph
  * that uses them).  Errors: RP_ENOTFOUND. */
 rp_status rp_graph_free(rp_ctx *ctx, rp_graph g);
@@ -277,6 +303,124 @@ typedef struct {
 } rp_stats_t;
 
 rp_status rp_stats(rp_ctx *ctx, rp_stats_t *out, int32_t reset);
+
+/* ------------------------------------------------------------------------
+ * Serving: a scheduler thread over one resident base graph that takes
+ * prune-to-(alpha, R) jobs and query batches as they arrive (continuous
+ * batching).  The paper tunes one graph at a time; serving many targets from
+ * one base is this library's extension of §3's RP-Tuning (every tuned graph
+ * is still computed from the base, never chained).
+ *
+ * Each scheduling round admits the waiting requests in arrival order while
+ * (a) the distinct tuned graphs they address fit in the graph budget and
+ * (b) their queries fit in max_batch_queries (the first waiting request is
+ * always admitted).  The round then evicts least-recently-used tuned graphs
+ * that none of its requests address until the new ones fit, tunes all
+ * missing graphs in batched launches (up to 16 targets each), and runs all
+ * of its searches in one mixed launch per k (rp_search_multi).  Results
+ * depend only on each request, never on the mix.  With `serial` set the
+ * scheduler is the plain path instead: one request per round, one target per
+ * tuning launch.
+ * ---------------------------------------------------------------------- */
+typedef struct rp_server rp_server;
+
+/* The operations a server runs, with their rp_ctx counterparts: tune_batch
+ * ~ rp_tune_batch (RP_SORTED), search_multi ~ rp_search_multi (host
+ * memory), graph_free ~ rp_graph_free.  rp_server_create supplies these for
+ * a context; rp_server_create_ex takes any implementation, e.g. one on a
+ * host without a GPU.  The callbacks run on the scheduler thread, one at a
+ * time. */
+typedef struct {
+  void *user;
+  rp_status (*tune_batch)(void *user, rp_graph src, const double *alphas, const int32_t *Rs,
+                          int32_t T, rp_graph *outs);
+  rp_status (*search_multi)(void *user, const rp_graph *graphs, int32_t ngraphs,
+                            const int32_t *q_graph, const int32_t *q_L, const void *queries,
+                            int64_t nq, int32_t k, int32_t *ids, float *dists);
+  rp_status (*graph_free)(void *user, rp_graph g);
+} rp_executor;
+
+typedef struct {
+  rp_graph base;               /* the graph every target is tuned from */
+  int32_t d;                   /* vector dimension */
+  int32_t dtype;               /* RP_U8 or RP_F32 */
+  uint64_t graph_bytes;        /* device bytes of one tuned graph (the budget's unit) */
+  uint64_t graph_budget_bytes; /* bytes for resident tuned graphs; 0 = unlimited */
+  int64_t max_batch_queries;   /* queries admitted per round; 0 = 65536 */
+  int32_t serial;              /* 1 = plain serial path */
+} rp_server_config;
+
+/* rp_server_create: a server over base graph `base` of ctx.  The ctx must
+ * outlive the server; other calls on the ctx may run meanwhile (calls are
+ * serialised by the ctx).  Errors: RP_EINVAL, RP_ENOTFOUND. */
+rp_status rp_server_create(rp_ctx *ctx, rp_graph base, uint64_t graph_budget_bytes,
+                           int64_t max_batch_queries, int32_t serial, rp_server **out);
+
+/* rp_server_create_ex: a server over an executor; *ex is copied.
+ * Errors: RP_EINVAL (missing callback, d < 1, bad dtype). */
+rp_status rp_server_create_ex(const rp_executor *ex, const rp_server_config *cfg, rp_server **out);
+
+/* rp_server_destroy: finish every submitted request, stop the scheduler and
+ * free the tuned graphs it holds (the base stays). */
+rp_status rp_server_destroy(rp_server *srv);
+
+/* rp_submit_tune: ask for the graph tuned to (alpha, R) to be resident.
+ * alpha >= 1 on the 0.001 grid, R >= 1 (RP_R_INF = no limit).  Returns at
+ * once with *request_id.  Errors: RP_EINVAL. */
+rp_status rp_submit_tune(rp_server *srv, double alpha, int32_t R, int64_t *request_id);
+
+/* rp_submit_search: queue GreedySearch of nq host query rows (packed, d
+ * elements of the base's dtype each; copied before the call returns) on the
+ * graph tuned to (alpha, R), tuning it first if it is not resident; alpha = 0
+ * searches the base itself.  The list size used is max(L, k) (a request with
+ * L < k is raised to k and counted as a clamp).  ids (int32[nq * k]) and
+ * dists (float[nq * k] or NULL) are host buffers that must stay valid until
+ * rp_poll reports the request finished; they receive rp_search's outputs.
+ * Errors: RP_EINVAL (nq < 1, k < 1, L or k above RP_MAX_L, bad alpha or R,
+ * null pointer). */
+rp_status rp_submit_search(rp_server *srv, double alpha, int32_t R, const void *queries,
+                           int64_t nq, int32_t L, int32_t k, int32_t *ids, float *dists,
+                           int64_t *request_id);
+
+enum { RP_REQ_QUEUED = 0, RP_REQ_RUNNING = 1, RP_REQ_DONE = 2 };
+
+typedef struct {
+  int32_t state;      /* RP_REQ_* */
+  rp_status status;   /* outcome of a finished request (RP_OK or the failing call's code) */
+  rp_graph graph;     /* the tuned graph that served it (0 if it failed) */
+  int32_t L_eff;      /* list size used by a search */
+  int32_t round;      /* scheduling round that ran it (1-based) */
+  int64_t submit_ns;  /* steady-clock times since the server started */
+  int64_t start_ns;
+  int64_t done_ns;
+} rp_request_info;
+
+/* rp_poll: wait up to timeout_ms (0 = do not wait) for a request.  Returns
+ * RP_OK with *info filled once it has finished (and forgets it: a second poll
+ * of the same id returns RP_ENOTFOUND), RP_ETIMEOUT if it has not finished in
+ * time (*info filled with its state), RP_ENOTFOUND for an unknown id,
+ * RP_EINVAL for timeout_ms < 0. */
+rp_status rp_poll(rp_server *srv, int64_t request_id, int32_t timeout_ms, rp_request_info *info);
+
+typedef struct {
+  int64_t requests_done;
+  int64_t requests_failed;
+  int64_t queries_done;
+  int64_t rounds;
+  int64_t tune_launches;     /* tune_batch calls */
+  int64_t targets_tuned;
+  int64_t search_launches;   /* search_multi calls */
+  int64_t evictions;
+  int64_t l_clamps;          /* searches submitted with L < k */
+  int64_t resident_graphs;   /* tuned graphs held now */
+  int64_t peak_resident_graphs;
+  int64_t busy_ns;           /* time the scheduler spent running rounds */
+} rp_server_stats_t;
+
+rp_status rp_server_stats(rp_server *srv, rp_server_stats_t *out);
+
+/* Message of the last failed request or call on the server (owned by it). */
+const char *rp_server_last_error(rp_server *srv);
 
 #ifdef __cplusplus
 }

@@ -44,6 +44,38 @@ class rp_stats_t(ctypes.Structure):
                 ("last_emit_ms", ctypes.c_float), ("last_search_ms", ctypes.c_float)]
 
 
+class rp_request_info(ctypes.Structure):
+    _fields_ = [("state", ctypes.c_int32), ("status", ctypes.c_int32), ("graph", ctypes.c_int64),
+                ("L_eff", ctypes.c_int32), ("round", ctypes.c_int32), ("submit_ns", ctypes.c_int64),
+                ("start_ns", ctypes.c_int64), ("done_ns", ctypes.c_int64)]
+
+
+class rp_server_stats_t(ctypes.Structure):
+    _fields_ = [(name, ctypes.c_int64) for name in (
+        "requests_done", "requests_failed", "queries_done", "rounds", "tune_launches", "targets_tuned",
+        "search_launches", "evictions", "l_clamps", "resident_graphs", "peak_resident_graphs", "busy_ns")]
+
+
+TUNE_FN = ctypes.CFUNCTYPE(ctypes.c_int32, ctypes.c_void_p, ctypes.c_int64, ctypes.POINTER(ctypes.c_double),
+                           ctypes.POINTER(ctypes.c_int32), ctypes.c_int32, ctypes.POINTER(ctypes.c_int64))
+SEARCH_FN = ctypes.CFUNCTYPE(ctypes.c_int32, ctypes.c_void_p, ctypes.POINTER(ctypes.c_int64), ctypes.c_int32,
+                             ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32), ctypes.c_void_p,
+                             ctypes.c_int64, ctypes.c_int32, ctypes.POINTER(ctypes.c_int32),
+                             ctypes.POINTER(ctypes.c_float))
+FREE_FN = ctypes.CFUNCTYPE(ctypes.c_int32, ctypes.c_void_p, ctypes.c_int64)
+
+
+class rp_executor(ctypes.Structure):
+    _fields_ = [("user", ctypes.c_void_p), ("tune_batch", TUNE_FN), ("search_multi", SEARCH_FN),
+                ("graph_free", FREE_FN)]
+
+
+class rp_server_config(ctypes.Structure):
+    _fields_ = [("base", ctypes.c_int64), ("d", ctypes.c_int32), ("dtype", ctypes.c_int32),
+                ("graph_bytes", ctypes.c_uint64), ("graph_budget_bytes", ctypes.c_uint64),
+                ("max_batch_queries", ctypes.c_int64), ("serial", ctypes.c_int32)]
+
+
 _lib = None
 
 
@@ -72,6 +104,15 @@ def load_library(path: str = LIB_PATH):
         "rp_graph_free": [P, i64],
         "rp_stats": [P, ctypes.POINTER(rp_stats_t), i32],
         "rp_search_noalloc": [P, i32, i64, i32, P, P, i64, P, i64, i32, i32, P, P, P],
+        "rp_search_multi": [P, P, i32, P, P, P, i64, i32, P, P, i32],
+        "rp_graph_shape": [P, i64, ctypes.POINTER(i32), ctypes.POINTER(i32), ctypes.POINTER(u64)],
+        "rp_server_create": [P, i64, u64, i64, i32, ctypes.POINTER(P)],
+        "rp_server_create_ex": [ctypes.POINTER(rp_executor), ctypes.POINTER(rp_server_config), ctypes.POINTER(P)],
+        "rp_server_destroy": [P],
+        "rp_submit_tune": [P, dbl, i32, ctypes.POINTER(i64)],
+        "rp_submit_search": [P, dbl, i32, P, i64, i32, i32, P, P, ctypes.POINTER(i64)],
+        "rp_poll": [P, i64, i32, ctypes.POINTER(rp_request_info)],
+        "rp_server_stats": [P, ctypes.POINTER(rp_server_stats_t)],
     }
     for name, args in sig.items():
         fn = getattr(lib, name)
@@ -79,6 +120,8 @@ def load_library(path: str = LIB_PATH):
         fn.restype = i32
     lib.rp_last_error.argtypes = [P]
     lib.rp_last_error.restype = ctypes.c_char_p
+    lib.rp_server_last_error.argtypes = [P]
+    lib.rp_server_last_error.restype = ctypes.c_char_p
     _lib = lib
     return lib
 
@@ -208,6 +251,31 @@ def rp_search(ctx, g: int, queries, L: int, k: int, ids=None, dists=None):
     return ids, dists
 
 
+def rp_search_multi(ctx, graphs, q_graph, q_L, queries, k: int, ids=None, dists=None):
+    """One search launch where query i runs on graphs[q_graph[i]] with list size q_L[i]."""
+    mem = _mem(queries, ids, dists)
+    nq = int(queries.shape[0])
+    dev = queries.device if mem == RP_MEM_DEVICE else None
+    if ids is None:
+        ids = _empty_like_mem(mem, (nq, k), np.int32, dev)
+    if dists is None:
+        dists = _empty_like_mem(mem, (nq, k), np.float32, dev)
+    g = np.ascontiguousarray(graphs, dtype=np.int64)
+    qg = np.ascontiguousarray(q_graph, dtype=np.int32)
+    qL = np.ascontiguousarray(q_L, dtype=np.int32)
+    if qg.shape != (nq,) or qL.shape != (nq,):
+        raise ValueError("q_graph and q_L need one entry per query")
+    _check(ctx, load_library().rp_search_multi(ctx, _ptr(g), int(g.shape[0]), _ptr(qg), _ptr(qL), _ptr(queries), nq,
+                                               int(k), _ptr(ids), _ptr(dists), mem))
+    return ids, dists
+
+
+def rp_graph_shape(ctx, g: int) -> dict:
+    d, dt, b = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_uint64()
+    _check(ctx, load_library().rp_graph_shape(ctx, int(g), ctypes.byref(d), ctypes.byref(dt), ctypes.byref(b)))
+    return dict(d=d.value, dtype=dt.value, adj_bytes=b.value)
+
+
 def rp_knn(ctx, g: int, queries, k: int, nq: int | None = None, ids=None, dists=None):
     """Exact kNN of ``queries`` (or of base points 0..nq-1 when queries is None)."""
     mem = _mem(queries, ids, dists) if queries is not None else (_mem(ids) if ids is not None else RP_MEM_HOST)
@@ -270,3 +338,89 @@ def rp_search_noalloc(vectors, row_ptr, col, start: int, queries, L: int, k: int
     if rc != RP_OK:
         raise RPError(rc, "rp_search_noalloc rejected its arguments or failed to launch")
     return ids, dists
+
+
+# ---- serving (rp_server_*): the binding keeps the buffers and callbacks the
+# library holds pointers to alive until the request is reaped / the server is
+# destroyed.
+RP_REQ_QUEUED, RP_REQ_RUNNING, RP_REQ_DONE = 0, 1, 2
+_held = {}  # server handle -> {"exec": callbacks, request id -> (ids, dists)}
+
+
+def _scheck(srv, rc, what):
+    if rc != RP_OK:
+        msg = load_library().rp_server_last_error(srv).decode(errors="replace") if srv else ""
+        raise RPError(rc, f"{what}: {msg}")
+
+
+def rp_server_create(ctx, base: int, graph_budget_bytes: int = 0, max_batch_queries: int = 0,
+                     serial: bool = False):
+    out = ctypes.c_void_p()
+    _check(ctx, load_library().rp_server_create(ctx, int(base), int(graph_budget_bytes), int(max_batch_queries),
+                                                int(bool(serial)), ctypes.byref(out)))
+    _held[out.value] = {}
+    return out.value
+
+
+def rp_server_create_ex(tune_batch, search_multi, graph_free, base: int, d: int, dtype: int, graph_bytes: int,
+                        graph_budget_bytes: int = 0, max_batch_queries: int = 0, serial: bool = False):
+    """A server over Python callables with the rp_executor signatures (raw ctypes arguments)."""
+    ex = rp_executor(None, TUNE_FN(tune_batch), SEARCH_FN(search_multi), FREE_FN(graph_free))
+    cfg = rp_server_config(int(base), int(d), int(dtype), int(graph_bytes), int(graph_budget_bytes),
+                           int(max_batch_queries), int(bool(serial)))
+    out = ctypes.c_void_p()
+    rc = load_library().rp_server_create_ex(ctypes.byref(ex), ctypes.byref(cfg), ctypes.byref(out))
+    if rc != RP_OK:
+        raise RPError(rc, "rp_server_create_ex rejected its arguments")
+    _held[out.value] = {"exec": ex}
+    return out.value
+
+
+def rp_server_destroy(srv):
+    rc = load_library().rp_server_destroy(srv)
+    _held.pop(srv, None)
+    if rc != RP_OK:
+        raise RPError(rc, "rp_server_destroy: freeing a tuned graph failed")
+
+
+def rp_submit_tune(srv, alpha: float, R: int) -> int:
+    rid = ctypes.c_int64()
+    _scheck(srv, load_library().rp_submit_tune(srv, float(alpha), int(R), ctypes.byref(rid)), "rp_submit_tune")
+    return rid.value
+
+
+def rp_submit_search(srv, alpha: float, R: int, queries: np.ndarray, L: int, k: int, ids=None, dists=None):
+    """Queue a search of host rows ``queries``; returns (request id, ids, dists), the
+    arrays being filled by the time rp_poll reports the request finished."""
+    queries = np.ascontiguousarray(queries)
+    nq = int(queries.shape[0])
+    if ids is None:
+        ids = np.empty((nq, k), dtype=np.int32)
+    if dists is None:
+        dists = np.empty((nq, k), dtype=np.float32)
+    rid = ctypes.c_int64()
+    _scheck(srv, load_library().rp_submit_search(srv, float(alpha), int(R), _ptr(queries), nq, int(L), int(k),
+                                                 _ptr(ids), _ptr(dists), ctypes.byref(rid)), "rp_submit_search")
+    _held[srv][rid.value] = (ids, dists)
+    return rid.value, ids, dists
+
+
+def rp_poll(srv, request_id: int, timeout_ms: int = 0):
+    """None while the request runs; its rp_request_info as a dict once finished."""
+    info = rp_request_info()
+    rc = load_library().rp_poll(srv, int(request_id), int(timeout_ms), ctypes.byref(info))
+    if rc == RP_ETIMEOUT:
+        return None
+    _scheck(srv, rc, "rp_poll")
+    _held.get(srv, {}).pop(int(request_id), None)
+    return {name: getattr(info, name) for name, _ in rp_request_info._fields_}
+
+
+def rp_server_stats(srv) -> dict:
+    s = rp_server_stats_t()
+    _scheck(srv, load_library().rp_server_stats(srv, ctypes.byref(s)), "rp_server_stats")
+    return {name: getattr(s, name) for name, _ in rp_server_stats_t._fields_}
+
+
+def rp_server_last_error(srv) -> str:
+    return load_library().rp_server_last_error(srv).decode(errors="replace")

@@ -68,11 +68,22 @@ cudaError_t launch_medoid(const DevData& D, double* mean /* d */, double* block_
 int64_t medoid_blocks(int64_t n);
 
 // search.cu
+// One graph of a mixed search launch (all graphs share the vectors).
+struct SearchGraph {
+  const int64_t* row_ptr;
+  const int32_t* col;
+  int64_t start;
+  int64_t pad;
+};
+
 struct SearchLaunch {
   DevData data;
   const int64_t* row_ptr = nullptr;
   const int32_t* col = nullptr;
   int64_t start = 0;
+  const SearchGraph* graphs = nullptr;  // device; with q_graph, replaces row_ptr/col/start
+  const int32_t* q_graph = nullptr;     // device, per query; validated by the caller
+  const int32_t* q_L = nullptr;         // device, per query, k <= q_L[i] <= L; validated by the caller
   const uint8_t* Q = nullptr;  // padded rows like data
   int64_t nq = 0;
   int L = 0;

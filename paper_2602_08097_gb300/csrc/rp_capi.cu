@@ -390,6 +390,97 @@ rp_status tune_impl(rp_ctx* c, rp_graph src, const double* alphas, const int32_t
   return RP_OK;
 }
 
+// GreedySearch over `nq` queries.  With q_graph == nullptr every query runs on
+// graphs[0] with list size L; otherwise query i runs on graphs[q_graph[i]] with
+// list size q_L[i] (both validated by the caller, L = their maximum).
+rp_status search_impl(rp_ctx* c, const rp_graph* graphs, int32_t ngraphs, const int32_t* q_graph,
+                      const int32_t* q_L, const void* queries, int64_t nq, int32_t L, int32_t k, int32_t* ids,
+                      float* dists, int32_t mem_flags) {
+  std::vector<Graph*> Gs(static_cast<size_t>(ngraphs));
+  for (int32_t j = 0; j < ngraphs; ++j) {
+    Gs[j] = find_graph(c, graphs[j]);
+    if (!Gs[j]) return fail(c, RP_ENOTFOUND, "unknown graph %lld", (long long)graphs[j]);
+    if (Gs[j]->data != Gs[0]->data) return fail(c, RP_EINVAL, "graphs of one search must share their vectors");
+  }
+  if (nq < 0 || k < 1 || L < k || L > RP_MAX_L)
+    return fail(c, RP_EINVAL, "need nq >= 0 and 1 <= k <= L <= %d (nq=%lld L=%d k=%d)", RP_MAX_L, (long long)nq, L, k);
+  if (mem_flags != RP_MEM_HOST && mem_flags != RP_MEM_DEVICE) return fail(c, RP_EINVAL, "bad mem_flags %d", mem_flags);
+  if (nq == 0) return RP_OK;
+  if (!queries || !ids) return fail(c, RP_EINVAL, "null argument");
+  const Dataset& D = *Gs[0]->data;
+  rp_status s;
+  const int64_t qbytes = nq * D.row_bytes;
+  const int64_t out_bytes = mem_flags == RP_MEM_HOST ? nq * k * 8 : 0;
+  // per-query tables of a mixed launch: graph refs, then graph index and L per query
+  const int64_t table_off = (qbytes + out_bytes + 255) / 256 * 256;
+  const int64_t table_bytes = q_graph ? int64_t(ngraphs) * int64_t(sizeof(SearchGraph)) + 8 * nq + 16 : 0;
+  if ((s = grow(c, &c->qbuf, &c->qbuf_bytes, table_off + table_bytes)) != RP_OK) return s;
+  if ((s = upload_rows(c, c->qbuf, D.row_bytes, queries, nq, D.d, D.dtype, mem_flags)) != RP_OK) return s;
+  const int slots = search_slots(c->num_sms, D.n);
+  const int64_t words = (D.n + 31) / 32;
+  if (c->seen_bits_words < words * slots) {
+    if ((s = grow(c, &c->seen_bits, &c->seen_bits_words, words * slots)) != RP_OK) return s;
+    CUDA_TRY(c, cudaMemsetAsync(c->seen_bits, 0, size_t(c->seen_bits_words) * 4, c->stream));
+  }
+  const int64_t list_cap = 16384;
+  if ((s = grow(c, &c->seen_list, &c->seen_list_elems, list_cap * slots)) != RP_OK) return s;
+  SearchLaunch S;
+  S.data = D.dev();
+  S.row_ptr = Gs[0]->row_ptr;
+  S.col = Gs[0]->col;
+  S.start = Gs[0]->start;
+  S.max_degree = 0;
+  for (Graph* G : Gs) S.max_degree = std::max(S.max_degree, G->max_deg_bound);
+  if (q_graph) {
+    std::vector<SearchGraph> tab(static_cast<size_t>(ngraphs));
+    for (int32_t j = 0; j < ngraphs; ++j) tab[j] = SearchGraph{Gs[j]->row_ptr, Gs[j]->col, Gs[j]->start, 0};
+    uint8_t* t = c->qbuf + table_off;
+    const size_t gb = size_t(ngraphs) * sizeof(SearchGraph);
+    CUDA_TRY(c, cudaMemcpyAsync(t, tab.data(), gb, cudaMemcpyHostToDevice, c->stream));
+    CUDA_TRY(c, cudaMemcpyAsync(t + gb, q_graph, size_t(nq) * 4, cudaMemcpyHostToDevice, c->stream));
+    CUDA_TRY(c, cudaMemcpyAsync(t + gb + size_t(nq) * 4, q_L, size_t(nq) * 4, cudaMemcpyHostToDevice, c->stream));
+    S.graphs = reinterpret_cast<const SearchGraph*>(t);
+    S.q_graph = reinterpret_cast<const int32_t*>(t + gb);
+    S.q_L = reinterpret_cast<const int32_t*>(t + gb + size_t(nq) * 4);
+  }
+  S.Q = c->qbuf;
+  S.nq = nq;
+  S.L = L;
+  S.k = k;
+  int32_t* dev_ids = ids;
+  float* dev_d = dists;
+  if (mem_flags == RP_MEM_HOST) {
+    dev_ids = reinterpret_cast<int32_t*>(c->qbuf + qbytes);
+    dev_d = reinterpret_cast<float*>(c->qbuf + qbytes + nq * k * 4);
+  }
+  S.out_ids = dev_ids;
+  S.out_dists = dev_d;
+  S.seen_bits = c->seen_bits;
+  S.seen_words = words;
+  S.seen_list = c->seen_list;
+  S.seen_list_cap = list_cap;
+  S.slots = slots;
+  S.work = c->work;
+  S.status = c->status;
+  CUDA_TRY(c, cudaMemsetAsync(c->work, 0, 8 * sizeof(unsigned), c->stream));
+  CUDA_TRY(c, record(c->ev[3], c->stream));
+  CUDA_TRY(c, launch_search(S, c->stream));
+  CUDA_TRY(c, record(c->ev[4], c->stream));
+  c->ev_search = true;
+  c->kernel_launches += 1;
+  if (mem_flags == RP_MEM_HOST) {
+    CUDA_TRY(c, cudaMemcpyAsync(ids, dev_ids, size_t(nq * k) * 4, cudaMemcpyDeviceToHost, c->stream));
+    if (dists) CUDA_TRY(c, cudaMemcpyAsync(dists, dev_d, size_t(nq * k) * 4, cudaMemcpyDeviceToHost, c->stream));
+    CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    return check_device_status(c);
+  }
+  if (q_graph) {
+    // the host tables were read by stream-ordered copies; finish them before returning
+    CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  }
+  return RP_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -685,6 +776,17 @@ rp_status rp_graph_export(rp_ctx* c, rp_graph g, int64_t* row_ptr, int32_t* col,
   return RP_OK;
 }
 
+rp_status rp_graph_shape(rp_ctx* c, rp_graph g, int32_t* d, int32_t* dtype, uint64_t* adj_bytes) {
+  if (!c) return RP_EINVAL;
+  std::lock_guard<std::mutex> lk(c->mu);
+  Graph* G = find_graph(c, g);
+  if (!G) return fail(c, RP_ENOTFOUND, "unknown graph %lld", (long long)g);
+  if (d) *d = G->data->d;
+  if (dtype) *dtype = G->data->dtype;
+  if (adj_bytes) *adj_bytes = uint64_t(G->n + 1) * 8 + uint64_t(std::max<int64_t>(G->col_cap, 1)) * 4;
+  return RP_OK;
+}
+
 rp_status rp_graph_free(rp_ctx* c, rp_graph g) {
   if (!c) return RP_EINVAL;
   std::lock_guard<std::mutex> lk(c->mu);
@@ -709,64 +811,26 @@ rp_status rp_search(rp_ctx* c, rp_graph g, const void* queries, int64_t nq, int3
   if (!c) return RP_EINVAL;
   std::lock_guard<std::mutex> lk(c->mu);
   cudaSetDevice(c->device);
-  Graph* G = find_graph(c, g);
-  if (!G) return fail(c, RP_ENOTFOUND, "unknown graph %lld", (long long)g);
-  if (nq < 0 || k < 1 || L < k || L > RP_MAX_L)
-    return fail(c, RP_EINVAL, "need nq >= 0 and 1 <= k <= L <= %d (nq=%lld L=%d k=%d)", RP_MAX_L, (long long)nq, L, k);
-  if (nq == 0) return RP_OK;
-  if (!queries || !ids) return fail(c, RP_EINVAL, "null argument");
-  const Dataset& D = *G->data;
-  rp_status s;
-  const int64_t qbytes = nq * D.row_bytes;
-  const int64_t out_bytes = nq * k * 8;
-  if ((s = grow(c, &c->qbuf, &c->qbuf_bytes, qbytes + (mem_flags == RP_MEM_HOST ? out_bytes : 0))) != RP_OK) return s;
-  if ((s = upload_rows(c, c->qbuf, D.row_bytes, queries, nq, D.d, D.dtype, mem_flags)) != RP_OK) return s;
-  const int slots = search_slots(c->num_sms, D.n);
-  const int64_t words = (D.n + 31) / 32;
-  if (c->seen_bits_words < words * slots) {
-    if ((s = grow(c, &c->seen_bits, &c->seen_bits_words, words * slots)) != RP_OK) return s;
-    CUDA_TRY(c, cudaMemsetAsync(c->seen_bits, 0, size_t(c->seen_bits_words) * 4, c->stream));
+  return search_impl(c, &g, 1, nullptr, nullptr, queries, nq, L, k, ids, dists, mem_flags);
+}
+
+rp_status rp_search_multi(rp_ctx* c, const rp_graph* graphs, int32_t ngraphs, const int32_t* q_graph,
+                          const int32_t* q_L, const void* queries, int64_t nq, int32_t k, int32_t* ids, float* dists,
+                          int32_t mem_flags) {
+  if (!c) return RP_EINVAL;
+  std::lock_guard<std::mutex> lk(c->mu);
+  cudaSetDevice(c->device);
+  if (!graphs || ngraphs < 1 || (nq > 0 && (!q_graph || !q_L)))
+    return fail(c, RP_EINVAL, "need ngraphs >= 1 and per-query graph indexes and list sizes");
+  int32_t Lmax = k;
+  for (int64_t i = 0; i < nq; ++i) {
+    if (q_graph[i] < 0 || q_graph[i] >= ngraphs)
+      return fail(c, RP_EINVAL, "query %lld: graph index %d outside [0, %d)", (long long)i, q_graph[i], ngraphs);
+    if (q_L[i] < k || q_L[i] > RP_MAX_L)
+      return fail(c, RP_EINVAL, "query %lld: need k <= L <= %d (L=%d k=%d)", (long long)i, RP_MAX_L, q_L[i], k);
+    Lmax = std::max(Lmax, q_L[i]);
   }
-  const int64_t list_cap = 16384;
-  if ((s = grow(c, &c->seen_list, &c->seen_list_elems, list_cap * slots)) != RP_OK) return s;
-  SearchLaunch S;
-  S.data = D.dev();
-  S.row_ptr = G->row_ptr;
-  S.col = G->col;
-  S.start = G->start;
-  S.Q = c->qbuf;
-  S.nq = nq;
-  S.L = L;
-  S.k = k;
-  int32_t* dev_ids = ids;
-  float* dev_d = dists;
-  if (mem_flags == RP_MEM_HOST) {
-    dev_ids = reinterpret_cast<int32_t*>(c->qbuf + qbytes);
-    dev_d = reinterpret_cast<float*>(c->qbuf + qbytes + nq * k * 4);
-  }
-  S.out_ids = dev_ids;
-  S.out_dists = dev_d;
-  S.seen_bits = c->seen_bits;
-  S.seen_words = words;
-  S.seen_list = c->seen_list;
-  S.seen_list_cap = list_cap;
-  S.slots = slots;
-  S.work = c->work;
-  S.status = c->status;
-  S.max_degree = G->max_deg_bound;
-  CUDA_TRY(c, cudaMemsetAsync(c->work, 0, 8 * sizeof(unsigned), c->stream));
-  CUDA_TRY(c, record(c->ev[3], c->stream));
-  CUDA_TRY(c, launch_search(S, c->stream));
-  CUDA_TRY(c, record(c->ev[4], c->stream));
-  c->ev_search = true;
-  c->kernel_launches += 1;
-  if (mem_flags == RP_MEM_HOST) {
-    CUDA_TRY(c, cudaMemcpyAsync(ids, dev_ids, size_t(nq * k) * 4, cudaMemcpyDeviceToHost, c->stream));
-    if (dists) CUDA_TRY(c, cudaMemcpyAsync(dists, dev_d, size_t(nq * k) * 4, cudaMemcpyDeviceToHost, c->stream));
-    CUDA_TRY(c, cudaStreamSynchronize(c->stream));
-    return check_device_status(c);
-  }
-  return RP_OK;
+  return search_impl(c, graphs, ngraphs, q_graph, q_L, queries, nq, Lmax, k, ids, dists, mem_flags);
 }
 
 rp_status rp_knn(rp_ctx* c, rp_graph g, const void* queries, int64_t nq, int32_t k, int32_t* ids, float* dists,

@@ -41,9 +41,12 @@ struct SearchArgs {
   const int64_t* row_ptr;
   const int32_t* col;
   int64_t start;
+  const SearchGraph* graphs;  // per-query graphs (with q_graph), or nullptr
+  const int32_t* q_graph;     // index into graphs per query, or nullptr
+  const int32_t* q_L;         // list size per query (k <= q_L <= L), or nullptr
   const uint8_t* Q;
   int64_t nq;
-  int L;
+  int L;                      // largest list size; sizes the shared memory
   int k;
   int32_t* out_ids;
   float* out_dists;
@@ -180,6 +183,16 @@ __global__ void __launch_bounds__(kWarps * 32) search_kernel(SearchArgs a) {
     if (lane == 0) qi = atomicAdd(a.work, 1u);
     qi = __shfl_sync(0xffffffffu, qi, 0);
     if (qi >= a.nq) break;
+    const int64_t* __restrict__ row_ptr = a.row_ptr;
+    const int32_t* __restrict__ col = a.col;
+    int64_t start = a.start;
+    if (a.q_graph) {
+      const SearchGraph g = a.graphs[a.q_graph[qi]];
+      row_ptr = g.row_ptr;
+      col = g.col;
+      start = g.start;
+    }
+    const int L = a.q_L ? a.q_L[qi] : a.L;
     // stage the query row
     const uint4* src = reinterpret_cast<const uint4*>(a.Q + int64_t(qi) * a.row_bytes);
     for (int c = lane; c < a.row_bytes / 16; c += 32) reinterpret_cast<uint4*>(S.q)[c] = src[c];
@@ -189,7 +202,7 @@ __global__ void __launch_bounds__(kWarps * 32) search_kernel(SearchArgs a) {
     int size = 1;
     int64_t nseen = 0;
     if (lane == 0) {
-      const unsigned s = unsigned(a.start);
+      const unsigned s = unsigned(start);
       S.key[0][0] = dist_bits<DT>(S.q, a.X + int64_t(s) * a.row_bytes, a.row_bytes);
       S.idv[0][0] = s;
       if (f32) S.d64[0][0] = qnan;
@@ -221,14 +234,14 @@ __global__ void __launch_bounds__(kWarps * 32) search_kernel(SearchArgs a) {
       __syncwarp();
       if (lane == 0) S.idv[cur][pos] |= kVisited;
       __syncwarp();
-      const int64_t e0 = a.row_ptr[ps], e1 = a.row_ptr[ps + 1];
+      const int64_t e0 = row_ptr[ps], e1 = row_ptr[ps + 1];
       for (int64_t eb = e0; eb < e1; eb += 32) {
         // ---- new neighbours of this batch
         const int64_t e = eb + lane;
         bool fresh = false;
         unsigned v = 0;
         if (e < e1) {
-          v = unsigned(a.col[e]);
+          v = unsigned(col[e]);
           const unsigned bit = 1u << (v & 31);
           const unsigned old = atomicOr(&bits[v >> 5], bit);
           fresh = !(old & bit);
@@ -245,10 +258,10 @@ __global__ void __launch_bounds__(kWarps * 32) search_kernel(SearchArgs a) {
         // would be cut right after the merge, so it skips the merge (it stays
         // marked as seen, which is all Algorithm 2 retains of it).
         bool enters = fresh;
-        if (enters && size == a.L) {
+        if (enters && size == L) {
           double cand_d64 = qnan;
-          enters = entry_less<DT>(kv, v, f32 ? &cand_d64 : nullptr, S.key[cur][a.L - 1],
-                                  S.idv[cur][a.L - 1] & kIdMask, f32 ? &S.d64[cur][a.L - 1] : nullptr, a, S.q,
+          enters = entry_less<DT>(kv, v, f32 ? &cand_d64 : nullptr, S.key[cur][L - 1],
+                                  S.idv[cur][L - 1] & kIdMask, f32 ? &S.d64[cur][L - 1] : nullptr, a, S.q,
                                   E, Eabs);
         }
         const unsigned fm = __ballot_sync(0xffffffffu, enters);
@@ -332,7 +345,7 @@ __global__ void __launch_bounds__(kWarps * 32) search_kernel(SearchArgs a) {
             else hi = mid;
           }
           const int np = i + lo;
-          if (np < a.L) {
+          if (np < L) {
             S.key[nxt][np] = bk;
             S.idv[nxt][np] = bi;
             if (f32) S.d64[nxt][np] = S.d64[cur][i];
@@ -350,14 +363,14 @@ __global__ void __launch_bounds__(kWarps * 32) search_kernel(SearchArgs a) {
             else hi = mid;
           }
           const int np = lane + lo;
-          if (np < a.L) {
+          if (np < L) {
             S.key[nxt][np] = ck;
             S.idv[nxt][np] = ci;
             if (f32) S.d64[nxt][np] = S.cd64[lane];
           }
         }
         __syncwarp();
-        size = min(a.L, size + nf);
+        size = min(L, size + nf);
         cur = nxt;
       }
     }
@@ -427,6 +440,9 @@ cudaError_t launch_search(const SearchLaunch& L, cudaStream_t s) {
   a.row_ptr = L.row_ptr;
   a.col = L.col;
   a.start = L.start;
+  a.graphs = L.graphs;
+  a.q_graph = L.q_graph;
+  a.q_L = L.q_L;
   a.Q = L.Q;
   a.nq = L.nq;
   a.L = L.L;
