@@ -16,6 +16,11 @@ HBM, L2 flushed before every step).  `e2e` repeats the step through the C ABI
 with host buffers: vectors, base CSR and queries copied in, tuned graphs and
 search results copied out, every step.
 
+`serving` (outside the timed step): a Poisson stream of prune-to-(alpha, R)
+jobs and query batches through the library's scheduler (rp_server_*), the
+continuous-batching scheduler against the plain serial path, at offered loads
+relative to the serial path's capacity; p50/p99 latency, QPS and recall@100.
+
 `--impl reference` times the CPU oracle (the reference arm of this build) on
 a bounded sample of the same workload and prints the same JSON line.
 """
@@ -43,6 +48,8 @@ UNIT = "nodes/s per alpha"
 TARGETS = [(1.1, 64), (1.05, 48), (1.0, 32)]
 BASE_ALPHA, BASE_R, KCAND = 1.2, 64, 128
 L_SEARCH, K_SEARCH = 128, 100
+SERVE_BUDGET_GB = 8                     # resident tuned graphs of the serving leg (~30 at this size)
+SERVE_LOADS = (0.5, 0.8, 1.0, 2.0, 4.0)  # offered load / capacity of the serial path
 
 
 def workload_name(n, nq):
@@ -402,6 +409,10 @@ def run_ours(args):
         e2e = {"value": ws * n * T / e2e_s, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
                "d2h_bytes_per_step": int(d2h), "ms_per_step": 1000 * e2e_s}
 
+    serving = None
+    if not args.quick and not args.no_serve:
+        serving = serve_bench(rp, ctx, base, Q, gt, args)
+
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline and not args.quick:
         cpu = cpu_baseline(args.cpu_sample)
@@ -432,11 +443,57 @@ def run_ours(args):
             "recall_at_100": dict(zip([f"{a},{r}" for a, r in TARGETS], recalls)),
             "avg_degree": {"base": float(deg.mean()), **{f"{a},{r}": nz / n for (a, r), nz in zip(TARGETS, nnz)}},
             "fixture_s": fixture_s,
+            "serving": serving,
         }
         print(json.dumps(line), flush=True)
     if ws > 1:
         torch.distributed.destroy_process_group()
     return 0
+
+
+def serve_bench(rp, ctx, base, Q, gt, args):
+    """Poisson stream of prune jobs (10%) and query batches (1..1024 queries, L in
+    64..256 raised to k=100) through the library's scheduler, continuous vs the
+    plain serial path, at offered loads relative to the serial path's capacity.
+    Latency is submission to completion, from the scheduler's own clock."""
+    from paper_2602_08097_gb300.serving import make_requests, replay
+    stream = datagen.poisson_stream(args.serve_requests, 1.0, seed=3001, prune_frac=0.10)
+    budget = SERVE_BUDGET_GB << 30
+
+    def run(serial, time_scale):
+        reqs = make_requests(stream, Q, seed=3001)
+        srv = rp.rp_server_create(ctx, base, graph_budget_bytes=budget, serial=serial)
+        try:
+            rep = replay(srv, reqs, time_scale=time_scale)
+        finally:
+            rp.rp_server_destroy(srv)
+        found = np.concatenate([r.ids for r in reqs if r.kind == "search"])
+        truth = np.ascontiguousarray(np.concatenate([gt[r.rows] for r in reqs if r.kind == "search"]))
+        rep["recall_at_100"] = rp.rp_recall(ctx, found, truth, K_SEARCH) / found.size
+        rep.pop("wall_s", None)
+        return rep
+
+    # capacity of the serial path: everything submitted at once
+    sat = run(True, 0.0)
+    span_s = stream[-1]["t"]
+    cap_rps = sat["requests"] / (sat["stats"]["busy_ns"] / 1e9)
+    out = {"requests": args.serve_requests, "graph_budget_gb": SERVE_BUDGET_GB,
+           "serial_capacity_req_per_s": cap_rps, "loads": {}}
+    for load in SERVE_LOADS:
+        rate = load * cap_rps
+        ts = 1.0 / rate  # stream generated at 1 request/s
+        entry = {"offered_req_per_s": rate}
+        for name, serial in (("serial", True), ("continuous", False)):
+            if serial and load > 1.0:
+                continue  # the serial queue grows without bound past its capacity
+            r = run(serial, ts)
+            entry[name] = {k: r[k] for k in ("p50_ms", "p99_ms", "search_p50_ms", "search_p99_ms", "qps",
+                                             "recall_at_100")}
+            entry[name].update({k: r["stats"][k] for k in ("rounds", "tune_launches", "targets_tuned",
+                                                            "search_launches", "evictions", "l_clamps")})
+        out["loads"][f"{load:g}x"] = entry
+    out["stream_span_s_at_1x"] = span_s / cap_rps
+    return out
 
 
 def kernel_hash():
@@ -458,6 +515,8 @@ def main():
     ap.add_argument("--nq", type=int, default=10_000)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-serve", action="store_true")
+    ap.add_argument("--serve-requests", type=int, default=400)
     ap.add_argument("--cpu-sample", type=int, default=20000)
     ap.add_argument("--ref-sample", type=int, default=20000)
     ap.add_argument("--quick", action="store_true",

@@ -474,27 +474,49 @@ __global__ void __launch_bounds__(160) prune_tc_kernel(PruneArgs a) {
           for (int w = 0; w < MW; ++w) mk[u][w] = 0;
         const float nt = live_row ? float(norm[t]) : 0.f;
         const float st = DT == kF32 && live_row ? sn[t] : 0.f;
-#pragma unroll 1
-        for (int c0 = 0; c0 < MAXM; c0 += 32) {
-          uint32_t v[32];
-          tmem_ld32(tmem + (uint32_t(32 * warp) << 16) + uint32_t(g * MAXM + c0), v);
-          tmem_ld_wait();
-          if (live_row) {
+        if constexpr (DT == kU8) {
+          // Columns at or past the degree hold no candidate: the bits set there
+          // can never meet a live bit in the scan, so they are not tested for.
 #pragma unroll
-            for (int j = 0; j < 32; ++j) {
-              const int c = c0 + j;
-              if (c >= m) break;
-              const float G = __uint_as_float(v[j]);
-              const unsigned long long bit = 1ull << (c & 63);
-              const int w = c >> 6;
-              if constexpr (DT == kU8) {
-                const float x = fmaf(2.f, G, -nt);  // exact integer
+          for (int c0 = 0; c0 < MAXM; c0 += 32) {
+            uint32_t v[32];
+            tmem_ld32(tmem + (uint32_t(32 * warp) << 16) + uint32_t(g * MAXM + c0), v);
+            tmem_ld_wait();
+            if (live_row) {
+              uint32_t wb[TB];
+#pragma unroll
+              for (int u = 0; u < TB; ++u) wb[u] = 0u;
+#pragma unroll
+              for (int j4 = 0; j4 < 32; j4 += 4) {
+                float x[4];
+#pragma unroll
+                for (int q = 0; q < 4; ++q) x[q] = fmaf(2.f, __uint_as_float(v[j4 + q]), -nt);  // exact integer
 #pragma unroll
                 for (int u = 0; u < TB; ++u) {
                   if (u >= T) break;
-                  if (x >= qlo[u * MAXM + c]) mk[u][w] |= bit;
+                  const float4 q4 = *reinterpret_cast<const float4*>(qlo + u * MAXM + c0 + j4);
+                  wb[u] |= (x[0] >= q4.x ? 1u << j4 : 0u) | (x[1] >= q4.y ? 2u << j4 : 0u) |
+                           (x[2] >= q4.z ? 4u << j4 : 0u) | (x[3] >= q4.w ? 8u << j4 : 0u);
                 }
-              } else {
+              }
+#pragma unroll
+              for (int u = 0; u < TB; ++u) mk[u][c0 >> 6] |= static_cast<unsigned long long>(wb[u]) << (c0 & 63);
+            }
+          }
+        } else {
+#pragma unroll 1
+          for (int c0 = 0; c0 < MAXM; c0 += 32) {
+            uint32_t v[32];
+            tmem_ld32(tmem + (uint32_t(32 * warp) << 16) + uint32_t(g * MAXM + c0), v);
+            tmem_ld_wait();
+            if (live_row) {
+#pragma unroll
+              for (int j = 0; j < 32; ++j) {
+                const int c = c0 + j;
+                if (c >= m) break;
+                const float G = __uint_as_float(v[j]);
+                const unsigned long long bit = 1ull << (c & 63);
+                const int w = c >> 6;
                 const float nc = float(norm[c]);
                 const float dv = (nt + nc) - 2.f * G;
                 const float err = 2.f * eps_ip * st * sn[c] * 1.0009765625f + eps_n * (nt + nc) + err_abs;

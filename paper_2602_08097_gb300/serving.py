@@ -24,6 +24,7 @@ class Request:
     R: int
     arrival: float                  # seconds from the start of the stream
     queries: np.ndarray | None = None
+    rows: np.ndarray | None = None  # which rows of the query set the batch holds
     L: int = 0
     k: int = 0
     rid: int = -1                   # library request id once submitted
@@ -46,7 +47,7 @@ def make_requests(stream: list, queries: np.ndarray, seed: int = 0, first_target
             a, R = targets[min(int(s["slot_u"] * len(targets)), len(targets) - 1)]
             nq = min(s["nq"], queries.shape[0])
             rows = rng.choice(queries.shape[0], size=nq, replace=False)
-            reqs.append(Request("search", a, R, s["t"], queries=np.ascontiguousarray(queries[rows]),
+            reqs.append(Request("search", a, R, s["t"], queries=np.ascontiguousarray(queries[rows]), rows=rows,
                                 L=s["L"], k=s["k"]))
     return reqs
 
