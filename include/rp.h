@@ -208,8 +208,8 @@ rp_status rp_search_multi(rp_ctx *ctx, const rp_graph *graphs, int32_t ngraphs,
  * not have allocations appear while they capture a stream.  It takes no
  * context, allocates nothing (no cudaMalloc, cudaMallocAsync or cudaFree, no
  * allocating library routine) and uses instead a fixed scratch array of
- * RP_NOALLOC_SCRATCH_BYTES that every GPU loading this library holds until
- * the process exits.
+ * RP_NOALLOC_SCRATCH_BYTES (a status word and a query counter) that every GPU
+ * loading this library holds until the process exits.
  *   vectors: n x d elements of dtype, device memory, rows packed (stride
  *     d * element size, which must be a multiple of 16 bytes; pointer
  *     16-byte aligned).
@@ -223,16 +223,14 @@ rp_status rp_search_multi(rp_ctx *ctx, const rp_graph *graphs, int32_t ngraphs,
  * The call is asynchronous on cuda_stream and runs on the current device.
  * The first call on a device looks up the scratch array's device address
  * (cudaGetSymbolAddress); make that first call outside any stream capture.
- * All calls share the one array and each clears what it needs at its start,
- * so calls whose work overlaps on the GPU (other streams, other threads) race
- * and must be serialised by the caller.
- * Limit: the per-query membership bitmaps need n/8 bytes each; with at least
- * 4 queries in flight, n may be at most about 134 million.
+ * All calls share the one array and each clears it at its start, so calls
+ * whose work overlaps on the GPU (other streams, other threads) race and must
+ * be serialised by the caller.
  * Errors (checked on the host, before any work is enqueued): RP_EINVAL for a
- * bad argument, a stride or pointer alignment off 16 bytes, or an n beyond
- * the scratch limit; RP_ECUDA if the symbol lookup or a launch fails.
+ * bad argument or a stride or pointer alignment off 16 bytes; RP_ECUDA if
+ * the symbol lookup or a launch fails.
  */
-#define RP_NOALLOC_SCRATCH_BYTES (64u << 20)
+#define RP_NOALLOC_SCRATCH_BYTES 4096u
 rp_status rp_search_noalloc(const void *vectors, int32_t dtype, int64_t n, int32_t d,
                             const int64_t *row_ptr, const int32_t *col, int64_t start,
                             const void *queries, int64_t nq, int32_t L, int32_t k, int32_t *ids,

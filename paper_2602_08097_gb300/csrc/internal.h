@@ -90,17 +90,12 @@ struct SearchLaunch {
   int k = 0;
   int32_t* out_ids = nullptr;
   float* out_dists = nullptr;
-  uint32_t* seen_bits = nullptr;  // per slot: n bits (words)
-  int64_t seen_words = 0;         // words per slot
-  int32_t* seen_list = nullptr;   // per slot: list of set ids, for clearing
-  int64_t seen_list_cap = 0;
-  int slots = 0;
+  int num_sms = 0;
   unsigned int* work = nullptr;   // zeroed
   DevStatus* status = nullptr;
   int max_degree = 0;
 };
 cudaError_t launch_search(const SearchLaunch& S, cudaStream_t s);
-int search_slots(int num_sms, int64_t n);
 cudaError_t launch_recall(const int32_t* found, int ld_found, const int32_t* truth, int ld_truth,
                           int64_t nq, int k, unsigned long long* hits, cudaStream_t s);
 

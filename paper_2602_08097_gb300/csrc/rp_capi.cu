@@ -86,10 +86,6 @@ struct rp_ctx {
   int64_t scratch_bsum_elems = 0;
   unsigned int* work = nullptr;       // device [8]
   // search scratch
-  uint32_t* seen_bits = nullptr;
-  int64_t seen_bits_words = 0;
-  int32_t* seen_list = nullptr;
-  int64_t seen_list_elems = 0;
   uint8_t* qbuf = nullptr;
   int64_t qbuf_bytes = 0;
   unsigned long long* hits = nullptr;  // device [1]
@@ -416,14 +412,6 @@ rp_status search_impl(rp_ctx* c, const rp_graph* graphs, int32_t ngraphs, const 
   const int64_t table_bytes = q_graph ? int64_t(ngraphs) * int64_t(sizeof(SearchGraph)) + 8 * nq + 16 : 0;
   if ((s = grow(c, &c->qbuf, &c->qbuf_bytes, table_off + table_bytes)) != RP_OK) return s;
   if ((s = upload_rows(c, c->qbuf, D.row_bytes, queries, nq, D.d, D.dtype, mem_flags)) != RP_OK) return s;
-  const int slots = search_slots(c->num_sms, D.n);
-  const int64_t words = (D.n + 31) / 32;
-  if (c->seen_bits_words < words * slots) {
-    if ((s = grow(c, &c->seen_bits, &c->seen_bits_words, words * slots)) != RP_OK) return s;
-    CUDA_TRY(c, cudaMemsetAsync(c->seen_bits, 0, size_t(c->seen_bits_words) * 4, c->stream));
-  }
-  const int64_t list_cap = 16384;
-  if ((s = grow(c, &c->seen_list, &c->seen_list_elems, list_cap * slots)) != RP_OK) return s;
   SearchLaunch S;
   S.data = D.dev();
   S.row_ptr = Gs[0]->row_ptr;
@@ -455,11 +443,7 @@ rp_status search_impl(rp_ctx* c, const rp_graph* graphs, int32_t ngraphs, const 
   }
   S.out_ids = dev_ids;
   S.out_dists = dev_d;
-  S.seen_bits = c->seen_bits;
-  S.seen_words = words;
-  S.seen_list = c->seen_list;
-  S.seen_list_cap = list_cap;
-  S.slots = slots;
+  S.num_sms = c->num_sms;
   S.work = c->work;
   S.status = c->status;
   CUDA_TRY(c, cudaMemsetAsync(c->work, 0, 8 * sizeof(unsigned), c->stream));
@@ -536,8 +520,6 @@ rp_status rp_destroy(rp_ctx* c) {
     dfree(c, c->scratch_col, size_t(c->scratch_col_elems) * 4);
     dfree(c, c->scratch_cnt, size_t(c->scratch_cnt_elems) * 4);
     dfree(c, c->scratch_bsum, size_t(c->scratch_bsum_elems) * 8);
-    dfree(c, c->seen_bits, size_t(c->seen_bits_words) * 4);
-    dfree(c, c->seen_list, size_t(c->seen_list_elems) * 4);
     dfree(c, c->qbuf, size_t(c->qbuf_bytes));
     dfree(c, c->status, sizeof(DevStatus));
     dfree(c, c->dropped, 16);

@@ -16,11 +16,11 @@
 
 namespace {
 
-// The whole scratch: a small header (status word and work counter), then one
-// membership bitmap and one list of set ids per in-flight query slot.  Every
-// GPU that loads this library holds these RP_NOALLOC_SCRATCH_BYTES until exit.
+// The whole scratch: the status word (offset 0) and the query counter
+// (offset 128).  Every GPU that loads this library holds these
+// RP_NOALLOC_SCRATCH_BYTES until exit.
 constexpr size_t kHeader = 256;
-constexpr int64_t kListCap = 4096;
+static_assert(kHeader <= RP_NOALLOC_SCRATCH_BYTES, "scratch too small for its header");
 static __device__ __align__(256) unsigned char g_noalloc_scratch[RP_NOALLOC_SCRATCH_BYTES];
 
 // Device addresses of the array, resolved once per device (in host code the
@@ -63,25 +63,13 @@ extern "C" rp_status rp_search_noalloc(const void* vectors, int32_t dtype, int64
   int num_sms = 0;
   if (cudaDeviceGetAttribute(&num_sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return RP_ECUDA;
 
-  // As many query slots as fit (at most 32 warps per SM, a multiple of 4);
-  // a graph too large for even 4 slots is refused.
-  const int64_t words = (n + 31) / 32;
-  const int64_t per_slot = words * 4 + kListCap * 4;
-  int64_t slots = (int64_t(RP_NOALLOC_SCRATCH_BYTES) - int64_t(kHeader)) / per_slot;
-  slots = std::min<int64_t>(slots, int64_t(num_sms) * 32);
-  slots = slots / 4 * 4;
-  if (slots < 4) return RP_EINVAL;
-
   unsigned char* s = static_cast<unsigned char*>(base);
   rpk::DevStatus* status = reinterpret_cast<rpk::DevStatus*>(s);
   unsigned int* work = reinterpret_cast<unsigned int*>(s + 128);
-  uint32_t* bits = reinterpret_cast<uint32_t*>(s + kHeader);
-  int32_t* lists = reinterpret_cast<int32_t*>(s + kHeader + slots * words * 4);
   cudaStream_t stream = static_cast<cudaStream_t>(cuda_stream);
 
-  // The array keeps the last call's contents: the header and the bitmaps
-  // must start at zero.
-  if (cudaMemsetAsync(s, 0, size_t(kHeader + slots * words * 4), stream) != cudaSuccess) return RP_ECUDA;
+  // The array keeps the last call's contents: the header must start at zero.
+  if (cudaMemsetAsync(s, 0, kHeader, stream) != cudaSuccess) return RP_ECUDA;
 
   rpk::SearchLaunch S;
   S.data.X = static_cast<const uint8_t*>(vectors);
@@ -98,11 +86,7 @@ extern "C" rp_status rp_search_noalloc(const void* vectors, int32_t dtype, int64
   S.k = k;
   S.out_ids = ids;
   S.out_dists = dists;
-  S.seen_bits = bits;
-  S.seen_words = words;
-  S.seen_list = lists;
-  S.seen_list_cap = kListCap;
-  S.slots = int(slots);
+  S.num_sms = num_sms;
   S.work = work;
   S.status = status;
   return rpk::launch_search(S, stream) == cudaSuccess ? RP_OK : RP_ECUDA;

@@ -6,12 +6,17 @@
 // member without its visited bit, and "retain the closest L" is a cut after
 // a merge.
 //
-// A per-warp bitmap over all n points remembers every point that ever
-// entered the list.  Skipping such points when a neighbour list is added is
-// exactly Algorithm 2: a point still in the list must not be added twice (the
-// list is a set), and a point that was cut can never come back -- once the
-// list has been cut to L members its L-th (distance, id) only decreases, and
-// the cut point was already behind an earlier L-th.
+// Algorithm 2 keeps a set: adding a point that is already in the list has
+// no effect.  A point that was in the list and was cut may be added again by
+// a later neighbour list, and then it is cut again at once: from the first cut
+// on the list holds L members and its L-th (distance, id) only decreases, so
+// the point still lies behind it.  (An expanded point that is cut is the same
+// case: it comes back behind the L-th and is never the closest unexpanded
+// member.)  So the only membership test the search needs is "is v in the
+// list now?", which a binary search of the sorted list answers exactly at the
+// position where v would be merged.  A small direct-mapped cache of recently
+// met ids in shared memory skips most repeated distance computations; a miss
+// only costs one more distance, never a different result.
 //
 // Neighbours are added 32 at a time, each batch merged and cut to L before the
 // next; the L closest of a union are the L closest of the L closest of its
@@ -50,10 +55,7 @@ struct SearchArgs {
   int k;
   int32_t* out_ids;
   float* out_dists;
-  uint32_t* seen_bits;
-  int64_t seen_words;
-  int32_t* seen_list;
-  int64_t seen_list_cap;
+  int cache_bits;             // log2 of the id-cache entries per warp
   unsigned int* work;
   DevStatus* status;
 };
@@ -66,20 +68,24 @@ struct WarpSmem {
   unsigned* cid;
   double* cd64;
   uint8_t* q;
+  unsigned* cache;  // direct-mapped ids met by this query (0xffffffff = empty)
 };
 
-__host__ __device__ inline size_t warp_bytes(int L, int64_t row_bytes, bool f32) {
+__host__ __device__ inline size_t warp_bytes(int L, int64_t row_bytes, bool f32, int cache_bits) {
   const size_t cap = size_t(L) + 32;
   size_t b = 2 * cap * 8 + 32 * 8;  // keys + ids for both buffers, candidate keys + ids
   if (f32) b += 2 * cap * 8 + 32 * 8;
   b += size_t(row_bytes);
+  b += size_t(4) << cache_bits;
   return (b + 127) & ~size_t(127);
 }
 
-__device__ inline WarpSmem carve(unsigned char* base, int L, int64_t row_bytes, bool f32) {
+__device__ inline WarpSmem carve(unsigned char* base, int L, int64_t row_bytes, bool f32, int cache_bits) {
   WarpSmem w;
   const size_t cap = size_t(L) + 32;
   unsigned char* p = base;
+  w.cache = reinterpret_cast<unsigned*>(p);
+  p += size_t(4) << cache_bits;
   if (f32) {
     w.d64[0] = reinterpret_cast<double*>(p);
     p += cap * 8;
@@ -171,10 +177,10 @@ __global__ void __launch_bounds__(kWarps * 32) search_kernel(SearchArgs a) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const bool f32 = DT == kF32;
-  WarpSmem S = carve(smem_raw + size_t(w) * warp_bytes(a.L, a.row_bytes, f32), a.L, a.row_bytes, f32);
-  const int64_t slot = int64_t(blockIdx.x) * kWarps + w;
-  uint32_t* bits = a.seen_bits + slot * a.seen_words;
-  int32_t* list = a.seen_list + slot * a.seen_list_cap;
+  WarpSmem S = carve(smem_raw + size_t(w) * warp_bytes(a.L, a.row_bytes, f32, a.cache_bits), a.L, a.row_bytes, f32,
+                     a.cache_bits);
+  const int cshift = 32 - a.cache_bits;
+  const int centries = 1 << a.cache_bits;
   const float E = rel_bound(a.d), Eabs = abs_bound(a.d);
   const double qnan = __longlong_as_double(0x7ff8000000000000ll);
 
@@ -196,20 +202,20 @@ __global__ void __launch_bounds__(kWarps * 32) search_kernel(SearchArgs a) {
     // stage the query row
     const uint4* src = reinterpret_cast<const uint4*>(a.Q + int64_t(qi) * a.row_bytes);
     for (int c = lane; c < a.row_bytes / 16; c += 32) reinterpret_cast<uint4*>(S.q)[c] = src[c];
+    for (int c = lane; c < centries; c += 32) S.cache[c] = 0xffffffffu;
     __syncwarp();
 
-    int cur = 0;  // which buffer holds the list
+    // the list and the buffer the next merge writes (swapped after each merge)
+    unsigned *keyc = S.key[0], *keyn = S.key[1], *idc = S.idv[0], *idn = S.idv[1];
+    double *dc = S.d64[0], *dn = S.d64[1];
     int size = 1;
-    int64_t nseen = 0;
     if (lane == 0) {
       const unsigned s = unsigned(start);
-      S.key[0][0] = dist_bits<DT>(S.q, a.X + int64_t(s) * a.row_bytes, a.row_bytes);
-      S.idv[0][0] = s;
-      if (f32) S.d64[0][0] = qnan;
-      bits[s >> 5] |= 1u << (s & 31);
-      list[0] = int32_t(s);
+      keyc[0] = dist_bits<DT>(S.q, a.X + int64_t(s) * a.row_bytes, a.row_bytes);
+      idc[0] = s;
+      if (f32) dc[0] = qnan;
+      S.cache[(s * 0x9E3779B1u) >> cshift] = s;
     }
-    nseen = 1;
     __syncwarp();
 
     int64_t iters = 0;
@@ -218,7 +224,7 @@ __global__ void __launch_bounds__(kWarps * 32) search_kernel(SearchArgs a) {
       int pos = -1;
       for (int c0 = 0; c0 < size; c0 += 32) {
         const int i = c0 + lane;
-        const bool open = i < size && !(S.idv[cur][i] & kVisited);
+        const bool open = i < size && !(idc[i] & kVisited);
         const unsigned b = __ballot_sync(0xffffffffu, open);
         if (b) {
           pos = c0 + __ffs(b) - 1;
@@ -230,9 +236,9 @@ __global__ void __launch_bounds__(kWarps * 32) search_kernel(SearchArgs a) {
         if (lane == 0) raise_status(a.status, kDevOverflow, qi);
         break;
       }
-      const unsigned ps = S.idv[cur][pos] & kIdMask;
+      const unsigned ps = idc[pos] & kIdMask;
       __syncwarp();
-      if (lane == 0) S.idv[cur][pos] |= kVisited;
+      if (lane == 0) idc[pos] |= kVisited;
       __syncwarp();
       const int64_t e0 = row_ptr[ps], e1 = row_ptr[ps + 1];
       for (int64_t eb = e0; eb < e1; eb += 32) {
@@ -242,27 +248,36 @@ __global__ void __launch_bounds__(kWarps * 32) search_kernel(SearchArgs a) {
         unsigned v = 0;
         if (e < e1) {
           v = unsigned(col[e]);
-          const unsigned bit = 1u << (v & 31);
-          const unsigned old = atomicOr(&bits[v >> 5], bit);
-          fresh = !(old & bit);
+          // a row holds distinct ids, so lanes that share a cache entry hold
+          // different ids: whichever write lands, no lane skips a new id
+          const unsigned h = (v * 0x9E3779B1u) >> cshift;
+          fresh = S.cache[h] != v;
+          if (fresh) S.cache[h] = v;
         }
-        const unsigned seen_m = __ballot_sync(0xffffffffu, fresh);
-        const int nseen_b = __popc(seen_m);
-        if (nseen_b == 0) continue;
-        const int rank = __popc(seen_m & ((1u << lane) - 1));
-        if (fresh && nseen + rank < a.seen_list_cap) list[nseen + rank] = int32_t(v);
-        nseen += nseen_b;
+        if (!__any_sync(0xffffffffu, fresh)) continue;
         unsigned kv = 0xffffffffu;
         if (fresh) kv = dist_bits<DT>(S.q, a.X + int64_t(v) * a.row_bytes, a.row_bytes);
-        // A full list keeps only entries before its L-th: a new point behind it
-        // would be cut right after the merge, so it skips the merge (it stays
-        // marked as seen, which is all Algorithm 2 retains of it).
+        // A full list keeps only entries before its L-th: a point behind it
+        // would be cut right after the merge, so it skips the merge.
         bool enters = fresh;
+        double cand_d64 = qnan;
         if (enters && size == L) {
-          double cand_d64 = qnan;
-          enters = entry_less<DT>(kv, v, f32 ? &cand_d64 : nullptr, S.key[cur][L - 1],
-                                  S.idv[cur][L - 1] & kIdMask, f32 ? &S.d64[cur][L - 1] : nullptr, a, S.q,
+          enters = entry_less<DT>(kv, v, f32 ? &cand_d64 : nullptr, keyc[L - 1],
+                                  idc[L - 1] & kIdMask, f32 ? &dc[L - 1] : nullptr, a, S.q,
                                   E, Eabs);
+        }
+        // Already in the list?  Its entry sits exactly where v would be merged.
+        if (enters) {
+          int lo = 0, hi = size;
+          while (lo < hi) {
+            const int mid = (lo + hi) >> 1;
+            const bool bl = entry_less<DT>(keyc[mid], idc[mid] & kIdMask,
+                                           f32 ? &dc[mid] : nullptr, kv, v, f32 ? &cand_d64 : nullptr, a,
+                                           S.q, E, Eabs);
+            if (bl) lo = mid + 1;
+            else hi = mid;
+          }
+          if (lo < size && (idc[lo] & kIdMask) == v) enters = false;
         }
         const unsigned fm = __ballot_sync(0xffffffffu, enters);
         const int nf = __popc(fm);
@@ -333,22 +348,21 @@ __global__ void __launch_bounds__(kWarps * 32) search_kernel(SearchArgs a) {
         }
         __syncwarp();
         // ---- merge the sorted batch into the list, keep the first L
-        const int nxt = cur ^ 1;
         for (int i = lane; i < size; i += 32) {
-          const unsigned bk = S.key[cur][i], bi = S.idv[cur][i];
+          const unsigned bk = keyc[i], bi = idc[i];
           int lo = 0, hi = nf;  // number of candidates before list entry i
           while (lo < hi) {
             const int mid = (lo + hi) >> 1;
             const bool cl = entry_less<DT>(S.ckey[mid], S.cid[mid], f32 ? &S.cd64[mid] : nullptr, bk, bi & kIdMask,
-                                           f32 ? &S.d64[cur][i] : nullptr, a, S.q, E, Eabs);
+                                           f32 ? &dc[i] : nullptr, a, S.q, E, Eabs);
             if (cl) lo = mid + 1;
             else hi = mid;
           }
           const int np = i + lo;
           if (np < L) {
-            S.key[nxt][np] = bk;
-            S.idv[nxt][np] = bi;
-            if (f32) S.d64[nxt][np] = S.d64[cur][i];
+            keyn[np] = bk;
+            idn[np] = bi;
+            if (f32) dn[np] = dc[i];
           }
         }
         if (lane < nf) {
@@ -356,41 +370,39 @@ __global__ void __launch_bounds__(kWarps * 32) search_kernel(SearchArgs a) {
           int lo = 0, hi = size;  // number of list entries before candidate lane
           while (lo < hi) {
             const int mid = (lo + hi) >> 1;
-            const bool bl = entry_less<DT>(S.key[cur][mid], S.idv[cur][mid] & kIdMask,
-                                           f32 ? &S.d64[cur][mid] : nullptr, ck, ci,
+            const bool bl = entry_less<DT>(keyc[mid], idc[mid] & kIdMask,
+                                           f32 ? &dc[mid] : nullptr, ck, ci,
                                            f32 ? &S.cd64[lane] : nullptr, a, S.q, E, Eabs);
             if (bl) lo = mid + 1;
             else hi = mid;
           }
           const int np = lane + lo;
           if (np < L) {
-            S.key[nxt][np] = ck;
-            S.idv[nxt][np] = ci;
-            if (f32) S.d64[nxt][np] = S.cd64[lane];
+            keyn[np] = ck;
+            idn[np] = ci;
+            if (f32) dn[np] = S.cd64[lane];
           }
         }
         __syncwarp();
         size = min(L, size + nf);
-        cur = nxt;
+        {
+          unsigned* t0 = keyc; keyc = keyn; keyn = t0;
+          unsigned* t1 = idc; idc = idn; idn = t1;
+          double* t2 = dc; dc = dn; dn = t2;
+        }
       }
     }
     // ---- the k closest members
     for (int j = lane; j < a.k; j += 32) {
       const bool have = j < size;
-      a.out_ids[int64_t(qi) * a.k + j] = have ? int32_t(S.idv[cur][j] & kIdMask) : -1;
+      a.out_ids[int64_t(qi) * a.k + j] = have ? int32_t(idc[j] & kIdMask) : -1;
       if (a.out_dists) {
         float dv;
         if (!have) dv = __int_as_float(0x7f800000);
-        else if (DT == kU8) dv = float(S.key[cur][j]);
-        else dv = __uint_as_float(S.key[cur][j]);
+        else if (DT == kU8) dv = float(keyc[j]);
+        else dv = __uint_as_float(keyc[j]);
         a.out_dists[int64_t(qi) * a.k + j] = dv;
       }
-    }
-    // ---- forget this query's marks
-    if (nseen <= a.seen_list_cap) {
-      for (int64_t j = lane; j < nseen; j += 32) bits[unsigned(list[j]) >> 5] = 0u;
-    } else {
-      for (int64_t j = lane; j < a.seen_words; j += 32) bits[j] = 0u;
     }
     __syncwarp();
   }
@@ -420,15 +432,15 @@ __global__ void recall_kernel(const int32_t* __restrict__ found, int ld_found, c
 
 }  // namespace
 
-// Queries in flight: enough warps to hide the latency of each expansion (32
-// per SM), fewer if the per-warp membership bitmaps (n bits each) would pass
-// 4 GB.
-int search_slots(int num_sms, int64_t n) {
-  const int64_t bitmap_bytes = ((n + 31) / 32) * 4;
-  int64_t slots = int64_t(num_sms) * 32;
-  const int64_t cap = (int64_t(4) << 30) / std::max<int64_t>(bitmap_bytes, 1);
-  slots = std::min(slots, std::max<int64_t>(cap, int64_t(num_sms) * kWarps));
-  return int(slots / kWarps * kWarps);
+// Shared memory of one SM that the search may plan with, and the CTAs per SM
+// it aims for (32 warps: enough queries in flight to hide the latency of each
+// expansion).
+constexpr int kSmemPerSm = 228 * 1024;
+constexpr int kCtaReserve = 1024;
+constexpr int kMaxCtasPerSm = 8;
+
+int ctas_per_sm(size_t cta_bytes) {
+  return int(std::min<size_t>(kMaxCtasPerSm, size_t(kSmemPerSm) / (cta_bytes + kCtaReserve)));
 }
 
 cudaError_t launch_search(const SearchLaunch& L, cudaStream_t s) {
@@ -449,15 +461,22 @@ cudaError_t launch_search(const SearchLaunch& L, cudaStream_t s) {
   a.k = L.k;
   a.out_ids = L.out_ids;
   a.out_dists = L.out_dists;
-  a.seen_bits = L.seen_bits;
-  a.seen_words = L.seen_words;
-  a.seen_list = L.seen_list;
-  a.seen_list_cap = L.seen_list_cap;
   a.work = L.work;
   a.status = L.status;
   const bool f32 = L.data.dtype == kF32;
-  const size_t bytes = warp_bytes(L.L, L.data.row_bytes, f32) * kWarps;
-  const int grid = L.slots / kWarps;
+  // the largest id cache (256 .. 4096 entries) that keeps the CTAs per SM of the smallest
+  int bits = 8;
+  const int base_ctas = ctas_per_sm(warp_bytes(L.L, L.data.row_bytes, f32, 8) * kWarps);
+  for (int b = 12; b > 8; --b)
+    if (ctas_per_sm(warp_bytes(L.L, L.data.row_bytes, f32, b) * kWarps) >= base_ctas) {
+      bits = b;
+      break;
+    }
+  a.cache_bits = bits;
+  const size_t bytes = warp_bytes(L.L, L.data.row_bytes, f32, bits) * kWarps;
+  const int64_t want = int64_t(L.num_sms) * std::max(base_ctas, 1);
+  const int64_t need = (L.nq + kWarps - 1) / kWarps;
+  const int grid = int(std::max<int64_t>(1, std::min(want, need)));
   cudaError_t err;
   if (f32) {
     err = cudaFuncSetAttribute(search_kernel<kF32>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(bytes));
