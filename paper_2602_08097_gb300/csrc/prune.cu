@@ -127,51 +127,6 @@ __device__ __forceinline__ bool tier3_dominates(const PruneArgs& a, int32_t u, i
   return canon_dominates(A2, d2a, d2b);
 }
 
-// Sort MAXM (key, position) pairs held by one warp, E = MAXM / 32 per lane
-// (element index lane + 32 e), ascending by key.  Keys are unique.
-template <int E>
-__device__ __forceinline__ void warp_bitonic(unsigned long long (&key)[E], int (&pos)[E]) {
-  const int lane = threadIdx.x & 31;
-  constexpr int N = 32 * E;
-#pragma unroll
-  for (int k = 2; k <= N; k <<= 1) {
-#pragma unroll
-    for (int j = k >> 1; j > 0; j >>= 1) {
-      if (j >= 32) {
-        const int je = j / 32;
-#pragma unroll
-        for (int e = 0; e < E; ++e) {
-          if (e & je) continue;
-          const int idx = lane + 32 * e;
-          const bool up = (idx & k) == 0;
-          const unsigned long long a = key[e], b = key[e + je];
-          const int pa = pos[e], pb = pos[e + je];
-          const bool sw = up ? (b < a) : (a < b);
-          if (sw) {
-            key[e] = b; key[e + je] = a;
-            pos[e] = pb; pos[e + je] = pa;
-          }
-        }
-      } else {
-#pragma unroll
-        for (int e = 0; e < E; ++e) {
-          const int idx = lane + 32 * e;
-          const unsigned long long o = __shfl_xor_sync(0xffffffffu, key[e], j);
-          const int op = __shfl_xor_sync(0xffffffffu, pos[e], j);
-          const bool lower = (idx & j) == 0;
-          const bool up = (idx & k) == 0;
-          const bool want_min = lower == up;
-          const bool take = want_min ? (o < key[e]) : (key[e] < o);
-          if (take) {
-            key[e] = o;
-            pos[e] = op;
-          }
-        }
-      }
-    }
-  }
-}
-
 // ---------------------------------------------------------------------------
 // tensor-core path: the candidate Gram on tcgen05
 // ---------------------------------------------------------------------------
@@ -210,12 +165,12 @@ struct TcLayout {
   static constexpr size_t p_sn = p_norm + size_t(MAXM) * 4;
   static constexpr size_t p_qlo = p_sn + size_t(MAXM) * 4;  // [TB][MAXM]
   static constexpr size_t p_qhi = p_qlo + size_t(TB) * MAXM * 4;
-  static constexpr size_t p_bytes = p_qhi + size_t(TB) * MAXM * 4;
+  static constexpr size_t p_sk = p_qhi + size_t(TB) * MAXM * 4;  // [MAXM] (key, id) in stored order
+  static constexpr size_t p_k64 = p_sk + size_t(MAXM) * 8;       // [MAXM] binary64 keys in stored order
+  static constexpr size_t p_bytes = p_k64 + size_t(MAXM) * 8;
   static constexpr size_t off_prod = off_slots + 2 * NG * s_bytes;
-  // per group, consumer side
-  static constexpr size_t off_perm = off_prod + NG * p_bytes;
   // small words: node/degree/row start per (slot, group) and the next claim, mbarrier, TMEM address
-  static constexpr size_t off_misc = off_perm + NG * size_t(MAXM) * 4;
+  static constexpr size_t off_misc = off_prod + NG * p_bytes;
   static constexpr size_t misc_bytes = 256;
   static constexpr size_t bytes = (off_misc + misc_bytes + 127) & ~size_t(127);
 };
@@ -250,19 +205,19 @@ __device__ __forceinline__ bool prod_sync_or(bool flag) {
   return res != 0;
 }
 
-// One CTA = 4 producer warps + 1 consumer warp.  The producers (warps 0-3,
-// CTA row r = TMEM lane r) handle NG = 128 / MAXM nodes at a time: gather,
-// keys, bf16 operands, the tcgen05 Gram, per-column thresholds and, from the
-// Gram rows read back from TMEM, one domination mask per target for every
-// candidate.  They hand the masks over through one of two slots; the consumer
-// warp sorts each node's candidates (a4) and walks the processing order per
+// One CTA = 4 producer warps + 1 consumer warp.  The producers handle NG =
+// 128 / MAXM nodes at a time, one candidate per thread: gather, pivot keys and
+// norms, the rank of each candidate in the processing order (a4), its bf16
+// operand row placed at CTA row (group, rank) = TMEM lane, the tcgen05 Gram,
+// per-column thresholds and, from the Gram rows read back from TMEM, one
+// domination mask per target for every rank.  They hand ids and masks over
+// through one of two slots; the consumer warp runs the greedy loop per node and
 // target (a7) while the producers already work on the next nodes.
 template <int DT, int MAXM, int TB>
 __global__ void __launch_bounds__(160) prune_tc_kernel(PruneArgs a) {
   using L = TcLayout<MAXM, TB>;
   using AT = typename Acc<DT>::T;
   constexpr int NG = L::NG;
-  constexpr int E = MAXM / 32;  // sort elements per lane
   constexpr int MW = L::MW;
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   const int T = a.T;
@@ -346,22 +301,19 @@ __global__ void __launch_bounds__(160) prune_tc_kernel(PruneArgs a) {
       const int p = misc[s * 2 + g];
       const int m = misc[4 + s * 2 + g];
       const int64_t e0 = misc64[s * 2 + g];
-      const bool live_row = t < m;
+      const bool live_row = t < m;  // thread t holds stored candidate t
       int32_t my_id = 0;
-      if (live_row) {
-        my_id = a.col[e0 + t];
-        ids[t] = my_id;
-        key64[t] = __longlong_as_double(0x7ff8000000000000ll);
-      }
-      // ---- a2 gather, a3 pivot keys, norms, bf16 operand rows; a5 Gram on tcgen05
-      AT kacc = 0, nacc = 0;
+      if (live_row) my_id = a.col[e0 + t];
       const uint8_t* xrow = a.X + int64_t(my_id) * a.row_bytes;
       const uint8_t* prow = a.X + int64_t(p >= 0 ? p : 0) * a.row_bytes;
-      for (int sl = 0; sl < nslices; ++sl) {
-        const int64_t rem = elems - int64_t(sl) * 128;
-        const int kd = int(rem < 128 ? rem : 128);  // a multiple of 16 here
-        if constexpr (DT == kU8) {
-          uint4 xs[8], ys[8];
+      // ---- a2 gather, a3 pivot key d2(p, x) and norm |x|^2 of candidate t
+      AT kacc = 0, nacc = 0;
+      uint4 xs[8];  // uint8, one slice: the row stays here for the operand pass
+      if constexpr (DT == kU8) {
+        for (int sl = 0; sl < nslices; ++sl) {
+          const int64_t rem = elems - int64_t(sl) * 128;
+          const int kd = int(rem < 128 ? rem : 128);  // a multiple of 16 here
+          uint4 ys[8];
 #pragma unroll
           for (int c = 0; c < 8; ++c) {
             xs[c] = make_uint4(0, 0, 0, 0);
@@ -373,10 +325,104 @@ __global__ void __launch_bounds__(160) prune_tc_kernel(PruneArgs a) {
           }
 #pragma unroll
           for (int c = 0; c < 8; ++c) {
+            kacc = Acc<kU8>::step4(xs[c], ys[c], kacc);
+            nacc = Acc<kU8>::dot4(xs[c], xs[c], nacc);
+          }
+        }
+      } else {
+        if (live_row) {
+          for (int c = 0; c < int(elems / 8); ++c) {
+            const uint4* xq = reinterpret_cast<const uint4*>(xrow) + 2 * c;
+            const uint4* pq = reinterpret_cast<const uint4*>(prow) + 2 * c;
+            const uint4 x0 = __ldg(xq), x1 = __ldg(xq + 1), y0 = __ldg(pq), y1 = __ldg(pq + 1);
+            kacc = Acc<kF32>::step4(x0, y0, kacc);
+            kacc = Acc<kF32>::step4(x1, y1, kacc);
+            const float xv[8] = {__uint_as_float(x0.x), __uint_as_float(x0.y), __uint_as_float(x0.z),
+                                 __uint_as_float(x0.w), __uint_as_float(x1.x), __uint_as_float(x1.y),
+                                 __uint_as_float(x1.z), __uint_as_float(x1.w)};
+#pragma unroll
+            for (int q = 0; q < 8; ++q) nacc = fmaf(xv[q], xv[q], nacc);
+          }
+        }
+      }
+      // ---- a4 processing order: the rank of (d2(p, x), id) among the m
+      // candidates is x's place in Algorithm 1's argmin sequence (stored order
+      // for the unsorted variant).  Rows, thresholds and masks below are all
+      // laid out by rank.
+      unsigned long long* sk = reinterpret_cast<unsigned long long*>(pb + L::p_sk);  // stored order
+      const unsigned long long my_sk = live_row ? (Acc<DT>::bits(kacc) << 32) | unsigned(my_id) : ~0ull;
+      sk[t] = my_sk;
+      named_sync(kBarProd, 128);
+      int rank = t;
+      if (a.variant == 0 && live_row) {
+        int cnt = 0;
+#pragma unroll 4
+        for (int j = 0; j < m; ++j) cnt += sk[j] < my_sk;
+        rank = cnt;
+      }
+      double my64 = __longlong_as_double(0x7ff8000000000000ll);
+      if constexpr (DT == kF32) {
+        // single-precision keys that might be out of order (intervals overlap):
+        // both ends of every such pair take their binary64 key, and those pairs
+        // are ordered by it (ties by id), as Algorithm 1 reads d2 in binary64
+        bool near = false;
+        if (a.variant == 0 && live_row) {
+          for (int j = 0; j < m && !near; ++j) {
+            const float kj = __uint_as_float(unsigned(sk[j] >> 32));
+            near = j != t && !sure_less(kj, kacc, E_rel, E_abs) && !sure_less(kacc, kj, E_rel, E_abs);
+          }
+        }
+        if (prod_sync_or(near)) {
+          double* k64s = reinterpret_cast<double*>(pb + L::p_k64);  // stored order
+          if (near) {
+            my64 = canon_d2_f32(reinterpret_cast<const float*>(prow), reinterpret_cast<const float*>(xrow), a.d);
+            atomicAdd(&a.status->fp64_sort_keys, 1ull);
+          }
+          k64s[t] = my64;
+          named_sync(kBarProd, 128);
+          if (near) {
+            int cnt = 0;
+            for (int j = 0; j < m; ++j) {
+              const float kj = __uint_as_float(unsigned(sk[j] >> 32));
+              if (sure_less(kj, kacc, E_rel, E_abs)) {
+                ++cnt;
+              } else if (j != t && !sure_less(kacc, kj, E_rel, E_abs)) {
+                const double dj = k64s[j];
+                const int32_t idj = int32_t(unsigned(sk[j]));
+                cnt += (dj < my64 || (dj == my64 && idj < my_id)) ? 1 : 0;
+              }
+            }
+            rank = cnt;
+          }
+        }
+      }
+      if (live_row) {
+        ids[rank] = my_id;
+        key[rank] = kacc;
+        norm[rank] = nacc;
+        if constexpr (DT == kF32) {
+          sn[rank] = sqrtf(nacc);
+          key64[rank] = my64;
+        }
+      }
+      // ---- bf16 operand row at position rank (rows past the degree stay zero);
+      // a5 Gram on tcgen05, one MMA chain per 128-dim slice
+      const int orow = g * MAXM + rank;
+      for (int sl = 0; sl < nslices; ++sl) {
+        const int64_t rem = elems - int64_t(sl) * 128;
+        const int kd = int(rem < 128 ? rem : 128);  // a multiple of 16 here
+        if constexpr (DT == kU8) {
+          if (nslices > 1) {
+#pragma unroll
+            for (int c = 0; c < 8; ++c) {
+              xs[c] = make_uint4(0, 0, 0, 0);
+              if (live_row && c < kd / 16) xs[c] = __ldg(reinterpret_cast<const uint4*>(xrow + sl * 128) + c);
+            }
+          }
+#pragma unroll
+          for (int c = 0; c < 8; ++c) {
             if (c >= kd / 16) break;
             const uint4 x = xs[c];
-            kacc = Acc<kU8>::step4(x, ys[c], kacc);
-            nacc = Acc<kU8>::dot4(x, x, nacc);
             const unsigned w4[4] = {x.x, x.y, x.z, x.w};
             uint32_t o[8];
 #pragma unroll
@@ -385,41 +431,28 @@ __global__ void __launch_bounds__(160) prune_tc_kernel(PruneArgs a) {
               o[2 * q + 1] = pack_bf16x2(float((w4[q] >> 16) & 0xff), float(w4[q] >> 24));
             }
             const int kc0 = 2 * c;
-            *reinterpret_cast<uint4*>(opnd + (kc0 * 16 + r / 8) * 128 + (r % 8) * 16) = make_uint4(o[0], o[1], o[2], o[3]);
-            *reinterpret_cast<uint4*>(opnd + ((kc0 + 1) * 16 + r / 8) * 128 + (r % 8) * 16) =
+            *reinterpret_cast<uint4*>(opnd + (kc0 * 16 + orow / 8) * 128 + (orow % 8) * 16) =
+                make_uint4(o[0], o[1], o[2], o[3]);
+            *reinterpret_cast<uint4*>(opnd + ((kc0 + 1) * 16 + orow / 8) * 128 + (orow % 8) * 16) =
                 make_uint4(o[4], o[5], o[6], o[7]);
           }
         } else {
 #pragma unroll 4
           for (int c = 0; c < kd / 8; ++c) {
-            float xv[8];
+            uint4 x0 = make_uint4(0, 0, 0, 0), x1 = make_uint4(0, 0, 0, 0);
             if (live_row) {
-              const uint4* xs = reinterpret_cast<const uint4*>(xrow + int64_t(sl) * 512) + 2 * c;
-              const uint4* ps = reinterpret_cast<const uint4*>(prow + int64_t(sl) * 512) + 2 * c;
-              const uint4 x0 = __ldg(xs), x1 = __ldg(xs + 1), y0 = __ldg(ps), y1 = __ldg(ps + 1);
-              kacc = Acc<kF32>::step4(x0, y0, kacc);
-              kacc = Acc<kF32>::step4(x1, y1, kacc);
-              xv[0] = __uint_as_float(x0.x); xv[1] = __uint_as_float(x0.y);
-              xv[2] = __uint_as_float(x0.z); xv[3] = __uint_as_float(x0.w);
-              xv[4] = __uint_as_float(x1.x); xv[5] = __uint_as_float(x1.y);
-              xv[6] = __uint_as_float(x1.z); xv[7] = __uint_as_float(x1.w);
-#pragma unroll
-              for (int q = 0; q < 8; ++q) nacc = fmaf(xv[q], xv[q], nacc);
-            } else {
-#pragma unroll
-              for (int q = 0; q < 8; ++q) xv[q] = 0.f;
+              const uint4* xq = reinterpret_cast<const uint4*>(xrow + int64_t(sl) * 512) + 2 * c;
+              x0 = __ldg(xq);
+              x1 = __ldg(xq + 1);
             }
-            *reinterpret_cast<uint4*>(opnd + (c * 16 + r / 8) * 128 + (r % 8) * 16) =
-                make_uint4(pack_bf16x2(xv[0], xv[1]), pack_bf16x2(xv[2], xv[3]), pack_bf16x2(xv[4], xv[5]),
-                           pack_bf16x2(xv[6], xv[7]));
+            *reinterpret_cast<uint4*>(opnd + (c * 16 + orow / 8) * 128 + (orow % 8) * 16) =
+                make_uint4(pack_bf16x2(__uint_as_float(x0.x), __uint_as_float(x0.y)),
+                           pack_bf16x2(__uint_as_float(x0.z), __uint_as_float(x0.w)),
+                           pack_bf16x2(__uint_as_float(x1.x), __uint_as_float(x1.y)),
+                           pack_bf16x2(__uint_as_float(x1.z), __uint_as_float(x1.w)));
           }
         }
         const bool last = sl == nslices - 1;
-        if (last && live_row) {
-          key[t] = kacc;
-          norm[t] = nacc;
-          if constexpr (DT == kF32) sn[t] = sqrtf(nacc);
-        }
         fence_async_smem();
         tc_fence_before();
         named_sync(kBarProd, 128);
@@ -433,7 +466,7 @@ __global__ void __launch_bounds__(160) prune_tc_kernel(PruneArgs a) {
           umma_commit(mbar);
         }
         if (last) {
-          // while the MMA runs: per-column thresholds of every target (a6), the next node
+          // while the MMA runs: the thresholds of column `rank` for every target (a6), the next node
           if (live_row) {
 #pragma unroll
             for (int u = 0; u < TB; ++u) {
@@ -444,11 +477,11 @@ __global__ void __launch_bounds__(160) prune_tc_kernel(PruneArgs a) {
                 //   <=>  2 G(u', v) - |u'|^2 >= |v|^2 - floor(1e6 d2(p, v) / A2)
                 // (every quantity an integer below 2^24, exact in f32)
                 const unsigned thr = exact_threshold(kacc, A2);
-                qlo[u * MAXM + t] = float(int(nacc) - int(thr));
+                qlo[u * MAXM + rank] = float(int(nacc) - int(thr));
               } else {
                 const float A2f = float(A2);
-                qlo[u * MAXM + t] = 1.0e6f * (kacc * (1.0f - E_rel) - E_abs) * 0.9999995f / A2f * 0.9999995f;
-                qhi[u * MAXM + t] = 1.0e6f * (kacc * (1.0f + E_rel) + E_abs) * 1.0000005f / A2f * 1.0000005f;
+                qlo[u * MAXM + rank] = 1.0e6f * (kacc * (1.0f - E_rel) - E_abs) * 0.9999995f / A2f * 0.9999995f;
+                qhi[u * MAXM + rank] = 1.0e6f * (kacc * (1.0f + E_rel) + E_abs) * 1.0000005f / A2f * 1.0000005f;
               }
             }
           }
@@ -463,8 +496,8 @@ __global__ void __launch_bounds__(160) prune_tc_kernel(PruneArgs a) {
         tc_fence_after();
       }
 
-      // ---- a6: each thread turns its candidate's Gram row (TMEM) into one
-      // mask per target of the candidates (stored positions) it would remove.
+      // ---- a6: thread t turns Gram row t (TMEM lane t: the candidate of rank
+      // t) into one mask per target of the ranks it would remove.
       // tcgen05.ld is warp-collective: every lane issues it, live rows use it.
       if (!dead) {
         unsigned long long mk[TB][MW];
@@ -569,81 +602,14 @@ __global__ void __launch_bounds__(160) prune_tc_kernel(PruneArgs a) {
       named_sync(kBarFull + s, 160);
       bool any = false;
 #pragma unroll
-      for (int q = 0; q < NG; ++q) any |= misc[s * 2 + q] >= 0;
-      if (!any) break;
-#pragma unroll 1
-      for (int g = 0; g < NG; ++g) {
-        const int p = misc[s * 2 + g];
-        if (p < 0) continue;
-        const int m = misc[4 + s * 2 + g];
-        unsigned char* sb = slot_base(s, g);
-        double* key64 = reinterpret_cast<double*>(sb + L::s_key64);
-        int32_t* ids = reinterpret_cast<int32_t*>(sb + L::s_ids);
-        AT* key = reinterpret_cast<AT*>(sb + L::s_key);
-        int32_t* perm = reinterpret_cast<int32_t*>(smem_raw + L::off_perm + size_t(g) * MAXM * 4);
-        // ---- a4 processing order: rank of each (key, id) among the m candidates
-        if (a.variant == 0) {
-          unsigned long long mkey[E];
-          int rank[E];
-#pragma unroll
-          for (int e = 0; e < E; ++e) {
-            const int j = lane + 32 * e;
-            mkey[e] = j < m ? (Acc<DT>::bits(key[j]) << 32) | unsigned(ids[j]) : ~0ull;
-            rank[e] = 0;
-          }
-#pragma unroll 4
-          for (int q = 0; q < m; ++q) {
-            const unsigned long long kq = (Acc<DT>::bits(key[q]) << 32) | unsigned(ids[q]);
-#pragma unroll
-            for (int e = 0; e < E; ++e) rank[e] += kq < mkey[e];
-          }
-#pragma unroll
-          for (int e = 0; e < E; ++e) {
-            const int j = lane + 32 * e;
-            if (j < m) perm[rank[e]] = j;
-          }
-          if constexpr (DT == kF32) {
-            // near-ties of single-precision keys: order them by the binary64 keys
-            __syncwarp();
-            bool link = false;
-#pragma unroll
-            for (int e = 0; e < E; ++e) {
-              const int i = lane + 32 * e;
-              if (i + 1 < m && !sure_less(key[perm[i]], key[perm[i + 1]], E_rel, E_abs)) link = true;
-            }
-            if (__any_sync(0xffffffffu, link) && lane == 0) {
-              const float* X = reinterpret_cast<const float*>(a.X);
-              const int64_t stride = a.row_bytes / 4;
-              int i = 0;
-              while (i < m) {
-                int end = i;
-                while (end + 1 < m && !sure_less(key[perm[end]], key[perm[end + 1]], E_rel, E_abs)) ++end;
-                if (end > i) {
-                  for (int q = i; q <= end; ++q)
-                    key64[perm[q]] = canon_d2_f32(X + int64_t(p) * stride, X + int64_t(ids[perm[q]]) * stride, a.d);
-                  atomicAdd(&a.status->fp64_sort_keys, static_cast<unsigned long long>(end - i + 1));
-                  for (int q = i + 1; q <= end; ++q) {
-                    const int v = perm[q];
-                    int z = q - 1;
-                    while (z >= i && (key64[perm[z]] > key64[v] || (key64[perm[z]] == key64[v] && ids[perm[z]] > ids[v]))) {
-                      perm[z + 1] = perm[z];
-                      --z;
-                    }
-                    perm[z + 1] = v;
-                  }
-                }
-                i = end + 1;
-              }
-            }
-          }
-        } else {
-#pragma unroll
-          for (int e = 0; e < E; ++e) perm[lane + 32 * e] = lane + 32 * e;
-        }
-        __syncwarp();
-        ++done;
+      for (int q = 0; q < NG; ++q) {
+        any |= misc[s * 2 + q] >= 0;
+        done += misc[s * 2 + q] >= 0;
       }
-      // ---- a7 greedy scan: lane (g * 16 + u) walks node g's processing order for target u
+      if (!any) break;
+      // ---- a7 greedy scan: lane (g * 16 + u) runs Algorithm 1's loop for node
+      // g and target u.  Candidates are laid out by rank, so the next argmin of
+      // the live set is its lowest set bit.
       {
         const int g = NG == 2 ? lane >> 4 : 0;
         const int u = NG == 2 ? (lane & 15) : lane;
@@ -654,7 +620,6 @@ __global__ void __launch_bounds__(160) prune_tc_kernel(PruneArgs a) {
           unsigned char* sb = slot_base(s, g);
           const unsigned long long* masks = reinterpret_cast<const unsigned long long*>(sb + L::s_masks);
           const int32_t* ids = reinterpret_cast<const int32_t*>(sb + L::s_ids);
-          const int32_t* perm = reinterpret_cast<const int32_t*>(smem_raw + L::off_perm + size_t(g) * MAXM * 4);
           unsigned long long al[MW];
 #pragma unroll
           for (int w = 0; w < MW; ++w) {
@@ -664,20 +629,16 @@ __global__ void __launch_bounds__(160) prune_tc_kernel(PruneArgs a) {
           const int R = a.R[u];
           int32_t* out = a.out_col[u] + e0;
           int kept = 0;
-          for (int i = 0; i < m; ++i) {
-            const int pos = perm[i];
-            const int w = pos >> 6;
-            const unsigned long long bit = 1ull << (pos & 63);
-            if (!(al[w] & bit)) continue;
-            out[kept++] = ids[pos];
-            if (kept == R) break;
-            bool left = false;
+          while (kept < R) {
+            int pos = -1;
 #pragma unroll
-            for (int q = 0; q < MW; ++q) {
-              al[q] &= ~masks[(u * MAXM + pos) * MW + q];
-              left |= al[q] != 0;
-            }
-            if (!left) break;
+            for (int w = MW - 1; w >= 0; --w)
+              if (al[w]) pos = 64 * w + __ffsll(static_cast<long long>(al[w])) - 1;
+            if (pos < 0) break;
+            out[kept++] = ids[pos];
+            al[pos >> 6] &= ~(1ull << (pos & 63));  // taken (its own mask bit is set too)
+#pragma unroll
+            for (int q = 0; q < MW; ++q) al[q] &= ~masks[(u * MAXM + pos) * MW + q];
           }
           a.out_cnt[u][p] = kept;
         }
