@@ -46,6 +46,7 @@ struct PruneArgs {
   int variant;
   int32_t A[kMaxTargets];
   int32_t R[kMaxTargets];
+  float inv_A2[kMaxTargets];  // 1 / A^2 rounded: a starting estimate for exact_threshold
   int32_t* out_col[kMaxTargets];
   int32_t* out_cnt[kMaxTargets];
   DevStatus* status;
@@ -169,22 +170,27 @@ struct TcLayout {
   static constexpr size_t p_k64 = p_sk + size_t(MAXM) * 8;       // [MAXM] binary64 keys in stored order
   static constexpr size_t p_bytes = p_k64 + size_t(MAXM) * 8;
   static constexpr size_t off_prod = off_slots + 2 * NG * s_bytes;
-  // small words: node/degree/row start per (slot, group) and the next claim, mbarrier, TMEM address
+  // small words: node/degree/row start per (slot, group), the claim queue's
+  // head, mbarrier, TMEM address; then the claim queue (node, degree, row start)
   static constexpr size_t off_misc = off_prod + NG * p_bytes;
-  static constexpr size_t misc_bytes = 256;
+  static constexpr size_t q_node = 256, q_deg = q_node + 32 * 4, q_e0 = q_deg + 32 * 4;
+  static constexpr size_t misc_bytes = q_e0 + 32 * 8;
   static constexpr size_t bytes = (off_misc + misc_bytes + 127) & ~size_t(127);
 };
 
-// floor(1e6 k / A2) for integers, exactly: a single-precision estimate
-// corrected with 64-bit products.
-__device__ __forceinline__ unsigned exact_threshold(unsigned k, unsigned long long A2) {
+// floor(1e6 k / A2) for integers, exactly: a single-precision estimate (off
+// by a few units at most) corrected with 64-bit products.
+__device__ __forceinline__ unsigned exact_threshold(unsigned k, unsigned long long A2, float inv_A2) {
   const unsigned long long num = 1000000ull * k;
-  long long q = static_cast<long long>(floorf(__fdiv_rn(1.0e6f * float(k), float(A2))));
+  long long q = static_cast<long long>(floorf(1.0e6f * float(k) * inv_A2));
   if (q < 0) q = 0;
   while (static_cast<unsigned long long>(q) * A2 > num) --q;
   while (static_cast<unsigned long long>(q + 1) * A2 <= num) ++q;
   return static_cast<unsigned>(q);
 }
+
+// Nodes claimed at a time by a prune_tc_kernel CTA (one per lane of warp 0).
+constexpr int kClaim = 32;
 
 // Named barriers of prune_tc_kernel (0 is __syncthreads, unused in the loop).
 constexpr int kBarProd = 1;       // the 128 producer threads
@@ -213,8 +219,14 @@ __device__ __forceinline__ bool prod_sync_or(bool flag) {
 // domination mask per target for every rank.  They hand ids and masks over
 // through one of two slots; the consumer warp runs the greedy loop per node and
 // target (a7) while the producers already work on the next nodes.
+// 4 CTAs per SM (the TMEM limit) need at most 96 registers per thread; the
+// kernels with more targets per launch, or one 128-candidate node per MMA
+// (more shared memory per CTA), trade that for registers.
+template <int MAXM, int TB>
+constexpr int tc_min_ctas() { return (MAXM == 64 && TB <= 4) ? 4 : 2; }
+
 template <int DT, int MAXM, int TB>
-__global__ void __launch_bounds__(160) prune_tc_kernel(PruneArgs a) {
+__global__ void __launch_bounds__(160, tc_min_ctas<MAXM, TB>()) prune_tc_kernel(PruneArgs a) {
   using L = TcLayout<MAXM, TB>;
   using AT = typename Acc<DT>::T;
   constexpr int NG = L::NG;
@@ -226,8 +238,11 @@ __global__ void __launch_bounds__(160) prune_tc_kernel(PruneArgs a) {
   const int lane = r & 31;
   unsigned char* opnd = smem_raw + L::off_opnd;
   int* misc = reinterpret_cast<int*>(smem_raw + L::off_misc);
-  // misc ints: [0..3] slot node (s*2+g), [4..7] slot degree, [8..9] next node, [10..11] next degree
-  int64_t* misc64 = reinterpret_cast<int64_t*>(smem_raw + L::off_misc + 64);  // [0..3] slot row start, [4..5] next
+  // misc ints: [0..3] slot node (s*2+g), [4..7] slot degree, [12] claim queue head
+  int64_t* misc64 = reinterpret_cast<int64_t*>(smem_raw + L::off_misc + 64);  // [0..3] slot row start
+  int* qnode = reinterpret_cast<int*>(smem_raw + L::off_misc + L::q_node);
+  int* qdeg = reinterpret_cast<int*>(smem_raw + L::off_misc + L::q_deg);
+  int64_t* qe0 = reinterpret_cast<int64_t*>(smem_raw + L::off_misc + L::q_e0);
   uint64_t* mbar = reinterpret_cast<uint64_t*>(smem_raw + L::off_misc + 128);
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem_raw + L::off_misc + 144);
   auto slot_base = [&](int s, int g) { return smem_raw + L::off_slots + (size_t(s) * NG + g) * L::s_bytes; };
@@ -235,7 +250,10 @@ __global__ void __launch_bounds__(160) prune_tc_kernel(PruneArgs a) {
   const int count = *a.count;
 
   if (warp == 0) tmem_alloc(tmem_slot, 128);  // 128 of the SM's 512 TMEM columns, for the kernel's life
-  if (r == 0) mbar_init(mbar, 1);
+  if (r == 0) {
+    mbar_init(mbar, 1);
+    misc[12] = kClaim;  // empty claim queue
+  }
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
@@ -250,40 +268,51 @@ __global__ void __launch_bounds__(160) prune_tc_kernel(PruneArgs a) {
     float* qlo = reinterpret_cast<float*>(pb + L::p_qlo);
     float* qhi = reinterpret_cast<float*>(pb + L::p_qhi);
     const uint32_t tmem = *tmem_slot;
-    constexpr uint32_t idesc = umma_idesc_bf16(128, 128);
+    // uint8 operands go in as f16 (exact for 0..255 and cheaper to convert), float ones as bf16
+    constexpr uint32_t idesc = DT == kU8 ? umma_idesc_f16(128, 128) : umma_idesc_bf16(128, 128);
     const int64_t elems = a.row_bytes / (DT == kU8 ? 1 : 4);  // padded dims per row
     const int nslices = int((elems + 127) / 128);
     const float eps_ip = 0.0078125f + 1.52587890625e-05f + float(a.d) * 2.384185791015625e-07f;
     const float eps_n = float(a.d + 12) * 5.9604645e-08f;
     const float err_abs = float(a.d) * 2.3509887e-38f;  // underflowed products, 2^-125 each
-    auto claim = [&]() {  // next node of the bucket list for group g, with its row bounds
-      const unsigned idx = atomicAdd(a.work, 1u);
-      const int p = idx < unsigned(count) ? a.nodes[idx] : -1;
-      int deg = 0;
-      int64_t e0 = 0;
-      if (p >= 0) {
-        e0 = a.row_ptr[p];
-        deg = int(a.row_ptr[p + 1] - e0);
-      }
-      if (deg > MAXM) {  // bucketing never sends such a node here; skip it, report it
-        raise_status(a.status, kDevBadDegree, p);
-        deg = 0;
-      }
-      misc[8 + g] = p;
-      misc[10 + g] = deg;
-      misc64[4 + g] = e0;
-    };
-    if (t == 0) claim();
-    named_sync(kBarProd, 128);
     uint32_t phase = 0;
     bool dead = false;
     for (int k = 0;; ++k) {
       const int s = k & 1;
       named_sync(kBarFree + s, 160);  // the consumer is done with this slot
-      if (t == 0) {
-        misc[s * 2 + g] = dead ? -1 : misc[8 + g];
-        misc[4 + s * 2 + g] = dead ? 0 : misc[10 + g];
-        misc64[s * 2 + g] = misc64[4 + g];
+      if (warp == 0) {
+        // next NG nodes from the claim queue; warp 0 refills it kClaim nodes at
+        // a time (one atomic, the row bounds loaded by all lanes at once)
+        int head = misc[12];
+        if (head >= kClaim) {
+          unsigned base = 0;
+          if (lane == 0) base = atomicAdd(a.work, unsigned(kClaim));
+          base = __shfl_sync(0xffffffffu, base, 0);
+          const unsigned idx = base + unsigned(lane);
+          const int pn = idx < unsigned(count) ? a.nodes[idx] : -1;
+          int deg = 0;
+          int64_t e0n = 0;
+          if (pn >= 0) {
+            e0n = a.row_ptr[pn];
+            deg = int(a.row_ptr[pn + 1] - e0n);
+          }
+          if (deg > MAXM) {  // bucketing never sends such a node here; skip it, report it
+            raise_status(a.status, kDevBadDegree, pn);
+            deg = 0;
+          }
+          qnode[lane] = pn;
+          qdeg[lane] = deg;
+          qe0[lane] = e0n;
+          __syncwarp();
+          head = 0;
+        }
+        if (lane < NG) {
+          misc[s * 2 + lane] = dead ? -1 : qnode[head + lane];
+          misc[4 + s * 2 + lane] = dead ? 0 : qdeg[head + lane];
+          misc64[s * 2 + lane] = qe0[head + lane];
+        }
+        __syncwarp();
+        if (lane == 0) misc[12] = head + NG;
       }
       named_sync(kBarProd, 128);
       bool any = false;
@@ -355,9 +384,14 @@ __global__ void __launch_bounds__(160) prune_tc_kernel(PruneArgs a) {
       named_sync(kBarProd, 128);
       int rank = t;
       if (a.variant == 0 && live_row) {
+        // entries past the degree hold ~0 and never count
+        const ulonglong2* sk2 = reinterpret_cast<const ulonglong2*>(sk);
         int cnt = 0;
 #pragma unroll 4
-        for (int j = 0; j < m; ++j) cnt += sk[j] < my_sk;
+        for (int j2 = 0; j2 < (m + 1) / 2; ++j2) {
+          const ulonglong2 v = sk2[j2];
+          cnt += int(v.x < my_sk) + int(v.y < my_sk);
+        }
         rank = cnt;
       }
       double my64 = __longlong_as_double(0x7ff8000000000000ll);
@@ -427,8 +461,8 @@ __global__ void __launch_bounds__(160) prune_tc_kernel(PruneArgs a) {
             uint32_t o[8];
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
-              o[2 * q] = pack_bf16x2(float(w4[q] & 0xff), float((w4[q] >> 8) & 0xff));
-              o[2 * q + 1] = pack_bf16x2(float((w4[q] >> 16) & 0xff), float(w4[q] >> 24));
+              o[2 * q] = u8x2_f16x2(w4[q], 0x4140u);      // bytes 0, 1
+              o[2 * q + 1] = u8x2_f16x2(w4[q], 0x4342u);  // bytes 2, 3
             }
             const int kc0 = 2 * c;
             *reinterpret_cast<uint4*>(opnd + (kc0 * 16 + orow / 8) * 128 + (orow % 8) * 16) =
@@ -466,7 +500,7 @@ __global__ void __launch_bounds__(160) prune_tc_kernel(PruneArgs a) {
           umma_commit(mbar);
         }
         if (last) {
-          // while the MMA runs: the thresholds of column `rank` for every target (a6), the next node
+          // while the MMA runs: the thresholds of column `rank` for every target (a6)
           if (live_row) {
 #pragma unroll
             for (int u = 0; u < TB; ++u) {
@@ -476,7 +510,7 @@ __global__ void __launch_bounds__(160) prune_tc_kernel(PruneArgs a) {
                 // v is removed by row u'  <=>  A2 d2(u', v) <= 1e6 d2(p, v)
                 //   <=>  2 G(u', v) - |u'|^2 >= |v|^2 - floor(1e6 d2(p, v) / A2)
                 // (every quantity an integer below 2^24, exact in f32)
-                const unsigned thr = exact_threshold(kacc, A2);
+                const unsigned thr = exact_threshold(kacc, A2, a.inv_A2[u]);
                 qlo[u * MAXM + rank] = float(int(nacc) - int(thr));
               } else {
                 const float A2f = float(A2);
@@ -485,7 +519,6 @@ __global__ void __launch_bounds__(160) prune_tc_kernel(PruneArgs a) {
               }
             }
           }
-          if (t == 0 && p >= 0) claim();
         }
         const bool ok = mbar_wait(mbar, phase, 1 << 24);
         if (prod_sync_or(!ok)) {  // the MMA never completed: report, stop after this slot (uniform)
@@ -1085,6 +1118,7 @@ cudaError_t launch_prune(const PruneLaunch& L, cudaStream_t s) {
   for (int t = 0; t < L.T; ++t) {
     a.A[t] = L.A[t];
     a.R[t] = L.R[t];
+    a.inv_A2[t] = float(1.0 / (double(L.A[t]) * double(L.A[t])));
     a.out_col[t] = L.out_col[t];
     a.out_cnt[t] = L.out_cnt[t];
   }
