@@ -21,6 +21,10 @@ jobs and query batches through the library's scheduler (rp_server_*), the
 continuous-batching scheduler against the plain serial path, at offered loads
 relative to the serial path's capacity; p50/p99 latency, QPS and recall@100.
 
+`--workload gist` runs the batched float sweep instead (1,000,000 x 960
+float32 rows, |N(0,1)| * 0.05 then L2-normalised; nine targets: alpha 1.175 down
+to 1.0 at R=64 plus (1.0, 32), in one launch; 1,000 queries, L=200, k=100).
+
 `--impl reference` times the CPU oracle (the reference arm of this build) on
 a bounded sample of the same workload and prints the same JSON line.
 """
@@ -45,16 +49,30 @@ import datagen  # noqa: E402
 
 METRIC = "RP-Tuning nodes/s per α (batched vs plain, same GPU); query p50/p99 at recall@100"
 UNIT = "nodes/s per alpha"
-TARGETS = [(1.1, 64), (1.05, 48), (1.0, 32)]
 BASE_ALPHA, BASE_R, KCAND = 1.2, 64, 128
-L_SEARCH, K_SEARCH = 128, 100
+K_SEARCH = 100
 SERVE_BUDGET_GB = 8                     # resident tuned graphs of the serving leg (~30 at this size)
 SERVE_LOADS = (0.5, 0.8, 1.0, 2.0, 4.0)  # offered load / capacity of the serial path
 
+# The paper-shaped workloads (synthetic; recipes in datagen).  sift is the
+# default bench line; gist is the batched float sweep (9 targets: alpha 1.175
+# down to 1.0 in steps of 0.025 at R=64, plus (1.0, 32)).
+WORKLOADS = {
+    "sift": dict(dtype="u8", n=1_000_000, d=128, nq=10_000, L=128,
+                 targets=[(1.1, 64), (1.05, 48), (1.0, 32)]),
+    "gist": dict(dtype="f32", n=1_000_000, d=960, nq=1_000, L=200,
+                 targets=[(round(1.175 - 0.025 * i, 3), 64) for i in range(8)] + [(1.0, 32)]),
+}
+TARGETS = WORKLOADS["sift"]["targets"]
+L_SEARCH = WORKLOADS["sift"]["L"]
 
-def workload_name(n, nq):
-    return (f"sift-shaped uint8 n={n:,} d=128; base RobustPrune(1.2,64) over exact kNN-128; "
-            f"tune (1.1,64),(1.05,48),(1.0,32); {nq:,} queries L=128 k=100")
+
+def workload_name(n, nq, name="sift"):
+    w = WORKLOADS[name]
+    shape = {"sift": "sift-shaped uint8", "gist": "gist-shaped float32"}[name]
+    tl = ",".join(f"({a:g},{r})" for a, r in w["targets"])
+    return (f"{shape} n={n:,} d={w['d']}; base RobustPrune(1.2,64) over exact kNN-128; "
+            f"tune {tl}; {nq:,} queries L={w['L']} k=100")
 
 
 def dist_env():
@@ -131,39 +149,41 @@ class ClockSampler:
 
 # ---------------------------------------------------------------- reference arm / CPU baseline
 
-def oracle_sample(n_sample, rank_seed=0):
+def oracle_sample(n_sample, name="sift"):
     """The oracle's own base rows over a prefix of the same dataset (no GPU input)."""
     import oracle
-    X = datagen.dataset("sift", n_sample)
+    X = datagen.dataset(name, n_sample)
     t0 = time.perf_counter()
     base_rp, base_col = oracle.knn_base(X, KCAND, BASE_ALPHA, BASE_R)
     return X, base_rp, base_col, time.perf_counter() - t0
 
 
-def time_oracle_tune(X, base_rp, base_col):
+def time_oracle_tune(X, base_rp, base_col, targets=None):
     import oracle
     t0 = time.perf_counter()
-    for a, r in TARGETS:
+    for a, r in (targets or TARGETS):
         oracle.rp_tune(X, base_rp, base_col, a, r)
     return time.perf_counter() - t0
 
 
-def cpu_baseline(n_sample=20000):
+def cpu_baseline(n_sample=20000, name="sift"):
     import oracle
-    X, brp, bcol, build_s = oracle_sample(n_sample)
+    w = WORKLOADS[name]
+    X, brp, bcol, build_s = oracle_sample(n_sample, name)
     secs, reps = 0.0, 0
     while secs < 10.0 or reps < 1:  # about ten seconds of CPU work
-        secs += time_oracle_tune(X, brp, bcol)
+        secs += time_oracle_tune(X, brp, bcol, w["targets"])
         reps += 1
-    Q = datagen.queries("sift", 200)
+    Q = datagen.queries(name, 200)
     start = oracle.medoid(X)
     t0 = time.perf_counter()
-    oracle.greedy_search(X, brp, bcol, start, Q, L_SEARCH, K_SEARCH)
+    oracle.greedy_search(X, brp, bcol, start, Q, w["L"], K_SEARCH)
     qs = time.perf_counter() - t0
-    return {"value": reps * n_sample * len(TARGETS) / secs, "unit": UNIT, "cores": oracle.num_threads(0),
+    T = len(w["targets"])
+    return {"value": reps * n_sample * T / secs, "unit": UNIT, "cores": oracle.num_threads(0),
             "kind": "oracle",
             "sample": (f"oracle RP-Tuning of all {n_sample:,} nodes of a {n_sample:,}-point prefix of the same "
-                       f"dataset (its own kNN-128 -> RobustPrune(1.2,64) base), 3 targets, repeated {reps}x "
+                       f"dataset (its own kNN-128 -> RobustPrune(1.2,64) base), {T} targets, repeated {reps}x "
                        f"({secs:.1f} s); GreedySearch of 200 queries {200 / qs:.1f} QPS"),
             "search_qps": 200 / qs}
 
@@ -174,19 +194,21 @@ def run_reference(args):
         return 0
     import oracle
     n_sample = args.ref_sample
-    X, brp, bcol, _ = oracle_sample(n_sample)
+    w = WORKLOADS[args.workload]
+    X, brp, bcol, _ = oracle_sample(n_sample, args.workload)
     for _ in range(args.warmup):
-        time_oracle_tune(X, brp, bcol)
-    times = [time_oracle_tune(X, brp, bcol) for _ in range(args.steps)]
+        time_oracle_tune(X, brp, bcol, w["targets"])
+    times = [time_oracle_tune(X, brp, bcol, w["targets"]) for _ in range(args.steps)]
     tot = sum(times)
-    value = n_sample * len(TARGETS) * args.steps / tot
+    value = n_sample * len(w["targets"]) * args.steps / tot
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * tot / args.steps,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u8",
-            "data": "synthetic", "config": {"workload": workload_name(args.n, args.nq),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": w["dtype"],
+            "data": "synthetic", "config": {"workload": workload_name(args.n, args.nq, args.workload),
                                             "reference_sample_nodes": n_sample},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": oracle.num_threads(0), "kind": "oracle",
-                             "sample": f"RP-Tuning of a {n_sample:,}-point prefix (its own base), 3 targets per step"},
+                             "sample": (f"RP-Tuning of a {n_sample:,}-point prefix (its own base), "
+                                        f"{len(w['targets'])} targets per step")},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
@@ -206,14 +228,18 @@ def run_ours(args):
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     b.build()
+    W = WORKLOADS[args.workload]
+    TARGETS_W = W["targets"]
+    L_W = W["L"]
     n, nq, k = args.n, args.nq, K_SEARCH
-    X = datagen.dataset("sift", n)
-    Q = datagen.queries("sift", nq)
+    X = datagen.dataset(args.workload, n)
+    Q = datagen.queries(args.workload, nq)
+    row_bytes = X.shape[1] * X.itemsize
     stream = torch.cuda.Stream(device=dev)
     ctx = rp.rp_create(local, stream=stream)
-    alphas = [a for a, _ in TARGETS]
-    Rs = [r for _, r in TARGETS]
-    T = len(TARGETS)
+    alphas = [a for a, _ in TARGETS_W]
+    Rs = [r for _, r in TARGETS_W]
+    T = len(TARGETS_W)
 
     # ---- fixture (not timed): vectors, base graph, ground truth
     t0 = time.perf_counter()
@@ -239,7 +265,7 @@ def run_ours(args):
             stats_acc["emit_ms"].append(st["last_emit_ms"])
         sms = 0.0
         for i, g in enumerate(outs):
-            rp.rp_search(ctx, g, Qd, L_SEARCH, k, ids=ids_d[i], dists=dist_d[i])
+            rp.rp_search(ctx, g, Qd, L_W, k, ids=ids_d[i], dists=dist_d[i])
             if record:
                 sms += rp.rp_stats(ctx)["last_search_ms"]
         if record:
@@ -294,17 +320,18 @@ def run_ours(args):
             flush.zero_()
         outs, _ = step(True)
         free(outs)
+    tuned_cfg = rp.rp_stats(ctx)  # the autotuner's pick for this source and target count
     prune_ms = statistics.mean(stats_acc["prune_ms"])
     if not prune_ms > 0:
         raise RuntimeError(f"prune kernel time not measured: {stats_acc}")
     emit_ms = statistics.mean(stats_acc["emit_ms"])
     search_ms = statistics.mean(stats_acc["search_ms"])
-    alg_bytes = float(((deg + 1) * 128 + 4 * deg + 8).sum() + 4 * sum(nnz))
+    alg_bytes = float(((deg + 1) * row_bytes + 4 * deg + 8).sum() + 4 * sum(nnz))
     hbm_peak, peak_kind = load_peaks()
     achieved = alg_bytes / (prune_ms / 1000.0) / 1e9
     traffic = None  # DRAM bytes per launch from the committed ncu summary, if it is of this kernel source
     prof = os.path.join(ROOT, "profiles", "prune_tc_u8_sift1m.md")
-    if os.path.exists(prof) and n == 1_000_000:
+    if os.path.exists(prof) and n == 1_000_000 and args.workload == "sift":
         fields = {}
         with open(prof) as f:
             for ln in f:
@@ -326,7 +353,7 @@ def run_ours(args):
             if batched:
                 outs = rp.rp_tune_batch(ctx, base, alphas, Rs)
             else:
-                outs = [rp.rp_tune(ctx, base, a, R) for a, R in TARGETS]
+                outs = [rp.rp_tune(ctx, base, a, R) for a, R in TARGETS_W]
             a1.record(stream)
             stream.synchronize()
             if r >= 2:
@@ -348,7 +375,7 @@ def run_ours(args):
         a0 = torch.cuda.Event(enable_timing=True)
         a1 = torch.cuda.Event(enable_timing=True)
         a0.record(stream)
-        rp.rp_search(ctx, g1, q, L_SEARCH, k, ids=i1, dists=d1)
+        rp.rp_search(ctx, g1, q, L_W, k, ids=i1, dists=d1)
         a1.record(stream)
         stream.synchronize()
         if i >= 20:
@@ -380,7 +407,7 @@ def run_ours(args):
             d2h = 0
             hits = []
             for i, t in enumerate(outs):
-                rp.rp_search(ctx, t, Qh, L_SEARCH, k, ids=idh[i], dists=dh[i])
+                rp.rp_search(ctx, t, Qh, L_W, k, ids=idh[i], dists=dh[i])
                 h2d += Q.nbytes
                 d2h += idh[i].numel() * 4 + dh[i].numel() * 4
                 hits.append(rp.rp_recall(ctx, idh[i], gth, k))
@@ -410,23 +437,24 @@ def run_ours(args):
                "d2h_bytes_per_step": int(d2h), "ms_per_step": 1000 * e2e_s}
 
     serving = None
-    if not args.quick and not args.no_serve:
+    if not args.quick and not args.no_serve and args.workload == "sift":
         serving = serve_bench(rp, ctx, base, Q, gt, args)
 
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline and not args.quick:
-        cpu = cpu_baseline(args.cpu_sample)
+        cpu = cpu_baseline(args.cpu_sample, args.workload)
 
     rp.rp_destroy(ctx)
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": tot_ms / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "u8", "data": "synthetic",
-            "config": {"workload": workload_name(n, nq), "n": n, "d": 128, "targets": TARGETS,
-                       "queries": nq, "L": L_SEARCH, "k": k, "l2": "flushed (512 MB write) before every timed step",
+            "scaling": "weak", "vs_baseline": None, "dtype": W["dtype"], "data": "synthetic",
+            "config": {"workload": workload_name(n, nq, args.workload), "n": n, "d": W["d"], "targets": TARGETS_W,
+                       "queries": nq, "L": L_W, "k": k, "l2": "flushed (512 MB write) before every timed step",
                        "parallelism": f"replicas x{ws}" if ws > 1 else "1 GPU"},
-            "roofline": {"bound": "hbm", "kernel": "prune_tc_kernel<u8,64> (tcgen05 Gram)", "achieved": achieved,
+            "roofline": {"bound": "hbm", "kernel": f"prune_tc_kernel<{W['dtype']},64> (tcgen05 Gram)",
+                         "achieved": achieved,
                          "peak": hbm_peak, "unit": "GB/s", "frac": achieved / hbm_peak, "traffic": traffic,
                          "peak_kind": peak_kind, "algorithmic_bytes_per_launch": alg_bytes,
                          "launch_ms": prune_ms},
@@ -437,11 +465,13 @@ def run_ours(args):
             "tune_batched_nodes_per_s_per_alpha": n * T / (tb / 1000.0),
             "tune_plain_nodes_per_s_per_alpha": n * T / (tp / 1000.0),
             "batched_over_plain": tp / tb,
-            "phase_ms": {"prune": prune_ms, "emit": emit_ms, "search_3x": search_ms},
-            "search_qps": 3 * nq / (search_ms / 1000.0),
+            "phase_ms": {"prune": prune_ms, "emit": emit_ms, f"search_{T}x": search_ms},
+            "prune_config": {"tile0": tuned_cfg["tile0"], "ctas_per_sm": tuned_cfg["ctas_per_sm"],
+                             "chosen_by": "autotuner (rp_set_tuning RP_TUNING_AUTO)"},
+            "search_qps": T * nq / (search_ms / 1000.0),
             "query_latency_ms_bs1": {"p50": p50, "p99": p99},
-            "recall_at_100": dict(zip([f"{a},{r}" for a, r in TARGETS], recalls)),
-            "avg_degree": {"base": float(deg.mean()), **{f"{a},{r}": nz / n for (a, r), nz in zip(TARGETS, nnz)}},
+            "recall_at_100": dict(zip([f"{a},{r}" for a, r in TARGETS_W], recalls)),
+            "avg_degree": {"base": float(deg.mean()), **{f"{a},{r}": nz / n for (a, r), nz in zip(TARGETS_W, nnz)}},
             "fixture_s": fixture_s,
             "serving": serving,
         }
@@ -511,8 +541,9 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--n", type=int, default=1_000_000)
-    ap.add_argument("--nq", type=int, default=10_000)
+    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="sift")
+    ap.add_argument("--n", type=int, default=None)
+    ap.add_argument("--nq", type=int, default=None)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-serve", action="store_true")
@@ -522,6 +553,10 @@ def main():
     ap.add_argument("--quick", action="store_true",
                     help="timed steps and the per-kernel pass only (for profiler runs)")
     args = ap.parse_args()
+    if args.n is None:
+        args.n = WORKLOADS[args.workload]["n"]
+    if args.nq is None:
+        args.nq = WORKLOADS[args.workload]["nq"]
     if args.warmup < 3 and args.impl == "ours":
         print("note: timing rules ask for >= 3 warm-up steps", file=sys.stderr)
     if args.impl == "reference":

@@ -271,6 +271,17 @@ rp_status rp_build_knn_base(rp_ctx *ctx, rp_graph data, int32_t kcand, double al
                             rp_graph *out);
 
 /*
+ * rp_graph_slice: the part of graph g that one of several GPUs tunes when the
+ * nodes are split by contiguous id ranges (RP-Tuning treats every node on its
+ * own, §3).  *out keeps the rows of nodes lo .. hi-1 with their edges, in
+ * order, and has no edges elsewhere; it shares g's vectors and start vertex.
+ * Tuning it gives exactly the rows of lo .. hi-1 of tuning g, and empty rows
+ * elsewhere.  Errors: RP_ENOTFOUND, RP_EINVAL (not 0 <= lo <= hi <= n),
+ * RP_ENOMEM, RP_ECUDA.
+ */
+rp_status rp_graph_slice(rp_ctx *ctx, rp_graph g, int64_t lo, int64_t hi, rp_graph *out);
+
+/*
  * rp_graph_shape: the vectors behind graph g (d and dtype) and the device
  * bytes of g's own adjacency (row_ptr and col capacity, vectors excluded).  A
  * graph tuned from g holds the same number of adjacency bytes.  Any output
@@ -298,9 +309,28 @@ typedef struct {
   float last_prune_ms;         /* device time of the prune kernels of the last tuning call */
   float last_emit_ms;          /* device time of its CSR emit (scan + compaction) */
   float last_search_ms;        /* device time of the last rp_search kernel */
+  int32_t tile0;               /* prune configuration of the last tuning call (rp_set_tuning) */
+  int32_t ctas_per_sm;
 } rp_stats_t;
 
 rp_status rp_stats(rp_ctx *ctx, rp_stats_t *out, int32_t reset);
+
+/*
+ * rp_set_tuning: how the tensor-core prune kernels are configured.  The
+ * paper fixes no kernel shape; these are this library's choices.
+ *   tile0: 0 = two nodes of degree <= 64 share one 128-row Gram MMA,
+ *          1 = one node per MMA (the shape of the 65..128 degree bucket).
+ *   ctas_per_sm: CTAs per SM of those kernels, 0 = as many as fit (<= 4).
+ * RP_TUNING_AUTO (the default): the first tuning call from a source graph
+ * with at least 65,536 nodes of degree <= 64 times every (tile0, ctas_per_sm)
+ * in {0, 1} x {all, 3, 2} on a 32,768-node sample and keeps the fastest for
+ * that source, target-count class (1, 2, 4, 8, 16) and variant; smaller
+ * sources use tile0 = 0 with all CTAs.  RP_TUNING_FIXED uses the given pair.
+ * Results never depend on the configuration.  rp_stats reports the one used
+ * by the last tuning call.  Errors: RP_EINVAL.
+ */
+enum { RP_TUNING_AUTO = 0, RP_TUNING_FIXED = 1 };
+rp_status rp_set_tuning(rp_ctx *ctx, int32_t mode, int32_t tile0, int32_t ctas_per_sm);
 
 /* ------------------------------------------------------------------------
  * Serving: a scheduler thread over one resident base graph that takes

@@ -23,6 +23,7 @@ RP_MEM_HOST, RP_MEM_DEVICE = 0, 1
 RP_R_INF = 2**31 - 1
 RP_MAX_DEGREE = 8192
 RP_MAX_L = 1024
+RP_TUNING_AUTO, RP_TUNING_FIXED = 0, 1
 
 _NAMES = {RP_EINVAL: "RP_EINVAL", RP_ENOMEM: "RP_ENOMEM", RP_ECUDA: "RP_ECUDA", RP_ETIMEOUT: "RP_ETIMEOUT",
           RP_ENOTFOUND: "RP_ENOTFOUND", RP_EDEVICE: "RP_EDEVICE"}
@@ -41,7 +42,8 @@ class rp_stats_t(ctypes.Structure):
                 ("generic_nodes", ctypes.c_int64), ("graph_replays", ctypes.c_int64),
                 ("bytes_in_use", ctypes.c_uint64), ("bytes_peak", ctypes.c_uint64),
                 ("kernel_launches", ctypes.c_int64), ("last_prune_ms", ctypes.c_float),
-                ("last_emit_ms", ctypes.c_float), ("last_search_ms", ctypes.c_float)]
+                ("last_emit_ms", ctypes.c_float), ("last_search_ms", ctypes.c_float),
+                ("tile0", ctypes.c_int32), ("ctas_per_sm", ctypes.c_int32)]
 
 
 class rp_request_info(ctypes.Structure):
@@ -106,6 +108,8 @@ def load_library(path: str = LIB_PATH):
         "rp_search_noalloc": [P, i32, i64, i32, P, P, i64, P, i64, i32, i32, P, P, P],
         "rp_search_multi": [P, P, i32, P, P, P, i64, i32, P, P, i32],
         "rp_graph_shape": [P, i64, ctypes.POINTER(i32), ctypes.POINTER(i32), ctypes.POINTER(u64)],
+        "rp_graph_slice": [P, i64, i64, i64, ctypes.POINTER(i64)],
+        "rp_set_tuning": [P, i32, i32, i32],
         "rp_server_create": [P, i64, u64, i64, i32, ctypes.POINTER(P)],
         "rp_server_create_ex": [ctypes.POINTER(rp_executor), ctypes.POINTER(rp_server_config), ctypes.POINTER(P)],
         "rp_server_destroy": [P],
@@ -276,6 +280,13 @@ def rp_graph_shape(ctx, g: int) -> dict:
     return dict(d=d.value, dtype=dt.value, adj_bytes=b.value)
 
 
+def rp_graph_slice(ctx, g: int, lo: int, hi: int) -> int:
+    """The rows of nodes lo .. hi-1 of graph g (other rows empty), sharing g's vectors."""
+    out = ctypes.c_int64()
+    _check(ctx, load_library().rp_graph_slice(ctx, int(g), int(lo), int(hi), ctypes.byref(out)))
+    return out.value
+
+
 def rp_knn(ctx, g: int, queries, k: int, nq: int | None = None, ids=None, dists=None):
     """Exact kNN of ``queries`` (or of base points 0..nq-1 when queries is None)."""
     mem = _mem(queries, ids, dists) if queries is not None else (_mem(ids) if ids is not None else RP_MEM_HOST)
@@ -306,6 +317,10 @@ def rp_build_knn_base(ctx, data: int, kcand: int, alpha: float, R: int) -> int:
 
 def rp_graph_free(ctx, g: int):
     _check(ctx, load_library().rp_graph_free(ctx, int(g)))
+
+
+def rp_set_tuning(ctx, mode: int, tile0: int = 0, ctas_per_sm: int = 0):
+    _check(ctx, load_library().rp_set_tuning(ctx, int(mode), int(tile0), int(ctas_per_sm)))
 
 
 def rp_stats(ctx, reset: bool = False) -> dict:

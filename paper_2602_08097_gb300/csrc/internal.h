@@ -37,6 +37,10 @@ struct PruneLaunch {
   unsigned int* work = nullptr;   // device unsigned[3], zeroed before the launch
   DevStatus* status = nullptr;
   int num_sms = 0;
+  // tile of the degree <= 64 bucket: 0 = two nodes per 128-row MMA, 1 = one
+  // node per MMA; CTAs per SM of the tensor-core kernels (0 = all that fit)
+  int tile0 = 0;
+  int ctas_per_sm = 0;
 };
 
 // prune.cu
@@ -63,6 +67,8 @@ cudaError_t launch_clean_write(const int64_t* row_ptr, const int32_t* col, int64
                                const int64_t* new_row_ptr, int32_t* new_col, cudaStream_t s);
 cudaError_t launch_scan_counts(const int32_t* cnt, int64_t n, int64_t* row_ptr,
                                int64_t* block_sums, int32_t* max_deg, cudaStream_t s);
+cudaError_t launch_slice_row_ptr(const int64_t* row_ptr, int64_t n, int64_t lo, int64_t hi, int64_t* out,
+                                 cudaStream_t s);
 cudaError_t launch_medoid(const DevData& D, double* mean /* d */, double* block_best /* 2*nb */,
                           int64_t* medoid, cudaStream_t s);
 int64_t medoid_blocks(int64_t n);

@@ -361,6 +361,24 @@ cudaError_t launch_scan_counts(const int32_t* cnt, int64_t n, int64_t* row_ptr, 
 
 int64_t medoid_blocks(int64_t n) { return std::min<int64_t>((n + 255) / 256, 2048); }
 
+// row_ptr of the slice of a graph that keeps the rows of [lo, hi): every row
+// outside is empty and the kept rows keep their edges (col starts at lo's).
+__global__ void slice_row_ptr_kernel(const int64_t* __restrict__ row_ptr, int64_t n, int64_t lo, int64_t hi,
+                                     int64_t* __restrict__ out) {
+  const int64_t e_lo = row_ptr[lo], e_hi = row_ptr[hi];
+  for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i <= n; i += int64_t(gridDim.x) * blockDim.x) {
+    const int64_t e = row_ptr[i];
+    out[i] = (e < e_lo ? e_lo : (e > e_hi ? e_hi : e)) - e_lo;
+  }
+}
+
+cudaError_t launch_slice_row_ptr(const int64_t* row_ptr, int64_t n, int64_t lo, int64_t hi, int64_t* out,
+                                 cudaStream_t s) {
+  const int64_t blocks = std::min<int64_t>((n + 256) / 256, 4096);
+  slice_row_ptr_kernel<<<unsigned(blocks), 256, 0, s>>>(row_ptr, n, lo, hi, out);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_medoid(const DevData& D, double* mean, double* block_best, int64_t* medoid,
                           cudaStream_t s) {
   if (D.dtype == kU8) {

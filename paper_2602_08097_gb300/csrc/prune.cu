@@ -1056,7 +1056,7 @@ static cudaError_t resident_ctas(K kern, int threads, size_t dyn_smem, int cap, 
 }
 
 template <int DT, int MAXM, int TB>
-static cudaError_t run_fast_t(const PruneArgs& args, int num_sms, int64_t host_count, cudaStream_t s) {
+static cudaError_t run_fast_t(const PruneArgs& args, int num_sms, int64_t host_count, int ctas_cap, cudaStream_t s) {
   const size_t bytes = TcLayout<MAXM, TB>::bytes;
   auto kern = prune_tc_kernel<DT, MAXM, TB>;
   constexpr int kThreadsTc = 160;  // 4 producer warps + 1 consumer warp
@@ -1068,6 +1068,7 @@ static cudaError_t run_fast_t(const PruneArgs& args, int num_sms, int64_t host_c
   int per_sm = 0;
   err = resident_ctas(kern, kThreadsTc, bytes, 4 /* 128 of the 512 TMEM columns per CTA */, &per_sm);
   if (err != cudaSuccess) return err;
+  if (ctas_cap > 0) per_sm = std::min(per_sm, ctas_cap);
   const int64_t groups_needed = (host_count + (128 / MAXM) - 1) / (128 / MAXM);
   const int64_t grid = std::min<int64_t>(int64_t(num_sms) * per_sm, groups_needed);
   kern<<<unsigned(grid), kThreadsTc, bytes, s>>>(args);
@@ -1076,13 +1077,13 @@ static cudaError_t run_fast_t(const PruneArgs& args, int num_sms, int64_t host_c
 
 // Picks the kernel instance whose per-node target slots cover T.
 template <int DT, int MAXM>
-static cudaError_t run_fast(const PruneArgs& args, int num_sms, int64_t host_count, cudaStream_t s) {
+static cudaError_t run_fast(const PruneArgs& args, int num_sms, int64_t host_count, int ctas_cap, cudaStream_t s) {
   if (host_count <= 0) return cudaSuccess;
-  if (args.T <= 1) return run_fast_t<DT, MAXM, 1>(args, num_sms, host_count, s);
-  if (args.T <= 2) return run_fast_t<DT, MAXM, 2>(args, num_sms, host_count, s);
-  if (args.T <= 4) return run_fast_t<DT, MAXM, 4>(args, num_sms, host_count, s);
-  if (args.T <= 8) return run_fast_t<DT, MAXM, 8>(args, num_sms, host_count, s);
-  return run_fast_t<DT, MAXM, kMaxTargets>(args, num_sms, host_count, s);
+  if (args.T <= 1) return run_fast_t<DT, MAXM, 1>(args, num_sms, host_count, ctas_cap, s);
+  if (args.T <= 2) return run_fast_t<DT, MAXM, 2>(args, num_sms, host_count, ctas_cap, s);
+  if (args.T <= 4) return run_fast_t<DT, MAXM, 4>(args, num_sms, host_count, ctas_cap, s);
+  if (args.T <= 8) return run_fast_t<DT, MAXM, 8>(args, num_sms, host_count, ctas_cap, s);
+  return run_fast_t<DT, MAXM, kMaxTargets>(args, num_sms, host_count, ctas_cap, s);
 }
 
 template <int DT>
@@ -1132,12 +1133,12 @@ cudaError_t launch_prune(const PruneLaunch& L, cudaStream_t s) {
       // The bf16 Gram is exact for uint8 only while every partial sum stays
       // below 2^24 (d <= 256 here); wider rows take the exact CUDA-core path.
       const bool exact_tc = L.data.d <= 256;
-      if (b == 0 && exact_tc) err = run_fast<kU8, 64>(a, L.num_sms, hc, s);
-      else if (b == 1 && exact_tc) err = run_fast<kU8, 128>(a, L.num_sms, hc, s);
+      if (b == 0 && exact_tc && L.tile0 == 0) err = run_fast<kU8, 64>(a, L.num_sms, hc, L.ctas_per_sm, s);
+      else if (b <= 1 && exact_tc) err = run_fast<kU8, 128>(a, L.num_sms, hc, L.ctas_per_sm, s);
       else err = run_generic<kU8>(a, L.num_sms, hc, L.host_max_degree, s);
     } else {
-      if (b == 0) err = run_fast<kF32, 64>(a, L.num_sms, hc, s);
-      else if (b == 1) err = run_fast<kF32, 128>(a, L.num_sms, hc, s);
+      if (b == 0 && L.tile0 == 0) err = run_fast<kF32, 64>(a, L.num_sms, hc, L.ctas_per_sm, s);
+      else if (b <= 1) err = run_fast<kF32, 128>(a, L.num_sms, hc, L.ctas_per_sm, s);
       else err = run_generic<kF32>(a, L.num_sms, hc, L.host_max_degree, s);
     }
   }

@@ -37,6 +37,12 @@ struct Dataset {
   }
 };
 
+// Tensor-core prune configuration picked for one source graph, per target-count
+// class (1, 2, 4, 8, 16) and variant.
+struct TuneChoice {
+  int tclass = 0, variant = 0, tile0 = 0, ctas = 0;
+};
+
 struct Graph {
   std::shared_ptr<Dataset> data;
   int64_t* row_ptr = nullptr;
@@ -49,6 +55,8 @@ struct Graph {
   int32_t* buckets = nullptr;  // 3 * n node lists + 3 counts, built on first use as a source
   size_t bytes = 0;
   size_t bucket_bytes = 0;
+  int64_t bucket0 = -1;  // nodes of degree <= 64, read back for the autotuner
+  std::vector<TuneChoice> choices;
 };
 
 struct BatchPlan {
@@ -58,6 +66,7 @@ struct BatchPlan {
   int variant = 0;
   int32_t A[kMaxTargets];
   int32_t R[kMaxTargets];
+  int tile0 = 0, ctas = 0;
   cudaGraphExec_t exec = nullptr;
 };
 
@@ -90,6 +99,11 @@ struct rp_ctx {
   int64_t qbuf_bytes = 0;
   unsigned long long* hits = nullptr;  // device [1]
   std::vector<BatchPlan> plans;
+  // prune configuration: autotuned per source graph, or fixed by rp_set_tuning
+  int tuning_mode = RP_TUNING_AUTO;
+  int fixed_tile0 = 0, fixed_ctas = 0;
+  int last_tile0 = 0, last_ctas = 0;
+  int32_t* trial_count = nullptr;  // device int[4]: bucket sizes of a trial launch
   int64_t graph_replays = 0;
   int64_t kernel_launches = 0;
   // phase timing: 0/1 prune, 1/2 emit, 3/4 search
@@ -240,9 +254,11 @@ rp_status ensure_buckets(rp_ctx* c, Graph* G) {
 }
 
 // Enqueue the whole tuning pipeline for `T` targets of `src` into `outs`.
-rp_status enqueue_tune(rp_ctx* c, Graph* S, int T, const int32_t* A, const int32_t* R, int variant,
-                       Graph* const* outs, int64_t* kernels) {
+rp_status enqueue_tune(rp_ctx* c, Graph* S, int T, const int32_t* A, const int32_t* R, int variant, int tile0,
+                       int ctas, Graph* const* outs, int64_t* kernels) {
   PruneLaunch L;
+  L.tile0 = tile0;
+  L.ctas_per_sm = ctas;
   L.data = S->data->dev();
   L.row_ptr = S->row_ptr;
   L.col = S->col;
@@ -287,6 +303,92 @@ rp_status enqueue_tune(rp_ctx* c, Graph* S, int T, const int32_t* A, const int32
   return RP_OK;
 }
 
+// The tensor-core prune configuration for T targets of S: fixed by
+// rp_set_tuning, or chosen once per (source, target-count class, variant) by
+// timing every candidate on a sample of the degree <= 64 nodes.  Runs before
+// any stream capture (it synchronises).
+constexpr int64_t kAutotuneMinNodes = 65536;
+constexpr int64_t kAutotuneSample = 32768;
+
+rp_status choose_config(rp_ctx* c, Graph* S, int T, const int32_t* A, const int32_t* R, int variant, int* tile0,
+                        int* ctas) {
+  *tile0 = 0;
+  *ctas = 0;
+  if (c->tuning_mode == RP_TUNING_FIXED) {
+    *tile0 = c->fixed_tile0;
+    *ctas = c->fixed_ctas;
+    return RP_OK;
+  }
+  if (S->data->dtype == RP_U8 && S->data->d > 256) return RP_OK;  // all nodes take the CUDA-core path
+  const int tclass = T <= 1 ? 1 : T <= 2 ? 2 : T <= 4 ? 4 : T <= 8 ? 8 : 16;
+  for (const TuneChoice& ch : S->choices)
+    if (ch.tclass == tclass && ch.variant == variant) {
+      *tile0 = ch.tile0;
+      *ctas = ch.ctas;
+      return RP_OK;
+    }
+  if (S->bucket0 < 0) {
+    int32_t cnt[3] = {0, 0, 0};
+    CUDA_TRY(c, cudaMemcpyAsync(cnt, S->buckets + 3 * S->n, sizeof cnt, cudaMemcpyDeviceToHost, c->stream));
+    CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    S->bucket0 = cnt[0];
+  }
+  TuneChoice best;
+  best.tclass = tclass;
+  best.variant = variant;
+  if (S->bucket0 >= kAutotuneMinNodes) {
+    rp_status st;
+    if (!c->trial_count && (st = dalloc(c, reinterpret_cast<void**>(&c->trial_count), 16)) != RP_OK) return st;
+    const int32_t sample[4] = {int32_t(std::min(S->bucket0, kAutotuneSample)), 0, 0, 0};
+    CUDA_TRY(c, cudaMemcpyAsync(c->trial_count, sample, sizeof sample, cudaMemcpyHostToDevice, c->stream));
+    PruneLaunch L;
+    L.data = S->data->dev();
+    L.row_ptr = S->row_ptr;
+    L.col = S->col;
+    for (int b = 0; b < 3; ++b) L.bucket_nodes[b] = S->buckets + int64_t(b) * S->n;
+    L.host_bucket_count[0] = sample[0];
+    L.bucket_count = c->trial_count;
+    L.host_max_degree = S->max_deg_bound;
+    L.T = T;
+    L.variant = variant;
+    L.work = c->work;
+    L.status = c->status;
+    L.num_sms = c->num_sms;
+    for (int t = 0; t < T; ++t) {
+      L.A[t] = A[t];
+      L.R[t] = R[t];
+      L.out_col[t] = c->scratch_col + int64_t(t) * std::max<int64_t>(S->col_cap, 1);
+      L.out_cnt[t] = c->scratch_cnt + int64_t(t) * S->n;
+    }
+    const int cand[6][2] = {{0, 0}, {0, 3}, {0, 2}, {1, 0}, {1, 3}, {1, 2}};
+    float best_ms = 0.f;
+    for (int i = 0; i < 6; ++i) {
+      L.tile0 = cand[i][0];
+      L.ctas_per_sm = cand[i][1];
+      float ms = 0.f;
+      for (int rep = 0; rep < 2; ++rep) {  // the first run loads the kernel
+        CUDA_TRY(c, cudaMemsetAsync(c->work, 0, 8 * sizeof(unsigned), c->stream));
+        CUDA_TRY(c, cudaEventRecord(c->ev[0], c->stream));
+        CUDA_TRY(c, launch_prune(L, c->stream));
+        CUDA_TRY(c, cudaEventRecord(c->ev[1], c->stream));
+        CUDA_TRY(c, cudaEventSynchronize(c->ev[1]));
+        CUDA_TRY(c, cudaEventElapsedTime(&ms, c->ev[0], c->ev[1]));
+        c->kernel_launches += 1;
+      }
+      if (i == 0 || ms < best_ms) {
+        best_ms = ms;
+        best.tile0 = cand[i][0];
+        best.ctas = cand[i][1];
+      }
+    }
+    if ((st = check_device_status(c)) != RP_OK) return st;
+  }
+  S->choices.push_back(best);
+  *tile0 = best.tile0;
+  *ctas = best.ctas;
+  return RP_OK;
+}
+
 rp_status tune_impl(rp_ctx* c, rp_graph src, const double* alphas, const int32_t* Rs, int32_t T, int32_t variant,
                     rp_graph* outs, bool use_graph) {
   if (!outs || !alphas || !Rs) return fail(c, RP_EINVAL, "null argument");
@@ -307,6 +409,10 @@ rp_status tune_impl(rp_ctx* c, rp_graph src, const double* alphas, const int32_t
   if ((s = grow(c, &c->scratch_col, &c->scratch_col_elems, cap * T)) != RP_OK) return s;
   if ((s = grow(c, &c->scratch_cnt, &c->scratch_cnt_elems, S->n * T)) != RP_OK) return s;
   if ((s = grow(c, &c->scratch_bsum, &c->scratch_bsum_elems, emit_csr_blocks(S->n) * T)) != RP_OK) return s;
+  int tile0 = 0, ctas = 0;
+  if ((s = choose_config(c, S, T, A, R, variant, &tile0, &ctas)) != RP_OK) return s;
+  c->last_tile0 = tile0;
+  c->last_ctas = ctas;
   Graph* G[kMaxTargets] = {};
   for (int t = 0; t < T; ++t) {
     G[t] = new Graph;
@@ -325,20 +431,21 @@ rp_status tune_impl(rp_ctx* c, rp_graph src, const double* alphas, const int32_t
   }
   int64_t nk = 0;
   if (!use_graph) {
-    s = enqueue_tune(c, S, T, A, R, variant, G, &nk);
+    s = enqueue_tune(c, S, T, A, R, variant, tile0, ctas, G, &nk);
     c->kernel_launches += nk;
   } else {
     // Replay: capture this call's launches and update the cached executable
     // graph of the same (source, targets, variant) in place.
     BatchPlan* plan = nullptr;
     for (auto& pl : c->plans)
-      if (pl.src == src && pl.T == T && pl.variant == variant && !memcmp(pl.A, A, 4 * T) && !memcmp(pl.R, R, 4 * T))
+      if (pl.src == src && pl.T == T && pl.variant == variant && pl.tile0 == tile0 && pl.ctas == ctas &&
+          !memcmp(pl.A, A, 4 * T) && !memcmp(pl.R, R, 4 * T))
         plan = &pl;
     cudaGraph_t graph = nullptr;
     cudaError_t ce = cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal);
     if (ce != cudaSuccess) s = fail(c, RP_ECUDA, "begin capture: %s", cudaGetErrorString(ce));
     if (s == RP_OK) {
-      s = enqueue_tune(c, S, T, A, R, variant, G, &nk);
+      s = enqueue_tune(c, S, T, A, R, variant, tile0, ctas, G, &nk);
       ce = cudaStreamEndCapture(c->stream, &graph);
       if (s == RP_OK && ce != cudaSuccess) s = fail(c, RP_ECUDA, "end capture: %s", cudaGetErrorString(ce));
     }
@@ -361,6 +468,8 @@ rp_status tune_impl(rp_ctx* c, rp_graph src, const double* alphas, const int32_t
             plan->src = src;
             plan->T = T;
             plan->variant = variant;
+            plan->tile0 = tile0;
+            plan->ctas = ctas;
             memcpy(plan->A, A, 4 * T);
             memcpy(plan->R, R, 4 * T);
           } else if (plan->exec) {
@@ -525,6 +634,7 @@ rp_status rp_destroy(rp_ctx* c) {
     dfree(c, c->dropped, 16);
     dfree(c, c->work, 32);
     dfree(c, c->hits, 8);
+    if (c->trial_count) dfree(c, c->trial_count, 16);
     cudaStreamSynchronize(c->stream);
     for (auto& e : c->ev)
       if (e) cudaEventDestroy(e);
@@ -758,6 +868,41 @@ rp_status rp_graph_export(rp_ctx* c, rp_graph g, int64_t* row_ptr, int32_t* col,
   return RP_OK;
 }
 
+rp_status rp_graph_slice(rp_ctx* c, rp_graph g, int64_t lo, int64_t hi, rp_graph* out) {
+  if (!c) return RP_EINVAL;
+  std::lock_guard<std::mutex> lk(c->mu);
+  cudaSetDevice(c->device);
+  Graph* G = find_graph(c, g);
+  if (!G) return fail(c, RP_ENOTFOUND, "unknown graph %lld", (long long)g);
+  if (!out || lo < 0 || hi < lo || hi > G->n)
+    return fail(c, RP_EINVAL, "need 0 <= lo <= hi <= n (lo=%lld hi=%lld n=%lld)", (long long)lo, (long long)hi,
+                (long long)G->n);
+  int64_t e[2] = {0, 0};
+  CUDA_TRY(c, cudaMemcpyAsync(&e[0], G->row_ptr + lo, 8, cudaMemcpyDeviceToHost, c->stream));
+  CUDA_TRY(c, cudaMemcpyAsync(&e[1], G->row_ptr + hi, 8, cudaMemcpyDeviceToHost, c->stream));
+  CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  const int64_t nnz = e[1] - e[0];
+  Graph* S = new Graph;
+  S->data = G->data;
+  S->n = G->n;
+  S->col_cap = std::max<int64_t>(nnz, 1);
+  S->nnz = nnz;
+  S->start = G->start;
+  S->max_deg_bound = G->max_deg_bound;
+  S->bytes = size_t(G->n + 1) * 8 + size_t(S->col_cap) * 4;
+  rp_status st = dalloc(c, reinterpret_cast<void**>(&S->row_ptr), size_t(G->n + 1) * 8);
+  if (st == RP_OK) st = dalloc(c, reinterpret_cast<void**>(&S->col), size_t(S->col_cap) * 4);
+  if (st != RP_OK) {
+    free_graph_mem(c, S);
+    return st;
+  }
+  CUDA_TRY(c, launch_slice_row_ptr(G->row_ptr, G->n, lo, hi, S->row_ptr, c->stream));
+  c->kernel_launches += 1;
+  if (nnz > 0) CUDA_TRY(c, cudaMemcpyAsync(S->col, G->col + e[0], size_t(nnz) * 4, cudaMemcpyDeviceToDevice, c->stream));
+  *out = add_graph(c, S);
+  return RP_OK;
+}
+
 rp_status rp_graph_shape(rp_ctx* c, rp_graph g, int32_t* d, int32_t* dtype, uint64_t* adj_bytes) {
   if (!c) return RP_EINVAL;
   std::lock_guard<std::mutex> lk(c->mu);
@@ -952,6 +1097,19 @@ rp_status rp_build_knn_base(rp_ctx* c, rp_graph data, int32_t kcand, double alph
   return RP_OK;
 }
 
+rp_status rp_set_tuning(rp_ctx* c, int32_t mode, int32_t tile0, int32_t ctas_per_sm) {
+  if (!c) return RP_EINVAL;
+  std::lock_guard<std::mutex> lk(c->mu);
+  if (mode != RP_TUNING_AUTO && mode != RP_TUNING_FIXED)
+    return fail(c, RP_EINVAL, "tuning mode %d is neither RP_TUNING_AUTO nor RP_TUNING_FIXED", mode);
+  if (mode == RP_TUNING_FIXED && (tile0 < 0 || tile0 > 1 || ctas_per_sm < 0 || ctas_per_sm > 4))
+    return fail(c, RP_EINVAL, "need tile0 in {0, 1} and ctas_per_sm in 0..4 (got %d, %d)", tile0, ctas_per_sm);
+  c->tuning_mode = mode;
+  c->fixed_tile0 = mode == RP_TUNING_FIXED ? tile0 : 0;
+  c->fixed_ctas = mode == RP_TUNING_FIXED ? ctas_per_sm : 0;
+  return RP_OK;
+}
+
 rp_status rp_stats(rp_ctx* c, rp_stats_t* out, int32_t reset) {
   if (!c || !out) return RP_EINVAL;
   std::lock_guard<std::mutex> lk(c->mu);
@@ -977,6 +1135,8 @@ rp_status rp_stats(rp_ctx* c, rp_stats_t* out, int32_t reset) {
   }
   if (c->ev_search) cudaEventElapsedTime(&out->last_search_ms, c->ev[3], c->ev[4]);
   cudaGetLastError();
+  out->tile0 = c->last_tile0;
+  out->ctas_per_sm = c->last_ctas;
   if (reset) {
     DevStatus z;
     memset(&z, 0, sizeof z);
