@@ -25,6 +25,10 @@ relative to the serial path's capacity; p50/p99 latency, QPS and recall@100.
 float32 rows, |N(0,1)| * 0.05 then L2-normalised; nine targets: alpha 1.175 down
 to 1.0 at R=64 plus (1.0, 32), in one launch; 1,000 queries, L=200, k=100).
 
+`--workload deep` runs the large float sweep (10,000,000 x 96 float32 unit rows
+from a 256-centre mixture; eight targets alpha in {1.15, 1.1, 1.05, 1.0} x R in
+{64, 48} in one launch; 10,000 queries, L=100, k=100).
+
 `--impl reference` times the CPU oracle (the reference arm of this build) on
 a bounded sample of the same workload and prints the same JSON line.
 """
@@ -62,6 +66,8 @@ WORKLOADS = {
                  targets=[(1.1, 64), (1.05, 48), (1.0, 32)]),
     "gist": dict(dtype="f32", n=1_000_000, d=960, nq=1_000, L=200,
                  targets=[(round(1.175 - 0.025 * i, 3), 64) for i in range(8)] + [(1.0, 32)]),
+    "deep": dict(dtype="f32", n=10_000_000, d=96, nq=10_000, L=100,
+                 targets=[(a, r) for a in (1.15, 1.1, 1.05, 1.0) for r in (64, 48)]),
 }
 TARGETS = WORKLOADS["sift"]["targets"]
 L_SEARCH = WORKLOADS["sift"]["L"]
@@ -69,7 +75,7 @@ L_SEARCH = WORKLOADS["sift"]["L"]
 
 def workload_name(n, nq, name="sift"):
     w = WORKLOADS[name]
-    shape = {"sift": "sift-shaped uint8", "gist": "gist-shaped float32"}[name]
+    shape = {"sift": "sift-shaped uint8", "gist": "gist-shaped float32", "deep": "deep-shaped float32"}[name]
     tl = ",".join(f"({a:g},{r})" for a, r in w["targets"])
     return (f"{shape} n={n:,} d={w['d']}; base RobustPrune(1.2,64) over exact kNN-128; "
             f"tune {tl}; {nq:,} queries L={w['L']} k=100")

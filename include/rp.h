@@ -311,6 +311,8 @@ typedef struct {
   float last_search_ms;        /* device time of the last rp_search kernel */
   int32_t tile0;               /* prune configuration of the last tuning call (rp_set_tuning) */
   int32_t ctas_per_sm;
+  int32_t knn_method;          /* path of the last rp_knn / rp_build_knn_base (RP_KNN_*) */
+  int32_t pad_;
 } rp_stats_t;
 
 rp_status rp_stats(rp_ctx *ctx, rp_stats_t *out, int32_t reset);
@@ -331,6 +333,21 @@ rp_status rp_stats(rp_ctx *ctx, rp_stats_t *out, int32_t reset);
  */
 enum { RP_TUNING_AUTO = 0, RP_TUNING_FIXED = 1 };
 rp_status rp_set_tuning(rp_ctx *ctx, int32_t mode, int32_t tile0, int32_t ctas_per_sm);
+
+/*
+ * rp_set_knn_method: which exact kNN scan rp_knn and rp_build_knn_base use.
+ * Both return the same lists (exact top k by (distance, id)).
+ *   RP_KNN_CUDA_CORE: every pair's distance on CUDA cores.
+ *   RP_KNN_TENSOR: an f16 Gram on tcgen05 filters candidates with a rigorous
+ *     error bound (none for uint8 rows of d <= 128), and the survivors are
+ *     ranked exactly; needs k <= 128 and uint8 rows of d <= 128 or float
+ *     rows of d <= 256 (RP_EINVAL otherwise).  Holds an f16 copy of the
+ *     vectors (n x d x 2 bytes) for the call.
+ *   RP_KNN_AUTO (default): RP_KNN_TENSOR where it applies.
+ * Errors: RP_EINVAL.
+ */
+enum { RP_KNN_AUTO = 0, RP_KNN_CUDA_CORE = 1, RP_KNN_TENSOR = 2 };
+rp_status rp_set_knn_method(rp_ctx *ctx, int32_t method);
 
 /* ------------------------------------------------------------------------
  * Serving: a scheduler thread over one resident base graph that takes

@@ -24,6 +24,7 @@ RP_R_INF = 2**31 - 1
 RP_MAX_DEGREE = 8192
 RP_MAX_L = 1024
 RP_TUNING_AUTO, RP_TUNING_FIXED = 0, 1
+RP_KNN_AUTO, RP_KNN_CUDA_CORE, RP_KNN_TENSOR = 0, 1, 2
 
 _NAMES = {RP_EINVAL: "RP_EINVAL", RP_ENOMEM: "RP_ENOMEM", RP_ECUDA: "RP_ECUDA", RP_ETIMEOUT: "RP_ETIMEOUT",
           RP_ENOTFOUND: "RP_ENOTFOUND", RP_EDEVICE: "RP_EDEVICE"}
@@ -43,7 +44,8 @@ class rp_stats_t(ctypes.Structure):
                 ("bytes_in_use", ctypes.c_uint64), ("bytes_peak", ctypes.c_uint64),
                 ("kernel_launches", ctypes.c_int64), ("last_prune_ms", ctypes.c_float),
                 ("last_emit_ms", ctypes.c_float), ("last_search_ms", ctypes.c_float),
-                ("tile0", ctypes.c_int32), ("ctas_per_sm", ctypes.c_int32)]
+                ("tile0", ctypes.c_int32), ("ctas_per_sm", ctypes.c_int32),
+                ("knn_method", ctypes.c_int32), ("pad_", ctypes.c_int32)]
 
 
 class rp_request_info(ctypes.Structure):
@@ -110,6 +112,7 @@ def load_library(path: str = LIB_PATH):
         "rp_graph_shape": [P, i64, ctypes.POINTER(i32), ctypes.POINTER(i32), ctypes.POINTER(u64)],
         "rp_graph_slice": [P, i64, i64, i64, ctypes.POINTER(i64)],
         "rp_set_tuning": [P, i32, i32, i32],
+        "rp_set_knn_method": [P, i32],
         "rp_server_create": [P, i64, u64, i64, i32, ctypes.POINTER(P)],
         "rp_server_create_ex": [ctypes.POINTER(rp_executor), ctypes.POINTER(rp_server_config), ctypes.POINTER(P)],
         "rp_server_destroy": [P],
@@ -323,10 +326,14 @@ def rp_set_tuning(ctx, mode: int, tile0: int = 0, ctas_per_sm: int = 0):
     _check(ctx, load_library().rp_set_tuning(ctx, int(mode), int(tile0), int(ctas_per_sm)))
 
 
+def rp_set_knn_method(ctx, method: int):
+    _check(ctx, load_library().rp_set_knn_method(ctx, int(method)))
+
+
 def rp_stats(ctx, reset: bool = False) -> dict:
     s = rp_stats_t()
     _check(ctx, load_library().rp_stats(ctx, ctypes.byref(s), int(bool(reset))))
-    return {name: getattr(s, name) for name, _ in rp_stats_t._fields_}
+    return {name: getattr(s, name) for name, _ in rp_stats_t._fields_ if name != "pad_"}
 
 
 def rp_search_noalloc(vectors, row_ptr, col, start: int, queries, L: int, k: int, ids=None, dists=None,

@@ -118,4 +118,21 @@ struct KnnLaunch {
 };
 cudaError_t launch_knn(const KnnLaunch& K, cudaStream_t s);
 
+// Exact kNN with the candidate filter on tcgen05 (uint8 rows of d <= 128,
+// float rows of at most 256 dimensions, k <= 128).
+struct KnnTcLaunch {
+  DevData data;
+  const uint8_t* Q = nullptr;  // padded query rows, or nullptr for base points 0..nq-1
+  int64_t nq = 0;
+  int k = 0;
+  int32_t* out_ids = nullptr;
+  float* out_dists = nullptr;
+  DevStatus* status = nullptr;
+  int num_sms = 0;
+  uint8_t* scratch = nullptr;  // knn_tc_scratch_bytes(), 256-byte aligned
+};
+bool knn_tc_eligible(int dtype, int d, int k);
+size_t knn_tc_scratch_bytes(int dtype, int d, int64_t n, int64_t nq_ext, int num_sms);
+cudaError_t launch_knn_tc(const KnnTcLaunch& K, cudaStream_t s);
+
 }  // namespace rpk

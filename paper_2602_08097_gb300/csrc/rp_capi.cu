@@ -103,6 +103,8 @@ struct rp_ctx {
   int tuning_mode = RP_TUNING_AUTO;
   int fixed_tile0 = 0, fixed_ctas = 0;
   int last_tile0 = 0, last_ctas = 0;
+  int knn_method = RP_KNN_AUTO;
+  int last_knn_method = 0;
   int32_t* trial_count = nullptr;  // device int[4]: bucket sizes of a trial launch
   int64_t graph_replays = 0;
   int64_t kernel_launches = 0;
@@ -492,6 +494,49 @@ rp_status tune_impl(rp_ctx* c, rp_graph src, const double* alphas, const int32_t
     return s;
   }
   for (int t = 0; t < T; ++t) outs[t] = add_graph(c, G[t]);
+  return RP_OK;
+}
+
+// Exact kNN of nq queries (padded device rows Q, or base points 0..nq-1 when
+// Q is null) by the tensor-core filter where it applies, else the CUDA-core scan.
+rp_status run_knn(rp_ctx* c, const Dataset& D, const uint8_t* Q, int64_t nq, int32_t k, int32_t* ids, float* dists) {
+  const bool tc_ok = knn_tc_eligible(D.dtype, D.d, k);
+  if (c->knn_method == RP_KNN_TENSOR && !tc_ok)
+    return fail(c, RP_EINVAL, "the tensor-core kNN needs k <= 128 and uint8 rows of d <= 128 or float rows of d <= 256");
+  if (tc_ok && c->knn_method != RP_KNN_CUDA_CORE) {
+    const size_t bytes = knn_tc_scratch_bytes(D.dtype, D.d, D.n, Q ? nq : 0, c->num_sms);
+    void* scratch = nullptr;
+    rp_status st = dalloc(c, &scratch, bytes);
+    if (st != RP_OK) return st;
+    KnnTcLaunch K;
+    K.data = D.dev();
+    K.Q = Q;
+    K.nq = nq;
+    K.k = k;
+    K.out_ids = ids;
+    K.out_dists = dists;
+    K.status = c->status;
+    K.num_sms = c->num_sms;
+    K.scratch = static_cast<uint8_t*>(scratch);
+    const cudaError_t ce = launch_knn_tc(K, c->stream);
+    dfree(c, scratch, bytes);
+    if (ce != cudaSuccess) return fail(c, RP_ECUDA, "tensor-core kNN: %s", cudaGetErrorString(ce));
+    c->kernel_launches += D.dtype == RP_F32 ? 5 : 3;
+    c->last_knn_method = RP_KNN_TENSOR;
+    return RP_OK;
+  }
+  KnnLaunch K;
+  K.data = D.dev();
+  K.Q = Q;
+  K.nq = nq;
+  K.k = k;
+  K.out_ids = ids;
+  K.out_dists = dists;
+  K.status = c->status;
+  K.num_sms = c->num_sms;
+  CUDA_TRY(c, launch_knn(K, c->stream));
+  c->kernel_launches += (nq + 65535) / 65536;
+  c->last_knn_method = RP_KNN_CUDA_CORE;
   return RP_OK;
 }
 
@@ -983,17 +1028,7 @@ rp_status rp_knn(rp_ctx* c, rp_graph g, const void* queries, int64_t nq, int32_t
     dev_ids = reinterpret_cast<int32_t*>(c->qbuf + qbytes);
     dev_d = reinterpret_cast<float*>(c->qbuf + qbytes + nq * k * 4);
   }
-  KnnLaunch K;
-  K.data = D.dev();
-  K.Q = queries ? c->qbuf : nullptr;
-  K.nq = nq;
-  K.k = k;
-  K.out_ids = dev_ids;
-  K.out_dists = dev_d;
-  K.status = c->status;
-  K.num_sms = c->num_sms;
-  CUDA_TRY(c, launch_knn(K, c->stream));
-  c->kernel_launches += 1;
+  if ((s = run_knn(c, D, queries ? c->qbuf : nullptr, nq, k, dev_ids, dev_d)) != RP_OK) return s;
   if (mem_flags == RP_MEM_HOST) {
     CUDA_TRY(c, cudaMemcpyAsync(ids, dev_ids, size_t(nq * k) * 4, cudaMemcpyDeviceToHost, c->stream));
     if (dists) CUDA_TRY(c, cudaMemcpyAsync(dists, dev_d, size_t(nq * k) * 4, cudaMemcpyDeviceToHost, c->stream));
@@ -1058,21 +1093,9 @@ rp_status rp_build_knn_base(rp_ctx* c, rp_graph data, int32_t kcand, double alph
     free_graph_mem(c, K);
     return s;
   }
-  if (kk > 0) {
-    KnnLaunch L;
-    L.data = G->data->dev();
-    L.Q = nullptr;
-    L.nq = n;
-    L.k = kk;
-    L.out_ids = K->col;
-    L.out_dists = nullptr;
-    L.status = c->status;
-    L.num_sms = c->num_sms;
-    cudaError_t ce = launch_knn(L, c->stream);
-    if (ce != cudaSuccess) {
-      free_graph_mem(c, K);
-      return fail(c, RP_ECUDA, "knn: %s", cudaGetErrorString(ce));
-    }
+  if (kk > 0 && (s = run_knn(c, *G->data, nullptr, n, kk, K->col, nullptr)) != RP_OK) {
+    free_graph_mem(c, K);
+    return s;
   }
   std::vector<int64_t> hrp(size_t(n + 1));
   for (int64_t p = 0; p <= n; ++p) hrp[size_t(p)] = p * kk;
@@ -1093,7 +1116,32 @@ rp_status rp_build_knn_base(rp_ctx* c, rp_graph data, int32_t kcand, double alph
   free_graph_mem(c, it->second);
   c->graphs.erase(it);
   if (s != RP_OK) return s;
+  // The result holds the candidate graph's capacity (n x kcand ids); keep only
+  // its edges, since every graph tuned from it takes its capacity too.
+  Graph* B = find_graph(c, res);
+  CUDA_TRY(c, cudaMemcpyAsync(&B->nnz, B->row_ptr + B->n, 8, cudaMemcpyDeviceToHost, c->stream));
+  CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  const int64_t cap = std::max<int64_t>(B->nnz, 1);
+  if (cap < B->col_cap) {
+    int32_t* col = nullptr;
+    if (dalloc(c, reinterpret_cast<void**>(&col), size_t(cap) * 4) == RP_OK) {
+      CUDA_TRY(c, cudaMemcpyAsync(col, B->col, size_t(cap) * 4, cudaMemcpyDeviceToDevice, c->stream));
+      dfree(c, B->col, size_t(B->col_cap) * 4);
+      B->col = col;
+      B->col_cap = cap;
+      B->bytes = size_t(B->n + 1) * 8 + size_t(cap) * 4;
+    }
+  }
   *out = res;
+  return RP_OK;
+}
+
+rp_status rp_set_knn_method(rp_ctx* c, int32_t method) {
+  if (!c) return RP_EINVAL;
+  std::lock_guard<std::mutex> lk(c->mu);
+  if (method != RP_KNN_AUTO && method != RP_KNN_CUDA_CORE && method != RP_KNN_TENSOR)
+    return fail(c, RP_EINVAL, "unknown kNN method %d", method);
+  c->knn_method = method;
   return RP_OK;
 }
 
@@ -1137,6 +1185,7 @@ rp_status rp_stats(rp_ctx* c, rp_stats_t* out, int32_t reset) {
   cudaGetLastError();
   out->tile0 = c->last_tile0;
   out->ctas_per_sm = c->last_ctas;
+  out->knn_method = c->last_knn_method;
   if (reset) {
     DevStatus z;
     memset(&z, 0, sizeof z);

@@ -113,6 +113,13 @@ __device__ __forceinline__ uint32_t u8x2_f16x2(uint32_t w, uint32_t sel) {
   return r;
 }
 
+// Round-to-nearest-even float pair -> f16x2 bits (lo in the low half).
+__device__ __forceinline__ uint32_t pack_f16x2(float lo, float hi) {
+  uint32_t r;
+  asm("cvt.rn.f16x2.f32 %0, %1, %2;" : "=r"(r) : "f"(hi), "f"(lo));
+  return r;
+}
+
 // Round-to-nearest-even float -> bf16 bits (exact for integers up to 256).
 __device__ __forceinline__ uint32_t pack_bf16x2(float lo, float hi) {
   uint32_t r;

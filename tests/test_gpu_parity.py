@@ -335,3 +335,43 @@ def test_sixteen_targets_in_one_launch(ctx, dtype):
                       oracle.rp_tune(X, row_ptr, col, a, r, "sorted" if variant == rp.RP_SORTED else "unsorted"),
                       f"{dtype} 16 targets a={a} R={r}")
             rp.rp_graph_free(ctx, t)
+
+
+@pytest.mark.parametrize("variant", ["sorted", "unsorted"])
+def test_gist_shaped_wide_float_rows(ctx, variant):
+    # d = 960: eight 128-dim slices per row on the tensor-core path, degrees
+    # across all three buckets
+    n = 2000
+    X = datagen.dataset("gist", n)
+    row_ptr, col = datagen.random_graph(n, 0, 150, seed=960, dup_frac=0.02, self_frac=0.01)
+    g = rp.rp_load_graph(ctx, X, row_ptr, col)
+    clean = rp.rp_graph_export(ctx, g)
+    v = rp.RP_SORTED if variant == "sorted" else rp.RP_UNSORTED
+    targets = [(1.175, 64), (1.1, 64), (1.025, 64), (1.0, 32)]
+    outs = rp.rp_tune_batch(ctx, g, [a for a, _ in targets], [r for _, r in targets], v)
+    for (a, r), o in zip(targets, outs):
+        _same_csr(rp.rp_graph_export(ctx, o), oracle.rp_tune(X, clean[0], clean[1], a, r, variant),
+                  f"gist {variant} a={a} R={r}")
+        rp.rp_graph_free(ctx, o)
+    rp.rp_graph_free(ctx, g)
+
+
+def test_gist_shaped_knn_base_and_search(ctx):
+    n = 3000
+    X = datagen.dataset("gist", n)
+    Q = datagen.queries("gist", 50)
+    data = rp.rp_load_graph(ctx, X)
+    base = rp.rp_build_knn_base(ctx, data, 64, 1.2, 48)
+    got = rp.rp_graph_export(ctx, base)
+    ref = oracle.knn_base(X, 64, 1.2, 48)
+    _same_csr(got, ref, "gist kNN-64 base")
+    start = rp.rp_graph_info(ctx, base)["start"]
+    ids, dists = rp.rp_search(ctx, base, Q, 200, 100)
+    ref_i, ref_d, _ = oracle.greedy_search(X, ref[0], ref[1], start, Q, 200, 100)
+    assert np.array_equal(ids, ref_i)
+    # float distances feeding recall: error against the binary64 reading
+    rel = np.abs(dists.astype(np.float64) - ref_d) / np.maximum(ref_d, 1e-30)
+    print(f"gist search distances: max relative error vs binary64 {rel.max():.3e}")
+    assert rel.max() <= (960 + 8) * 2.0**-24
+    rp.rp_graph_free(ctx, base)
+    rp.rp_graph_free(ctx, data)
