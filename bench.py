@@ -67,7 +67,8 @@ WORKLOADS = {
     "gist": dict(dtype="f32", n=1_000_000, d=960, nq=1_000, L=200,
                  targets=[(round(1.175 - 0.025 * i, 3), 64) for i in range(8)] + [(1.0, 32)]),
     "deep": dict(dtype="f32", n=10_000_000, d=96, nq=10_000, L=100,
-                 targets=[(a, r) for a in (1.15, 1.1, 1.05, 1.0) for r in (64, 48)]),
+                 targets=[(a, r) for a in (1.15, 1.1, 1.05, 1.0) for r in (64, 48)],
+                 base=dict(kcand=96, nrand=32, seed=4003)),
 }
 TARGETS = WORKLOADS["sift"]["targets"]
 L_SEARCH = WORKLOADS["sift"]["L"]
@@ -77,7 +78,8 @@ def workload_name(n, nq, name="sift"):
     w = WORKLOADS[name]
     shape = {"sift": "sift-shaped uint8", "gist": "gist-shaped float32", "deep": "deep-shaped float32"}[name]
     tl = ",".join(f"({a:g},{r})" for a, r in w["targets"])
-    return (f"{shape} n={n:,} d={w['d']}; base RobustPrune(1.2,64) over exact kNN-128; "
+    cand = (f"exact kNN-{w['base']['kcand']} + {w['base']['nrand']} random" if "base" in w else "exact kNN-128")
+    return (f"{shape} n={n:,} d={w['d']}; base RobustPrune(1.2,64) over {cand}; "
             f"tune {tl}; {nq:,} queries L={w['L']} k=100")
 
 
@@ -250,7 +252,11 @@ def run_ours(args):
     # ---- fixture (not timed): vectors, base graph, ground truth
     t0 = time.perf_counter()
     data = rp.rp_load_graph(ctx, X)
-    base = rp.rp_build_knn_base(ctx, data, KCAND, BASE_ALPHA, BASE_R)
+    if "base" in W:  # exact kNN plus random candidates (the mixture's clusters are far apart)
+        bw = W["base"]
+        base = rp.rp_build_knn_random_base(ctx, data, bw["kcand"], bw["nrand"], bw["seed"], BASE_ALPHA, BASE_R)
+    else:
+        base = rp.rp_build_knn_base(ctx, data, KCAND, BASE_ALPHA, BASE_R)
     base_rp, base_col = rp.rp_graph_export(ctx, base)
     gt, _ = rp.rp_knn(ctx, data, Q, k)
     fixture_s = time.perf_counter() - t0

@@ -271,6 +271,19 @@ rp_status rp_build_knn_base(rp_ctx *ctx, rp_graph data, int32_t kcand, double al
                             rp_graph *out);
 
 /*
+ * rp_build_knn_random_base: as rp_build_knn_base, with each point's
+ * candidates being its exact kcand nearest neighbours followed by nrand ids
+ * drawn uniformly from the other points (counter-based: splitmix64 of seed,
+ * the point and the draw), repeats dropped.  The random candidates give the
+ * base the long edges that a Vamana graph gets from its random start (§4.1),
+ * which a pure kNN graph of well-separated clusters lacks (its search cannot
+ * leave the start's cluster).  0 <= nrand <= 128.
+ * Errors: as rp_build_knn_base.
+ */
+rp_status rp_build_knn_random_base(rp_ctx *ctx, rp_graph data, int32_t kcand, int32_t nrand,
+                                   uint64_t seed, double alpha, int32_t R, rp_graph *out);
+
+/*
  * rp_graph_slice: the part of graph g that one of several GPUs tunes when the
  * nodes are split by contiguous id ranges (RP-Tuning treats every node on its
  * own, §3).  *out keeps the rows of nodes lo .. hi-1 with their edges, in

@@ -105,6 +105,7 @@ def load_library(path: str = LIB_PATH):
         "rp_knn": [P, i64, P, i64, i32, P, P, i32],
         "rp_recall": [P, P, i32, P, i32, i64, i32, ctypes.POINTER(i64), i32],
         "rp_build_knn_base": [P, i64, i32, dbl, i32, ctypes.POINTER(i64)],
+        "rp_build_knn_random_base": [P, i64, i32, i32, u64, dbl, i32, ctypes.POINTER(i64)],
         "rp_graph_free": [P, i64],
         "rp_stats": [P, ctypes.POINTER(rp_stats_t), i32],
         "rp_search_noalloc": [P, i32, i64, i32, P, P, i64, P, i64, i32, i32, P, P, P],
@@ -315,6 +316,13 @@ def rp_recall(ctx, found, truth, k: int) -> int:
 def rp_build_knn_base(ctx, data: int, kcand: int, alpha: float, R: int) -> int:
     out = ctypes.c_int64()
     _check(ctx, load_library().rp_build_knn_base(ctx, int(data), int(kcand), float(alpha), int(R), ctypes.byref(out)))
+    return out.value
+
+
+def rp_build_knn_random_base(ctx, data: int, kcand: int, nrand: int, seed: int, alpha: float, R: int) -> int:
+    out = ctypes.c_int64()
+    _check(ctx, load_library().rp_build_knn_random_base(ctx, int(data), int(kcand), int(nrand), int(seed),
+                                                        float(alpha), int(R), ctypes.byref(out)))
     return out.value
 
 

@@ -74,6 +74,13 @@ __device__ __forceinline__ bool canon_dominates(double A2, double d2a, double d2
 // d dimensions, including the bound of the binary64 canonical value itself
 // (folded in generously: (d + 8) ulps instead of (d + 2)).
 __device__ __forceinline__ float rel_bound(int d) { return (float)(d + 8) * 5.9604645e-08f; }
+// The same for a difference-form squared distance summed per 32-dimension
+// slice (index order within a slice, then the slice sums in order):
+// (min(d, 32) + ceil(d / 32) + 8) ulps.  Every single-precision distance of
+// the float paths is summed this way.
+__device__ __forceinline__ float slice_rel_bound(int d) {
+  return float((d < 32 ? d : 32) + (d + 31) / 32 + 8) * 5.9604645e-08f;
+}
 // Absolute allowance for terms that underflow (at most 2^-149 each).
 __device__ __forceinline__ float abs_bound(int d) { return (float)(d + 1) * 1.4012985e-45f * 4.0f; }
 

@@ -17,6 +17,7 @@ struct DevData {
   int64_t n = 0;
   int d = 0;
   int dtype = 0;
+  float scale = 1.f;  // a power of two with max |x| * scale <= 1 (float rows; 1 for uint8)
 };
 
 // A source graph for the prune kernels.
@@ -67,6 +68,8 @@ cudaError_t launch_clean_write(const int64_t* row_ptr, const int32_t* col, int64
                                const int64_t* new_row_ptr, int32_t* new_col, cudaStream_t s);
 cudaError_t launch_scan_counts(const int32_t* cnt, int64_t n, int64_t* row_ptr,
                                int64_t* block_sums, int32_t* max_deg, cudaStream_t s);
+cudaError_t launch_add_random_candidates(const int32_t* knn, int kk, int64_t n, int nr, uint64_t seed, int32_t* out,
+                                         cudaStream_t s);
 cudaError_t launch_slice_row_ptr(const int64_t* row_ptr, int64_t n, int64_t lo, int64_t hi, int64_t* out,
                                  cudaStream_t s);
 cudaError_t launch_medoid(const DevData& D, double* mean /* d */, double* block_best /* 2*nb */,
@@ -132,6 +135,8 @@ struct KnnTcLaunch {
   uint8_t* scratch = nullptr;  // knn_tc_scratch_bytes(), 256-byte aligned
 };
 bool knn_tc_eligible(int dtype, int d, int k);
+// max |x| over n float rows, as the bits of a non-negative float (atomicMax into *out)
+cudaError_t launch_maxabs_f32(const uint8_t* X, int64_t row_bytes, int64_t n, int d, unsigned* out, cudaStream_t s);
 size_t knn_tc_scratch_bytes(int dtype, int d, int64_t n, int64_t nq_ext, int num_sms);
 cudaError_t launch_knn_tc(const KnnTcLaunch& K, cudaStream_t s);
 

@@ -60,10 +60,6 @@ struct KnnSmem {
   alignas(16) unsigned char ps[PB * kPitch];
 };
 
-__device__ __forceinline__ float knn_rel_bound(int d) {
-  return float((d < 32 ? d : 32) + (d + 31) / 32 + 8) * 5.9604645e-08f;
-}
-
 template <int DT>
 __device__ __forceinline__ void acc_pair(uint2 x, uint2 y, unsigned& acc) {
   if constexpr (DT == kU8) {
@@ -84,7 +80,7 @@ __device__ __forceinline__ void acc_pair(uint2 x, uint2 y, unsigned& acc) {
 // rare.  Returns the end of the run holding position k - 1 (or -1).
 __device__ int fix_near_ties(const uint8_t* Xb, int64_t row_bytes, int d, DevStatus* status,
                              unsigned long long* b, int m, const float* qv, int64_t qg, int k = 0) {
-  const float E = knn_rel_bound(d), Eabs = abs_bound(d);
+  const float E = slice_rel_bound(d), Eabs = abs_bound(d);
   const float* X = reinterpret_cast<const float*>(Xb);
   const int64_t stride = row_bytes / 4;
   int i = 0;
@@ -677,6 +673,11 @@ cudaError_t launch_knn(const KnnLaunch& K, cudaStream_t s) {
     else knn_kernel<kU8><<<grid, kThreads, bytes, s>>>(a);
     if ((err = cudaGetLastError()) != cudaSuccess) return err;
   }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_maxabs_f32(const uint8_t* X, int64_t row_bytes, int64_t n, int d, unsigned* out, cudaStream_t s) {
+  if (n > 0) maxabs_kernel<<<1024, 256, 0, s>>>(X, row_bytes, n, d, out);
   return cudaGetLastError();
 }
 

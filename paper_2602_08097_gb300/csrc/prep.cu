@@ -361,6 +361,39 @@ cudaError_t launch_scan_counts(const int32_t* cnt, int64_t n, int64_t* row_ptr, 
 
 int64_t medoid_blocks(int64_t n) { return std::min<int64_t>((n + 255) / 256, 2048); }
 
+// Candidate rows of width kk + nr: the kk nearest neighbours of p, then nr ids
+// drawn uniformly from the other points by a counter-based generator
+// (splitmix64 of seed, p and j), repeated ids left for the cleaning pass.
+__device__ __forceinline__ uint64_t splitmix64(uint64_t x) {
+  x += 0x9E3779B97F4A7C15ull;
+  x = (x ^ (x >> 30)) * 0xBF58476D1CE4E5B9ull;
+  x = (x ^ (x >> 27)) * 0x94D049BB133111EBull;
+  return x ^ (x >> 31);
+}
+
+__global__ void add_random_candidates_kernel(const int32_t* __restrict__ knn, int kk, int64_t n, int nr,
+                                             uint64_t seed, int32_t* __restrict__ out) {
+  const int w = kk + nr;
+  for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n * w; i += int64_t(gridDim.x) * blockDim.x) {
+    const int64_t p = i / w;
+    const int j = int(i % w);
+    if (j < kk) {
+      out[i] = knn[p * kk + j];
+    } else {
+      const uint64_t h = splitmix64(seed ^ splitmix64(uint64_t(p) * 131ull + uint64_t(j - kk)));
+      int64_t v = int64_t(h % uint64_t(n - 1));
+      if (v >= p) ++v;  // every point but p
+      out[i] = int32_t(v);
+    }
+  }
+}
+
+cudaError_t launch_add_random_candidates(const int32_t* knn, int kk, int64_t n, int nr, uint64_t seed, int32_t* out,
+                                         cudaStream_t s) {
+  add_random_candidates_kernel<<<1024, 256, 0, s>>>(knn, kk, n, nr, seed, out);
+  return cudaGetLastError();
+}
+
 // row_ptr of the slice of a graph that keeps the rows of [lo, hi): every row
 // outside is empty and the kept rows keep their edges (col starts at lo's).
 __global__ void slice_row_ptr_kernel(const int64_t* __restrict__ row_ptr, int64_t n, int64_t lo, int64_t hi,

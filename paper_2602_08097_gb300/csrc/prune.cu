@@ -25,6 +25,8 @@
 // Tensor-core path: m <= 64 (two nodes per 128-thread CTA, one 128 x 128
 // MMA) and 64 < m <= 128 (one node per CTA).  Larger degrees take the generic
 // path (one node per 256-thread CTA, lazy CUDA-core distances).
+#include <cmath>
+
 #include "internal.h"
 #include "tc.cuh"
 
@@ -47,6 +49,10 @@ struct PruneArgs {
   int32_t A[kMaxTargets];
   int32_t R[kMaxTargets];
   float inv_A2[kMaxTargets];  // 1 / A^2 rounded: a starting estimate for exact_threshold
+  float scale;                // float rows enter the f16 Gram as scale * x (a power of two: exact)
+  float inv_s;                // 1 / scale
+  float inv_s2;               // 1 / scale^2: the Gram back in the rows' units (exact)
+  float sqrt_d;               // sqrt(d), rounded up
   int32_t* out_col[kMaxTargets];
   int32_t* out_cnt[kMaxTargets];
   DevStatus* status;
@@ -103,13 +109,19 @@ struct Acc<kF32> {
 };
 
 // Full single-precision difference-form d2 between two global rows.
+// Float rows are summed per 32-dimension slice (slice_rel_bound).
 template <int DT>
 __device__ __forceinline__ typename Acc<DT>::T row_d2(const uint8_t* a, const uint8_t* b,
                                                        int64_t row_bytes) {
   typename Acc<DT>::T acc = 0;
   const uint4* pa = reinterpret_cast<const uint4*>(a);
   const uint4* pb = reinterpret_cast<const uint4*>(b);
-  for (int64_t c = 0; c < row_bytes / 16; ++c) acc = Acc<DT>::step4(__ldg(pa + c), __ldg(pb + c), acc);
+  const int64_t nv = row_bytes / 16;
+  for (int64_t c0 = 0; c0 < nv; c0 += 8) {
+    typename Acc<DT>::T part = 0;
+    for (int64_t c = c0; c < (c0 + 8 < nv ? c0 + 8 : nv); ++c) part = Acc<DT>::step4(__ldg(pa + c), __ldg(pb + c), part);
+    acc += part;
+  }
   return acc;
 }
 
@@ -246,7 +258,7 @@ __global__ void __launch_bounds__(160, tc_min_ctas<MAXM, TB>()) prune_tc_kernel(
   uint64_t* mbar = reinterpret_cast<uint64_t*>(smem_raw + L::off_misc + 128);
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem_raw + L::off_misc + 144);
   auto slot_base = [&](int s, int g) { return smem_raw + L::off_slots + (size_t(s) * NG + g) * L::s_bytes; };
-  const float E_rel = rel_bound(a.d), E_abs = abs_bound(a.d);
+  const float E_rel = slice_rel_bound(a.d), E_abs = abs_bound(a.d);
   const int count = *a.count;
 
   if (warp == 0) tmem_alloc(tmem_slot, 128);  // 128 of the SM's 512 TMEM columns, for the kernel's life
@@ -268,11 +280,15 @@ __global__ void __launch_bounds__(160, tc_min_ctas<MAXM, TB>()) prune_tc_kernel(
     float* qlo = reinterpret_cast<float*>(pb + L::p_qlo);
     float* qhi = reinterpret_cast<float*>(pb + L::p_qhi);
     const uint32_t tmem = *tmem_slot;
-    // uint8 operands go in as f16 (exact for 0..255 and cheaper to convert), float ones as bf16
-    constexpr uint32_t idesc = DT == kU8 ? umma_idesc_f16(128, 128) : umma_idesc_bf16(128, 128);
+    // operands go in as f16: uint8 values exactly, float rows scaled by a power
+    // of two into [-1, 1] and rounded
+    constexpr uint32_t idesc = umma_idesc_f16(128, 128);
     const int64_t elems = a.row_bytes / (DT == kU8 ? 1 : 4);  // padded dims per row
     const int nslices = int((elems + 127) / 128);
-    const float eps_ip = 0.0078125f + 1.52587890625e-05f + float(a.d) * 2.384185791015625e-07f;
+    // f16 Gram of scaled rows: |G~ - G| <= eps_ip |u||v| + 2^-25 sqrt(d) (|u| + |v|) / scale (f16
+    // rounding of both operands, u = 2^-11, subnormals, f32 accumulation with a factor 2 allowance)
+    const float eps_ip = 9.765625e-04f + 4.76837158e-07f + float(a.d) * 2.384185791015625e-07f;
+    const float sub_abs = a.sqrt_d * 1.001f * 5.9604645e-08f * a.inv_s;  // twice 2^-25 sqrt(d) / scale
     const float eps_n = float(a.d + 12) * 5.9604645e-08f;
     const float err_abs = float(a.d) * 2.3509887e-38f;  // underflowed products, 2^-125 each
     uint32_t phase = 0;
@@ -360,12 +376,17 @@ __global__ void __launch_bounds__(160, tc_min_ctas<MAXM, TB>()) prune_tc_kernel(
         }
       } else {
         if (live_row) {
+          float part = 0.f;  // the key is summed per 32-dimension slice (slice_rel_bound)
           for (int c = 0; c < int(elems / 8); ++c) {
             const uint4* xq = reinterpret_cast<const uint4*>(xrow) + 2 * c;
             const uint4* pq = reinterpret_cast<const uint4*>(prow) + 2 * c;
             const uint4 x0 = __ldg(xq), x1 = __ldg(xq + 1), y0 = __ldg(pq), y1 = __ldg(pq + 1);
-            kacc = Acc<kF32>::step4(x0, y0, kacc);
-            kacc = Acc<kF32>::step4(x1, y1, kacc);
+            part = Acc<kF32>::step4(x0, y0, part);
+            part = Acc<kF32>::step4(x1, y1, part);
+            if ((c & 3) == 3 || c == int(elems / 8) - 1) {
+              kacc += part;
+              part = 0.f;
+            }
             const float xv[8] = {__uint_as_float(x0.x), __uint_as_float(x0.y), __uint_as_float(x0.z),
                                  __uint_as_float(x0.w), __uint_as_float(x1.x), __uint_as_float(x1.y),
                                  __uint_as_float(x1.z), __uint_as_float(x1.w)};
@@ -480,10 +501,10 @@ __global__ void __launch_bounds__(160, tc_min_ctas<MAXM, TB>()) prune_tc_kernel(
               x1 = __ldg(xq + 1);
             }
             *reinterpret_cast<uint4*>(opnd + (c * 16 + orow / 8) * 128 + (orow % 8) * 16) =
-                make_uint4(pack_bf16x2(__uint_as_float(x0.x), __uint_as_float(x0.y)),
-                           pack_bf16x2(__uint_as_float(x0.z), __uint_as_float(x0.w)),
-                           pack_bf16x2(__uint_as_float(x1.x), __uint_as_float(x1.y)),
-                           pack_bf16x2(__uint_as_float(x1.z), __uint_as_float(x1.w)));
+                make_uint4(pack_f16x2(__uint_as_float(x0.x) * a.scale, __uint_as_float(x0.y) * a.scale),
+                           pack_f16x2(__uint_as_float(x0.z) * a.scale, __uint_as_float(x0.w) * a.scale),
+                           pack_f16x2(__uint_as_float(x1.x) * a.scale, __uint_as_float(x1.y) * a.scale),
+                           pack_f16x2(__uint_as_float(x1.z) * a.scale, __uint_as_float(x1.w) * a.scale));
           }
         }
         const bool last = sl == nslices - 1;
@@ -580,12 +601,13 @@ __global__ void __launch_bounds__(160, tc_min_ctas<MAXM, TB>()) prune_tc_kernel(
               for (int j = 0; j < 32; ++j) {
                 const int c = c0 + j;
                 if (c >= m) break;
-                const float G = __uint_as_float(v[j]);
+                const float G = __uint_as_float(v[j]) * a.inv_s2;  // exact: a power of two
                 const unsigned long long bit = 1ull << (c & 63);
                 const int w = c >> 6;
                 const float nc = float(norm[c]);
                 const float dv = (nt + nc) - 2.f * G;
-                const float err = 2.f * eps_ip * st * sn[c] * 1.0009765625f + eps_n * (nt + nc) + err_abs;
+                const float err = 2.f * eps_ip * st * sn[c] * 1.0009765625f + sub_abs * (st + sn[c]) +
+                                  eps_n * (nt + nc) + err_abs;
                 const float hi = (dv + err) * 1.0000005f, lo = (dv - err) * 0.9999995f;
 #pragma unroll
                 for (int u = 0; u < TB; ++u) {
@@ -1110,6 +1132,10 @@ cudaError_t launch_prune(const PruneLaunch& L, cudaStream_t s) {
   PruneArgs a{};
   a.X = L.data.X;
   a.row_bytes = L.data.row_bytes;
+  a.scale = L.data.scale;
+  a.inv_s = 1.f / L.data.scale;
+  a.inv_s2 = a.inv_s * a.inv_s;
+  a.sqrt_d = std::sqrt(float(L.data.d)) * 1.0001f;
   a.d = L.data.d;
   a.row_ptr = L.row_ptr;
   a.col = L.col;

@@ -25,6 +25,7 @@ struct Dataset {
   int64_t n = 0;
   int d = 0;
   int dtype = 0;
+  float scale = 1.f;  // power of two bringing max |x| to at most 1 (float rows)
   size_t bytes = 0;
   DevData dev() const {
     DevData D;
@@ -33,6 +34,7 @@ struct Dataset {
     D.n = n;
     D.d = d;
     D.dtype = dtype;
+    D.scale = scale;
     return D;
   }
 };
@@ -619,6 +621,118 @@ rp_status search_impl(rp_ctx* c, const rp_graph* graphs, int32_t ngraphs, const 
   return RP_OK;
 }
 
+rp_status build_base(rp_ctx* c, rp_graph data, int32_t kcand, int32_t nrand, uint64_t seed, double alpha, int32_t R,
+                     rp_graph* out) {
+  Graph* G = find_graph(c, data);
+  if (!G) return fail(c, RP_ENOTFOUND, "unknown graph %lld", (long long)data);
+  if (!out) return fail(c, RP_EINVAL, "null out");
+  if (kcand < 1 || kcand > 128) return fail(c, RP_EINVAL, "kcand=%d outside [1, 128]", kcand);
+  if (nrand < 0 || nrand > 128) return fail(c, RP_EINVAL, "nrand=%d outside [0, 128]", nrand);
+  const int64_t n = G->n;
+  const int kk = int(std::min<int64_t>(kcand, n - 1));
+  const int nr = n > 1 ? nrand : 0;
+  Graph* K = new Graph;
+  K->data = G->data;
+  K->n = n;
+  K->col_cap = std::max<int64_t>(n * kk, 1);
+  K->start = G->start;
+  K->max_deg_bound = kk + nr;
+  K->nnz = n * kk;
+  rp_status s = dalloc(c, reinterpret_cast<void**>(&K->row_ptr), size_t(n + 1) * 8);
+  if (s == RP_OK) s = dalloc(c, reinterpret_cast<void**>(&K->col), size_t(K->col_cap) * 4);
+  if (s != RP_OK) {
+    free_graph_mem(c, K);
+    return s;
+  }
+  if (kk > 0 && (s = run_knn(c, *G->data, nullptr, n, kk, K->col, nullptr)) != RP_OK) {
+    free_graph_mem(c, K);
+    return s;
+  }
+  std::vector<int64_t> hrp(size_t(n + 1));
+  for (int64_t p = 0; p <= n; ++p) hrp[size_t(p)] = p * kk;
+  cudaError_t ce = cudaMemcpyAsync(K->row_ptr, hrp.data(), size_t(n + 1) * 8, cudaMemcpyHostToDevice, c->stream);
+  if (ce == cudaSuccess && nr > 0) {
+    // rows of kNN ids followed by nr seeded random ids, then repeated ids dropped
+    const int w = kk + nr;
+    int32_t* raw = nullptr;
+    int64_t* rp_raw = nullptr;
+    int32_t* cnt = nullptr;
+    int64_t* bsum = nullptr;
+    int32_t* maxd = nullptr;
+    unsigned long long* dropped = nullptr;
+    int32_t* col2 = nullptr;
+    const int64_t nblk = (n + 4095) / 4096;
+    auto release = [&]() {
+      dfree(c, raw, size_t(n * w) * 4);
+      dfree(c, rp_raw, size_t(n + 1) * 8);
+      dfree(c, cnt, size_t(n) * 4);
+      dfree(c, bsum, size_t(nblk) * 8);
+      dfree(c, maxd, 8);
+      dfree(c, dropped, 16);
+    };
+    s = dalloc(c, reinterpret_cast<void**>(&raw), size_t(n * w) * 4);
+    if (s == RP_OK) s = dalloc(c, reinterpret_cast<void**>(&rp_raw), size_t(n + 1) * 8);
+    if (s == RP_OK) s = dalloc(c, reinterpret_cast<void**>(&cnt), size_t(n) * 4);
+    if (s == RP_OK) s = dalloc(c, reinterpret_cast<void**>(&bsum), size_t(nblk) * 8);
+    if (s == RP_OK) s = dalloc(c, reinterpret_cast<void**>(&maxd), 8);
+    if (s == RP_OK) s = dalloc(c, reinterpret_cast<void**>(&dropped), 16);
+    if (s == RP_OK) s = dalloc(c, reinterpret_cast<void**>(&col2), size_t(n * w) * 4);
+    if (s != RP_OK) {
+      release();
+      free_graph_mem(c, K);
+      return s;
+    }
+    for (int64_t p = 0; p <= n; ++p) hrp[size_t(p)] = p * w;
+    ce = cudaMemcpyAsync(rp_raw, hrp.data(), size_t(n + 1) * 8, cudaMemcpyHostToDevice, c->stream);
+    if (ce == cudaSuccess) ce = launch_add_random_candidates(K->col, kk, n, nr, seed, raw, c->stream);
+    if (ce == cudaSuccess) ce = cudaMemsetAsync(dropped, 0, 16, c->stream);
+    if (ce == cudaSuccess) ce = launch_clean_count(rp_raw, raw, n, cnt, dropped, c->stream);
+    if (ce == cudaSuccess) ce = launch_scan_counts(cnt, n, K->row_ptr, bsum, maxd, c->stream);
+    if (ce == cudaSuccess) ce = launch_clean_write(rp_raw, raw, n, K->row_ptr, col2, c->stream);
+    if (ce == cudaSuccess) ce = cudaStreamSynchronize(c->stream);
+    release();
+    dfree(c, K->col, size_t(K->col_cap) * 4);
+    K->col = col2;
+    K->col_cap = std::max<int64_t>(n * w, 1);
+    K->nnz = -1;
+    c->kernel_launches += 5;
+  }
+  if (ce == cudaSuccess) ce = cudaStreamSynchronize(c->stream);
+  if (ce != cudaSuccess) {
+    free_graph_mem(c, K);
+    return fail(c, RP_ECUDA, "knn graph: %s", cudaGetErrorString(ce));
+  }
+  if ((s = check_device_status(c)) != RP_OK) {
+    free_graph_mem(c, K);
+    return s;
+  }
+  const rp_graph kid = add_graph(c, K);
+  rp_graph res = 0;
+  s = tune_impl(c, kid, &alpha, &R, 1, RP_SORTED, &res, false);
+  auto it = c->graphs.find(kid);
+  free_graph_mem(c, it->second);
+  c->graphs.erase(it);
+  if (s != RP_OK) return s;
+  // The result holds the candidate graph's capacity (n x kcand ids); keep only
+  // its edges, since every graph tuned from it takes its capacity too.
+  Graph* B = find_graph(c, res);
+  CUDA_TRY(c, cudaMemcpyAsync(&B->nnz, B->row_ptr + B->n, 8, cudaMemcpyDeviceToHost, c->stream));
+  CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  const int64_t cap = std::max<int64_t>(B->nnz, 1);
+  if (cap < B->col_cap) {
+    int32_t* col = nullptr;
+    if (dalloc(c, reinterpret_cast<void**>(&col), size_t(cap) * 4) == RP_OK) {
+      CUDA_TRY(c, cudaMemcpyAsync(col, B->col, size_t(cap) * 4, cudaMemcpyDeviceToDevice, c->stream));
+      dfree(c, B->col, size_t(B->col_cap) * 4);
+      B->col = col;
+      B->col_cap = cap;
+      B->bytes = size_t(B->n + 1) * 8 + size_t(cap) * 4;
+    }
+  }
+  *out = res;
+  return RP_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -727,6 +841,20 @@ rp_status rp_load_graph(rp_ctx* c, const void* vectors, int32_t dtype, int64_t n
   if ((s = upload_rows(c, D->X, D->row_bytes, vectors, n, d, dtype, mem_flags)) != RP_OK) return fail_free(s);
   if (launch_check_finite(D->dev(), c->status, c->stream) != cudaSuccess)
     return fail_free(fail(c, RP_ECUDA, "check_finite launch failed"));
+  if (dtype == RP_F32) {
+    // the power-of-two scale under which float rows enter the f16 Gram
+    unsigned mb = 0;
+    CUDA_TRY(c, cudaMemsetAsync(c->work, 0, 4, c->stream));
+    CUDA_TRY(c, launch_maxabs_f32(D->X, D->row_bytes, n, d, c->work, c->stream));
+    CUDA_TRY(c, cudaMemcpyAsync(&mb, c->work, 4, cudaMemcpyDeviceToHost, c->stream));
+    CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    float mx = 0.f;
+    memcpy(&mx, &mb, 4);
+    int e = 0;
+    if (mx > 0.f && std::isfinite(mx)) std::frexp(mx, &e);  // mx < 2^e
+    D->scale = std::ldexp(1.f, -e);
+    c->kernel_launches += 1;
+  }
 
   Graph* G = new Graph;
   G->data = D;
@@ -1074,66 +1202,15 @@ rp_status rp_build_knn_base(rp_ctx* c, rp_graph data, int32_t kcand, double alph
   if (!c) return RP_EINVAL;
   std::lock_guard<std::mutex> lk(c->mu);
   cudaSetDevice(c->device);
-  Graph* G = find_graph(c, data);
-  if (!G) return fail(c, RP_ENOTFOUND, "unknown graph %lld", (long long)data);
-  if (!out) return fail(c, RP_EINVAL, "null out");
-  if (kcand < 1 || kcand > 128) return fail(c, RP_EINVAL, "kcand=%d outside [1, 128]", kcand);
-  const int64_t n = G->n;
-  const int kk = int(std::min<int64_t>(kcand, n - 1));
-  Graph* K = new Graph;
-  K->data = G->data;
-  K->n = n;
-  K->col_cap = std::max<int64_t>(n * kk, 1);
-  K->start = G->start;
-  K->max_deg_bound = kk;
-  K->nnz = n * kk;
-  rp_status s = dalloc(c, reinterpret_cast<void**>(&K->row_ptr), size_t(n + 1) * 8);
-  if (s == RP_OK) s = dalloc(c, reinterpret_cast<void**>(&K->col), size_t(K->col_cap) * 4);
-  if (s != RP_OK) {
-    free_graph_mem(c, K);
-    return s;
-  }
-  if (kk > 0 && (s = run_knn(c, *G->data, nullptr, n, kk, K->col, nullptr)) != RP_OK) {
-    free_graph_mem(c, K);
-    return s;
-  }
-  std::vector<int64_t> hrp(size_t(n + 1));
-  for (int64_t p = 0; p <= n; ++p) hrp[size_t(p)] = p * kk;
-  cudaError_t ce = cudaMemcpyAsync(K->row_ptr, hrp.data(), size_t(n + 1) * 8, cudaMemcpyHostToDevice, c->stream);
-  if (ce == cudaSuccess) ce = cudaStreamSynchronize(c->stream);
-  if (ce != cudaSuccess) {
-    free_graph_mem(c, K);
-    return fail(c, RP_ECUDA, "knn graph: %s", cudaGetErrorString(ce));
-  }
-  if ((s = check_device_status(c)) != RP_OK) {
-    free_graph_mem(c, K);
-    return s;
-  }
-  const rp_graph kid = add_graph(c, K);
-  rp_graph res = 0;
-  s = tune_impl(c, kid, &alpha, &R, 1, RP_SORTED, &res, false);
-  auto it = c->graphs.find(kid);
-  free_graph_mem(c, it->second);
-  c->graphs.erase(it);
-  if (s != RP_OK) return s;
-  // The result holds the candidate graph's capacity (n x kcand ids); keep only
-  // its edges, since every graph tuned from it takes its capacity too.
-  Graph* B = find_graph(c, res);
-  CUDA_TRY(c, cudaMemcpyAsync(&B->nnz, B->row_ptr + B->n, 8, cudaMemcpyDeviceToHost, c->stream));
-  CUDA_TRY(c, cudaStreamSynchronize(c->stream));
-  const int64_t cap = std::max<int64_t>(B->nnz, 1);
-  if (cap < B->col_cap) {
-    int32_t* col = nullptr;
-    if (dalloc(c, reinterpret_cast<void**>(&col), size_t(cap) * 4) == RP_OK) {
-      CUDA_TRY(c, cudaMemcpyAsync(col, B->col, size_t(cap) * 4, cudaMemcpyDeviceToDevice, c->stream));
-      dfree(c, B->col, size_t(B->col_cap) * 4);
-      B->col = col;
-      B->col_cap = cap;
-      B->bytes = size_t(B->n + 1) * 8 + size_t(cap) * 4;
-    }
-  }
-  *out = res;
-  return RP_OK;
+  return build_base(c, data, kcand, 0, 0, alpha, R, out);
+}
+
+rp_status rp_build_knn_random_base(rp_ctx* c, rp_graph data, int32_t kcand, int32_t nrand, uint64_t seed,
+                                   double alpha, int32_t R, rp_graph* out) {
+  if (!c) return RP_EINVAL;
+  std::lock_guard<std::mutex> lk(c->mu);
+  cudaSetDevice(c->device);
+  return build_base(c, data, kcand, nrand, seed, alpha, R, out);
 }
 
 rp_status rp_set_knn_method(rp_ctx* c, int32_t method) {

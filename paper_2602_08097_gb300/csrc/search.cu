@@ -22,8 +22,8 @@
 // next; the L closest of a union are the L closest of the L closest of its
 // parts, so this equals adding the whole list and cutting once.
 //
-// Ordering: uint8 distances are exact integers.  float32 distances carry a
-// rigorous single-precision error bound; when two intervals overlap, both
+// Ordering: uint8 distances are exact integers.  float32 distances (summed
+// per 32-dimension slice) carry a rigorous single-precision error bound; when two intervals overlap, both
 // distances are recomputed in binary64 (index order, no fused multiply-add)
 // and compared there, so every comparison agrees with the binary64 reading.
 #include <cfloat>
@@ -129,14 +129,20 @@ __device__ __forceinline__ unsigned dist_bits(const uint8_t* __restrict__ q, con
     }
     return acc;
   } else {
+    // summed per 32-dimension slice (slice_rel_bound)
     float acc = 0.f;
-    for (int64_t c = 0; c < row_bytes / 16; ++c) {
-      const uint4 a = pq[c], b = __ldg(px + c);
-      float t;
-      t = __uint_as_float(a.x) - __uint_as_float(b.x); acc = fmaf(t, t, acc);
-      t = __uint_as_float(a.y) - __uint_as_float(b.y); acc = fmaf(t, t, acc);
-      t = __uint_as_float(a.z) - __uint_as_float(b.z); acc = fmaf(t, t, acc);
-      t = __uint_as_float(a.w) - __uint_as_float(b.w); acc = fmaf(t, t, acc);
+    for (int64_t c0 = 0; c0 < row_bytes / 16; c0 += 8) {
+      float part = 0.f;
+      const int64_t c1 = c0 + 8 < row_bytes / 16 ? c0 + 8 : row_bytes / 16;
+      for (int64_t c = c0; c < c1; ++c) {
+        const uint4 a = pq[c], b = __ldg(px + c);
+        float t;
+        t = __uint_as_float(a.x) - __uint_as_float(b.x); part = fmaf(t, t, part);
+        t = __uint_as_float(a.y) - __uint_as_float(b.y); part = fmaf(t, t, part);
+        t = __uint_as_float(a.z) - __uint_as_float(b.z); part = fmaf(t, t, part);
+        t = __uint_as_float(a.w) - __uint_as_float(b.w); part = fmaf(t, t, part);
+      }
+      acc += part;
     }
     return __float_as_uint(acc);
   }
@@ -181,7 +187,7 @@ __global__ void __launch_bounds__(kWarps * 32) search_kernel(SearchArgs a) {
                      a.cache_bits);
   const int cshift = 32 - a.cache_bits;
   const int centries = 1 << a.cache_bits;
-  const float E = rel_bound(a.d), Eabs = abs_bound(a.d);
+  const float E = slice_rel_bound(a.d), Eabs = abs_bound(a.d);
   const double qnan = __longlong_as_double(0x7ff8000000000000ll);
 
   for (;;) {

@@ -109,3 +109,38 @@ def test_method_limits(ctx):
         rp.rp_knn(ctx, gg, G[:3].copy(), 10)
     rp.rp_set_knn_method(ctx, rp.RP_KNN_AUTO)
     rp.rp_graph_free(ctx, gg)
+
+
+def _splitmix64(x):
+    # splitmix64 (Steele, Lea and Flood; Vigna's reference form), on uint64 arrays
+    x = (x + np.uint64(0x9E3779B97F4A7C15)).astype(np.uint64)
+    x = ((x ^ (x >> np.uint64(30))) * np.uint64(0xBF58476D1CE4E5B9)).astype(np.uint64)
+    x = ((x ^ (x >> np.uint64(27))) * np.uint64(0x94D049BB133111EB)).astype(np.uint64)
+    return x ^ (x >> np.uint64(31))
+
+
+@pytest.mark.parametrize("name", ["deep", "sift"])
+def test_random_candidate_base_matches_the_oracle(ctx, name):
+    n, kk, nr, seed = 3000, 32, 16, 77
+    X = datagen.dataset(name, n)
+    g = rp.rp_load_graph(ctx, X)
+    b = rp.rp_build_knn_random_base(ctx, g, kk, nr, seed, 1.2, 40)
+    got = rp.rp_graph_export(ctx, b)
+    # the candidate rows: exact kNN, then nr draws over the other points
+    knn_ids, _ = oracle.knn(X, kk, qid=np.arange(n))
+    with np.errstate(over="ignore"):
+        p = np.repeat(np.arange(n, dtype=np.uint64), nr)
+        j = np.tile(np.arange(nr, dtype=np.uint64), n)
+        h = _splitmix64(np.uint64(seed) ^ _splitmix64(p * np.uint64(131) + j))
+    v = (h % np.uint64(n - 1)).astype(np.int64).reshape(n, nr)
+    v += v >= np.arange(n)[:, None]
+    cand = np.concatenate([knn_ids.astype(np.int64), v], axis=1).astype(np.int32)
+    row_ptr = np.arange(n + 1, dtype=np.int64) * (kk + nr)
+    ref = oracle.rp_tune(X, row_ptr, cand.ravel(), 1.2, 40)
+    assert np.array_equal(got[0], ref[0]) and np.array_equal(got[1], ref[1])
+    # the base now links far points: some kept edge is not among the kNN candidates
+    assert any(set(got[1][got[0][q]:got[0][q + 1]]) - set(knn_ids[q]) for q in range(0, n, 10))
+    with pytest.raises(rp.RPError):
+        rp.rp_build_knn_random_base(ctx, g, kk, 200, seed, 1.2, 40)
+    rp.rp_graph_free(ctx, b)
+    rp.rp_graph_free(ctx, g)
