@@ -333,6 +333,10 @@ def run_ours(args):
         outs, _ = step(True)
         free(outs)
     tuned_cfg = rp.rp_stats(ctx)  # the autotuner's pick for this source and target count
+    st_tiers = rp.rp_stats(ctx, reset=True)  # decision tiers over the whole run so far
+    tiers = {"f32_rechecks_per_node_target": st_tiers["f32_rechecks"] / max(st_tiers["nodes_pruned"], 1),
+             "fp64_decisions_per_node_target": st_tiers["fp64_decisions"] / max(st_tiers["nodes_pruned"], 1),
+             "fp64_sort_keys": st_tiers["fp64_sort_keys"], "fp64_search_dists": st_tiers["fp64_search_dists"]}
     prune_ms = statistics.mean(stats_acc["prune_ms"])
     if not prune_ms > 0:
         raise RuntimeError(f"prune kernel time not measured: {stats_acc}")
@@ -478,6 +482,7 @@ def run_ours(args):
             "tune_plain_nodes_per_s_per_alpha": n * T / (tp / 1000.0),
             "batched_over_plain": tp / tb,
             "phase_ms": {"prune": prune_ms, "emit": emit_ms, f"search_{T}x": search_ms},
+            "decision_tiers": tiers,
             "prune_config": {"tile0": tuned_cfg["tile0"], "ctas_per_sm": tuned_cfg["ctas_per_sm"],
                              "chosen_by": "autotuner (rp_set_tuning RP_TUNING_AUTO)"},
             "search_qps": T * nq / (search_ms / 1000.0),

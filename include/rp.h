@@ -326,6 +326,7 @@ typedef struct {
   int32_t ctas_per_sm;
   int32_t knn_method;          /* path of the last rp_knn / rp_build_knn_base (RP_KNN_*) */
   int32_t pad_;
+  int64_t f32_rechecks;        /* float domination tests redone in single-precision difference form */
 } rp_stats_t;
 
 rp_status rp_stats(rp_ctx *ctx, rp_stats_t *out, int32_t reset);

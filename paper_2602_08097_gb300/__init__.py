@@ -45,7 +45,8 @@ class rp_stats_t(ctypes.Structure):
                 ("kernel_launches", ctypes.c_int64), ("last_prune_ms", ctypes.c_float),
                 ("last_emit_ms", ctypes.c_float), ("last_search_ms", ctypes.c_float),
                 ("tile0", ctypes.c_int32), ("ctas_per_sm", ctypes.c_int32),
-                ("knn_method", ctypes.c_int32), ("pad_", ctypes.c_int32)]
+                ("knn_method", ctypes.c_int32), ("pad_", ctypes.c_int32),
+                ("f32_rechecks", ctypes.c_int64)]
 
 
 class rp_request_info(ctypes.Structure):

@@ -293,6 +293,7 @@ __global__ void __launch_bounds__(160, tc_min_ctas<MAXM, TB>()) prune_tc_kernel(
     const float err_abs = float(a.d) * 2.3509887e-38f;  // underflowed products, 2^-125 each
     uint32_t phase = 0;
     bool dead = false;
+    unsigned long long n_rechecks = 0;  // single-precision rechecks, added to the status once at the end
     for (int k = 0;; ++k) {
       const int s = k & 1;
       named_sync(kBarFree + s, 160);  // the consumer is done with this slot
@@ -622,7 +623,7 @@ __global__ void __launch_bounds__(160, tc_min_ctas<MAXM, TB>()) prune_tc_kernel(
                     const int64_t A2 = int64_t(a.A[u]) * a.A[u];
                     const float d2a = row_d2<kF32>(a.X + int64_t(ids[t]) * a.row_bytes,
                                                    a.X + int64_t(ids[c]) * a.row_bytes, a.row_bytes);
-                    atomicAdd(&a.status->spare[2], 1ull);
+                    ++n_rechecks;
                     const int rr = sure_dominates(float(A2), d2a, key[c], E_rel, E_abs);
                     dom = rr >= 0 ? (rr == 1) : tier3_dominates(a, ids[t], ids[c], p, &key64[c], double(A2));
                   }
@@ -646,6 +647,11 @@ __global__ void __launch_bounds__(160, tc_min_ctas<MAXM, TB>()) prune_tc_kernel(
       named_sync(kBarProd, 128);  // every producer's masks and TMEM reads are done
       tc_fence_after();
       bar_arrive(kBarFull + s, 160);
+    }
+    if constexpr (DT == kF32) {
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) n_rechecks += __shfl_xor_sync(0xffffffffu, n_rechecks, o);
+      if (lane == 0 && n_rechecks) atomicAdd(&a.status->spare[2], n_rechecks);
     }
   } else {
     // =========================== consumer warp ===========================

@@ -1263,6 +1263,7 @@ rp_status rp_stats(rp_ctx* c, rp_stats_t* out, int32_t reset) {
   out->tile0 = c->last_tile0;
   out->ctas_per_sm = c->last_ctas;
   out->knn_method = c->last_knn_method;
+  out->f32_rechecks = int64_t(h.spare[2]);
   if (reset) {
     DevStatus z;
     memset(&z, 0, sizeof z);
