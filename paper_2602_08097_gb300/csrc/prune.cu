@@ -161,18 +161,18 @@ __device__ __forceinline__ bool tier3_dominates(const PruneArgs& a, int32_t u, i
 // Shared-memory plan of prune_tc_kernel.  Per node group the producer warps
 // keep norms and thresholds; per pipeline slot (2) and group they hand the
 // consumer warp the candidate ids, keys, binary64 key cache and masks.
-template <int MAXM, int TB>
+template <int MAXM, int TB, int NOP>
 struct TcLayout {
   static constexpr int NG = 128 / MAXM;
   static constexpr int MW = MAXM / 64;
-  static constexpr size_t off_opnd = 0;  // 128 rows x 128 dims bf16 = 32 KB
+  static constexpr size_t off_opnd = 0;  // NOP operands of 128 rows x 128 dims f16 = 32 KB each
   // per (slot, group)
   static constexpr size_t s_key64 = 0;
   static constexpr size_t s_masks = s_key64 + size_t(MAXM) * 8;  // [TB][MAXM][MW] u64
   static constexpr size_t s_ids = s_masks + size_t(TB) * MAXM * MW * 8;
   static constexpr size_t s_key = s_ids + size_t(MAXM) * 4;
   static constexpr size_t s_bytes = s_key + size_t(MAXM) * 4;
-  static constexpr size_t off_slots = 128 * 128 * 2;
+  static constexpr size_t off_slots = size_t(NOP) * 128 * 128 * 2;
   // per group, producer side
   static constexpr size_t p_norm = 0;
   static constexpr size_t p_sn = p_norm + size_t(MAXM) * 4;
@@ -234,12 +234,15 @@ __device__ __forceinline__ bool prod_sync_or(bool flag) {
 // 4 CTAs per SM (the TMEM limit) need at most 96 registers per thread; the
 // kernels with more targets per launch, or one 128-candidate node per MMA
 // (more shared memory per CTA), trade that for registers.
-template <int MAXM, int TB>
-constexpr int tc_min_ctas() { return (MAXM == 64 && TB <= 4) ? 4 : 2; }
+template <int DT, int MAXM, int TB>
+constexpr int tc_min_ctas() { return (DT == kU8 && MAXM == 64 && TB <= 4) ? 4 : 2; }
 
 template <int DT, int MAXM, int TB>
-__global__ void __launch_bounds__(160, tc_min_ctas<MAXM, TB>()) prune_tc_kernel(PruneArgs a) {
-  using L = TcLayout<MAXM, TB>;
+__global__ void __launch_bounds__(160, tc_min_ctas<DT, MAXM, TB>()) prune_tc_kernel(PruneArgs a) {
+  // float rows: two f16 operands (hi, lo) and two accumulators (256 TMEM columns)
+  constexpr int kNop = DT == kF32 ? 2 : 1;
+  constexpr uint32_t kTmemCols = DT == kF32 ? 256u : 128u;
+  using L = TcLayout<MAXM, TB, kNop>;
   using AT = typename Acc<DT>::T;
   constexpr int NG = L::NG;
   constexpr int MW = L::MW;
@@ -261,7 +264,7 @@ __global__ void __launch_bounds__(160, tc_min_ctas<MAXM, TB>()) prune_tc_kernel(
   const float E_rel = slice_rel_bound(a.d), E_abs = abs_bound(a.d);
   const int count = *a.count;
 
-  if (warp == 0) tmem_alloc(tmem_slot, 128);  // 128 of the SM's 512 TMEM columns, for the kernel's life
+  if (warp == 0) tmem_alloc(tmem_slot, kTmemCols);  // of the SM's 512 TMEM columns, for the kernel's life
   if (r == 0) {
     mbar_init(mbar, 1);
     misc[12] = kClaim;  // empty claim queue
@@ -285,10 +288,12 @@ __global__ void __launch_bounds__(160, tc_min_ctas<MAXM, TB>()) prune_tc_kernel(
     constexpr uint32_t idesc = umma_idesc_f16(128, 128);
     const int64_t elems = a.row_bytes / (DT == kU8 ? 1 : 4);  // padded dims per row
     const int nslices = int((elems + 127) / 128);
-    // f16 Gram of scaled rows: |G~ - G| <= eps_ip |u||v| + 2^-25 sqrt(d) (|u| + |v|) / scale (f16
-    // rounding of both operands, u = 2^-11, subnormals, f32 accumulation with a factor 2 allowance)
-    const float eps_ip = 9.765625e-04f + 4.76837158e-07f + float(a.d) * 2.384185791015625e-07f;
-    const float sub_abs = a.sqrt_d * 1.001f * 5.9604645e-08f * a.inv_s;  // twice 2^-25 sqrt(d) / scale
+    // Split f16 Gram of scaled rows, G' = hi hi^T + 2^-11 (hi lo^T + lo hi^T):
+    // |G~ - G| <= eps_ip |u||v| + 2^-36 sqrt(d) (|u| + |v|) / scale (the split
+    // leaves 2^-22 per operand, the dropped lo lo^T term 2^-22, the last sum
+    // 2^-23, f32 accumulation d 2^-22 with a factor 2 allowance; subnormal lo)
+    const float eps_ip = 4.f * 2.384185791015625e-07f + 1.1920929e-07f + float(a.d) * 2.384185791015625e-07f;
+    const float sub_abs = a.sqrt_d * 1.001f * 2.910383e-11f * a.inv_s;  // twice 2^-36 sqrt(d) / scale
     const float eps_n = float(a.d + 12) * 5.9604645e-08f;
     const float err_abs = float(a.d) * 2.3509887e-38f;  // underflowed products, 2^-125 each
     uint32_t phase = 0;
@@ -501,11 +506,14 @@ __global__ void __launch_bounds__(160, tc_min_ctas<MAXM, TB>()) prune_tc_kernel(
               x0 = __ldg(xq);
               x1 = __ldg(xq + 1);
             }
-            *reinterpret_cast<uint4*>(opnd + (c * 16 + orow / 8) * 128 + (orow % 8) * 16) =
-                make_uint4(pack_f16x2(__uint_as_float(x0.x) * a.scale, __uint_as_float(x0.y) * a.scale),
-                           pack_f16x2(__uint_as_float(x0.z) * a.scale, __uint_as_float(x0.w) * a.scale),
-                           pack_f16x2(__uint_as_float(x1.x) * a.scale, __uint_as_float(x1.y) * a.scale),
-                           pack_f16x2(__uint_as_float(x1.z) * a.scale, __uint_as_float(x1.w) * a.scale));
+            uint4 hi, lo;
+            split_f16x2(__uint_as_float(x0.x) * a.scale, __uint_as_float(x0.y) * a.scale, hi.x, lo.x);
+            split_f16x2(__uint_as_float(x0.z) * a.scale, __uint_as_float(x0.w) * a.scale, hi.y, lo.y);
+            split_f16x2(__uint_as_float(x1.x) * a.scale, __uint_as_float(x1.y) * a.scale, hi.z, lo.z);
+            split_f16x2(__uint_as_float(x1.z) * a.scale, __uint_as_float(x1.w) * a.scale, hi.w, lo.w);
+            const size_t at = size_t(c * 16 + orow / 8) * 128 + (orow % 8) * 16;
+            *reinterpret_cast<uint4*>(opnd + at) = hi;
+            *reinterpret_cast<uint4*>(opnd + 128 * 128 * 2 + at) = lo;
           }
         }
         const bool last = sl == nslices - 1;
@@ -518,6 +526,12 @@ __global__ void __launch_bounds__(160, tc_min_ctas<MAXM, TB>()) prune_tc_kernel(
           for (int kk = 0; kk < kd / 16; ++kk) {
             const uint64_t dsc = umma_desc(smem_addr(opnd) + uint32_t(kk) * 2u * 16u * 128u, 16u * 128u, 128u);
             umma_bf16(tmem, dsc, dsc, idesc, sl > 0 || kk > 0);
+            if constexpr (DT == kF32) {  // the cross terms with the low halves into the second accumulator
+              const uint64_t dlo =
+                  umma_desc(smem_addr(opnd + 128 * 128 * 2) + uint32_t(kk) * 2u * 16u * 128u, 16u * 128u, 128u);
+              umma_bf16(tmem + 128u, dsc, dlo, idesc, sl > 0 || kk > 0);
+              umma_bf16(tmem + 128u, dlo, dsc, idesc, true);
+            }
           }
           umma_commit(mbar);
         }
@@ -594,15 +608,17 @@ __global__ void __launch_bounds__(160, tc_min_ctas<MAXM, TB>()) prune_tc_kernel(
         } else {
 #pragma unroll 1
           for (int c0 = 0; c0 < MAXM; c0 += 32) {
-            uint32_t v[32];
+            uint32_t v[32], v2[32];
             tmem_ld32(tmem + (uint32_t(32 * warp) << 16) + uint32_t(g * MAXM + c0), v);
+            tmem_ld32(tmem + (uint32_t(32 * warp) << 16) + uint32_t(128 + g * MAXM + c0), v2);
             tmem_ld_wait();
             if (live_row) {
 #pragma unroll
               for (int j = 0; j < 32; ++j) {
                 const int c = c0 + j;
                 if (c >= m) break;
-                const float G = __uint_as_float(v[j]) * a.inv_s2;  // exact: a power of two
+                // hi hi^T + 2^-11 (cross terms), back in the rows' units (powers of two: exact scalings)
+                const float G = fmaf(__uint_as_float(v2[j]), 4.8828125e-04f, __uint_as_float(v[j])) * a.inv_s2;
                 const unsigned long long bit = 1ull << (c & 63);
                 const int w = c >> 6;
                 const float nc = float(norm[c]);
@@ -714,7 +730,7 @@ __global__ void __launch_bounds__(160, tc_min_ctas<MAXM, TB>()) prune_tc_kernel(
     tc_fence_before();
     named_sync(kBarProd, 128);
     tc_fence_after();
-    if (warp == 0) tmem_dealloc(*tmem_slot, 128);
+    if (warp == 0) tmem_dealloc(*tmem_slot, kTmemCols);
   }
 }
 
@@ -1085,7 +1101,7 @@ static cudaError_t resident_ctas(K kern, int threads, size_t dyn_smem, int cap, 
 
 template <int DT, int MAXM, int TB>
 static cudaError_t run_fast_t(const PruneArgs& args, int num_sms, int64_t host_count, int ctas_cap, cudaStream_t s) {
-  const size_t bytes = TcLayout<MAXM, TB>::bytes;
+  const size_t bytes = TcLayout<MAXM, TB, DT == kF32 ? 2 : 1>::bytes;
   auto kern = prune_tc_kernel<DT, MAXM, TB>;
   constexpr int kThreadsTc = 160;  // 4 producer warps + 1 consumer warp
   cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(bytes));
@@ -1094,7 +1110,8 @@ static cudaError_t run_fast_t(const PruneArgs& args, int num_sms, int64_t host_c
   err = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
   if (err != cudaSuccess) return err;
   int per_sm = 0;
-  err = resident_ctas(kern, kThreadsTc, bytes, 4 /* 128 of the 512 TMEM columns per CTA */, &per_sm);
+  // 128 (uint8) or 256 (float) of the SM's 512 TMEM columns per CTA
+  err = resident_ctas(kern, kThreadsTc, bytes, DT == kF32 ? 2 : 4, &per_sm);
   if (err != cudaSuccess) return err;
   if (ctas_cap > 0) per_sm = std::min(per_sm, ctas_cap);
   const int64_t groups_needed = (host_count + (128 / MAXM) - 1) / (128 / MAXM);

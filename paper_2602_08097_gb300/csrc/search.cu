@@ -157,6 +157,7 @@ __device__ __forceinline__ bool entry_less(unsigned ka, unsigned ia, double* d64
   if constexpr (DT == kU8) {
     return ka < kb || (ka == kb && ia < ib);
   } else {
+    if (ia == ib) return false;  // the same point: never less than itself (no binary64 needed)
     const float fa = __uint_as_float(ka), fb = __uint_as_float(kb);
     if (sure_less(fa, fb, E, Eabs)) return true;
     if (sure_less(fb, fa, E, Eabs)) return false;

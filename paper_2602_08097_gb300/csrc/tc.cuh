@@ -120,6 +120,17 @@ __device__ __forceinline__ uint32_t pack_f16x2(float lo, float hi) {
   return r;
 }
 
+// Split two floats into f16 pairs hi and lo with a = hi + 2^-11 lo up to
+// 2^-22 |a| (+ 2^-36 where lo is subnormal): hi = f16(a), lo = f16(2^11 (a - hi)),
+// the difference and the scaling being exact in single precision.
+__device__ __forceinline__ void split_f16x2(float a0, float a1, uint32_t& hi, uint32_t& lo) {
+  hi = pack_f16x2(a0, a1);
+  float h0, h1;
+  asm("{\n.reg .f16 l, h;\nmov.b32 {l, h}, %2;\ncvt.f32.f16 %0, l;\ncvt.f32.f16 %1, h;\n}" : "=f"(h0), "=f"(h1)
+      : "r"(hi));
+  lo = pack_f16x2((a0 - h0) * 2048.f, (a1 - h1) * 2048.f);
+}
+
 // Round-to-nearest-even float -> bf16 bits (exact for integers up to 256).
 __device__ __forceinline__ uint32_t pack_bf16x2(float lo, float hi) {
   uint32_t r;
