@@ -363,6 +363,18 @@ rp_status rp_set_tuning(rp_ctx *ctx, int32_t mode, int32_t tile0, int32_t ctas_p
 enum { RP_KNN_AUTO = 0, RP_KNN_CUDA_CORE = 1, RP_KNN_TENSOR = 2 };
 rp_status rp_set_knn_method(rp_ctx *ctx, int32_t method);
 
+/*
+ * rp_set_search_config: the launch plan of rp_search and rp_search_multi.
+ * The paper fixes none; results never depend on it.
+ *   cache_bits: 8..12, a direct-mapped cache of 2^cache_bits recently met
+ *     ids per query in shared memory (a miss only costs one more distance);
+ *     0 = the largest cache that keeps 8 CTAs of 4 queries per SM.
+ *   ctas_per_sm: at most this many CTAs per SM (0 = as many as shared
+ *     memory allows, up to 16).
+ * Errors: RP_EINVAL.
+ */
+rp_status rp_set_search_config(rp_ctx *ctx, int32_t cache_bits, int32_t ctas_per_sm);
+
 /* ------------------------------------------------------------------------
  * Serving: a scheduler thread over one resident base graph that takes
  * prune-to-(alpha, R) jobs and query batches as they arrive (continuous

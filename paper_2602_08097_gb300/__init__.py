@@ -115,6 +115,7 @@ def load_library(path: str = LIB_PATH):
         "rp_graph_slice": [P, i64, i64, i64, ctypes.POINTER(i64)],
         "rp_set_tuning": [P, i32, i32, i32],
         "rp_set_knn_method": [P, i32],
+        "rp_set_search_config": [P, i32, i32],
         "rp_server_create": [P, i64, u64, i64, i32, ctypes.POINTER(P)],
         "rp_server_create_ex": [ctypes.POINTER(rp_executor), ctypes.POINTER(rp_server_config), ctypes.POINTER(P)],
         "rp_server_destroy": [P],
@@ -333,6 +334,10 @@ def rp_graph_free(ctx, g: int):
 
 def rp_set_tuning(ctx, mode: int, tile0: int = 0, ctas_per_sm: int = 0):
     _check(ctx, load_library().rp_set_tuning(ctx, int(mode), int(tile0), int(ctas_per_sm)))
+
+
+def rp_set_search_config(ctx, cache_bits: int = 0, ctas_per_sm: int = 0):
+    _check(ctx, load_library().rp_set_search_config(ctx, int(cache_bits), int(ctas_per_sm)))
 
 
 def rp_set_knn_method(ctx, method: int):

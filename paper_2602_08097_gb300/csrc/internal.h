@@ -100,6 +100,8 @@ struct SearchLaunch {
   int32_t* out_ids = nullptr;
   float* out_dists = nullptr;
   int num_sms = 0;
+  int cache_bits = 0;   // id-cache entries per warp as a power of two (8..12); 0 = chosen by the launcher
+  int ctas_per_sm = 0;  // CTAs per SM cap; 0 = as many as shared memory allows (<= 16)
   unsigned int* work = nullptr;   // zeroed
   DevStatus* status = nullptr;
   int max_degree = 0;

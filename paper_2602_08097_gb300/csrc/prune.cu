@@ -576,11 +576,17 @@ __global__ void __launch_bounds__(160, tc_min_ctas<DT, MAXM, TB>()) prune_tc_ker
           for (int w = 0; w < MW; ++w) mk[u][w] = 0;
         const float nt = live_row ? float(norm[t]) : 0.f;
         const float st = DT == kF32 && live_row ? sn[t] : 0.f;
+        // A row only removes candidates after it in the processing order (the
+        // scan has decided every earlier one), so a warp whose rows all come
+        // after a 32-column chunk skips it (a uniform choice: the TMEM read is
+        // warp-collective).  Bits set for earlier columns are harmless too.
+        const int first_col = 32 * (warp % (MAXM / 32));
         if constexpr (DT == kU8) {
           // Columns at or past the degree hold no candidate: the bits set there
           // can never meet a live bit in the scan, so they are not tested for.
 #pragma unroll
           for (int c0 = 0; c0 < MAXM; c0 += 32) {
+            if (c0 < first_col) continue;
             uint32_t v[32];
             tmem_ld32(tmem + (uint32_t(32 * warp) << 16) + uint32_t(g * MAXM + c0), v);
             tmem_ld_wait();
@@ -607,7 +613,7 @@ __global__ void __launch_bounds__(160, tc_min_ctas<DT, MAXM, TB>()) prune_tc_ker
           }
         } else {
 #pragma unroll 1
-          for (int c0 = 0; c0 < MAXM; c0 += 32) {
+          for (int c0 = first_col; c0 < MAXM; c0 += 32) {
             uint32_t v[32], v2[32];
             tmem_ld32(tmem + (uint32_t(32 * warp) << 16) + uint32_t(g * MAXM + c0), v);
             tmem_ld32(tmem + (uint32_t(32 * warp) << 16) + uint32_t(128 + g * MAXM + c0), v2);
@@ -1032,14 +1038,37 @@ __global__ void __launch_bounds__(kScanThreads) emit_write(EmitArgs e) {
   if (blockIdx.x == 0 && threadIdx.x == 0) e.dst_row_ptr[tt][0] = 0;
   __syncthreads();
   if (e.dst_col[tt] == nullptr) return;
+  // A warp takes 32 consecutive rows: their counts and offsets in one coalesced
+  // load, then the rows' ids four rows at a time (independent loads in flight).
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  for (int li = w; li < kScanChunk; li += kScanThreads / 32) {
-    const int64_t p = b0 + li;
-    if (p >= e.n) break;
-    const int c = e.cnt[tt][p];
-    const int32_t* src = e.scratch[tt] + e.src_row_ptr[p];
-    int32_t* dst = e.dst_col[tt] + off[li];
-    for (int j = lane; j < c; j += 32) dst[j] = src[j];
+  const int32_t* scr = e.scratch[tt];
+  int32_t* dcol = e.dst_col[tt];
+  for (int base = w * 32; base < kScanChunk; base += kScanThreads) {
+    const int64_t p = b0 + base + lane;
+    const bool valid = p < e.n;
+    const int c_l = valid ? e.cnt[tt][p] : 0;
+    const int64_t s_l = valid ? e.src_row_ptr[p] : 0;
+    const int64_t o_l = off[base + lane];
+    for (int r0 = 0; r0 < 32; r0 += 4) {
+      int c[4];
+      int64_t so[4], dof[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        c[q] = __shfl_sync(0xffffffffu, c_l, r0 + q);
+        so[q] = __shfl_sync(0xffffffffu, s_l, r0 + q);
+        dof[q] = __shfl_sync(0xffffffffu, o_l, r0 + q);
+      }
+      const int cmax = max(max(c[0], c[1]), max(c[2], c[3]));
+      for (int j = lane; j < cmax; j += 32) {
+        int32_t v[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+          if (j < c[q]) v[q] = scr[so[q] + j];
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+          if (j < c[q]) dcol[dof[q] + j] = v[q];
+      }
+    }
   }
 }
 

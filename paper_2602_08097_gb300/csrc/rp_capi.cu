@@ -106,6 +106,7 @@ struct rp_ctx {
   int fixed_tile0 = 0, fixed_ctas = 0;
   int last_tile0 = 0, last_ctas = 0;
   int knn_method = RP_KNN_AUTO;
+  int search_cache_bits = 0, search_ctas = 0;  // rp_set_search_config
   int last_knn_method = 0;
   int32_t* trial_count = nullptr;  // device int[4]: bucket sizes of a trial launch
   int64_t graph_replays = 0;
@@ -600,6 +601,8 @@ rp_status search_impl(rp_ctx* c, const rp_graph* graphs, int32_t ngraphs, const 
   S.out_ids = dev_ids;
   S.out_dists = dev_d;
   S.num_sms = c->num_sms;
+  S.cache_bits = c->search_cache_bits;
+  S.ctas_per_sm = c->search_ctas;
   S.work = c->work;
   S.status = c->status;
   CUDA_TRY(c, cudaMemsetAsync(c->work, 0, 8 * sizeof(unsigned), c->stream));
@@ -1211,6 +1214,17 @@ rp_status rp_build_knn_random_base(rp_ctx* c, rp_graph data, int32_t kcand, int3
   std::lock_guard<std::mutex> lk(c->mu);
   cudaSetDevice(c->device);
   return build_base(c, data, kcand, nrand, seed, alpha, R, out);
+}
+
+rp_status rp_set_search_config(rp_ctx* c, int32_t cache_bits, int32_t ctas_per_sm) {
+  if (!c) return RP_EINVAL;
+  std::lock_guard<std::mutex> lk(c->mu);
+  if (cache_bits != 0 && (cache_bits < 8 || cache_bits > 12))
+    return fail(c, RP_EINVAL, "cache_bits=%d: use 0 or 8..12", cache_bits);
+  if (ctas_per_sm < 0 || ctas_per_sm > 16) return fail(c, RP_EINVAL, "ctas_per_sm=%d outside 0..16", ctas_per_sm);
+  c->search_cache_bits = cache_bits;
+  c->search_ctas = ctas_per_sm;
+  return RP_OK;
 }
 
 rp_status rp_set_knn_method(rp_ctx* c, int32_t method) {

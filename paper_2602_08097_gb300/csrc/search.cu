@@ -444,7 +444,8 @@ __global__ void recall_kernel(const int32_t* __restrict__ found, int ld_found, c
 // expansion).
 constexpr int kSmemPerSm = 228 * 1024;
 constexpr int kCtaReserve = 1024;
-constexpr int kMaxCtasPerSm = 8;
+constexpr int kMaxCtasPerSm = 8;    // the default plan's target
+constexpr int kMaxCtasPerSmCap = 16;
 
 int ctas_per_sm(size_t cta_bytes) {
   return int(std::min<size_t>(kMaxCtasPerSm, size_t(kSmemPerSm) / (cta_bytes + kCtaReserve)));
@@ -471,14 +472,21 @@ cudaError_t launch_search(const SearchLaunch& L, cudaStream_t s) {
   a.work = L.work;
   a.status = L.status;
   const bool f32 = L.data.dtype == kF32;
-  // the largest id cache (256 .. 4096 entries) that keeps the CTAs per SM of the smallest
+  // default: the largest id cache (256 .. 4096 entries) that keeps the CTAs per SM of the smallest
   int bits = 8;
-  const int base_ctas = ctas_per_sm(warp_bytes(L.L, L.data.row_bytes, f32, 8) * kWarps);
+  int base_ctas = ctas_per_sm(warp_bytes(L.L, L.data.row_bytes, f32, 8) * kWarps);
   for (int b = 12; b > 8; --b)
     if (ctas_per_sm(warp_bytes(L.L, L.data.row_bytes, f32, b) * kWarps) >= base_ctas) {
       bits = b;
       break;
     }
+  if (L.cache_bits >= 8 && L.cache_bits <= 12) {  // a configured plan (rp_set_search_config)
+    bits = L.cache_bits;
+    const size_t cta = warp_bytes(L.L, L.data.row_bytes, f32, bits) * kWarps;
+    base_ctas = int(std::min<size_t>(kMaxCtasPerSmCap, size_t(kSmemPerSm) / (cta + kCtaReserve)));
+  }
+  if (L.ctas_per_sm > 0) base_ctas = std::min(base_ctas, L.ctas_per_sm);
+  base_ctas = std::max(base_ctas, 1);
   a.cache_bits = bits;
   const size_t bytes = warp_bytes(L.L, L.data.row_bytes, f32, bits) * kWarps;
   const int64_t want = int64_t(L.num_sms) * std::max(base_ctas, 1);
