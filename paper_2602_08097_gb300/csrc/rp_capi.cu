@@ -1004,11 +1004,9 @@ rp_status rp_graph_info(rp_ctx* c, rp_graph g, int64_t* n, int64_t* nnz, int32_t
   Graph* G = find_graph(c, g);
   if (!G) return fail(c, RP_ENOTFOUND, "unknown graph %lld", (long long)g);
   if (G->nnz < 0 || max_deg) {
-    int64_t* rp = nullptr;
     std::vector<int64_t> h(size_t(G->n + 1));
     CUDA_TRY(c, cudaMemcpyAsync(h.data(), G->row_ptr, size_t(G->n + 1) * 8, cudaMemcpyDeviceToHost, c->stream));
     CUDA_TRY(c, cudaStreamSynchronize(c->stream));
-    (void)rp;
     G->nnz = h[size_t(G->n)];
     int64_t mx = 0;
     for (int64_t p = 0; p < G->n; ++p) mx = std::max(mx, h[size_t(p + 1)] - h[size_t(p)]);

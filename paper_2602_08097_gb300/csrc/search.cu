@@ -27,6 +27,9 @@
 // distances are recomputed in binary64 (index order, no fused multiply-add)
 // and compared there, so every comparison agrees with the binary64 reading.
 #include <cfloat>
+#include <map>
+#include <mutex>
+#include <tuple>
 
 #include "internal.h"
 
@@ -439,16 +442,60 @@ __global__ void recall_kernel(const int32_t* __restrict__ found, int ld_found, c
 
 }  // namespace
 
-// Shared memory of one SM that the search may plan with, and the CTAs per SM
-// it aims for (32 warps: enough queries in flight to hide the latency of each
-// expansion).
-constexpr int kSmemPerSm = 228 * 1024;
-constexpr int kCtaReserve = 1024;
-constexpr int kMaxCtasPerSm = 8;    // the default plan's target
+// The CTAs per SM a configured plan may ask for.
 constexpr int kMaxCtasPerSmCap = 16;
+constexpr int kMinCacheBits = 8, kMaxCacheBits = 12;
 
-int ctas_per_sm(size_t cta_bytes) {
-  return int(std::min<size_t>(kMaxCtasPerSm, size_t(kSmemPerSm) / (cta_bytes + kCtaReserve)));
+// CTAs of search_kernel<DT> one SM holds with `bytes` of dynamic shared memory
+// (registers and shared memory both count), from the occupancy calculator.
+template <int DT>
+cudaError_t resident_ctas(size_t bytes, size_t max_bytes, int* out) {
+  cudaError_t err = cudaFuncSetAttribute(search_kernel<DT>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(max_bytes));
+  if (err != cudaSuccess) return err;
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(out, search_kernel<DT>, kWarps * 32, bytes);
+}
+
+// Default plan: the queries in flight hide the latency of each expansion, so
+// the search first maximises the CTAs per SM, then takes the largest id cache
+// (256 .. 4096 entries per warp) that keeps that many.  Plans are remembered
+// per (dtype, L, row bytes); the occupancy queries run once for each.
+struct SearchPlan {
+  int bits = kMinCacheBits;
+  int ctas = 1;
+};
+
+cudaError_t default_plan(bool f32, int L, int64_t row_bytes, SearchPlan* plan) {
+  static std::mutex mu;
+  static std::map<std::tuple<bool, int, int64_t>, SearchPlan> memo;
+  const auto key = std::make_tuple(f32, L, row_bytes);
+  {
+    std::lock_guard<std::mutex> g(mu);
+    auto it = memo.find(key);
+    if (it != memo.end()) {
+      *plan = it->second;
+      return cudaSuccess;
+    }
+  }
+  const size_t max_bytes = warp_bytes(L, row_bytes, f32, kMaxCacheBits) * kWarps;
+  SearchPlan best;
+  int best_ctas = 0;
+  for (int b = kMinCacheBits; b <= kMaxCacheBits; ++b) {
+    int nb = 0;
+    const size_t bytes = warp_bytes(L, row_bytes, f32, b) * kWarps;
+    cudaError_t err = f32 ? resident_ctas<kF32>(bytes, max_bytes, &nb) : resident_ctas<kU8>(bytes, max_bytes, &nb);
+    if (err != cudaSuccess) return err;
+    if (nb >= best_ctas && nb > 0) {  // ties go to the larger cache
+      best_ctas = nb;
+      best.bits = b;
+      best.ctas = nb;
+    }
+  }
+  if (best_ctas == 0) return cudaErrorInvalidConfiguration;
+  best.ctas = std::min(best.ctas, kMaxCtasPerSmCap);
+  std::lock_guard<std::mutex> g(mu);
+  memo[key] = best;
+  *plan = best;
+  return cudaSuccess;
 }
 
 cudaError_t launch_search(const SearchLaunch& L, cudaStream_t s) {
@@ -472,24 +519,23 @@ cudaError_t launch_search(const SearchLaunch& L, cudaStream_t s) {
   a.work = L.work;
   a.status = L.status;
   const bool f32 = L.data.dtype == kF32;
-  // default: the largest id cache (256 .. 4096 entries) that keeps the CTAs per SM of the smallest
-  int bits = 8;
-  int base_ctas = ctas_per_sm(warp_bytes(L.L, L.data.row_bytes, f32, 8) * kWarps);
-  for (int b = 12; b > 8; --b)
-    if (ctas_per_sm(warp_bytes(L.L, L.data.row_bytes, f32, b) * kWarps) >= base_ctas) {
-      bits = b;
-      break;
-    }
-  if (L.cache_bits >= 8 && L.cache_bits <= 12) {  // a configured plan (rp_set_search_config)
-    bits = L.cache_bits;
-    const size_t cta = warp_bytes(L.L, L.data.row_bytes, f32, bits) * kWarps;
-    base_ctas = int(std::min<size_t>(kMaxCtasPerSmCap, size_t(kSmemPerSm) / (cta + kCtaReserve)));
+  SearchPlan plan;
+  if (L.cache_bits >= kMinCacheBits && L.cache_bits <= kMaxCacheBits) {  // a configured plan (rp_set_search_config)
+    plan.bits = L.cache_bits;
+    const size_t bytes = warp_bytes(L.L, L.data.row_bytes, f32, plan.bits) * kWarps;
+    cudaError_t err = f32 ? resident_ctas<kF32>(bytes, bytes, &plan.ctas) : resident_ctas<kU8>(bytes, bytes, &plan.ctas);
+    if (err != cudaSuccess) return err;
+    plan.ctas = std::min(plan.ctas, kMaxCtasPerSmCap);
+  } else {
+    cudaError_t err = default_plan(f32, L.L, L.data.row_bytes, &plan);
+    if (err != cudaSuccess) return err;
   }
+  int base_ctas = plan.ctas;
   if (L.ctas_per_sm > 0) base_ctas = std::min(base_ctas, L.ctas_per_sm);
   base_ctas = std::max(base_ctas, 1);
-  a.cache_bits = bits;
-  const size_t bytes = warp_bytes(L.L, L.data.row_bytes, f32, bits) * kWarps;
-  const int64_t want = int64_t(L.num_sms) * std::max(base_ctas, 1);
+  a.cache_bits = plan.bits;
+  const size_t bytes = warp_bytes(L.L, L.data.row_bytes, f32, plan.bits) * kWarps;
+  const int64_t want = int64_t(L.num_sms) * base_ctas;
   const int64_t need = (L.nq + kWarps - 1) / kWarps;
   const int grid = int(std::max<int64_t>(1, std::min(want, need)));
   cudaError_t err;

@@ -280,6 +280,30 @@ def test_u8_search_and_recall_match_oracle(ctx):
     assert hits / (100 * Q.shape[0]) == pytest.approx(oracle.recall_at_k(ref, gt, 100), abs=0)
 
 
+
+@pytest.mark.parametrize("name", ["sift", "deep"])
+def test_every_search_plan_gives_the_oracle_lists(ctx, name):
+    """rp_set_search_config only moves work between CTAs and the id cache:
+    every plan must return Algorithm 2's lists (a cache miss costs a distance,
+    never a result)."""
+    X = datagen.dataset(name, 3000)
+    Q = datagen.queries(name, 150)
+    brp, bcol = oracle.knn_base(X, 48, 1.2, 32)
+    g = rp.rp_load_graph(ctx, X, brp, bcol)
+    start = rp.rp_graph_info(ctx, g)["start"]
+    ref, _, _ = oracle.greedy_search(X, brp, bcol, start, Q, 96, 50)
+    try:
+        for bits, ctas in [(0, 0), (8, 0), (9, 0), (12, 0), (8, 1), (10, 3), (11, 16), (0, 2)]:
+            rp.rp_set_search_config(ctx, bits, ctas)
+            ids, _ = rp.rp_search(ctx, g, Q, 96, 50)
+            assert np.array_equal(ids, ref), (bits, ctas)
+        for bits, ctas in [(7, 0), (13, 0), (-1, 0), (0, -1), (0, 17)]:
+            with pytest.raises(rp.RPError):
+                rp.rp_set_search_config(ctx, bits, ctas)
+    finally:
+        rp.rp_set_search_config(ctx, 0, 0)
+    rp.rp_graph_free(ctx, g)
+
 def test_search_unreachable_pads(ctx):
     X = np.arange(6, dtype=np.uint8)[:, None]
     row_ptr = np.array([0, 1, 2, 3, 4, 5, 6], np.int64)
