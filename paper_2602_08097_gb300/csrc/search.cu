@@ -64,20 +64,23 @@ struct SearchArgs {
 };
 
 struct WarpSmem {
-  unsigned* key[2];
-  unsigned* idv[2];
-  double* d64[2];
-  unsigned* ckey;  // sorted candidates of the current batch
+  unsigned* key;   // the list: distance bits, sorted by (distance, id)
+  unsigned* idv;   // its ids (| kVisited once expanded)
+  double* d64;     // float data: binary64 distances of the list (NaN until computed)
+  unsigned* ckey;  // a batch's new members, then
   unsigned* cid;
+  int* clo;        // their insertion points (sorted: the merge's shift table)
   double* cd64;
   uint8_t* q;
   unsigned* cache;  // direct-mapped ids met by this query (0xffffffff = empty)
 };
 
+__host__ __device__ inline size_t list_cap(int L) { return (size_t(L) + 3) & ~size_t(3); }
+
 __host__ __device__ inline size_t warp_bytes(int L, int64_t row_bytes, bool f32, int cache_bits) {
-  const size_t cap = size_t(L) + 32;
-  size_t b = 2 * cap * 8 + 32 * 8;  // keys + ids for both buffers, candidate keys + ids
-  if (f32) b += 2 * cap * 8 + 32 * 8;
+  const size_t cap = list_cap(L);
+  size_t b = cap * 8 + 32 * 12;  // list keys + ids; batch keys, ids, insertion points
+  if (f32) b += cap * 8 + 32 * 8;
   b += size_t(row_bytes);
   b += size_t(4) << cache_bits;
   return (b + 127) & ~size_t(127);
@@ -85,33 +88,29 @@ __host__ __device__ inline size_t warp_bytes(int L, int64_t row_bytes, bool f32,
 
 __device__ inline WarpSmem carve(unsigned char* base, int L, int64_t row_bytes, bool f32, int cache_bits) {
   WarpSmem w;
-  const size_t cap = size_t(L) + 32;
+  const size_t cap = list_cap(L);
   unsigned char* p = base;
   w.cache = reinterpret_cast<unsigned*>(p);
   p += size_t(4) << cache_bits;
   if (f32) {
-    w.d64[0] = reinterpret_cast<double*>(p);
-    p += cap * 8;
-    w.d64[1] = reinterpret_cast<double*>(p);
+    w.d64 = reinterpret_cast<double*>(p);
     p += cap * 8;
     w.cd64 = reinterpret_cast<double*>(p);
     p += 32 * 8;
   } else {
-    w.d64[0] = w.d64[1] = w.cd64 = nullptr;
+    w.d64 = w.cd64 = nullptr;
   }
-  w.q = p;
+  w.q = p;  // 16-byte aligned: cap is a multiple of 4 and row_bytes of 16
   p += row_bytes;
-  w.key[0] = reinterpret_cast<unsigned*>(p);
+  w.key = reinterpret_cast<unsigned*>(p);
   p += cap * 4;
-  w.key[1] = reinterpret_cast<unsigned*>(p);
-  p += cap * 4;
-  w.idv[0] = reinterpret_cast<unsigned*>(p);
-  p += cap * 4;
-  w.idv[1] = reinterpret_cast<unsigned*>(p);
+  w.idv = reinterpret_cast<unsigned*>(p);
   p += cap * 4;
   w.ckey = reinterpret_cast<unsigned*>(p);
   p += 32 * 4;
   w.cid = reinterpret_cast<unsigned*>(p);
+  p += 32 * 4;
+  w.clo = reinterpret_cast<int*>(p);
   return w;
 }
 
@@ -183,7 +182,7 @@ __device__ __forceinline__ bool entry_less(unsigned ka, unsigned ia, double* d64
 }
 
 template <int DT>
-__global__ void __launch_bounds__(kWarps * 32) search_kernel(SearchArgs a) {
+__global__ void __launch_bounds__(kWarps * 32, 9) search_kernel(SearchArgs a) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const bool f32 = DT == kF32;
@@ -215,10 +214,11 @@ __global__ void __launch_bounds__(kWarps * 32) search_kernel(SearchArgs a) {
     for (int c = lane; c < centries; c += 32) S.cache[c] = 0xffffffffu;
     __syncwarp();
 
-    // the list and the buffer the next merge writes (swapped after each merge)
-    unsigned *keyc = S.key[0], *keyn = S.key[1], *idc = S.idv[0], *idn = S.idv[1];
-    double *dc = S.d64[0], *dn = S.d64[1];
+    unsigned* const keyc = S.key;
+    unsigned* const idc = S.idv;
+    double* const dc = S.d64;
     int size = 1;
+    int f = 0;  // the members before index f are all expanded
     if (lane == 0) {
       const unsigned s = unsigned(start);
       keyc[0] = dist_bits<DT>(S.q, a.X + int64_t(s) * a.row_bytes, a.row_bytes);
@@ -232,7 +232,7 @@ __global__ void __launch_bounds__(kWarps * 32) search_kernel(SearchArgs a) {
     for (;;) {
       // the closest member not yet expanded
       int pos = -1;
-      for (int c0 = 0; c0 < size; c0 += 32) {
+      for (int c0 = f & ~31; c0 < size; c0 += 32) {
         const int i = c0 + lane;
         const bool open = i < size && !(idc[i] & kVisited);
         const unsigned b = __ballot_sync(0xffffffffu, open);
@@ -250,6 +250,7 @@ __global__ void __launch_bounds__(kWarps * 32) search_kernel(SearchArgs a) {
       __syncwarp();
       if (lane == 0) idc[pos] |= kVisited;
       __syncwarp();
+      f = pos + 1;
       const int64_t e0 = row_ptr[ps], e1 = row_ptr[ps + 1];
       for (int64_t eb = e0; eb < e1; eb += 32) {
         // ---- new neighbours of this batch
@@ -276,9 +277,11 @@ __global__ void __launch_bounds__(kWarps * 32) search_kernel(SearchArgs a) {
                                   idc[L - 1] & kIdMask, f32 ? &dc[L - 1] : nullptr, a, S.q,
                                   E, Eabs);
         }
-        // Already in the list?  Its entry sits exactly where v would be merged.
+        // Already in the list?  Its entry sits exactly where v would be
+        // merged; otherwise `lo` (the members before v) is v's insertion point.
+        int lo = 0;
         if (enters) {
-          int lo = 0, hi = size;
+          int hi = size;
           while (lo < hi) {
             const int mid = (lo + hi) >> 1;
             const bool bl = entry_less<DT>(keyc[mid], idc[mid] & kIdMask,
@@ -292,114 +295,112 @@ __global__ void __launch_bounds__(kWarps * 32) search_kernel(SearchArgs a) {
         const unsigned fm = __ballot_sync(0xffffffffu, enters);
         const int nf = __popc(fm);
         if (nf == 0) continue;
-        // compact the fresh ones into lanes 0..nf-1
-        unsigned myk = 0xffffffffu, myid = 0xffffffffu;
-        {
-          // lane j takes the j-th fresh entry
-          int srcl = -1;
-          unsigned m = fm;
-          for (int j = 0; j < 32 && m; ++j) {
-            const int l = __ffs(m) - 1;
-            if (j == lane) srcl = l;
-            m &= m - 1;
-          }
-          const unsigned k2 = __shfl_sync(0xffffffffu, kv, srcl < 0 ? 0 : srcl);
-          const unsigned i2 = __shfl_sync(0xffffffffu, v, srcl < 0 ? 0 : srcl);
-          if (srcl >= 0) {
-            myk = k2;
-            myid = i2;
-          }
-        }
-        // ---- sort the batch (bitonic over the warp); empty lanes sort last
-        double myd = qnan;
-        if (f32) S.cd64[lane] = qnan;
-        for (int kk = 2; kk <= 32; kk <<= 1) {
-          for (int j = kk >> 1; j > 0; j >>= 1) {
-            const unsigned ok = __shfl_xor_sync(0xffffffffu, myk, j);
-            const unsigned oi = __shfl_xor_sync(0xffffffffu, myid, j);
-            // dec: 1 = my entry comes first, 0 = the partner's, -1 = undecided
-            int dec;
-            const bool me_empty = myid == 0xffffffffu, o_empty = oi == 0xffffffffu;
-            if (me_empty && o_empty) dec = lane < (lane ^ j) ? 1 : 0;
-            else if (me_empty) dec = 0;
-            else if (o_empty) dec = 1;
-            else if (DT == kU8) dec = (myk < ok || (myk == ok && myid < oi)) ? 1 : 0;
-            else {
-              const float fa = __uint_as_float(myk), fb = __uint_as_float(ok);
-              dec = sure_less(fa, fb, E, Eabs) ? 1 : (sure_less(fb, fa, E, Eabs) ? 0 : -1);
-            }
-            double od = 0.0;
-            if constexpr (DT == kF32) {
-              // an undecided pair is undecided for both lanes: each brings its
-              // own binary64 distance, then both compare there
-              if (dec < 0 && isnan(myd)) {
-                myd = canon_d2_f32(reinterpret_cast<const float*>(S.q),
-                                   reinterpret_cast<const float*>(a.X + int64_t(myid) * a.row_bytes), a.d);
-                atomicAdd(&a.status->fp64_search, 1ull);
-              }
-              od = __shfl_xor_sync(0xffffffffu, myd, j);
-              if (dec < 0) dec = (myd < od || (myd == od && myid < oi)) ? 1 : 0;
-            }
-            const bool less_me = dec == 1;
-            const bool up = (lane & kk) == 0;
-            const bool lower = (lane & j) == 0;
-            const bool take_partner = (lower == up) ? !less_me : less_me;
-            if (take_partner) {
-              myk = ok;
-              myid = oi;
-              myd = od;
-            }
-          }
-        }
-        if (lane < nf) {
-          S.ckey[lane] = myk;
-          S.cid[lane] = myid;
-          if (f32) S.cd64[lane] = myd;
+        // ---- the new members, compacted into lanes 0..nf-1
+        if (enters) {
+          const int r = __popc(fm & ((1u << lane) - 1u));
+          S.ckey[r] = kv;
+          S.cid[r] = v;
+          S.clo[r] = lo;
+          if (f32) S.cd64[r] = cand_d64;
         }
         __syncwarp();
-        // ---- merge the sorted batch into the list, keep the first L
-        for (int i = lane; i < size; i += 32) {
-          const unsigned bk = keyc[i], bi = idc[i];
-          int lo = 0, hi = nf;  // number of candidates before list entry i
-          while (lo < hi) {
-            const int mid = (lo + hi) >> 1;
-            const bool cl = entry_less<DT>(S.ckey[mid], S.cid[mid], f32 ? &S.cd64[mid] : nullptr, bk, bi & kIdMask,
-                                           f32 ? &dc[i] : nullptr, a, S.q, E, Eabs);
-            if (cl) lo = mid + 1;
-            else hi = mid;
-          }
-          const int np = i + lo;
-          if (np < L) {
-            keyn[np] = bk;
-            idn[np] = bi;
-            if (f32) dn[np] = dc[i];
-          }
-        }
+        unsigned myk = 0xffffffffu, myid = 0xffffffffu;
+        int mylo = 0x7fffffff;
+        double myd = qnan;
         if (lane < nf) {
-          const unsigned ck = S.ckey[lane], ci = S.cid[lane];
-          int lo = 0, hi = size;  // number of list entries before candidate lane
-          while (lo < hi) {
-            const int mid = (lo + hi) >> 1;
-            const bool bl = entry_less<DT>(keyc[mid], idc[mid] & kIdMask,
-                                           f32 ? &dc[mid] : nullptr, ck, ci,
-                                           f32 ? &S.cd64[lane] : nullptr, a, S.q, E, Eabs);
-            if (bl) lo = mid + 1;
-            else hi = mid;
+          myk = S.ckey[lane];
+          myid = S.cid[lane];
+          mylo = S.clo[lane];
+          if (f32) myd = S.cd64[lane];
+        }
+        // ---- sort them: bitonic over the smallest power of two >= nf lanes
+        // (empty lanes sort last).  Different insertion points order two new
+        // members without a distance: a list member lies between them.
+        if (nf > 1) {
+          const int w = 1 << (32 - __clz(nf - 1));
+          for (int kk = 2; kk <= w; kk <<= 1) {
+            for (int j = kk >> 1; j > 0; j >>= 1) {
+              const unsigned ok = __shfl_xor_sync(0xffffffffu, myk, j);
+              const unsigned oi = __shfl_xor_sync(0xffffffffu, myid, j);
+              const int olo = __shfl_xor_sync(0xffffffffu, mylo, j);
+              // dec: 1 = my entry comes first, 0 = the partner's, -1 = undecided
+              int dec;
+              const bool me_empty = myid == 0xffffffffu, o_empty = oi == 0xffffffffu;
+              if (me_empty && o_empty) dec = lane < (lane ^ j) ? 1 : 0;
+              else if (me_empty) dec = 0;
+              else if (o_empty) dec = 1;
+              else if (mylo != olo) dec = mylo < olo ? 1 : 0;
+              else if (DT == kU8) dec = (myk < ok || (myk == ok && myid < oi)) ? 1 : 0;
+              else {
+                const float fa = __uint_as_float(myk), fb = __uint_as_float(ok);
+                dec = sure_less(fa, fb, E, Eabs) ? 1 : (sure_less(fb, fa, E, Eabs) ? 0 : -1);
+              }
+              double od = 0.0;
+              if constexpr (DT == kF32) {
+                // an undecided pair is undecided for both lanes: each brings its
+                // own binary64 distance, then both compare there
+                if (dec < 0 && isnan(myd)) {
+                  myd = canon_d2_f32(reinterpret_cast<const float*>(S.q),
+                                     reinterpret_cast<const float*>(a.X + int64_t(myid) * a.row_bytes), a.d);
+                  atomicAdd(&a.status->fp64_search, 1ull);
+                }
+                od = __shfl_xor_sync(0xffffffffu, myd, j);
+                if (dec < 0) dec = (myd < od || (myd == od && myid < oi)) ? 1 : 0;
+              }
+              const bool less_me = dec == 1;
+              const bool up = (lane & kk) == 0;
+              const bool lower = (lane & j) == 0;
+              const bool take_partner = (lower == up) ? !less_me : less_me;
+              if (take_partner) {
+                myk = ok;
+                myid = oi;
+                mylo = olo;
+                myd = od;
+              }
+            }
           }
-          const int np = lane + lo;
-          if (np < L) {
-            keyn[np] = ck;
-            idn[np] = ci;
-            if (f32) dn[np] = S.cd64[lane];
+          if (lane < nf) S.clo[lane] = mylo;
+          __syncwarp();
+        }
+        // ---- merge in place, back to front: member i moves to i + #{r : clo[r] <= i}
+        // and new member r to clo[r] + r; positions from L on are cut.  New
+        // positions only grow and never meet, so a chunk read before any write
+        // to its range is never clobbered.  Members before clo[0] stay.
+        const int first = __shfl_sync(0xffffffffu, mylo, 0);
+        for (int c0 = (size - 1) & ~31; c0 >= (first & ~31) && first < size; c0 -= 32) {
+          const int i = c0 + lane;
+          const bool mv = i >= first && i < size;
+          unsigned bk = 0, bi = 0;
+          double bd = 0.0;
+          int np = L;
+          if (mv) {
+            bk = keyc[i];
+            bi = idc[i];
+            if (f32) bd = dc[i];
+            int l2 = 1, h2 = nf;  // clo[0] = first <= i
+            while (l2 < h2) {
+              const int mid = (l2 + h2) >> 1;
+              if (S.clo[mid] <= i) l2 = mid + 1;
+              else h2 = mid;
+            }
+            np = i + l2;
           }
+          __syncwarp();
+          if (mv && np < L) {
+            keyc[np] = bk;
+            idc[np] = bi;
+            if (f32) dc[np] = bd;
+          }
+          __syncwarp();
+        }
+        if (lane < nf && mylo + lane < L) {
+          keyc[mylo + lane] = myk;
+          idc[mylo + lane] = myid;
+          if (f32) dc[mylo + lane] = myd;
         }
         __syncwarp();
         size = min(L, size + nf);
-        {
-          unsigned* t0 = keyc; keyc = keyn; keyn = t0;
-          unsigned* t1 = idc; idc = idn; idn = t1;
-          double* t2 = dc; dc = dn; dn = t2;
-        }
+        f = min(f, first);
       }
     }
     // ---- the k closest members
