@@ -368,8 +368,8 @@ rp_status rp_set_knn_method(rp_ctx *ctx, int32_t method);
  * The paper fixes none; results never depend on it.
  *   cache_bits: 8..12, a direct-mapped cache of 2^cache_bits recently met
  *     ids per query in shared memory (a miss only costs one more distance);
- *     0 = the largest cache that keeps the most CTAs (of 4 queries each)
- *     resident per SM, as registers and shared memory allow.
+ *     0 = 256 or 512 entries, the larger if it keeps the most CTAs (of 4
+ *     queries each) resident per SM that registers and shared memory allow.
  *   ctas_per_sm: at most this many CTAs per SM (0 = as many as one SM
  *     holds with the chosen cache, up to 16).
  * Errors: RP_EINVAL.

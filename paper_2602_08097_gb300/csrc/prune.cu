@@ -361,6 +361,15 @@ __global__ void __launch_bounds__(160, tc_min_ctas<DT, MAXM, TB>()) prune_tc_ker
       AT kacc = 0, nacc = 0;
       uint4 xs[8];  // uint8, one slice: the row stays here for the operand pass
       if constexpr (DT == kU8) {
+        // d2(p, x) = |p|^2 + |x|^2 - 2 <p, x>: an identity of integers, exact in
+        // 32-bit modular arithmetic since d2 < 2^32; |p|^2 is summed across the warp
+        unsigned dacc = 0, pacc = 0;
+        for (int64_t w4 = lane; w4 < elems / 4; w4 += 32) {
+          const unsigned pw = __ldg(reinterpret_cast<const unsigned*>(prow) + w4);
+          pacc = __dp4a(pw, pw, pacc);
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) pacc += __shfl_xor_sync(0xffffffffu, pacc, o);
         for (int sl = 0; sl < nslices; ++sl) {
           const int64_t rem = elems - int64_t(sl) * 128;
           const int kd = int(rem < 128 ? rem : 128);  // a multiple of 16 here
@@ -376,10 +385,11 @@ __global__ void __launch_bounds__(160, tc_min_ctas<DT, MAXM, TB>()) prune_tc_ker
           }
 #pragma unroll
           for (int c = 0; c < 8; ++c) {
-            kacc = Acc<kU8>::step4(xs[c], ys[c], kacc);
+            dacc = Acc<kU8>::dot4(xs[c], ys[c], dacc);
             nacc = Acc<kU8>::dot4(xs[c], xs[c], nacc);
           }
         }
+        kacc = pacc + nacc - 2u * dacc;
       } else {
         if (live_row) {
           float part = 0.f;  // the key is summed per 32-dimension slice (slice_rel_bound)
@@ -410,7 +420,20 @@ __global__ void __launch_bounds__(160, tc_min_ctas<DT, MAXM, TB>()) prune_tc_ker
       sk[t] = my_sk;
       named_sync(kBarProd, 128);
       int rank = t;
-      if (a.variant == 0 && live_row) {
+      // A list that Algorithm 1 wrote is already in its processing order
+      // ((d2, id) ascending): then every rank is the stored position.  Checked,
+      // not assumed: each candidate against the one before it (for float keys,
+      // "surely less", which chains, so no two keys of the list can be near).
+      bool in_order = true;
+      if (a.variant == 0) {
+        bool inv = false;
+        if (live_row && t > 0) {
+          if constexpr (DT == kU8) inv = !(sk[t - 1] < my_sk);
+          else inv = !sure_less(__uint_as_float(unsigned(sk[t - 1] >> 32)), kacc, E_rel, E_abs);
+        }
+        in_order = !prod_sync_or(inv);
+      }
+      if (!in_order && live_row) {
         // entries past the degree hold ~0 and never count
         const ulonglong2* sk2 = reinterpret_cast<const ulonglong2*>(sk);
         int cnt = 0;
@@ -427,13 +450,13 @@ __global__ void __launch_bounds__(160, tc_min_ctas<DT, MAXM, TB>()) prune_tc_ker
         // both ends of every such pair take their binary64 key, and those pairs
         // are ordered by it (ties by id), as Algorithm 1 reads d2 in binary64
         bool near = false;
-        if (a.variant == 0 && live_row) {
+        if (!in_order && live_row) {
           for (int j = 0; j < m && !near; ++j) {
             const float kj = __uint_as_float(unsigned(sk[j] >> 32));
             near = j != t && !sure_less(kj, kacc, E_rel, E_abs) && !sure_less(kacc, kj, E_rel, E_abs);
           }
         }
-        if (prod_sync_or(near)) {
+        if (!in_order && prod_sync_or(near)) {
           double* k64s = reinterpret_cast<double*>(pb + L::p_k64);  // stored order
           if (near) {
             my64 = canon_d2_f32(reinterpret_cast<const float*>(prow), reinterpret_cast<const float*>(xrow), a.d);
@@ -591,24 +614,30 @@ __global__ void __launch_bounds__(160, tc_min_ctas<DT, MAXM, TB>()) prune_tc_ker
             tmem_ld32(tmem + (uint32_t(32 * warp) << 16) + uint32_t(g * MAXM + c0), v);
             tmem_ld_wait();
             if (live_row) {
-              uint32_t wb[TB];
+              // x = 2 G - |t|^2 lies in [-|t|^2, |c|^2], an integer below 2^24,
+              // exact; q too.  x - q keeps its sign when rounded and is +0 when
+              // x = q, so its sign bit is exactly "x < q": not removed.  Columns
+              // go in last to first, so column c0 + j ends at bit j.
+              uint32_t nb[TB];
 #pragma unroll
-              for (int u = 0; u < TB; ++u) wb[u] = 0u;
+              for (int u = 0; u < TB; ++u) nb[u] = 0u;
 #pragma unroll
-              for (int j4 = 0; j4 < 32; j4 += 4) {
+              for (int j4 = 28; j4 >= 0; j4 -= 4) {
                 float x[4];
 #pragma unroll
-                for (int q = 0; q < 4; ++q) x[q] = fmaf(2.f, __uint_as_float(v[j4 + q]), -nt);  // exact integer
+                for (int q = 0; q < 4; ++q) x[q] = fmaf(2.f, __uint_as_float(v[j4 + q]), -nt);
 #pragma unroll
                 for (int u = 0; u < TB; ++u) {
                   if (u >= T) break;
                   const float4 q4 = *reinterpret_cast<const float4*>(qlo + u * MAXM + c0 + j4);
-                  wb[u] |= (x[0] >= q4.x ? 1u << j4 : 0u) | (x[1] >= q4.y ? 2u << j4 : 0u) |
-                           (x[2] >= q4.z ? 4u << j4 : 0u) | (x[3] >= q4.w ? 8u << j4 : 0u);
+                  nb[u] = __funnelshift_l(__float_as_uint(x[3] - q4.w), nb[u], 1);
+                  nb[u] = __funnelshift_l(__float_as_uint(x[2] - q4.z), nb[u], 1);
+                  nb[u] = __funnelshift_l(__float_as_uint(x[1] - q4.y), nb[u], 1);
+                  nb[u] = __funnelshift_l(__float_as_uint(x[0] - q4.x), nb[u], 1);
                 }
               }
 #pragma unroll
-              for (int u = 0; u < TB; ++u) mk[u][c0 >> 6] |= static_cast<unsigned long long>(wb[u]) << (c0 & 63);
+              for (int u = 0; u < TB; ++u) mk[u][c0 >> 6] |= static_cast<unsigned long long>(~nb[u]) << (c0 & 63);
             }
           }
         } else {

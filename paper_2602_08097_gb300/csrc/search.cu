@@ -446,6 +446,10 @@ __global__ void recall_kernel(const int32_t* __restrict__ found, int ld_found, c
 // The CTAs per SM a configured plan may ask for.
 constexpr int kMaxCtasPerSmCap = 16;
 constexpr int kMinCacheBits = 8, kMaxCacheBits = 12;
+// The default plan stops at 512 entries: a larger cache takes shared memory
+// that L1 would otherwise give to the neighbour rows and vectors, and measured
+// slower on 1M x 128 uint8 at L = 128 (1,024 entries 6% slower, 4,096 50%).
+constexpr int kDefaultMaxCacheBits = 9;
 
 // CTAs of search_kernel<DT> one SM holds with `bytes` of dynamic shared memory
 // (registers and shared memory both count), from the occupancy calculator.
@@ -458,7 +462,7 @@ cudaError_t resident_ctas(size_t bytes, size_t max_bytes, int* out) {
 
 // Default plan: the queries in flight hide the latency of each expansion, so
 // the search first maximises the CTAs per SM, then takes the largest id cache
-// (256 .. 4096 entries per warp) that keeps that many.  Plans are remembered
+// (256 or 512 entries per warp) that keeps that many.  Plans are remembered
 // per (dtype, L, row bytes); the occupancy queries run once for each.
 struct SearchPlan {
   int bits = kMinCacheBits;
@@ -480,7 +484,7 @@ cudaError_t default_plan(bool f32, int L, int64_t row_bytes, SearchPlan* plan) {
   const size_t max_bytes = warp_bytes(L, row_bytes, f32, kMaxCacheBits) * kWarps;
   SearchPlan best;
   int best_ctas = 0;
-  for (int b = kMinCacheBits; b <= kMaxCacheBits; ++b) {
+  for (int b = kMinCacheBits; b <= kDefaultMaxCacheBits; ++b) {
     int nb = 0;
     const size_t bytes = warp_bytes(L, row_bytes, f32, b) * kWarps;
     cudaError_t err = f32 ? resident_ctas<kF32>(bytes, max_bytes, &nb) : resident_ctas<kU8>(bytes, max_bytes, &nb);
