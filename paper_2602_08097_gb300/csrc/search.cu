@@ -115,21 +115,27 @@ __device__ inline WarpSmem carve(unsigned char* base, int L, int64_t row_bytes, 
 }
 
 // d2(q, v) in the search's working precision, as order-preserving bits.
+// uint8: d2 = |q|^2 + |x|^2 - 2 <q, x> from dp4a alone, `qn` = |q|^2 (an
+// identity of integers, exact in 32-bit modular arithmetic since d2 < 2^32).
 template <int DT>
 __device__ __forceinline__ unsigned dist_bits(const uint8_t* __restrict__ q, const uint8_t* __restrict__ x,
-                                              int64_t row_bytes) {
+                                              int64_t row_bytes, unsigned qn) {
   const uint4* pq = reinterpret_cast<const uint4*>(q);
   const uint4* px = reinterpret_cast<const uint4*>(x);
   if constexpr (DT == kU8) {
-    unsigned acc = 0;
+    unsigned dot = 0, xn = 0;
     for (int64_t c = 0; c < row_bytes / 16; ++c) {
       const uint4 a = pq[c], b = __ldg(px + c);
-      acc = sqdiff4_u8(a.x, b.x, acc);
-      acc = sqdiff4_u8(a.y, b.y, acc);
-      acc = sqdiff4_u8(a.z, b.z, acc);
-      acc = sqdiff4_u8(a.w, b.w, acc);
+      dot = __dp4a(a.x, b.x, dot);
+      dot = __dp4a(a.y, b.y, dot);
+      dot = __dp4a(a.z, b.z, dot);
+      dot = __dp4a(a.w, b.w, dot);
+      xn = __dp4a(b.x, b.x, xn);
+      xn = __dp4a(b.y, b.y, xn);
+      xn = __dp4a(b.z, b.z, xn);
+      xn = __dp4a(b.w, b.w, xn);
     }
-    return acc;
+    return qn + xn - 2u * dot;
   } else {
     // summed per 32-dimension slice (slice_rel_bound)
     float acc = 0.f;
@@ -213,6 +219,15 @@ __global__ void __launch_bounds__(kWarps * 32, 9) search_kernel(SearchArgs a) {
     for (int c = lane; c < a.row_bytes / 16; c += 32) reinterpret_cast<uint4*>(S.q)[c] = src[c];
     for (int c = lane; c < centries; c += 32) S.cache[c] = 0xffffffffu;
     __syncwarp();
+    unsigned qn = 0;  // uint8: |q|^2
+    if constexpr (DT == kU8) {
+      for (int w4 = lane; w4 < a.row_bytes / 4; w4 += 32) {
+        const unsigned qw = reinterpret_cast<const unsigned*>(S.q)[w4];
+        qn = __dp4a(qw, qw, qn);
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) qn += __shfl_xor_sync(0xffffffffu, qn, o);
+    }
 
     unsigned* const keyc = S.key;
     unsigned* const idc = S.idv;
@@ -221,7 +236,7 @@ __global__ void __launch_bounds__(kWarps * 32, 9) search_kernel(SearchArgs a) {
     int f = 0;  // the members before index f are all expanded
     if (lane == 0) {
       const unsigned s = unsigned(start);
-      keyc[0] = dist_bits<DT>(S.q, a.X + int64_t(s) * a.row_bytes, a.row_bytes);
+      keyc[0] = dist_bits<DT>(S.q, a.X + int64_t(s) * a.row_bytes, a.row_bytes, qn);
       idc[0] = s;
       if (f32) dc[0] = qnan;
       S.cache[(s * 0x9E3779B1u) >> cshift] = s;
@@ -267,7 +282,7 @@ __global__ void __launch_bounds__(kWarps * 32, 9) search_kernel(SearchArgs a) {
         }
         if (!__any_sync(0xffffffffu, fresh)) continue;
         unsigned kv = 0xffffffffu;
-        if (fresh) kv = dist_bits<DT>(S.q, a.X + int64_t(v) * a.row_bytes, a.row_bytes);
+        if (fresh) kv = dist_bits<DT>(S.q, a.X + int64_t(v) * a.row_bytes, a.row_bytes, qn);
         // A full list keeps only entries before its L-th: a point behind it
         // would be cut right after the merge, so it skips the merge.
         bool enters = fresh;
