@@ -41,13 +41,6 @@ constexpr int kWarps = 4;  // warps (queries in flight) per CTA
 constexpr unsigned kVisited = 0x80000000u;
 constexpr unsigned kIdMask = 0x7fffffffu;
 
-// A member's neighbour list, read when the member is first met (beside its
-// vector), so expanding it needs no row_ptr round trip: first edge in the
-// high 48 bits, degree (<= RP_MAX_DEGREE < 2^16) in the low 16.
-__device__ __forceinline__ unsigned long long pack_adj(int64_t e0, int64_t e1) {
-  return (static_cast<unsigned long long>(e0) << 16) | static_cast<unsigned long long>(e1 - e0);
-}
-
 struct SearchArgs {
   const uint8_t* X;
   int64_t row_bytes;
@@ -73,12 +66,10 @@ struct SearchArgs {
 struct WarpSmem {
   unsigned* key;   // the list: distance bits, sorted by (distance, id)
   unsigned* idv;   // its ids (| kVisited once expanded)
-  unsigned long long* adj;  // its neighbour lists: first edge << 16 | degree
   double* d64;     // float data: binary64 distances of the list (NaN until computed)
   unsigned* ckey;  // a batch's new members, then
   unsigned* cid;
   int* clo;        // their insertion points (sorted: the merge's shift table)
-  unsigned long long* cadj;
   double* cd64;
   uint8_t* q;
   unsigned* cache;  // direct-mapped ids met by this query (0xffffffff = empty)
@@ -88,7 +79,7 @@ __host__ __device__ inline size_t list_cap(int L) { return (size_t(L) + 3) & ~si
 
 __host__ __device__ inline size_t warp_bytes(int L, int64_t row_bytes, bool f32, int cache_bits) {
   const size_t cap = list_cap(L);
-  size_t b = cap * 16 + 32 * 20;  // list keys, ids, lists; batch keys, ids, insertion points, lists
+  size_t b = cap * 8 + 32 * 12;  // list keys + ids; batch keys, ids, insertion points
   if (f32) b += cap * 8 + 32 * 8;
   b += size_t(row_bytes);
   b += size_t(4) << cache_bits;
@@ -101,10 +92,6 @@ __device__ inline WarpSmem carve(unsigned char* base, int L, int64_t row_bytes, 
   unsigned char* p = base;
   w.cache = reinterpret_cast<unsigned*>(p);
   p += size_t(4) << cache_bits;
-  w.adj = reinterpret_cast<unsigned long long*>(p);
-  p += cap * 8;
-  w.cadj = reinterpret_cast<unsigned long long*>(p);
-  p += 32 * 8;
   if (f32) {
     w.d64 = reinterpret_cast<double*>(p);
     p += cap * 8;
@@ -244,7 +231,6 @@ __global__ void __launch_bounds__(kWarps * 32, 9) search_kernel(SearchArgs a) {
 
     unsigned* const keyc = S.key;
     unsigned* const idc = S.idv;
-    unsigned long long* const adjc = S.adj;
     double* const dc = S.d64;
     int size = 1;
     int f = 0;  // the members before index f are all expanded
@@ -252,7 +238,6 @@ __global__ void __launch_bounds__(kWarps * 32, 9) search_kernel(SearchArgs a) {
       const unsigned s = unsigned(start);
       keyc[0] = dist_bits<DT>(S.q, a.X + int64_t(s) * a.row_bytes, a.row_bytes, qn);
       idc[0] = s;
-      adjc[0] = pack_adj(row_ptr[s], row_ptr[s + 1]);
       if (f32) dc[0] = qnan;
       S.cache[(s * 0x9E3779B1u) >> cshift] = s;
     }
@@ -276,12 +261,12 @@ __global__ void __launch_bounds__(kWarps * 32, 9) search_kernel(SearchArgs a) {
         if (lane == 0) raise_status(a.status, kDevOverflow, qi);
         break;
       }
+      const unsigned ps = idc[pos] & kIdMask;
       __syncwarp();
       if (lane == 0) idc[pos] |= kVisited;
       __syncwarp();
       f = pos + 1;
-      const unsigned long long pa = adjc[pos];
-      const int64_t e0 = int64_t(pa >> 16), e1 = e0 + int64_t(pa & 0xffffu);
+      const int64_t e0 = row_ptr[ps], e1 = row_ptr[ps + 1];
       for (int64_t eb = e0; eb < e1; eb += 32) {
         // ---- new neighbours of this batch
         const int64_t e = eb + lane;
@@ -297,11 +282,7 @@ __global__ void __launch_bounds__(kWarps * 32, 9) search_kernel(SearchArgs a) {
         }
         if (!__any_sync(0xffffffffu, fresh)) continue;
         unsigned kv = 0xffffffffu;
-        unsigned long long av = 0;
-        if (fresh) {
-          av = pack_adj(row_ptr[v], row_ptr[v + 1]);  // loads issued beside the vector's
-          kv = dist_bits<DT>(S.q, a.X + int64_t(v) * a.row_bytes, a.row_bytes, qn);
-        }
+        if (fresh) kv = dist_bits<DT>(S.q, a.X + int64_t(v) * a.row_bytes, a.row_bytes, qn);
         // A full list keeps only entries before its L-th: a point behind it
         // would be cut right after the merge, so it skips the merge.
         bool enters = fresh;
@@ -335,12 +316,11 @@ __global__ void __launch_bounds__(kWarps * 32, 9) search_kernel(SearchArgs a) {
           S.ckey[r] = kv;
           S.cid[r] = v;
           S.clo[r] = lo;
-          S.cadj[r] = av;
           if (f32) S.cd64[r] = cand_d64;
         }
         __syncwarp();
         unsigned myk = 0xffffffffu, myid = 0xffffffffu;
-        int mylo = 0x7fffffff, myr = lane;  // myr: the compacted slot, for the list's adjacency word
+        int mylo = 0x7fffffff;
         double myd = qnan;
         if (lane < nf) {
           myk = S.ckey[lane];
@@ -358,7 +338,6 @@ __global__ void __launch_bounds__(kWarps * 32, 9) search_kernel(SearchArgs a) {
               const unsigned ok = __shfl_xor_sync(0xffffffffu, myk, j);
               const unsigned oi = __shfl_xor_sync(0xffffffffu, myid, j);
               const int olo = __shfl_xor_sync(0xffffffffu, mylo, j);
-              const int orr = __shfl_xor_sync(0xffffffffu, myr, j);
               // dec: 1 = my entry comes first, 0 = the partner's, -1 = undecided
               int dec;
               const bool me_empty = myid == 0xffffffffu, o_empty = oi == 0xffffffffu;
@@ -391,7 +370,6 @@ __global__ void __launch_bounds__(kWarps * 32, 9) search_kernel(SearchArgs a) {
                 myk = ok;
                 myid = oi;
                 mylo = olo;
-                myr = orr;
                 myd = od;
               }
             }
@@ -408,13 +386,11 @@ __global__ void __launch_bounds__(kWarps * 32, 9) search_kernel(SearchArgs a) {
           const int i = c0 + lane;
           const bool mv = i >= first && i < size;
           unsigned bk = 0, bi = 0;
-          unsigned long long ba = 0;
           double bd = 0.0;
           int np = L;
           if (mv) {
             bk = keyc[i];
             bi = idc[i];
-            ba = adjc[i];
             if (f32) bd = dc[i];
             int l2 = 1, h2 = nf;  // clo[0] = first <= i
             while (l2 < h2) {
@@ -428,7 +404,6 @@ __global__ void __launch_bounds__(kWarps * 32, 9) search_kernel(SearchArgs a) {
           if (mv && np < L) {
             keyc[np] = bk;
             idc[np] = bi;
-            adjc[np] = ba;
             if (f32) dc[np] = bd;
           }
           __syncwarp();
@@ -436,7 +411,6 @@ __global__ void __launch_bounds__(kWarps * 32, 9) search_kernel(SearchArgs a) {
         if (lane < nf && mylo + lane < L) {
           keyc[mylo + lane] = myk;
           idc[mylo + lane] = myid;
-          adjc[mylo + lane] = S.cadj[myr];
           if (f32) dc[mylo + lane] = myd;
         }
         __syncwarp();
