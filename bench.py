@@ -20,6 +20,8 @@ search results copied out, every step.
 jobs and query batches through the library's scheduler (rp_server_*), the
 continuous-batching scheduler against the plain serial path, at offered loads
 relative to the serial path's capacity; p50/p99 latency, QPS and recall@100.
+It runs over the sift base (8 GB of tuned graphs, so the stream evicts) and
+over the deep base (120 GB), with the queries of that workload.
 
 `--workload gist` runs the batched float sweep instead (1,000,000 x 960
 float32 rows, |N(0,1)| * 0.05 then L2-normalised; nine targets: alpha 1.175 down
@@ -55,7 +57,9 @@ METRIC = "RP-Tuning nodes/s per α (batched vs plain, same GPU); query p50/p99 a
 UNIT = "nodes/s per alpha"
 BASE_ALPHA, BASE_R, KCAND = 1.2, 64, 128
 K_SEARCH = 100
-SERVE_BUDGET_GB = 8                     # resident tuned graphs of the serving leg (~30 at this size)
+# graph budget of the serving leg: 8 GB keeps ~30 sift-sized tuned graphs (the
+# stream evicts); the deep stream runs under 120 GB of tuned graphs
+SERVE_BUDGET_GB = {"sift": 8, "deep": 120}
 SERVE_LOADS = (0.5, 0.8, 1.0, 2.0, 4.0)  # offered load / capacity of the serial path
 
 # The paper-shaped workloads (synthetic; recipes in datagen).  sift is the
@@ -453,7 +457,7 @@ def run_ours(args):
                "d2h_bytes_per_step": int(d2h), "ms_per_step": 1000 * e2e_s}
 
     serving = None
-    if not args.quick and not args.no_serve and args.workload == "sift":
+    if not args.quick and not args.no_serve and args.workload in SERVE_BUDGET_GB:
         serving = serve_bench(rp, ctx, base, Q, gt, args)
 
     cpu = None
@@ -505,7 +509,8 @@ def serve_bench(rp, ctx, base, Q, gt, args):
     Latency is submission to completion, from the scheduler's own clock."""
     from paper_2602_08097_gb300.serving import make_requests, replay
     stream = datagen.poisson_stream(args.serve_requests, 1.0, seed=3001, prune_frac=0.10)
-    budget = SERVE_BUDGET_GB << 30
+    budget_gb = SERVE_BUDGET_GB[args.workload]
+    budget = budget_gb << 30
 
     def run(serial, time_scale):
         reqs = make_requests(stream, Q, seed=3001)
@@ -524,7 +529,7 @@ def serve_bench(rp, ctx, base, Q, gt, args):
     sat = run(True, 0.0)
     span_s = stream[-1]["t"]
     cap_rps = sat["requests"] / (sat["stats"]["busy_ns"] / 1e9)
-    out = {"requests": args.serve_requests, "graph_budget_gb": SERVE_BUDGET_GB,
+    out = {"requests": args.serve_requests, "graph_budget_gb": budget_gb,
            "serial_capacity_req_per_s": cap_rps, "loads": {}}
     for load in SERVE_LOADS:
         rate = load * cap_rps
