@@ -386,11 +386,13 @@ rp_status rp_set_search_config(rp_ctx *ctx, int32_t cache_bits, int32_t ctas_per
  * Each scheduling round admits the waiting requests in arrival order while
  * (a) the distinct tuned graphs they address fit in the graph budget and
  * (b) their queries fit in max_batch_queries (the first waiting request is
- * always admitted).  The round then evicts least-recently-used tuned graphs
- * that none of its requests address until the new ones fit, tunes all
- * missing graphs in batched launches (up to 16 targets each), and runs all
- * of its searches in one mixed launch per k (rp_search_multi).  Results
- * depend only on each request, never on the mix.  With `serial` set the
+ * always admitted).  Requests on graphs that are already resident (or on the
+ * base) run first and complete at once: their searches in one mixed launch
+ * per k (rp_search_multi).  The round then evicts least-recently-used tuned
+ * graphs that none of its requests address until the new ones fit, tunes all
+ * missing graphs in batched launches (up to 16 targets each), and runs the
+ * remaining searches in one mixed launch per k.  Results depend only on each
+ * request, never on the mix.  With `serial` set the
  * scheduler is the plain path instead: one request per round, one target per
  * tuning launch.
  * ---------------------------------------------------------------------- */

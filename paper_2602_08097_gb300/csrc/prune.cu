@@ -140,6 +140,19 @@ __device__ __forceinline__ bool tier3_dominates(const PruneArgs& a, int32_t u, i
   return canon_dominates(A2, d2a, d2b);
 }
 
+// A float domination test the Gram tier left undecided: row `t` of the node
+// (candidate ids[t]) against column `c`, target A: single-precision difference
+// form from the rows, then binary64.
+__device__ __forceinline__ bool recheck_dominates(const PruneArgs& a, const int32_t* ids, const float* key,
+                                                  double* key64, int t, int c, int u, int p, float E_rel,
+                                                  float E_abs) {
+  const int64_t A2 = int64_t(a.A[u]) * a.A[u];
+  const float d2a = row_d2<kF32>(a.X + int64_t(ids[t]) * a.row_bytes, a.X + int64_t(ids[c]) * a.row_bytes,
+                                 a.row_bytes);
+  const int rr = sure_dominates(float(A2), d2a, key[c], E_rel, E_abs);
+  return rr >= 0 ? (rr == 1) : tier3_dominates(a, ids[t], ids[c], p, &key64[c], double(A2));
+}
+
 // ---------------------------------------------------------------------------
 // tensor-core path: the candidate Gram on tcgen05
 // ---------------------------------------------------------------------------
@@ -187,7 +200,11 @@ struct TcLayout {
   static constexpr size_t off_misc = off_prod + NG * p_bytes;
   static constexpr size_t q_node = 256, q_deg = q_node + 32 * 4, q_e0 = q_deg + 32 * 4;
   static constexpr size_t misc_bytes = q_e0 + 32 * 8;
-  static constexpr size_t bytes = (off_misc + misc_bytes + 127) & ~size_t(127);
+  // float rows: the slot's undecided (row, column, target) triples, resolved
+  // after the mask pass by all producer threads at once
+  static constexpr int rq_cap = NOP == 2 ? 1024 : 0;
+  static constexpr size_t off_rq = off_misc + misc_bytes;
+  static constexpr size_t bytes = (off_rq + size_t(rq_cap) * 4 + 127) & ~size_t(127);
 };
 
 // floor(1e6 k / A2) for integers, exactly: a single-precision estimate (off
@@ -260,6 +277,8 @@ __global__ void __launch_bounds__(160, tc_min_ctas<DT, MAXM, TB>()) prune_tc_ker
   int64_t* qe0 = reinterpret_cast<int64_t*>(smem_raw + L::off_misc + L::q_e0);
   uint64_t* mbar = reinterpret_cast<uint64_t*>(smem_raw + L::off_misc + 128);
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem_raw + L::off_misc + 144);
+  int* rq_count = misc + 14;  // [2]: per slot parity
+  uint32_t* rq = reinterpret_cast<uint32_t*>(smem_raw + L::off_rq);
   auto slot_base = [&](int s, int g) { return smem_raw + L::off_slots + (size_t(s) * NG + g) * L::s_bytes; };
   const float E_rel = slice_rel_bound(a.d), E_abs = abs_bound(a.d);
   const int count = *a.count;
@@ -268,6 +287,7 @@ __global__ void __launch_bounds__(160, tc_min_ctas<DT, MAXM, TB>()) prune_tc_ker
   if (r == 0) {
     mbar_init(mbar, 1);
     misc[12] = kClaim;  // empty claim queue
+    rq_count[0] = rq_count[1] = 0;
   }
   tc_fence_before();
   __syncthreads();
@@ -302,6 +322,8 @@ __global__ void __launch_bounds__(160, tc_min_ctas<DT, MAXM, TB>()) prune_tc_ker
     for (int k = 0;; ++k) {
       const int s = k & 1;
       named_sync(kBarFree + s, 160);  // the consumer is done with this slot
+      // every producer has left the previous slot, and with it that slot's queue
+      if (DT == kF32 && r == 0) rq_count[s ^ 1] = 0;
       if (warp == 0) {
         // next NG nodes from the claim queue; warp 0 refills it kClaim nodes at
         // a time (one atomic, the row bounds loaded by all lanes at once)
@@ -670,13 +692,17 @@ __global__ void __launch_bounds__(160, tc_min_ctas<DT, MAXM, TB>()) prune_tc_ker
                   } else if (lo > qhi[u * MAXM + c]) {
                     dom = false;
                   } else {
-                    // difference-form single precision from the rows, then binary64
-                    const int64_t A2 = int64_t(a.A[u]) * a.A[u];
-                    const float d2a = row_d2<kF32>(a.X + int64_t(ids[t]) * a.row_bytes,
-                                                   a.X + int64_t(ids[c]) * a.row_bytes, a.row_bytes);
-                    ++n_rechecks;
-                    const int rr = sure_dominates(float(A2), d2a, key[c], E_rel, E_abs);
-                    dom = rr >= 0 ? (rr == 1) : tier3_dominates(a, ids[t], ids[c], p, &key64[c], double(A2));
+                    // Undecided: queued, and resolved after this pass by all producer
+                    // threads at once (one lane's recheck no longer holds up its warp
+                    // and, at the barrier, the others); decided here if the queue is full.
+                    const int qi = atomicAdd(rq_count + s, 1);
+                    if (qi < L::rq_cap) {
+                      rq[qi] = (unsigned(g * MAXM + t) << 16) | (unsigned(c) << 5) | unsigned(u);
+                      dom = false;
+                    } else {
+                      dom = recheck_dominates(a, ids, key, key64, t, c, u, p, E_rel, E_abs);
+                      ++n_rechecks;
+                    }
                   }
                   if (dom) mk[u][w] |= bit;
                 }
@@ -697,6 +723,26 @@ __global__ void __launch_bounds__(160, tc_min_ctas<DT, MAXM, TB>()) prune_tc_ker
       tc_fence_before();
       named_sync(kBarProd, 128);  // every producer's masks and TMEM reads are done
       tc_fence_after();
+      if constexpr (DT == kF32) {
+        // the queued tests, one per thread: a removal sets its bit in the row's mask
+        const int nq = min(rq_count[s], L::rq_cap);  // the same for every producer
+        if (nq > 0) {
+          for (int i = r; i < nq; i += 128) {
+            const uint32_t e = rq[i];
+            const int tr = int(e >> 16), c = int((e >> 5) & 0x7ffu), u = int(e & 31u);
+            const int gq = tr / MAXM, tq = tr % MAXM;
+            unsigned char* sbq = slot_base(s, gq);
+            if (recheck_dominates(a, reinterpret_cast<const int32_t*>(sbq + L::s_ids),
+                                  reinterpret_cast<const float*>(sbq + L::s_key),
+                                  reinterpret_cast<double*>(sbq + L::s_key64), tq, c, u, misc[s * 2 + gq], E_rel,
+                                  E_abs))
+              atomicOr(reinterpret_cast<unsigned long long*>(sbq + L::s_masks) + (u * MAXM + tq) * MW + (c >> 6),
+                       1ull << (c & 63));
+            ++n_rechecks;
+          }
+          named_sync(kBarProd, 128);
+        }
+      }
       bar_arrive(kBarFull + s, 160);
     }
     if constexpr (DT == kF32) {

@@ -117,6 +117,8 @@ struct rp_server {
 
   void run();
   void round(std::vector<Req*>& batch, int32_t round_no);
+  void run_searches(std::vector<Req*>& rs);
+  void publish(std::vector<Req*>& rs);
   void evict_for(size_t nnew, const std::map<Key, int>& needed);
 };
 
@@ -137,6 +139,82 @@ void rp_server::evict_for(size_t nnew, const std::map<Key, int>& needed) {
   }
 }
 
+void rp_server::run_searches(std::vector<Req*>& rs) {
+  auto graph_of = [&](const Key& k) -> rp_graph {
+    if (k.first == 0) return cfg.base;
+    auto it = resident.find(k);
+    return it == resident.end() ? 0 : it->second->second;
+  };
+  for (Req* r : rs)
+    if (r->status == RP_OK) r->graph = graph_of(r->key);
+  // one mixed search launch per k
+  std::map<int32_t, std::vector<Req*>> by_k;
+  for (Req* r : rs)
+    if (r->search && r->status == RP_OK) by_k[r->k].push_back(r);
+  for (auto& kv : by_k) {
+    const int32_t k = kv.first;
+    std::vector<Req*>& group = kv.second;
+    std::vector<rp_graph> graphs;
+    std::map<rp_graph, int32_t> gidx;
+    std::vector<int32_t> qg, qL;
+    int64_t nq = 0;
+    for (Req* r : group) nq += r->nq;
+    qbuf.resize(size_t(nq) * row_bytes);
+    ibuf.resize(size_t(nq) * size_t(k));
+    dbuf.resize(size_t(nq) * size_t(k));
+    qg.reserve(size_t(nq));
+    qL.reserve(size_t(nq));
+    int64_t off = 0;
+    for (Req* r : group) {
+      auto ins = gidx.emplace(r->graph, int32_t(graphs.size()));
+      if (ins.second) graphs.push_back(r->graph);
+      std::memcpy(qbuf.data() + size_t(off) * row_bytes, r->q.data(), size_t(r->nq) * row_bytes);
+      for (int64_t i = 0; i < r->nq; ++i) {
+        qg.push_back(ins.first->second);
+        qL.push_back(r->L_eff);
+      }
+      off += r->nq;
+    }
+    const rp_status s = ex.search_multi(ex.user, graphs.data(), int32_t(graphs.size()), qg.data(), qL.data(),
+                                        qbuf.data(), nq, k, ibuf.data(), dbuf.data());
+    if (s != RP_OK) set_error("search launch over %lld queries failed with status %d", (long long)nq, s);
+    off = 0;
+    for (Req* r : group) {
+      if (s == RP_OK) {
+        const size_t m = size_t(r->nq) * size_t(k);
+        std::memcpy(r->ids, ibuf.data() + size_t(off) * size_t(k), m * 4);
+        if (r->dists) std::memcpy(r->dists, dbuf.data() + size_t(off) * size_t(k), m * 4);
+      } else {
+        r->status = s;
+        r->graph = 0;
+      }
+      off += r->nq;
+    }
+    std::lock_guard<std::mutex> lk(mu);
+    stats.search_launches += 1;
+  }
+}
+
+void rp_server::publish(std::vector<Req*>& rs) {
+  const int64_t t_done = now_ns(t0);
+  std::lock_guard<std::mutex> lk(mu);
+  for (Req* r : rs) {
+    r->info.state = RP_REQ_DONE;
+    r->info.status = r->status;
+    r->info.graph = r->graph;
+    r->info.done_ns = t_done;
+    r->q.clear();
+    r->q.shrink_to_fit();
+    if (r->status == RP_OK) {
+      stats.requests_done += 1;
+      stats.queries_done += r->nq;
+    } else {
+      stats.requests_failed += 1;
+    }
+  }
+  cv_done.notify_all();
+}
+
 void rp_server::round(std::vector<Req*>& batch, int32_t round_no) {
   const int64_t t_start = now_ns(t0);
   {
@@ -151,8 +229,31 @@ void rp_server::round(std::vector<Req*>& batch, int32_t round_no) {
   std::map<Key, int> needed;  // key -> order
   std::vector<Key> missing;
   for (Req* r : batch) {
+    r->status = RP_OK;
     if (r->key.first == 0) continue;
     if (needed.emplace(r->key, int(needed.size())).second && !resident.count(r->key)) missing.push_back(r->key);
+  }
+  // mark use (most recent last)
+  for (auto& kv : needed) {
+    auto it = resident.find(kv.first);
+    if (it != resident.end()) lru.splice(lru.end(), lru, it->second);
+  }
+  // Requests on graphs that are already resident (or on the base) run before
+  // this round's tuning launch and complete at once: a search never waits for
+  // a prune of the whole base that other requests of the round asked for.
+  std::vector<Req*> rest;
+  if (!missing.empty()) {
+    std::vector<Req*> early;
+    for (Req* r : batch) {
+      const bool ready = r->key.first == 0 || resident.count(r->key);
+      (ready ? early : rest).push_back(r);
+    }
+    if (!early.empty()) {
+      run_searches(early);
+      publish(early);
+    }
+  } else {
+    rest = batch;
   }
   std::map<Key, rp_status> failed;
   evict_for(missing.size(), needed);
@@ -188,86 +289,18 @@ void rp_server::round(std::vector<Req*>& batch, int32_t round_no) {
     stats.resident_graphs = int64_t(lru.size());
     stats.peak_resident_graphs = std::max(stats.peak_resident_graphs, stats.resident_graphs);
   }
-  // mark use (most recent last) and resolve each request's graph
-  for (auto& kv : needed) {
-    auto it = resident.find(kv.first);
-    if (it != resident.end()) lru.splice(lru.end(), lru, it->second);
-  }
-  auto graph_of = [&](const Key& k) -> rp_graph {
-    if (k.first == 0) return cfg.base;
-    auto it = resident.find(k);
-    return it == resident.end() ? 0 : it->second->second;
-  };
-  for (Req* r : batch) {
+  for (Req* r : rest) {
     auto f = failed.find(r->key);
-    r->status = f == failed.end() ? RP_OK : f->second;
-    r->graph = r->status == RP_OK ? graph_of(r->key) : 0;
-  }
-  // one mixed search launch per k
-  std::map<int32_t, std::vector<Req*>> by_k;
-  for (Req* r : batch)
-    if (r->search && r->status == RP_OK) by_k[r->k].push_back(r);
-  for (auto& kv : by_k) {
-    const int32_t k = kv.first;
-    std::vector<Req*>& rs = kv.second;
-    std::vector<rp_graph> graphs;
-    std::map<rp_graph, int32_t> gidx;
-    std::vector<int32_t> qg, qL;
-    int64_t nq = 0;
-    for (Req* r : rs) nq += r->nq;
-    qbuf.resize(size_t(nq) * row_bytes);
-    ibuf.resize(size_t(nq) * size_t(k));
-    dbuf.resize(size_t(nq) * size_t(k));
-    qg.reserve(size_t(nq));
-    qL.reserve(size_t(nq));
-    int64_t off = 0;
-    for (Req* r : rs) {
-      auto ins = gidx.emplace(r->graph, int32_t(graphs.size()));
-      if (ins.second) graphs.push_back(r->graph);
-      std::memcpy(qbuf.data() + size_t(off) * row_bytes, r->q.data(), size_t(r->nq) * row_bytes);
-      for (int64_t i = 0; i < r->nq; ++i) {
-        qg.push_back(ins.first->second);
-        qL.push_back(r->L_eff);
-      }
-      off += r->nq;
+    if (f != failed.end()) {
+      r->status = f->second;
+      r->graph = 0;
     }
-    const rp_status s = ex.search_multi(ex.user, graphs.data(), int32_t(graphs.size()), qg.data(), qL.data(),
-                                        qbuf.data(), nq, k, ibuf.data(), dbuf.data());
-    if (s != RP_OK) set_error("search launch over %lld queries failed with status %d", (long long)nq, s);
-    off = 0;
-    for (Req* r : rs) {
-      if (s == RP_OK) {
-        const size_t m = size_t(r->nq) * size_t(k);
-        std::memcpy(r->ids, ibuf.data() + size_t(off) * size_t(k), m * 4);
-        if (r->dists) std::memcpy(r->dists, dbuf.data() + size_t(off) * size_t(k), m * 4);
-      } else {
-        r->status = s;
-        r->graph = 0;
-      }
-      off += r->nq;
-    }
-    std::lock_guard<std::mutex> lk(mu);
-    stats.search_launches += 1;
   }
-  const int64_t t_done = now_ns(t0);
+  run_searches(rest);
+  publish(rest);
   std::lock_guard<std::mutex> lk(mu);
-  for (Req* r : batch) {
-    r->info.state = RP_REQ_DONE;
-    r->info.status = r->status;
-    r->info.graph = r->graph;
-    r->info.done_ns = t_done;
-    r->q.clear();
-    r->q.shrink_to_fit();
-    if (r->status == RP_OK) {
-      stats.requests_done += 1;
-      stats.queries_done += r->nq;
-    } else {
-      stats.requests_failed += 1;
-    }
-  }
   stats.rounds += 1;
-  stats.busy_ns += t_done - t_start;
-  cv_done.notify_all();
+  stats.busy_ns += now_ns(t0) - t_start;
 }
 
 void rp_server::run() {

@@ -98,6 +98,32 @@ def test_random_graphs_all_paths(ctx, dtype, deg_hi):
     rp.rp_graph_free(ctx, g)
 
 
+
+@pytest.mark.parametrize("dtype", ["u8", "f32"])
+@pytest.mark.parametrize("variant", ["sorted", "unsorted"])
+def test_lists_in_and_out_of_algorithm_order(ctx, dtype, variant):
+    """A list that RobustPrune wrote is already in Algorithm 1's processing
+    order, and the kernel then takes each rank from the stored position; a
+    reordered list takes the counted ranks.  Both kinds share launches and
+    slots here (every third list reversed, one in seven rotated by one)."""
+    X = datagen.dataset("sift" if dtype == "u8" else "deep", 3000)
+    row_ptr, col = oracle.knn_base(X, 64, 1.2, 64)
+    col = col.copy()
+    for v in range(len(row_ptr) - 1):
+        a, b = row_ptr[v], row_ptr[v + 1]
+        if v % 3 == 0:
+            col[a:b] = col[a:b][::-1]
+        elif v % 7 == 0 and b - a > 1:
+            col[a:b] = np.roll(col[a:b], 1)
+    vt = rp.RP_SORTED if variant == "sorted" else rp.RP_UNSORTED
+    g = rp.rp_load_graph(ctx, X, row_ptr, col)
+    targets = [(1.15, 64), (1.05, 40), (1.0, 16)]
+    outs = rp.rp_tune_batch(ctx, g, [t[0] for t in targets], [t[1] for t in targets], vt)
+    for t, o in zip(targets, outs):
+        _same_csr(rp.rp_graph_export(ctx, o), oracle.rp_tune(X, row_ptr, col, *t, variant), f"{dtype} {variant} {t}")
+        rp.rp_graph_free(ctx, o)
+    rp.rp_graph_free(ctx, g)
+
 def test_ties_and_duplicate_vectors(ctx):
     # many identical vectors and exact distance ties (uint8 values in {0, 1})
     rng = np.random.default_rng(5)

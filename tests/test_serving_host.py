@@ -177,6 +177,56 @@ def test_rounds_batch_what_arrived(world):
         rp.rp_server_destroy(srv)
 
 
+
+class GatedExec(OracleExec):
+    """Tuning call i waits on gates[i] (at most 10 s)."""
+
+    def __init__(self, X, base, start, gates):
+        super().__init__(X, base, start)
+        self.gates = list(gates)
+        self.calls = 0
+
+    def tune(self, user, src, alphas, Rs, T, outs):
+        i = self.calls
+        self.calls += 1
+        if i < len(self.gates):
+            self.gates[i].wait(10)
+        return super().tune(user, src, alphas, Rs, T, outs)
+
+
+def test_resident_requests_do_not_wait_for_the_rounds_tuning(world):
+    """In a round that tunes, the searches on graphs already resident (and on
+    the base) complete before its tuning call returns; the rest after it."""
+    X, base, start, Q = world
+    g1, g2 = threading.Event(), threading.Event()
+    ex = GatedExec(X, base, start, [g1, g2])
+    srv = ex.server()
+    try:
+        first = rp.rp_submit_tune(srv, 1.15, 24)  # round 1: held in its tuning call by g1
+        early = [rp.rp_submit_search(srv, 1.15, 24, Q[0:3], 12, 10), rp.rp_submit_search(srv, 0.0, 0, Q[3:5], 12, 10)]
+        late = [(rp.rp_submit_tune(srv, 1.1, 24), None, None), rp.rp_submit_search(srv, 1.1, 24, Q[5:8], 12, 10)]
+        g1.set()
+        assert rp.rp_poll(srv, first, 20000)["round"] == 1
+        for rid, _, _ in early:  # round 2's tuning call is still held by g2
+            info = rp.rp_poll(srv, rid, 5000)
+            assert info is not None and info["round"] == 2 and info["status"] == rp.RP_OK
+        assert rp.rp_poll(srv, late[0][0], 50) is None and rp.rp_poll(srv, late[1][0], 50) is None
+        g2.set()
+        for rid, _, _ in late:
+            info = rp.rp_poll(srv, rid, 20000)
+            assert info is not None and info["round"] == 2 and info["status"] == rp.RP_OK
+        st = rp.rp_server_stats(srv)
+        assert st["rounds"] == 2 and st["tune_launches"] == 2 and st["search_launches"] == 2
+        for (rid, ids, _), (a, R, rows) in zip(early + late[1:], [(1.15, 24, slice(0, 3)), (0, 0, slice(3, 5)),
+                                                                 (1.1, 24, slice(5, 8))]):
+            g = base if a == 0 else oracle.rp_tune(X, base[0], base[1], a, R)
+            ref, _, _ = oracle.greedy_search(X, g[0], g[1], start, Q[rows], 12, 10)
+            assert np.array_equal(ids, ref)
+    finally:
+        g1.set()
+        g2.set()
+        rp.rp_server_destroy(srv)
+
 def test_budget_evicts_least_recently_used(world):
     from paper_2602_08097_gb300.serving import Request, replay
     X, base, start, Q = world
