@@ -143,7 +143,7 @@ __device__ __forceinline__ bool tier3_dominates(const PruneArgs& a, int32_t u, i
 // A float domination test the Gram tier left undecided: row `t` of the node
 // (candidate ids[t]) against column `c`, target A: single-precision difference
 // form from the rows, then binary64.
-__device__ __forceinline__ bool recheck_dominates(const PruneArgs& a, const int32_t* ids, const float* key,
+__device__ __noinline__ bool recheck_dominates(const PruneArgs& a, const int32_t* ids, const float* key,
                                                   double* key64, int t, int c, int u, int p, float E_rel,
                                                   float E_abs) {
   const int64_t A2 = int64_t(a.A[u]) * a.A[u];
@@ -413,12 +413,24 @@ __global__ void __launch_bounds__(160, tc_min_ctas<DT, MAXM, TB>()) prune_tc_ker
         }
         kacc = pacc + nacc - 2u * dacc;
       } else {
-        if (live_row) {
+        // Rows of one 128-dimension slice also write their split f16 operand
+        // here, at the stored position: when the ranks turn out to be the
+        // stored positions (lists in Algorithm 1's order), the operand pass
+        // below has nothing left to do and the row is read once.
+        const bool one_slice = nslices == 1;
+        if (live_row || one_slice) {
           float part = 0.f;  // the key is summed per 32-dimension slice (slice_rel_bound)
+#pragma unroll 2
           for (int c = 0; c < int(elems / 8); ++c) {
-            const uint4* xq = reinterpret_cast<const uint4*>(xrow) + 2 * c;
-            const uint4* pq = reinterpret_cast<const uint4*>(prow) + 2 * c;
-            const uint4 x0 = __ldg(xq), x1 = __ldg(xq + 1), y0 = __ldg(pq), y1 = __ldg(pq + 1);
+            uint4 x0 = make_uint4(0, 0, 0, 0), x1 = x0, y0 = x0, y1 = x0;
+            if (live_row) {
+              const uint4* xq = reinterpret_cast<const uint4*>(xrow) + 2 * c;
+              const uint4* pq = reinterpret_cast<const uint4*>(prow) + 2 * c;
+              x0 = __ldg(xq);
+              x1 = __ldg(xq + 1);
+              y0 = __ldg(pq);
+              y1 = __ldg(pq + 1);
+            }
             part = Acc<kF32>::step4(x0, y0, part);
             part = Acc<kF32>::step4(x1, y1, part);
             if ((c & 3) == 3 || c == int(elems / 8) - 1) {
@@ -430,6 +442,17 @@ __global__ void __launch_bounds__(160, tc_min_ctas<DT, MAXM, TB>()) prune_tc_ker
                                  __uint_as_float(x1.z), __uint_as_float(x1.w)};
 #pragma unroll
             for (int q = 0; q < 8; ++q) nacc = fmaf(xv[q], xv[q], nacc);
+            if (one_slice) {  // zero rows past the degree, as the operand pass writes them
+              uint4 hi, lo;
+              split_f16x2(xv[0] * a.scale, xv[1] * a.scale, hi.x, lo.x);
+              split_f16x2(xv[2] * a.scale, xv[3] * a.scale, hi.y, lo.y);
+              split_f16x2(xv[4] * a.scale, xv[5] * a.scale, hi.z, lo.z);
+              split_f16x2(xv[6] * a.scale, xv[7] * a.scale, hi.w, lo.w);
+              const int srow = g * MAXM + t;
+              const size_t at = size_t(c * 16 + srow / 8) * 128 + (srow % 8) * 16;
+              *reinterpret_cast<uint4*>(opnd + at) = hi;
+              *reinterpret_cast<uint4*>(opnd + 128 * 128 * 2 + at) = lo;
+            }
           }
         }
       }
@@ -542,7 +565,7 @@ __global__ void __launch_bounds__(160, tc_min_ctas<DT, MAXM, TB>()) prune_tc_ker
             *reinterpret_cast<uint4*>(opnd + ((kc0 + 1) * 16 + orow / 8) * 128 + (orow % 8) * 16) =
                 make_uint4(o[4], o[5], o[6], o[7]);
           }
-        } else {
+        } else if (!(nslices == 1 && in_order)) {  // else written with the keys
 #pragma unroll 4
           for (int c = 0; c < kd / 8; ++c) {
             uint4 x0 = make_uint4(0, 0, 0, 0), x1 = make_uint4(0, 0, 0, 0);
@@ -677,7 +700,7 @@ __global__ void __launch_bounds__(160, tc_min_ctas<DT, MAXM, TB>()) prune_tc_ker
                 // hi hi^T + 2^-11 (cross terms), back in the rows' units (powers of two: exact scalings)
                 const float G = fmaf(__uint_as_float(v2[j]), 4.8828125e-04f, __uint_as_float(v[j])) * a.inv_s2;
                 const unsigned long long bit = 1ull << (c & 63);
-                const int w = c >> 6;
+                const int w = MW == 1 ? 0 : (c >> 6);
                 const float nc = float(norm[c]);
                 const float dv = (nt + nc) - 2.f * G;
                 const float err = 2.f * eps_ip * st * sn[c] * 1.0009765625f + sub_abs * (st + sn[c]) +
