@@ -142,8 +142,10 @@ __device__ __forceinline__ bool tier3_dominates(const PruneArgs& a, int32_t u, i
 
 // A float domination test the Gram tier left undecided: row `t` of the node
 // (candidate ids[t]) against column `c`, target A: single-precision difference
-// form from the rows, then binary64.
-__device__ __noinline__ bool recheck_dominates(const PruneArgs& a, const int32_t* ids, const float* key,
+// form from the rows, then binary64.  Inlined: as an out-of-line call it let
+// the per-target mask loop unroll fully, and the larger code measured 50%
+// slower (64 candidates, 8 targets, 1M x 96 float rows).
+__device__ __forceinline__ bool recheck_dominates(const PruneArgs& a, const int32_t* ids, const float* key,
                                                   double* key64, int t, int c, int u, int p, float E_rel,
                                                   float E_abs) {
   const int64_t A2 = int64_t(a.A[u]) * a.A[u];
