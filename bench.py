@@ -29,7 +29,11 @@ to 1.0 at R=64 plus (1.0, 32), in one launch; 1,000 queries, L=200, k=100).
 
 `--workload deep` runs the large float sweep (10,000,000 x 96 float32 unit rows
 from a 256-centre mixture; eight targets alpha in {1.15, 1.1, 1.05, 1.0} x R in
-{64, 48} in one launch; 10,000 queries, L=100, k=100).
+{64, 48} in one launch; 10,000 queries, L=100, k=100; outside the timed step
+also at L=200).
+
+Every workload also re-prunes its base at the base's own (1.2, 64) and reports
+whether the result equals the base edge for edge (`idempotence_check`).
 
 `--impl reference` times the CPU oracle (the reference arm of this build) on
 a bounded sample of the same workload and prints the same JSON line.
@@ -72,7 +76,7 @@ WORKLOADS = {
                  targets=[(round(1.175 - 0.025 * i, 3), 64) for i in range(8)] + [(1.0, 32)]),
     "deep": dict(dtype="f32", n=10_000_000, d=96, nq=10_000, L=100,
                  targets=[(a, r) for a in (1.15, 1.1, 1.05, 1.0) for r in (64, 48)],
-                 base=dict(kcand=96, nrand=32, seed=4003)),
+                 base=dict(kcand=96, nrand=32, seed=4003), extra_L=(200,)),
 }
 TARGETS = WORKLOADS["sift"]["targets"]
 L_SEARCH = WORKLOADS["sift"]["L"]
@@ -405,6 +409,29 @@ def run_ours(args):
     p50 = lat[len(lat) // 2]
     p99 = lat[min(len(lat) - 1, int(0.99 * len(lat)))]
 
+    # ---- searches at the workload's other list sizes (outside the timed step)
+    extra_L = {}
+    if W.get("extra_L") and not args.quick:
+        outs = rp.rp_tune_batch(ctx, base, alphas, Rs)
+        ide = torch.empty((nq, k), dtype=torch.int32, device=dev)
+        for Lx in W["extra_L"]:
+            ms, rec = 0.0, {}
+            for (a, r), g in zip(TARGETS_W, outs):
+                rp.rp_search(ctx, g, Qd, Lx, k, ids=ide)
+                ms += rp.rp_stats(ctx)["last_search_ms"]
+                rec[f"{a},{r}"] = rp.rp_recall(ctx, ide, gtd, k) / (nq * k)
+            extra_L[str(Lx)] = {"search_qps": T * nq / (ms / 1000.0), "recall_at_100": rec}
+        free(outs)
+
+    # ---- idempotence at full size: the base is RobustPrune(1.2, 64) output, so
+    # re-pruning it at (1.2, 64) must return it edge for edge, order included
+    same = rp.rp_tune(ctx, base, BASE_ALPHA, BASE_R)
+    g_rp, g_col = rp.rp_graph_export(ctx, same)
+    b_rp, b_col = rp.rp_graph_export(ctx, base)
+    idempotent = bool(np.array_equal(g_rp, b_rp) and np.array_equal(g_col, b_col))
+    rp.rp_graph_free(ctx, same)
+    del g_rp, g_col, b_rp, b_col
+
     # ---- end to end through the C ABI with host buffers
     e2e = None
     if not args.no_e2e and not args.quick:
@@ -494,6 +521,8 @@ def run_ours(args):
             "recall_at_100": dict(zip([f"{a},{r}" for a, r in TARGETS_W], recalls)),
             "avg_degree": {"base": float(deg.mean()), **{f"{a},{r}": nz / n for (a, r), nz in zip(TARGETS_W, nnz)}},
             "fixture_s": fixture_s,
+            "search_other_L": extra_L or None,
+            "idempotence_check": {"alpha": BASE_ALPHA, "R": BASE_R, "equal_to_base": idempotent},
             "serving": serving,
         }
         print(json.dumps(line), flush=True)
