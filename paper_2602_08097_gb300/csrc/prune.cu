@@ -25,6 +25,7 @@
 // Tensor-core path: m <= 64 (two nodes per 128-thread CTA, one 128 x 128
 // MMA) and 64 < m <= 128 (one node per CTA).  Larger degrees take the generic
 // path (one node per 256-thread CTA, lazy CUDA-core distances).
+#include <algorithm>
 #include <cmath>
 
 #include "internal.h"
@@ -708,6 +709,10 @@ __global__ void __launch_bounds__(160, tc_min_ctas<DT, MAXM, TB>()) prune_tc_ker
                 const float err = 2.f * eps_ip * st * sn[c] * 1.0009765625f + sub_abs * (st + sn[c]) +
                                   eps_n * (nt + nc) + err_abs;
                 const float hi = (dv + err) * 1.0000005f, lo = (dv - err) * 0.9999995f;
+                // Targets come in ascending A, and qhi (1e6 x an upper key, divided
+                // by A^2, every step rounded monotonically) cannot grow with u: a
+                // pair surely not removed here is surely not removed at any later
+                // target, so the loop stops there.
 #pragma unroll
                 for (int u = 0; u < TB; ++u) {
                   if (u >= T) break;
@@ -715,7 +720,7 @@ __global__ void __launch_bounds__(160, tc_min_ctas<DT, MAXM, TB>()) prune_tc_ker
                   if (hi < qlo[u * MAXM + c]) {
                     dom = true;
                   } else if (lo > qhi[u * MAXM + c]) {
-                    dom = false;
+                    break;
                   } else {
                     // Undecided: queued, and resolved after this pass by all producer
                     // threads at once (one lane's recheck no longer holds up its warp
@@ -1294,12 +1299,19 @@ cudaError_t launch_prune(const PruneLaunch& L, cudaStream_t s) {
   a.T = L.T;
   a.variant = L.variant;
   a.status = L.status;
+  // Targets go to the kernel in ascending A (each with its own outputs), so
+  // that the float pass may stop at the first target where a pair is surely
+  // not removed: it is then surely not removed at every later one.
+  int order[kMaxTargets];
+  for (int t = 0; t < L.T; ++t) order[t] = t;
+  std::stable_sort(order, order + L.T, [&](int x, int y) { return L.A[x] < L.A[y]; });
   for (int t = 0; t < L.T; ++t) {
-    a.A[t] = L.A[t];
-    a.R[t] = L.R[t];
-    a.inv_A2[t] = float(1.0 / (double(L.A[t]) * double(L.A[t])));
-    a.out_col[t] = L.out_col[t];
-    a.out_cnt[t] = L.out_cnt[t];
+    const int o = order[t];
+    a.A[t] = L.A[o];
+    a.R[t] = L.R[o];
+    a.inv_A2[t] = float(1.0 / (double(L.A[o]) * double(L.A[o])));
+    a.out_col[t] = L.out_col[o];
+    a.out_cnt[t] = L.out_cnt[o];
   }
   cudaError_t err = cudaSuccess;
   for (int b = 0; b < 3 && err == cudaSuccess; ++b) {
