@@ -29,8 +29,10 @@ to 1.0 at R=64 plus (1.0, 32), in one launch; 1,000 queries, L=200, k=100).
 
 `--workload deep` runs the large float sweep (10,000,000 x 96 float32 unit rows
 from a 256-centre mixture; eight targets alpha in {1.15, 1.1, 1.05, 1.0} x R in
-{64, 48} in one launch; 10,000 queries, L=100, k=100; outside the timed step
-also at L=200).
+{64, 48} in one launch; 10,000 queries, L=100, k=100).
+
+Outside the timed step every workload also sweeps L over 100..256 on the base
+and on each tuned graph (`recall_qps_frontier`: QPS and recall@100 per L).
 
 Every workload also re-prunes its base at the base's own (1.2, 64) and reports
 whether the result equals the base edge for edge (`idempotence_check`).
@@ -65,6 +67,7 @@ K_SEARCH = 100
 # stream evicts); the deep stream runs under 120 GB of tuned graphs
 SERVE_BUDGET_GB = {"sift": 8, "deep": 120}
 SERVE_LOADS = (0.5, 0.8, 1.0, 2.0, 4.0)  # offered load / capacity of the serial path
+FRONTIER_L = (100, 128, 160, 200, 256)   # list sizes of the recall-QPS frontier (k = 100)
 
 # The paper-shaped workloads (synthetic; recipes in datagen).  sift is the
 # default bench line; gist is the batched float sweep (9 targets: alpha 1.175
@@ -76,7 +79,7 @@ WORKLOADS = {
                  targets=[(round(1.175 - 0.025 * i, 3), 64) for i in range(8)] + [(1.0, 32)]),
     "deep": dict(dtype="f32", n=10_000_000, d=96, nq=10_000, L=100,
                  targets=[(a, r) for a in (1.15, 1.1, 1.05, 1.0) for r in (64, 48)],
-                 base=dict(kcand=96, nrand=32, seed=4003), extra_L=(200,)),
+                 base=dict(kcand=96, nrand=32, seed=4003)),
 }
 TARGETS = WORKLOADS["sift"]["targets"]
 L_SEARCH = WORKLOADS["sift"]["L"]
@@ -409,18 +412,21 @@ def run_ours(args):
     p50 = lat[len(lat) // 2]
     p99 = lat[min(len(lat) - 1, int(0.99 * len(lat)))]
 
-    # ---- searches at the workload's other list sizes (outside the timed step)
-    extra_L = {}
-    if W.get("extra_L") and not args.quick:
+    # ---- recall-QPS frontier over L (outside the timed step): the base and each
+    # tuned graph, every query batch at once
+    frontier = None
+    if not args.quick:
         outs = rp.rp_tune_batch(ctx, base, alphas, Rs)
         ide = torch.empty((nq, k), dtype=torch.int32, device=dev)
-        for Lx in W["extra_L"]:
-            ms, rec = 0.0, {}
-            for (a, r), g in zip(TARGETS_W, outs):
+        frontier = {}
+        for gname, g in [("base", base)] + [(f"{a},{r}", o) for (a, r), o in zip(TARGETS_W, outs)]:
+            pts = []
+            for Lx in FRONTIER_L:
                 rp.rp_search(ctx, g, Qd, Lx, k, ids=ide)
-                ms += rp.rp_stats(ctx)["last_search_ms"]
-                rec[f"{a},{r}"] = rp.rp_recall(ctx, ide, gtd, k) / (nq * k)
-            extra_L[str(Lx)] = {"search_qps": T * nq / (ms / 1000.0), "recall_at_100": rec}
+                ms = rp.rp_stats(ctx)["last_search_ms"]
+                pts.append({"L": Lx, "qps": nq / (ms / 1000.0),
+                            "recall_at_100": rp.rp_recall(ctx, ide, gtd, k) / (nq * k)})
+            frontier[gname] = pts
         free(outs)
 
     # ---- idempotence at full size: the base is RobustPrune(1.2, 64) output, so
@@ -521,7 +527,7 @@ def run_ours(args):
             "recall_at_100": dict(zip([f"{a},{r}" for a, r in TARGETS_W], recalls)),
             "avg_degree": {"base": float(deg.mean()), **{f"{a},{r}": nz / n for (a, r), nz in zip(TARGETS_W, nnz)}},
             "fixture_s": fixture_s,
-            "search_other_L": extra_L or None,
+            "recall_qps_frontier": frontier,
             "idempotence_check": {"alpha": BASE_ALPHA, "R": BASE_R, "equal_to_base": idempotent},
             "serving": serving,
         }

@@ -124,6 +124,25 @@ def test_lists_in_and_out_of_algorithm_order(ctx, dtype, variant):
         rp.rp_graph_free(ctx, o)
     rp.rp_graph_free(ctx, g)
 
+
+@pytest.mark.parametrize("name,n,alpha,variant", [("tiny", 2000, 1.5, "sorted"), ("tiny", 2000, 1.2, "unsorted"),
+                                                  ("sift", 1200, 1.2, "sorted")])
+def test_slow_preprocessing_base_on_the_gpu(ctx, name, n, alpha, variant):
+    """§2.1's slow preprocessing, RobustPrune of every point over all the
+    others, through the library: the complete graph (lists in id order),
+    tuned at (alpha, unbounded R) on the wide-degree path."""
+    X = datagen.dataset(name, n)
+    ids = np.arange(n, dtype=np.int32)
+    col = np.concatenate([np.delete(ids, p) for p in range(n)])
+    row_ptr = np.arange(n + 1, dtype=np.int64) * (n - 1)
+    g = rp.rp_load_graph(ctx, X, row_ptr, col)
+    vt = rp.RP_SORTED if variant == "sorted" else rp.RP_UNSORTED
+    t = rp.rp_tune(ctx, g, alpha, rp.RP_R_INF, vt)
+    _same_csr(rp.rp_graph_export(ctx, t), oracle.slow_base(X, alpha, variant=variant),
+              f"slow base {name} alpha={alpha} {variant}")
+    rp.rp_graph_free(ctx, t)
+    rp.rp_graph_free(ctx, g)
+
 def test_ties_and_duplicate_vectors(ctx):
     # many identical vectors and exact distance ties (uint8 values in {0, 1})
     rng = np.random.default_rng(5)
