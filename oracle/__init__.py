@@ -16,7 +16,7 @@ Every function cites the passage of the paper it follows:
   alpha, R) for every p (Lemma 2.2).
 * :func:`greedy_search` -- Algorithm 2, from the start vertex of §4.1.
 * :func:`knn` -- exact k nearest neighbours, the recall ground truth (§4).
-* :func:`reachability` -- alpha* of Definition 2.1.
+* :func:`reachability` -- alpha* of Definition 2.1 (:func:`reachability_nodes`: its per-node terms).
 * :func:`recall_at_k` -- k-recall@k as defined at the start of §4.
 """
 from __future__ import annotations
@@ -72,6 +72,8 @@ def _load():
         _lib.orc_reachability.argtypes = [P, ci, i64, ci, P, P, ci]
         _lib.orc_reachability_dmat.restype = dbl
         _lib.orc_reachability_dmat.argtypes = [P, i64, P, P]
+        _lib.orc_reachability_nodes.restype = ci
+        _lib.orc_reachability_nodes.argtypes = [P, ci, i64, ci, P, P, P, i64, ci, P]
         _lib.orc_d2_pairs.restype = ci
         _lib.orc_d2_pairs.argtypes = [P, ci, ci, P, P, i64, P]
         _lib.orc_d2_query.restype = ci
@@ -257,6 +259,21 @@ def reachability(X, row_ptr, col, nthreads: int = 0) -> float:
     col = np.ascontiguousarray(col, dtype=np.int32)
     return float(_load().orc_reachability(_ptr(X), dt, X.shape[0], X.shape[1], _ptr(row_ptr),
                                           _ptr(col), int(nthreads)))
+
+
+def reachability_nodes(X, row_ptr, col, nodes=None, nthreads: int = 0) -> np.ndarray:
+    """Per-node terms of alpha*(G) (Definition 2.1) at ``nodes`` (default: all):
+    min over non-neighbours q of max over out-neighbours p' of D(p, q) / D(p', q).
+    Distances pair by pair, so any n; alpha*(G) is the minimum over all nodes."""
+    X, dt = _vecs(X)
+    row_ptr = np.ascontiguousarray(row_ptr, dtype=np.int64)
+    col = np.ascontiguousarray(col, dtype=np.int32)
+    nodes_arr = None if nodes is None else np.ascontiguousarray(nodes, dtype=np.int64)
+    m = X.shape[0] if nodes_arr is None else nodes_arr.shape[0]
+    out = np.zeros(m, dtype=np.float64)
+    _load().orc_reachability_nodes(_ptr(X), dt, X.shape[0], X.shape[1], _ptr(row_ptr), _ptr(col),
+                                   _ptr(nodes_arr), m, int(nthreads), _ptr(out))
+    return out
 
 
 def reachability_dmat(D, row_ptr, col) -> float:

@@ -584,15 +584,22 @@ typedef struct {
   const int64_t *row_ptr;
   const int32_t *col;
   double *per_node;
+  /* with neither matrix: distances from the vectors, one pair at a time */
+  const void *X;
+  int dtype, d;
+  const int64_t *nodes; /* item i is node nodes[i] (NULL: node i) */
 } reach_job;
 
 static double rj_dist(const reach_job *J, int64_t a, int64_t b) {
-  return J->Dm ? J->Dm[a * J->n + b] : sqrt(J->D2[a * J->n + b]);
+  if (J->Dm) return J->Dm[a * J->n + b];
+  if (J->D2) return sqrt(J->D2[a * J->n + b]);
+  return sqrt(d2_pts(J->X, J->dtype, J->d, a, b));
 }
 
-static void reach_item(void *arg, int64_t p, int tid) {
+static void reach_item(void *arg, int64_t i, int tid) {
   (void)tid;
   reach_job *J = (reach_job *)arg;
+  const int64_t p = J->nodes ? J->nodes[i] : i;
   double worst = INFINITY;
   int64_t a = J->row_ptr[p], b = J->row_ptr[p + 1];
   for (int64_t q = 0; q < J->n; q++) {
@@ -610,7 +617,7 @@ static void reach_item(void *arg, int64_t p, int tid) {
     }
     if (best < worst) worst = best;
   }
-  J->per_node[p] = worst;
+  J->per_node[i] = worst;
 }
 
 static double reach_run(reach_job *J, int nthreads) {
@@ -628,7 +635,7 @@ double orc_reachability(const void *X, int dtype, int64_t n, int d, const int64_
   double *D2 = (double *)malloc(sizeof(double) * (size_t)(n * n > 0 ? n * n : 1));
   for (int64_t a = 0; a < n; a++)
     for (int64_t b = 0; b < n; b++) D2[a * n + b] = d2_pts(X, dtype, d, a, b);
-  reach_job J = {D2, NULL, n, row_ptr, col, NULL};
+  reach_job J = {D2, NULL, n, row_ptr, col, NULL, NULL, 0, 0, NULL};
   double r = reach_run(&J, nthreads);
   free(D2);
   return r;
@@ -636,8 +643,20 @@ double orc_reachability(const void *X, int dtype, int64_t n, int d, const int64_
 
 double orc_reachability_dmat(const double *D, int64_t n, const int64_t *row_ptr,
                              const int32_t *col) {
-  reach_job J = {NULL, D, n, row_ptr, col, NULL};
+  reach_job J = {NULL, D, n, row_ptr, col, NULL, NULL, 0, 0, NULL};
   return reach_run(&J, 1);
+}
+
+/* Per-node terms of alpha*(G) at the nodes asked for (NULL: every node),
+   distances computed pair by pair (no n x n matrix, so any n):
+   out[i] = min over q != p, (p, q) not an edge, of max over p' in N_out(p)
+   of D(p, q) / D(p', q), p = nodes[i]. */
+int orc_reachability_nodes(const void *X, int dtype, int64_t n, int d, const int64_t *row_ptr,
+                           const int32_t *col, const int64_t *nodes, int64_t n_nodes, int nthreads,
+                           double *out) {
+  reach_job J = {NULL, NULL, n, row_ptr, col, out, X, dtype, d, nodes};
+  parallel_for(n_nodes, resolve_threads(nthreads), reach_item, &J);
+  return 0;
 }
 
 /* canonical squared distances for a list of (a, b) base-point pairs */

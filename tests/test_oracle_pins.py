@@ -372,3 +372,28 @@ def test_reachability_small_line():
     rp, col = _csr([[1], [2], [1]])
     # non-edges: (0,2): D(0,2)/D(1,2) = 3/2; (1,0): D(1,0)/D(2,0) = 1/3; (2,0): D(2,0)/D(1,0) = 3
     assert oracle.reachability(X, rp, col) == pytest.approx(1 / 3, rel=1e-12)
+
+
+def test_reachability_per_node_terms():
+    """Definition 2.1 per node, distances pair by pair: the line worked by hand
+    above, the closed forms (a node with no out-neighbour gives 0, a node
+    adjacent to every other point gives +inf), Lemma 2.2 on the slow
+    preprocessing base, and the minimum over nodes against the all-pairs
+    routine on several graphs."""
+    X = np.array([[0], [1], [3]], dtype=np.uint8)
+    rp, col = _csr([[1], [2], [1]])
+    # node 0: q=2 via p'=1: 3/2; node 1: q=0 via p'=2: 1/3; node 2: q=0 via p'=1: 3/1
+    np.testing.assert_array_equal(oracle.reachability_nodes(X, rp, col), [1.5, 1 / 3, 3.0])
+    np.testing.assert_array_equal(oracle.reachability_nodes(X, rp, col, nodes=[2, 0]), [3.0, 1.5])
+    rp, col = _csr([[], [0, 2], [1]])  # node 0 has no out-neighbour; node 1 reaches everything
+    np.testing.assert_array_equal(oracle.reachability_nodes(X, rp, col), [0.0, np.inf, 3.0])
+    T = datagen.dataset("tiny", 400)
+    rpb, colb = oracle.slow_base(T, 1.5)
+    assert oracle.reachability_nodes(T, rpb, colb).min() >= 1.5  # Lemma 2.2
+    for R in (8, 32):
+        rpt, colt = oracle.rp_tune(T, rpb, colb, 1.1, R)
+        assert oracle.reachability_nodes(T, rpt, colt).min() == oracle.reachability(T, rpt, colt)
+    U = datagen.dataset("sift", 300)
+    rpu, colu = oracle.slow_base(U, 1.2)
+    per = oracle.reachability_nodes(U, rpu, colu)
+    assert per.min() == oracle.reachability(U, rpu, colu) and per.min() >= 1.2
