@@ -32,7 +32,10 @@ from a 256-centre mixture; eight targets alpha in {1.15, 1.1, 1.05, 1.0} x R in
 {64, 48} in one launch; 10,000 queries, L=100, k=100).
 
 Outside the timed step every workload also sweeps L over 100..256 on the base
-and on each tuned graph (`recall_qps_frontier`: QPS and recall@100 per L).
+and on each tuned graph (`recall_qps_frontier`: QPS and recall@100 per L), and
+measures alpha-reachability (Definition 2.1) at 64 seeded nodes of the base and
+of every target tuned with the sorted and the unsorted variant
+(`reachability_sample`: min and median of the per-node terms).
 
 Every workload also re-prunes its base at the base's own (1.2, 64) and reports
 whether the result equals the base edge for edge (`idempotence_check`).
@@ -68,6 +71,7 @@ K_SEARCH = 100
 SERVE_BUDGET_GB = {"sift": 8, "deep": 120}
 SERVE_LOADS = (0.5, 0.8, 1.0, 2.0, 4.0)  # offered load / capacity of the serial path
 FRONTIER_L = (100, 128, 160, 200, 256)   # list sizes of the recall-QPS frontier (k = 100)
+REACH_SAMPLE = 64                        # nodes whose alpha-reachability terms are measured
 
 # The paper-shaped workloads (synthetic; recipes in datagen).  sift is the
 # default bench line; gist is the batched float sweep (9 targets: alpha 1.175
@@ -429,6 +433,24 @@ def run_ours(args):
             frontier[gname] = pts
         free(outs)
 
+    # ---- alpha-reachability (Definition 2.1) at a seeded sample of nodes: the base
+    # and every target tuned with each of Algorithm 1's variants (sorted and
+    # unsorted), the comparison Theorems 3.1-3.2 are about; outside the timed step
+    reach = None
+    if not args.quick:
+        sample = np.sort(np.random.default_rng(5005).choice(n, min(n, REACH_SAMPLE), replace=False))
+        reach = {"nodes": int(sample.size), "graphs": {}}
+        r0 = time.perf_counter()
+        a_b, per_b = rp.rp_reachability(ctx, base, sample)
+        reach["graphs"]["base"] = {"min": a_b, "median": float(np.median(per_b))}
+        for vname, vcode in (("sorted", rp.RP_SORTED), ("unsorted", rp.RP_UNSORTED)):
+            outs = rp.rp_tune_batch(ctx, base, alphas, Rs, vcode)
+            for (a, r), g in zip(TARGETS_W, outs):
+                a_t, per_t = rp.rp_reachability(ctx, g, sample)
+                reach["graphs"][f"{a},{r} {vname}"] = {"min": a_t, "median": float(np.median(per_t))}
+            free(outs)
+        reach["seconds"] = time.perf_counter() - r0
+
     # ---- idempotence at full size: the base is RobustPrune(1.2, 64) output, so
     # re-pruning it at (1.2, 64) must return it edge for edge, order included
     same = rp.rp_tune(ctx, base, BASE_ALPHA, BASE_R)
@@ -528,6 +550,7 @@ def run_ours(args):
             "avg_degree": {"base": float(deg.mean()), **{f"{a},{r}": nz / n for (a, r), nz in zip(TARGETS_W, nnz)}},
             "fixture_s": fixture_s,
             "recall_qps_frontier": frontier,
+            "reachability_sample": reach,
             "idempotence_check": {"alpha": BASE_ALPHA, "R": BASE_R, "equal_to_base": idempotent},
             "serving": serving,
         }

@@ -249,6 +249,27 @@ rp_status rp_knn(rp_ctx *ctx, rp_graph g, const void *queries, int64_t nq, int32
                  int32_t *ids, float *dists, int32_t mem_flags);
 
 /*
+ * rp_reachability: alpha-reachability of graph g (Definition 2.1), per node.
+ * The term of node p is the min over q != p with (p, q) not an edge of the
+ * max over p' in N_out(p) of D(p, q) / D(p', q), with D = Euclidean distance.
+ * D(p', q) = 0 gives +inf. A node without out-neighbours gives 0; a node with
+ * no such q gives +inf. g is alpha-reachable exactly for alpha <= alpha*(g),
+ * the minimum of the terms over all nodes.
+ * Distances: uint8 exact; float32 the canonical binary64 difference form; D
+ * and the ratio in IEEE binary64, so the terms are exact.
+ *   nodes: host int64[n_nodes], the nodes to measure, or NULL for every node
+ *     (n_nodes is then ignored). Cost: about n * (deg + 1) * d per node, so
+ *     at scale pass a sample.
+ *   per_node: host double[n_nodes or n] receiving the terms (may be NULL).
+ *   alpha_star: host double receiving their minimum, +inf for no node (may be
+ *     NULL). Over a sample it is an upper bound of alpha*(g).
+ * Errors: RP_ENOTFOUND, RP_EINVAL (both outputs NULL, n_nodes < 0, a node
+ *   outside [0, n)), RP_ENOMEM, RP_ECUDA, RP_EDEVICE.
+ */
+rp_status rp_reachability(rp_ctx *ctx, rp_graph g, const int64_t *nodes, int64_t n_nodes, double *per_node,
+                          double *alpha_star);
+
+/*
  * rp_recall: k-recall@k (§4: the share of the true k nearest neighbours
  * found among the k returned).  found: int32[nq * ld_found], truth:
  * int32[nq * ld_truth]; the first k entries of each row are compared;

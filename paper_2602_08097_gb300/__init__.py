@@ -105,6 +105,7 @@ def load_library(path: str = LIB_PATH):
         "rp_search": [P, i64, P, i64, i32, i32, P, P, i32],
         "rp_knn": [P, i64, P, i64, i32, P, P, i32],
         "rp_recall": [P, P, i32, P, i32, i64, i32, ctypes.POINTER(i64), i32],
+        "rp_reachability": [P, i64, P, i64, P, ctypes.POINTER(ctypes.c_double)],
         "rp_build_knn_base": [P, i64, i32, dbl, i32, ctypes.POINTER(i64)],
         "rp_build_knn_random_base": [P, i64, i32, i32, u64, dbl, i32, ctypes.POINTER(i64)],
         "rp_graph_free": [P, i64],
@@ -313,6 +314,22 @@ def rp_recall(ctx, found, truth, k: int) -> int:
     _check(ctx, load_library().rp_recall(ctx, _ptr(found), int(found.shape[1]), _ptr(truth), int(truth.shape[1]),
                                          int(found.shape[0]), int(k), ctypes.byref(hits), mem))
     return hits.value
+
+
+def rp_reachability(ctx, g: int, nodes=None):
+    """alpha-reachability (Definition 2.1): returns (alpha_star, per-node terms)
+    at ``nodes`` (default: every node; at scale pass a sample)."""
+    if nodes is None:
+        n = rp_graph_info(ctx, g)["n"]
+        arr, m = None, n
+    else:
+        arr = np.ascontiguousarray(nodes, dtype=np.int64)
+        m = arr.shape[0]
+    per = np.zeros(m, dtype=np.float64)
+    a = ctypes.c_double()
+    _check(ctx, load_library().rp_reachability(ctx, int(g), None if arr is None else arr.ctypes.data, int(m),
+                                               per.ctypes.data, ctypes.byref(a)))
+    return a.value, per
 
 
 def rp_build_knn_base(ctx, data: int, kcand: int, alpha: float, R: int) -> int:

@@ -110,6 +110,11 @@ cudaError_t launch_search(const SearchLaunch& S, cudaStream_t s);
 cudaError_t launch_recall(const int32_t* found, int ld_found, const int32_t* truth, int ld_truth,
                           int64_t nq, int k, unsigned long long* hits, cudaStream_t s);
 
+// Per-node terms of alpha-reachability (Definition 2.1) at nodes[0..n_nodes)
+// (nodes == nullptr: node i), into out[n_nodes] (reach.cu).
+cudaError_t launch_reach(const DevData& D, const int64_t* row_ptr, const int32_t* col, const int64_t* nodes,
+                         int64_t n_nodes, double* out, cudaStream_t s);
+
 // knn.cu
 struct KnnLaunch {
   DevData data;

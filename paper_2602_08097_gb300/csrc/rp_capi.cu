@@ -1199,6 +1199,42 @@ rp_status rp_recall(rp_ctx* c, const int32_t* found, int32_t ld_found, const int
   return check_device_status(c);
 }
 
+rp_status rp_reachability(rp_ctx* c, rp_graph g, const int64_t* nodes, int64_t n_nodes, double* per_node,
+                          double* alpha_star) {
+  if (!c) return RP_EINVAL;
+  std::lock_guard<std::mutex> lk(c->mu);
+  cudaSetDevice(c->device);
+  Graph* G = find_graph(c, g);
+  if (!G) return fail(c, RP_ENOTFOUND, "unknown graph %lld", (long long)g);
+  if (!alpha_star && !per_node) return fail(c, RP_EINVAL, "nothing to return: per_node and alpha_star are null");
+  if (nodes && n_nodes < 0) return fail(c, RP_EINVAL, "n_nodes=%lld", (long long)n_nodes);
+  const int64_t m = nodes ? n_nodes : G->n;
+  for (int64_t i = 0; nodes && i < m; ++i)
+    if (nodes[i] < 0 || nodes[i] >= G->n)
+      return fail(c, RP_EINVAL, "nodes[%lld]=%lld outside [0, %lld)", (long long)i, (long long)nodes[i],
+                  (long long)G->n);
+  if (alpha_star) *alpha_star = INFINITY;
+  if (m == 0) return RP_OK;
+  rp_status s;
+  const int64_t need = m * 8 * (nodes ? 2 : 1);
+  if ((s = grow(c, &c->qbuf, &c->qbuf_bytes, need)) != RP_OK) return s;
+  double* d_out = reinterpret_cast<double*>(c->qbuf);
+  int64_t* d_nodes = nullptr;
+  if (nodes) {
+    d_nodes = reinterpret_cast<int64_t*>(d_out + m);
+    CUDA_TRY(c, cudaMemcpyAsync(d_nodes, nodes, size_t(m) * 8, cudaMemcpyHostToDevice, c->stream));
+  }
+  CUDA_TRY(c, launch_reach(G->data->dev(), G->row_ptr, G->col, d_nodes, m, d_out, c->stream));
+  c->kernel_launches += 1;
+  std::vector<double> h(static_cast<size_t>(m));
+  CUDA_TRY(c, cudaMemcpyAsync(h.data(), d_out, size_t(m) * 8, cudaMemcpyDeviceToHost, c->stream));
+  CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  if (per_node) std::memcpy(per_node, h.data(), size_t(m) * 8);
+  if (alpha_star)
+    for (double v : h) *alpha_star = std::min(*alpha_star, v);
+  return check_device_status(c);
+}
+
 rp_status rp_build_knn_base(rp_ctx* c, rp_graph data, int32_t kcand, double alpha, int32_t R, rp_graph* out) {
   if (!c) return RP_EINVAL;
   std::lock_guard<std::mutex> lk(c->mu);
