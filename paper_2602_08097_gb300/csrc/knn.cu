@@ -436,7 +436,7 @@ __global__ void __launch_bounds__(128) knn_tc_kernel(KnnTcArgs a) {
         for (int kk = 0; kk < a.ksteps; ++kk) {
           const uint64_t da = umma_desc(smem_addr(sA) + uint32_t(kk) * 2u * lbo, lbo, 128u);
           const uint64_t db = umma_desc(smem_addr(sB) + uint32_t(kk) * 2u * lbo, lbo, 128u);
-          umma_bf16(tmem + uint32_t(b * 128), da, db, idesc, kk > 0);
+          umma_f16(tmem + uint32_t(b * 128), da, db, idesc, kk > 0);
         }
         umma_commit(&mbar[b]);
       }

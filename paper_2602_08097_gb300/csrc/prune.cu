@@ -3,7 +3,7 @@
 //
 // Per node p with m = |N_out(p)| candidates (Algorithm 1):
 //   a2 gather    each thread loads its candidate's row (and p's row) with
-//                16-byte vector loads and writes it as a bf16 MMA operand;
+//                16-byte vector loads and writes it as an f16 MMA operand;
 //   a3 keys      d2(p, v) for every candidate v, exactly / single precision;
 //   a5 Gram      G = A A^T for the candidates on the tensor cores (tcgen05,
 //                accumulator in TMEM), d2(u, v) = |u|^2 + |v|^2 - 2 G(u, v);
@@ -160,20 +160,22 @@ __device__ __forceinline__ bool recheck_dominates(const PruneArgs& a, const int3
 // tensor-core path: the candidate Gram on tcgen05
 // ---------------------------------------------------------------------------
 // One CTA of 128 threads stacks the candidates of NG = 128 / MAXM nodes as the
-// 128 rows of one MMA (M = N = 128): D = A A^T, A = candidates x dims in bf16,
+// 128 rows of one MMA (M = N = 128): D = A A^T, A = candidates x dims in f16,
 // accumulated in f32 in TMEM.  Row r of the CTA is candidate r % MAXM of node
 // group r / MAXM, and TMEM lane r holds its Gram row; the diagonal MAXM x MAXM
 // blocks are the nodes' Grams.
-//   uint8: values 0..255 are exact in bf16, products exact in f32, and every
-//          partial sum is an integer below 2^24, so G is exact and
+//   uint8: values 0..255 are exact in f16, products exact in f32, and every
+//          partial sum is an integer below 2^24 (d <= 256), so G is exact and
 //          d2(u, v) = |u|^2 + |v|^2 - 2 G(u, v) is the exact integer.
-//   float: d2~ = |u|^2 + |v|^2 - 2 G~ with |d2~ - d2| <= err(u, v) =
-//          2 eps_ip |u||v| + (d + 12) 2^-24 (|u|^2 + |v|^2) + tiny, eps_ip =
-//          2^-7 + 2^-16 + d 2^-22 (bf16 rounding of both operands plus f32
-//          accumulation with a factor 2 allowance).  A domination test whose
-//          margin is inside that bound is redone in single-precision
-//          difference form from the rows (rigorous relative bound), and if
-//          still inside, in binary64.
+//   float: rows scaled by a power of two into [-1, 1] and split into f16 hi
+//          and lo (x = hi + 2^-11 lo up to 2^-22 relative); G~ = hi hi^T +
+//          2^-11 (hi lo^T + lo hi^T) from two accumulators, with |G~ - G| <=
+//          eps_ip |u||v| + 2^-36 sqrt(d) (|u| + |v|) / scale, eps_ip = 4 2^-22 +
+//          2^-23 + d 2^-22 (the split, the dropped lo lo^T term, the last sum,
+//          f32 accumulation with a factor 4 allowance).  A domination test
+//          whose margin is inside the resulting d2 bound is redone in
+//          single-precision difference form from the rows (rigorous relative
+//          bound), and if still inside, in binary64.
 // Shared-memory plan of prune_tc_kernel.  Per node group the producer warps
 // keep norms and thresholds; per pipeline slot (2) and group they hand the
 // consumer warp the candidate ids, keys, binary64 key cache and masks.
@@ -245,7 +247,7 @@ __device__ __forceinline__ bool prod_sync_or(bool flag) {
 
 // One CTA = 4 producer warps + 1 consumer warp.  The producers handle NG =
 // 128 / MAXM nodes at a time, one candidate per thread: gather, pivot keys and
-// norms, the rank of each candidate in the processing order (a4), its bf16
+// norms, the rank of each candidate in the processing order (a4), its f16
 // operand row placed at CTA row (group, rank) = TMEM lane, the tcgen05 Gram,
 // per-column thresholds and, from the Gram rows read back from TMEM, one
 // domination mask per target for every rank.  They hand ids and masks over
@@ -537,7 +539,7 @@ __global__ void __launch_bounds__(160, tc_min_ctas<DT, MAXM, TB>()) prune_tc_ker
           key64[rank] = my64;
         }
       }
-      // ---- bf16 operand row at position rank (rows past the degree stay zero);
+      // ---- f16 operand row at position rank (rows past the degree stay zero);
       // a5 Gram on tcgen05, one MMA chain per 128-dim slice
       const int orow = g * MAXM + rank;
       for (int sl = 0; sl < nslices; ++sl) {
@@ -596,12 +598,12 @@ __global__ void __launch_bounds__(160, tc_min_ctas<DT, MAXM, TB>()) prune_tc_ker
 #pragma unroll 1
           for (int kk = 0; kk < kd / 16; ++kk) {
             const uint64_t dsc = umma_desc(smem_addr(opnd) + uint32_t(kk) * 2u * 16u * 128u, 16u * 128u, 128u);
-            umma_bf16(tmem, dsc, dsc, idesc, sl > 0 || kk > 0);
+            umma_f16(tmem, dsc, dsc, idesc, sl > 0 || kk > 0);
             if constexpr (DT == kF32) {  // the cross terms with the low halves into the second accumulator
               const uint64_t dlo =
                   umma_desc(smem_addr(opnd + 128 * 128 * 2) + uint32_t(kk) * 2u * 16u * 128u, 16u * 128u, 128u);
-              umma_bf16(tmem + 128u, dsc, dlo, idesc, sl > 0 || kk > 0);
-              umma_bf16(tmem + 128u, dlo, dsc, idesc, true);
+              umma_f16(tmem + 128u, dsc, dlo, idesc, sl > 0 || kk > 0);
+              umma_f16(tmem + 128u, dlo, dsc, idesc, true);
             }
           }
           umma_commit(mbar);
@@ -1320,7 +1322,7 @@ cudaError_t launch_prune(const PruneLaunch& L, cudaStream_t s) {
     a.work = L.work + b;
     const int64_t hc = L.host_bucket_count[b];
     if (L.data.dtype == kU8) {
-      // The bf16 Gram is exact for uint8 only while every partial sum stays
+      // The f16 Gram is exact for uint8 only while every partial sum stays
       // below 2^24 (d <= 256 here); wider rows take the exact CUDA-core path.
       const bool exact_tc = L.data.d <= 256;
       if (b == 0 && exact_tc && L.tile0 == 0) err = run_fast<kU8, 64>(a, L.num_sms, hc, L.ctas_per_sm, s);

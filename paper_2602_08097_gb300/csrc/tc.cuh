@@ -2,7 +2,7 @@
 // and mbarriers, written as inline PTX.
 //
 // Operand layout used throughout: K-major, no swizzle.  A tile of R rows x K
-// bf16 elements is stored as 8-row x 16-byte "core matrices" (128 bytes each,
+// 16-bit elements is stored as 8-row x 16-byte "core matrices" (128 bytes each,
 // rows contiguous), core (k-chunk kc, row-group rg) at byte offset
 // (kc * (R / 8) + rg) * 128.  In the shared-memory descriptor the leading
 // byte offset is then the distance between k-adjacent core matrices
@@ -28,13 +28,6 @@ __device__ __forceinline__ uint64_t umma_desc(uint32_t saddr, uint32_t lbo, uint
   return d;
 }
 
-// Instruction descriptor for kind::f16 with bf16 A and B, f32 accumulator,
-// both operands K-major.
-__host__ __device__ constexpr uint32_t umma_idesc_bf16(int M, int N) {
-  return (1u << 4) | (1u << 7) | (1u << 10) | (static_cast<uint32_t>(N >> 3) << 17) |
-         (static_cast<uint32_t>(M >> 4) << 24);
-}
-
 // Instruction descriptor for kind::f16 with f16 A and B, f32 accumulator,
 // both operands K-major.
 __host__ __device__ constexpr uint32_t umma_idesc_f16(int M, int N) {
@@ -55,8 +48,9 @@ __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence:
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 
-// D[tmem] (+)= A * B^T, issued by one thread.
-__device__ __forceinline__ void umma_bf16(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+// D[tmem] (+)= A * B^T (kind::f16: the operand type is in the instruction
+// descriptor), issued by one thread.
+__device__ __forceinline__ void umma_f16(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
                                           bool accumulate) {
   asm volatile(
       "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
@@ -129,13 +123,6 @@ __device__ __forceinline__ void split_f16x2(float a0, float a1, uint32_t& hi, ui
   asm("{\n.reg .f16 l, h;\nmov.b32 {l, h}, %2;\ncvt.f32.f16 %0, l;\ncvt.f32.f16 %1, h;\n}" : "=f"(h0), "=f"(h1)
       : "r"(hi));
   lo = pack_f16x2((a0 - h0) * 2048.f, (a1 - h1) * 2048.f);
-}
-
-// Round-to-nearest-even float -> bf16 bits (exact for integers up to 256).
-__device__ __forceinline__ uint32_t pack_bf16x2(float lo, float hi) {
-  uint32_t r;
-  asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(r) : "f"(hi), "f"(lo));
-  return r;
 }
 
 }  // namespace rpk
