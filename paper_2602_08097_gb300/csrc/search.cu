@@ -23,9 +23,11 @@
 // parts, so this equals adding the whole list and cutting once.
 //
 // Ordering: uint8 distances are exact integers.  float32 distances (summed
-// per 32-dimension slice) carry a rigorous single-precision error bound; when two intervals overlap, both
-// distances are recomputed in binary64 (index order, no fused multiply-add)
-// and compared there, so every comparison agrees with the binary64 reading.
+// per 32-dimension slice) carry a rigorous single-precision error bound; when
+// two intervals overlap, both distances are recomputed in float-float
+// arithmetic (bound about d 2^-46 relative), and only if those intervals still
+// overlap in binary64 (index order, no fused multiply-add), so every
+// comparison agrees with the binary64 reading.
 #include <cfloat>
 #include <map>
 #include <mutex>
