@@ -116,7 +116,9 @@ rp_status rp_sync(rp_ctx *ctx);
  * occurrence; the cleaned graph is what every later call sees.  Counts of
  * dropped entries are available through rp_stats.
  * Errors: RP_EINVAL (n < 1, d < 1, bad dtype, row_ptr not monotone, an id
- *   outside [0, n), a cleaned out-degree above RP_MAX_DEGREE, start >= n);
+ *   outside [0, n), a cleaned out-degree above RP_MAX_DEGREE, start >= n, a
+ *   float value above 2^50 in magnitude: squared distances of such rows could
+ *   leave the single-precision range the bounded tiers work in);
  *   RP_ENOMEM (over budget); RP_ECUDA.
  */
 rp_status rp_load_graph(rp_ctx *ctx, const void *vectors, int32_t dtype, int64_t n, int32_t d,

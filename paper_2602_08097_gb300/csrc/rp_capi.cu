@@ -853,10 +853,14 @@ rp_status rp_load_graph(rp_ctx* c, const void* vectors, int32_t dtype, int64_t n
     CUDA_TRY(c, cudaStreamSynchronize(c->stream));
     float mx = 0.f;
     memcpy(&mx, &mb, 4);
+    c->kernel_launches += 1;
+    // |x| <= 2^50 keeps every squared distance below 2^120 even at d = 65536,
+    // so no single-precision sum on the path can overflow.
+    if (std::isfinite(mx) && mx > 1125899906842624.f)  // non-finite rows: the status check below
+      return fail_free(fail(c, RP_EINVAL, "float rows with |x| above 2^50 (max %g) are not supported", double(mx)));
     int e = 0;
     if (mx > 0.f && std::isfinite(mx)) std::frexp(mx, &e);  // mx < 2^e
     D->scale = std::ldexp(1.f, -e);
-    c->kernel_launches += 1;
   }
 
   Graph* G = new Graph;

@@ -216,6 +216,11 @@ __device__ __forceinline__ FFBound ff_bound(int d) {
 __device__ __forceinline__ void slot_interval(double v, const FFBound& b, double* lo, double* hi) {
   if (signbit(v)) {
     const double f = -v;
+    if (!(f <= 1.0e300)) {  // not finite: no bound (decided in binary64)
+      *lo = 0.0;
+      *hi = INFINITY;
+      return;
+    }
     *lo = __dsub_rd(__dmul_rd(f, 1.0 - b.E2), b.A2);
     *hi = __dadd_ru(__dmul_ru(f, 1.0 + b.E2), b.A2);
   } else {

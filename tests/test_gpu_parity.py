@@ -238,6 +238,13 @@ def test_invalid_inputs_are_rejected(ctx):
     Xn[4, 2] = np.nan
     with pytest.raises(rp.RPError):
         rp.rp_load_graph(ctx, Xn, row_ptr, col)
+    Xb = X.copy()
+    Xb[7, 0] = 2.0 ** 51  # finite, but its squared distances could leave single precision
+    with pytest.raises(rp.RPError) as e:
+        rp.rp_load_graph(ctx, Xb, row_ptr, col)
+    assert e.value.code == rp.RP_EINVAL
+    Xb[7, 0] = 2.0 ** 50  # the largest magnitude accepted
+    rp.rp_graph_free(ctx, rp.rp_load_graph(ctx, Xb, row_ptr, col))
     with pytest.raises(rp.RPError):
         rp.rp_search(ctx, g, X[:2], 5, 10)  # L < k
     # the context still works after the errors
