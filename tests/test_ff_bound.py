@@ -1,9 +1,16 @@
-"""The float-float squared distance of the search's middle ordering tier
-(`ff_d2` in csrc/search.cu), emulated step for step in IEEE single precision,
-against exact rational arithmetic: its error must stay within the bound the
-kernel uses, (3d + 13) 2^-48 d2 + (4d + 4) 2^-149, on rows of ordinary,
-concentrated, wide-exponent, equal and subnormal values.  The GPU parity tests
-check the kernel itself against the oracle; this pins the bound."""
+"""The error bounds of the float ordering tiers, pinned by emulating the
+kernels' arithmetic step for step in IEEE single precision (fused
+multiply-adds rounded once) against exact rational arithmetic, on rows of
+ordinary, concentrated, wide-exponent, equal and subnormal values:
+
+* the float-float squared distance of the search's middle tier (`ff_d2` in
+  csrc/search.cu): (3d + 13) 2^-48 d2 + (4d + 4) 2^-149;
+* the single-precision distance summed per 32-dimension slice, the first tier
+  of the prune, the search and the exact kNN: (min(d, 32) + ceil(d / 32) + 8)
+  2^-24 d2 + 4 (d + 1) 2^-149.
+
+The GPU parity tests check the kernels themselves against the oracle; these
+check that the bounds the kernels decide with hold for their arithmetic."""
 from fractions import Fraction
 
 import numpy as np
@@ -81,3 +88,39 @@ def test_equal_subnormal_and_long_rows():
     _check(tiny, (tiny * 2).astype(np.float32))
     a = rng.normal(size=4096).astype(np.float32)
     _check(a, (a + rng.normal(size=4096) * 1e-3).astype(np.float32))
+
+
+# ---- the single-precision tier: d2 summed per 32-dimension slice, each
+# difference rounded and its square added by a fused multiply-add, the slice
+# sums then added in order; its bound (slice_rel_bound, abs_bound in
+# csrc/common.cuh) is (min(d, 32) + ceil(d / 32) + 8) 2^-24 d2 + (d + 1) 2^-149 4.
+
+def _sliced_d2(a, b):
+    acc = f32(0)
+    with np.errstate(over="ignore", under="ignore"):
+        for c0 in range(0, a.shape[0], 32):
+            part = f32(0)
+            for x, y in zip(a[c0:c0 + 32], b[c0:c0 + 32]):
+                t = f32(x - y)
+                part = _fma(t, t, part)
+            acc = f32(acc + part)
+    return acc
+
+
+def _check_sliced(a, b):
+    d = a.shape[0]
+    got = Fraction(float(_sliced_d2(a, b)))
+    exact = sum((Fraction(float(x)) - Fraction(float(y))) ** 2 for x, y in zip(a, b))
+    rel = Fraction(min(d, 32) + (d + 31) // 32 + 8, 2 ** 24)
+    bound = rel * exact + Fraction(4 * (d + 1), 2 ** 149)
+    assert abs(got - exact) <= bound, (float(abs(got - exact)), float(bound))
+
+
+@pytest.mark.parametrize("d,seed", [(24, 0), (96, 1), (128, 2), (960, 3), (1000, 4)])
+def test_single_precision_slice_bound(d, seed):
+    rng = np.random.default_rng(200 + seed)
+    a = np.abs(rng.normal(size=d)).astype(np.float32)
+    _check_sliced(a, (a + rng.normal(size=d) * 1e-2).astype(np.float32))
+    w = (rng.normal(size=d) * np.exp(rng.uniform(-20, 20, d))).astype(np.float32)
+    _check_sliced(w, (rng.normal(size=d) * np.exp(rng.uniform(-20, 20, d))).astype(np.float32))
+    _check_sliced((rng.integers(1, 9, d) * 2.0 ** -149).astype(np.float32), np.zeros(d, np.float32))
