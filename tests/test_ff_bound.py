@@ -7,7 +7,9 @@ ordinary, concentrated, wide-exponent, equal and subnormal values:
   csrc/search.cu): (3d + 13) 2^-48 d2 + (4d + 4) 2^-149;
 * the single-precision distance summed per 32-dimension slice, the first tier
   of the prune, the search and the exact kNN: (min(d, 32) + ceil(d / 32) + 8)
-  2^-24 d2 + 4 (d + 1) 2^-149.
+  2^-24 d2 + 4 (d + 1) 2^-149;
+* the float prune's split-f16 Gram: eps_ip |u||v| + 2^-36 sqrt(d) (|u| + |v|) /
+  scale, summed in one of the tensor core's possible orders.
 
 The GPU parity tests check the kernels themselves against the oracle; these
 check that the bounds the kernels decide with hold for their arithmetic."""
@@ -124,3 +126,49 @@ def test_single_precision_slice_bound(d, seed):
     w = (rng.normal(size=d) * np.exp(rng.uniform(-20, 20, d))).astype(np.float32)
     _check_sliced(w, (rng.normal(size=d) * np.exp(rng.uniform(-20, 20, d))).astype(np.float32))
     _check_sliced((rng.integers(1, 9, d) * 2.0 ** -149).astype(np.float32), np.zeros(d, np.float32))
+
+
+# ---- the float prune's Gram tier: rows scaled by a power of two into [-1, 1],
+# split into f16 hi and lo (hi = f16(x), lo = f16(2^11 (x - hi))), the two
+# accumulators hi hi^T and hi lo^T + lo hi^T summed in f32, combined as
+# fma(D2, 2^-11, D1).  Bound (csrc/prune.cu): |G~ - G| <= eps_ip |u||v| +
+# 2^-36 sqrt(d) (|u| + |v|) / scale, eps_ip = 4 2^-22 + 2^-23 + d 2^-22.  The
+# emulation sums in k order, one of the orders the tensor core may take; the
+# bound's factor-4 accumulation allowance is what covers the others.
+
+def _split(x):
+    hi = x.astype(np.float16)
+    lo = ((x - hi.astype(np.float32)) * f32(2048)).astype(np.float16)  # exact difference and scaling
+    return hi.astype(np.float32), lo.astype(np.float32)
+
+
+def _gram_tier(u, v, scale):
+    hu, lu = _split((u * scale).astype(np.float32))
+    hv, lv = _split((v * scale).astype(np.float32))
+    d1 = f32(0)
+    d2 = f32(0)
+    for k in range(u.shape[0]):  # f16 x f16 products are exact in f32
+        d1 = f32(d1 + f32(hu[k] * hv[k]))
+        d2 = f32(d2 + f32(hu[k] * lv[k]))
+        d2 = f32(d2 + f32(lu[k] * hv[k]))
+    return Fraction(float(_fma(d2, f32(2.0 ** -11), d1))) / Fraction(float(scale)) ** 2
+
+
+@pytest.mark.parametrize("d,seed", [(32, 0), (96, 1), (960, 2)])
+def test_split_f16_gram_bound(d, seed):
+    rng = np.random.default_rng(300 + seed)
+    for trial in range(3):
+        u = rng.normal(size=d).astype(np.float32)
+        v = (u + rng.normal(size=d) * 0.3).astype(np.float32)
+        if trial == 1:  # components spread over many binades: low halves go subnormal in f16
+            u = (u * np.exp(rng.uniform(-12, 0, d))).astype(np.float32)
+            v = (v * np.exp(rng.uniform(-12, 0, d))).astype(np.float32)
+        mx = float(max(np.abs(u).max(), np.abs(v).max()))
+        scale = f32(2.0 ** -np.frexp(mx)[1])  # a power of two bringing max |x| to at most 1
+        got = _gram_tier(u, v, scale)
+        exact = sum(Fraction(float(a)) * Fraction(float(b)) for a, b in zip(u, v))
+        nu = float(np.sqrt(np.sum(u.astype(np.float64) ** 2)))
+        nv = float(np.sqrt(np.sum(v.astype(np.float64) ** 2)))
+        eps_ip = 4 * 2.0 ** -22 + 2.0 ** -23 + d * 2.0 ** -22
+        bound = eps_ip * nu * nv + 2.0 ** -36 * np.sqrt(d) * (nu + nv) / float(scale)
+        assert abs(float(got - exact)) <= bound, (float(got - exact), bound)
