@@ -172,3 +172,21 @@ def test_split_f16_gram_bound(d, seed):
         eps_ip = 4 * 2.0 ** -22 + 2.0 ** -23 + d * 2.0 ** -22
         bound = eps_ip * nu * nv + 2.0 ** -36 * np.sqrt(d) * (nu + nv) / float(scale)
         assert abs(float(got - exact)) <= bound, (float(got - exact), bound)
+
+
+# ---- the uint8 prune's mask bits: x = 2 G - |t|^2 and q are integers of
+# magnitude below 2^24 held exactly in single precision; the sign bit of the
+# rounded x - q is exactly "x < q" (+0 at equality, and rounding never crosses
+# zero), which the kernel funnel-shifts into a "not removed" word.
+
+def test_sign_of_rounded_integer_difference():
+    rng = np.random.default_rng(9)
+    lim = 2 ** 24 - 1
+    x = rng.integers(-lim, lim + 1, 200000)
+    q = rng.integers(-lim, lim + 1, 200000)
+    edge = np.array([0, 1, -1, lim, -lim, lim - 1, 2 ** 23, -(2 ** 23)])
+    x = np.concatenate([x, np.repeat(edge, edge.size), edge, edge])
+    q = np.concatenate([q, np.tile(edge, edge.size), edge, edge + 1])
+    diff = x.astype(np.float32) - q.astype(np.float32)  # one rounding
+    sign = np.signbit(diff)
+    assert np.array_equal(sign, x < q)
