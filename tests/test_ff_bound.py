@@ -9,7 +9,9 @@ ordinary, concentrated, wide-exponent, equal and subnormal values:
   of the prune, the search and the exact kNN: (min(d, 32) + ceil(d / 32) + 8)
   2^-24 d2 + 4 (d + 1) 2^-149;
 * the float prune's split-f16 Gram: eps_ip |u||v| + 2^-36 sqrt(d) (|u| + |v|) /
-  scale, summed in one of the tensor core's possible orders.
+  scale, summed in one of the tensor core's possible orders;
+* and, for the uint8 prune, that the sign of a rounded difference of two
+  integers below 2^24 in magnitude is exactly their order.
 
 The GPU parity tests check the kernels themselves against the oracle; these
 check that the bounds the kernels decide with hold for their arithmetic."""
