@@ -316,3 +316,31 @@ def test_invalid_submissions_are_refused(world):
         assert rp.rp_server_stats(srv)["rounds"] == 0
     finally:
         rp.rp_server_destroy(srv)
+
+
+def test_mixed_round_evicts_only_what_it_does_not_use(world):
+    """Budget of 2 tuned graphs, A and B resident: a round that searches A
+    (resident, served first) and C (new) evicts B, never A, and a later search
+    on A needs no tuning."""
+    from paper_2602_08097_gb300.serving import Request, replay
+    X, base, start, Q = world
+    ex = OracleExec(X, base, start)
+    srv = ex.server(budget_graphs=2)
+    A, B, C = (1.15, 24), (1.1, 24), (1.05, 16)
+    try:
+        replay(srv, [Request("tune", *A, 0.0), Request("tune", *B, 0.0)], time_scale=0.0)
+        mixed = [Request("search", *A, 0.0, queries=Q[0:3], L=12, k=10),
+                 Request("search", *C, 0.0, queries=Q[3:6], L=12, k=10)]
+        replay(srv, mixed, time_scale=0.0)
+        st = rp.rp_server_stats(srv)
+        assert st["evictions"] == 1 and st["targets_tuned"] == 3
+        again = [Request("search", *A, 0.0, queries=Q[6:8], L=12, k=10)]
+        replay(srv, again, time_scale=0.0)
+        st = rp.rp_server_stats(srv)
+        assert st["targets_tuned"] == 3 and st["evictions"] == 1  # A stayed resident
+        assert ex.live_peak <= 2
+        for r in mixed + again:
+            ids, d2 = _expected(X, base, start, r)
+            assert np.array_equal(r.ids, ids) and np.array_equal(r.dists, d2)
+    finally:
+        rp.rp_server_destroy(srv)
