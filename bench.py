@@ -173,7 +173,7 @@ class ClockSampler:
 # ---------------------------------------------------------------- reference arm / CPU baseline
 
 def oracle_sample(n_sample, name="sift"):
-    """The oracle's own base rows over a prefix of the same dataset (no GPU input)."""
+    """The oracle's own base over the generator's first n points of the workload (no GPU input)."""
     import oracle
     X = datagen.dataset(name, n_sample)
     t0 = time.perf_counter()
@@ -205,8 +205,8 @@ def cpu_baseline(n_sample=20000, name="sift"):
     T = len(w["targets"])
     return {"value": reps * n_sample * T / secs, "unit": UNIT, "cores": oracle.num_threads(0),
             "kind": "oracle",
-            "sample": (f"oracle RP-Tuning of all {n_sample:,} nodes of a {n_sample:,}-point prefix of the same "
-                       f"dataset (its own kNN-128 -> RobustPrune(1.2,64) base), {T} targets, repeated {reps}x "
+            "sample": (f"oracle RP-Tuning of all {n_sample:,} nodes of the generator's first {n_sample:,} points "
+                       f"of the workload (its own kNN-128 -> RobustPrune(1.2,64) base), {T} targets, repeated {reps}x "
                        f"({secs:.1f} s); GreedySearch of 200 queries {200 / qs:.1f} QPS"),
             "search_qps": 200 / qs}
 
@@ -230,7 +230,7 @@ def run_reference(args):
             "data": "synthetic", "config": {"workload": workload_name(args.n, args.nq, args.workload),
                                             "reference_sample_nodes": n_sample},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": oracle.num_threads(0), "kind": "oracle",
-                             "sample": (f"RP-Tuning of a {n_sample:,}-point prefix (its own base), "
+                             "sample": (f"RP-Tuning of the generator's first {n_sample:,} points (its own base), "
                                         f"{len(w['targets'])} targets per step")},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
