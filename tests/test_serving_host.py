@@ -189,6 +189,7 @@ class GatedExec(OracleExec):
     def tune(self, user, src, alphas, Rs, T, outs):
         i = self.calls
         self.calls += 1
+        self.entered.set()  # the scheduler is inside a tuning call
         if i < len(self.gates):
             self.gates[i].wait(10)
         return super().tune(user, src, alphas, Rs, T, outs)
@@ -203,6 +204,7 @@ def test_resident_requests_do_not_wait_for_the_rounds_tuning(world):
     srv = ex.server()
     try:
         first = rp.rp_submit_tune(srv, 1.15, 24)  # round 1: held in its tuning call by g1
+        assert ex.entered.wait(10)  # round 1 has started: what follows waits for round 2
         early = [rp.rp_submit_search(srv, 1.15, 24, Q[0:3], 12, 10), rp.rp_submit_search(srv, 0.0, 0, Q[3:5], 12, 10)]
         late = [(rp.rp_submit_tune(srv, 1.1, 24), None, None), rp.rp_submit_search(srv, 1.1, 24, Q[5:8], 12, 10)]
         g1.set()
