@@ -316,7 +316,7 @@ __global__ void __launch_bounds__(160, tc_min_ctas<DT, MAXM, TB>()) prune_tc_ker
     // Split f16 Gram of scaled rows, G' = hi hi^T + 2^-11 (hi lo^T + lo hi^T):
     // |G~ - G| <= eps_ip |u||v| + 2^-36 sqrt(d) (|u| + |v|) / scale (the split
     // leaves 2^-22 per operand, the dropped lo lo^T term 2^-22, the last sum
-    // 2^-23, f32 accumulation d 2^-22 with a factor 2 allowance; subnormal lo)
+    // 2^-23, f32 accumulation d 2^-24 with a factor 4 allowance; subnormal lo)
     const float eps_ip = 4.f * 2.384185791015625e-07f + 1.1920929e-07f + float(a.d) * 2.384185791015625e-07f;
     const float sub_abs = a.sqrt_d * 1.001f * 2.910383e-11f * a.inv_s;  // twice 2^-36 sqrt(d) / scale
     const float eps_n = float(a.d + 12) * 5.9604645e-08f;

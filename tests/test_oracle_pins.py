@@ -397,3 +397,43 @@ def test_reachability_per_node_terms():
     rpu, colu = oracle.slow_base(U, 1.2)
     per = oracle.reachability_nodes(U, rpu, colu)
     assert per.min() == oracle.reachability(U, rpu, colu) and per.min() >= 1.2
+
+
+# ---- k-recall@k (§4): |returned ∩ true top-k| / k, averaged over the queries.
+# Each case is worked by hand; a plausible slip (counting the -1 padding of
+# Algorithm 2's short answers, counting a repeated id twice, or reading past k
+# in either list) changes at least one of the expected values.
+@pytest.mark.parametrize("found,truth,k,expected", [
+    # padding: two real ids, both true; the two -1 entries must not match each other
+    ([[1, 2, -1, -1]], [[1, 2, 3, 4]], 4, 2 / 4),
+    ([[1, 2, -1, -1]], [[1, 2, -1, -1]], 4, 2 / 4),
+    # a repeated id in the returned list counts once
+    ([[5, 5, 6, 7]], [[5, 6, 8, 9]], 4, 2 / 4),
+    # only the first k entries of each list count: 9 and 8 are past k in `found`,
+    # 7 and 6 past k in `truth`
+    ([[1, 2, 3, 9, 8]], [[9, 8, 7, 6, 5]], 3, 0 / 3),
+    ([[9, 1, 2, 8]], [[9, 3, 4, 8]], 3, 1 / 3),
+    # order inside the first k does not matter
+    ([[3, 2, 1]], [[1, 2, 3]], 3, 3 / 3),
+    # the mean over queries, not over returned ids
+    ([[1, 2], [7, -1]], [[1, 2], [8, 9]], 2, (2 + 0) / (2 * 2)),
+    ([[0, 1, 2, 3], [4, 5, 6, 7], [8, 9, 10, 11]], [[0, 1, 2, 3], [4, 5, 0, 1], [1, 2, 3, 4]], 4,
+     (4 + 2 + 0) / 12),
+])
+def test_recall_at_k_hand_worked(found, truth, k, expected):
+    assert oracle.recall_at_k(np.array(found), np.array(truth), k) == pytest.approx(expected, abs=0)
+
+
+def test_recall_at_k_of_exact_search_is_one():
+    """GreedySearch on a complete graph with L >= k is exact kNN (Alg. 2), so its
+    recall against the exact kNN is 1; a list shifted by one place loses the
+    k-th true neighbour and gains the (k+1)-th, which is not in the truth."""
+    X = datagen.dataset("tiny", 300)
+    Q = datagen.queries("tiny", 20)
+    n = X.shape[0]
+    row_ptr = np.arange(0, n * (n - 1) + 1, n - 1, dtype=np.int64)
+    col = np.array([j for i in range(n) for j in range(n) if j != i], dtype=np.int32)
+    ids, _, _ = oracle.greedy_search(X, row_ptr, col, 0, Q, 40, 10)
+    truth, _ = oracle.knn(X, 11, Q=Q)
+    assert oracle.recall_at_k(ids, truth[:, :10], 10) == 1.0
+    assert oracle.recall_at_k(truth[:, 1:11], truth[:, :10], 10) == pytest.approx(9 / 10, abs=1e-15)
