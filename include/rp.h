@@ -214,29 +214,47 @@ rp_status rp_search_multi(rp_ctx *ctx, const rp_graph *graphs, int32_t ngraphs,
  * loading this library holds until the process exits.
  *   vectors: n x d elements of dtype, device memory, rows packed (stride
  *     d * element size, which must be a multiple of 16 bytes; pointer
- *     16-byte aligned).
+ *     16-byte aligned).  Float rows must be finite with |x| <= 2^50, as
+ *     rp_load_graph requires; this call does not check them (the bounds of
+ *     the float ordering tiers and the (distance, id) order rest on it).
  *   row_ptr, col: the graph in CSR on the device; ids must lie in [0, n) and
  *     rows must hold no repeated id (graphs from rp_graph_export qualify).
  *   start: the start vertex in [0, n).
  *   queries: nq x d elements of dtype, device memory, same stride rule.
- *   ids: int32[nq * k], dists: float[nq * k] or NULL, device memory; same
- *     contents as rp_search's outputs.
+ *   ids: int32[nq * k], dists: float[nq * k] or NULL (distances not
+ *     written), device memory; same contents as rp_search's outputs.
  *   cuda_stream: the stream to run on (NULL: the legacy default stream).
  * The call is asynchronous on cuda_stream and runs on the current device.
- * The first call on a device looks up the scratch array's device address
- * (cudaGetSymbolAddress); make that first call outside any stream capture.
+ * Outside a stream capture every call looks up the scratch array's device
+ * address (cudaGetSymbolAddress), so a device reset between calls is safe; a
+ * call inside a capture reuses the address the last uncaptured call on that
+ * device found, so make one call outside any capture first.
  * All calls share the one array and each clears it at its start, so calls
  * whose work overlaps on the GPU (other streams, other threads) race and must
  * be serialised by the caller.
  * Errors (checked on the host, before any work is enqueued): RP_EINVAL for a
  * bad argument or a stride or pointer alignment off 16 bytes; RP_ECUDA if
- * the symbol lookup or a launch fails.
+ * the symbol lookup or a launch fails.  Problems the kernel detects on the
+ * device go to the status word of the scratch array: read them with
+ * rp_search_noalloc_status.
  */
 #define RP_NOALLOC_SCRATCH_BYTES 4096u
 rp_status rp_search_noalloc(const void *vectors, int32_t dtype, int64_t n, int32_t d,
                             const int64_t *row_ptr, const int32_t *col, int64_t start,
                             const void *queries, int64_t nq, int32_t L, int32_t k, int32_t *ids,
                             float *dists, void *cuda_stream);
+
+/*
+ * rp_search_noalloc_status: the device status of the last rp_search_noalloc
+ * call on the current device.  It waits for cuda_stream (the stream that call
+ * ran on), then reads the status word of the scratch array into host memory
+ * (no allocation).  Returns RP_OK if the kernel reported nothing, RP_EDEVICE if
+ * it reported a problem (*info, if info is not NULL, receives the offending
+ * query index), RP_EINVAL inside a stream capture (it must wait for the
+ * stream), RP_ECUDA if the wait or the read fails.  A later rp_search_noalloc
+ * call on the same device clears the word, so read it before the next call.
+ */
+rp_status rp_search_noalloc_status(void *cuda_stream, int64_t *info);
 
 /*
  * rp_knn: exact k nearest neighbours by brute force over the vectors of

@@ -111,6 +111,7 @@ def load_library(path: str = LIB_PATH):
         "rp_graph_free": [P, i64],
         "rp_stats": [P, ctypes.POINTER(rp_stats_t), i32],
         "rp_search_noalloc": [P, i32, i64, i32, P, P, i64, P, i64, i32, i32, P, P, P],
+        "rp_search_noalloc_status": [P, ctypes.POINTER(i64)],
         "rp_search_multi": [P, P, i32, P, P, P, i64, i32, P, P, i32],
         "rp_graph_shape": [P, i64, ctypes.POINTER(i32), ctypes.POINTER(i32), ctypes.POINTER(u64)],
         "rp_graph_slice": [P, i64, i64, i64, ctypes.POINTER(i64)],
@@ -368,29 +369,75 @@ def rp_stats(ctx, reset: bool = False) -> dict:
 
 
 def rp_search_noalloc(vectors, row_ptr, col, start: int, queries, L: int, k: int, ids=None, dists=None,
-                      stream=None):
+                      stream=None, want_dists: bool = True, check_status: bool = True):
     """GreedySearch with caller-owned CUDA tensors and no device allocation by the library.
 
-    ``vectors``/``queries`` are CUDA tensors of uint8 or float32 rows; ``row_ptr``/``col`` the
-    graph on the device.  Runs on ``stream`` (a torch.cuda.Stream or raw handle; default: the
-    current torch stream).  Returns (ids, dists) tensors.
+    ``vectors``/``queries`` are CUDA tensors of uint8 or float32 rows (same dtype and width);
+    ``row_ptr`` (int64, n+1) and ``col`` (int32) the graph, all on one device.  Runs on
+    ``stream`` (a torch.cuda.Stream or raw handle; default: the current torch stream of that
+    device).  ``want_dists=False`` passes no distance buffer.  With ``check_status`` the call
+    waits for the stream and raises RPError(RP_EDEVICE) if the kernel reported a problem.
+    Returns (ids, dists) tensors (dists None when not wanted).
     """
     import torch
+    tens = {"vectors": vectors, "row_ptr": row_ptr, "col": col, "queries": queries}
+    for name, t in tens.items():
+        if not (_is_torch(t) and t.is_cuda):
+            raise TypeError(f"{name} must be a CUDA tensor")
+    dev = queries.device
+    if any(t.device != dev for t in tens.values()):
+        raise ValueError("vectors, row_ptr, col and queries must be on one device")
+    if vectors.dim() != 2 or queries.dim() != 2:
+        raise ValueError("vectors and queries must be 2-D (rows x dims)")
+    if queries.dtype != vectors.dtype or queries.shape[1] != vectors.shape[1]:
+        raise ValueError("queries must have the vectors' dtype and width")
+    n = int(vectors.shape[0])
+    if row_ptr.dtype != torch.int64 or row_ptr.dim() != 1 or int(row_ptr.numel()) != n + 1:
+        raise ValueError("row_ptr must be int64 with n + 1 entries")
+    if col.dtype != torch.int32 or col.dim() != 1:
+        raise ValueError("col must be 1-D int32")
     nq = int(queries.shape[0])
     if ids is None:
-        ids = torch.empty((nq, k), dtype=torch.int32, device=queries.device)
-    if dists is None:
-        dists = torch.empty((nq, k), dtype=torch.float32, device=queries.device)
-    if stream is None:
-        stream = torch.cuda.current_stream(queries.device)
-    h = stream.cuda_stream if hasattr(stream, "cuda_stream") else stream
-    rc = load_library().rp_search_noalloc(_ptr(vectors), _dtype_code(vectors), int(vectors.shape[0]),
-                                          int(vectors.shape[1]), _ptr(row_ptr), _ptr(col), int(start),
-                                          _ptr(queries), nq, int(L), int(k), _ptr(ids), _ptr(dists),
-                                          ctypes.c_void_p(h) if h else None)
-    if rc != RP_OK:
-        raise RPError(rc, "rp_search_noalloc rejected its arguments or failed to launch")
+        ids = torch.empty((nq, k), dtype=torch.int32, device=dev)
+    if dists is None and want_dists:
+        dists = torch.empty((nq, k), dtype=torch.float32, device=dev)
+    for name, t, dt in (("ids", ids, torch.int32), ("dists", dists, torch.float32)):
+        if t is None:
+            continue
+        if not (_is_torch(t) and t.is_cuda and t.device == dev and t.dtype == dt):
+            raise ValueError(f"{name} must be a {dt} CUDA tensor on the queries' device")
+        if int(t.numel()) < nq * k:
+            raise ValueError(f"{name} must hold at least nq * k entries")
+    with torch.cuda.device(dev):
+        if stream is None:
+            stream = torch.cuda.current_stream(dev)
+        h = stream.cuda_stream if hasattr(stream, "cuda_stream") else stream
+        hs = ctypes.c_void_p(h) if h else None
+        rc = load_library().rp_search_noalloc(_ptr(vectors), _dtype_code(vectors), n, int(vectors.shape[1]),
+                                              _ptr(row_ptr), _ptr(col), int(start), _ptr(queries), nq, int(L),
+                                              int(k), _ptr(ids), _ptr(dists), hs)
+        if rc != RP_OK:
+            raise RPError(rc, "rp_search_noalloc rejected its arguments or failed to launch")
+        if check_status:
+            info = ctypes.c_int64(0)
+            rc = load_library().rp_search_noalloc_status(hs, ctypes.byref(info))
+            if rc != RP_OK:
+                raise RPError(rc, f"rp_search_noalloc: the kernel reported a problem (query {info.value})")
     return ids, dists
+
+
+def rp_search_noalloc_status(stream=None) -> None:
+    """Device status of the last rp_search_noalloc call on the current device: waits for
+    ``stream`` (default: the current torch stream) and raises RPError(RP_EDEVICE), naming
+    the offending query, if the kernel reported a problem."""
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    h = stream.cuda_stream if hasattr(stream, "cuda_stream") else stream
+    info = ctypes.c_int64(0)
+    rc = load_library().rp_search_noalloc_status(ctypes.c_void_p(h) if h else None, ctypes.byref(info))
+    if rc != RP_OK:
+        raise RPError(rc, f"rp_search_noalloc: the kernel reported a problem (query {info.value})")
 
 
 # ---- serving (rp_server_*): the binding keeps the buffers and callbacks the

@@ -67,3 +67,20 @@ def _load_fresh(rp, path):
     finally:
         rp._lib = saved
 
+
+
+def test_no_alloc_binding_rejects_host_arrays_before_the_call(lib_path):
+    """rp_search_noalloc hands its pointers straight to a kernel, so the binding
+    refuses host memory (numpy arrays, CPU tensors) before the library sees a
+    pointer; this needs no GPU."""
+    import numpy as np
+    torch = pytest.importorskip("torch")
+    import paper_2602_08097_gb300 as rp
+    X = np.zeros((10, 16), dtype=np.uint8)
+    row_ptr = np.zeros(11, dtype=np.int64)
+    col = np.zeros(1, dtype=np.int32)
+    with pytest.raises(TypeError):
+        rp.rp_search_noalloc(X, row_ptr, col, 0, X[:2], 8, 4)
+    with pytest.raises(TypeError):
+        rp.rp_search_noalloc(torch.from_numpy(X), torch.from_numpy(row_ptr), torch.from_numpy(col), 0,
+                             torch.from_numpy(X[:2]), 8, 4)

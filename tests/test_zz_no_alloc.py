@@ -25,9 +25,19 @@ def env():
     rp.rp_destroy(ctx)
 
 
-def _graph_on_device(torch, ctx, name, n, nq, kcand, alpha, R):
+def _rows(name, n, nq, dims):
+    """The workload's seeded rows, cut to their first ``dims`` dimensions when
+    given (a row stride that is not a multiple of 128 bytes)."""
     X = datagen.dataset(name, n)
     Q = datagen.queries(name, nq)
+    if dims is not None:
+        X = np.ascontiguousarray(X[:, :dims])
+        Q = np.ascontiguousarray(Q[:, :dims])
+    return X, Q
+
+
+def _graph_on_device(torch, ctx, name, n, nq, kcand, alpha, R, dims=None):
+    X, Q = _rows(name, n, nq, dims)
     g = rp.rp_load_graph(ctx, X)
     b = rp.rp_build_knn_base(ctx, g, kcand, alpha, R)
     row_ptr, col = rp.rp_graph_export(ctx, b)
@@ -37,16 +47,40 @@ def _graph_on_device(torch, ctx, name, n, nq, kcand, alpha, R):
     return b, Q, start, tens
 
 
-@pytest.mark.parametrize("name,n,L,k", [("sift", 6000, 128, 100), ("deep", 5000, 64, 10), ("tiny", 2000, 64, 10)])
-def test_no_alloc_search_matches_rp_search(env, name, n, L, k):
+# (workload, n, L, k, dims): the last two cases cut the rows to 100 float32
+# dimensions (400-byte rows: a short last 32-dimension slice) and to 48 uint8
+# dimensions (48-byte rows), strides rp_search never sees (it pads rows to 128
+# bytes), so the packed-row reads are compared with the padded ones.
+@pytest.mark.parametrize("name,n,L,k,dims", [("sift", 6000, 128, 100, None), ("deep", 5000, 64, 10, None),
+                                             ("tiny", 2000, 64, 10, None), ("gist", 3000, 64, 10, 100),
+                                             ("sift", 4000, 64, 10, 48)])
+def test_no_alloc_search_matches_rp_search(env, name, n, L, k, dims):
     torch, ctx = env
-    b, Q, start, (Xd, rpd, cold, Qd) = _graph_on_device(torch, ctx, name, n, 300, 64, 1.2, 32)
+    b, Q, start, (Xd, rpd, cold, Qd) = _graph_on_device(torch, ctx, name, n, 300, 64, 1.2, 32, dims)
     ref_ids, ref_d = rp.rp_search(ctx, b, Q, L, k)
     for _ in range(2):
         ids, dists = rp.rp_search_noalloc(Xd, rpd, cold, start, Qd, L, k)
         torch.cuda.synchronize()
         assert np.array_equal(ids.cpu().numpy(), ref_ids)
         np.testing.assert_allclose(dists.cpu().numpy(), ref_d, rtol=1e-5)
+    # no distance buffer (dists == NULL at the C ABI): the same ids
+    ids2, none = rp.rp_search_noalloc(Xd, rpd, cold, start, Qd, L, k, want_dists=False)
+    assert none is None
+    assert np.array_equal(ids2.cpu().numpy(), ref_ids)
+    rp.rp_graph_free(ctx, b)
+
+
+def test_no_alloc_status_is_read_back(env):
+    """The device status word of the last call comes back through
+    rp_search_noalloc_status; a clean search reports RP_OK."""
+    import ctypes
+    torch, ctx = env
+    b, Q, start, (Xd, rpd, cold, Qd) = _graph_on_device(torch, ctx, "tiny", 1000, 50, 64, 1.2, 32)
+    s = torch.cuda.Stream()
+    rp.rp_search_noalloc(Xd, rpd, cold, start, Qd, 32, 10, stream=s, check_status=False)
+    info = ctypes.c_int64(-7)
+    rc = rp.load_library().rp_search_noalloc_status(ctypes.c_void_p(s.cuda_stream), ctypes.byref(info))
+    assert rc == rp.RP_OK and info.value == 0
     rp.rp_graph_free(ctx, b)
 
 
@@ -64,3 +98,15 @@ def test_no_alloc_search_rejects_bad_arguments(env):
         rp.rp_search_noalloc(Xok, rp_, col, 0, Xok[:2], 4, 8)  # L < k
     with pytest.raises(rp.RPError):
         rp.rp_search_noalloc(Xok, rp_, col, 10, Xok[:2], 8, 4)  # start outside [0, n)
+    # caught by the binding before the library sees a pointer
+    with pytest.raises(ValueError):
+        rp.rp_search_noalloc(Xok, rp_.to(torch.int32), col, 0, Xok[:2], 8, 4)  # row_ptr not int64
+    with pytest.raises(ValueError):
+        rp.rp_search_noalloc(Xok, rp_[:-1], col, 0, Xok[:2], 8, 4)  # row_ptr not n + 1 long
+    with pytest.raises(ValueError):
+        rp.rp_search_noalloc(Xok, rp_, col, 0, Xok[:2].float(), 8, 4)  # queries of another dtype
+    with pytest.raises(ValueError):
+        rp.rp_search_noalloc(Xok, rp_, col, 0, Xok[:2, :8], 8, 4)  # queries of another width
+    with pytest.raises(ValueError):
+        rp.rp_search_noalloc(Xok, rp_, col, 0, Xok[:2], 8, 4,
+                             ids=torch.empty(3, dtype=torch.int32, device=dev))  # ids too small
