@@ -98,6 +98,16 @@ def workload_name(n, nq, name="sift"):
             f"tune {tl}; {nq:,} queries L={w['L']} k=100")
 
 
+def build_base(rp, ctx, data, name):
+    """The workload's base graph, built by the library on the GPU (the benchmark's
+    untimed fixture; the full-size parity tests build the same one)."""
+    W = WORKLOADS[name]
+    if "base" in W:  # exact kNN plus random candidates (the mixture's clusters are far apart)
+        bw = W["base"]
+        return rp.rp_build_knn_random_base(ctx, data, bw["kcand"], bw["nrand"], bw["seed"], BASE_ALPHA, BASE_R)
+    return rp.rp_build_knn_base(ctx, data, KCAND, BASE_ALPHA, BASE_R)
+
+
 def dist_env():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -267,11 +277,7 @@ def run_ours(args):
     # ---- fixture (not timed): vectors, base graph, ground truth
     t0 = time.perf_counter()
     data = rp.rp_load_graph(ctx, X)
-    if "base" in W:  # exact kNN plus random candidates (the mixture's clusters are far apart)
-        bw = W["base"]
-        base = rp.rp_build_knn_random_base(ctx, data, bw["kcand"], bw["nrand"], bw["seed"], BASE_ALPHA, BASE_R)
-    else:
-        base = rp.rp_build_knn_base(ctx, data, KCAND, BASE_ALPHA, BASE_R)
+    base = build_base(rp, ctx, data, args.workload)
     base_rp, base_col = rp.rp_graph_export(ctx, base)
     gt, _ = rp.rp_knn(ctx, data, Q, k)
     fixture_s = time.perf_counter() - t0

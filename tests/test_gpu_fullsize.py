@@ -103,3 +103,19 @@ def test_search_properties_at_full_size(sift_full):
     assert np.array_equal(gt[sample[:8]], ref_gt)
     hits = rp.rp_recall(ctx, ids, gt, 100)
     assert hits == sum(len(set(a.tolist()) & set(b.tolist())) for a, b in zip(ids, gt))
+
+
+def test_search_matches_oracle_on_the_tuned_graphs(sift_full):
+    """Algorithm 2 on each exported tuned graph: the oracle's lists, element by
+    element (uint8 distances are exact integers, so ids and distances agree)."""
+    ctx, X, data, base, outs, graphs = sift_full
+    Q = datagen.queries("sift", 10_000)
+    sample = np.unique(np.concatenate([np.random.default_rng(11).integers(0, Q.shape[0], 62), [0, 9999]]))
+    for (a, r), g in zip(TARGETS, outs):
+        trp, tcol = graphs[(a, r)]
+        start = rp.rp_graph_info(ctx, g)["start"]
+        ids, dists = rp.rp_search(ctx, g, Q[sample], 128, 100)
+        ref_ids, ref_d2, _ = oracle.greedy_search(X, trp, tcol, start, Q[sample], 128, 100)
+        assert np.array_equal(ids, ref_ids), f"target ({a}, {r})"
+        ok = ref_ids >= 0
+        assert np.array_equal(dists[ok].astype(np.float64), ref_d2[ok])

@@ -1,0 +1,98 @@
+"""Full-size parity of the float paths in the launch configuration bench.py
+times: the deep-shaped sweep (10,000,000 x 96 float32, eight targets in one
+batched launch) and the gist-shaped sweep (1,000,000 x 960 float32, nine
+targets in one launch), each over the benchmark's own base graph.
+
+These are the runs in which the float decision tiers do the most work (near
+ties in the sort keys, Gram-tier tests inside the error bound, recheck queues
+filling up), so the bit-exact claim is checked here and not only on small
+inputs.  For a seeded sample of nodes the oracle re-prunes the exported base
+graph's rows (§3, RP-Tuning: RobustPrune(p, N_out(p), alpha, R) for every p)
+and every target's row must match the GPU's bit for bit, order included.  The
+tier counters of the launch are checked for consistency.  Searches (Alg. 2)
+of sampled queries on a tuned graph must return the oracle's lists exactly
+(float search orders every near tie in binary64), with distances within the
+single-precision slice bound of the oracle's binary64 values.
+"""
+import numpy as np
+import pytest
+
+import datagen
+import oracle
+
+rp = pytest.importorskip("paper_2602_08097_gb300")
+pytestmark = [pytest.mark.gpu, pytest.mark.slow]
+
+
+def _bench():
+    import bench
+    return bench
+
+
+def _sample(n, count, seed):
+    rng = np.random.default_rng(seed)
+    return np.unique(np.concatenate([rng.integers(0, n, count), [0, n - 1]])).astype(np.int64)
+
+
+@pytest.fixture(scope="module", params=["deep", "gist"])
+def float_full(request):
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2602_08097_gb300 import build as b
+    b.build()
+    bench = _bench()
+    name = request.param
+    W = bench.WORKLOADS[name]
+    ctx = rp.rp_create(0)
+    X = datagen.dataset(name, W["n"])
+    data = rp.rp_load_graph(ctx, X)
+    base = bench.build_base(rp, ctx, data, name)
+    rp.rp_stats(ctx, reset=True)
+    outs = rp.rp_tune_batch(ctx, base, [a for a, _ in W["targets"]], [r for _, r in W["targets"]])
+    stats = rp.rp_stats(ctx)
+    yield name, W, ctx, X, base, outs, stats
+    rp.rp_destroy(ctx)
+
+
+def test_sampled_rows_match_oracle(float_full):
+    name, W, ctx, X, base, outs, stats = float_full
+    n = X.shape[0]
+    brp, bcol = rp.rp_graph_export(ctx, base)
+    nodes = _sample(n, 40, 4242)
+    for (a, r), g in zip(W["targets"], outs):
+        trp, tcol = rp.rp_graph_export(ctx, g)
+        ref_rows = oracle.rp_tune(X, brp, bcol, a, r, nodes=nodes)
+        for p, ref in zip(nodes, ref_rows):
+            got = tcol[trp[p]:trp[p + 1]].tolist()
+            assert got == ref.tolist(), f"{name}: node {p} target ({a}, {r})"
+        del trp, tcol
+
+
+def test_tier_counters_of_the_launch(float_full):
+    """One batched launch prunes every node once per target; every Gram-tier
+    test it could not settle went to single precision, and only what stayed
+    undecided to binary64, so binary64 decisions never outnumber the rechecks."""
+    name, W, ctx, X, base, outs, stats = float_full
+    T = len(W["targets"])
+    assert stats["nodes_pruned"] == X.shape[0] * T
+    assert stats["fp64_decisions"] <= stats["f32_rechecks"]
+    print(f"{name}: tiers per node-target: f32 rechecks {stats['f32_rechecks'] / (X.shape[0] * T):.4f}, "
+          f"fp64 decisions {stats['fp64_decisions'] / (X.shape[0] * T):.6f}, fp64 sort keys {stats['fp64_sort_keys']}")
+
+
+def test_search_matches_oracle_at_full_size(float_full):
+    name, W, ctx, X, base, outs, stats = float_full
+    Q = datagen.queries(name, W["nq"])
+    sample = _sample(Q.shape[0], 62, 77)
+    g = outs[len(outs) // 2]
+    trp, tcol = rp.rp_graph_export(ctx, g)
+    start = rp.rp_graph_info(ctx, g)["start"]
+    ids, dists = rp.rp_search(ctx, g, Q[sample], W["L"], 100)
+    ref_ids, ref_d2, _ = oracle.greedy_search(X, trp, tcol, start, Q[sample], W["L"], 100)
+    assert np.array_equal(ids, ref_ids)
+    # single-precision distances against the binary64 ones: the slice-sum bound
+    d = X.shape[1]
+    rel = (min(d, 32) + -(-d // 32) + 8) * 2.0**-24
+    ok = ref_ids >= 0
+    assert np.all(np.abs(dists[ok].astype(np.float64) - ref_d2[ok]) <= rel * ref_d2[ok] + 1e-30)
