@@ -107,6 +107,89 @@ __device__ __forceinline__ int sure_dominates(float A2, float d2a, float d2b, fl
 }
 
 // ---------------------------------------------------------------------------
+// float-float tier
+// ---------------------------------------------------------------------------
+// Float-float squared distance: each difference split exactly (two-sum), its
+// square with the fused multiply-add error term, summed into a renormalised
+// (high, low) pair.  |ff - d2| <= (3d + 13) 2^-48 d2 + (4d + 4) 2^-149: each
+// term is off by at most 4u^2 of itself (u = 2^-24: the rounded cross term and
+// the dropped low square), each step of the low sum by u^2 (3 S + 8 term), and
+// the final conversion by 2^-53.  Only intrinsics (never contracted) are used.
+__device__ __forceinline__ void ff_step(float x, float y, float& sh, float& sl) {
+  const float th = __fsub_rn(x, y);  // two-sum of x and -y
+  const float bv = __fsub_rn(th, x);
+  const float tl = __fadd_rn(__fsub_rn(x, __fsub_rn(th, bv)), __fsub_rn(__fsub_rn(0.f, y), bv));
+  const float ph = __fmul_rn(th, th);
+  const float pl = __fmaf_rn(th, th, -ph);
+  const float xt = __fmaf_rn(__fmul_rn(2.f, th), tl, pl);  // pl + 2 th tl
+  const float s1 = __fadd_rn(sh, ph);                      // two-sum of sh and ph
+  const float b1 = __fsub_rn(s1, sh);
+  const float e = __fadd_rn(__fsub_rn(sh, __fsub_rn(s1, b1)), __fsub_rn(ph, b1));
+  const float l1 = __fadd_rn(sl, __fadd_rn(e, xt));
+  sh = __fadd_rn(s1, l1);  // renormalise: |sl| <= u |sh|
+  sl = __fsub_rn(l1, __fsub_rn(sh, s1));
+}
+
+// `q` may be in shared memory (plain loads); `x` is a global row.  Both are
+// 16-byte aligned and zero-padded to row_bytes; a zero pair adds exactly
+// nothing, so the bound for d holds over the padded length.  Used by the
+// search's ordering and by the prune's decisions between the single-precision
+// and the binary64 tiers.
+__device__ __forceinline__ double ff_d2(const float* q, const float* __restrict__ x, int64_t row_bytes) {
+  const float4* pq = reinterpret_cast<const float4*>(q);
+  const float4* px = reinterpret_cast<const float4*>(x);
+  float sh = 0.f, sl = 0.f;
+  for (int64_t c = 0; c < row_bytes / 16; ++c) {
+    const float4 a = pq[c], b = __ldg(px + c);
+    ff_step(a.x, b.x, sh, sl);
+    ff_step(a.y, b.y, sh, sl);
+    ff_step(a.z, b.z, sh, sl);
+    ff_step(a.w, b.w, sh, sl);
+  }
+  return __dadd_rn(double(sh), double(sl));
+}
+
+// Cached distance slots of float entries: NaN = not computed yet, sign bit
+// set = a float-float value (its magnitude), else the canonical binary64 one.
+// Order of two slots when their intervals allow it: 1 = a first, 0 = b first,
+// -1 = undecided.  A float-float f stands for a binary64 value within
+// [f (1 - E2) - A2, f (1 + E2) + A2], E2 = its bound plus the canonical sum's
+// (d + 4) 2^-53 with room to spare, ends rounded outwards.
+struct FFBound {
+  double E2, A2;
+};
+__device__ __forceinline__ FFBound ff_bound(int d) {
+  const double u2 = 3.552713678800501e-15;  // 2^-48
+  const double u53 = 1.1102230246251565e-16;
+  FFBound b;
+  b.E2 = ((3.0 * d + 13.0) * u2 + (d + 4.0) * u53) * 1.01 + 4.0 * u53;
+  b.A2 = (4.0 * d + 4.0) * 1.401298464324817e-45 * 2.0;
+  return b;
+}
+__device__ __forceinline__ void slot_interval(double v, const FFBound& b, double* lo, double* hi) {
+  if (signbit(v)) {
+    const double f = -v;
+    if (!(f <= 1.0e300)) {  // not finite: no bound (decided in binary64)
+      *lo = 0.0;
+      *hi = INFINITY;
+      return;
+    }
+    *lo = __dsub_rd(__dmul_rd(f, 1.0 - b.E2), b.A2);
+    *hi = __dadd_ru(__dmul_ru(f, 1.0 + b.E2), b.A2);
+  } else {
+    *lo = *hi = v;
+  }
+}
+__device__ __forceinline__ int slot_order(double va, double vb, const FFBound& b) {
+  double la, ha, lb, hb;
+  slot_interval(va, b, &la, &ha);
+  slot_interval(vb, b, &lb, &hb);
+  if (ha < lb) return 1;
+  if (hb < la) return 0;
+  return -1;
+}
+
+// ---------------------------------------------------------------------------
 // uint8 helpers
 // ---------------------------------------------------------------------------
 // Sum over four byte lanes of (a_i - b_i)^2, added to acc.

@@ -126,16 +126,36 @@ __device__ __forceinline__ typename Acc<DT>::T row_d2(const uint8_t* a, const ui
   return acc;
 }
 
-// The canonical binary64 decision for float rows (tier 3).
-__device__ __forceinline__ bool tier3_dominates(const PruneArgs& a, int32_t u, int32_t v, int32_t p,
-                                                double* key64_v, double A2) {
+// The tiers past single precision for float rows.  First float-float
+// distances (error (3d + 13) 2^-48 relative, ff_bound), whose intervals settle
+// the canonical decision fl(A^2 d2a) <= fl(1e6 d2b) unless the two products'
+// roundings could meet; only then both distances in binary64, exactly as the
+// canonical reading computes them.  `key64_v` caches d2(p, v) for column v as
+// the search's slots do: NaN, a float-float value (sign bit set) or the
+// binary64 value.  Every writer of a slot stores a valid value of its kind.
+__device__ __forceinline__ bool fine_dominates(const PruneArgs& a, int32_t u, int32_t v, int32_t p,
+                                               double* key64_v, double A2) {
   const float* X = reinterpret_cast<const float*>(a.X);
   const int64_t stride = a.row_bytes / 4;
-  double d2a = canon_d2_f32(X + int64_t(u) * stride, X + int64_t(v) * stride, a.d);
-  double d2b = *key64_v;
-  if (isnan(d2b)) {
-    d2b = canon_d2_f32(X + int64_t(p) * stride, X + int64_t(v) * stride, a.d);
-    *key64_v = d2b;  // every writer stores the same value
+  const float* xv = X + int64_t(v) * stride;
+  double sb = *key64_v;
+  if (isnan(sb)) {
+    sb = -ff_d2(X + int64_t(p) * stride, xv, a.row_bytes);
+    *key64_v = sb;
+  }
+  const double fa = -ff_d2(X + int64_t(u) * stride, xv, a.row_bytes);
+  const FFBound B = ff_bound(a.d);
+  double la, ha, lb, hb;
+  slot_interval(fa, B, &la, &ha);
+  slot_interval(sb, B, &lb, &hb);
+  // rounding is monotone: fl(A2 d2a) <= fl(A2 ha) and fl(1e6 lb) <= fl(1e6 d2b)
+  if (__dmul_rn(A2, ha) <= __dmul_rn(1.0e6, lb)) return true;
+  if (__dmul_rn(A2, la) > __dmul_rn(1.0e6, hb)) return false;
+  const double d2a = canon_d2_f32(X + int64_t(u) * stride, xv, a.d);
+  double d2b = sb;
+  if (signbit(d2b)) {
+    d2b = canon_d2_f32(X + int64_t(p) * stride, xv, a.d);
+    *key64_v = d2b;
   }
   atomicAdd(&a.status->fp64_decisions, 1ull);
   return canon_dominates(A2, d2a, d2b);
@@ -143,9 +163,10 @@ __device__ __forceinline__ bool tier3_dominates(const PruneArgs& a, int32_t u, i
 
 // A float domination test the Gram tier left undecided: row `t` of the node
 // (candidate ids[t]) against column `c`, target A: single-precision difference
-// form from the rows, then binary64.  Inlined: as an out-of-line call it let
-// the per-target mask loop unroll fully, and the larger code measured 50%
-// slower (64 candidates, 8 targets, 1M x 96 float rows).
+// form from the rows, then float-float, then binary64.  Inlined: as an
+// out-of-line call it let the per-target mask loop unroll fully, and the
+// larger code measured 50% slower (64 candidates, 8 targets, 1M x 96 float
+// rows).
 __device__ __forceinline__ bool recheck_dominates(const PruneArgs& a, const int32_t* ids, const float* key,
                                                   double* key64, int t, int c, int u, int p, float E_rel,
                                                   float E_abs) {
@@ -153,7 +174,7 @@ __device__ __forceinline__ bool recheck_dominates(const PruneArgs& a, const int3
   const float d2a = row_d2<kF32>(a.X + int64_t(ids[t]) * a.row_bytes, a.X + int64_t(ids[c]) * a.row_bytes,
                                  a.row_bytes);
   const int rr = sure_dominates(float(A2), d2a, key[c], E_rel, E_abs);
-  return rr >= 0 ? (rr == 1) : tier3_dominates(a, ids[t], ids[c], p, &key64[c], double(A2));
+  return rr >= 0 ? (rr == 1) : fine_dominates(a, ids[t], ids[c], p, &key64[c], double(A2));
 }
 
 // ---------------------------------------------------------------------------
@@ -175,7 +196,7 @@ __device__ __forceinline__ bool recheck_dominates(const PruneArgs& a, const int3
 //          f32 accumulation with a factor 4 allowance).  A domination test
 //          whose margin is inside the resulting d2 bound is redone in
 //          single-precision difference form from the rows (rigorous relative
-//          bound), and if still inside, in binary64.
+//          bound), and if still inside, in float-float, then binary64.
 // Shared-memory plan of prune_tc_kernel.  Per node group the producer warps
 // keep norms and thresholds; per pipeline slot (2) and group they hand the
 // consumer warp the candidate ids, keys, binary64 key cache and masks.
@@ -1000,7 +1021,7 @@ __global__ void __launch_bounds__(256) prune_generic_kernel(PruneArgs a, int M2)
             dom = static_cast<unsigned long long>(A2) * d2a <= 1000000ull * static_cast<unsigned long long>(key[pj]);
           } else {
             const int r = sure_dominates(float(A2), d2a, key[pj], E, Eabs);
-            dom = r >= 0 ? (r == 1) : tier3_dominates(a, ui, ids[pj], p, &key64[pj], double(A2));
+            dom = r >= 0 ? (r == 1) : fine_dominates(a, ui, ids[pj], p, &key64[pj], double(A2));
           }
           if (dom) alive[j] = 0;
         }
