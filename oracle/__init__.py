@@ -18,6 +18,8 @@ Every function cites the passage of the paper it follows:
 * :func:`knn` -- exact k nearest neighbours, the recall ground truth (§4).
 * :func:`reachability` -- alpha* of Definition 2.1 (:func:`reachability_nodes`: its per-node terms).
 * :func:`recall_at_k` -- k-recall@k as defined at the start of §4.
+* :func:`vamana` -- the Vamana ("fast preprocessing") construction of §2.1 with
+  which §4.1 builds its base indices, in a fixed batch schedule.
 """
 from __future__ import annotations
 
@@ -78,6 +80,8 @@ def _load():
         _lib.orc_d2_pairs.argtypes = [P, ci, ci, P, P, i64, P]
         _lib.orc_d2_query.restype = ci
         _lib.orc_d2_query.argtypes = [P, ci, ci, P, i64, P, ci, P]
+        _lib.orc_vamana.restype = ci
+        _lib.orc_vamana.argtypes = [P, ci, i64, ci, P, ci, P, i32, i32, i32, i64, i64, ci, P, P, P]
         _lib.orc_num_threads.restype = ci
         _lib.orc_num_threads.argtypes = [ci]
     return _lib
@@ -313,3 +317,29 @@ def recall_at_k(found, truth, k: int) -> float:
     for f, t in zip(found, truth):
         tot += len(set(int(x) for x in f[:k] if x >= 0) & set(int(x) for x in t[:k] if x >= 0))
     return tot / (k * max(1, found.shape[0]))
+
+
+def vamana(X, perm, alphas, R: int, L: int, vcap: int, max_batch: int, start: int, nthreads: int = 0):
+    """Vamana (§2.1 "fast preprocessing"; §4.1 builds its base indices this way), run in
+    batches: the graph starts empty and the points of ``perm`` are inserted in batches of
+    1, 2, 4, ... points (at most ``max_batch``), one pass per entry of ``alphas``.  Each
+    point of a batch searches the graph as it stood at the batch's start (Algorithm 2,
+    list size L, its first ``vcap`` visited points), is pruned over them (Algorithm 1,
+    sorted, degree bound R), then every point it kept gets it as a back edge, a list
+    growing past R being pruned again (Algorithm 1).  Returns (row_ptr, col, overflows),
+    overflows counting searches whose visited set was cut to ``vcap``."""
+    X, dt = _vecs(X)
+    n = X.shape[0]
+    perm = np.ascontiguousarray(perm, dtype=np.int32)
+    if perm.shape != (n,) or not np.array_equal(np.sort(perm), np.arange(n, dtype=np.int32)):
+        raise ValueError("perm must be a permutation of 0 .. n-1")
+    A = np.ascontiguousarray([milli(a) for a in alphas], dtype=np.int32)
+    nbr = np.zeros((n, R), dtype=np.int32)
+    deg = np.zeros(n, dtype=np.int32)
+    over = np.zeros(1, dtype=np.int64)
+    rc = _load().orc_vamana(_ptr(X), dt, n, X.shape[1], _ptr(perm), A.shape[0], _ptr(A), int(R), int(L),
+                            int(vcap), int(max_batch), int(start), int(nthreads), _ptr(nbr), _ptr(deg), _ptr(over))
+    if rc != 0:
+        raise ValueError("vamana: bad arguments")
+    row_ptr, col = _to_csr(deg, nbr)
+    return row_ptr, col, int(over[0])

@@ -678,3 +678,221 @@ int orc_d2_query(const void *X, int dtype, int d, const void *Q, int64_t nq,
     }
   return 0;
 }
+
+/* ------------------------------------------------------------------ */
+/* Vamana, the "fast preprocessing" construction (§2.1; §4.1 builds   */
+/* the base indices with it at alpha1 = 1.2, R, L_build = 75), run in */
+/* batches.                                                           */
+/* ------------------------------------------------------------------ */
+/*
+ * The paper treats Vamana as a black box and prints no listing of it.  This
+ * is its reading of the construction, with the batch schedule fixed so that
+ * the result is defined independently of any parallel execution:
+ *
+ *   The graph starts empty.  Points are inserted in the order perm[], in
+ *   batches of 1, 2, 4, ... points, each at most max_batch.  For every point
+ *   p of a batch, against the graph as it stood when the batch began:
+ *     V_p   = the visited set of GreedySearch(s, x_p, 1, L) (Algorithm 2), in
+ *             expansion order, its first vcap members (vcap bounds memory);
+ *     N'(p) = RobustPrune(p, V_p, alpha, R) (Algorithm 1, sorted; its first
+ *             step takes the union with the current N_out(p) and drops p).
+ *   Then every N_out(p) <- N'(p).  Then the back edges: for every j named in
+ *   some N'(p), P_j = the batch points naming j, ascending by id; the merged
+ *   list is N_out(j) followed by the members of P_j not already in it; if it
+ *   holds at most R points it becomes N_out(j), otherwise
+ *   N_out(j) <- RobustPrune(j, merged, alpha, R).
+ * A pass inserts every point once; pass i uses alpha = A[i] / 1000 (the
+ * original construction runs alpha = 1 and then alpha1).  s is the start
+ * vertex.  The graph is held as nbr[p * R + 0 .. deg[p]).
+ */
+
+typedef struct {
+  const void *X;
+  int dtype, d;
+  int64_t n;
+  const int32_t *nbr, *deg; /* the graph at the batch's start */
+  int32_t R, L, vcap;
+  int64_t start;
+  int32_t A;
+  const int32_t *batch;
+  int32_t *new_nbr, *new_deg; /* per batch point: R slots */
+  int64_t *visited_over;      /* searches whose visited set was cut to vcap */
+  char **inL, **vis, **seen;
+  int64_t **touched;
+  int32_t **scratch;
+} vamana_job;
+
+/* GreedySearch(s, x_p, 1, L) on (nbr, deg), recording the expanded points in
+   order; returns how many were expanded, writing the first vcap into out. */
+static int64_t vamana_visit(const vamana_job *J, int64_t p, int tid, int32_t *out) {
+  size_t esz = J->dtype == ORC_U8 ? 1 : 4;
+  const void *q = (const char *)J->X + (size_t)p * (size_t)J->d * esz;
+  char *inL = J->inL[tid], *vis = J->vis[tid], *seen = J->seen[tid];
+  int64_t *touched = J->touched[tid]; /* every point marked during this search, once */
+  int64_t ntouched = 0, ls = 0, expansions = 0;
+  entry *Lst = (entry *)malloc(sizeof(entry) * (size_t)(J->L + J->R + 1));
+  Lst[ls].dist = d2_vec(J->X, J->dtype, J->d, q, J->start);
+  Lst[ls].id = (int32_t)J->start;
+  ls++;
+  inL[J->start] = 1;
+  seen[J->start] = 1;
+  touched[ntouched++] = J->start;
+  for (;;) {
+    int64_t best = -1;
+    for (int64_t j = 0; j < ls; j++) {
+      if (vis[Lst[j].id]) continue;
+      if (best < 0 || entry_cmp(&Lst[j], &Lst[best]) < 0) best = j;
+    }
+    if (best < 0) break;
+    int32_t ps = Lst[best].id;
+    if (expansions < J->vcap) out[expansions] = ps;
+    expansions++;
+    vis[ps] = 1;
+    for (int32_t e = 0; e < J->deg[ps]; e++) {
+      int32_t v = J->nbr[(int64_t)ps * J->R + e];
+      if (inL[v]) continue;
+      inL[v] = 1;
+      if (!seen[v]) { seen[v] = 1; touched[ntouched++] = v; }
+      Lst[ls].dist = d2_vec(J->X, J->dtype, J->d, q, v);
+      Lst[ls].id = v;
+      ls++;
+    }
+    if (ls > J->L) {
+      qsort(Lst, (size_t)ls, sizeof(entry), entry_cmp);
+      for (int64_t j = J->L; j < ls; j++) inL[Lst[j].id] = 0;
+      ls = J->L;
+    }
+  }
+  for (int64_t j = 0; j < ntouched; j++) {
+    inL[touched[j]] = 0;
+    vis[touched[j]] = 0;
+    seen[touched[j]] = 0;
+  }
+  free(Lst);
+  return expansions;
+}
+
+static void vamana_item(void *arg, int64_t i, int tid) {
+  vamana_job *J = (vamana_job *)arg;
+  int64_t p = J->batch[i];
+  int32_t *cand = J->scratch[tid];
+  int64_t nv = vamana_visit(J, p, tid, cand);
+  if (nv > J->vcap) {
+    __atomic_fetch_add(J->visited_over, 1, __ATOMIC_RELAXED);
+    nv = J->vcap;
+  }
+  /* V_p, then the current N_out(p); Algorithm 1 takes the union and drops p */
+  for (int32_t e = 0; e < J->deg[p]; e++) cand[nv++] = J->nbr[p * J->R + e];
+  prune_env E;
+  memset(&E, 0, sizeof E);
+  E.X = J->X; E.dtype = J->dtype; E.d = J->d; E.A = J->A; E.p = p;
+  J->new_deg[i] = (int32_t)robust_prune_env(&E, cand, nv, J->R, ORC_SORTED, J->new_nbr + i * J->R);
+}
+
+typedef struct {
+  int32_t j, p;
+} back_edge;
+
+static int back_edge_cmp(const void *a, const void *b) {
+  const back_edge *x = (const back_edge *)a, *y = (const back_edge *)b;
+  if (x->j != y->j) return (x->j > y->j) - (x->j < y->j);
+  return (x->p > y->p) - (x->p < y->p);
+}
+
+/* Batch sizes: 1, 2, 4, ... capped at max_batch; the last batch takes the rest. */
+static int64_t vamana_batch_size(int64_t k, int64_t max_batch) {
+  int64_t b = 1;
+  for (int64_t i = 0; i < k && b < max_batch; i++) b *= 2;
+  return b < max_batch ? b : max_batch;
+}
+
+int orc_vamana(const void *X, int dtype, int64_t n, int d, const int32_t *perm, int npass,
+               const int32_t *A, int32_t R, int32_t L, int32_t vcap, int64_t max_batch, int64_t start,
+               int nthreads, int32_t *nbr /* n * R */, int32_t *deg /* n */, int64_t *visited_over) {
+  if (n < 1 || R < 1 || L < 1 || vcap < 1 || max_batch < 1 || start < 0 || start >= n) return -1;
+  int T = resolve_threads(nthreads);
+  vamana_job J;
+  memset(&J, 0, sizeof J);
+  J.X = X; J.dtype = dtype; J.d = d; J.n = n; J.R = R; J.L = L; J.vcap = vcap; J.start = start;
+  J.nbr = nbr; J.deg = deg;
+  int64_t over = 0;
+  J.visited_over = &over;
+  memset(deg, 0, sizeof(int32_t) * (size_t)n);
+  int32_t *new_nbr = (int32_t *)malloc(sizeof(int32_t) * (size_t)max_batch * (size_t)R);
+  int32_t *new_deg = (int32_t *)malloc(sizeof(int32_t) * (size_t)max_batch);
+  back_edge *be = (back_edge *)malloc(sizeof(back_edge) * (size_t)max_batch * (size_t)R);
+  int32_t *merged = (int32_t *)malloc(sizeof(int32_t) * (size_t)(R + max_batch));
+  int32_t *kept = (int32_t *)malloc(sizeof(int32_t) * (size_t)R);
+  J.new_nbr = new_nbr; J.new_deg = new_deg;
+  J.inL = (char **)malloc(sizeof(char *) * (size_t)T);
+  J.vis = (char **)malloc(sizeof(char *) * (size_t)T);
+  J.seen = (char **)malloc(sizeof(char *) * (size_t)T);
+  J.touched = (int64_t **)malloc(sizeof(int64_t *) * (size_t)T);
+  J.scratch = (int32_t **)malloc(sizeof(int32_t *) * (size_t)T);
+  for (int t = 0; t < T; t++) {
+    J.inL[t] = (char *)calloc((size_t)n, 1);
+    J.vis[t] = (char *)calloc((size_t)n, 1);
+    J.seen[t] = (char *)calloc((size_t)n, 1);
+    J.touched[t] = (int64_t *)malloc(sizeof(int64_t) * (size_t)n);
+    J.scratch[t] = (int32_t *)malloc(sizeof(int32_t) * (size_t)(vcap + R));
+  }
+  for (int pass = 0; pass < npass; pass++) {
+    J.A = A[pass];
+    int64_t b0 = 0;
+    for (int64_t k = 0; b0 < n; k++) {
+      int64_t bsz = vamana_batch_size(k, max_batch);
+      if (bsz > n - b0) bsz = n - b0;
+      J.batch = perm + b0;
+      parallel_for(bsz, T, vamana_item, &J);
+      int64_t nbe = 0;
+      for (int64_t i = 0; i < bsz; i++) {
+        int64_t p = perm[b0 + i];
+        memcpy(nbr + p * R, new_nbr + i * R, sizeof(int32_t) * (size_t)new_deg[i]);
+        deg[p] = new_deg[i];
+        for (int32_t e = 0; e < new_deg[i]; e++) {
+          be[nbe].j = new_nbr[i * R + e];
+          be[nbe].p = (int32_t)p;
+          nbe++;
+        }
+      }
+      qsort(be, (size_t)nbe, sizeof(back_edge), back_edge_cmp);
+      for (int64_t g0 = 0; g0 < nbe;) {
+        int64_t g1 = g0;
+        while (g1 < nbe && be[g1].j == be[g0].j) g1++;
+        int64_t j = be[g0].j, m = 0;
+        for (int32_t e = 0; e < deg[j]; e++) merged[m++] = nbr[j * R + e];
+        int64_t have = m;
+        for (int64_t g = g0; g < g1; g++) {
+          int dup = 0;
+          for (int64_t e = 0; e < have; e++)
+            if (merged[e] == be[g].p) { dup = 1; break; }
+          if (!dup) merged[m++] = be[g].p;
+        }
+        if (m <= R) {
+          memcpy(nbr + j * R, merged, sizeof(int32_t) * (size_t)m);
+          deg[j] = (int32_t)m;
+        } else {
+          prune_env E;
+          memset(&E, 0, sizeof E);
+          E.X = X; E.dtype = dtype; E.d = d; E.A = A[pass]; E.p = j;
+          int64_t c = robust_prune_env(&E, merged, m, R, ORC_SORTED, kept);
+          memcpy(nbr + j * R, kept, sizeof(int32_t) * (size_t)c);
+          deg[j] = (int32_t)c;
+        }
+        g0 = g1;
+      }
+      b0 += bsz;
+    }
+  }
+  for (int t = 0; t < T; t++) {
+    free(J.inL[t]);
+    free(J.vis[t]);
+    free(J.seen[t]);
+    free(J.touched[t]);
+    free(J.scratch[t]);
+  }
+  free(J.inL); free(J.vis); free(J.seen); free(J.touched); free(J.scratch);
+  free(new_nbr); free(new_deg); free(be); free(merged); free(kept);
+  if (visited_over) *visited_over = over;
+  return 0;
+}

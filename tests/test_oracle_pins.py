@@ -437,3 +437,43 @@ def test_recall_at_k_of_exact_search_is_one():
     truth, _ = oracle.knn(X, 11, Q=Q)
     assert oracle.recall_at_k(ids, truth[:, :10], 10) == 1.0
     assert oracle.recall_at_k(truth[:, 1:11], truth[:, :10], 10) == pytest.approx(9 / 10, abs=1e-15)
+
+
+# ---- Vamana (§2.1 "fast preprocessing"; §4.1 builds its bases with it), the
+# batched reading the oracle states.
+def test_vamana_hand_trace_on_a_line():
+    g = _gold("vamana_line.json")
+    X = np.asarray(g["x"], dtype=np.float32)[:, None]
+    rp_, col, over = oracle.vamana(X, g["perm"], g["alphas"], g["R"], g["L"], g["vcap"], g["max_batch"],
+                                   g["start"])
+    rows = [col[rp_[p]:rp_[p + 1]].tolist() for p in range(X.shape[0])]
+    assert rows == g["rows"]
+    assert over == 0
+
+
+@pytest.mark.parametrize("dtype", ["u8", "f32"])
+def test_vamana_graph_is_valid_and_navigable(dtype):
+    """Every list holds at most R distinct points other than its owner, the
+    last pass's RobustPrune makes every list obey Algorithm 1's degree bound,
+    and the graph does what the construction is for: GreedySearch from the
+    start finds most true nearest neighbours (recall@10 at L = 64)."""
+    if dtype == "u8":
+        X = datagen.dataset("sift", 1500)[:, :32]
+        X = np.ascontiguousarray(X)
+        Q = np.ascontiguousarray(datagen.queries("sift", 100)[:, :32])
+    else:
+        X = datagen.dataset("tiny", 1500)
+        Q = datagen.queries("tiny", 100)
+    n = X.shape[0]
+    perm = np.random.default_rng(9).permutation(n).astype(np.int32)
+    s = oracle.medoid(X)
+    R = 24
+    rp_, col, over = oracle.vamana(X, perm, [1.0, 1.2], R, 40, 160, 64, s)
+    deg = np.diff(rp_)
+    assert deg.max() <= R and deg.min() >= 1
+    for p in range(n):
+        row = col[rp_[p]:rp_[p + 1]]
+        assert p not in row and len(set(row.tolist())) == row.shape[0]
+    ids, _, _ = oracle.greedy_search(X, rp_, col, s, Q, 64, 10)
+    truth, _ = oracle.knn(X, 10, Q=Q)
+    assert oracle.recall_at_k(ids, truth, 10) >= 0.9
