@@ -325,6 +325,36 @@ rp_status rp_build_knn_random_base(rp_ctx *ctx, rp_graph data, int32_t kcand, in
                                    uint64_t seed, double alpha, int32_t R, rp_graph *out);
 
 /*
+ * rp_build_vamana: a Vamana graph, the "fast preprocessing" construction of
+ * §2.1 with which §4.1 builds the paper's base indices (alpha1 = 1.2,
+ * L_build = 75).  The paper does not open the construction; this is its
+ * batched reading.  The graph starts empty; the points are inserted in the
+ * order perm[0 .. n) in batches of 1, 2, 4, ... points, at most max_batch.
+ * Every point p of a batch searches the graph as it stood when the batch
+ * began (Algorithm 2 from the start vertex, list size L; its first vcap
+ * visited points V_p, in expansion order), then N_out(p) <- RobustPrune(p,
+ * V_p, alpha, R) (Algorithm 1, sorted; its first step adds the current
+ * N_out(p)).  Then every point j kept by some batch point takes those points
+ * as back edges, ascending by id, after its current list; a list that grows
+ * past R is pruned again, RobustPrune(j, merged list, alpha, R).  Pass i
+ * inserts every point with alpha = alphas[i] (the original construction runs
+ * alpha = 1, then alpha1).  The result is fully determined by these rules.
+ *   data: a graph whose vectors and start vertex are used (its edges are not).
+ *   perm: host int32[n], a permutation of 0 .. n-1, or NULL for 0 .. n-1.
+ *   npass in [1, 8]; alphas: host double[npass], each >= 1 on the 0.001 grid.
+ *   R in [1, 1024]; L in [1, RP_MAX_L]; vcap in [1, 4096]; max_batch >= 1.
+ *   visited_cut: if not NULL, receives how many searches expanded more than
+ *     vcap points (their V_p was cut to the first vcap).
+ *   out: receives the graph (CSR, each list in its stored order; vectors
+ *     shared with data).
+ * Errors: RP_ENOTFOUND, RP_EINVAL (a bad argument or perm), RP_ENOMEM,
+ *   RP_ECUDA, RP_EDEVICE.
+ */
+rp_status rp_build_vamana(rp_ctx *ctx, rp_graph data, const int32_t *perm, int32_t npass, const double *alphas,
+                          int32_t R, int32_t L, int32_t vcap, int64_t max_batch, int64_t *visited_cut,
+                          rp_graph *out);
+
+/*
  * rp_graph_slice: the part of graph g that one of several GPUs tunes when the
  * nodes are split by contiguous id ranges (RP-Tuning treats every node on its
  * own, §3).  *out keeps the rows of nodes lo .. hi-1 with their edges, in

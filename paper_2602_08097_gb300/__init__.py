@@ -108,6 +108,7 @@ def load_library(path: str = LIB_PATH):
         "rp_reachability": [P, i64, P, i64, P, ctypes.POINTER(ctypes.c_double)],
         "rp_build_knn_base": [P, i64, i32, dbl, i32, ctypes.POINTER(i64)],
         "rp_build_knn_random_base": [P, i64, i32, i32, u64, dbl, i32, ctypes.POINTER(i64)],
+        "rp_build_vamana": [P, i64, P, i32, P, i32, i32, i32, i64, ctypes.POINTER(i64), ctypes.POINTER(i64)],
         "rp_graph_free": [P, i64],
         "rp_stats": [P, ctypes.POINTER(rp_stats_t), i32],
         "rp_search_noalloc": [P, i32, i64, i32, P, P, i64, P, i64, i32, i32, P, P, P],
@@ -344,6 +345,27 @@ def rp_build_knn_random_base(ctx, data: int, kcand: int, nrand: int, seed: int, 
     _check(ctx, load_library().rp_build_knn_random_base(ctx, int(data), int(kcand), int(nrand), int(seed),
                                                         float(alpha), int(R), ctypes.byref(out)))
     return out.value
+
+
+def rp_build_vamana(ctx, data: int, alphas, R: int, L: int, vcap: int = 0, max_batch: int = 0, perm=None):
+    """Vamana graph (§2.1 fast preprocessing, §4.1 base indices) over the vectors of ``data``:
+    one insertion pass per entry of ``alphas``, batches of 1, 2, 4, ... points up to
+    ``max_batch`` (default n // 50), visited sets cut to ``vcap`` (default 4 L), insertion
+    order ``perm`` (default 0 .. n-1).  Returns (graph, searches whose visited set was cut)."""
+    n = rp_graph_info(ctx, data)["n"]
+    vcap = int(vcap) if vcap else 4 * int(L)
+    max_batch = int(max_batch) if max_batch else max(1, n // 50)
+    a = (ctypes.c_double * len(alphas))(*[float(x) for x in alphas])
+    pa = None
+    if perm is not None:
+        pa = np.ascontiguousarray(perm, dtype=np.int32)
+        if pa.shape != (n,):
+            raise ValueError("perm must hold n entries")
+    cut = ctypes.c_int64()
+    out = ctypes.c_int64()
+    _check(ctx, load_library().rp_build_vamana(ctx, int(data), _ptr(pa), len(alphas), a, int(R), int(L), vcap,
+                                               max_batch, ctypes.byref(cut), ctypes.byref(out)))
+    return out.value, cut.value
 
 
 def rp_graph_free(ctx, g: int):

@@ -13,7 +13,7 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "librp.so")
-SOURCES = ["rp_capi.cu", "prune.cu", "prep.cu", "search.cu", "knn.cu", "reach.cu", "rp_noalloc.cu", "serve.cpp"]
+SOURCES = ["rp_capi.cu", "prune.cu", "prep.cu", "search.cu", "knn.cu", "reach.cu", "rp_noalloc.cu", "vamana.cu", "serve.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

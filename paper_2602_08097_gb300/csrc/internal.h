@@ -42,6 +42,9 @@ struct PruneLaunch {
   // node per MMA; CTAs per SM of the tensor-core kernels (0 = all that fit)
   int tile0 = 0;
   int ctas_per_sm = 0;
+  // row p of row_ptr/col holds the candidates of point point_of[p] (graph
+  // construction prunes batch-local rows); nullptr: row p is point p
+  const int32_t* point_of = nullptr;
 };
 
 // prune.cu
@@ -105,6 +108,15 @@ struct SearchLaunch {
   unsigned int* work = nullptr;   // zeroed
   DevStatus* status = nullptr;
   int max_degree = 0;
+  // graph construction: query i = base point q_point[i] (Q unused); graph as
+  // adj_deg[v] ids at col + v * adj_stride (row_ptr unused); expanded points
+  // recorded per query (first visited_cap) with their count
+  const int32_t* q_point = nullptr;
+  const int32_t* adj_deg = nullptr;
+  int64_t adj_stride = 0;
+  int32_t* visited = nullptr;
+  int32_t* visited_cnt = nullptr;
+  int visited_cap = 0;
 };
 cudaError_t launch_search(const SearchLaunch& S, cudaStream_t s);
 cudaError_t launch_recall(const int32_t* found, int ld_found, const int32_t* truth, int ld_truth,
@@ -146,5 +158,25 @@ bool knn_tc_eligible(int dtype, int d, int k);
 cudaError_t launch_maxabs_f32(const uint8_t* X, int64_t row_bytes, int64_t n, int d, unsigned* out, cudaStream_t s);
 size_t knn_tc_scratch_bytes(int dtype, int d, int64_t n, int64_t nq_ext, int num_sms);
 cudaError_t launch_knn_tc(const KnnTcLaunch& K, cudaStream_t s);
+
+// vamana.cu: batched Vamana construction (graph held as nbr[p * R ..], deg[p])
+cudaError_t launch_vamana_candidates(const int32_t* pts, int64_t nb, const int32_t* visited, const int32_t* vis_cnt,
+                                     int vcap, const int32_t* nbr, const int32_t* deg, int R, int32_t* cand,
+                                     int32_t* cnt, unsigned long long* cut, cudaStream_t s);
+cudaError_t launch_compact_rows(const int32_t* src, int64_t stride, const int64_t* src_off, const int32_t* cnt,
+                                int64_t rows, const int64_t* row_ptr, int32_t* col, cudaStream_t s);
+cudaError_t launch_vamana_write_back(const int32_t* pts, int64_t rows, const int64_t* row_ptr, const int32_t* kept_col,
+                                     const int32_t* kept_cnt, int32_t* nbr, int32_t* deg, int R, cudaStream_t s);
+cudaError_t launch_back_count(const int32_t* pts, int64_t nb, const int32_t* nbr, const int32_t* deg, int R,
+                              int32_t* pend, int32_t* slot, int32_t* jlist, int32_t* nj, cudaStream_t s);
+cudaError_t launch_slot_counts(const int32_t* jlist, int64_t nj, const int32_t* pend, int32_t* out, cudaStream_t s);
+cudaError_t launch_back_scatter(const int32_t* pts, int64_t nb, const int32_t* nbr, const int32_t* deg, int R,
+                                const int32_t* slot, const int64_t* seg_ptr, int32_t* cursor, int32_t* seg,
+                                cudaStream_t s);
+cudaError_t launch_back_merge(const int32_t* jlist, int64_t nj, const int64_t* seg_ptr, const int32_t* seg,
+                              int32_t* sorted, int32_t* nbr, int32_t* deg, int R, int32_t* pend, int32_t* ov_raw,
+                              int32_t* ov_slot, int32_t* ov_cnt, int32_t* n_ov, cudaStream_t s);
+cudaError_t launch_ov_prep(const int32_t* ov_slot, int64_t no, const int32_t* jlist, const int64_t* seg_ptr, int R,
+                           int32_t* ov_pts, int64_t* ov_src, cudaStream_t s);
 
 }  // namespace rpk

@@ -57,7 +57,13 @@ struct PruneArgs {
   int32_t* out_col[kMaxTargets];
   int32_t* out_cnt[kMaxTargets];
   DevStatus* status;
+  const int32_t* point_of;  // row p holds the candidates of point point_of[p] (nullptr: of point p)
 };
+
+// The point whose candidates row p holds.
+__device__ __forceinline__ int32_t point_of_row(const PruneArgs& a, int p) {
+  return a.point_of ? a.point_of[p] : p;
+}
 
 template <int DT>
 struct Acc;
@@ -404,7 +410,8 @@ __global__ void __launch_bounds__(160, tc_min_ctas<DT, MAXM, TB>()) prune_tc_ker
       int32_t my_id = 0;
       if (live_row) my_id = a.col[e0 + t];
       const uint8_t* xrow = a.X + int64_t(my_id) * a.row_bytes;
-      const uint8_t* prow = a.X + int64_t(p >= 0 ? p : 0) * a.row_bytes;
+      const int32_t ppt = p >= 0 ? point_of_row(a, p) : 0;  // the point being pruned
+      const uint8_t* prow = a.X + int64_t(ppt) * a.row_bytes;
       // ---- a2 gather, a3 pivot key d2(p, x) and norm |x|^2 of candidate t
       AT kacc = 0, nacc = 0;
       uint4 xs[8];  // uint8, one slice: the row stays here for the operand pass
@@ -753,7 +760,7 @@ __global__ void __launch_bounds__(160, tc_min_ctas<DT, MAXM, TB>()) prune_tc_ker
                       rq[qi] = (unsigned(g * MAXM + t) << 16) | (unsigned(c) << 5) | unsigned(u);
                       dom = false;
                     } else {
-                      dom = recheck_dominates(a, ids, key, key64, t, c, u, p, E_rel, E_abs);
+                      dom = recheck_dominates(a, ids, key, key64, t, c, u, ppt, E_rel, E_abs);
                       ++n_rechecks;
                     }
                   }
@@ -787,8 +794,8 @@ __global__ void __launch_bounds__(160, tc_min_ctas<DT, MAXM, TB>()) prune_tc_ker
             unsigned char* sbq = slot_base(s, gq);
             if (recheck_dominates(a, reinterpret_cast<const int32_t*>(sbq + L::s_ids),
                                   reinterpret_cast<const float*>(sbq + L::s_key),
-                                  reinterpret_cast<double*>(sbq + L::s_key64), tq, c, u, misc[s * 2 + gq], E_rel,
-                                  E_abs))
+                                  reinterpret_cast<double*>(sbq + L::s_key64), tq, c, u,
+                                  point_of_row(a, misc[s * 2 + gq]), E_rel, E_abs))
               atomicOr(reinterpret_cast<unsigned long long*>(sbq + L::s_masks) + (u * MAXM + tq) * MW + (c >> 6),
                        1ull << (c & 63));
             ++n_rechecks;
@@ -909,7 +916,8 @@ __global__ void __launch_bounds__(256) prune_generic_kernel(PruneArgs a, int M2)
       __syncthreads();
       continue;
     }
-    const uint8_t* xp = a.X + int64_t(p) * a.row_bytes;
+    const int32_t ppt = point_of_row(a, p);  // the point being pruned
+    const uint8_t* xp = a.X + int64_t(ppt) * a.row_bytes;
     for (int j = t; j < M2; j += NT) {
       if (j < m) {
         const int32_t v = a.col[e0 + j];
@@ -958,7 +966,7 @@ __global__ void __launch_bounds__(256) prune_generic_kernel(PruneArgs a, int M2)
           const int64_t stride = a.row_bytes / 4;
           for (int i = t; i < m; i += NT) {
             if (lnk[i] || (i > 0 && lnk[i - 1])) {
-              key64[perm[i]] = canon_d2_f32(X + int64_t(p) * stride, X + int64_t(ids[perm[i]]) * stride, a.d);
+              key64[perm[i]] = canon_d2_f32(X + int64_t(ppt) * stride, X + int64_t(ids[perm[i]]) * stride, a.d);
               atomicAdd(&a.status->fp64_sort_keys, 1ull);
             }
           }
@@ -1021,7 +1029,7 @@ __global__ void __launch_bounds__(256) prune_generic_kernel(PruneArgs a, int M2)
             dom = static_cast<unsigned long long>(A2) * d2a <= 1000000ull * static_cast<unsigned long long>(key[pj]);
           } else {
             const int r = sure_dominates(float(A2), d2a, key[pj], E, Eabs);
-            dom = r >= 0 ? (r == 1) : fine_dominates(a, ui, ids[pj], p, &key64[pj], double(A2));
+            dom = r >= 0 ? (r == 1) : fine_dominates(a, ui, ids[pj], ppt, &key64[pj], double(A2));
           }
           if (dom) alive[j] = 0;
         }
@@ -1322,6 +1330,7 @@ cudaError_t launch_prune(const PruneLaunch& L, cudaStream_t s) {
   a.T = L.T;
   a.variant = L.variant;
   a.status = L.status;
+  a.point_of = L.point_of;
   // Targets go to the kernel in ascending A (each with its own outputs), so
   // that the float pass may stop at the first target where a pair is surely
   // not removed: it is then surely not removed at every later one.

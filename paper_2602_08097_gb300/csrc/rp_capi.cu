@@ -738,6 +738,265 @@ rp_status build_base(rp_ctx* c, rp_graph data, int32_t kcand, int32_t nrand, uin
 
 }  // namespace
 
+namespace {
+
+// Device buffers of one Vamana build, freed together.
+struct VamanaBufs {
+  rp_ctx* c;
+  std::vector<std::pair<void*, size_t>> held;
+  explicit VamanaBufs(rp_ctx* ctx) : c(ctx) {}
+  template <typename T>
+  rp_status get(T** p, int64_t elems) {
+    const size_t b = size_t(std::max<int64_t>(elems, 1)) * sizeof(T);
+    rp_status s = dalloc(c, reinterpret_cast<void**>(p), b);
+    if (s == RP_OK) held.emplace_back(static_cast<void*>(*p), b);
+    return s;
+  }
+  ~VamanaBufs() {
+    for (auto& h : held) dfree(c, h.first, h.second);
+  }
+};
+
+// Batch k of a pass holds min(2^k, max_batch) points (the last one the rest).
+int64_t vamana_batch(int64_t k, int64_t max_batch) {
+  int64_t b = 1;
+  for (int64_t i = 0; i < k && b < max_batch; ++i) b *= 2;
+  return std::min(b, max_batch);
+}
+
+// RobustPrune(point_of[i], row i of (row_ptr, col), A, R) for `rows` rows,
+// kept ids to kept_col at the rows' offsets, counts to kept_cnt.
+rp_status vamana_prune(rp_ctx* c, const Dataset& D, const int64_t* row_ptr, const int32_t* col, int64_t rows,
+                       int max_deg, const int32_t* point_of, int32_t A, int32_t R, int32_t* lists, int32_t* kept_col,
+                       int32_t* kept_cnt) {
+  CUDA_TRY(c, launch_bucket_nodes(row_ptr, rows, lists, lists + 3 * rows, c->stream));
+  PruneLaunch P;
+  P.data = D.dev();
+  P.row_ptr = row_ptr;
+  P.col = col;
+  for (int b = 0; b < 3; ++b) {
+    P.bucket_nodes[b] = lists + int64_t(b) * rows;
+    P.host_bucket_count[b] = rows;  // upper bound; the kernels stop at the device count
+  }
+  if (max_deg <= 128 && !(D.dtype == RP_U8 && D.d > 256)) P.host_bucket_count[2] = 0;
+  if (max_deg <= 64) P.host_bucket_count[1] = 0;
+  P.bucket_count = lists + 3 * rows;
+  P.host_max_degree = max_deg;
+  P.T = 1;
+  P.A[0] = A;
+  P.R[0] = R;
+  P.variant = RP_SORTED;
+  P.out_col[0] = kept_col;
+  P.out_cnt[0] = kept_cnt;
+  P.work = c->work;
+  P.status = c->status;
+  P.num_sms = c->num_sms;
+  P.point_of = point_of;
+  CUDA_TRY(c, cudaMemsetAsync(c->work, 0, 8 * sizeof(unsigned), c->stream));
+  CUDA_TRY(c, launch_prune(P, c->stream));
+  c->kernel_launches += 4;
+  return RP_OK;
+}
+
+int32_t read_i32(rp_ctx* c, const int32_t* d, rp_status* st) {
+  int32_t h = 0;
+  cudaError_t e = cudaMemcpyAsync(&h, d, 4, cudaMemcpyDeviceToHost, c->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) *st = fail(c, RP_ECUDA, "read back: %s", cudaGetErrorString(e));
+  return h;
+}
+
+rp_status build_vamana(rp_ctx* c, rp_graph data, const int32_t* perm, int32_t npass, const double* alphas, int32_t R,
+                       int32_t L, int32_t vcap, int64_t max_batch, int64_t* visited_cut, rp_graph* out) {
+  Graph* G = find_graph(c, data);
+  if (!G) return fail(c, RP_ENOTFOUND, "unknown graph %lld", (long long)data);
+  if (!out || !alphas) return fail(c, RP_EINVAL, "null argument");
+  if (npass < 1 || npass > 8) return fail(c, RP_EINVAL, "npass=%d outside [1, 8]", npass);
+  if (R < 1 || R > 1024) return fail(c, RP_EINVAL, "R=%d outside [1, 1024]", R);
+  if (L < 1 || L > RP_MAX_L) return fail(c, RP_EINVAL, "L=%d outside [1, %d]", L, RP_MAX_L);
+  if (vcap < 1 || vcap > 4096) return fail(c, RP_EINVAL, "vcap=%d outside [1, 4096]", vcap);
+  if (max_batch < 1) return fail(c, RP_EINVAL, "max_batch=%lld", (long long)max_batch);
+  std::vector<int32_t> A(static_cast<size_t>(npass));
+  for (int i = 0; i < npass; ++i)
+    if (!alpha_to_milli(alphas[i], &A[size_t(i)]))
+      return fail(c, RP_EINVAL, "alpha=%.17g must lie in [1, 100] on the 0.001 grid", alphas[i]);
+  const Dataset& D = *G->data;
+  const int64_t n = G->n;
+  std::vector<int32_t> hperm(static_cast<size_t>(n));
+  if (perm) {
+    std::vector<char> seen(static_cast<size_t>(n), 0);
+    for (int64_t i = 0; i < n; ++i) {
+      const int32_t v = perm[i];
+      if (v < 0 || v >= n || seen[size_t(v)]) return fail(c, RP_EINVAL, "perm is not a permutation of 0 .. n-1");
+      seen[size_t(v)] = 1;
+      hperm[size_t(i)] = v;
+    }
+  } else {
+    for (int64_t i = 0; i < n; ++i) hperm[size_t(i)] = int32_t(i);
+  }
+  const int64_t B = std::min<int64_t>(max_batch, n);
+  const int64_t W = int64_t(vcap) + R;          // candidate row width
+  const int64_t J = std::min<int64_t>(n, B * R);  // distinct back-edge targets per batch
+  VamanaBufs buf(c);
+  int32_t *nbr, *deg, *pend, *slot, *dperm, *vis, *vis_cnt, *sids, *cand, *ccnt, *ccol, *lists, *kept_col, *kept_cnt;
+  int32_t *maxd, *jlist, *nj, *scnt, *cursor, *seg, *sorted, *ov_raw, *ov_slot, *ov_cnt, *n_ov, *ov_pts, *ov_col;
+  int32_t *ov_kept, *ov_kcnt;
+  int64_t *crp, *bsum, *seg_ptr, *ov_src, *ov_rp;
+  unsigned long long* cut;
+  rp_status s = RP_OK;
+  const int64_t nblk = (std::max(n, J + 1) + 4095) / 4096 + 1;
+  if (s == RP_OK) s = buf.get(&nbr, n * R);
+  if (s == RP_OK) s = buf.get(&deg, n);
+  if (s == RP_OK) s = buf.get(&pend, n);
+  if (s == RP_OK) s = buf.get(&slot, n);
+  if (s == RP_OK) s = buf.get(&dperm, n);
+  if (s == RP_OK) s = buf.get(&vis, B * vcap);
+  if (s == RP_OK) s = buf.get(&vis_cnt, B);
+  if (s == RP_OK) s = buf.get(&sids, B);
+  if (s == RP_OK) s = buf.get(&cand, B * W);
+  if (s == RP_OK) s = buf.get(&ccnt, B);
+  if (s == RP_OK) s = buf.get(&ccol, B * W);
+  if (s == RP_OK) s = buf.get(&crp, B + 1);
+  if (s == RP_OK) s = buf.get(&bsum, nblk);
+  if (s == RP_OK) s = buf.get(&maxd, 2);
+  if (s == RP_OK) s = buf.get(&lists, 3 * std::max(B, J) + 3);
+  if (s == RP_OK) s = buf.get(&kept_col, B * W);
+  if (s == RP_OK) s = buf.get(&kept_cnt, B);
+  if (s == RP_OK) s = buf.get(&jlist, J);
+  if (s == RP_OK) s = buf.get(&nj, 2);
+  if (s == RP_OK) s = buf.get(&scnt, J);
+  if (s == RP_OK) s = buf.get(&seg_ptr, J + 1);
+  if (s == RP_OK) s = buf.get(&cursor, J);
+  if (s == RP_OK) s = buf.get(&seg, B * R);
+  if (s == RP_OK) s = buf.get(&sorted, B * R);
+  if (s == RP_OK) s = buf.get(&ov_raw, B * R + J * R);
+  if (s == RP_OK) s = buf.get(&ov_slot, J);
+  if (s == RP_OK) s = buf.get(&ov_cnt, J);
+  if (s == RP_OK) s = buf.get(&n_ov, 2);
+  if (s == RP_OK) s = buf.get(&ov_pts, J);
+  if (s == RP_OK) s = buf.get(&ov_src, J);
+  if (s == RP_OK) s = buf.get(&ov_rp, J + 1);
+  if (s == RP_OK) s = buf.get(&ov_col, B * R + J * R);
+  if (s == RP_OK) s = buf.get(&ov_kept, B * R + J * R);
+  if (s == RP_OK) s = buf.get(&ov_kcnt, J);
+  if (s == RP_OK) s = buf.get(&cut, 1);
+  if (s != RP_OK) return s;
+  CUDA_TRY(c, cudaMemsetAsync(deg, 0, size_t(n) * 4, c->stream));
+  CUDA_TRY(c, cudaMemsetAsync(pend, 0, size_t(n) * 4, c->stream));
+  CUDA_TRY(c, cudaMemsetAsync(cut, 0, 8, c->stream));
+  CUDA_TRY(c, cudaMemcpyAsync(dperm, hperm.data(), size_t(n) * 4, cudaMemcpyHostToDevice, c->stream));
+  for (int pass = 0; pass < npass; ++pass) {
+    int64_t b0 = 0;
+    for (int64_t k = 0; b0 < n; ++k) {
+      const int64_t nb = std::min(vamana_batch(k, max_batch), n - b0);
+      const int32_t* pts = dperm + b0;
+      // Algorithm 2 for every point of the batch on the graph as it stands
+      SearchLaunch S;
+      S.data = D.dev();
+      S.col = nbr;
+      S.adj_deg = deg;
+      S.adj_stride = R;
+      S.q_point = pts;
+      S.start = G->start;
+      S.nq = nb;
+      S.L = L;
+      S.k = 1;
+      S.out_ids = sids;
+      S.visited = vis;
+      S.visited_cnt = vis_cnt;
+      S.visited_cap = vcap;
+      S.num_sms = c->num_sms;
+      S.cache_bits = c->search_cache_bits;
+      S.ctas_per_sm = c->search_ctas;
+      S.work = c->work;
+      S.status = c->status;
+      CUDA_TRY(c, cudaMemsetAsync(c->work, 0, 8 * sizeof(unsigned), c->stream));
+      CUDA_TRY(c, launch_search(S, c->stream));
+      // candidates V_p u N_out(p) \ {p}, Algorithm 1 over them, write back
+      CUDA_TRY(c, launch_vamana_candidates(pts, nb, vis, vis_cnt, vcap, nbr, deg, R, cand, ccnt, cut, c->stream));
+      CUDA_TRY(c, launch_scan_counts(ccnt, nb, crp, bsum, maxd, c->stream));
+      CUDA_TRY(c, launch_compact_rows(cand, W, nullptr, ccnt, nb, crp, ccol, c->stream));
+      if ((s = vamana_prune(c, D, crp, ccol, nb, int(W), pts, A[size_t(pass)], R, lists, kept_col, kept_cnt)) !=
+          RP_OK)
+        return s;
+      CUDA_TRY(c, launch_vamana_write_back(pts, nb, crp, kept_col, kept_cnt, nbr, deg, R, c->stream));
+      // back edges
+      CUDA_TRY(c, cudaMemsetAsync(nj, 0, 4, c->stream));
+      CUDA_TRY(c, launch_back_count(pts, nb, nbr, deg, R, pend, slot, jlist, nj, c->stream));
+      c->kernel_launches += 8;
+      const int64_t nJ = read_i32(c, nj, &s);
+      if (s != RP_OK) return s;
+      if (nJ > 0) {
+        CUDA_TRY(c, launch_slot_counts(jlist, nJ, pend, scnt, c->stream));
+        CUDA_TRY(c, launch_scan_counts(scnt, nJ, seg_ptr, bsum, maxd, c->stream));
+        CUDA_TRY(c, cudaMemsetAsync(cursor, 0, size_t(nJ) * 4, c->stream));
+        CUDA_TRY(c, launch_back_scatter(pts, nb, nbr, deg, R, slot, seg_ptr, cursor, seg, c->stream));
+        CUDA_TRY(c, cudaMemsetAsync(n_ov, 0, 4, c->stream));
+        CUDA_TRY(c, launch_back_merge(jlist, nJ, seg_ptr, seg, sorted, nbr, deg, R, pend, ov_raw, ov_slot, ov_cnt,
+                                      n_ov, c->stream));
+        c->kernel_launches += 6;
+        const int64_t nO = read_i32(c, n_ov, &s);
+        if (s != RP_OK) return s;
+        if (nO > 0) {
+          CUDA_TRY(c, launch_ov_prep(ov_slot, nO, jlist, seg_ptr, R, ov_pts, ov_src, c->stream));
+          CUDA_TRY(c, launch_scan_counts(ov_cnt, nO, ov_rp, bsum, maxd, c->stream));
+          CUDA_TRY(c, launch_compact_rows(ov_raw, 0, ov_src, ov_cnt, nO, ov_rp, ov_col, c->stream));
+          int32_t mx = 0;
+          CUDA_TRY(c, cudaMemcpyAsync(&mx, maxd, 4, cudaMemcpyDeviceToHost, c->stream));
+          CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+          if ((s = vamana_prune(c, D, ov_rp, ov_col, nO, mx, ov_pts, A[size_t(pass)], R, lists, ov_kept, ov_kcnt)) !=
+              RP_OK)
+            return s;
+          CUDA_TRY(c, launch_vamana_write_back(ov_pts, nO, ov_rp, ov_kept, ov_kcnt, nbr, deg, R, c->stream));
+          c->kernel_launches += 6;
+        }
+      }
+      b0 += nb;
+    }
+  }
+  // the adjacency as a CSR graph
+  Graph* V = new Graph;
+  V->data = G->data;
+  V->n = n;
+  V->start = G->start;
+  V->max_deg_bound = R;
+  if ((s = dalloc(c, reinterpret_cast<void**>(&V->row_ptr), size_t(n + 1) * 8)) != RP_OK) {
+    free_graph_mem(c, V);
+    return s;
+  }
+  cudaError_t ce = launch_scan_counts(deg, n, V->row_ptr, bsum, maxd, c->stream);
+  if (ce == cudaSuccess) ce = cudaMemcpyAsync(&V->nnz, V->row_ptr + n, 8, cudaMemcpyDeviceToHost, c->stream);
+  if (ce == cudaSuccess) ce = cudaStreamSynchronize(c->stream);
+  if (ce != cudaSuccess) {
+    free_graph_mem(c, V);
+    return fail(c, RP_ECUDA, "vamana graph: %s", cudaGetErrorString(ce));
+  }
+  V->col_cap = std::max<int64_t>(V->nnz, 1);
+  V->bytes = size_t(n + 1) * 8 + size_t(V->col_cap) * 4;
+  if ((s = dalloc(c, reinterpret_cast<void**>(&V->col), size_t(V->col_cap) * 4)) != RP_OK) {
+    free_graph_mem(c, V);
+    return s;
+  }
+  ce = launch_compact_rows(nbr, R, nullptr, deg, n, V->row_ptr, V->col, c->stream);
+  unsigned long long hcut = 0;
+  if (ce == cudaSuccess) ce = cudaMemcpyAsync(&hcut, cut, 8, cudaMemcpyDeviceToHost, c->stream);
+  if (ce == cudaSuccess) ce = cudaStreamSynchronize(c->stream);
+  c->kernel_launches += 4;
+  if (ce != cudaSuccess) {
+    free_graph_mem(c, V);
+    return fail(c, RP_ECUDA, "vamana graph: %s", cudaGetErrorString(ce));
+  }
+  if ((s = check_device_status(c)) != RP_OK) {
+    free_graph_mem(c, V);
+    return s;
+  }
+  if (visited_cut) *visited_cut = int64_t(hcut);
+  *out = add_graph(c, V);
+  return RP_OK;
+}
+
+}  // namespace
+
 extern "C" {
 
 rp_status rp_create(rp_ctx** out, int32_t device, uint64_t hbm_budget_bytes, void* cuda_stream) {
@@ -1252,6 +1511,15 @@ rp_status rp_build_knn_random_base(rp_ctx* c, rp_graph data, int32_t kcand, int3
   std::lock_guard<std::mutex> lk(c->mu);
   cudaSetDevice(c->device);
   return build_base(c, data, kcand, nrand, seed, alpha, R, out);
+}
+
+rp_status rp_build_vamana(rp_ctx* c, rp_graph data, const int32_t* perm, int32_t npass, const double* alphas,
+                          int32_t R, int32_t L, int32_t vcap, int64_t max_batch, int64_t* visited_cut,
+                          rp_graph* out) {
+  if (!c) return RP_EINVAL;
+  std::lock_guard<std::mutex> lk(c->mu);
+  cudaSetDevice(c->device);
+  return build_vamana(c, data, perm, npass, alphas, R, L, vcap, max_batch, visited_cut, out);
 }
 
 rp_status rp_set_search_config(rp_ctx* c, int32_t cache_bits, int32_t ctas_per_sm) {

@@ -63,6 +63,16 @@ struct SearchArgs {
   int cache_bits;             // log2 of the id-cache entries per warp
   unsigned int* work;
   DevStatus* status;
+  // graph construction (Vamana): query i is base point q_point[i]; the graph
+  // is held as adj_deg[v] ids at col + v * adj_stride; the expanded points of
+  // query i go to visited[i * visited_cap ..] (the first visited_cap of them),
+  // their number to visited_cnt[i]
+  const int32_t* q_point;
+  const int32_t* adj_deg;
+  int64_t adj_stride;
+  int32_t* visited;
+  int32_t* visited_cnt;
+  int visited_cap;
 };
 
 struct WarpSmem {
@@ -222,7 +232,8 @@ __global__ void __launch_bounds__(kWarps * 32, 9) search_kernel(SearchArgs a) {
     }
     const int L = a.q_L ? a.q_L[qi] : a.L;
     // stage the query row
-    const uint4* src = reinterpret_cast<const uint4*>(a.Q + int64_t(qi) * a.row_bytes);
+    const uint4* src = reinterpret_cast<const uint4*>(
+        a.q_point ? a.X + int64_t(a.q_point[qi]) * a.row_bytes : a.Q + int64_t(qi) * a.row_bytes);
     for (int c = lane; c < a.row_bytes / 16; c += 32) reinterpret_cast<uint4*>(S.q)[c] = src[c];
     for (int c = lane; c < centries; c += 32) S.cache[c] = 0xffffffffu;
     __syncwarp();
@@ -273,7 +284,15 @@ __global__ void __launch_bounds__(kWarps * 32, 9) search_kernel(SearchArgs a) {
       if (lane == 0) idc[pos] |= kVisited;
       __syncwarp();
       f = pos + 1;
-      const int64_t e0 = row_ptr[ps], e1 = row_ptr[ps + 1];
+      if (a.visited && lane == 0 && iters <= a.visited_cap) a.visited[int64_t(qi) * a.visited_cap + iters - 1] = int32_t(ps);
+      int64_t e0, e1;
+      if (a.adj_deg) {
+        e0 = int64_t(ps) * a.adj_stride;
+        e1 = e0 + a.adj_deg[ps];
+      } else {
+        e0 = row_ptr[ps];
+        e1 = row_ptr[ps + 1];
+      }
       for (int64_t eb = e0; eb < e1; eb += 32) {
         // ---- new neighbours of this batch
         const int64_t e = eb + lane;
@@ -429,6 +448,7 @@ __global__ void __launch_bounds__(kWarps * 32, 9) search_kernel(SearchArgs a) {
         f = min(f, first);
       }
     }
+    if (a.visited_cnt && lane == 0) a.visited_cnt[qi] = int32_t(iters < INT32_MAX ? iters : INT32_MAX);
     // ---- the k closest members
     for (int j = lane; j < a.k; j += 32) {
       const bool have = j < size;
@@ -549,6 +569,12 @@ cudaError_t launch_search(const SearchLaunch& L, cudaStream_t s) {
   a.out_dists = L.out_dists;
   a.work = L.work;
   a.status = L.status;
+  a.q_point = L.q_point;
+  a.adj_deg = L.adj_deg;
+  a.adj_stride = L.adj_stride;
+  a.visited = L.visited;
+  a.visited_cnt = L.visited_cnt;
+  a.visited_cap = L.visited_cap;
   const bool f32 = L.data.dtype == kF32;
   SearchPlan plan;
   if (L.cache_bits >= kMinCacheBits && L.cache_bits <= kMaxCacheBits) {  // a configured plan (rp_set_search_config)
