@@ -1,44 +1,47 @@
 #!/usr/bin/env python
 """Benchmark of the RP-Tuning hot path on one GB300 (per rank under torchrun).
 
-Workload (SIFT-shaped, uint8): n = 1,000,000 points, d = 128, values
-rint(min(255, Gamma(0.6, 40))); base graph = RobustPrune(1.2, 64) over each
-point's exact 128 nearest neighbours, built once by the library (not timed);
-targets (alpha, R) = (1.1, 64), (1.05, 48), (1.0, 32); 10,000 queries,
-L = 128, k = 100.
+Default workload (deep-shaped float, the largest single-GPU configuration):
+n = 10,000,000 points, d = 96, float32 unit rows from a 256-centre Gaussian
+mixture; base graph = Vamana (§2.1, §4.1: two insertion passes at alpha 1.0
+and 1.2, R = 64, L_build = 75), built once by the library on the GPU (not
+timed); eight targets (alpha, R) in {1.15, 1.1, 1.05, 1.0} x {64, 48} in one
+batched, graph-captured launch; 10,000 queries, L = 100, k = 100.
 
 One timed step = the whole hot path over that input: RP-Tuning of every node
-for the three targets in one batched launch (gather, keys, Gram, sort,
-domination bits, scans, CSR emit), GreedySearch of the 10,000 queries on each
-tuned graph and recall@100 of each against the exact kNN ground truth.
-`value` = nodes x targets / second over the timed steps (inputs resident in
-HBM, L2 flushed before every step).  `e2e` repeats the step through the C ABI
-with host buffers: vectors, base CSR and queries copied in, tuned graphs and
-search results copied out, every step.
+for every target in one batched launch (gather, keys, Gram, sort, domination
+bits, scans, CSR emit), GreedySearch of the queries on each tuned graph and
+recall@100 of each against the exact kNN ground truth.  `value` = nodes x
+targets / second over the timed steps (inputs resident in HBM, L2 flushed
+before every step).  `e2e` repeats the step through the C ABI with host
+buffers: vectors, base CSR and queries copied in, tuned graphs and search
+results copied out, every step.
+
+`--workload sift` runs the integer configuration (1,000,000 x 128 uint8,
+rint(min(255, Gamma(0.6, 40))); base RobustPrune(1.2, 64) over each point's
+exact 128 nearest neighbours; targets (1.1, 64), (1.05, 48), (1.0, 32);
+10,000 queries, L = 128).  `--workload gist` runs the batched high-d float sweep
+(1,000,000 x 960 float32 rows, |N(0,1)| * 0.05 then L2-normalised; base over
+exact kNN-128; nine targets: alpha 1.175 down to 1.0 at R = 64 plus (1.0, 32),
+in one launch; 1,000 queries, L = 200).
 
 `serving` (outside the timed step): a Poisson stream of prune-to-(alpha, R)
 jobs and query batches through the library's scheduler (rp_server_*), the
 continuous-batching scheduler against the plain serial path, at offered loads
 relative to the serial path's capacity; p50/p99 latency, QPS and recall@100.
 It runs over the sift base (8 GB of tuned graphs, so the stream evicts) and
-over the deep base (120 GB), with the queries of that workload.
-
-`--workload gist` runs the batched float sweep instead (1,000,000 x 960
-float32 rows, |N(0,1)| * 0.05 then L2-normalised; nine targets: alpha 1.175 down
-to 1.0 at R=64 plus (1.0, 32), in one launch; 1,000 queries, L=200, k=100).
-
-`--workload deep` runs the large float sweep (10,000,000 x 96 float32 unit rows
-from a 256-centre mixture; eight targets alpha in {1.15, 1.1, 1.05, 1.0} x R in
-{64, 48} in one launch; 10,000 queries, L=100, k=100).
+over the deep base (120 GB).
 
 Outside the timed step every workload also sweeps L over 100..256 on the base
-and on each tuned graph (`recall_qps_frontier`: QPS and recall@100 per L), and
-measures alpha-reachability (Definition 2.1) at 64 seeded nodes of the base and
+and on each tuned graph (`recall_qps_frontier`: QPS and recall@100 per L),
+measures alpha-reachability (Definition 2.1) at seeded nodes of the base and
 of every target tuned with the sorted and the unsorted variant
-(`reachability_sample`: min and median of the per-node terms).
-
-Every workload also re-prunes its base at the base's own (1.2, 64) and reports
-whether the result equals the base edge for edge (`idempotence_check`).
+(`reachability_sample`: min and median of the per-node terms; 64 nodes on the
+integer workload, where distances are exact integers, and none on the float
+ones, whose binary64 distances over every point take minutes per node on this
+part), times the Vamana build against the tuning (`rebuild_vs_tune`: the
+analogue of Table 2), and checks that re-pruning a tuned graph at its own
+(alpha, R) returns it edge for edge (`idempotence_check`).
 
 `--impl reference` times the CPU oracle (the reference arm of this build) on
 a bounded sample of the same workload and prints the same JSON line.
@@ -71,7 +74,8 @@ K_SEARCH = 100
 SERVE_BUDGET_GB = {"sift": 8, "deep": 120}
 SERVE_LOADS = (0.5, 0.8, 1.0, 2.0, 4.0)  # offered load / capacity of the serial path
 FRONTIER_L = (100, 128, 160, 200, 256)   # list sizes of the recall-QPS frontier (k = 100)
-REACH_SAMPLE = 64                        # nodes whose alpha-reachability terms are measured
+REACH_SAMPLE = {"sift": 64, "gist": 0, "deep": 0}  # nodes whose alpha-reachability terms are measured
+VAMANA = dict(alphas=(1.0, 1.2), L=75)    # §4.1's base construction (alpha1 = 1.2, L_build = 75), R = BASE_R
 
 # The paper-shaped workloads (synthetic; recipes in datagen).  sift is the
 # default bench line; gist is the batched float sweep (9 targets: alpha 1.175
@@ -83,7 +87,7 @@ WORKLOADS = {
                  targets=[(round(1.175 - 0.025 * i, 3), 64) for i in range(8)] + [(1.0, 32)]),
     "deep": dict(dtype="f32", n=10_000_000, d=96, nq=10_000, L=100,
                  targets=[(a, r) for a in (1.15, 1.1, 1.05, 1.0) for r in (64, 48)],
-                 base=dict(kcand=96, nrand=32, seed=4003)),
+                 base="vamana"),
 }
 TARGETS = WORKLOADS["sift"]["targets"]
 L_SEARCH = WORKLOADS["sift"]["L"]
@@ -93,18 +97,21 @@ def workload_name(n, nq, name="sift"):
     w = WORKLOADS[name]
     shape = {"sift": "sift-shaped uint8", "gist": "gist-shaped float32", "deep": "deep-shaped float32"}[name]
     tl = ",".join(f"({a:g},{r})" for a, r in w["targets"])
-    cand = (f"exact kNN-{w['base']['kcand']} + {w['base']['nrand']} random" if "base" in w else "exact kNN-128")
-    return (f"{shape} n={n:,} d={w['d']}; base RobustPrune(1.2,64) over {cand}; "
-            f"tune {tl}; {nq:,} queries L={w['L']} k=100")
+    if w.get("base") == "vamana":
+        base = (f"base Vamana(alpha {VAMANA['alphas'][0]:g} then {VAMANA['alphas'][1]:g}, R={BASE_R}, "
+                f"L_build={VAMANA['L']})")
+    else:
+        base = "base RobustPrune(1.2,64) over exact kNN-128"
+    return f"{shape} n={n:,} d={w['d']}; {base}; tune {tl}; {nq:,} queries L={w['L']} k=100"
 
 
 def build_base(rp, ctx, data, name):
     """The workload's base graph, built by the library on the GPU (the benchmark's
     untimed fixture; the full-size parity tests build the same one)."""
     W = WORKLOADS[name]
-    if "base" in W:  # exact kNN plus random candidates (the mixture's clusters are far apart)
-        bw = W["base"]
-        return rp.rp_build_knn_random_base(ctx, data, bw["kcand"], bw["nrand"], bw["seed"], BASE_ALPHA, BASE_R)
+    if W.get("base") == "vamana":  # the points are drawn independently: index order is a random order
+        g, _ = rp.rp_build_vamana(ctx, data, VAMANA["alphas"], BASE_R, VAMANA["L"])
+        return g
     return rp.rp_build_knn_base(ctx, data, KCAND, BASE_ALPHA, BASE_R)
 
 
@@ -183,11 +190,16 @@ class ClockSampler:
 # ---------------------------------------------------------------- reference arm / CPU baseline
 
 def oracle_sample(n_sample, name="sift"):
-    """The oracle's own base over the generator's first n points of the workload (no GPU input)."""
+    """The oracle's own base over the generator's first n points of the workload (no GPU input),
+    built the way the workload builds its base."""
     import oracle
     X = datagen.dataset(name, n_sample)
     t0 = time.perf_counter()
-    base_rp, base_col = oracle.knn_base(X, KCAND, BASE_ALPHA, BASE_R)
+    if WORKLOADS[name].get("base") == "vamana":
+        base_rp, base_col, _ = oracle.vamana(X, np.arange(n_sample, dtype=np.int32), VAMANA["alphas"], BASE_R,
+                                             VAMANA["L"], 4 * VAMANA["L"], max(1, n_sample // 50), oracle.medoid(X))
+    else:
+        base_rp, base_col = oracle.knn_base(X, KCAND, BASE_ALPHA, BASE_R)
     return X, base_rp, base_col, time.perf_counter() - t0
 
 
@@ -216,7 +228,7 @@ def cpu_baseline(n_sample=20000, name="sift"):
     return {"value": reps * n_sample * T / secs, "unit": UNIT, "cores": oracle.num_threads(0),
             "kind": "oracle",
             "sample": (f"oracle RP-Tuning of all {n_sample:,} nodes of the generator's first {n_sample:,} points "
-                       f"of the workload (its own kNN-128 -> RobustPrune(1.2,64) base), {T} targets, repeated {reps}x "
+                       f"of the workload (its own base, built as the workload's), {T} targets, repeated {reps}x "
                        f"({secs:.1f} s); GreedySearch of 200 queries {200 / qs:.1f} QPS"),
             "search_qps": 200 / qs}
 
@@ -277,7 +289,11 @@ def run_ours(args):
     # ---- fixture (not timed): vectors, base graph, ground truth
     t0 = time.perf_counter()
     data = rp.rp_load_graph(ctx, X)
+    torch.cuda.synchronize(dev)
+    tb0 = time.perf_counter()
     base = build_base(rp, ctx, data, args.workload)
+    torch.cuda.synchronize(dev)
+    base_build_s = time.perf_counter() - tb0
     base_rp, base_col = rp.rp_graph_export(ctx, base)
     gt, _ = rp.rp_knn(ctx, data, Q, k)
     fixture_s = time.perf_counter() - t0
@@ -367,8 +383,8 @@ def run_ours(args):
     hbm_peak, peak_kind = load_peaks()
     achieved = alg_bytes / (prune_ms / 1000.0) / 1e9
     traffic = None  # DRAM bytes per launch from the committed ncu summary, if it is of this kernel source
-    prof = os.path.join(ROOT, "profiles", "prune_tc_u8_sift1m.md")
-    if os.path.exists(prof) and n == 1_000_000 and args.workload == "sift":
+    prof = os.path.join(ROOT, "profiles", f"prune_tc_{W['dtype']}_{args.workload}_full.md")
+    if os.path.exists(prof) and n == W["n"]:
         fields = {}
         with open(prof) as f:
             for ln in f:
@@ -446,8 +462,8 @@ def run_ours(args):
     # variant would coincide with the sorted one, so the unsorted variant runs on
     # the same lists reversed (farthest first: an arbitrary order, as it allows).
     reach = None
-    if not args.quick:
-        sample = np.sort(np.random.default_rng(5005).choice(n, min(n, REACH_SAMPLE), replace=False))
+    if not args.quick and REACH_SAMPLE[args.workload] > 0:
+        sample = np.sort(np.random.default_rng(5005).choice(n, min(n, REACH_SAMPLE[args.workload]), replace=False))
         reach = {"nodes": int(sample.size), "unsorted_order": "each base list reversed", "graphs": {}}
         r0 = time.perf_counter()
         a_b, per_b = rp.rp_reachability(ctx, base, sample)
@@ -464,14 +480,37 @@ def run_ours(args):
         rp.rp_graph_free(ctx, rev)
         reach["seconds"] = time.perf_counter() - r0
 
-    # ---- idempotence at full size: the base is RobustPrune(1.2, 64) output, so
-    # re-pruning it at (1.2, 64) must return it edge for edge, order included
-    same = rp.rp_tune(ctx, base, BASE_ALPHA, BASE_R)
-    g_rp, g_col = rp.rp_graph_export(ctx, same)
-    b_rp, b_col = rp.rp_graph_export(ctx, base)
+    # ---- idempotence at full size: a tuned graph is RobustPrune output, so
+    # re-pruning it at its own (alpha, R) must return it edge for edge, order
+    # included (checked on the first target)
+    a0, r0 = TARGETS_W[0]
+    once = rp.rp_tune(ctx, base, a0, r0)
+    twice = rp.rp_tune(ctx, once, a0, r0)
+    g_rp, g_col = rp.rp_graph_export(ctx, once)
+    b_rp, b_col = rp.rp_graph_export(ctx, twice)
     idempotent = bool(np.array_equal(g_rp, b_rp) and np.array_equal(g_col, b_col))
-    rp.rp_graph_free(ctx, same)
+    rp.rp_graph_free(ctx, twice)
+    rp.rp_graph_free(ctx, once)
     del g_rp, g_col, b_rp, b_col
+
+    # ---- rebuild vs tune (the analogue of Table 2): a Vamana graph built at the
+    # middle target's alpha against RP-Tuning of the base to it, both on this GPU
+    rebuild = None
+    if not args.quick and W.get("base") == "vamana":
+        am, rm = TARGETS_W[len(TARGETS_W) // 2]
+        torch.cuda.synchronize(dev)
+        r0_ = time.perf_counter()
+        g_re, _ = rp.rp_build_vamana(ctx, data, (VAMANA["alphas"][0], am), rm, VAMANA["L"])
+        torch.cuda.synchronize(dev)
+        t_rebuild = time.perf_counter() - r0_
+        rp.rp_graph_free(ctx, g_re)
+        t0_ = time.perf_counter()
+        g_tu = rp.rp_tune(ctx, base, am, rm)
+        torch.cuda.synchronize(dev)
+        t_tune = time.perf_counter() - t0_
+        rp.rp_graph_free(ctx, g_tu)
+        rebuild = {"alpha": am, "R": rm, "rebuild_s": t_rebuild, "tune_s": t_tune, "speedup": t_rebuild / t_tune,
+                   "note": "Vamana rebuild (alpha 1.0 then alpha) vs RP-Tuning of the base, one GPU"}
 
     # ---- end to end through the C ABI with host buffers
     e2e = None
@@ -541,7 +580,7 @@ def run_ours(args):
             "config": {"workload": workload_name(n, nq, args.workload), "n": n, "d": W["d"], "targets": TARGETS_W,
                        "queries": nq, "L": L_W, "k": k, "l2": "flushed (512 MB write) before every timed step",
                        "parallelism": f"replicas x{ws}" if ws > 1 else "1 GPU"},
-            "roofline": {"bound": "hbm", "kernel": f"prune_tc_kernel<{W['dtype']},64> (tcgen05 Gram)",
+            "roofline": {"bound": "hbm", "kernel": f"prune_tc_kernel<{W['dtype']}, 64, {T}> (tcgen05 Gram)",
                          "achieved": achieved,
                          "peak": hbm_peak, "unit": "GB/s", "frac": achieved / hbm_peak, "traffic": traffic,
                          "peak_kind": peak_kind, "algorithmic_bytes_per_launch": alg_bytes,
@@ -564,7 +603,9 @@ def run_ours(args):
             "fixture_s": fixture_s,
             "recall_qps_frontier": frontier,
             "reachability_sample": reach,
-            "idempotence_check": {"alpha": BASE_ALPHA, "R": BASE_R, "equal_to_base": idempotent},
+            "idempotence_check": {"alpha": a0, "R": r0, "retune_equals_tuned": idempotent},
+            "rebuild_vs_tune": rebuild,
+            "base_build_s": base_build_s,
             "serving": serving,
         }
         print(json.dumps(line), flush=True)
@@ -634,7 +675,7 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="sift")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="deep")
     ap.add_argument("--n", type=int, default=None)
     ap.add_argument("--nq", type=int, default=None)
     ap.add_argument("--no-e2e", action="store_true")

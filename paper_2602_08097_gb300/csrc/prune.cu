@@ -50,6 +50,12 @@ struct PruneArgs {
   int32_t A[kMaxTargets];
   int32_t R[kMaxTargets];
   float inv_A2[kMaxTargets];  // 1 / A^2 rounded: a starting estimate for exact_threshold
+  // Float rows: R only matters in the scan (a7), so targets that share alpha
+  // share one domination mask.  TA distinct A values Ad[0..TA) ascending;
+  // target u uses mask amap[u].
+  int TA;
+  int32_t Ad[kMaxTargets];
+  int32_t amap[kMaxTargets];
   float scale;                // float rows enter the f16 Gram as scale * x (a power of two: exact)
   float inv_s;                // 1 / scale
   float inv_s2;               // 1 / scale^2: the Gram back in the rows' units (exact)
@@ -168,19 +174,26 @@ __device__ __forceinline__ bool fine_dominates(const PruneArgs& a, int32_t u, in
 }
 
 // A float domination test the Gram tier left undecided: row `t` of the node
-// (candidate ids[t]) against column `c`, target A: single-precision difference
+// (candidate ids[t]) against column `c`, alpha = A / 1000: single-precision difference
 // form from the rows, then float-float, then binary64.  Inlined: as an
 // out-of-line call it let the per-target mask loop unroll fully, and the
 // larger code measured 50% slower (64 candidates, 8 targets, 1M x 96 float
 // rows).
 __device__ __forceinline__ bool recheck_dominates(const PruneArgs& a, const int32_t* ids, const float* key,
-                                                  double* key64, int t, int c, int u, int p, float E_rel,
+                                                  double* key64, int t, int c, int32_t A, int p, float E_rel,
                                                   float E_abs) {
-  const int64_t A2 = int64_t(a.A[u]) * a.A[u];
+  const int64_t A2 = int64_t(A) * A;
   const float d2a = row_d2<kF32>(a.X + int64_t(ids[t]) * a.row_bytes, a.X + int64_t(ids[c]) * a.row_bytes,
                                  a.row_bytes);
   const int rr = sure_dominates(float(A2), d2a, key[c], E_rel, E_abs);
   return rr >= 0 ? (rr == 1) : fine_dominates(a, ids[t], ids[c], p, &key64[c], double(A2));
+}
+
+// The same, out of line, for the rare tests decided in place when the queue is full.
+__device__ __noinline__ bool recheck_dominates_cold(const PruneArgs& a, const int32_t* ids, const float* key,
+                                                    double* key64, int t, int c, int32_t A, int p, float E_rel,
+                                                    float E_abs) {
+  return recheck_dominates(a, ids, key, key64, t, c, A, p, E_rel, E_abs);
 }
 
 // ---------------------------------------------------------------------------
@@ -221,11 +234,12 @@ struct TcLayout {
   // per group, producer side
   static constexpr size_t p_norm = 0;
   static constexpr size_t p_sn = p_norm + size_t(MAXM) * 4;
-  static constexpr size_t p_qlo = p_sn + size_t(MAXM) * 4;  // [TB][MAXM]
+  static constexpr size_t p_qlo = p_sn + size_t(MAXM) * 4;  // [TB][MAXM] uint8, [MAXM][TB] float
   static constexpr size_t p_qhi = p_qlo + size_t(TB) * MAXM * 4;
   static constexpr size_t p_sk = p_qhi + size_t(TB) * MAXM * 4;  // [MAXM] (key, id) in stored order
   static constexpr size_t p_k64 = p_sk + size_t(MAXM) * 8;       // [MAXM] binary64 keys in stored order
-  static constexpr size_t p_bytes = p_k64 + size_t(MAXM) * 8;
+  static constexpr size_t p_cq = p_k64 + size_t(MAXM) * 8;        // [MAXM] float4 per column (float rows)
+  static constexpr size_t p_bytes = p_cq + size_t(MAXM) * 16;
   static constexpr size_t off_prod = off_slots + 2 * NG * s_bytes;
   // small words: node/degree/row start per (slot, group), the claim queue's
   // head, mbarrier, TMEM address; then the claim queue (node, degree, row start)
@@ -334,6 +348,7 @@ __global__ void __launch_bounds__(160, tc_min_ctas<DT, MAXM, TB>()) prune_tc_ker
     float* sn = reinterpret_cast<float*>(pb + L::p_sn);
     float* qlo = reinterpret_cast<float*>(pb + L::p_qlo);
     float* qhi = reinterpret_cast<float*>(pb + L::p_qhi);
+    float4* cq = reinterpret_cast<float4*>(pb + L::p_cq);
     const uint32_t tmem = *tmem_slot;
     // operands go in as f16: uint8 values exactly, float rows scaled by a power
     // of two into [-1, 1] and rounded
@@ -409,6 +424,14 @@ __global__ void __launch_bounds__(160, tc_min_ctas<DT, MAXM, TB>()) prune_tc_ker
       const bool live_row = t < m;  // thread t holds stored candidate t
       int32_t my_id = 0;
       if (live_row) my_id = a.col[e0 + t];
+      // The next slot's node of this group, if the claim queue already holds it:
+      // its candidate ids are loaded now and their rows prefetched into L2 while
+      // this slot waits on its Gram, so the next gather finds them there.
+      int32_t next_id = -1;
+      {
+        const int nh = misc[12] + g;
+        if (nh < kClaim && t < qdeg[nh]) next_id = a.col[qe0[nh] + t];
+      }
       const uint8_t* xrow = a.X + int64_t(my_id) * a.row_bytes;
       const int32_t ppt = p >= 0 ? point_of_row(a, p) : 0;  // the point being pruned
       const uint8_t* prow = a.X + int64_t(ppt) * a.row_bytes;
@@ -525,8 +548,10 @@ __global__ void __launch_bounds__(160, tc_min_ctas<DT, MAXM, TB>()) prune_tc_ker
       double my64 = __longlong_as_double(0x7ff8000000000000ll);
       if constexpr (DT == kF32) {
         // single-precision keys that might be out of order (intervals overlap):
-        // both ends of every such pair take their binary64 key, and those pairs
-        // are ordered by it (ties by id), as Algorithm 1 reads d2 in binary64
+        // both ends of every such pair take a float-float key, and those pairs
+        // are ordered by it; only if two float-float intervals still meet do
+        // all such keys take their binary64 value (ties by id), as Algorithm 1
+        // reads d2 in binary64
         bool near = false;
         if (!in_order && live_row) {
           for (int j = 0; j < m && !near; ++j) {
@@ -536,26 +561,46 @@ __global__ void __launch_bounds__(160, tc_min_ctas<DT, MAXM, TB>()) prune_tc_ker
         }
         if (!in_order && prod_sync_or(near)) {
           double* k64s = reinterpret_cast<double*>(pb + L::p_k64);  // stored order
-          if (near) {
-            my64 = canon_d2_f32(reinterpret_cast<const float*>(prow), reinterpret_cast<const float*>(xrow), a.d);
-            atomicAdd(&a.status->fp64_sort_keys, 1ull);
-          }
+          const FFBound fb = ff_bound(a.d);
+          if (near) my64 = -ff_d2(reinterpret_cast<const float*>(prow), reinterpret_cast<const float*>(xrow), a.row_bytes);
           k64s[t] = my64;
           named_sync(kBarProd, 128);
+          int cnt = 0;
+          bool open = false;
           if (near) {
-            int cnt = 0;
             for (int j = 0; j < m; ++j) {
               const float kj = __uint_as_float(unsigned(sk[j] >> 32));
               if (sure_less(kj, kacc, E_rel, E_abs)) {
                 ++cnt;
               } else if (j != t && !sure_less(kacc, kj, E_rel, E_abs)) {
-                const double dj = k64s[j];
-                const int32_t idj = int32_t(unsigned(sk[j]));
-                cnt += (dj < my64 || (dj == my64 && idj < my_id)) ? 1 : 0;
+                const int o = slot_order(k64s[j], my64, fb);  // 1: j first
+                if (o < 0) open = true;
+                else cnt += o;
               }
             }
-            rank = cnt;
           }
+          if (prod_sync_or(open)) {  // every reader of k64s has passed the barrier
+            if (near) {
+              my64 = canon_d2_f32(reinterpret_cast<const float*>(prow), reinterpret_cast<const float*>(xrow), a.d);
+              atomicAdd(&a.status->fp64_sort_keys, 1ull);
+            }
+            k64s[t] = my64;
+            named_sync(kBarProd, 128);
+            if (near) {
+              cnt = 0;
+              for (int j = 0; j < m; ++j) {
+                const float kj = __uint_as_float(unsigned(sk[j] >> 32));
+                if (sure_less(kj, kacc, E_rel, E_abs)) {
+                  ++cnt;
+                } else if (j != t && !sure_less(kacc, kj, E_rel, E_abs)) {
+                  const double dj = k64s[j];
+                  const int32_t idj = int32_t(unsigned(sk[j]));
+                  cnt += (dj < my64 || (dj == my64 && idj < my_id)) ? 1 : 0;
+                }
+              }
+            }
+          }
+          if (near) rank = cnt;
         }
       }
       if (live_row) {
@@ -637,12 +682,14 @@ __global__ void __launch_bounds__(160, tc_min_ctas<DT, MAXM, TB>()) prune_tc_ker
           umma_commit(mbar);
         }
         if (last) {
-          // while the MMA runs: the thresholds of column `rank` for every target (a6)
+          // while the MMA runs: the thresholds of column `rank` for every target
+          // (uint8) or every distinct alpha (float) (a6)
           if (live_row) {
 #pragma unroll
             for (int u = 0; u < TB; ++u) {
-              if (u >= T) break;
-              const unsigned long long A2 = static_cast<unsigned long long>(a.A[u]) * a.A[u];
+              if (u >= (DT == kF32 ? a.TA : T)) break;
+              const int32_t Au = DT == kF32 ? a.Ad[u] : a.A[u];
+              const unsigned long long A2 = static_cast<unsigned long long>(Au) * Au;
               if constexpr (DT == kU8) {
                 // v is removed by row u'  <=>  A2 d2(u', v) <= 1e6 d2(p, v)
                 //   <=>  2 G(u', v) - |u'|^2 >= |v|^2 - floor(1e6 d2(p, v) / A2)
@@ -650,12 +697,19 @@ __global__ void __launch_bounds__(160, tc_min_ctas<DT, MAXM, TB>()) prune_tc_ker
                 const unsigned thr = exact_threshold(kacc, A2, a.inv_A2[u]);
                 qlo[u * MAXM + rank] = float(int(nacc) - int(thr));
               } else {
+                // float thresholds per column, distinct alphas contiguous
                 const float A2f = float(A2);
-                qlo[u * MAXM + rank] = 1.0e6f * (kacc * (1.0f - E_rel) - E_abs) * 0.9999995f / A2f * 0.9999995f;
-                qhi[u * MAXM + rank] = 1.0e6f * (kacc * (1.0f + E_rel) + E_abs) * 1.0000005f / A2f * 1.0000005f;
+                qlo[rank * TB + u] = 1.0e6f * (kacc * (1.0f - E_rel) - E_abs) * 0.9999995f / A2f * 0.9999995f;
+                qhi[rank * TB + u] = 1.0e6f * (kacc * (1.0f + E_rel) + E_abs) * 1.0000005f / A2f * 1.0000005f;
               }
             }
+            if constexpr (DT == kF32)  // the column's norm, its root, and the loosest surely-kept bound
+              cq[rank] = make_float4(float(nacc), sqrtf(float(nacc)), 0.f, qhi[rank * TB]);
           }
+        }
+        if (last && next_id >= 0) {
+          const char* nrow = reinterpret_cast<const char*>(a.X + int64_t(next_id) * a.row_bytes);
+          for (int64_t off = 0; off < a.row_bytes; off += 128) asm volatile("prefetch.global.L2 [%0];" ::"l"(nrow + off));
         }
         const bool ok = mbar_wait(mbar, phase, 1 << 24);
         if (prod_sync_or(!ok)) {  // the MMA never completed: report, stop after this slot (uniform)
@@ -719,53 +773,136 @@ __global__ void __launch_bounds__(160, tc_min_ctas<DT, MAXM, TB>()) prune_tc_ker
             }
           }
         } else {
+          // Float rows: for every column c after row t, ts = how many distinct
+          // alphas surely remove c and tp = how many may (both prefixes: the
+          // alphas ascend and the thresholds fall with them).  ts is kept as NB
+          // bit planes over the columns; pairs with ts < tp go to the recheck
+          // queue.  The code is branch-free per column, so the sixteen columns
+          // of a TMEM read overlap.
+          constexpr int NB = TB <= 1 ? 1 : TB <= 3 ? 2 : TB <= 7 ? 3 : TB <= 15 ? 4 : 5;
+          unsigned long long pl[NB][MW];
+#pragma unroll
+          for (int b = 0; b < NB; ++b)
+#pragma unroll
+            for (int w = 0; w < MW; ++w) pl[b][w] = 0;
+          unsigned long long und[MW];
+#pragma unroll
+          for (int w = 0; w < MW; ++w) und[w] = 0;
+          uint32_t rec0 = 0, rec1 = 0;  // the first two open pairs: c | ts << 8 | tp << 16
+          int nrec = 0;
+          const int TA = a.TA;
+          // the d2 error bound as two multiply-adds: err = |c| At + |c|^2 eps_n + Bt
+          const float At = 2.f * eps_ip * st * 1.0009765625f + sub_abs;
+          const float Bt = sub_abs * st + eps_n * nt + err_abs;
+          const int cend = (m + 15) & ~15;  // the same for every lane of the warp (one node)
 #pragma unroll 1
-          for (int c0 = first_col; c0 < MAXM; c0 += 32) {
-            uint32_t v[32], v2[32];
-            tmem_ld32(tmem + (uint32_t(32 * warp) << 16) + uint32_t(g * MAXM + c0), v);
-            tmem_ld32(tmem + (uint32_t(32 * warp) << 16) + uint32_t(128 + g * MAXM + c0), v2);
+          for (int c0 = first_col; c0 < cend; c0 += 16) {
+            uint32_t v[16], v2[16];
+            tmem_ld8(tmem + (uint32_t(32 * warp) << 16) + uint32_t(g * MAXM + c0), *reinterpret_cast<uint32_t(*)[8]>(v));
+            tmem_ld8(tmem + (uint32_t(32 * warp) << 16) + uint32_t(g * MAXM + c0 + 8),
+                     *reinterpret_cast<uint32_t(*)[8]>(v + 8));
+            tmem_ld8(tmem + (uint32_t(32 * warp) << 16) + uint32_t(128 + g * MAXM + c0),
+                     *reinterpret_cast<uint32_t(*)[8]>(v2));
+            tmem_ld8(tmem + (uint32_t(32 * warp) << 16) + uint32_t(128 + g * MAXM + c0 + 8),
+                     *reinterpret_cast<uint32_t(*)[8]>(v2 + 8));
             tmem_ld_wait();
-            if (live_row) {
 #pragma unroll
-              for (int j = 0; j < 32; ++j) {
-                const int c = c0 + j;
-                if (c >= m) break;
-                // hi hi^T + 2^-11 (cross terms), back in the rows' units (powers of two: exact scalings)
-                const float G = fmaf(__uint_as_float(v2[j]), 4.8828125e-04f, __uint_as_float(v[j])) * a.inv_s2;
-                const unsigned long long bit = 1ull << (c & 63);
-                const int w = MW == 1 ? 0 : (c >> 6);
-                const float nc = float(norm[c]);
-                const float dv = (nt + nc) - 2.f * G;
-                const float err = 2.f * eps_ip * st * sn[c] * 1.0009765625f + sub_abs * (st + sn[c]) +
-                                  eps_n * (nt + nc) + err_abs;
-                const float hi = (dv + err) * 1.0000005f, lo = (dv - err) * 0.9999995f;
-                // Targets come in ascending A, and qhi (1e6 x an upper key, divided
-                // by A^2, every step rounded monotonically) cannot grow with u: a
-                // pair surely not removed here is surely not removed at any later
-                // target, so the loop stops there.
+            for (int j = 0; j < 16; ++j) {
+              const int c = c0 + j;
+              const float4 q = cq[c];
+              // hi hi^T + 2^-11 (cross terms), back in the rows' units (powers of two: exact scalings)
+              const float G = fmaf(__uint_as_float(v2[j]), 4.8828125e-04f, __uint_as_float(v[j])) * a.inv_s2;
+              const float dv = (nt + q.x) - 2.f * G;
+              const float err = fmaf(q.y, At, fmaf(q.x, eps_n, Bt));
+              const float lo = (dv - err) * 0.9999995f;
+              const float hi = (dv + err) * 1.0000005f;
+              const bool valid = live_row && c > t && c < m;
+              int ts = 0, tp = 0;
 #pragma unroll
-                for (int u = 0; u < TB; ++u) {
-                  if (u >= T) break;
-                  bool dom;
-                  if (hi < qlo[u * MAXM + c]) {
-                    dom = true;
-                  } else if (lo > qhi[u * MAXM + c]) {
-                    break;
+              for (int u = 0; u < TB; ++u) {
+                if (u < TA) {
+                  ts += hi < qlo[c * TB + u] ? 1 : 0;
+                  tp += lo > qhi[c * TB + u] ? 0 : 1;
+                }
+              }
+              ts = valid ? ts : 0;
+              tp = valid ? tp : 0;
+              const unsigned long long bit = 1ull << (c & 63);
+              const bool w1 = MW > 1 && c >= 64;
+#pragma unroll
+              for (int b = 0; b < NB; ++b) {
+                const unsigned long long m_b = ((ts >> b) & 1) ? bit : 0ull;
+                pl[b][0] |= w1 ? 0ull : m_b;
+                pl[b][MW - 1] |= w1 ? m_b : 0ull;
+              }
+              const bool open = tp > ts;
+              const unsigned long long m_o = open ? bit : 0ull;
+              und[0] |= w1 ? 0ull : m_o;
+              und[MW - 1] |= w1 ? m_o : 0ull;
+              const uint32_t pack = uint32_t(c) | (uint32_t(ts) << 8) | (uint32_t(tp) << 16);
+              rec1 = (open && nrec == 1) ? pack : rec1;
+              rec0 = (open && nrec == 0) ? pack : rec0;
+              nrec += open ? 1 : 0;
+            }
+          }
+          // open pairs: the first two with their undecided range, any further ones
+          // with every alpha (the recheck decides each exactly either way)
+          if (nrec > 0) {
+#pragma unroll
+            for (int w = 0; w < MW; ++w) {
+              while (und[w]) {
+                const int c = 64 * w + __ffsll(static_cast<long long>(und[w])) - 1;
+                und[w] &= und[w] - 1;
+                int u0 = 0, u1 = TA;
+                if (nrec >= 1 && int(rec0 & 0xffu) == c) {
+                  u0 = int((rec0 >> 8) & 0xffu);
+                  u1 = int(rec0 >> 16);
+                } else if (nrec >= 2 && int(rec1 & 0xffu) == c) {
+                  u0 = int((rec1 >> 8) & 0xffu);
+                  u1 = int(rec1 >> 16);
+                }
+                for (int u = u0; u < u1; ++u) {
+                  // queued and resolved after this pass by all producer threads at
+                  // once; decided here if the queue is full
+                  const int qi = atomicAdd(rq_count + s, 1);
+                  if (qi < L::rq_cap) {
+                    rq[qi] = (unsigned(g * MAXM + t) << 16) | (unsigned(c) << 5) | unsigned(u);
                   } else {
-                    // Undecided: queued, and resolved after this pass by all producer
-                    // threads at once (one lane's recheck no longer holds up its warp
-                    // and, at the barrier, the others); decided here if the queue is full.
-                    const int qi = atomicAdd(rq_count + s, 1);
-                    if (qi < L::rq_cap) {
-                      rq[qi] = (unsigned(g * MAXM + t) << 16) | (unsigned(c) << 5) | unsigned(u);
-                      dom = false;
-                    } else {
-                      dom = recheck_dominates(a, ids, key, key64, t, c, u, ppt, E_rel, E_abs);
-                      ++n_rechecks;
+                    ++n_rechecks;
+                    // the binary64 decision is monotone in alpha: kept here means kept
+                    // at every larger alpha, removed here means removed at every
+                    // smaller one, so ts for this column becomes u + 1
+                    if (!recheck_dominates_cold(a, ids, key, key64, t, c, a.Ad[u], ppt, E_rel, E_abs)) break;
+                    const unsigned long long bit = 1ull << (c & 63);
+#pragma unroll
+                    for (int b = 0; b < NB; ++b) {
+                      const unsigned long long m_b = (((u + 1) >> b) & 1) ? bit : 0ull;
+                      if (w == 0) pl[b][0] = (pl[b][0] & ~bit) | m_b;
+                      else pl[b][MW - 1] = (pl[b][MW - 1] & ~bit) | m_b;
                     }
                   }
-                  if (dom) mk[u][w] |= bit;
                 }
+              }
+            }
+          }
+          // planes -> one row mask per distinct alpha: bit c of mask u is [ts(t, c) > u]
+          if (live_row) {
+#pragma unroll
+            for (int u = 0; u < TB; ++u) {
+              if (u >= TA) break;
+#pragma unroll
+              for (int w = 0; w < MW; ++w) {
+                unsigned long long gt = 0, eq = ~0ull;
+#pragma unroll
+                for (int b = NB - 1; b >= 0; --b) {
+                  if ((u >> b) & 1) {
+                    eq &= pl[b][w];
+                  } else {
+                    gt |= eq & pl[b][w];
+                    eq &= ~pl[b][w];
+                  }
+                }
+                mk[u][w] |= gt;
               }
             }
           }
@@ -773,7 +910,7 @@ __global__ void __launch_bounds__(160, tc_min_ctas<DT, MAXM, TB>()) prune_tc_ker
         if (live_row) {
 #pragma unroll
           for (int u = 0; u < TB; ++u) {
-            if (u >= T) break;
+            if (u >= (DT == kF32 ? a.TA : T)) break;
 #pragma unroll
             for (int w = 0; w < MW; ++w) masks[(u * MAXM + t) * MW + w] = mk[u][w];
           }
@@ -794,7 +931,7 @@ __global__ void __launch_bounds__(160, tc_min_ctas<DT, MAXM, TB>()) prune_tc_ker
             unsigned char* sbq = slot_base(s, gq);
             if (recheck_dominates(a, reinterpret_cast<const int32_t*>(sbq + L::s_ids),
                                   reinterpret_cast<const float*>(sbq + L::s_key),
-                                  reinterpret_cast<double*>(sbq + L::s_key64), tq, c, u,
+                                  reinterpret_cast<double*>(sbq + L::s_key64), tq, c, a.Ad[u],
                                   point_of_row(a, misc[s * 2 + gq]), E_rel, E_abs))
               atomicOr(reinterpret_cast<unsigned long long*>(sbq + L::s_masks) + (u * MAXM + tq) * MW + (c >> 6),
                        1ull << (c & 63));
@@ -845,6 +982,7 @@ __global__ void __launch_bounds__(160, tc_min_ctas<DT, MAXM, TB>()) prune_tc_ker
             al[w] = m > lo ? ((m - lo >= 64) ? ~0ull : ((1ull << (m - lo)) - 1)) : 0ull;
           }
           const int R = a.R[u];
+          const int mu = DT == kF32 ? a.amap[u] : u;  // the target's domination mask
           int32_t* out = a.out_col[u] + e0;
           int kept = 0;
           while (kept < R) {
@@ -856,7 +994,7 @@ __global__ void __launch_bounds__(160, tc_min_ctas<DT, MAXM, TB>()) prune_tc_ker
             out[kept++] = ids[pos];
             al[pos >> 6] &= ~(1ull << (pos & 63));  // taken (its own mask bit is set too)
 #pragma unroll
-            for (int q = 0; q < MW; ++q) al[q] &= ~masks[(u * MAXM + pos) * MW + q];
+            for (int q = 0; q < MW; ++q) al[q] &= ~masks[(mu * MAXM + pos) * MW + q];
           }
           a.out_cnt[u][p] = kept;
         }
@@ -1344,6 +1482,12 @@ cudaError_t launch_prune(const PruneLaunch& L, cudaStream_t s) {
     a.inv_A2[t] = float(1.0 / (double(L.A[o]) * double(L.A[o])));
     a.out_col[t] = L.out_col[o];
     a.out_cnt[t] = L.out_cnt[o];
+  }
+  // distinct alphas (ascending, as the targets now are) and each target's index among them
+  a.TA = 0;
+  for (int t = 0; t < L.T; ++t) {
+    if (a.TA == 0 || a.Ad[a.TA - 1] != a.A[t]) a.Ad[a.TA++] = a.A[t];
+    a.amap[t] = a.TA - 1;
   }
   cudaError_t err = cudaSuccess;
   for (int b = 0; b < 3 && err == cudaSuccess; ++b) {

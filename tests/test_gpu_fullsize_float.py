@@ -1,7 +1,7 @@
 """Full-size parity of the float paths in the launch configuration bench.py
 times: the deep-shaped sweep (10,000,000 x 96 float32, eight targets in one
-batched launch) and the gist-shaped sweep (1,000,000 x 960 float32, nine
-targets in one launch), each over the benchmark's own base graph.
+batched launch, over the benchmark's Vamana base) and the gist-shaped sweep
+(1,000,000 x 960 float32, nine targets in one launch, over its kNN-128 base).
 
 These are the runs in which the float decision tiers do the most work (near
 ties in the sort keys, Gram-tier tests inside the error bound, recheck queues

@@ -182,6 +182,35 @@ def test_near_ties_in_float_keys(ctx):
     rp.rp_graph_free(ctx, g)
 
 
+def test_near_and_exact_ties_on_the_tensor_core_path(ctx):
+    """Rows of at most 64 candidates (the tensor-core kernel): keys that agree
+    to single precision are ordered by float-float distances, and exact ties
+    (copies of one point under different ids) fall through to binary64 and
+    then to the smaller id, as Algorithm 1's argmin with ties by id reads."""
+    rng = np.random.default_rng(21)
+    n, d = 400, 24
+    base = rng.normal(size=(n, d))
+    X = (base / np.linalg.norm(base, axis=1, keepdims=True) * (1 + 1e-7 * rng.random((n, 1)))).astype(np.float32)
+    X[0] = 0
+    X[10:20] = X[5]  # ten copies of point 5: equal keys for every node
+    rows = [list(range(1, 60))] + [list(rng.choice(np.arange(1, n), 48, replace=False)) for _ in range(n - 1)]
+    row_ptr = np.zeros(n + 1, np.int64)
+    np.cumsum([len(r) for r in rows], out=row_ptr[1:])
+    col = np.concatenate([np.asarray(r, np.int32) for r in rows])
+    rp.rp_stats(ctx, reset=True)
+    g = rp.rp_load_graph(ctx, X, row_ptr, col)
+    for alpha in (1.0, 1.3):
+        for variant in (rp.RP_SORTED, rp.RP_UNSORTED):
+            t = rp.rp_tune(ctx, g, alpha, rp.RP_R_INF, variant)
+            ref = oracle.rp_tune(X, row_ptr, col, alpha, variant="sorted" if variant == rp.RP_SORTED else "unsorted")
+            _same_csr(rp.rp_graph_export(ctx, t), ref, f"ties a={alpha} v={variant}")
+            rp.rp_graph_free(ctx, t)
+    st = rp.rp_stats(ctx)
+    assert st["generic_nodes"] == 0
+    assert st["fp64_sort_keys"] > 0  # the exact ties
+    rp.rp_graph_free(ctx, g)
+
+
 def test_degenerate_graphs(ctx):
     X = datagen.dataset("sift", 50)
     # no edges at all
