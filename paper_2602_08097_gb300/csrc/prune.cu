@@ -234,12 +234,17 @@ struct TcLayout {
   // per group, producer side
   static constexpr size_t p_norm = 0;
   static constexpr size_t p_sn = p_norm + size_t(MAXM) * 4;
-  static constexpr size_t p_qlo = p_sn + size_t(MAXM) * 4;  // [TB][MAXM] uint8, [MAXM][TB] float
-  static constexpr size_t p_qhi = p_qlo + size_t(TB) * MAXM * 4;
-  static constexpr size_t p_sk = p_qhi + size_t(TB) * MAXM * 4;  // [MAXM] (key, id) in stored order
+  // thresholds: [TB][MAXM] for uint8; [MAXM][TB4] for float (distinct alphas of a
+  // column contiguous, padded to a multiple of 4 for 16-byte reads)
+  static constexpr int TB4 = (TB + 3) / 4 * 4;
+  static constexpr size_t p_qlo = p_sn + size_t(MAXM) * 4;
+  static constexpr size_t p_qhi = p_qlo + size_t(TB4) * MAXM * 4;
+  static constexpr size_t p_sk = p_qhi + size_t(TB4) * MAXM * 4;  // [MAXM] (key, id) in stored order
   static constexpr size_t p_k64 = p_sk + size_t(MAXM) * 8;       // [MAXM] binary64 keys in stored order
   static constexpr size_t p_cq = p_k64 + size_t(MAXM) * 8;        // [MAXM] float4 per column (float rows)
-  static constexpr size_t p_bytes = p_cq + size_t(MAXM) * 16;
+  static constexpr size_t p_srt = p_cq + size_t(MAXM) * 16;       // [MAXM] float keys by rank (float rows)
+  static constexpr size_t p_bytes = p_srt + size_t(MAXM) * 4;
+  static_assert(p_qlo % 16 == 0 && p_qhi % 16 == 0 && p_cq % 16 == 0 && p_bytes % 16 == 0, "16-byte reads");
   static constexpr size_t off_prod = off_slots + 2 * NG * s_bytes;
   // small words: node/degree/row start per (slot, group), the claim queue's
   // head, mbarrier, TMEM address; then the claim queue (node, degree, row start)
@@ -552,12 +557,18 @@ __global__ void __launch_bounds__(160, tc_min_ctas<DT, MAXM, TB>()) prune_tc_ker
         // are ordered by it; only if two float-float intervals still meet do
         // all such keys take their binary64 value (ties by id), as Algorithm 1
         // reads d2 in binary64
+        // A key has a near partner iff a neighbour in single-precision order has
+        // one: sure_less is monotone, so every key between two near keys is near
+        // both.  The keys are laid out by rank (that order) and each thread looks
+        // at its two neighbours.
         bool near = false;
-        if (!in_order && live_row) {
-          for (int j = 0; j < m && !near; ++j) {
-            const float kj = __uint_as_float(unsigned(sk[j] >> 32));
-            near = j != t && !sure_less(kj, kacc, E_rel, E_abs) && !sure_less(kacc, kj, E_rel, E_abs);
-          }
+        if (!in_order) {
+          float* srt = reinterpret_cast<float*>(pb + L::p_srt);
+          if (live_row) srt[rank] = kacc;
+          named_sync(kBarProd, 128);
+          if (live_row)
+            near = (rank > 0 && !sure_less(srt[rank - 1], kacc, E_rel, E_abs)) ||
+                   (rank + 1 < m && !sure_less(kacc, srt[rank + 1], E_rel, E_abs));
         }
         if (!in_order && prod_sync_or(near)) {
           double* k64s = reinterpret_cast<double*>(pb + L::p_k64);  // stored order
@@ -697,14 +708,21 @@ __global__ void __launch_bounds__(160, tc_min_ctas<DT, MAXM, TB>()) prune_tc_ker
                 const unsigned thr = exact_threshold(kacc, A2, a.inv_A2[u]);
                 qlo[u * MAXM + rank] = float(int(nacc) - int(thr));
               } else {
-                // float thresholds per column, distinct alphas contiguous
+                // float thresholds per column, distinct alphas contiguous.  The
+                // last factor of each (1 -+ 1e-6) covers the roundings of the
+                // pair's d2 - err and d2 + err, compared against them directly.
                 const float A2f = float(A2);
-                qlo[rank * TB + u] = 1.0e6f * (kacc * (1.0f - E_rel) - E_abs) * 0.9999995f / A2f * 0.9999995f;
-                qhi[rank * TB + u] = 1.0e6f * (kacc * (1.0f + E_rel) + E_abs) * 1.0000005f / A2f * 1.0000005f;
+                qlo[rank * L::TB4 + u] =
+                    1.0e6f * (kacc * (1.0f - E_rel) - E_abs) * 0.9999995f / A2f * 0.9999995f * 0.999999f;
+                qhi[rank * L::TB4 + u] =
+                    1.0e6f * (kacc * (1.0f + E_rel) + E_abs) * 1.0000005f / A2f * 1.0000005f * 1.000001f;
               }
             }
-            if constexpr (DT == kF32)  // the column's norm, its root, and the loosest surely-kept bound
-              cq[rank] = make_float4(float(nacc), sqrtf(float(nacc)), 0.f, qhi[rank * TB]);
+            if constexpr (DT == kF32) {
+              // padding past the last alpha never counts (hi < -inf, lo > -inf)
+              for (int u = a.TA; u < L::TB4; ++u) qlo[rank * L::TB4 + u] = qhi[rank * L::TB4 + u] = -INFINITY;
+              cq[rank] = make_float4(float(nacc), sqrtf(float(nacc)), 0.f, 0.f);  // the column's norm and its root
+            }
           }
         }
         if (last && next_id >= 0) {
@@ -778,7 +796,8 @@ __global__ void __launch_bounds__(160, tc_min_ctas<DT, MAXM, TB>()) prune_tc_ker
           // alphas ascend and the thresholds fall with them).  ts is kept as NB
           // bit planes over the columns; pairs with ts < tp go to the recheck
           // queue.  The code is branch-free per column, so the sixteen columns
-          // of a TMEM read overlap.
+          // of a TMEM read overlap; each column's bits go first into 16-bit
+          // chunk words at constant positions.
           constexpr int NB = TB <= 1 ? 1 : TB <= 3 ? 2 : TB <= 7 ? 3 : TB <= 15 ? 4 : 5;
           unsigned long long pl[NB][MW];
 #pragma unroll
@@ -788,12 +807,12 @@ __global__ void __launch_bounds__(160, tc_min_ctas<DT, MAXM, TB>()) prune_tc_ker
           unsigned long long und[MW];
 #pragma unroll
           for (int w = 0; w < MW; ++w) und[w] = 0;
-          uint32_t rec0 = 0, rec1 = 0;  // the first two open pairs: c | ts << 8 | tp << 16
-          int nrec = 0;
           const int TA = a.TA;
           // the d2 error bound as two multiply-adds: err = |c| At + |c|^2 eps_n + Bt
           const float At = 2.f * eps_ip * st * 1.0009765625f + sub_abs;
           const float Bt = sub_abs * st + eps_n * nt + err_abs;
+          const float4* ql4 = reinterpret_cast<const float4*>(qlo);
+          const float4* qh4 = reinterpret_cast<const float4*>(qhi);
           const int cend = (m + 15) & ~15;  // the same for every lane of the warp (one node)
 #pragma unroll 1
           for (int c0 = first_col; c0 < cend; c0 += 16) {
@@ -806,6 +825,9 @@ __global__ void __launch_bounds__(160, tc_min_ctas<DT, MAXM, TB>()) prune_tc_ker
             tmem_ld8(tmem + (uint32_t(32 * warp) << 16) + uint32_t(128 + g * MAXM + c0 + 8),
                      *reinterpret_cast<uint32_t(*)[8]>(v2 + 8));
             tmem_ld_wait();
+            uint32_t cp[NB], cu = 0;
+#pragma unroll
+            for (int b = 0; b < NB; ++b) cp[b] = 0;
 #pragma unroll
             for (int j = 0; j < 16; ++j) {
               const int c = c0 + j;
@@ -814,72 +836,64 @@ __global__ void __launch_bounds__(160, tc_min_ctas<DT, MAXM, TB>()) prune_tc_ker
               const float G = fmaf(__uint_as_float(v2[j]), 4.8828125e-04f, __uint_as_float(v[j])) * a.inv_s2;
               const float dv = (nt + q.x) - 2.f * G;
               const float err = fmaf(q.y, At, fmaf(q.x, eps_n, Bt));
-              const float lo = (dv - err) * 0.9999995f;
-              const float hi = (dv + err) * 1.0000005f;
-              const bool valid = live_row && c > t && c < m;
+              const float lo = dv - err, hi = dv + err;
               int ts = 0, tp = 0;
 #pragma unroll
-              for (int u = 0; u < TB; ++u) {
-                if (u < TA) {
-                  ts += hi < qlo[c * TB + u] ? 1 : 0;
-                  tp += lo > qhi[c * TB + u] ? 0 : 1;
+              for (int u4 = 0; u4 < L::TB4; u4 += 4) {
+                if (u4 < TA) {  // uniform
+                  const float4 l4 = ql4[(c * L::TB4 + u4) / 4];
+                  const float4 h4 = qh4[(c * L::TB4 + u4) / 4];
+                  ts += int(hi < l4.x) + int(hi < l4.y) + int(hi < l4.z) + int(hi < l4.w);
+                  tp += int(!(lo > h4.x)) + int(!(lo > h4.y)) + int(!(lo > h4.z)) + int(!(lo > h4.w));
                 }
               }
+              const bool valid = live_row && c > t && c < m;
               ts = valid ? ts : 0;
               tp = valid ? tp : 0;
-              const unsigned long long bit = 1ull << (c & 63);
-              const bool w1 = MW > 1 && c >= 64;
 #pragma unroll
-              for (int b = 0; b < NB; ++b) {
-                const unsigned long long m_b = ((ts >> b) & 1) ? bit : 0ull;
-                pl[b][0] |= w1 ? 0ull : m_b;
-                pl[b][MW - 1] |= w1 ? m_b : 0ull;
-              }
-              const bool open = tp > ts;
-              const unsigned long long m_o = open ? bit : 0ull;
-              und[0] |= w1 ? 0ull : m_o;
-              und[MW - 1] |= w1 ? m_o : 0ull;
-              const uint32_t pack = uint32_t(c) | (uint32_t(ts) << 8) | (uint32_t(tp) << 16);
-              rec1 = (open && nrec == 1) ? pack : rec1;
-              rec0 = (open && nrec == 0) ? pack : rec0;
-              nrec += open ? 1 : 0;
+              for (int b = 0; b < NB; ++b) cp[b] |= ((uint32_t(ts) >> b) & 1u) << j;
+              cu |= uint32_t(tp > ts) << j;
             }
+            const int sh = c0 & 63;
+            const bool w1 = MW > 1 && c0 >= 64;
+#pragma unroll
+            for (int b = 0; b < NB; ++b) {
+              const unsigned long long x = static_cast<unsigned long long>(cp[b]) << sh;
+              pl[b][0] |= w1 ? 0ull : x;
+              pl[b][MW - 1] |= w1 ? x : 0ull;
+            }
+            const unsigned long long xu = static_cast<unsigned long long>(cu) << sh;
+            und[0] |= w1 ? 0ull : xu;
+            und[MW - 1] |= w1 ? xu : 0ull;
           }
-          // open pairs: the first two with their undecided range, any further ones
-          // with every alpha (the recheck decides each exactly either way)
-          if (nrec > 0) {
+          // open pairs (rare): every alpha from ts on goes to the recheck, which
+          // decides each exactly (those that in fact keep the pair say so)
 #pragma unroll
-            for (int w = 0; w < MW; ++w) {
-              while (und[w]) {
-                const int c = 64 * w + __ffsll(static_cast<long long>(und[w])) - 1;
-                und[w] &= und[w] - 1;
-                int u0 = 0, u1 = TA;
-                if (nrec >= 1 && int(rec0 & 0xffu) == c) {
-                  u0 = int((rec0 >> 8) & 0xffu);
-                  u1 = int(rec0 >> 16);
-                } else if (nrec >= 2 && int(rec1 & 0xffu) == c) {
-                  u0 = int((rec1 >> 8) & 0xffu);
-                  u1 = int(rec1 >> 16);
-                }
-                for (int u = u0; u < u1; ++u) {
-                  // queued and resolved after this pass by all producer threads at
-                  // once; decided here if the queue is full
-                  const int qi = atomicAdd(rq_count + s, 1);
-                  if (qi < L::rq_cap) {
-                    rq[qi] = (unsigned(g * MAXM + t) << 16) | (unsigned(c) << 5) | unsigned(u);
-                  } else {
-                    ++n_rechecks;
-                    // the binary64 decision is monotone in alpha: kept here means kept
-                    // at every larger alpha, removed here means removed at every
-                    // smaller one, so ts for this column becomes u + 1
-                    if (!recheck_dominates_cold(a, ids, key, key64, t, c, a.Ad[u], ppt, E_rel, E_abs)) break;
-                    const unsigned long long bit = 1ull << (c & 63);
+          for (int w = 0; w < MW; ++w) {
+            while (und[w]) {
+              const int cb = __ffsll(static_cast<long long>(und[w])) - 1;
+              und[w] &= und[w] - 1;
+              const int c = 64 * w + cb;
+              int u0 = 0;
 #pragma unroll
-                    for (int b = 0; b < NB; ++b) {
-                      const unsigned long long m_b = (((u + 1) >> b) & 1) ? bit : 0ull;
-                      if (w == 0) pl[b][0] = (pl[b][0] & ~bit) | m_b;
-                      else pl[b][MW - 1] = (pl[b][MW - 1] & ~bit) | m_b;
-                    }
+              for (int b = 0; b < NB; ++b) u0 |= int((pl[b][w] >> cb) & 1ull) << b;
+              for (int u = u0; u < TA; ++u) {
+                // queued and resolved after this pass by all producer threads at
+                // once; decided here if the queue is full
+                const int qi = atomicAdd(rq_count + s, 1);
+                if (qi < L::rq_cap) {
+                  rq[qi] = (unsigned(g * MAXM + t) << 16) | (unsigned(c) << 5) | unsigned(u);
+                } else {
+                  ++n_rechecks;
+                  // the binary64 decision is monotone in alpha: kept here means kept
+                  // at every larger alpha, removed here means removed at every
+                  // smaller one, so ts for this column becomes u + 1
+                  if (!recheck_dominates_cold(a, ids, key, key64, t, c, a.Ad[u], ppt, E_rel, E_abs)) break;
+                  const unsigned long long bit = 1ull << cb;
+#pragma unroll
+                  for (int b = 0; b < NB; ++b) {
+                    const unsigned long long m_b = (((u + 1) >> b) & 1) ? bit : 0ull;
+                    pl[b][w] = (pl[b][w] & ~bit) | m_b;
                   }
                 }
               }
@@ -992,7 +1006,9 @@ __global__ void __launch_bounds__(160, tc_min_ctas<DT, MAXM, TB>()) prune_tc_ker
               if (al[w]) pos = 64 * w + __ffsll(static_cast<long long>(al[w])) - 1;
             if (pos < 0) break;
             out[kept++] = ids[pos];
-            al[pos >> 6] &= ~(1ull << (pos & 63));  // taken (its own mask bit is set too)
+            const unsigned long long pb = 1ull << (pos & 63);
+            if (MW == 1 || pos < 64) al[0] &= ~pb;  // taken (its own mask bit is set too)
+            else al[MW - 1] &= ~pb;
 #pragma unroll
             for (int q = 0; q < MW; ++q) al[q] &= ~masks[(mu * MAXM + pos) * MW + q];
           }
