@@ -152,6 +152,31 @@ rp_status rp_tune_batch(rp_ctx *ctx, rp_graph src, const double *alphas, const i
                         int32_t T, int32_t variant, rp_graph *outs);
 
 /*
+ * rp_tune_batch_async: rp_tune_batch on a stream of the lowest priority, the
+ * prune cut into `chunks` launches over node ranges, so that work the context
+ * runs meanwhile on its own stream (searches, which the context gives the
+ * highest priority when it creates that stream) takes the GPU between them.
+ * The graphs in outs[0..T) exist at once but must not be used (searched,
+ * exported, tuned from or freed) until rp_tune_wait(ticket) has returned
+ * RP_OK.  One job runs at a time: a call waits for the previous job to
+ * finish.  Results equal rp_tune_batch's.  The paper has no counterpart; this
+ * is the serving layer's way to keep searches running during a prune.
+ *   chunks in [1, 4096]; *ticket receives the job's ticket (1, 2, ...).
+ * Errors: as rp_tune_batch, and RP_EINVAL for a bad chunk count.
+ */
+rp_status rp_tune_batch_async(rp_ctx *ctx, rp_graph src, const double *alphas, const int32_t *Rs,
+                              int32_t T, int32_t variant, int32_t chunks, rp_graph *outs,
+                              int64_t *ticket);
+
+/*
+ * rp_tune_wait: wait up to timeout_ms (0 = do not wait) for tuning job
+ * `ticket`.  RP_OK once its graphs are in place, RP_ETIMEOUT if not yet,
+ * RP_ENOTFOUND for an unknown ticket, RP_EDEVICE if a kernel reported a
+ * problem, RP_EINVAL for timeout_ms < 0.
+ */
+rp_status rp_tune_wait(rp_ctx *ctx, int64_t ticket, int32_t timeout_ms);
+
+/*
  * rp_graph_info: n, number of edges, largest out-degree and start vertex of
  * a graph (waits for the graph to be complete).  Any output pointer may be
  * NULL.  Errors: RP_ENOTFOUND, RP_ECUDA.
@@ -463,9 +488,14 @@ rp_status rp_set_search_config(rp_ctx *ctx, int32_t cache_bits, int32_t ctas_per
  * graphs that none of its requests address until the new ones fit, tunes all
  * missing graphs in batched launches (up to 16 targets each), and runs the
  * remaining searches in one mixed launch per k.  Results depend only on each
- * request, never on the mix.  With `serial` set the
- * scheduler is the plain path instead: one request per round, one target per
- * tuning launch.
+ * request, never on the mix.  With an executor that tunes asynchronously
+ * (rp_server_create's does), a round does not wait for its tuning: requests
+ * on graphs being tuned are parked, rounds keep admitting arrivals and
+ * running searches on resident graphs while the job runs (on the device the
+ * searches take the SMs between the job's chunks), and the parked requests
+ * run once their graphs are in; the next job starts when one finishes.  With
+ * `serial` set the scheduler is the plain path instead: one request per
+ * round, one target per tuning launch, each waited for.
  * ---------------------------------------------------------------------- */
 typedef struct rp_server rp_server;
 
@@ -483,6 +513,15 @@ typedef struct {
                             const int32_t *q_graph, const int32_t *q_L, const void *queries,
                             int64_t nq, int32_t k, int32_t *ids, float *dists);
   rp_status (*graph_free)(void *user, rp_graph g);
+  /* Optional (NULL: the scheduler tunes with tune_batch and waits).  tune_start
+   * begins what tune_batch does without waiting, returning a ticket; the
+   * graphs in outs may be used once tune_ready(ticket) returns RP_OK
+   * (RP_ETIMEOUT while the job runs, another code if it failed).  With both,
+   * a non-serial server keeps searching resident graphs while a tuning job
+   * runs (~ rp_tune_batch_async / rp_tune_wait). */
+  rp_status (*tune_start)(void *user, rp_graph src, const double *alphas, const int32_t *Rs,
+                          int32_t T, rp_graph *outs, int64_t *ticket);
+  rp_status (*tune_ready)(void *user, int64_t ticket, int32_t timeout_ms);
 } rp_executor;
 
 typedef struct {

@@ -68,11 +68,15 @@ SEARCH_FN = ctypes.CFUNCTYPE(ctypes.c_int32, ctypes.c_void_p, ctypes.POINTER(cty
                              ctypes.c_int64, ctypes.c_int32, ctypes.POINTER(ctypes.c_int32),
                              ctypes.POINTER(ctypes.c_float))
 FREE_FN = ctypes.CFUNCTYPE(ctypes.c_int32, ctypes.c_void_p, ctypes.c_int64)
+TUNE_START_FN = ctypes.CFUNCTYPE(ctypes.c_int32, ctypes.c_void_p, ctypes.c_int64, ctypes.POINTER(ctypes.c_double),
+                                 ctypes.POINTER(ctypes.c_int32), ctypes.c_int32, ctypes.POINTER(ctypes.c_int64),
+                                 ctypes.POINTER(ctypes.c_int64))
+TUNE_READY_FN = ctypes.CFUNCTYPE(ctypes.c_int32, ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32)
 
 
 class rp_executor(ctypes.Structure):
     _fields_ = [("user", ctypes.c_void_p), ("tune_batch", TUNE_FN), ("search_multi", SEARCH_FN),
-                ("graph_free", FREE_FN)]
+                ("graph_free", FREE_FN), ("tune_start", TUNE_START_FN), ("tune_ready", TUNE_READY_FN)]
 
 
 class rp_server_config(ctypes.Structure):
@@ -100,6 +104,8 @@ def load_library(path: str = LIB_PATH):
         "rp_load_graph": [P, P, i32, i64, i32, P, P, i32, i32, ctypes.POINTER(i64)],
         "rp_tune": [P, i64, dbl, i32, i32, ctypes.POINTER(i64)],
         "rp_tune_batch": [P, i64, P, P, i32, i32, P],
+        "rp_tune_batch_async": [P, i64, P, P, i32, i32, i32, P, ctypes.POINTER(i64)],
+        "rp_tune_wait": [P, i64, i32],
         "rp_graph_info": [P, i64, ctypes.POINTER(i64), ctypes.POINTER(i64), ctypes.POINTER(i32), ctypes.POINTER(i64)],
         "rp_graph_export": [P, i64, P, P, i64, i32],
         "rp_search": [P, i64, P, i64, i32, i32, P, P, i32],
@@ -229,6 +235,28 @@ def rp_tune_batch(ctx, src: int, alphas, Rs, variant: int = RP_SORTED):
     outs = (ctypes.c_int64 * T)()
     _check(ctx, load_library().rp_tune_batch(ctx, int(src), a, r, T, int(variant), outs))
     return list(outs)
+
+
+def rp_tune_batch_async(ctx, src: int, alphas, Rs, chunks: int = 16, variant: int = RP_SORTED):
+    """rp_tune_batch on the low-priority stream in `chunks` launches; returns (graphs, ticket).
+    The graphs may be used once rp_tune_wait(ctx, ticket) returns True."""
+    T = len(alphas)
+    a = (ctypes.c_double * T)(*[float(x) for x in alphas])
+    r = (ctypes.c_int32 * T)(*[int(x) for x in Rs])
+    outs = (ctypes.c_int64 * T)()
+    ticket = ctypes.c_int64()
+    _check(ctx, load_library().rp_tune_batch_async(ctx, int(src), a, r, T, int(variant), int(chunks), outs,
+                                                   ctypes.byref(ticket)))
+    return list(outs), ticket.value
+
+
+def rp_tune_wait(ctx, ticket: int, timeout_ms: int = 0) -> bool:
+    """True once tuning job `ticket` is finished, False if still running after timeout_ms."""
+    rc = load_library().rp_tune_wait(ctx, int(ticket), int(timeout_ms))
+    if rc == RP_ETIMEOUT:
+        return False
+    _check(ctx, rc)
+    return True
 
 
 def rp_graph_info(ctx, g: int):
@@ -485,9 +513,13 @@ def rp_server_create(ctx, base: int, graph_budget_bytes: int = 0, max_batch_quer
 
 
 def rp_server_create_ex(tune_batch, search_multi, graph_free, base: int, d: int, dtype: int, graph_bytes: int,
-                        graph_budget_bytes: int = 0, max_batch_queries: int = 0, serial: bool = False):
-    """A server over Python callables with the rp_executor signatures (raw ctypes arguments)."""
-    ex = rp_executor(None, TUNE_FN(tune_batch), SEARCH_FN(search_multi), FREE_FN(graph_free))
+                        graph_budget_bytes: int = 0, max_batch_queries: int = 0, serial: bool = False,
+                        tune_start=None, tune_ready=None):
+    """A server over Python callables with the rp_executor signatures (raw ctypes arguments);
+    tune_start/tune_ready are the optional asynchronous tuning pair."""
+    ex = rp_executor(None, TUNE_FN(tune_batch), SEARCH_FN(search_multi), FREE_FN(graph_free),
+                     TUNE_START_FN(tune_start) if tune_start else TUNE_START_FN(),
+                     TUNE_READY_FN(tune_ready) if tune_ready else TUNE_READY_FN())
     cfg = rp_server_config(int(base), int(d), int(dtype), int(graph_bytes), int(graph_budget_bytes),
                            int(max_batch_queries), int(bool(serial)))
     out = ctypes.c_void_p()

@@ -2,6 +2,7 @@
 // budget, stream-ordered allocation and CUDA-graph replay of batched tuning.
 // The public contract of every function is documented in include/rp.h.
 #include <algorithm>
+#include <chrono>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -10,6 +11,7 @@
 #include <memory>
 #include <mutex>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "internal.h"
@@ -58,6 +60,7 @@ struct Graph {
   size_t bytes = 0;
   size_t bucket_bytes = 0;
   int64_t bucket0 = -1;  // nodes of degree <= 64, read back for the autotuner
+  int64_t bucket_cnt[3] = {-1, -1, -1};  // every bucket's size, read back for chunked tuning
   std::vector<TuneChoice> choices;
 };
 
@@ -109,6 +112,20 @@ struct rp_ctx {
   int search_cache_bits = 0, search_ctas = 0;  // rp_set_search_config
   int last_knn_method = 0;
   int32_t* trial_count = nullptr;  // device int[4]: bucket sizes of a trial launch
+  // asynchronous tuning (rp_tune_batch_async): a lowest-priority stream that
+  // runs one job at a time in node-range chunks, with scratch of its own
+  cudaStream_t tune_stream = nullptr;
+  cudaEvent_t tune_ready = nullptr;   // the outputs of the job in flight are in place
+  cudaEvent_t tune_inputs = nullptr;  // its allocations on the ctx stream are done
+  int64_t tune_ticket = 0;            // last job started (tickets count from 1)
+  int32_t* a_col = nullptr;
+  int64_t a_col_elems = 0;
+  int32_t* a_cnt = nullptr;
+  int64_t a_cnt_elems = 0;
+  int64_t* a_bsum = nullptr;
+  int64_t a_bsum_elems = 0;
+  int32_t* a_chunk = nullptr;  // per chunk: 3 bucket counts, then 4 work counters
+  int64_t a_chunk_elems = 0;
   int64_t graph_replays = 0;
   int64_t kernel_launches = 0;
   // phase timing: 0/1 prune, 1/2 emit, 3/4 search
@@ -497,6 +514,145 @@ rp_status tune_impl(rp_ctx* c, rp_graph src, const double* alphas, const int32_t
     return s;
   }
   for (int t = 0; t < T; ++t) outs[t] = add_graph(c, G[t]);
+  return RP_OK;
+}
+
+// Asynchronous tuning: the pipeline of enqueue_tune on the ctx's lowest-
+// priority stream, each bucket's nodes cut into `chunks` launches so that work
+// on the ctx stream (searches) gets the SMs between them.  Outputs are
+// allocated on the ctx stream before any chunk runs; they may be used once
+// tune_ready has completed (rp_tune_wait).  One job at a time: a new one waits
+// for the previous to finish.
+rp_status tune_async_impl(rp_ctx* c, rp_graph src, const double* alphas, const int32_t* Rs, int32_t T,
+                          int32_t variant, int32_t chunks, rp_graph* outs, int64_t* ticket) {
+  if (!outs || !alphas || !Rs || !ticket) return fail(c, RP_EINVAL, "null argument");
+  if (T < 1 || T > kMaxTargets) return fail(c, RP_EINVAL, "T=%d outside [1, %d]", T, kMaxTargets);
+  if (variant != RP_SORTED && variant != RP_UNSORTED) return fail(c, RP_EINVAL, "bad variant %d", variant);
+  if (chunks < 1 || chunks > 4096) return fail(c, RP_EINVAL, "chunks=%d outside [1, 4096]", chunks);
+  Graph* S = find_graph(c, src);
+  if (!S) return fail(c, RP_ENOTFOUND, "unknown graph %lld", (long long)src);
+  int32_t A[kMaxTargets], R[kMaxTargets];
+  for (int t = 0; t < T; ++t) {
+    if (!alpha_to_milli(alphas[t], &A[t]))
+      return fail(c, RP_EINVAL, "alpha=%.17g must lie in [1, 100] on the 0.001 grid", alphas[t]);
+    if (Rs[t] < 1) return fail(c, RP_EINVAL, "R=%d must be >= 1", Rs[t]);
+    R[t] = Rs[t];
+  }
+  if (!c->tune_stream) {
+    int least = 0, greatest = 0;
+    CUDA_TRY(c, cudaDeviceGetStreamPriorityRange(&least, &greatest));
+    CUDA_TRY(c, cudaStreamCreateWithPriority(&c->tune_stream, cudaStreamNonBlocking, least));
+    CUDA_TRY(c, cudaEventCreateWithFlags(&c->tune_ready, cudaEventDisableTiming));
+    CUDA_TRY(c, cudaEventCreateWithFlags(&c->tune_inputs, cudaEventDisableTiming));
+  }
+  CUDA_TRY(c, cudaStreamSynchronize(c->tune_stream));  // the previous job is finished with the scratch
+  rp_status s = ensure_buckets(c, S);
+  if (s != RP_OK) return s;
+  if (S->bucket_cnt[0] < 0) {
+    int32_t cnt[3] = {0, 0, 0};
+    CUDA_TRY(c, cudaMemcpyAsync(cnt, S->buckets + 3 * S->n, sizeof cnt, cudaMemcpyDeviceToHost, c->stream));
+    CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    for (int b = 0; b < 3; ++b) S->bucket_cnt[b] = cnt[b];
+  }
+  const int64_t cap = std::max<int64_t>(S->col_cap, 1);
+  if ((s = grow(c, &c->a_col, &c->a_col_elems, cap * T)) != RP_OK) return s;
+  if ((s = grow(c, &c->a_cnt, &c->a_cnt_elems, S->n * T)) != RP_OK) return s;
+  if ((s = grow(c, &c->a_bsum, &c->a_bsum_elems, emit_csr_blocks(S->n) * T)) != RP_OK) return s;
+  // the launches: every bucket cut into `chunks` contiguous ranges of its node list
+  std::vector<int32_t> host;  // per launch: 3 counts (only its bucket's nonzero), 4 work counters
+  std::vector<std::pair<int, int64_t>> launches;  // (bucket, first list entry)
+  for (int b = 0; b < 3; ++b) {
+    const int64_t nb = S->bucket_cnt[b];
+    if (nb <= 0) continue;
+    const int64_t per = (nb + chunks - 1) / chunks;
+    for (int64_t lo = 0; lo < nb; lo += per) {
+      const int64_t hi = std::min(nb, lo + per);
+      launches.emplace_back(b, lo);
+      for (int q = 0; q < 3; ++q) host.push_back(q == b ? int32_t(hi - lo) : 0);
+      for (int q = 0; q < 4; ++q) host.push_back(0);
+    }
+  }
+  if ((s = grow(c, &c->a_chunk, &c->a_chunk_elems, std::max<int64_t>(int64_t(host.size()), 7))) != RP_OK) return s;
+  if (!host.empty())
+    CUDA_TRY(c, cudaMemcpyAsync(c->a_chunk, host.data(), host.size() * 4, cudaMemcpyHostToDevice, c->stream));
+  int tile0 = 0, ctas = 0;  // a configuration chosen earlier for this source, else the default
+  const int tclass = T <= 1 ? 1 : T <= 2 ? 2 : T <= 4 ? 4 : T <= 8 ? 8 : 16;
+  if (c->tuning_mode == RP_TUNING_FIXED) {
+    tile0 = c->fixed_tile0;
+    ctas = c->fixed_ctas;
+  } else {
+    for (const TuneChoice& ch : S->choices)
+      if (ch.tclass == tclass && ch.variant == variant) {
+        tile0 = ch.tile0;
+        ctas = ch.ctas;
+      }
+  }
+  Graph* G[kMaxTargets] = {};
+  for (int t = 0; t < T; ++t) {
+    G[t] = new Graph;
+    G[t]->data = S->data;
+    G[t]->n = S->n;
+    G[t]->col_cap = S->col_cap;
+    G[t]->start = S->start;
+    G[t]->max_deg_bound = std::min(S->max_deg_bound, R[t]);
+    G[t]->bytes = size_t(S->n + 1) * 8 + size_t(cap) * 4;
+    s = dalloc(c, reinterpret_cast<void**>(&G[t]->row_ptr), size_t(S->n + 1) * 8);
+    if (s == RP_OK) s = dalloc(c, reinterpret_cast<void**>(&G[t]->col), size_t(cap) * 4);
+    if (s != RP_OK) {
+      for (int u = 0; u <= t; ++u) free_graph_mem(c, G[u]);
+      return s;
+    }
+  }
+  // the tuning stream starts once the ctx stream has made the allocations and copies
+  CUDA_TRY(c, cudaEventRecord(c->tune_inputs, c->stream));
+  CUDA_TRY(c, cudaStreamWaitEvent(c->tune_stream, c->tune_inputs, 0));
+  PruneLaunch L;
+  L.tile0 = tile0;
+  L.ctas_per_sm = ctas;
+  L.data = S->data->dev();
+  L.row_ptr = S->row_ptr;
+  L.col = S->col;
+  L.host_max_degree = S->max_deg_bound;
+  L.T = T;
+  L.variant = variant;
+  L.status = c->status;
+  L.num_sms = c->num_sms;
+  int32_t* scr[kMaxTargets];
+  int32_t* cnt[kMaxTargets];
+  int32_t* dst_col[kMaxTargets];
+  int64_t* dst_rp[kMaxTargets];
+  for (int t = 0; t < T; ++t) {
+    L.A[t] = A[t];
+    L.R[t] = R[t];
+    scr[t] = c->a_col + int64_t(t) * cap;
+    cnt[t] = c->a_cnt + int64_t(t) * S->n;
+    L.out_col[t] = scr[t];
+    L.out_cnt[t] = cnt[t];
+    dst_col[t] = G[t]->col;
+    dst_rp[t] = G[t]->row_ptr;
+  }
+  cudaError_t ce = cudaSuccess;
+  for (size_t i = 0; i < launches.size() && ce == cudaSuccess; ++i) {
+    const int b = launches[i].first;
+    int32_t* blk = c->a_chunk + 7 * int64_t(i);
+    for (int q = 0; q < 3; ++q) {
+      L.bucket_nodes[q] = S->buckets + int64_t(q) * S->n + (q == b ? launches[i].second : 0);
+      L.host_bucket_count[q] = q == b ? host[7 * i + size_t(q)] : 0;
+    }
+    L.bucket_count = blk;
+    L.work = reinterpret_cast<unsigned int*>(blk + 3) - b;  // launch_prune adds the bucket index
+    ce = launch_prune(L, c->tune_stream);
+  }
+  if (ce == cudaSuccess) ce = launch_emit_csr(S->n, T, S->row_ptr, scr, cnt, dst_rp, dst_col, c->a_bsum, c->tune_stream);
+  if (ce == cudaSuccess) ce = cudaEventRecord(c->tune_ready, c->tune_stream);
+  if (ce != cudaSuccess) {
+    cudaStreamSynchronize(c->tune_stream);
+    for (int t = 0; t < T; ++t) free_graph_mem(c, G[t]);
+    return fail(c, RP_ECUDA, "asynchronous tuning: %s", cudaGetErrorString(ce));
+  }
+  c->kernel_launches += int64_t(launches.size()) + 3;
+  for (int t = 0; t < T; ++t) outs[t] = add_graph(c, G[t]);
+  *ticket = ++c->tune_ticket;
   return RP_OK;
 }
 
@@ -1015,7 +1171,10 @@ rp_status rp_create(rp_ctx** out, int32_t device, uint64_t hbm_budget_bytes, voi
   if (cuda_stream) {
     c->stream = static_cast<cudaStream_t>(cuda_stream);
   } else {
-    if (cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking) != cudaSuccess) return RP_ECUDA;
+    // searches on this stream run ahead of asynchronous tuning (lowest priority)
+    int least = 0, greatest = 0;
+    if (cudaDeviceGetStreamPriorityRange(&least, &greatest) != cudaSuccess) return RP_ECUDA;
+    if (cudaStreamCreateWithPriority(&c->stream, cudaStreamNonBlocking, greatest) != cudaSuccess) return RP_ECUDA;
     c->own_stream = true;
   }
   cudaMemPool_t pool;
@@ -1056,7 +1215,15 @@ rp_status rp_destroy(rp_ctx* c) {
     dfree(c, c->work, 32);
     dfree(c, c->hits, 8);
     if (c->trial_count) dfree(c, c->trial_count, 16);
+    if (c->tune_stream) cudaStreamSynchronize(c->tune_stream);
+    dfree(c, c->a_col, size_t(c->a_col_elems) * 4);
+    dfree(c, c->a_cnt, size_t(c->a_cnt_elems) * 4);
+    dfree(c, c->a_bsum, size_t(c->a_bsum_elems) * 8);
+    dfree(c, c->a_chunk, size_t(c->a_chunk_elems) * 4);
     cudaStreamSynchronize(c->stream);
+    if (c->tune_ready) cudaEventDestroy(c->tune_ready);
+    if (c->tune_inputs) cudaEventDestroy(c->tune_inputs);
+    if (c->tune_stream) cudaStreamDestroy(c->tune_stream);
     for (auto& e : c->ev)
       if (e) cudaEventDestroy(e);
     if (c->own_stream) cudaStreamDestroy(c->stream);
@@ -1258,6 +1425,34 @@ rp_status rp_tune_batch(rp_ctx* c, rp_graph src, const double* alphas, const int
   std::lock_guard<std::mutex> lk(c->mu);
   cudaSetDevice(c->device);
   return tune_impl(c, src, alphas, Rs, T, variant, outs, true);
+}
+
+rp_status rp_tune_batch_async(rp_ctx* c, rp_graph src, const double* alphas, const int32_t* Rs, int32_t T,
+                              int32_t variant, int32_t chunks, rp_graph* outs, int64_t* ticket) {
+  if (!c) return RP_EINVAL;
+  std::lock_guard<std::mutex> lk(c->mu);
+  cudaSetDevice(c->device);
+  return tune_async_impl(c, src, alphas, Rs, T, variant, chunks, outs, ticket);
+}
+
+rp_status rp_tune_wait(rp_ctx* c, int64_t ticket, int32_t timeout_ms) {
+  if (!c) return RP_EINVAL;
+  if (timeout_ms < 0) return fail(c, RP_EINVAL, "timeout_ms=%d", timeout_ms);
+  const auto t_end = std::chrono::steady_clock::now() + std::chrono::milliseconds(timeout_ms);
+  for (;;) {
+    {
+      std::lock_guard<std::mutex> lk(c->mu);
+      cudaSetDevice(c->device);
+      if (ticket < 1 || ticket > c->tune_ticket) return fail(c, RP_ENOTFOUND, "unknown tuning ticket %lld", (long long)ticket);
+      // jobs run one after another, so an earlier ticket is done once the latest is
+      const cudaError_t e = cudaEventQuery(c->tune_ready);
+      if (e == cudaSuccess) return check_device_status(c);
+      if (e != cudaErrorNotReady) return fail(c, RP_ECUDA, "tuning: %s", cudaGetErrorString(e));
+      if (ticket < c->tune_ticket) return RP_OK;  // a later job was started, so this one finished before it
+    }
+    if (std::chrono::steady_clock::now() >= t_end) return RP_ETIMEOUT;
+    std::this_thread::sleep_for(std::chrono::microseconds(100));
+  }
 }
 
 rp_status rp_graph_info(rp_ctx* c, rp_graph g, int64_t* n, int64_t* nnz, int32_t* max_deg, int64_t* start) {

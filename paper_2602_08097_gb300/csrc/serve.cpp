@@ -78,6 +78,23 @@ rp_status ctx_search(void* u, const rp_graph* g, int32_t ng, const int32_t* qg, 
 
 rp_status ctx_free(void* u, rp_graph g) { return rp_graph_free(static_cast<CtxExec*>(u)->ctx, g); }
 
+// Asynchronous tuning over the ctx: chunks of about 256K nodes, so that a
+// search waits at most for one chunk.
+rp_status ctx_tune_start(void* u, rp_graph src, const double* a, const int32_t* R, int32_t T, rp_graph* outs,
+                         int64_t* ticket) {
+  rp_ctx* ctx = static_cast<CtxExec*>(u)->ctx;
+  int64_t n = 0, nnz = 0, start = 0;
+  int32_t md = 0;
+  rp_status st = rp_graph_info(ctx, src, &n, &nnz, &md, &start);
+  if (st != RP_OK) return st;
+  const int32_t chunks = int32_t(std::min<int64_t>(64, std::max<int64_t>(1, n / 262144)));
+  return rp_tune_batch_async(ctx, src, a, R, T, RP_SORTED, chunks, outs, ticket);
+}
+
+rp_status ctx_tune_ready(void* u, int64_t ticket, int32_t timeout_ms) {
+  return rp_tune_wait(static_cast<CtxExec*>(u)->ctx, ticket, timeout_ms);
+}
+
 }  // namespace
 
 struct rp_server {
@@ -98,6 +115,13 @@ struct rp_server {
   std::string err;
 
   // scheduler-thread state
+  struct Inflight {
+    bool active = false;
+    int64_t ticket = 0;
+    std::vector<Key> keys;
+    std::vector<rp_graph> outs;
+  } inflight;                 // the asynchronous tuning job running now
+  std::vector<Req*> parked;   // admitted requests waiting for a graph being tuned (or to be)
   std::list<std::pair<Key, rp_graph>> lru;  // front = least recently used
   std::map<Key, std::list<std::pair<Key, rp_graph>>::iterator> resident;
   std::vector<uint8_t> qbuf;
@@ -117,6 +141,7 @@ struct rp_server {
 
   void run();
   void round(std::vector<Req*>& batch, int32_t round_no);
+  void round_async(std::vector<Req*>& batch, int32_t* round_no);
   void run_searches(std::vector<Req*>& rs);
   void publish(std::vector<Req*>& rs);
   void evict_for(size_t nnew, const std::map<Key, int>& needed);
@@ -303,14 +328,131 @@ void rp_server::round(std::vector<Req*>& batch, int32_t round_no) {
   stats.busy_ns += now_ns(t0) - t_start;
 }
 
+// One step of the scheduler with an asynchronous executor: take in the tuning
+// job that finished, admit the new batch, run every request whose graph is
+// resident, and start the next tuning job for the parked requests.
+void rp_server::round_async(std::vector<Req*>& batch, int32_t* round_no) {
+  const int64_t t_start = now_ns(t0);
+  bool worked = false;
+  std::map<Key, rp_status> failed;
+  if (inflight.active) {
+    const rp_status st = ex.tune_ready(ex.user, inflight.ticket, 0);
+    if (st != RP_ETIMEOUT) {
+      worked = true;
+      for (size_t t = 0; t < inflight.keys.size(); ++t) {
+        if (st == RP_OK) {
+          lru.emplace_back(inflight.keys[t], inflight.outs[t]);
+          resident[inflight.keys[t]] = std::prev(lru.end());
+        } else {
+          failed[inflight.keys[t]] = st;
+          ex.graph_free(ex.user, inflight.outs[t]);
+        }
+      }
+      if (st != RP_OK) set_error("tuning %zu target(s) from the base failed with status %d", inflight.keys.size(), st);
+      std::lock_guard<std::mutex> lk(mu);
+      if (st == RP_OK) stats.targets_tuned += int64_t(inflight.keys.size());
+      stats.resident_graphs = int64_t(lru.size());
+      stats.peak_resident_graphs = std::max(stats.peak_resident_graphs, stats.resident_graphs);
+      inflight = Inflight{};
+    }
+  }
+  if (!batch.empty()) {
+    worked = true;
+    ++*round_no;
+    std::lock_guard<std::mutex> lk(mu);
+    for (Req* r : batch) {
+      r->status = RP_OK;
+      r->info.state = RP_REQ_RUNNING;
+      r->info.start_ns = t_start;
+      r->info.round = *round_no;
+    }
+  }
+  // mark use (most recent last) and split: ready now, or parked
+  for (Req* r : batch) {
+    auto it = resident.find(r->key);
+    if (it != resident.end()) lru.splice(lru.end(), lru, it->second);
+    parked.push_back(r);
+  }
+  std::vector<Req*> ready, still;
+  for (Req* r : parked) {
+    auto f = failed.find(r->key);
+    if (f != failed.end()) {
+      r->status = f->second;
+      r->graph = 0;
+      ready.push_back(r);
+    } else if (r->key.first == 0 || resident.count(r->key)) {
+      ready.push_back(r);
+    } else {
+      still.push_back(r);
+    }
+  }
+  parked.swap(still);
+  if (!ready.empty()) {
+    run_searches(ready);
+    publish(ready);
+  }
+  // the next tuning job: the graphs the parked requests need, in order of first use
+  if (!inflight.active && !parked.empty()) {
+    worked = true;
+    std::map<Key, int> needed;
+    std::vector<Key> missing;
+    for (Req* r : parked)
+      if (needed.emplace(r->key, int(needed.size())).second && missing.size() < size_t(kMaxTargets))
+        missing.push_back(r->key);
+    evict_for(missing.size(), needed);
+    double alphas[kMaxTargets];
+    int32_t Rs[kMaxTargets];
+    rp_graph outs[kMaxTargets] = {};
+    for (size_t t = 0; t < missing.size(); ++t) {
+      alphas[t] = missing[t].first / 1000.0;
+      Rs[t] = missing[t].second;
+    }
+    int64_t ticket = 0;
+    const rp_status st = ex.tune_start(ex.user, cfg.base, alphas, Rs, int32_t(missing.size()), outs, &ticket);
+    {
+      std::lock_guard<std::mutex> lk(mu);
+      stats.tune_launches += 1;
+    }
+    if (st == RP_OK) {
+      inflight.active = true;
+      inflight.ticket = ticket;
+      inflight.keys = missing;
+      inflight.outs.assign(outs, outs + missing.size());
+    } else {
+      set_error("starting to tune %zu target(s) from the base failed with status %d", missing.size(), st);
+      std::vector<Req*> bad, keep;
+      std::map<Key, int> mk;
+      for (const Key& k : missing) mk[k] = 0;
+      for (Req* r : parked) (mk.count(r->key) ? bad : keep).push_back(r);
+      for (Req* r : bad) {
+        r->status = st;
+        r->graph = 0;
+      }
+      parked.swap(keep);
+      publish(bad);
+    }
+  }
+  if (worked) {
+    std::lock_guard<std::mutex> lk(mu);
+    if (!batch.empty()) stats.rounds += 1;
+    stats.busy_ns += now_ns(t0) - t_start;
+  }
+}
+
 void rp_server::run() {
   int32_t round_no = 0;
+  const bool async = ex.tune_start && ex.tune_ready && !cfg.serial;
   for (;;) {
     std::vector<Req*> batch;
     {
       std::unique_lock<std::mutex> lk(mu);
-      cv_work.wait(lk, [&] { return stop || !queue.empty(); });
-      if (queue.empty()) break;  // stopping and drained
+      if (async && (inflight.active || !parked.empty())) {
+        // a tuning job runs: look at it again soon even if nothing arrives
+        cv_work.wait_for(lk, std::chrono::microseconds(200), [&] { return !queue.empty(); });
+      } else {
+        cv_work.wait(lk, [&] { return stop || !queue.empty(); });
+        if (queue.empty()) break;  // stopping and drained
+      }
       // admission in arrival order
       std::map<Key, int> keys;
       int64_t qsum = 0;
@@ -328,7 +470,11 @@ void rp_server::run() {
         queue.pop_front();
       }
     }
-    round(batch, ++round_no);
+    if (async) {
+      round_async(batch, &round_no);
+    } else {
+      round(batch, ++round_no);
+    }
   }
 }
 
@@ -403,6 +549,8 @@ rp_status rp_server_create(rp_ctx* ctx, rp_graph base, uint64_t graph_budget_byt
   s->ex.tune_batch = ctx_tune;
   s->ex.search_multi = ctx_search;
   s->ex.graph_free = ctx_free;
+  s->ex.tune_start = ctx_tune_start;
+  s->ex.tune_ready = ctx_tune_ready;
   s->cfg = cfg;
   return start_server(s, out);
 }

@@ -122,3 +122,26 @@ def test_server_searches_the_base(ctx, world):
     assert info["status"] == rp.RP_OK and info["graph"] == base
     ref_i, _, _ = oracle.greedy_search(X, brp, bcol, start, Q[:16], 64, 10)
     assert np.array_equal(ids, ref_i)
+
+
+@pytest.mark.parametrize("chunks", [1, 3, 17])
+def test_async_tuning_equals_batched_tuning(ctx, world, chunks):
+    """rp_tune_batch_async (lowest-priority stream, the prune cut into node-range
+    chunks) gives rp_tune_batch's graphs edge for edge; searches launched on
+    the context's stream while it runs return the oracle's lists."""
+    name, X, (brp, bcol), base, Q, start = world
+    al, Rs = [a for a, _ in TARGETS], [r for _, r in TARGETS]
+    ref = rp.rp_tune_batch(ctx, base, al, Rs)
+    outs, ticket = rp.rp_tune_batch_async(ctx, base, al, Rs, chunks=chunks)
+    ids, _ = rp.rp_search(ctx, base, Q[:32], 40, 10)  # on the ctx stream, meanwhile
+    assert rp.rp_tune_wait(ctx, ticket, 60000)
+    ref_i, _, _ = oracle.greedy_search(X, brp, bcol, start, Q[:32], 40, 10)
+    assert np.array_equal(ids, ref_i)
+    for g, r in zip(outs, ref):
+        a_rp, a_col = rp.rp_graph_export(ctx, g)
+        r_rp, r_col = rp.rp_graph_export(ctx, r)
+        assert np.array_equal(a_rp, r_rp) and np.array_equal(a_col, r_col)
+        rp.rp_graph_free(ctx, g)
+        rp.rp_graph_free(ctx, r)
+    with pytest.raises(rp.RPError):
+        rp.rp_tune_wait(ctx, ticket + 5)

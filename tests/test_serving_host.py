@@ -346,3 +346,104 @@ def test_mixed_round_evicts_only_what_it_does_not_use(world):
             assert np.array_equal(r.ids, ids) and np.array_equal(r.dists, d2)
     finally:
         rp.rp_server_destroy(srv)
+
+
+class AsyncExec(OracleExec):
+    """rp_executor with the asynchronous tuning pair: tune_start computes at once
+    but a job counts as finished only after its gate is set, so the test holds
+    a job "on the device" while the scheduler goes on."""
+
+    def __init__(self, X, base, start, gates=(), fail_alpha_milli=None):
+        super().__init__(X, base, start, fail_alpha_milli=fail_alpha_milli)
+        self.gates = list(gates)
+        self.jobs = {}  # ticket -> (gate index, status)
+        self.started = threading.Event()
+
+    def tune_start(self, user, src, alphas, Rs, T, outs, ticket):
+        try:
+            st = self.tune(user, src, alphas, Rs, T, outs)
+            t = len(self.jobs) + 1
+            self.jobs[t] = (t - 1, st)
+            ticket[0] = t
+            self.started.set()
+            return rp.RP_OK if st == rp.RP_OK else st
+        except Exception:
+            return rp.RP_EINVAL
+
+    def tune_ready(self, user, ticket, timeout_ms):
+        gi, st = self.jobs[ticket]
+        if gi < len(self.gates) and not self.gates[gi].is_set():
+            return rp.RP_ETIMEOUT
+        return st
+
+    def server(self, budget_graphs=0, serial=False, max_batch=0):
+        gb = 1000
+        return rp.rp_server_create_ex(self.tune, self.search, self.free, self.BASE, D, rp.RP_F32, gb,
+                                      budget_graphs * gb, max_batch, serial, self.tune_start, self.tune_ready)
+
+
+def test_async_searches_run_while_a_tuning_job_runs(world):
+    """With an asynchronous executor a round does not wait for its tuning job:
+    a search on a resident graph that arrives while a job runs completes
+    before the job does; the requests on the graph being tuned complete after."""
+    X, base, start, Q = world
+    g1, g2 = threading.Event(), threading.Event()
+    ex = AsyncExec(X, base, start, gates=[g1, g2])
+    srv = ex.server()
+    try:
+        g1.set()  # the first job (1.15, 24) finishes at once
+        a = rp.rp_submit_search(srv, 1.15, 24, Q[0:3], 12, 10)
+        assert rp.rp_poll(srv, a[0], 20000)["status"] == rp.RP_OK
+        held = rp.rp_submit_search(srv, 1.1, 24, Q[3:6], 12, 10)  # job 2, held by g2
+        for _ in range(200):
+            if len(ex.jobs) >= 2:
+                break
+            threading.Event().wait(0.01)
+        assert len(ex.jobs) == 2
+        quick = [rp.rp_submit_search(srv, 1.15, 24, Q[6:8], 12, 10), rp.rp_submit_search(srv, 0.0, 0, Q[8:9], 12, 10)]
+        for rid, _, _ in quick:  # served while job 2 is still "running"
+            info = rp.rp_poll(srv, rid, 5000)
+            assert info is not None and info["status"] == rp.RP_OK
+        assert rp.rp_poll(srv, held[0], 50) is None
+        g2.set()
+        assert rp.rp_poll(srv, held[0], 20000)["status"] == rp.RP_OK
+        for (rid, ids, _), (al, R, rows) in zip([a, held] + quick, [(1.15, 24, slice(0, 3)), (1.1, 24, slice(3, 6)),
+                                                                  (1.15, 24, slice(6, 8)), (0, 0, slice(8, 9))]):
+            g = base if al == 0 else oracle.rp_tune(X, base[0], base[1], al, R)
+            ref, _, _ = oracle.greedy_search(X, g[0], g[1], start, Q[rows], 12, 10)
+            assert np.array_equal(ids, ref)
+        st = rp.rp_server_stats(srv)
+        assert st["tune_launches"] == 2 and st["targets_tuned"] == 2
+    finally:
+        g1.set()
+        g2.set()
+        rp.rp_server_destroy(srv)
+
+
+def test_async_mixed_stream_and_failures(world):
+    """The asynchronous path serves a mixed stream with every result equal to
+    the request's answer alone; a failing job fails only its own requests."""
+    from paper_2602_08097_gb300.serving import replay
+    X, base, start, Q = world
+    ex = AsyncExec(X, base, start)
+    srv = ex.server()
+    reqs = _stream(Q, n=30, seed=5)
+    try:
+        rep = replay(srv, reqs, time_scale=0.0)
+    finally:
+        rp.rp_server_destroy(srv)
+    for r in reqs:
+        if r.kind == "search":
+            ids, d2 = _expected(X, base, start, r)
+            assert np.array_equal(r.ids, ids) and np.array_equal(r.dists, d2)
+    assert rep["stats"]["requests_done"] == len(reqs) and rep["stats"]["requests_failed"] == 0
+    assert not ex.graphs.keys() - {OracleExec.BASE}
+    ex2 = AsyncExec(X, base, start, fail_alpha_milli=1050)
+    srv = ex2.server()
+    try:
+        ok = rp.rp_submit_search(srv, 1.1, 24, Q[:2], 10, 10)
+        assert rp.rp_poll(srv, ok[0], 20000)["status"] == rp.RP_OK
+        bad = rp.rp_submit_search(srv, 1.05, 24, Q[:2], 10, 10)
+        assert rp.rp_poll(srv, bad[0], 20000)["status"] == rp.RP_ENOMEM
+    finally:
+        rp.rp_server_destroy(srv)
