@@ -152,6 +152,20 @@ rp_status rp_tune_batch(rp_ctx *ctx, rp_graph src, const double *alphas, const i
                         int32_t T, int32_t variant, rp_graph *outs);
 
 /*
+ * rp_graph_attach: a graph over the vectors (and start vertex) of graph `data`
+ * from a CSR adjacency, cleaned as rp_load_graph cleans it (ids checked to lie
+ * in [0, n), self loops and repeated ids dropped), without uploading the
+ * vectors again.  A multi-GPU tuning assembles the node-range slices of the
+ * ranks into one graph this way (each rank then searches it).
+ *   row_ptr: int64[n + 1], col: int32[row_ptr[n]], host or device memory
+ *     (mem_flags), borrowed for the call.
+ * Errors: RP_ENOTFOUND, RP_EINVAL (a malformed CSR or an id out of range),
+ *   RP_ENOMEM, RP_ECUDA.
+ */
+rp_status rp_graph_attach(rp_ctx *ctx, rp_graph data, const int64_t *row_ptr, const int32_t *col,
+                          int32_t mem_flags, rp_graph *out);
+
+/*
  * rp_tune_batch_async: rp_tune_batch on a stream of the lowest priority, the
  * prune cut into `chunks` launches over node ranges, so that work the context
  * runs meanwhile on its own stream (searches, which the context gives the

@@ -697,8 +697,10 @@ int orc_d2_query(const void *X, int dtype, int d, const void *Q, int64_t nq,
  *     N'(p) = RobustPrune(p, V_p, alpha, R) (Algorithm 1, sorted; its first
  *             step takes the union with the current N_out(p) and drops p).
  *   Then every N_out(p) <- N'(p).  Then the back edges: for every j named in
- *   some N'(p), P_j = the batch points naming j, ascending by id; the merged
- *   list is N_out(j) followed by the members of P_j not already in it; if it
+ *   some N'(p), P_j = the batch points naming j, ascending by id, its first
+ *   4096 members (VAMANA_MAX_SENDERS: this bounds every candidate list a
+ *   hub point gets); the merged list is N_out(j) followed by the members of
+ *   P_j not already in it; if it
  *   holds at most R points it becomes N_out(j), otherwise
  *   N_out(j) <- RobustPrune(j, merged, alpha, R).
  * A pass inserts every point once; pass i uses alpha = A[i] / 1000 (the
@@ -799,6 +801,8 @@ static int back_edge_cmp(const void *a, const void *b) {
   return (x->p > y->p) - (x->p < y->p);
 }
 
+#define VAMANA_MAX_SENDERS 4096
+
 /* Batch sizes: 1, 2, 4, ... capped at max_batch; the last batch takes the rest. */
 static int64_t vamana_batch_size(int64_t k, int64_t max_batch) {
   int64_t b = 1;
@@ -862,7 +866,9 @@ int orc_vamana(const void *X, int dtype, int64_t n, int d, const int32_t *perm, 
         int64_t j = be[g0].j, m = 0;
         for (int32_t e = 0; e < deg[j]; e++) merged[m++] = nbr[j * R + e];
         int64_t have = m;
-        for (int64_t g = g0; g < g1; g++) {
+        /* at most VAMANA_MAX_SENDERS back edges per batch: the smallest sender ids */
+        int64_t gl = g1 - g0 > VAMANA_MAX_SENDERS ? g0 + VAMANA_MAX_SENDERS : g1;
+        for (int64_t g = g0; g < gl; g++) {
           int dup = 0;
           for (int64_t e = 0; e < have; e++)
             if (merged[e] == be[g].p) { dup = 1; break; }

@@ -105,6 +105,7 @@ def load_library(path: str = LIB_PATH):
         "rp_tune": [P, i64, dbl, i32, i32, ctypes.POINTER(i64)],
         "rp_tune_batch": [P, i64, P, P, i32, i32, P],
         "rp_tune_batch_async": [P, i64, P, P, i32, i32, i32, P, ctypes.POINTER(i64)],
+        "rp_graph_attach": [P, i64, P, P, i32, ctypes.POINTER(i64)],
         "rp_tune_wait": [P, i64, i32],
         "rp_graph_info": [P, i64, ctypes.POINTER(i64), ctypes.POINTER(i64), ctypes.POINTER(i32), ctypes.POINTER(i64)],
         "rp_graph_export": [P, i64, P, P, i64, i32],
@@ -235,6 +236,14 @@ def rp_tune_batch(ctx, src: int, alphas, Rs, variant: int = RP_SORTED):
     outs = (ctypes.c_int64 * T)()
     _check(ctx, load_library().rp_tune_batch(ctx, int(src), a, r, T, int(variant), outs))
     return list(outs)
+
+
+def rp_graph_attach(ctx, data: int, row_ptr, col) -> int:
+    """A graph over the vectors of ``data`` from a CSR (numpy arrays or CUDA tensors)."""
+    mem = _mem(row_ptr, col)
+    out = ctypes.c_int64()
+    _check(ctx, load_library().rp_graph_attach(ctx, int(data), _ptr(row_ptr), _ptr(col), mem, ctypes.byref(out)))
+    return out.value
 
 
 def rp_tune_batch_async(ctx, src: int, alphas, Rs, chunks: int = 16, variant: int = RP_SORTED):

@@ -1153,6 +1153,118 @@ rp_status build_vamana(rp_ctx* c, rp_graph data, const int32_t* perm, int32_t np
 
 }  // namespace
 
+// The CSR part of loading a graph over G->data (G->n rows): copy, validate
+// (ids in [0, n), row_ptr monotone), drop self loops and repeated ids, exact
+// degrees, and the start vertex (the medoid if start < 0).  On failure G keeps
+// whatever it allocated; the caller frees it.
+rp_status attach_csr(rp_ctx* c, Graph* G, const int64_t* row_ptr, const int32_t* col, int64_t start,
+                     int32_t mem_flags) {
+  const int64_t n = G->n;
+  const int d = G->data->d;
+  rp_status s = RP_OK;
+  int64_t nnz_in = 0;
+  if (row_ptr) {
+    if (mem_flags == RP_MEM_HOST) {
+      nnz_in = row_ptr[n];
+      if (row_ptr[0] != 0 || nnz_in < 0) return fail(c, RP_EINVAL, "row_ptr[0] must be 0 and row_ptr[n] >= 0");
+    } else {
+      int64_t ends[2];
+      cudaMemcpyAsync(&ends[0], row_ptr, 8, cudaMemcpyDeviceToHost, c->stream);
+      cudaMemcpyAsync(&ends[1], row_ptr + n, 8, cudaMemcpyDeviceToHost, c->stream);
+      if (cudaStreamSynchronize(c->stream) != cudaSuccess || ends[0] != 0 || ends[1] < 0)
+        return fail(c, RP_EINVAL, "row_ptr[0] must be 0 and row_ptr[n] >= 0");
+      nnz_in = ends[1];
+    }
+  }
+  // device copies of the input CSR
+  int64_t* rp_in = nullptr;
+  int32_t* col_in = nullptr;
+  int32_t* cnt = nullptr;
+  int64_t* bsum = nullptr;
+  int32_t* maxd = nullptr;
+  int64_t* med = nullptr;
+  double* mean = nullptr;
+  double* best = nullptr;
+  const int64_t nblk = (n + 4095) / 4096;
+  auto cleanup = [&]() {
+    dfree(c, rp_in, size_t(n + 1) * 8);
+    dfree(c, col_in, size_t(std::max<int64_t>(nnz_in, 1)) * 4);
+    dfree(c, cnt, size_t(n) * 4);
+    dfree(c, bsum, size_t(nblk) * 8);
+    dfree(c, maxd, 8);
+    dfree(c, med, 8);
+    dfree(c, mean, size_t(d) * 8);
+    dfree(c, best, size_t(2 * medoid_blocks(n)) * 8);
+  };
+  G->col_cap = std::max<int64_t>(nnz_in, 1);
+  s = dalloc(c, reinterpret_cast<void**>(&G->row_ptr), size_t(n + 1) * 8);
+  if (s == RP_OK) s = dalloc(c, reinterpret_cast<void**>(&G->col), size_t(G->col_cap) * 4);
+  if (s == RP_OK) s = dalloc(c, reinterpret_cast<void**>(&rp_in), size_t(n + 1) * 8);
+  if (s == RP_OK) s = dalloc(c, reinterpret_cast<void**>(&col_in), size_t(std::max<int64_t>(nnz_in, 1)) * 4);
+  if (s == RP_OK) s = dalloc(c, reinterpret_cast<void**>(&cnt), size_t(n) * 4);
+  if (s == RP_OK) s = dalloc(c, reinterpret_cast<void**>(&bsum), size_t(nblk) * 8);
+  if (s == RP_OK) s = dalloc(c, reinterpret_cast<void**>(&maxd), 8);
+  if (s == RP_OK) s = dalloc(c, reinterpret_cast<void**>(&med), 8);
+  if (s == RP_OK) s = dalloc(c, reinterpret_cast<void**>(&mean), size_t(d) * 8);
+  if (s == RP_OK) s = dalloc(c, reinterpret_cast<void**>(&best), size_t(2 * medoid_blocks(n)) * 8);
+  if (s != RP_OK) {
+    cleanup();
+    return s;
+  }
+  const cudaMemcpyKind kind = mem_flags == RP_MEM_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
+  cudaError_t ce = cudaSuccess;
+  if (row_ptr) {
+    ce = cudaMemcpyAsync(rp_in, row_ptr, size_t(n + 1) * 8, kind, c->stream);
+    if (ce == cudaSuccess && nnz_in > 0) ce = cudaMemcpyAsync(col_in, col, size_t(nnz_in) * 4, kind, c->stream);
+  } else {
+    ce = cudaMemsetAsync(rp_in, 0, size_t(n + 1) * 8, c->stream);
+  }
+  const unsigned long long zero2[2] = {0, 0};
+  if (ce == cudaSuccess) ce = cudaMemcpyAsync(c->dropped, zero2, 16, cudaMemcpyHostToDevice, c->stream);
+  if (ce == cudaSuccess) ce = launch_validate_csr(rp_in, col_in, n, nnz_in, c->status, c->stream);
+  if (ce == cudaSuccess) ce = cudaStreamSynchronize(c->stream);
+  if (ce != cudaSuccess) {
+    cleanup();
+    return fail(c, RP_ECUDA, "graph upload/validate: %s", cudaGetErrorString(ce));
+  }
+  if ((s = check_device_status(c)) != RP_OK) {
+    cleanup();
+    return fail(c, RP_EINVAL, "invalid input: %s", c->err.c_str());
+  }
+  ce = launch_clean_count(rp_in, col_in, n, cnt, c->dropped, c->stream);
+  if (ce == cudaSuccess) ce = launch_scan_counts(cnt, n, G->row_ptr, bsum, maxd, c->stream);
+  if (ce == cudaSuccess) ce = launch_clean_write(rp_in, col_in, n, G->row_ptr, G->col, c->stream);
+  if (ce == cudaSuccess && start < 0) ce = launch_medoid(G->data->dev(), mean, best, med, c->stream);
+  int64_t nnz = 0, medoid = start;
+  int32_t maxdeg = 0;
+  unsigned long long dropped[2] = {0, 0};
+  if (ce == cudaSuccess) ce = cudaMemcpyAsync(&nnz, G->row_ptr + n, 8, cudaMemcpyDeviceToHost, c->stream);
+  if (ce == cudaSuccess) ce = cudaMemcpyAsync(&maxdeg, maxd, 4, cudaMemcpyDeviceToHost, c->stream);
+  if (ce == cudaSuccess && start < 0) ce = cudaMemcpyAsync(&medoid, med, 8, cudaMemcpyDeviceToHost, c->stream);
+  if (ce == cudaSuccess) ce = cudaMemcpyAsync(dropped, c->dropped, 16, cudaMemcpyDeviceToHost, c->stream);
+  if (ce == cudaSuccess) ce = cudaStreamSynchronize(c->stream);
+  cleanup();
+  if (ce != cudaSuccess) return fail(c, RP_ECUDA, "graph cleaning: %s", cudaGetErrorString(ce));
+  if ((s = check_device_status(c)) != RP_OK) return s;
+  if (maxdeg > RP_MAX_DEGREE)
+    return fail(c, RP_EINVAL, "out-degree %d after cleaning exceeds RP_MAX_DEGREE=%d", maxdeg, RP_MAX_DEGREE);
+  G->nnz = nnz;
+  G->max_deg_bound = maxdeg;
+  G->start = medoid;
+  G->bytes = size_t(n + 1) * 8 + size_t(G->col_cap) * 4;
+  static_assert(sizeof(unsigned long long) == 8, "");
+  // stats carry the cleaning counters in the spare slots of the status word
+  unsigned long long add[2] = {dropped[0], dropped[1]};
+  DevStatus hs;
+  cudaMemcpyAsync(&hs, c->status, sizeof hs, cudaMemcpyDeviceToHost, c->stream);
+  cudaStreamSynchronize(c->stream);
+  hs.spare[0] += add[0];
+  hs.spare[1] += add[1];
+  cudaMemcpyAsync(c->status, &hs, sizeof hs, cudaMemcpyHostToDevice, c->stream);
+  cudaStreamSynchronize(c->stream);
+  return RP_OK;
+}
+
 extern "C" {
 
 rp_status rp_create(rp_ctx** out, int32_t device, uint64_t hbm_budget_bytes, void* cuda_stream) {
@@ -1292,123 +1404,33 @@ rp_status rp_load_graph(rp_ctx* c, const void* vectors, int32_t dtype, int64_t n
   Graph* G = new Graph;
   G->data = D;
   G->n = n;
-  int64_t nnz_in = 0;
-  if (row_ptr) {
-    if (mem_flags == RP_MEM_HOST) {
-      nnz_in = row_ptr[n];
-      if (row_ptr[0] != 0 || nnz_in < 0) {
-        delete G;
-        return fail_free(fail(c, RP_EINVAL, "row_ptr[0] must be 0 and row_ptr[n] >= 0"));
-      }
-    } else {
-      int64_t ends[2];
-      cudaMemcpyAsync(&ends[0], row_ptr, 8, cudaMemcpyDeviceToHost, c->stream);
-      cudaMemcpyAsync(&ends[1], row_ptr + n, 8, cudaMemcpyDeviceToHost, c->stream);
-      if (cudaStreamSynchronize(c->stream) != cudaSuccess || ends[0] != 0 || ends[1] < 0) {
-        delete G;
-        return fail_free(fail(c, RP_EINVAL, "row_ptr[0] must be 0 and row_ptr[n] >= 0"));
-      }
-      nnz_in = ends[1];
-    }
-  }
-  // device copies of the input CSR
-  int64_t* rp_in = nullptr;
-  int32_t* col_in = nullptr;
-  int32_t* cnt = nullptr;
-  int64_t* bsum = nullptr;
-  int32_t* maxd = nullptr;
-  int64_t* med = nullptr;
-  double* mean = nullptr;
-  double* best = nullptr;
-  const int64_t nblk = (n + 4095) / 4096;
-  auto cleanup = [&]() {
-    dfree(c, rp_in, size_t(n + 1) * 8);
-    dfree(c, col_in, size_t(std::max<int64_t>(nnz_in, 1)) * 4);
-    dfree(c, cnt, size_t(n) * 4);
-    dfree(c, bsum, size_t(nblk) * 8);
-    dfree(c, maxd, 8);
-    dfree(c, med, 8);
-    dfree(c, mean, size_t(d) * 8);
-    dfree(c, best, size_t(2 * medoid_blocks(n)) * 8);
-  };
-  G->col_cap = std::max<int64_t>(nnz_in, 1);
-  s = dalloc(c, reinterpret_cast<void**>(&G->row_ptr), size_t(n + 1) * 8);
-  if (s == RP_OK) s = dalloc(c, reinterpret_cast<void**>(&G->col), size_t(G->col_cap) * 4);
-  if (s == RP_OK) s = dalloc(c, reinterpret_cast<void**>(&rp_in), size_t(n + 1) * 8);
-  if (s == RP_OK) s = dalloc(c, reinterpret_cast<void**>(&col_in), size_t(std::max<int64_t>(nnz_in, 1)) * 4);
-  if (s == RP_OK) s = dalloc(c, reinterpret_cast<void**>(&cnt), size_t(n) * 4);
-  if (s == RP_OK) s = dalloc(c, reinterpret_cast<void**>(&bsum), size_t(nblk) * 8);
-  if (s == RP_OK) s = dalloc(c, reinterpret_cast<void**>(&maxd), 8);
-  if (s == RP_OK) s = dalloc(c, reinterpret_cast<void**>(&med), 8);
-  if (s == RP_OK) s = dalloc(c, reinterpret_cast<void**>(&mean), size_t(d) * 8);
-  if (s == RP_OK) s = dalloc(c, reinterpret_cast<void**>(&best), size_t(2 * medoid_blocks(n)) * 8);
-  if (s != RP_OK) {
-    cleanup();
+  D.reset();  // the graph owns the vectors now: freeing it on failure frees them
+  if ((s = attach_csr(c, G, row_ptr, col, start, mem_flags)) != RP_OK) {
     free_graph_mem(c, G);
     return s;
   }
-  const cudaMemcpyKind kind = mem_flags == RP_MEM_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
-  cudaError_t ce = cudaSuccess;
-  if (row_ptr) {
-    ce = cudaMemcpyAsync(rp_in, row_ptr, size_t(n + 1) * 8, kind, c->stream);
-    if (ce == cudaSuccess && nnz_in > 0) ce = cudaMemcpyAsync(col_in, col, size_t(nnz_in) * 4, kind, c->stream);
-  } else {
-    ce = cudaMemsetAsync(rp_in, 0, size_t(n + 1) * 8, c->stream);
-  }
-  const unsigned long long zero2[2] = {0, 0};
-  if (ce == cudaSuccess) ce = cudaMemcpyAsync(c->dropped, zero2, 16, cudaMemcpyHostToDevice, c->stream);
-  if (ce == cudaSuccess) ce = launch_validate_csr(rp_in, col_in, n, nnz_in, c->status, c->stream);
-  if (ce == cudaSuccess) ce = cudaStreamSynchronize(c->stream);
-  if (ce != cudaSuccess) {
-    cleanup();
-    free_graph_mem(c, G);
-    return fail(c, RP_ECUDA, "graph upload/validate: %s", cudaGetErrorString(ce));
-  }
-  if ((s = check_device_status(c)) != RP_OK) {
-    cleanup();
-    free_graph_mem(c, G);
-    return fail(c, RP_EINVAL, "invalid input: %s", c->err.c_str());
-  }
-  ce = launch_clean_count(rp_in, col_in, n, cnt, c->dropped, c->stream);
-  if (ce == cudaSuccess) ce = launch_scan_counts(cnt, n, G->row_ptr, bsum, maxd, c->stream);
-  if (ce == cudaSuccess) ce = launch_clean_write(rp_in, col_in, n, G->row_ptr, G->col, c->stream);
-  if (ce == cudaSuccess && start < 0) ce = launch_medoid(D->dev(), mean, best, med, c->stream);
-  int64_t nnz = 0, medoid = start;
-  int32_t maxdeg = 0;
-  unsigned long long dropped[2] = {0, 0};
-  if (ce == cudaSuccess) ce = cudaMemcpyAsync(&nnz, G->row_ptr + n, 8, cudaMemcpyDeviceToHost, c->stream);
-  if (ce == cudaSuccess) ce = cudaMemcpyAsync(&maxdeg, maxd, 4, cudaMemcpyDeviceToHost, c->stream);
-  if (ce == cudaSuccess && start < 0) ce = cudaMemcpyAsync(&medoid, med, 8, cudaMemcpyDeviceToHost, c->stream);
-  if (ce == cudaSuccess) ce = cudaMemcpyAsync(dropped, c->dropped, 16, cudaMemcpyDeviceToHost, c->stream);
-  if (ce == cudaSuccess) ce = cudaStreamSynchronize(c->stream);
-  cleanup();
-  if (ce != cudaSuccess) {
-    free_graph_mem(c, G);
-    return fail(c, RP_ECUDA, "graph cleaning: %s", cudaGetErrorString(ce));
-  }
-  if ((s = check_device_status(c)) != RP_OK) {
-    free_graph_mem(c, G);
-    return s;
-  }
-  if (maxdeg > RP_MAX_DEGREE) {
-    free_graph_mem(c, G);
-    return fail(c, RP_EINVAL, "out-degree %d after cleaning exceeds RP_MAX_DEGREE=%d", maxdeg, RP_MAX_DEGREE);
-  }
-  G->nnz = nnz;
-  G->max_deg_bound = maxdeg;
-  G->start = medoid;
-  G->bytes = size_t(n + 1) * 8 + size_t(G->col_cap) * 4;
-  static_assert(sizeof(unsigned long long) == 8, "");
-  // stats carry the cleaning counters in the spare slots of the status word
-  unsigned long long add[2] = {dropped[0], dropped[1]};
-  DevStatus hs;
-  cudaMemcpyAsync(&hs, c->status, sizeof hs, cudaMemcpyDeviceToHost, c->stream);
-  cudaStreamSynchronize(c->stream);
-  hs.spare[0] += add[0];
-  hs.spare[1] += add[1];
-  cudaMemcpyAsync(c->status, &hs, sizeof hs, cudaMemcpyHostToDevice, c->stream);
-  cudaStreamSynchronize(c->stream);
   *base_out = add_graph(c, G);
+  return RP_OK;
+}
+
+rp_status rp_graph_attach(rp_ctx* c, rp_graph data, const int64_t* row_ptr, const int32_t* col, int32_t mem_flags,
+                          rp_graph* out) {
+  if (!c) return RP_EINVAL;
+  std::lock_guard<std::mutex> lk(c->mu);
+  cudaSetDevice(c->device);
+  if (!out || !row_ptr) return fail(c, RP_EINVAL, "null argument");
+  if (mem_flags != RP_MEM_HOST && mem_flags != RP_MEM_DEVICE) return fail(c, RP_EINVAL, "bad mem_flags");
+  Graph* D = find_graph(c, data);
+  if (!D) return fail(c, RP_ENOTFOUND, "unknown graph %lld", (long long)data);
+  Graph* G = new Graph;
+  G->data = D->data;
+  G->n = D->n;
+  const rp_status s = attach_csr(c, G, row_ptr, col, D->start, mem_flags);
+  if (s != RP_OK) {
+    free_graph_mem(c, G);
+    return s;
+  }
+  *out = add_graph(c, G);
   return RP_OK;
 }
 

@@ -9,9 +9,10 @@
 //   list size L; its first vcap visited points V_p, in expansion order) and
 //   gets N_out(p) <- RobustPrune(p, V_p, alpha, R) (Algorithm 1, sorted; its
 //   first step adds the current N_out(p) and drops p).  Then every point j
-//   kept by some p of the batch takes those p as back edges, ascending by id,
-//   after its current list; a list that grows past R is pruned again,
-//   N_out(j) <- RobustPrune(j, merged, alpha, R).
+//   kept by some p of the batch takes those p as back edges, ascending by id
+//   (at most 4096 of them, the smallest ids), after its current list; a list
+//   that grows past R is pruned again, N_out(j) <- RobustPrune(j, merged,
+//   alpha, R).
 //
 // One batch on the device: the search kernel (queries are the batch's own
 // rows, the graph is read from the fixed-capacity adjacency, the visited
@@ -30,6 +31,7 @@ namespace rpk {
 namespace {
 
 constexpr int kWarpsPerBlock = 8;
+constexpr int kMaxSenders = 4096;  // back edges a point takes per batch (the smallest sender ids)
 
 __device__ __forceinline__ unsigned lanemask_lt() {
   unsigned m;
@@ -171,12 +173,15 @@ __global__ void back_merge_kernel(const int32_t* __restrict__ jlist, int64_t nj,
     __syncwarp();
     const int dj = deg[j];
     int32_t* nj_row = nbr + int64_t(j) * R;
-    // the senders not already in N_out(j), in ascending order
+    // the senders not already in N_out(j), in ascending order; a point takes at
+    // most kMaxSenders of them per batch (the smallest ids), which bounds every
+    // list the prune sees
+    const int ms = m < kMaxSenders ? m : kMaxSenders;
     int fresh = 0;
-    for (int x0 = 0; x0 < m; x0 += 32) {
+    for (int x0 = 0; x0 < ms; x0 += 32) {
       const int x = x0 + lane;
-      const int32_t v = x < m ? sorted[a + x] : -1;
-      bool keep = x < m;
+      const int32_t v = x < ms ? sorted[a + x] : -1;
+      bool keep = x < ms;
       for (int e = 0; keep && e < dj; ++e) keep = nj_row[e] != v;
       const unsigned msk = __ballot_sync(0xffffffffu, keep);
       if (keep) sorted[a + fresh + __popc(msk & lanemask_lt())] = v;  // in place: fresh <= x

@@ -5,8 +5,9 @@ RP-Tuning rewrites every node's out-list from that node's own list alone
 rank tunes the slice of the base graph holding its range (rp_graph_slice ->
 rp_tune_batch), and the tuned CSR is the concatenation of the ranks' rows in
 range order.  Gathering the slices is optional (a caller may keep the graph
-sharded); :func:`gather_slices` does it with one all-gather over a
-torch.distributed process group.
+sharded); :func:`gather_slices` does it with tensor all-gathers of the row
+lengths and column ids over a torch.distributed process group (nccl on the
+GPUs, gloo on the host).
 """
 from __future__ import annotations
 
@@ -75,11 +76,53 @@ def assemble(slices: list, n: int) -> tuple[np.ndarray, np.ndarray]:
     return row_ptr, np.ascontiguousarray(col, dtype=np.int32)
 
 
-def gather_slices(my_slices: list, n: int, group=None) -> list:
-    """All-gather every rank's Slices (one list per target) and assemble each
-    target's graph on every rank.  Uses torch.distributed (gloo or nccl)."""
+def allgather_csr(counts, col, n: int, group=None):
+    """One target's tuned graph from every rank's part, as torch tensors on the
+    device the inputs live on (this rank's GPU under nccl, the host under gloo).
+
+    counts: int64 row lengths of this rank's node range (node_range order);
+    col: int32 column ids of those rows.  Three tensor all-gathers: the row
+    lengths (padded to the longest range), the slice sizes, the column ids
+    (padded to the largest slice).  Returns (row_ptr int64[n+1], col int32).
+    """
+    import torch
     import torch.distributed as dist
     world = dist.get_world_size(group)
-    got = [None] * world
-    dist.all_gather_object(got, my_slices, group=group)
-    return [assemble([got[r][t] for r in range(world)], n) for t in range(len(my_slices))]
+    dev = counts.device
+    ranges = [node_range(r, world, n) for r in range(world)]
+    span = max(hi - lo for lo, hi in ranges)
+    cnt = torch.zeros(span, dtype=torch.int64, device=dev)
+    cnt[:counts.shape[0]] = counts
+    all_cnt = [torch.empty_like(cnt) for _ in range(world)]
+    dist.all_gather(all_cnt, cnt, group=group)
+    nnz = torch.tensor([col.shape[0]], dtype=torch.int64, device=dev)
+    all_nnz = [torch.empty_like(nnz) for _ in range(world)]
+    dist.all_gather(all_nnz, nnz, group=group)
+    sizes = [int(x.item()) for x in all_nnz]
+    pad = torch.full((max(max(sizes), 1),), -1, dtype=torch.int32, device=dev)
+    pad[:col.shape[0]] = col
+    all_col = [torch.empty_like(pad) for _ in range(world)]
+    dist.all_gather(all_col, pad, group=group)
+    lengths = torch.cat([all_cnt[r][:hi - lo] for r, (lo, hi) in enumerate(ranges)])
+    row_ptr = torch.zeros(n + 1, dtype=torch.int64, device=dev)
+    torch.cumsum(lengths, 0, out=row_ptr[1:])
+    return row_ptr, torch.cat([all_col[r][:sizes[r]] for r in range(world)])
+
+
+def gather_slices(my_slices: list, n: int, group=None, device=None) -> list:
+    """All-gather every rank's Slices (one list per target) and assemble each
+    target's graph on every rank (:func:`allgather_csr` per target, tensors on
+    `device`: by default this rank's GPU under nccl, the host under gloo).
+    Returns (row_ptr, col) numpy arrays per target."""
+    import torch
+    import torch.distributed as dist
+    if device is None:
+        nccl = dist.get_backend(group) == "nccl"
+        device = torch.device("cuda", torch.cuda.current_device()) if nccl else torch.device("cpu")
+    out = []
+    for s in my_slices:
+        counts = torch.from_numpy(np.diff(s.row_ptr).astype(np.int64)).to(device)
+        col = torch.from_numpy(np.ascontiguousarray(s.col, dtype=np.int32)).to(device)
+        row_ptr, col_all = allgather_csr(counts, col, n, group)
+        out.append((row_ptr.cpu().numpy(), col_all.cpu().numpy()))
+    return out

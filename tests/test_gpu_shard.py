@@ -61,3 +61,48 @@ def test_slice_bounds(ctx):
             rp.rp_graph_slice(ctx, base, lo, hi)
     for g in (empty, full, part, base):
         rp.rp_graph_free(ctx, g)
+
+
+def test_device_assembly_and_attach(ctx):
+    """The multi-GPU step's assembly on the device: each rank's slice as device
+    tensors (row lengths of its range, its column ids), concatenated in range
+    order with a prefix sum (shard.allgather_csr's arithmetic), registered over
+    the resident vectors with rp_graph_attach; the attached graph equals the
+    unsharded tuning and its searches return the oracle's lists."""
+    import torch
+    from paper_2602_08097_gb300 import shard
+    X = datagen.dataset("deep", 3000)
+    Q = datagen.queries("deep", 40)
+    base_rp, base_col = oracle.knn_base(X, 64, 1.2, 48)
+    base = rp.rp_load_graph(ctx, X, base_rp, base_col)
+    start = rp.rp_graph_info(ctx, base)["start"]
+    dev = torch.device("cuda", 0)
+    world, n = 3, X.shape[0]
+    a, R = TARGETS[1]
+    parts = []
+    for r in range(world):
+        lo, hi = shard.node_range(r, world, n)
+        part = rp.rp_graph_slice(ctx, base, lo, hi)
+        (g,) = rp.rp_tune_batch(ctx, part, [a], [R])
+        rp_d, col_d = rp.rp_graph_export(ctx, g, device=dev)
+        parts.append((torch.diff(rp_d[lo:hi + 1]), col_d.clone()))
+        rp.rp_graph_free(ctx, g)
+        rp.rp_graph_free(ctx, part)
+    lengths = torch.cat([c for c, _ in parts])
+    row_ptr = torch.zeros(n + 1, dtype=torch.int64, device=dev)
+    torch.cumsum(lengths, 0, out=row_ptr[1:])
+    col = torch.cat([c for _, c in parts])
+    g = rp.rp_graph_attach(ctx, base, row_ptr, col)
+    got_rp, got_col = rp.rp_graph_export(ctx, g)
+    ref_rp, ref_col = oracle.rp_tune(X, base_rp, base_col, a, R)
+    assert np.array_equal(got_rp, ref_rp) and np.array_equal(got_col, ref_col)
+    assert rp.rp_graph_info(ctx, g)["start"] == start
+    ids, _ = rp.rp_search(ctx, g, Q, 40, 10)
+    ref_ids, _, _ = oracle.greedy_search(X, ref_rp, ref_col, start, Q, 40, 10)
+    assert np.array_equal(ids, ref_ids)
+    bad = col.clone()
+    bad[0] = n  # an id out of range is refused
+    with pytest.raises(rp.RPError):
+        rp.rp_graph_attach(ctx, base, row_ptr, bad)
+    rp.rp_graph_free(ctx, g)
+    rp.rp_graph_free(ctx, base)
