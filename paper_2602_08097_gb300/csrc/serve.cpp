@@ -396,9 +396,11 @@ void rp_server::round_async(std::vector<Req*>& batch, int32_t* round_no) {
     worked = true;
     std::map<Key, int> needed;
     std::vector<Key> missing;
+    // at most what the budget holds (evict_for can free every resident graph:
+    // no parked request uses one)
+    const size_t cap = size_t(std::min<int64_t>(kMaxTargets, capacity));
     for (Req* r : parked)
-      if (needed.emplace(r->key, int(needed.size())).second && missing.size() < size_t(kMaxTargets))
-        missing.push_back(r->key);
+      if (needed.emplace(r->key, int(needed.size())).second && missing.size() < cap) missing.push_back(r->key);
     evict_for(missing.size(), needed);
     double alphas[kMaxTargets];
     int32_t Rs[kMaxTargets];

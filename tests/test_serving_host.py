@@ -447,3 +447,23 @@ def test_async_mixed_stream_and_failures(world):
         assert rp.rp_poll(srv, bad[0], 20000)["status"] == rp.RP_ENOMEM
     finally:
         rp.rp_server_destroy(srv)
+
+
+def test_async_respects_the_budget(world):
+    """The asynchronous path never holds more tuned graphs than the budget,
+    however many distinct targets are parked at once."""
+    from paper_2602_08097_gb300.serving import Request, replay
+    X, base, start, Q = world
+    ex = AsyncExec(X, base, start)
+    srv = ex.server(budget_graphs=2)
+    targets = [(1.15, 24), (1.1, 24), (1.05, 16), (1.0, 16), (1.12, 20), (1.15, 24)]
+    reqs = [Request("search", a, R, 0.0, queries=Q[i:i + 2], L=10, k=10) for i, (a, R) in enumerate(targets)]
+    try:
+        replay(srv, reqs, time_scale=0.0)
+        st = rp.rp_server_stats(srv)
+    finally:
+        rp.rp_server_destroy(srv)
+    assert st["peak_resident_graphs"] <= 2 and ex.live_peak <= 2
+    for r in reqs:
+        ids, d2 = _expected(X, base, start, r)
+        assert np.array_equal(r.ids, ids)
