@@ -152,6 +152,20 @@ rp_status rp_tune_batch(rp_ctx *ctx, rp_graph src, const double *alphas, const i
                         int32_t T, int32_t variant, rp_graph *outs);
 
 /*
+ * rp_debug_gram: test support, not part of the hot path.  The split-f16
+ * tcgen05 Gram of float rows exactly as the prune kernel forms it (the same
+ * operand stores, MMA sequence and combination of its two accumulators),
+ * 128 rows at a time: out[(128 g + i) * 128 + j] = G~(rows[128 g + i],
+ * rows[128 g + j]).  Tests hold every entry against the exact inner product
+ * and the error bound the float decision tiers assume.
+ *   rows: host int32[nrows], nrows a multiple of 128, ids in [0, n);
+ *   out: host float[nrows * 128].
+ * Errors: RP_ENOTFOUND, RP_EINVAL (uint8 vectors, a bad row count or id),
+ *   RP_ENOMEM, RP_ECUDA, RP_EDEVICE.
+ */
+rp_status rp_debug_gram(rp_ctx *ctx, rp_graph g, const int32_t *rows, int64_t nrows, float *out);
+
+/*
  * rp_graph_attach: a graph over the vectors (and start vertex) of graph `data`
  * from a CSR adjacency, cleaned as rp_load_graph cleans it (ids checked to lie
  * in [0, n), self loops and repeated ids dropped), without uploading the

@@ -58,6 +58,11 @@ cudaError_t launch_emit_csr(int64_t n, int T, const int64_t* src_row_ptr,
                             int64_t* block_sums /* T * nblk */, cudaStream_t s);
 int64_t emit_csr_blocks(int64_t n);
 
+// Test support: the split-f16 Gram of float rows, 128 rows (rows[g*128 ..]) per group,
+// out[(g*128 + i)*128 + j] = G~(row i, row j) of group g (prune.cu)
+cudaError_t launch_gram_probe(const DevData& D, const int32_t* rows, int64_t groups, float* out, DevStatus* status,
+                              int num_sms, cudaStream_t s);
+
 // prep.cu
 cudaError_t launch_pad_rows(const void* src, int64_t n, int64_t src_row_bytes, uint8_t* dst,
                             int64_t dst_row_bytes, cudaStream_t s);

@@ -216,6 +216,45 @@ __device__ __noinline__ bool recheck_dominates_cold(const PruneArgs& a, const in
 //          whose margin is inside the resulting d2 bound is redone in
 //          single-precision difference form from the rows (rigorous relative
 //          bound), and if still inside, in float-float, then binary64.
+// Eight float values of one row (dimensions 8c .. 8c+7 of a 128-dimension
+// slice), scaled by a power of two and split into f16 hi and lo, stored at
+// CTA row `orow` of the two operands (hi at opnd, lo 32 KB further) in the
+// K-major core-matrix layout of tc.cuh.
+__device__ __forceinline__ void store_split8(unsigned char* opnd, int orow, int c, const float (&xv)[8], float scale) {
+  uint4 hi, lo;
+  split_f16x2(xv[0] * scale, xv[1] * scale, hi.x, lo.x);
+  split_f16x2(xv[2] * scale, xv[3] * scale, hi.y, lo.y);
+  split_f16x2(xv[4] * scale, xv[5] * scale, hi.z, lo.z);
+  split_f16x2(xv[6] * scale, xv[7] * scale, hi.w, lo.w);
+  const size_t at = size_t(c * 16 + orow / 8) * 128 + (orow % 8) * 16;
+  *reinterpret_cast<uint4*>(opnd + at) = hi;
+  *reinterpret_cast<uint4*>(opnd + 128 * 128 * 2 + at) = lo;
+}
+
+// One 128-dimension slice (kd dimensions) of the 128 x 128 candidate Gram,
+// issued by one thread: hi hi^T into the accumulator at TMEM column 0 and, for
+// split float rows, hi lo^T + lo hi^T into the one at column 128.
+template <bool SPLIT>
+__device__ __forceinline__ void issue_gram_slice(uint32_t tmem, const unsigned char* opnd, int kd, bool accumulate) {
+  constexpr uint32_t idesc = umma_idesc_f16(128, 128);
+#pragma unroll 1
+  for (int kk = 0; kk < kd / 16; ++kk) {
+    const uint64_t dsc = umma_desc(smem_addr(opnd) + uint32_t(kk) * 2u * 16u * 128u, 16u * 128u, 128u);
+    umma_f16(tmem, dsc, dsc, idesc, accumulate || kk > 0);
+    if constexpr (SPLIT) {  // the cross terms with the low halves into the second accumulator
+      const uint64_t dlo = umma_desc(smem_addr(opnd + 128 * 128 * 2) + uint32_t(kk) * 2u * 16u * 128u, 16u * 128u, 128u);
+      umma_f16(tmem + 128u, dsc, dlo, idesc, accumulate || kk > 0);
+      umma_f16(tmem + 128u, dlo, dsc, idesc, true);
+    }
+  }
+}
+
+// A split Gram entry from its two accumulators, back in the rows' units
+// (scalings by powers of two: exact).
+__device__ __forceinline__ float split_gram_value(uint32_t acc0, uint32_t acc1, float inv_s2) {
+  return fmaf(__uint_as_float(acc1), 4.8828125e-04f, __uint_as_float(acc0)) * inv_s2;
+}
+
 // Shared-memory plan of prune_tc_kernel.  Per node group the producer warps
 // keep norms and thresholds; per pipeline slot (2) and group they hand the
 // consumer warp the candidate ids, keys, binary64 key cache and masks.
@@ -356,8 +395,7 @@ __global__ void __launch_bounds__(160, tc_min_ctas<DT, MAXM, TB>()) prune_tc_ker
     float4* cq = reinterpret_cast<float4*>(pb + L::p_cq);
     const uint32_t tmem = *tmem_slot;
     // operands go in as f16: uint8 values exactly, float rows scaled by a power
-    // of two into [-1, 1] and rounded
-    constexpr uint32_t idesc = umma_idesc_f16(128, 128);
+    // of two into [-1, 1] and split (issue_gram_slice)
     const int64_t elems = a.row_bytes / (DT == kU8 ? 1 : 4);  // padded dims per row
     const int nslices = int((elems + 127) / 128);
     // Split f16 Gram of scaled rows, G' = hi hi^T + 2^-11 (hi lo^T + lo hi^T):
@@ -503,17 +541,7 @@ __global__ void __launch_bounds__(160, tc_min_ctas<DT, MAXM, TB>()) prune_tc_ker
                                  __uint_as_float(x1.z), __uint_as_float(x1.w)};
 #pragma unroll
             for (int q = 0; q < 8; ++q) nacc = fmaf(xv[q], xv[q], nacc);
-            if (one_slice) {  // zero rows past the degree, as the operand pass writes them
-              uint4 hi, lo;
-              split_f16x2(xv[0] * a.scale, xv[1] * a.scale, hi.x, lo.x);
-              split_f16x2(xv[2] * a.scale, xv[3] * a.scale, hi.y, lo.y);
-              split_f16x2(xv[4] * a.scale, xv[5] * a.scale, hi.z, lo.z);
-              split_f16x2(xv[6] * a.scale, xv[7] * a.scale, hi.w, lo.w);
-              const int srow = g * MAXM + t;
-              const size_t at = size_t(c * 16 + srow / 8) * 128 + (srow % 8) * 16;
-              *reinterpret_cast<uint4*>(opnd + at) = hi;
-              *reinterpret_cast<uint4*>(opnd + 128 * 128 * 2 + at) = lo;
-            }
+            if (one_slice) store_split8(opnd, g * MAXM + t, c, xv, a.scale);  // rows past the degree: zeros
           }
         }
       }
@@ -663,14 +691,10 @@ __global__ void __launch_bounds__(160, tc_min_ctas<DT, MAXM, TB>()) prune_tc_ker
               x0 = __ldg(xq);
               x1 = __ldg(xq + 1);
             }
-            uint4 hi, lo;
-            split_f16x2(__uint_as_float(x0.x) * a.scale, __uint_as_float(x0.y) * a.scale, hi.x, lo.x);
-            split_f16x2(__uint_as_float(x0.z) * a.scale, __uint_as_float(x0.w) * a.scale, hi.y, lo.y);
-            split_f16x2(__uint_as_float(x1.x) * a.scale, __uint_as_float(x1.y) * a.scale, hi.z, lo.z);
-            split_f16x2(__uint_as_float(x1.z) * a.scale, __uint_as_float(x1.w) * a.scale, hi.w, lo.w);
-            const size_t at = size_t(c * 16 + orow / 8) * 128 + (orow % 8) * 16;
-            *reinterpret_cast<uint4*>(opnd + at) = hi;
-            *reinterpret_cast<uint4*>(opnd + 128 * 128 * 2 + at) = lo;
+            const float xv[8] = {__uint_as_float(x0.x), __uint_as_float(x0.y), __uint_as_float(x0.z),
+                                 __uint_as_float(x0.w), __uint_as_float(x1.x), __uint_as_float(x1.y),
+                                 __uint_as_float(x1.z), __uint_as_float(x1.w)};
+            store_split8(opnd, orow, c, xv, a.scale);
           }
         }
         const bool last = sl == nslices - 1;
@@ -679,17 +703,7 @@ __global__ void __launch_bounds__(160, tc_min_ctas<DT, MAXM, TB>()) prune_tc_ker
         named_sync(kBarProd, 128);
         tc_fence_after();
         if (r == 0) {
-#pragma unroll 1
-          for (int kk = 0; kk < kd / 16; ++kk) {
-            const uint64_t dsc = umma_desc(smem_addr(opnd) + uint32_t(kk) * 2u * 16u * 128u, 16u * 128u, 128u);
-            umma_f16(tmem, dsc, dsc, idesc, sl > 0 || kk > 0);
-            if constexpr (DT == kF32) {  // the cross terms with the low halves into the second accumulator
-              const uint64_t dlo =
-                  umma_desc(smem_addr(opnd + 128 * 128 * 2) + uint32_t(kk) * 2u * 16u * 128u, 16u * 128u, 128u);
-              umma_f16(tmem + 128u, dsc, dlo, idesc, sl > 0 || kk > 0);
-              umma_f16(tmem + 128u, dlo, dsc, idesc, true);
-            }
-          }
+          issue_gram_slice<DT == kF32>(tmem, opnd, kd, sl > 0);
           umma_commit(mbar);
         }
         if (last) {
@@ -833,7 +847,7 @@ __global__ void __launch_bounds__(160, tc_min_ctas<DT, MAXM, TB>()) prune_tc_ker
               const int c = c0 + j;
               const float4 q = cq[c];
               // hi hi^T + 2^-11 (cross terms), back in the rows' units (powers of two: exact scalings)
-              const float G = fmaf(__uint_as_float(v2[j]), 4.8828125e-04f, __uint_as_float(v[j])) * a.inv_s2;
+              const float G = split_gram_value(v[j], v2[j], a.inv_s2);
               const float dv = (nt + q.x) - 2.f * G;
               const float err = fmaf(q.y, At, fmaf(q.x, eps_n, Bt));
               const float lo = dv - err, hi = dv + err;
@@ -1467,6 +1481,92 @@ static cudaError_t run_generic(const PruneArgs& args, int num_sms, int64_t host_
   if (err != cudaSuccess) return err;
   const int64_t grid = std::min<int64_t>(int64_t(num_sms) * per_sm, host_count);
   kern<<<unsigned(grid), 256, bytes, s>>>(args, M2);
+  return cudaGetLastError();
+}
+
+namespace {
+
+// Test support: the split-f16 tcgen05 Gram of 128 float rows per CTA, through
+// the prune kernel's own operand stores, MMA sequence and combination, written
+// out so that a test can hold every entry against the exact inner product and
+// the bound the float decision tiers rely on.
+__global__ void __launch_bounds__(128, 1) gram_probe_kernel(const uint8_t* X, int64_t row_bytes, float scale,
+                                                           float inv_s2, const int32_t* rows, int64_t groups,
+                                                           float* out, DevStatus* status) {
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  unsigned char* opnd = smem_raw;  // hi and lo operands: 2 x 128 rows x 128 dims of f16
+  uint64_t* mbar = reinterpret_cast<uint64_t*>(smem_raw + 2 * 128 * 128 * 2);
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem_raw + 2 * 128 * 128 * 2 + 16);
+  const int r = threadIdx.x, warp = r >> 5;
+  if (warp == 0) tmem_alloc(tmem_slot, 256u);
+  if (r == 0) mbar_init(mbar, 1);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+  const int64_t elems = row_bytes / 4;
+  const int nslices = int((elems + 127) / 128);
+  uint32_t phase = 0;
+  bool ok = true;
+  for (int64_t gi = blockIdx.x; gi < groups && ok; gi += gridDim.x) {
+    const float* xr = reinterpret_cast<const float*>(X + int64_t(rows[gi * 128 + r]) * row_bytes);
+    for (int sl = 0; sl < nslices && ok; ++sl) {
+      const int64_t rem = elems - int64_t(sl) * 128;
+      const int kd = int(rem < 128 ? rem : 128);
+      for (int c = 0; c < kd / 8; ++c) {
+        float xv[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) xv[q] = xr[int64_t(sl) * 128 + c * 8 + q];
+        store_split8(opnd, r, c, xv, scale);
+      }
+      fence_async_smem();
+      tc_fence_before();
+      __syncthreads();
+      tc_fence_after();
+      if (r == 0) {
+        issue_gram_slice<true>(tmem, opnd, kd, sl > 0);
+        umma_commit(mbar);
+      }
+      ok = mbar_wait(mbar, phase, 1 << 24);
+      phase ^= 1u;
+      tc_fence_after();
+      if (!__syncthreads_and(ok)) {
+        if (r == 0) raise_status(status, kDevOverflow, -3);
+        ok = false;
+      }
+    }
+    if (!ok) break;
+    for (int c0 = 0; c0 < 128; c0 += 8) {
+      uint32_t v[8], v2[8];
+      tmem_ld8(tmem + (uint32_t(32 * warp) << 16) + uint32_t(c0), v);
+      tmem_ld8(tmem + (uint32_t(32 * warp) << 16) + uint32_t(128 + c0), v2);
+      tmem_ld_wait();
+#pragma unroll
+      for (int j = 0; j < 8; ++j) out[(gi * 128 + r) * 128 + c0 + j] = split_gram_value(v[j], v2[j], inv_s2);
+    }
+    tc_fence_before();
+    __syncthreads();  // TMEM read before the next group's MMA overwrites it
+    tc_fence_after();
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  if (warp == 0) tmem_dealloc(tmem, 256u);
+}
+
+}  // namespace
+
+cudaError_t launch_gram_probe(const DevData& D, const int32_t* rows, int64_t groups, float* out, DevStatus* status,
+                              int num_sms, cudaStream_t s) {
+  if (groups <= 0) return cudaSuccess;
+  // 64 KB of operands, requested as 120 KB so that one CTA (256 TMEM columns) runs per SM
+  const size_t bytes = 120 * 1024;
+  cudaError_t err = cudaFuncSetAttribute(gram_probe_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(bytes));
+  if (err != cudaSuccess) return err;
+  const float inv_s = 1.f / D.scale;
+  const int64_t grid = std::min<int64_t>(groups, num_sms);
+  gram_probe_kernel<<<unsigned(grid), 128, bytes, s>>>(D.X, D.row_bytes, D.scale, inv_s * inv_s, rows, groups, out,
+                                                       status);
   return cudaGetLastError();
 }
 

@@ -1449,6 +1449,37 @@ rp_status rp_tune_batch(rp_ctx* c, rp_graph src, const double* alphas, const int
   return tune_impl(c, src, alphas, Rs, T, variant, outs, true);
 }
 
+rp_status rp_debug_gram(rp_ctx* c, rp_graph g, const int32_t* rows, int64_t nrows, float* out) {
+  if (!c) return RP_EINVAL;
+  std::lock_guard<std::mutex> lk(c->mu);
+  cudaSetDevice(c->device);
+  Graph* G = find_graph(c, g);
+  if (!G) return fail(c, RP_ENOTFOUND, "unknown graph %lld", (long long)g);
+  if (G->data->dtype != RP_F32) return fail(c, RP_EINVAL, "the split Gram is for float rows");
+  if (!rows || !out || nrows < 0 || nrows % 128 != 0) return fail(c, RP_EINVAL, "need rows and out, nrows a multiple of 128");
+  for (int64_t i = 0; i < nrows; ++i)
+    if (rows[i] < 0 || rows[i] >= G->n) return fail(c, RP_EINVAL, "rows[%lld]=%d outside [0, n)", (long long)i, rows[i]);
+  if (nrows == 0) return RP_OK;
+  int32_t* drows = nullptr;
+  float* dout = nullptr;
+  rp_status s = dalloc(c, reinterpret_cast<void**>(&drows), size_t(nrows) * 4);
+  if (s == RP_OK) s = dalloc(c, reinterpret_cast<void**>(&dout), size_t(nrows) * 128 * 4);
+  cudaError_t ce = cudaSuccess;
+  if (s == RP_OK) {
+    ce = cudaMemcpyAsync(drows, rows, size_t(nrows) * 4, cudaMemcpyHostToDevice, c->stream);
+    if (ce == cudaSuccess)
+      ce = launch_gram_probe(G->data->dev(), drows, nrows / 128, dout, c->status, c->num_sms, c->stream);
+    if (ce == cudaSuccess) ce = cudaMemcpyAsync(out, dout, size_t(nrows) * 128 * 4, cudaMemcpyDeviceToHost, c->stream);
+    if (ce == cudaSuccess) ce = cudaStreamSynchronize(c->stream);
+    c->kernel_launches += 1;
+  }
+  dfree(c, drows, size_t(nrows) * 4);
+  dfree(c, dout, size_t(nrows) * 128 * 4);
+  if (s != RP_OK) return s;
+  if (ce != cudaSuccess) return fail(c, RP_ECUDA, "Gram probe: %s", cudaGetErrorString(ce));
+  return check_device_status(c);
+}
+
 rp_status rp_tune_batch_async(rp_ctx* c, rp_graph src, const double* alphas, const int32_t* Rs, int32_t T,
                               int32_t variant, int32_t chunks, rp_graph* outs, int64_t* ticket) {
   if (!c) return RP_EINVAL;
