@@ -11,9 +11,18 @@ name   recipe                                                       seeds
 tiny   n=2,000, d=32, f32; 16 centres ~ N(0, 4 I), x = c_z + N(0,I)  1000/2000
 sift   n=1,000,000, d=128, u8 = rint(min(255, Gamma(0.6, 40)))       1001/2001
 gist   n=1,000,000, d=960, f32 = |N(0,1)| * 0.05, rows L2-normalised 1002/2002
-deep   n=10,000,000, d=96, f32; 256 centres ~ N(0, I), sigma 0.5,     1003/2003
+deep   n=10,000,000, d=96, f32; 256 centres ~ N(0, I), component     1003/2003
+       covariance diag(s_i^2) with s_i = 1.5 i^-0.75 (i = 1 .. 96),
        rows unit-normalised in f64 then cast to f32
 =====  ==========================================================  =========
+
+Deep's 96 values are PCA outputs of network embeddings: their variance falls
+off with the component index and the local intrinsic dimension is far below
+96.  The deep mixture's components have that shape (a maximum-likelihood
+estimate of the intrinsic dimension from 20 nearest neighbours is about 15);
+an isotropic component of the same dimension (about 38 by that estimate)
+would make every graph index far harder to search than the data it stands
+for.
 
 Rows are drawn in fixed chunks of ``CHUNK`` rows so that a prefix of ``n`` rows
 is the same whatever total is asked for; a smaller ``n`` therefore gives the
@@ -37,6 +46,9 @@ CONFIGS = {
     "gist": dict(index=2, dtype="f32", d=960, n=1_000_000, nq=1_000),
     "deep": dict(index=3, dtype="f32", d=96, n=10_000_000, nq=10_000),
 }
+
+# deep: per-dimension standard deviation of a mixture component, 1.5 i^-0.75
+DEEP_SPREAD = 1.5 * np.arange(1, 97, dtype=np.float64) ** -0.75
 
 
 def _gen(seed: int) -> np.random.Generator:
@@ -75,7 +87,7 @@ def _rows(name: str, n: int, rng: np.random.Generator, centres) -> np.ndarray:
             out[lo:hi] = _unit_rows_f32(g)
         elif name == "deep":
             z = rng.integers(0, 256, size=b)
-            g = centres[z] + 0.5 * rng.normal(0.0, 1.0, size=(b, d))
+            g = centres[z] + rng.normal(0.0, 1.0, size=(b, d)) * DEEP_SPREAD
             out[lo:hi] = _unit_rows_f32(g)
         else:
             raise KeyError(name)

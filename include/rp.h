@@ -155,15 +155,19 @@ rp_status rp_tune_batch(rp_ctx *ctx, rp_graph src, const double *alphas, const i
  * rp_debug_gram: test support, not part of the hot path.  The split-f16
  * tcgen05 Gram of float rows exactly as the prune kernel forms it (the same
  * operand stores, MMA sequence and combination of its two accumulators),
- * 128 rows at a time: out[(128 g + i) * 128 + j] = G~(rows[128 g + i],
- * rows[128 g + j]).  Tests hold every entry against the exact inner product
- * and the error bound the float decision tiers assume.
+ * 128 rows at a time: out[(128 g + i) * 128 + j] = G~(y_i, y_j) for the rows
+ * y_i = x[rows[128 g + i]] - c_i, where c_i = x[centres[2 g + i / 64]] (each
+ * 64-row half centred on its own pivot, at the prune's scale for centred
+ * rows), or c_i = 0 when centres is NULL.  Tests hold every entry against the
+ * exact inner product and the error bound the float decision tiers assume.
  *   rows: host int32[nrows], nrows a multiple of 128, ids in [0, n);
+ *   centres: host int32[nrows / 64], ids in [0, n), or NULL;
  *   out: host float[nrows * 128].
  * Errors: RP_ENOTFOUND, RP_EINVAL (uint8 vectors, a bad row count or id),
  *   RP_ENOMEM, RP_ECUDA, RP_EDEVICE.
  */
-rp_status rp_debug_gram(rp_ctx *ctx, rp_graph g, const int32_t *rows, int64_t nrows, float *out);
+rp_status rp_debug_gram(rp_ctx *ctx, rp_graph g, const int32_t *rows, const int32_t *centres, int64_t nrows,
+                        float *out);
 
 /*
  * rp_graph_attach: a graph over the vectors (and start vertex) of graph `data`
@@ -388,8 +392,9 @@ rp_status rp_build_knn_random_base(rp_ctx *ctx, rp_graph data, int32_t kcand, in
  * visited points V_p, in expansion order), then N_out(p) <- RobustPrune(p,
  * V_p, alpha, R) (Algorithm 1, sorted; its first step adds the current
  * N_out(p)).  Then every point j kept by some batch point takes those points
- * as back edges, ascending by id, after its current list; a list that grows
- * past R is pruned again, RobustPrune(j, merged list, alpha, R).  Pass i
+ * as back edges, ascending by id and at most 512 of them (the smallest ids),
+ * after its current list; a list that grows past R is pruned again,
+ * RobustPrune(j, merged list, alpha, R).  Pass i
  * inserts every point with alpha = alphas[i] (the original construction runs
  * alpha = 1, then alpha1).  The result is fully determined by these rules.
  *   data: a graph whose vectors and start vertex are used (its edges are not).
@@ -476,11 +481,13 @@ rp_status rp_set_tuning(rp_ctx *ctx, int32_t mode, int32_t tile0, int32_t ctas_p
  * rp_set_knn_method: which exact kNN scan rp_knn and rp_build_knn_base use.
  * Both return the same lists (exact top k by (distance, id)).
  *   RP_KNN_CUDA_CORE: every pair's distance on CUDA cores.
- *   RP_KNN_TENSOR: an f16 Gram on tcgen05 filters candidates with a rigorous
- *     error bound (none for uint8 rows of d <= 128), and the survivors are
- *     ranked exactly; needs k <= 128 and uint8 rows of d <= 128 or float
- *     rows of d <= 256 (RP_EINVAL otherwise).  Holds an f16 copy of the
- *     vectors (n x d x 2 bytes) for the call.
+ *   RP_KNN_TENSOR: a Gram on tcgen05 filters candidates with a rigorous
+ *     error bound (uint8 rows of d <= 128: exact f16 products, no bound;
+ *     float rows: each split into two f16 operands, hi and 2^11 times the
+ *     remainder, bound near 2^-22 |q||p|), and the survivors are ranked
+ *     exactly; needs k <= 128 and uint8 rows of d <= 128 or float rows of
+ *     d <= 128 (RP_EINVAL otherwise).  Holds an f16 copy of the vectors
+ *     (n x d x 2 bytes, twice that for float rows) for the call.
  *   RP_KNN_AUTO (default): RP_KNN_TENSOR where it applies.
  * Errors: RP_EINVAL.
  */

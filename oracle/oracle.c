@@ -698,7 +698,7 @@ int orc_d2_query(const void *X, int dtype, int d, const void *Q, int64_t nq,
  *             step takes the union with the current N_out(p) and drops p).
  *   Then every N_out(p) <- N'(p).  Then the back edges: for every j named in
  *   some N'(p), P_j = the batch points naming j, ascending by id, its first
- *   4096 members (VAMANA_MAX_SENDERS: this bounds every candidate list a
+ *   512 members (VAMANA_MAX_SENDERS: this bounds every candidate list a
  *   hub point gets); the merged list is N_out(j) followed by the members of
  *   P_j not already in it; if it
  *   holds at most R points it becomes N_out(j), otherwise
@@ -801,7 +801,7 @@ static int back_edge_cmp(const void *a, const void *b) {
   return (x->p > y->p) - (x->p < y->p);
 }
 
-#define VAMANA_MAX_SENDERS 4096
+#define VAMANA_MAX_SENDERS 512
 
 /* Batch sizes: 1, 2, 4, ... capped at max_batch; the last batch takes the rest. */
 static int64_t vamana_batch_size(int64_t k, int64_t max_batch) {

@@ -106,7 +106,7 @@ def load_library(path: str = LIB_PATH):
         "rp_tune_batch": [P, i64, P, P, i32, i32, P],
         "rp_tune_batch_async": [P, i64, P, P, i32, i32, i32, P, ctypes.POINTER(i64)],
         "rp_graph_attach": [P, i64, P, P, i32, ctypes.POINTER(i64)],
-        "rp_debug_gram": [P, i64, P, i64, P],
+        "rp_debug_gram": [P, i64, P, P, i64, P],
         "rp_tune_wait": [P, i64, i32],
         "rp_graph_info": [P, i64, ctypes.POINTER(i64), ctypes.POINTER(i64), ctypes.POINTER(i32), ctypes.POINTER(i64)],
         "rp_graph_export": [P, i64, P, P, i64, i32],
@@ -239,12 +239,17 @@ def rp_tune_batch(ctx, src: int, alphas, Rs, variant: int = RP_SORTED):
     return list(outs)
 
 
-def rp_debug_gram(ctx, g: int, rows) -> np.ndarray:
-    """Test support: the prune kernel's split-f16 Gram of float rows, 128 at a time;
+def rp_debug_gram(ctx, g: int, rows, centres=None) -> np.ndarray:
+    """Test support: the prune kernel's split-f16 Gram of float rows, 128 at a time,
+    each 64-row half centred on its row of ``centres`` (one per half) if given;
     returns float32[len(rows) // 128, 128, 128]."""
     rows = np.ascontiguousarray(rows, dtype=np.int32)
+    if centres is not None:
+        centres = np.ascontiguousarray(centres, dtype=np.int32)
+        if centres.shape != (rows.shape[0] // 64,):
+            raise ValueError("centres needs one row id per 64 rows")
     out = np.empty((rows.shape[0] // 128, 128, 128), dtype=np.float32)
-    _check(ctx, load_library().rp_debug_gram(ctx, int(g), _ptr(rows), rows.shape[0], _ptr(out)))
+    _check(ctx, load_library().rp_debug_gram(ctx, int(g), _ptr(rows), _ptr(centres), rows.shape[0], _ptr(out)))
     return out
 
 

@@ -59,9 +59,10 @@ cudaError_t launch_emit_csr(int64_t n, int T, const int64_t* src_row_ptr,
 int64_t emit_csr_blocks(int64_t n);
 
 // Test support: the split-f16 Gram of float rows, 128 rows (rows[g*128 ..]) per group,
-// out[(g*128 + i)*128 + j] = G~(row i, row j) of group g (prune.cu)
-cudaError_t launch_gram_probe(const DevData& D, const int32_t* rows, int64_t groups, float* out, DevStatus* status,
-                              int num_sms, cudaStream_t s);
+// out[(g*128 + i)*128 + j] = G~(row i, row j) of group g, the rows of each 64-row half
+// centred on centres[2g + half] when centres is not null (prune.cu)
+cudaError_t launch_gram_probe(const DevData& D, const int32_t* rows, const int32_t* centres, int64_t groups,
+                              float* out, DevStatus* status, int num_sms, cudaStream_t s);
 
 // prep.cu
 cudaError_t launch_pad_rows(const void* src, int64_t n, int64_t src_row_bytes, uint8_t* dst,
@@ -178,7 +179,7 @@ cudaError_t launch_slot_counts(const int32_t* jlist, int64_t nj, const int32_t* 
 cudaError_t launch_back_scatter(const int32_t* pts, int64_t nb, const int32_t* nbr, const int32_t* deg, int R,
                                 const int32_t* slot, const int64_t* seg_ptr, int32_t* cursor, int32_t* seg,
                                 cudaStream_t s);
-cudaError_t launch_back_merge(const int32_t* jlist, int64_t nj, const int64_t* seg_ptr, const int32_t* seg,
+cudaError_t launch_back_merge(const int32_t* jlist, int64_t nj, const int64_t* seg_ptr, int32_t* seg,
                               int32_t* sorted, int32_t* nbr, int32_t* deg, int R, int32_t* pend, int32_t* ov_raw,
                               int32_t* ov_slot, int32_t* ov_cnt, int32_t* n_ov, cudaStream_t s);
 cudaError_t launch_ov_prep(const int32_t* ov_slot, int64_t no, const int32_t* jlist, const int64_t* seg_ptr, int R,

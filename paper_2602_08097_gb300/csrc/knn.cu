@@ -292,12 +292,17 @@ __global__ void __launch_bounds__(kThreads) knn_kernel(KnnArgs a) {
 // ---------------------------------------------------------------------------
 // tensor-core path: exact kNN with an f16 Gram filter
 // ---------------------------------------------------------------------------
-// Points and queries are packed once as f16 rows (float rows scaled by a power
-// of two so that |x| <= 1; uint8 values as they are) in tiles of 128 rows,
-// each tile already in the core-matrix order of the tcgen05 operand layout.
-// A CTA of 4 warps owns 128 queries (thread t = query t = TMEM lane t) and
-// streams every point tile past them: D = Q P^T on tcgen05 into one of two
-// TMEM accumulators, the next tile's copy in flight meanwhile.
+// Points and queries are packed once as f16 rows in tiles of 128 rows, each
+// tile already in the core-matrix order of the tcgen05 operand layout: uint8
+// values as they are (exact), float rows scaled by a power of two so that
+// |x| <= 1 and split into two f16 operands, hi = f16(x) and lo =
+// f16(2^11 (x - hi)), the tile holding hi then lo.  A CTA of 4 warps owns 128
+// queries (thread t = query t = TMEM lane t) and streams every point tile past
+// them: D = Q P^T on tcgen05 into one of two TMEM accumulator sets (float rows:
+// hi hi^T in one accumulator, hi lo^T + lo hi^T in a second, G~ = the first +
+// 2^-11 the second), the next tile's copy in flight meanwhile.  The split keeps
+// the Gram error near 2^-22 |q||p| instead of f16's 2^-11, so the candidate
+// window stays narrow on data whose neighbours lie close together.
 //
 // From G~ the thread forms d2~ = |q|^2 + |p|^2 - 2 G~ (scaled units) and a
 // rigorous error bound err (zero for uint8 rows of d <= 128, where every
@@ -323,13 +328,13 @@ struct KnnTcArgs {
   int k;
   const uint8_t* qtiles;     // packed query tiles (the point tiles for base-point queries)
   const uint8_t* ptiles;     // packed point tiles
-  int64_t tile_bytes;        // kTcP * dpad * 2
+  int64_t tile_bytes;        // kTcP * dpad * 2 per operand: uint8 one (f16), float two (hi, lo)
   int ksteps;                // dpad / 16
   const float* qnorm;        // |q'|^2 per query (scaled)
   const float* pnorm;        // |p'|^2 per point, padded to whole tiles with 0
   const float2* tmax;        // per point tile: (max |p'|^2, max |p'|)
   int exact;                 // 1: G~ and d2~ are exact
-  float eps_ip, eps_n, sqrt_d;
+  float eps_ip, eps_n, sub_abs;  // sub_abs: the subnormal-rounding term per unit of |q| + |p|
   uint4* cand;               // per CTA: kTcQ x capc entries {lb, ub, id, 0}
   int capc;
   int32_t* out_ids;
@@ -348,26 +353,34 @@ __device__ __forceinline__ float fkey_inv(unsigned k) {
 }
 
 // Bound on |d2~ - d2'| for one (query, point) pair in scaled units: twice the
-// f16 Gram error (eps_ip |q'||p'| plus subnormal rounding sqrt(d) 2^-25 per
-// operand norm), the single-precision norms, and the roundings that form
-// d2~ and its two bounds (2^-21 (|q'|^2 + |p'|^2) covers them).
+// Gram error (eps_ip |q'||p'| plus the subnormal roundings, sub_abs (|q'| +
+// |p'|) in all), the single-precision norms, and the roundings that form d2~
+// and its two bounds (2^-21 (|q'|^2 + |p'|^2) covers them).
 __device__ __forceinline__ float tc_err(const KnnTcArgs& a, float nq, float sq, float np, float sp) {
-  return (2.f * a.eps_ip * sq * sp + a.sqrt_d * 5.9604645e-08f * (sq + sp) + (a.eps_n + 4.7683716e-07f) * (nq + np)) *
+  return (2.f * a.eps_ip * sq * sp * 1.001f + a.sub_abs * (sq + sp) + (a.eps_n + 4.7683716e-07f) * (nq + np)) *
              1.0001f +
          1e-30f;
 }
 
-size_t knn_tc_smem(int64_t tile_bytes, int capc) {
-  // A tile, two B tiles, two point-norm rows, per-warp sort buffers, misc;
-  // at least a third of an SM's shared memory, so that at most two CTAs (each
-  // holding 256 of the SM's 512 TMEM columns) share an SM
+// Operands per tile: uint8 rows one f16 operand, float rows two (hi, lo).
+__host__ __device__ constexpr int tc_nop(int dtype) { return dtype == kF32 ? 2 : 1; }
+
+size_t knn_tc_smem(int dtype, int64_t tile_bytes, int capc) {
+  // A tile, two B tiles, two point-norm rows, per-warp sort buffers, misc.
+  // uint8: at least a third of an SM's shared memory, so that at most two CTAs
+  // (each holding 256 of the SM's 512 TMEM columns) share an SM; float: more
+  // than half, one CTA holding all 512 (two sets of two accumulators).
   const size_t need = size_t(tile_bytes) * 3 + 2 * kTcP * 4 + size_t(4) * capc * 8 + 256;
-  return std::max(need, size_t(228 * 1024 / 3 + 1024));
+  return std::max(need, dtype == kF32 ? size_t(228 * 1024 / 2 + 1024) : size_t(228 * 1024 / 3 + 1024));
 }
 
 template <int DT>
 __global__ void __launch_bounds__(128) knn_tc_kernel(KnnTcArgs a) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
+  // float rows: hi and lo operands, two accumulators per set (acc0 at column
+  // 0 of the set, acc1 at 128)
+  constexpr bool kSplit = DT == kF32;
+  constexpr uint32_t kSetCols = kSplit ? 256u : 128u;
   const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
   unsigned char* sA = smem_raw;
   unsigned char* sB0 = smem_raw + a.tile_bytes;
@@ -383,7 +396,7 @@ __global__ void __launch_bounds__(128) knn_tc_kernel(KnnTcArgs a) {
   constexpr uint32_t idesc = umma_idesc_f16(128, 128);
   constexpr uint32_t lbo = 16u * 128u;  // 16 row-groups of 128 bytes per k-chunk
 
-  if (warp == 0) tmem_alloc(tmem_slot, 256);  // two 128-column accumulators
+  if (warp == 0) tmem_alloc(tmem_slot, 2 * kSetCols);  // two accumulator sets
   if (t == 0) {
     mbar_init(&mbar[0], 1);
     mbar_init(&mbar[1], 1);
@@ -433,10 +446,18 @@ __global__ void __launch_bounds__(128) knn_tc_kernel(KnnTcArgs a) {
       __syncthreads();  // tile j in smem; every read of accumulator b (tile j - 2) finished
       tc_fence_after();
       if (t == 0) {
+        const uint32_t acc = tmem + uint32_t(b) * kSetCols;
+        const uint32_t lo_off = uint32_t(a.tile_bytes / 2);  // float tiles: lo after hi
         for (int kk = 0; kk < a.ksteps; ++kk) {
           const uint64_t da = umma_desc(smem_addr(sA) + uint32_t(kk) * 2u * lbo, lbo, 128u);
           const uint64_t db = umma_desc(smem_addr(sB) + uint32_t(kk) * 2u * lbo, lbo, 128u);
-          umma_f16(tmem + uint32_t(b * 128), da, db, idesc, kk > 0);
+          umma_f16(acc, da, db, idesc, kk > 0);
+          if constexpr (kSplit) {  // the cross terms with the low halves
+            const uint64_t dal = umma_desc(smem_addr(sA) + lo_off + uint32_t(kk) * 2u * lbo, lbo, 128u);
+            const uint64_t dbl = umma_desc(smem_addr(sB) + lo_off + uint32_t(kk) * 2u * lbo, lbo, 128u);
+            umma_f16(acc + 128u, da, dbl, idesc, kk > 0);
+            umma_f16(acc + 128u, dal, db, idesc, true);
+          }
         }
         umma_commit(&mbar[b]);
       }
@@ -460,15 +481,20 @@ __global__ void __launch_bounds__(128) knn_tc_kernel(KnnTcArgs a) {
       const int64_t p0 = j * kTcP;
 #pragma unroll 1
       for (int c0 = 0; c0 < kTcP; c0 += 32) {
-        uint32_t v[32];
-        tmem_ld32(tmem + (uint32_t(32 * warp) << 16) + uint32_t(b * 128 + c0), v);
+        uint32_t v[32], v2[kSplit ? 32 : 1];
+        const uint32_t acc = tmem + (uint32_t(32 * warp) << 16) + uint32_t(b) * kSetCols + uint32_t(c0);
+        tmem_ld32(acc, v);
+        if constexpr (kSplit) tmem_ld32(acc + 128u, *reinterpret_cast<uint32_t(*)[32]>(v2));
         tmem_ld_wait();
         if (!qlive) continue;
 #pragma unroll
         for (int jj = 0; jj < 32; ++jj) {
           const int c = c0 + jj;
           const float pn = pnb[c];
-          const float d2 = fmaf(-2.f, __uint_as_float(v[jj]), nqq + pn);
+          // float rows: hi hi^T + 2^-11 (hi lo^T + lo hi^T), scaled units
+          const float G = kSplit ? fmaf(__uint_as_float(v2[jj]), 4.8828125e-04f, __uint_as_float(v[jj]))
+                                 : __uint_as_float(v[jj]);
+          const float d2 = fmaf(-2.f, G, nqq + pn);
           if (d2 <= thr) {
             const int64_t pid = p0 + c;
             if (pid >= a.n || (!a.Qraw && pid == qi)) continue;
@@ -578,7 +604,7 @@ __global__ void __launch_bounds__(128) knn_tc_kernel(KnnTcArgs a) {
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
-  if (warp == 0) tmem_dealloc(tmem, 256);
+  if (warp == 0) tmem_dealloc(tmem, 2 * kSetCols);
 }
 
 // ---- packing: f16 operand tiles, scaled squared norms, per-tile maxima
@@ -597,8 +623,9 @@ __global__ void maxabs_kernel(const uint8_t* __restrict__ X, int64_t row_bytes, 
   if ((threadIdx.x & 31) == 0) atomicMax(out, __float_as_uint(m));
 }
 
-// Row i -> tile i / 128, row i % 128 of the core-matrix layout, scaled by s
-// (a power of two: exact) and rounded to f16 (uint8 values are exact); the
+// Row i -> tile i / 128, row i % 128 of the core-matrix layout: uint8 values
+// as f16 (exact); float rows scaled by s (a power of two: exact) and split
+// into f16 hi and lo (split_f16x2), lo kTcP * dpad * 2 bytes after hi; the
 // norm |x'|^2 in single precision in index order.
 template <int DT>
 __global__ void pack_f16_kernel(const uint8_t* __restrict__ X, int64_t row_bytes, int64_t n, int d, int dpad,
@@ -608,7 +635,8 @@ __global__ void pack_f16_kernel(const uint8_t* __restrict__ X, int64_t row_bytes
   if (i >= ntile * kTcP) return;
   const int64_t tile = i / kTcP;
   const int r = int(i % kTcP);
-  uint8_t* tb = tiles + tile * int64_t(kTcP) * dpad * 2;
+  const int64_t op_bytes = int64_t(kTcP) * dpad * 2;
+  uint8_t* tb = tiles + tile * op_bytes * tc_nop(DT);
   float acc = 0.f;
   for (int kc = 0; kc < dpad / 8; ++kc) {
     float v[8];
@@ -623,9 +651,19 @@ __global__ void pack_f16_kernel(const uint8_t* __restrict__ X, int64_t row_bytes
       v[e] = x;
       acc = fmaf(x, x, acc);
     }
-    const uint4 o = make_uint4(pack_f16x2(v[0], v[1]), pack_f16x2(v[2], v[3]), pack_f16x2(v[4], v[5]),
-                               pack_f16x2(v[6], v[7]));
-    *reinterpret_cast<uint4*>(tb + (int64_t(kc) * 16 + r / 8) * 128 + (r % 8) * 16) = o;
+    const int64_t at = (int64_t(kc) * 16 + r / 8) * 128 + (r % 8) * 16;
+    if constexpr (DT == kF32) {
+      uint4 hi, lo;
+      split_f16x2(v[0], v[1], hi.x, lo.x);
+      split_f16x2(v[2], v[3], hi.y, lo.y);
+      split_f16x2(v[4], v[5], hi.z, lo.z);
+      split_f16x2(v[6], v[7], hi.w, lo.w);
+      *reinterpret_cast<uint4*>(tb + at) = hi;
+      *reinterpret_cast<uint4*>(tb + op_bytes + at) = lo;
+    } else {
+      *reinterpret_cast<uint4*>(tb + at) = make_uint4(pack_f16x2(v[0], v[1]), pack_f16x2(v[2], v[3]),
+                                                      pack_f16x2(v[4], v[5]), pack_f16x2(v[6], v[7]));
+    }
   }
   norms[i] = acc;
 }
@@ -684,7 +722,7 @@ cudaError_t launch_maxabs_f32(const uint8_t* X, int64_t row_bytes, int64_t n, in
 bool knn_tc_eligible(int dtype, int d, int k) {
   if (k < 1 || k > 128) return false;
   const int dpad = (d + 15) / 16 * 16;
-  return dtype == kU8 ? d <= 128 : dpad <= 256;
+  return dtype == kU8 ? d <= 128 : dpad <= 128;  // float: three split tiles fit in shared memory
 }
 
 namespace {
@@ -699,9 +737,9 @@ size_t align256(size_t x) { return (x + 255) / 256 * 256; }
 TcPlan tc_plan(int dtype, int d, int64_t n, int64_t nq_ext, int num_sms) {
   TcPlan P{};
   P.dpad = (d + 15) / 16 * 16;
-  P.capc = dtype == kU8 ? 512 : 1024;
-  P.tile_bytes = int64_t(kTcP) * P.dpad * 2;
-  const size_t smem = knn_tc_smem(P.tile_bytes, P.capc);
+  P.capc = 512;
+  P.tile_bytes = int64_t(kTcP) * P.dpad * 2 * tc_nop(dtype);
+  const size_t smem = knn_tc_smem(dtype, P.tile_bytes, P.capc);
   P.ctas = int(std::max<size_t>(1, std::min<size_t>(2, size_t(228 * 1024) / (smem + 1024))));
   P.grid = num_sms * P.ctas;
   P.ntile = (n + kTcP - 1) / kTcP;
@@ -793,16 +831,20 @@ cudaError_t launch_knn_tc(const KnnTcLaunch& K, cudaStream_t s) {
   a.pnorm = pnorm;
   a.tmax = tmax;
   a.exact = f32 ? 0 : 1;
-  a.eps_ip = 9.765625e-04f + 4.76837158e-07f + float(K.data.d) * 2.38418579e-07f;  // 2^-10 + 2^-21 + d 2^-22
+  // Split Gram of scaled rows: |G~ - G| <= eps_ip |q'||p'| + 2^-36 sqrt(d) (|q'| + |p'|):
+  // 2^-22 left by the split of each operand, 2^-22 for the dropped lo lo^T, 2^-23 for
+  // the last sum, f32 accumulation d 2^-24 with a factor 4 allowance; the lo halves
+  // that fall below f16's normal range round to 2^-25 in their units, 2^-36 here.
+  a.eps_ip = 4.f * 2.384185791015625e-07f + 1.1920929e-07f + float(K.data.d) * 2.384185791015625e-07f;
   a.eps_n = float(K.data.d + 2) * 5.9604645e-08f;
-  a.sqrt_d = std::sqrt(float(K.data.d)) * 1.001f;  // (1 + 2^-11) for the f16 rounding of the other operand
+  a.sub_abs = std::sqrt(float(K.data.d)) * 1.001f * 2.910383e-11f;  // twice 2^-36 sqrt(d)
   a.cand = reinterpret_cast<uint4*>(base + P.off_cand);
   a.capc = P.capc;
   a.out_ids = K.out_ids;
   a.out_dists = K.out_dists;
   a.work = work;
   a.status = K.status;
-  const size_t smem = knn_tc_smem(P.tile_bytes, P.capc);
+  const size_t smem = knn_tc_smem(K.data.dtype, P.tile_bytes, P.capc);
   if (f32) {
     if ((err = cudaFuncSetAttribute(knn_tc_kernel<kF32>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem))) !=
         cudaSuccess)

@@ -173,27 +173,36 @@ __device__ __forceinline__ bool fine_dominates(const PruneArgs& a, int32_t u, in
   return canon_dominates(A2, d2a, d2b);
 }
 
-// A float domination test the Gram tier left undecided: row `t` of the node
-// (candidate ids[t]) against column `c`, alpha = A / 1000: single-precision difference
-// form from the rows, then float-float, then binary64.  Inlined: as an
-// out-of-line call it let the per-target mask loop unroll fully, and the
-// larger code measured 50% slower (64 candidates, 8 targets, 1M x 96 float
-// rows).
-__device__ __forceinline__ bool recheck_dominates(const PruneArgs& a, const int32_t* ids, const float* key,
-                                                  double* key64, int t, int c, int32_t A, int p, float E_rel,
-                                                  float E_abs) {
-  const int64_t A2 = int64_t(A) * A;
+// An open pair of the float decision pass: row `t` against column `c` for the
+// distinct alphas u0 .. TA - 1 (ascending; the Gram tier found u0 of them
+// surely removing).  One single-precision difference-form distance from the
+// rows serves every alpha; a test inside its bound goes on to float-float and
+// binary64.  Removal is monotone in alpha (removed at a larger alpha means
+// removed at every smaller one), so the alphas that remove the column are a
+// prefix: returns u1, the first that keeps it (TA if none), after
+// recheck_tests(u0, u1, TA) tests.  Inlined into the queue's resolution
+// loop; the in-place use below is out of line, since inlining it there let
+// the mask loop unroll fully and the larger code ran slower.
+__device__ __forceinline__ int recheck_prefix(const PruneArgs& a, const int32_t* ids, const float* key,
+                                              double* key64, int t, int c, int u0, int TA, int p, float E_rel,
+                                              float E_abs) {
   const float d2a = row_d2<kF32>(a.X + int64_t(ids[t]) * a.row_bytes, a.X + int64_t(ids[c]) * a.row_bytes,
                                  a.row_bytes);
-  const int rr = sure_dominates(float(A2), d2a, key[c], E_rel, E_abs);
-  return rr >= 0 ? (rr == 1) : fine_dominates(a, ids[t], ids[c], p, &key64[c], double(A2));
+  int u = u0;
+  for (; u < TA; ++u) {
+    const int64_t A2 = int64_t(a.Ad[u]) * a.Ad[u];
+    const int rr = sure_dominates(float(A2), d2a, key[c], E_rel, E_abs);
+    if (!(rr >= 0 ? (rr == 1) : fine_dominates(a, ids[t], ids[c], p, &key64[c], double(A2)))) break;
+  }
+  return u;
 }
+__device__ __forceinline__ int recheck_tests(int u0, int u1, int TA) { return u1 - u0 + (u1 < TA ? 1 : 0); }
 
-// The same, out of line, for the rare tests decided in place when the queue is full.
-__device__ __noinline__ bool recheck_dominates_cold(const PruneArgs& a, const int32_t* ids, const float* key,
-                                                    double* key64, int t, int c, int32_t A, int p, float E_rel,
-                                                    float E_abs) {
-  return recheck_dominates(a, ids, key, key64, t, c, A, p, E_rel, E_abs);
+// The same, out of line, for the rare pairs decided in place when the queue is full.
+__device__ __noinline__ int recheck_prefix_cold(const PruneArgs& a, const int32_t* ids, const float* key,
+                                                double* key64, int t, int c, int u0, int TA, int p, float E_rel,
+                                                float E_abs) {
+  return recheck_prefix(a, ids, key, key64, t, c, u0, TA, p, E_rel, E_abs);
 }
 
 // ---------------------------------------------------------------------------
@@ -207,15 +216,20 @@ __device__ __noinline__ bool recheck_dominates_cold(const PruneArgs& a, const in
 //   uint8: values 0..255 are exact in f16, products exact in f32, and every
 //          partial sum is an integer below 2^24 (d <= 256), so G is exact and
 //          d2(u, v) = |u|^2 + |v|^2 - 2 G(u, v) is the exact integer.
-//   float: rows scaled by a power of two into [-1, 1] and split into f16 hi
-//          and lo (x = hi + 2^-11 lo up to 2^-22 relative); G~ = hi hi^T +
-//          2^-11 (hi lo^T + lo hi^T) from two accumulators, with |G~ - G| <=
-//          eps_ip |u||v| + 2^-36 sqrt(d) (|u| + |v|) / scale, eps_ip = 4 2^-22 +
-//          2^-23 + d 2^-22 (the split, the dropped lo lo^T term, the last sum,
-//          f32 accumulation with a factor 4 allowance).  A domination test
-//          whose margin is inside the resulting d2 bound is redone in
-//          single-precision difference form from the rows (rigorous relative
-//          bound), and if still inside, in float-float, then binary64.
+//   float: each candidate row enters centred on the pivot p, y = x - p (one
+//          f32 subtraction per value, as in the pivot key's difference form),
+//          scaled by a power of two into [-1, 1] and split into f16 hi and lo
+//          (y = hi + 2^-11 lo up to 2^-22 relative); G~ = hi hi^T + 2^-11
+//          (hi lo^T + lo hi^T) from two accumulators, with |G~ - <y_u, y_v>|
+//          <= eps_ip |y_u||y_v| + 2^-36 sqrt(d) (|y_u| + |y_v|) / scale,
+//          eps_ip = 5 2^-22 + 2^-23 + d 2^-22 (the subtractions, the split, the
+//          dropped lo lo^T term, the last sum, f32 accumulation with a factor
+//          4 allowance).  Then d2(u, v) = |y_u|^2 + |y_v|^2 - 2 <y_u, y_v>,
+//          where |y|^2 = d2(p, x) is the pivot key: the bound scales with the
+//          candidates' distances from p, not with their norms.  A domination
+//          test whose margin is inside it is redone in single-precision
+//          difference form from the rows (rigorous relative bound), and if
+//          still inside, in float-float, then binary64.
 // Eight float values of one row (dimensions 8c .. 8c+7 of a 128-dimension
 // slice), scaled by a power of two and split into f16 hi and lo, stored at
 // CTA row `orow` of the two operands (hi at opnd, lo 32 KB further) in the
@@ -229,6 +243,15 @@ __device__ __forceinline__ void store_split8(unsigned char* opnd, int orow, int 
   const size_t at = size_t(c * 16 + orow / 8) * 128 + (orow % 8) * 16;
   *reinterpret_cast<uint4*>(opnd + at) = hi;
   *reinterpret_cast<uint4*>(opnd + 128 * 128 * 2 + at) = lo;
+}
+
+// The same for a row centred on the pivot: xv - pv in f32, then scaled and split.
+__device__ __forceinline__ void store_split8_centred(unsigned char* opnd, int orow, int c, const float (&xv)[8],
+                                                     const float (&pv)[8], float scale) {
+  float y[8];
+#pragma unroll
+  for (int q = 0; q < 8; ++q) y[q] = xv[q] - pv[q];
+  store_split8(opnd, orow, c, y, scale);
 }
 
 // One 128-dimension slice (kd dimensions) of the 128 x 128 candidate Gram,
@@ -394,18 +417,22 @@ __global__ void __launch_bounds__(160, tc_min_ctas<DT, MAXM, TB>()) prune_tc_ker
     float* qhi = reinterpret_cast<float*>(pb + L::p_qhi);
     float4* cq = reinterpret_cast<float4*>(pb + L::p_cq);
     const uint32_t tmem = *tmem_slot;
-    // operands go in as f16: uint8 values exactly, float rows scaled by a power
-    // of two into [-1, 1] and split (issue_gram_slice)
+    // operands go in as f16: uint8 values exactly, float rows centred on the
+    // pivot, scaled by a power of two into [-1, 1] and split (issue_gram_slice)
     const int64_t elems = a.row_bytes / (DT == kU8 ? 1 : 4);  // padded dims per row
     const int nslices = int((elems + 127) / 128);
-    // Split f16 Gram of scaled rows, G' = hi hi^T + 2^-11 (hi lo^T + lo hi^T):
-    // |G~ - G| <= eps_ip |u||v| + 2^-36 sqrt(d) (|u| + |v|) / scale (the split
-    // leaves 2^-22 per operand, the dropped lo lo^T term 2^-22, the last sum
-    // 2^-23, f32 accumulation d 2^-24 with a factor 4 allowance; subnormal lo)
-    const float eps_ip = 4.f * 2.384185791015625e-07f + 1.1920929e-07f + float(a.d) * 2.384185791015625e-07f;
+    // Split f16 Gram of the scaled centred rows y = x - p, G' = hi hi^T + 2^-11
+    // (hi lo^T + lo hi^T): |G~ - <y_u, y_v>| <= eps_ip |y_u||y_v| + 2^-36 sqrt(d)
+    // (|y_u| + |y_v|) / scale (the f32 subtractions 2^-23 relative to
+    // |y_u||y_v|, the split 2^-22 per operand, the dropped lo lo^T term 2^-22,
+    // the last sum 2^-23, f32 accumulation d 2^-24 with a factor 4 allowance;
+    // subnormal lo).  The squared norms |y|^2 are the pivot keys, whose
+    // single-precision bound is E_rel relative (+ E_abs); eps_n adds the
+    // roundings that form d2 and its two bounds.
+    const float eps_ip = 5.f * 2.384185791015625e-07f + 1.1920929e-07f + float(a.d) * 2.384185791015625e-07f;
     const float sub_abs = a.sqrt_d * 1.001f * 2.910383e-11f * a.inv_s;  // twice 2^-36 sqrt(d) / scale
-    const float eps_n = float(a.d + 12) * 5.9604645e-08f;
-    const float err_abs = float(a.d) * 2.3509887e-38f;  // underflowed products, 2^-125 each
+    const float eps_n = E_rel + 6.f * 5.9604645e-08f;
+    const float err_abs = 2.f * E_abs + float(a.d) * 2.3509887e-38f;  // + underflowed products, 2^-125 each
     uint32_t phase = 0;
     bool dead = false;
     unsigned long long n_rechecks = 0;  // single-precision rechecks, added to the status once at the end
@@ -536,12 +563,15 @@ __global__ void __launch_bounds__(160, tc_min_ctas<DT, MAXM, TB>()) prune_tc_ker
               kacc += part;
               part = 0.f;
             }
-            const float xv[8] = {__uint_as_float(x0.x), __uint_as_float(x0.y), __uint_as_float(x0.z),
-                                 __uint_as_float(x0.w), __uint_as_float(x1.x), __uint_as_float(x1.y),
-                                 __uint_as_float(x1.z), __uint_as_float(x1.w)};
-#pragma unroll
-            for (int q = 0; q < 8; ++q) nacc = fmaf(xv[q], xv[q], nacc);
-            if (one_slice) store_split8(opnd, g * MAXM + t, c, xv, a.scale);  // rows past the degree: zeros
+            if (one_slice) {  // rows past the degree: zeros
+              const float xv[8] = {__uint_as_float(x0.x), __uint_as_float(x0.y), __uint_as_float(x0.z),
+                                   __uint_as_float(x0.w), __uint_as_float(x1.x), __uint_as_float(x1.y),
+                                   __uint_as_float(x1.z), __uint_as_float(x1.w)};
+              const float pv[8] = {__uint_as_float(y0.x), __uint_as_float(y0.y), __uint_as_float(y0.z),
+                                   __uint_as_float(y0.w), __uint_as_float(y1.x), __uint_as_float(y1.y),
+                                   __uint_as_float(y1.z), __uint_as_float(y1.w)};
+              store_split8_centred(opnd, g * MAXM + t, c, xv, pv, a.scale);
+            }
           }
         }
       }
@@ -645,10 +675,13 @@ __global__ void __launch_bounds__(160, tc_min_ctas<DT, MAXM, TB>()) prune_tc_ker
       if (live_row) {
         ids[rank] = my_id;
         key[rank] = kacc;
-        norm[rank] = nacc;
         if constexpr (DT == kF32) {
-          sn[rank] = sqrtf(nacc);
+          // the centred rows' squared norms are the pivot keys
+          norm[rank] = kacc;
+          sn[rank] = sqrtf(kacc);
           key64[rank] = my64;
+        } else {
+          norm[rank] = nacc;
         }
       }
       // ---- f16 operand row at position rank (rows past the degree stay zero);
@@ -685,16 +718,22 @@ __global__ void __launch_bounds__(160, tc_min_ctas<DT, MAXM, TB>()) prune_tc_ker
         } else if (!(nslices == 1 && in_order)) {  // else written with the keys
 #pragma unroll 4
           for (int c = 0; c < kd / 8; ++c) {
-            uint4 x0 = make_uint4(0, 0, 0, 0), x1 = make_uint4(0, 0, 0, 0);
-            if (live_row) {
+            uint4 x0 = make_uint4(0, 0, 0, 0), x1 = x0, y0 = x0, y1 = x0;
+            if (live_row) {  // rows past the degree stay zero
               const uint4* xq = reinterpret_cast<const uint4*>(xrow + int64_t(sl) * 512) + 2 * c;
+              const uint4* pq = reinterpret_cast<const uint4*>(prow + int64_t(sl) * 512) + 2 * c;
               x0 = __ldg(xq);
               x1 = __ldg(xq + 1);
+              y0 = __ldg(pq);
+              y1 = __ldg(pq + 1);
             }
             const float xv[8] = {__uint_as_float(x0.x), __uint_as_float(x0.y), __uint_as_float(x0.z),
                                  __uint_as_float(x0.w), __uint_as_float(x1.x), __uint_as_float(x1.y),
                                  __uint_as_float(x1.z), __uint_as_float(x1.w)};
-            store_split8(opnd, orow, c, xv, a.scale);
+            const float pv[8] = {__uint_as_float(y0.x), __uint_as_float(y0.y), __uint_as_float(y0.z),
+                                 __uint_as_float(y0.w), __uint_as_float(y1.x), __uint_as_float(y1.y),
+                                 __uint_as_float(y1.z), __uint_as_float(y1.w)};
+            store_split8_centred(opnd, orow, c, xv, pv, a.scale);
           }
         }
         const bool last = sl == nslices - 1;
@@ -735,7 +774,7 @@ __global__ void __launch_bounds__(160, tc_min_ctas<DT, MAXM, TB>()) prune_tc_ker
             if constexpr (DT == kF32) {
               // padding past the last alpha never counts (hi < -inf, lo > -inf)
               for (int u = a.TA; u < L::TB4; ++u) qlo[rank * L::TB4 + u] = qhi[rank * L::TB4 + u] = -INFINITY;
-              cq[rank] = make_float4(float(nacc), sqrtf(float(nacc)), 0.f, 0.f);  // the column's norm and its root
+              cq[rank] = make_float4(kacc, sqrtf(kacc), 0.f, 0.f);  // the column's centred norm^2 and its root
             }
           }
         }
@@ -880,8 +919,9 @@ __global__ void __launch_bounds__(160, tc_min_ctas<DT, MAXM, TB>()) prune_tc_ker
             und[0] |= w1 ? 0ull : xu;
             und[MW - 1] |= w1 ? xu : 0ull;
           }
-          // open pairs (rare): every alpha from ts on goes to the recheck, which
-          // decides each exactly (those that in fact keep the pair say so)
+          // open pairs (rare): the alphas from ts on go to the recheck, one entry
+          // per pair, which decides them in ascending order from one distance
+          // (those that in fact keep the pair say so)
 #pragma unroll
           for (int w = 0; w < MW; ++w) {
             while (und[w]) {
@@ -891,24 +931,22 @@ __global__ void __launch_bounds__(160, tc_min_ctas<DT, MAXM, TB>()) prune_tc_ker
               int u0 = 0;
 #pragma unroll
               for (int b = 0; b < NB; ++b) u0 |= int((pl[b][w] >> cb) & 1ull) << b;
-              for (int u = u0; u < TA; ++u) {
-                // queued and resolved after this pass by all producer threads at
-                // once; decided here if the queue is full
-                const int qi = atomicAdd(rq_count + s, 1);
-                if (qi < L::rq_cap) {
-                  rq[qi] = (unsigned(g * MAXM + t) << 16) | (unsigned(c) << 5) | unsigned(u);
-                } else {
-                  ++n_rechecks;
-                  // the binary64 decision is monotone in alpha: kept here means kept
-                  // at every larger alpha, removed here means removed at every
-                  // smaller one, so ts for this column becomes u + 1
-                  if (!recheck_dominates_cold(a, ids, key, key64, t, c, a.Ad[u], ppt, E_rel, E_abs)) break;
-                  const unsigned long long bit = 1ull << cb;
+              // queued and resolved after this pass by all producer threads at
+              // once; decided here if the queue is full
+              const int qi = atomicAdd(rq_count + s, 1);
+              if (qi < L::rq_cap) {
+                rq[qi] = (unsigned(g * MAXM + t) << 16) | (unsigned(c) << 5) | unsigned(u0);
+              } else {
+                // the binary64 decision is monotone in alpha: kept at u means kept
+                // at every larger alpha, removed at u means removed at every
+                // smaller one, so ts for this column becomes the first u that keeps
+                const int u1 = recheck_prefix_cold(a, ids, key, key64, t, c, u0, TA, ppt, E_rel, E_abs);
+                n_rechecks += recheck_tests(u0, u1, TA);
+                const unsigned long long bit = 1ull << cb;
 #pragma unroll
-                  for (int b = 0; b < NB; ++b) {
-                    const unsigned long long m_b = (((u + 1) >> b) & 1) ? bit : 0ull;
-                    pl[b][w] = (pl[b][w] & ~bit) | m_b;
-                  }
+                for (int b = 0; b < NB; ++b) {
+                  const unsigned long long m_b = ((u1 >> b) & 1) ? bit : 0ull;
+                  pl[b][w] = (pl[b][w] & ~bit) | m_b;
                 }
               }
             }
@@ -949,21 +987,22 @@ __global__ void __launch_bounds__(160, tc_min_ctas<DT, MAXM, TB>()) prune_tc_ker
       named_sync(kBarProd, 128);  // every producer's masks and TMEM reads are done
       tc_fence_after();
       if constexpr (DT == kF32) {
-        // the queued tests, one per thread: a removal sets its bit in the row's mask
+        // the queued pairs, one per thread: each alpha that removes the column
+        // sets its bit in the row's mask for that alpha
         const int nq = min(rq_count[s], L::rq_cap);  // the same for every producer
         if (nq > 0) {
           for (int i = r; i < nq; i += 128) {
             const uint32_t e = rq[i];
-            const int tr = int(e >> 16), c = int((e >> 5) & 0x7ffu), u = int(e & 31u);
+            const int tr = int(e >> 16), c = int((e >> 5) & 0x7ffu), u0 = int(e & 31u);
             const int gq = tr / MAXM, tq = tr % MAXM;
             unsigned char* sbq = slot_base(s, gq);
-            if (recheck_dominates(a, reinterpret_cast<const int32_t*>(sbq + L::s_ids),
-                                  reinterpret_cast<const float*>(sbq + L::s_key),
-                                  reinterpret_cast<double*>(sbq + L::s_key64), tq, c, a.Ad[u],
-                                  point_of_row(a, misc[s * 2 + gq]), E_rel, E_abs))
-              atomicOr(reinterpret_cast<unsigned long long*>(sbq + L::s_masks) + (u * MAXM + tq) * MW + (c >> 6),
-                       1ull << (c & 63));
-            ++n_rechecks;
+            const int u1 = recheck_prefix(a, reinterpret_cast<const int32_t*>(sbq + L::s_ids),
+                                          reinterpret_cast<const float*>(sbq + L::s_key),
+                                          reinterpret_cast<double*>(sbq + L::s_key64), tq, c, u0, a.TA,
+                                          point_of_row(a, misc[s * 2 + gq]), E_rel, E_abs);
+            n_rechecks += recheck_tests(u0, u1, a.TA);
+            unsigned long long* mrow = reinterpret_cast<unsigned long long*>(sbq + L::s_masks) + tq * MW + (c >> 6);
+            for (int u = u0; u < u1; ++u) atomicOr(mrow + u * MAXM * MW, 1ull << (c & 63));
           }
           named_sync(kBarProd, 128);
         }
@@ -1086,7 +1125,11 @@ __global__ void __launch_bounds__(256) prune_generic_kernel(PruneArgs a, int M2)
     }
     const int32_t ppt = point_of_row(a, p);  // the point being pruned
     const uint8_t* xp = a.X + int64_t(ppt) * a.row_bytes;
-    for (int j = t; j < M2; j += NT) {
+    // this node's sort width: the smallest power of two >= m (M2 is the launch's
+    // largest, sized for its longest list; the others sort no more than their own)
+    int Mp = 1;
+    while (Mp < m) Mp <<= 1;
+    for (int j = t; j < Mp; j += NT) {
       if (j < m) {
         const int32_t v = a.col[e0 + j];
         ids[j] = v;
@@ -1100,9 +1143,9 @@ __global__ void __launch_bounds__(256) prune_generic_kernel(PruneArgs a, int M2)
     }
     __syncthreads();
     if (a.variant == 0) {
-      for (int k = 2; k <= M2; k <<= 1) {
+      for (int k = 2; k <= Mp; k <<= 1) {
         for (int j = k >> 1; j > 0; j >>= 1) {
-          for (int idx = t; idx < M2 / 2; idx += NT) {
+          for (int idx = t; idx < Mp / 2; idx += NT) {
             const int i = (idx / j) * 2 * j + (idx % j);
             const int l = i + j;
             const bool up = (i & k) == 0;
@@ -1118,7 +1161,7 @@ __global__ void __launch_bounds__(256) prune_generic_kernel(PruneArgs a, int M2)
           __syncthreads();
         }
       }
-      for (int j = t; j < M2; j += NT) key64[j] = __longlong_as_double(0x7ff8000000000000ll);
+      for (int j = t; j < Mp; j += NT) key64[j] = __longlong_as_double(0x7ff8000000000000ll);
       __syncthreads();
       if constexpr (DT == kF32) {
         for (int i = t; i < m; i += NT) {
@@ -1158,7 +1201,7 @@ __global__ void __launch_bounds__(256) prune_generic_kernel(PruneArgs a, int M2)
         }
       }
     } else {
-      for (int j = t; j < M2; j += NT) key64[j] = __longlong_as_double(0x7ff8000000000000ll);
+      for (int j = t; j < Mp; j += NT) key64[j] = __longlong_as_double(0x7ff8000000000000ll);
     }
     __syncthreads();
 
@@ -1489,10 +1532,11 @@ namespace {
 // Test support: the split-f16 tcgen05 Gram of 128 float rows per CTA, through
 // the prune kernel's own operand stores, MMA sequence and combination, written
 // out so that a test can hold every entry against the exact inner product and
-// the bound the float decision tiers rely on.
+// the bound the float decision tiers rely on.  With `centres`, each 64-row half
+// of a group enters centred on its own pivot row, as the prune's nodes do.
 __global__ void __launch_bounds__(128, 1) gram_probe_kernel(const uint8_t* X, int64_t row_bytes, float scale,
-                                                           float inv_s2, const int32_t* rows, int64_t groups,
-                                                           float* out, DevStatus* status) {
+                                                           float inv_s2, const int32_t* rows, const int32_t* centres,
+                                                           int64_t groups, float* out, DevStatus* status) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* opnd = smem_raw;  // hi and lo operands: 2 x 128 rows x 128 dims of f16
   uint64_t* mbar = reinterpret_cast<uint64_t*>(smem_raw + 2 * 128 * 128 * 2);
@@ -1510,14 +1554,19 @@ __global__ void __launch_bounds__(128, 1) gram_probe_kernel(const uint8_t* X, in
   bool ok = true;
   for (int64_t gi = blockIdx.x; gi < groups && ok; gi += gridDim.x) {
     const float* xr = reinterpret_cast<const float*>(X + int64_t(rows[gi * 128 + r]) * row_bytes);
+    const float* pr = centres ? reinterpret_cast<const float*>(X + int64_t(centres[gi * 2 + r / 64]) * row_bytes)
+                              : nullptr;
     for (int sl = 0; sl < nslices && ok; ++sl) {
       const int64_t rem = elems - int64_t(sl) * 128;
       const int kd = int(rem < 128 ? rem : 128);
       for (int c = 0; c < kd / 8; ++c) {
-        float xv[8];
+        float xv[8], pv[8];
 #pragma unroll
-        for (int q = 0; q < 8; ++q) xv[q] = xr[int64_t(sl) * 128 + c * 8 + q];
-        store_split8(opnd, r, c, xv, scale);
+        for (int q = 0; q < 8; ++q) {
+          xv[q] = xr[int64_t(sl) * 128 + c * 8 + q];
+          pv[q] = pr ? pr[int64_t(sl) * 128 + c * 8 + q] : 0.f;
+        }
+        store_split8_centred(opnd, r, c, xv, pv, scale);
       }
       fence_async_smem();
       tc_fence_before();
@@ -1556,17 +1605,18 @@ __global__ void __launch_bounds__(128, 1) gram_probe_kernel(const uint8_t* X, in
 
 }  // namespace
 
-cudaError_t launch_gram_probe(const DevData& D, const int32_t* rows, int64_t groups, float* out, DevStatus* status,
-                              int num_sms, cudaStream_t s) {
+cudaError_t launch_gram_probe(const DevData& D, const int32_t* rows, const int32_t* centres, int64_t groups,
+                              float* out, DevStatus* status, int num_sms, cudaStream_t s) {
   if (groups <= 0) return cudaSuccess;
   // 64 KB of operands, requested as 120 KB so that one CTA (256 TMEM columns) runs per SM
   const size_t bytes = 120 * 1024;
   cudaError_t err = cudaFuncSetAttribute(gram_probe_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(bytes));
   if (err != cudaSuccess) return err;
-  const float inv_s = 1.f / D.scale;
+  const float scale = centres ? 0.5f * D.scale : D.scale;  // the prune's scale for centred rows
+  const float inv_s = 1.f / scale;
   const int64_t grid = std::min<int64_t>(groups, num_sms);
-  gram_probe_kernel<<<unsigned(grid), 128, bytes, s>>>(D.X, D.row_bytes, D.scale, inv_s * inv_s, rows, groups, out,
-                                                       status);
+  gram_probe_kernel<<<unsigned(grid), 128, bytes, s>>>(D.X, D.row_bytes, scale, inv_s * inv_s, rows, centres, groups,
+                                                       out, status);
   return cudaGetLastError();
 }
 
@@ -1574,8 +1624,10 @@ cudaError_t launch_prune(const PruneLaunch& L, cudaStream_t s) {
   PruneArgs a{};
   a.X = L.data.X;
   a.row_bytes = L.data.row_bytes;
-  a.scale = L.data.scale;
-  a.inv_s = 1.f / L.data.scale;
+  // float rows enter centred on the pivot, |x - p| <= 2 max |x|: half the
+  // data's power-of-two scale keeps them in [-1, 1]
+  a.scale = L.data.dtype == kF32 ? 0.5f * L.data.scale : L.data.scale;
+  a.inv_s = 1.f / a.scale;
   a.inv_s2 = a.inv_s * a.inv_s;
   a.sqrt_d = std::sqrt(float(L.data.d)) * 1.0001f;
   a.d = L.data.d;

@@ -661,7 +661,7 @@ rp_status tune_async_impl(rp_ctx* c, rp_graph src, const double* alphas, const i
 rp_status run_knn(rp_ctx* c, const Dataset& D, const uint8_t* Q, int64_t nq, int32_t k, int32_t* ids, float* dists) {
   const bool tc_ok = knn_tc_eligible(D.dtype, D.d, k);
   if (c->knn_method == RP_KNN_TENSOR && !tc_ok)
-    return fail(c, RP_EINVAL, "the tensor-core kNN needs k <= 128 and uint8 rows of d <= 128 or float rows of d <= 256");
+    return fail(c, RP_EINVAL, "the tensor-core kNN needs k <= 128 and uint8 rows of d <= 128 or float rows of d <= 128");
   if (tc_ok && c->knn_method != RP_KNN_CUDA_CORE) {
     const size_t bytes = knn_tc_scratch_bytes(D.dtype, D.d, D.n, Q ? nq : 0, c->num_sms);
     void* scratch = nullptr;
@@ -1449,7 +1449,8 @@ rp_status rp_tune_batch(rp_ctx* c, rp_graph src, const double* alphas, const int
   return tune_impl(c, src, alphas, Rs, T, variant, outs, true);
 }
 
-rp_status rp_debug_gram(rp_ctx* c, rp_graph g, const int32_t* rows, int64_t nrows, float* out) {
+rp_status rp_debug_gram(rp_ctx* c, rp_graph g, const int32_t* rows, const int32_t* centres, int64_t nrows,
+                        float* out) {
   if (!c) return RP_EINVAL;
   std::lock_guard<std::mutex> lk(c->mu);
   cudaSetDevice(c->device);
@@ -1459,21 +1460,29 @@ rp_status rp_debug_gram(rp_ctx* c, rp_graph g, const int32_t* rows, int64_t nrow
   if (!rows || !out || nrows < 0 || nrows % 128 != 0) return fail(c, RP_EINVAL, "need rows and out, nrows a multiple of 128");
   for (int64_t i = 0; i < nrows; ++i)
     if (rows[i] < 0 || rows[i] >= G->n) return fail(c, RP_EINVAL, "rows[%lld]=%d outside [0, n)", (long long)i, rows[i]);
+  const int64_t ncen = centres ? nrows / 64 : 0;
+  for (int64_t i = 0; i < ncen; ++i)
+    if (centres[i] < 0 || centres[i] >= G->n)
+      return fail(c, RP_EINVAL, "centres[%lld]=%d outside [0, n)", (long long)i, centres[i]);
   if (nrows == 0) return RP_OK;
   int32_t* drows = nullptr;
   float* dout = nullptr;
-  rp_status s = dalloc(c, reinterpret_cast<void**>(&drows), size_t(nrows) * 4);
+  const size_t row_bytes = size_t(nrows + ncen) * 4;  // rows, then the centres
+  rp_status s = dalloc(c, reinterpret_cast<void**>(&drows), row_bytes);
   if (s == RP_OK) s = dalloc(c, reinterpret_cast<void**>(&dout), size_t(nrows) * 128 * 4);
   cudaError_t ce = cudaSuccess;
   if (s == RP_OK) {
     ce = cudaMemcpyAsync(drows, rows, size_t(nrows) * 4, cudaMemcpyHostToDevice, c->stream);
+    if (ce == cudaSuccess && ncen)
+      ce = cudaMemcpyAsync(drows + nrows, centres, size_t(ncen) * 4, cudaMemcpyHostToDevice, c->stream);
     if (ce == cudaSuccess)
-      ce = launch_gram_probe(G->data->dev(), drows, nrows / 128, dout, c->status, c->num_sms, c->stream);
+      ce = launch_gram_probe(G->data->dev(), drows, ncen ? drows + nrows : nullptr, nrows / 128, dout, c->status,
+                             c->num_sms, c->stream);
     if (ce == cudaSuccess) ce = cudaMemcpyAsync(out, dout, size_t(nrows) * 128 * 4, cudaMemcpyDeviceToHost, c->stream);
     if (ce == cudaSuccess) ce = cudaStreamSynchronize(c->stream);
     c->kernel_launches += 1;
   }
-  dfree(c, drows, size_t(nrows) * 4);
+  dfree(c, drows, row_bytes);
   dfree(c, dout, size_t(nrows) * 128 * 4);
   if (s != RP_OK) return s;
   if (ce != cudaSuccess) return fail(c, RP_ECUDA, "Gram probe: %s", cudaGetErrorString(ce));

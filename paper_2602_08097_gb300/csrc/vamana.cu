@@ -10,7 +10,7 @@
 //   gets N_out(p) <- RobustPrune(p, V_p, alpha, R) (Algorithm 1, sorted; its
 //   first step adds the current N_out(p) and drops p).  Then every point j
 //   kept by some p of the batch takes those p as back edges, ascending by id
-//   (at most 4096 of them, the smallest ids), after its current list; a list
+//   (at most 512 of them, the smallest ids), after its current list; a list
 //   that grows past R is pruned again, N_out(j) <- RobustPrune(j, merged,
 //   alpha, R).
 //
@@ -31,7 +31,7 @@ namespace rpk {
 namespace {
 
 constexpr int kWarpsPerBlock = 8;
-constexpr int kMaxSenders = 4096;  // back edges a point takes per batch (the smallest sender ids)
+constexpr int kMaxSenders = 512;  // back edges a point takes per batch (the smallest sender ids)
 
 __device__ __forceinline__ unsigned lanemask_lt() {
   unsigned m;
@@ -148,12 +148,16 @@ __global__ void back_scatter_kernel(const int32_t* __restrict__ pts, int64_t nb,
   }
 }
 
-// Back edges, step 3, one warp per target j: its senders in ascending order
-// (rank of each among distinct ids), the merged list N_out(j) followed by
-// the senders not already in it; a list of at most R points is written at
-// once, a longer one is queued (ov_*) for RobustPrune.  pend[j] is reset.
+// Back edges, step 3, one warp per target j: its kMaxSenders smallest senders
+// in ascending order, the merged list N_out(j) followed by those not already
+// in it; a list of at most R points is written at once, a longer one is
+// queued (ov_*) for RobustPrune.  pend[j] is reset.  The senders of j are
+// distinct points.  Up to kMaxSenders of them are ordered by rank (the count
+// of smaller ones); from more, a bisection on the id value first finds the
+// bound below which exactly kMaxSenders lie and moves those to the front of
+// the segment (in place, in their order there), which are then ranked.
 __global__ void back_merge_kernel(const int32_t* __restrict__ jlist, int64_t nj, const int64_t* __restrict__ seg_ptr,
-                                  const int32_t* __restrict__ seg, int32_t* __restrict__ sorted,
+                                  int32_t* __restrict__ seg, int32_t* __restrict__ sorted,
                                   int32_t* __restrict__ nbr, int32_t* __restrict__ deg, int R,
                                   int32_t* __restrict__ pend, int32_t* __restrict__ ov_raw,
                                   int32_t* __restrict__ ov_slot, int32_t* __restrict__ ov_cnt,
@@ -164,19 +168,43 @@ __global__ void back_merge_kernel(const int32_t* __restrict__ jlist, int64_t nj,
     const int32_t j = jlist[s];
     const int64_t a = seg_ptr[s];
     const int m = int(seg_ptr[s + 1] - a);
-    for (int x = lane; x < m; x += 32) {
+    // a point takes at most kMaxSenders back edges per batch (the smallest
+    // sender ids), which bounds every list the prune sees
+    const int ms = m < kMaxSenders ? m : kMaxSenders;
+    if (m > ms) {
+      // the least bound t with #{senders < t} >= ms: then exactly ms lie below it
+      long long lo = 0, hi = 0x80000000ll;  // #{< lo} < ms <= #{< hi}
+      while (hi - lo > 1) {
+        const long long mid = (lo + hi) >> 1;
+        int cnt = 0;
+        for (int x = lane; x < m; x += 32) cnt += seg[a + x] < mid;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
+        if (cnt >= ms) hi = mid;
+        else lo = mid;
+      }
+      int w = 0;  // move the ms senders below hi to the front (w <= x: in place)
+      for (int x0 = 0; x0 < m; x0 += 32) {
+        const int x = x0 + lane;
+        const int32_t v = x < m ? seg[a + x] : 0;
+        const bool take = x < m && v < hi;
+        const unsigned msk = __ballot_sync(0xffffffffu, take);
+        __syncwarp();
+        if (take) seg[a + w + __popc(msk & lanemask_lt())] = v;
+        w += __popc(msk);
+        __syncwarp();
+      }
+    }
+    for (int x = lane; x < ms; x += 32) {
       const int32_t v = seg[a + x];
       int r = 0;
-      for (int y = 0; y < m; ++y) r += seg[a + y] < v;
+      for (int y = 0; y < ms; ++y) r += seg[a + y] < v;
       sorted[a + r] = v;
     }
     __syncwarp();
     const int dj = deg[j];
     int32_t* nj_row = nbr + int64_t(j) * R;
-    // the senders not already in N_out(j), in ascending order; a point takes at
-    // most kMaxSenders of them per batch (the smallest ids), which bounds every
-    // list the prune sees
-    const int ms = m < kMaxSenders ? m : kMaxSenders;
+    // the senders not already in N_out(j), in ascending order
     int fresh = 0;
     for (int x0 = 0; x0 < ms; x0 += 32) {
       const int x = x0 + lane;
@@ -269,7 +297,7 @@ cudaError_t launch_back_scatter(const int32_t* pts, int64_t nb, const int32_t* n
   return cudaGetLastError();
 }
 
-cudaError_t launch_back_merge(const int32_t* jlist, int64_t nj, const int64_t* seg_ptr, const int32_t* seg,
+cudaError_t launch_back_merge(const int32_t* jlist, int64_t nj, const int64_t* seg_ptr, int32_t* seg,
                               int32_t* sorted, int32_t* nbr, int32_t* deg, int R, int32_t* pend, int32_t* ov_raw,
                               int32_t* ov_slot, int32_t* ov_cnt, int32_t* n_ov, cudaStream_t s) {
   back_merge_kernel<<<grid_warps(nj), kWarpsPerBlock * 32, 0, s>>>(jlist, nj, seg_ptr, seg, sorted, nbr, deg, R, pend,

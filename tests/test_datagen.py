@@ -41,3 +41,26 @@ def test_prefix_across_a_chunk_boundary():
     big = datagen.dataset("sift", datagen.CHUNK + 100)
     assert np.array_equal(datagen.dataset("sift", 1000), big[:1000])
     assert np.array_equal(datagen.dataset("sift", datagen.CHUNK + 7), big[:datagen.CHUNK + 7])
+
+
+def _lid_mle(X, nq=200, k=20):
+    # Levina-Bickel maximum-likelihood estimate of the local intrinsic
+    # dimension from k nearest neighbours, median over the first nq rows
+    Q = X[:nq]
+    d2 = np.einsum("ij,ij->i", Q, Q)[:, None] + np.einsum("ij,ij->i", X, X)[None, :] - 2.0 * Q @ X.T
+    d2[np.arange(nq), np.arange(nq)] = np.inf  # not its own neighbour
+    r = np.sqrt(np.maximum(np.sort(np.partition(d2, k, axis=1)[:, :k], axis=1), 1e-300))
+    return float(np.median(-1.0 / np.mean(np.log(r[:, :-1] / r[:, -1:]), axis=1)))
+
+
+def test_deep_intrinsic_dimension_is_low():
+    # The deep mixture's components spread like PCA outputs (s_i = 1.5 i^-0.75),
+    # so its local intrinsic dimension sits far below d = 96, and far below that
+    # of isotropic components (sigma 0.5) around centres drawn the same way.
+    n = 20000
+    X = datagen.dataset("deep", n).astype(np.float64)
+    rng = np.random.default_rng(5)
+    Y = rng.normal(0.0, 1.0, (256, 96))[rng.integers(0, 256, n)] + 0.5 * rng.normal(0.0, 1.0, (n, 96))
+    Y /= np.linalg.norm(Y, axis=1, keepdims=True)
+    lx, ly = _lid_mle(X), _lid_mle(Y)
+    assert 4.0 < lx < 12.0 and ly > 20.0 and lx < 0.5 * ly

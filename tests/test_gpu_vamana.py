@@ -98,3 +98,30 @@ def test_rejects_bad_arguments(ctx):
         with pytest.raises(rp.RPError):
             rp.rp_build_vamana(ctx, data, args["alphas"], args["R"], args["L"], args["vcap"], args["max_batch"],
                                args["perm"])
+
+
+def test_hub_takes_at_most_512_back_edges_a_batch(ctx):
+    # Point 0 sits at the centre of a thin shell of 2,999 points in 64 dimensions,
+    # nearer to each of them than any other point, so every point keeps it (first
+    # in its processing order), and the batches of 1,024 and 953 points name it
+    # that many times: its senders are cut to the 512 smallest ids (found by the
+    # bisection on the id value) before the merge and the prune.
+    rng = np.random.default_rng(11)
+    n = 3000
+    U = rng.normal(size=(n, 64))
+    U /= np.linalg.norm(U, axis=1, keepdims=True)
+    X = (U * (1.0 + 0.05 * rng.random((n, 1)))).astype(np.float32)
+    X[0] = 0.0
+    perm = rng.permutation(n).astype(np.int32)
+    data = rp.rp_load_graph(ctx, X)
+    start = rp.rp_graph_info(ctx, data)["start"]
+    assert start == oracle.medoid(X) == 0
+    for alphas in ([1.2], [1.0, 1.2]):
+        v, cut = rp.rp_build_vamana(ctx, data, alphas, 16, 32, 128, 2048, perm)
+        got_rp, got_col = rp.rp_graph_export(ctx, v)
+        ref_rp, ref_col, ref_cut = oracle.vamana(X, perm, alphas, 16, 32, 128, 2048, start)
+        assert all(0 in ref_col[ref_rp[p]:ref_rp[p + 1]] for p in range(1, n))
+        assert cut == ref_cut
+        assert np.array_equal(got_rp, ref_rp) and np.array_equal(got_col, ref_col)
+        rp.rp_graph_free(ctx, v)
+    rp.rp_graph_free(ctx, data)
