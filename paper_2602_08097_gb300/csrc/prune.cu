@@ -305,7 +305,8 @@ struct TcLayout {
   static constexpr size_t p_k64 = p_sk + size_t(MAXM) * 8;       // [MAXM] binary64 keys in stored order
   static constexpr size_t p_cq = p_k64 + size_t(MAXM) * 8;        // [MAXM] float4 per column (float rows)
   static constexpr size_t p_srt = p_cq + size_t(MAXM) * 16;       // [MAXM] float keys by rank (float rows)
-  static constexpr size_t p_bytes = p_srt + size_t(MAXM) * 4;
+  static constexpr size_t p_st = p_srt + size_t(MAXM) * 4;        // [MAXM] stored position of each rank (float rows)
+  static constexpr size_t p_bytes = p_st + size_t(MAXM) * 4;
   static_assert(p_qlo % 16 == 0 && p_qhi % 16 == 0 && p_cq % 16 == 0 && p_bytes % 16 == 0, "16-byte reads");
   static constexpr size_t off_prod = off_slots + 2 * NG * s_bytes;
   // small words: node/degree/row start per (slot, group), the claim queue's
@@ -313,11 +314,15 @@ struct TcLayout {
   static constexpr size_t off_misc = off_prod + NG * p_bytes;
   static constexpr size_t q_node = 256, q_deg = q_node + 32 * 4, q_e0 = q_deg + 32 * 4;
   static constexpr size_t misc_bytes = q_e0 + 32 * 8;
-  // float rows: the slot's undecided (row, column, target) triples, resolved
-  // after the mask pass by all producer threads at once
+  // float rows: per slot, the undecided (row, column, first alpha) entries,
+  // resolved by the consumer warp before its scan of the slot
   static constexpr int rq_cap = NOP == 2 ? 1024 : 0;
   static constexpr size_t off_rq = off_misc + misc_bytes;
-  static constexpr size_t bytes = (off_rq + size_t(rq_cap) * 4 + 127) & ~size_t(127);
+  static constexpr size_t bytes = (off_rq + 2 * size_t(rq_cap) * 4 + 127) & ~size_t(127);
+  // float rows: a group's Gram staged in shared memory over the operands (which
+  // the MMA has read by then), MAXM x MAXM floats in stored order, each row
+  // rotated by its index so that a warp's accesses spread over the banks
+  static_assert(NOP == 1 || size_t(NG) * MAXM * MAXM * 4 <= off_slots, "staged Gram fits over the operands");
 };
 
 // floor(1e6 k / A2) for integers, exactly: a single-precision estimate (off
@@ -439,8 +444,8 @@ __global__ void __launch_bounds__(160, tc_min_ctas<DT, MAXM, TB>()) prune_tc_ker
     for (int k = 0;; ++k) {
       const int s = k & 1;
       named_sync(kBarFree + s, 160);  // the consumer is done with this slot
-      // every producer has left the previous slot, and with it that slot's queue
-      if (DT == kF32 && r == 0) rq_count[s ^ 1] = 0;
+      // the consumer has resolved this slot's queue of two rounds ago: empty it
+      if (DT == kF32 && r == 0) rq_count[s] = 0;
       if (warp == 0) {
         // next NG nodes from the claim queue; warp 0 refills it kClaim nodes at
         // a time (one atomic, the row bounds loaded by all lanes at once)
@@ -577,12 +582,27 @@ __global__ void __launch_bounds__(160, tc_min_ctas<DT, MAXM, TB>()) prune_tc_ker
       }
       // ---- a4 processing order: the rank of (d2(p, x), id) among the m
       // candidates is x's place in Algorithm 1's argmin sequence (stored order
-      // for the unsorted variant).  Rows, thresholds and masks below are all
-      // laid out by rank.
+      // for the unsorted variant).  Ids, keys, thresholds and masks below are
+      // laid out by rank; uint8 operand rows too, float operand rows stay at
+      // the stored position.
       unsigned long long* sk = reinterpret_cast<unsigned long long*>(pb + L::p_sk);  // stored order
       const unsigned long long my_sk = live_row ? (Acc<DT>::bits(kacc) << 32) | unsigned(my_id) : ~0ull;
       sk[t] = my_sk;
+      // Float rows of one slice have their operands in place: the Gram (a5)
+      // starts now and runs while the ranks are found.
+      const bool early_mma = DT == kF32 && nslices == 1;
+      if (early_mma) {
+        fence_async_smem();
+        tc_fence_before();
+      }
       named_sync(kBarProd, 128);
+      if (early_mma) {
+        tc_fence_after();
+        if (r == 0) {
+          issue_gram_slice<true>(tmem, opnd, int(elems), false);
+          umma_commit(mbar);
+        }
+      }
       int rank = t;
       // A list that Algorithm 1 wrote is already in its processing order
       // ((d2, id) ascending): then every rank is the stored position.  Checked,
@@ -684,38 +704,352 @@ __global__ void __launch_bounds__(160, tc_min_ctas<DT, MAXM, TB>()) prune_tc_ker
           norm[rank] = nacc;
         }
       }
-      // ---- f16 operand row at position rank (rows past the degree stay zero);
-      // a5 Gram on tcgen05, one MMA chain per 128-dim slice
-      const int orow = g * MAXM + rank;
-      for (int sl = 0; sl < nslices; ++sl) {
-        const int64_t rem = elems - int64_t(sl) * 128;
-        const int kd = int(rem < 128 ? rem : 128);  // a multiple of 16 here
-        if constexpr (DT == kU8) {
-          if (nslices > 1) {
+      if constexpr (DT == kU8) {
+        // ---- f16 operand row at position rank (rows past the degree stay zero);
+        // a5 Gram on tcgen05, one MMA chain per 128-dim slice
+        const int orow = g * MAXM + rank;
+        for (int sl = 0; sl < nslices; ++sl) {
+          const int64_t rem = elems - int64_t(sl) * 128;
+          const int kd = int(rem < 128 ? rem : 128);  // a multiple of 16 here
+          if constexpr (DT == kU8) {
+            if (nslices > 1) {
+#pragma unroll
+              for (int c = 0; c < 8; ++c) {
+                xs[c] = make_uint4(0, 0, 0, 0);
+                if (live_row && c < kd / 16) xs[c] = __ldg(reinterpret_cast<const uint4*>(xrow + sl * 128) + c);
+              }
+            }
 #pragma unroll
             for (int c = 0; c < 8; ++c) {
-              xs[c] = make_uint4(0, 0, 0, 0);
-              if (live_row && c < kd / 16) xs[c] = __ldg(reinterpret_cast<const uint4*>(xrow + sl * 128) + c);
+              if (c >= kd / 16) break;
+              const uint4 x = xs[c];
+              const unsigned w4[4] = {x.x, x.y, x.z, x.w};
+              uint32_t o[8];
+#pragma unroll
+              for (int q = 0; q < 4; ++q) {
+                o[2 * q] = u8x2_f16x2(w4[q], 0x4140u);      // bytes 0, 1
+                o[2 * q + 1] = u8x2_f16x2(w4[q], 0x4342u);  // bytes 2, 3
+              }
+              const int kc0 = 2 * c;
+              *reinterpret_cast<uint4*>(opnd + (kc0 * 16 + orow / 8) * 128 + (orow % 8) * 16) =
+                  make_uint4(o[0], o[1], o[2], o[3]);
+              *reinterpret_cast<uint4*>(opnd + ((kc0 + 1) * 16 + orow / 8) * 128 + (orow % 8) * 16) =
+                  make_uint4(o[4], o[5], o[6], o[7]);
+            }
+          } else if (!(nslices == 1 && in_order)) {  // else written with the keys
+#pragma unroll 4
+            for (int c = 0; c < kd / 8; ++c) {
+              uint4 x0 = make_uint4(0, 0, 0, 0), x1 = x0, y0 = x0, y1 = x0;
+              if (live_row) {  // rows past the degree stay zero
+                const uint4* xq = reinterpret_cast<const uint4*>(xrow + int64_t(sl) * 512) + 2 * c;
+                const uint4* pq = reinterpret_cast<const uint4*>(prow + int64_t(sl) * 512) + 2 * c;
+                x0 = __ldg(xq);
+                x1 = __ldg(xq + 1);
+                y0 = __ldg(pq);
+                y1 = __ldg(pq + 1);
+              }
+              const float xv[8] = {__uint_as_float(x0.x), __uint_as_float(x0.y), __uint_as_float(x0.z),
+                                   __uint_as_float(x0.w), __uint_as_float(x1.x), __uint_as_float(x1.y),
+                                   __uint_as_float(x1.z), __uint_as_float(x1.w)};
+              const float pv[8] = {__uint_as_float(y0.x), __uint_as_float(y0.y), __uint_as_float(y0.z),
+                                   __uint_as_float(y0.w), __uint_as_float(y1.x), __uint_as_float(y1.y),
+                                   __uint_as_float(y1.z), __uint_as_float(y1.w)};
+              store_split8_centred(opnd, orow, c, xv, pv, a.scale);
             }
           }
-#pragma unroll
-          for (int c = 0; c < 8; ++c) {
-            if (c >= kd / 16) break;
-            const uint4 x = xs[c];
-            const unsigned w4[4] = {x.x, x.y, x.z, x.w};
-            uint32_t o[8];
-#pragma unroll
-            for (int q = 0; q < 4; ++q) {
-              o[2 * q] = u8x2_f16x2(w4[q], 0x4140u);      // bytes 0, 1
-              o[2 * q + 1] = u8x2_f16x2(w4[q], 0x4342u);  // bytes 2, 3
-            }
-            const int kc0 = 2 * c;
-            *reinterpret_cast<uint4*>(opnd + (kc0 * 16 + orow / 8) * 128 + (orow % 8) * 16) =
-                make_uint4(o[0], o[1], o[2], o[3]);
-            *reinterpret_cast<uint4*>(opnd + ((kc0 + 1) * 16 + orow / 8) * 128 + (orow % 8) * 16) =
-                make_uint4(o[4], o[5], o[6], o[7]);
+          const bool last = sl == nslices - 1;
+          fence_async_smem();
+          tc_fence_before();
+          named_sync(kBarProd, 128);
+          tc_fence_after();
+          if (r == 0) {
+            issue_gram_slice<DT == kF32>(tmem, opnd, kd, sl > 0);
+            umma_commit(mbar);
           }
-        } else if (!(nslices == 1 && in_order)) {  // else written with the keys
+          if (last) {
+            // while the MMA runs: the thresholds of column `rank` for every target
+            // (uint8) or every distinct alpha (float) (a6)
+            if (live_row) {
+#pragma unroll
+              for (int u = 0; u < TB; ++u) {
+                if (u >= (DT == kF32 ? a.TA : T)) break;
+                const int32_t Au = DT == kF32 ? a.Ad[u] : a.A[u];
+                const unsigned long long A2 = static_cast<unsigned long long>(Au) * Au;
+                if constexpr (DT == kU8) {
+                  // v is removed by row u'  <=>  A2 d2(u', v) <= 1e6 d2(p, v)
+                  //   <=>  2 G(u', v) - |u'|^2 >= |v|^2 - floor(1e6 d2(p, v) / A2)
+                  // (every quantity an integer below 2^24, exact in f32)
+                  const unsigned thr = exact_threshold(kacc, A2, a.inv_A2[u]);
+                  qlo[u * MAXM + rank] = float(int(nacc) - int(thr));
+                } else {
+                  // float thresholds per column, distinct alphas contiguous.  The
+                  // last factor of each (1 -+ 1e-6) covers the roundings of the
+                  // pair's d2 - err and d2 + err, compared against them directly.
+                  const float A2f = float(A2);
+                  qlo[rank * L::TB4 + u] =
+                      1.0e6f * (kacc * (1.0f - E_rel) - E_abs) * 0.9999995f / A2f * 0.9999995f * 0.999999f;
+                  qhi[rank * L::TB4 + u] =
+                      1.0e6f * (kacc * (1.0f + E_rel) + E_abs) * 1.0000005f / A2f * 1.0000005f * 1.000001f;
+                }
+              }
+              if constexpr (DT == kF32) {
+                // padding past the last alpha never counts (hi < -inf, lo > -inf)
+                for (int u = a.TA; u < L::TB4; ++u) qlo[rank * L::TB4 + u] = qhi[rank * L::TB4 + u] = -INFINITY;
+                cq[rank] = make_float4(kacc, sqrtf(kacc), 0.f, 0.f);  // the column's centred norm^2 and its root
+              }
+            }
+          }
+          if (last && next_id >= 0) {
+            const char* nrow = reinterpret_cast<const char*>(a.X + int64_t(next_id) * a.row_bytes);
+            for (int64_t off = 0; off < a.row_bytes; off += 128) asm volatile("prefetch.global.L2 [%0];" ::"l"(nrow + off));
+          }
+          const bool ok = mbar_wait(mbar, phase, 1 << 24);
+          if (prod_sync_or(!ok)) {  // the MMA never completed: report, stop after this slot (uniform)
+            if (r == 0) raise_status(a.status, kDevOverflow, -2);
+            dead = true;
+          }
+          phase ^= 1u;
+          tc_fence_after();
+        }
+
+        // ---- a6: thread t turns Gram row t (TMEM lane t: the candidate of rank
+        // t) into one mask per target of the ranks it would remove.
+        // tcgen05.ld is warp-collective: every lane issues it, live rows use it.
+        if (!dead) {
+          unsigned long long mk[TB][MW];
+#pragma unroll
+          for (int u = 0; u < TB; ++u)
+#pragma unroll
+            for (int w = 0; w < MW; ++w) mk[u][w] = 0;
+          const float nt = live_row ? float(norm[t]) : 0.f;
+          const float st = DT == kF32 && live_row ? sn[t] : 0.f;
+          // A row only removes candidates after it in the processing order (the
+          // scan has decided every earlier one), so a warp whose rows all come
+          // after a 32-column chunk skips it (a uniform choice: the TMEM read is
+          // warp-collective).  Bits set for earlier columns are harmless too.
+          const int first_col = 32 * (warp % (MAXM / 32));
+          if constexpr (DT == kU8) {
+            // Columns at or past the degree hold no candidate: the bits set there
+            // can never meet a live bit in the scan, so they are not tested for.
+#pragma unroll
+            for (int c0 = 0; c0 < MAXM; c0 += 32) {
+              if (c0 < first_col) continue;
+              uint32_t v[32];
+              tmem_ld32(tmem + (uint32_t(32 * warp) << 16) + uint32_t(g * MAXM + c0), v);
+              tmem_ld_wait();
+              if (live_row) {
+                // x = 2 G - |t|^2 lies in [-|t|^2, |c|^2], an integer below 2^24,
+                // exact; q too.  x - q keeps its sign when rounded and is +0 when
+                // x = q, so its sign bit is exactly "x < q": not removed.  Columns
+                // go in last to first, so column c0 + j ends at bit j.
+                uint32_t nb[TB];
+#pragma unroll
+                for (int u = 0; u < TB; ++u) nb[u] = 0u;
+#pragma unroll
+                for (int j4 = 28; j4 >= 0; j4 -= 4) {
+                  float x[4];
+#pragma unroll
+                  for (int q = 0; q < 4; ++q) x[q] = fmaf(2.f, __uint_as_float(v[j4 + q]), -nt);
+#pragma unroll
+                  for (int u = 0; u < TB; ++u) {
+                    if (u >= T) break;
+                    const float4 q4 = *reinterpret_cast<const float4*>(qlo + u * MAXM + c0 + j4);
+                    nb[u] = __funnelshift_l(__float_as_uint(x[3] - q4.w), nb[u], 1);
+                    nb[u] = __funnelshift_l(__float_as_uint(x[2] - q4.z), nb[u], 1);
+                    nb[u] = __funnelshift_l(__float_as_uint(x[1] - q4.y), nb[u], 1);
+                    nb[u] = __funnelshift_l(__float_as_uint(x[0] - q4.x), nb[u], 1);
+                  }
+                }
+#pragma unroll
+                for (int u = 0; u < TB; ++u) mk[u][c0 >> 6] |= static_cast<unsigned long long>(~nb[u]) << (c0 & 63);
+              }
+            }
+          } else {
+            // Float rows: for every column c after row t, ts = how many distinct
+            // alphas surely remove c and tp = how many may (both prefixes: the
+            // alphas ascend and the thresholds fall with them).  ts is kept as NB
+            // bit planes over the columns; pairs with ts < tp go to the recheck
+            // queue.  The code is branch-free per column, so the sixteen columns
+            // of a TMEM read overlap; each column's bits go first into 16-bit
+            // chunk words at constant positions.
+            constexpr int NB = TB <= 1 ? 1 : TB <= 3 ? 2 : TB <= 7 ? 3 : TB <= 15 ? 4 : 5;
+            unsigned long long pl[NB][MW];
+#pragma unroll
+            for (int b = 0; b < NB; ++b)
+#pragma unroll
+              for (int w = 0; w < MW; ++w) pl[b][w] = 0;
+            unsigned long long und[MW];
+#pragma unroll
+            for (int w = 0; w < MW; ++w) und[w] = 0;
+            const int TA = a.TA;
+            // the d2 error bound as two multiply-adds: err = |c| At + |c|^2 eps_n + Bt
+            const float At = 2.f * eps_ip * st * 1.0009765625f + sub_abs;
+            const float Bt = sub_abs * st + eps_n * nt + err_abs;
+            const float4* ql4 = reinterpret_cast<const float4*>(qlo);
+            const float4* qh4 = reinterpret_cast<const float4*>(qhi);
+            const int cend = (m + 15) & ~15;  // the same for every lane of the warp (one node)
+#pragma unroll 1
+            for (int c0 = first_col; c0 < cend; c0 += 16) {
+              uint32_t v[16], v2[16];
+              tmem_ld8(tmem + (uint32_t(32 * warp) << 16) + uint32_t(g * MAXM + c0), *reinterpret_cast<uint32_t(*)[8]>(v));
+              tmem_ld8(tmem + (uint32_t(32 * warp) << 16) + uint32_t(g * MAXM + c0 + 8),
+                       *reinterpret_cast<uint32_t(*)[8]>(v + 8));
+              tmem_ld8(tmem + (uint32_t(32 * warp) << 16) + uint32_t(128 + g * MAXM + c0),
+                       *reinterpret_cast<uint32_t(*)[8]>(v2));
+              tmem_ld8(tmem + (uint32_t(32 * warp) << 16) + uint32_t(128 + g * MAXM + c0 + 8),
+                       *reinterpret_cast<uint32_t(*)[8]>(v2 + 8));
+              tmem_ld_wait();
+              uint32_t cp[NB], cu = 0;
+#pragma unroll
+              for (int b = 0; b < NB; ++b) cp[b] = 0;
+#pragma unroll
+              for (int j = 0; j < 16; ++j) {
+                const int c = c0 + j;
+                const float4 q = cq[c];
+                // hi hi^T + 2^-11 (cross terms), back in the rows' units (powers of two: exact scalings)
+                const float G = split_gram_value(v[j], v2[j], a.inv_s2);
+                const float dv = (nt + q.x) - 2.f * G;
+                const float err = fmaf(q.y, At, fmaf(q.x, eps_n, Bt));
+                const float lo = dv - err, hi = dv + err;
+                int ts = 0, tp = 0;
+#pragma unroll
+                for (int u4 = 0; u4 < L::TB4; u4 += 4) {
+                  if (u4 < TA) {  // uniform
+                    const float4 l4 = ql4[(c * L::TB4 + u4) / 4];
+                    const float4 h4 = qh4[(c * L::TB4 + u4) / 4];
+                    ts += int(hi < l4.x) + int(hi < l4.y) + int(hi < l4.z) + int(hi < l4.w);
+                    tp += int(!(lo > h4.x)) + int(!(lo > h4.y)) + int(!(lo > h4.z)) + int(!(lo > h4.w));
+                  }
+                }
+                const bool valid = live_row && c > t && c < m;
+                ts = valid ? ts : 0;
+                tp = valid ? tp : 0;
+#pragma unroll
+                for (int b = 0; b < NB; ++b) cp[b] |= ((uint32_t(ts) >> b) & 1u) << j;
+                cu |= uint32_t(tp > ts) << j;
+              }
+              const int sh = c0 & 63;
+              const bool w1 = MW > 1 && c0 >= 64;
+#pragma unroll
+              for (int b = 0; b < NB; ++b) {
+                const unsigned long long x = static_cast<unsigned long long>(cp[b]) << sh;
+                pl[b][0] |= w1 ? 0ull : x;
+                pl[b][MW - 1] |= w1 ? x : 0ull;
+              }
+              const unsigned long long xu = static_cast<unsigned long long>(cu) << sh;
+              und[0] |= w1 ? 0ull : xu;
+              und[MW - 1] |= w1 ? xu : 0ull;
+            }
+            // open pairs (rare): the alphas from ts on go to the recheck, one entry
+            // per pair, which decides them in ascending order from one distance
+            // (those that in fact keep the pair say so)
+#pragma unroll
+            for (int w = 0; w < MW; ++w) {
+              while (und[w]) {
+                const int cb = __ffsll(static_cast<long long>(und[w])) - 1;
+                und[w] &= und[w] - 1;
+                const int c = 64 * w + cb;
+                int u0 = 0;
+#pragma unroll
+                for (int b = 0; b < NB; ++b) u0 |= int((pl[b][w] >> cb) & 1ull) << b;
+                // queued and resolved after this pass by all producer threads at
+                // once; decided here if the queue is full
+                const int qi = atomicAdd(rq_count + s, 1);
+                if (qi < L::rq_cap) {
+                  rq[qi] = (unsigned(g * MAXM + t) << 16) | (unsigned(c) << 5) | unsigned(u0);
+                } else {
+                  // the binary64 decision is monotone in alpha: kept at u means kept
+                  // at every larger alpha, removed at u means removed at every
+                  // smaller one, so ts for this column becomes the first u that keeps
+                  const int u1 = recheck_prefix_cold(a, ids, key, key64, t, c, u0, TA, ppt, E_rel, E_abs);
+                  n_rechecks += recheck_tests(u0, u1, TA);
+                  const unsigned long long bit = 1ull << cb;
+#pragma unroll
+                  for (int b = 0; b < NB; ++b) {
+                    const unsigned long long m_b = ((u1 >> b) & 1) ? bit : 0ull;
+                    pl[b][w] = (pl[b][w] & ~bit) | m_b;
+                  }
+                }
+              }
+            }
+            // planes -> one row mask per distinct alpha: bit c of mask u is [ts(t, c) > u]
+            if (live_row) {
+#pragma unroll
+              for (int u = 0; u < TB; ++u) {
+                if (u >= TA) break;
+#pragma unroll
+                for (int w = 0; w < MW; ++w) {
+                  unsigned long long gt = 0, eq = ~0ull;
+#pragma unroll
+                  for (int b = NB - 1; b >= 0; --b) {
+                    if ((u >> b) & 1) {
+                      eq &= pl[b][w];
+                    } else {
+                      gt |= eq & pl[b][w];
+                      eq &= ~pl[b][w];
+                    }
+                  }
+                  mk[u][w] |= gt;
+                }
+              }
+            }
+          }
+          if (live_row) {
+#pragma unroll
+            for (int u = 0; u < TB; ++u) {
+              if (u >= (DT == kF32 ? a.TA : T)) break;
+#pragma unroll
+              for (int w = 0; w < MW; ++w) masks[(u * MAXM + t) * MW + w] = mk[u][w];
+            }
+          }
+        }
+        if (dead && t == 0) misc[s * 2 + g] = -1;  // nothing valid in this slot
+        tc_fence_before();
+        named_sync(kBarProd, 128);  // every producer's masks and TMEM reads are done
+        tc_fence_after();
+        if constexpr (DT == kF32) {
+          // the queued pairs, one per thread: each alpha that removes the column
+          // sets its bit in the row's mask for that alpha
+          const int nq = min(rq_count[s], L::rq_cap);  // the same for every producer
+          if (nq > 0) {
+            for (int i = r; i < nq; i += 128) {
+              const uint32_t e = rq[i];
+              const int tr = int(e >> 16), c = int((e >> 5) & 0x7ffu), u0 = int(e & 31u);
+              const int gq = tr / MAXM, tq = tr % MAXM;
+              unsigned char* sbq = slot_base(s, gq);
+              const int u1 = recheck_prefix(a, reinterpret_cast<const int32_t*>(sbq + L::s_ids),
+                                            reinterpret_cast<const float*>(sbq + L::s_key),
+                                            reinterpret_cast<double*>(sbq + L::s_key64), tq, c, u0, a.TA,
+                                            point_of_row(a, misc[s * 2 + gq]), E_rel, E_abs);
+              n_rechecks += recheck_tests(u0, u1, a.TA);
+              unsigned long long* mrow = reinterpret_cast<unsigned long long*>(sbq + L::s_masks) + tq * MW + (c >> 6);
+              for (int u = u0; u < u1; ++u) atomicOr(mrow + u * MAXM * MW, 1ull << (c & 63));
+            }
+            named_sync(kBarProd, 128);
+          }
+        }
+      } else {
+        // ---- float rows: the operands stay at the stored position, so the
+        // Gram is in stored order; it is staged in shared memory and every pair
+        // (row before column in rank order) is decided from there, the pairs
+        // spread evenly over the 128 producer threads.
+        int* st_of = reinterpret_cast<int*>(pb + L::p_st);  // stored position of each rank
+        if (live_row) st_of[rank] = t;
+        // rows of several 128-dimension slices: one MMA chain per slice, a
+        // slice's operands written once the previous MMA has read its own
+        for (int sl = 0; !early_mma && sl < nslices; ++sl) {
+          const int64_t rem = elems - int64_t(sl) * 128;
+          const int kd = int(rem < 128 ? rem : 128);  // a multiple of 16 here
+          if (sl > 0) {
+            const bool ok = mbar_wait(mbar, phase, 1 << 24);
+            if (prod_sync_or(!ok)) {  // the MMA never completed: report, stop after this slot (uniform)
+              if (r == 0) raise_status(a.status, kDevOverflow, -2);
+              dead = true;
+            }
+            phase ^= 1u;
+            tc_fence_after();
+            if (dead) break;
+          }
 #pragma unroll 4
           for (int c = 0; c < kd / 8; ++c) {
             uint4 x0 = make_uint4(0, 0, 0, 0), x1 = x0, y0 = x0, y1 = x0;
@@ -733,279 +1067,177 @@ __global__ void __launch_bounds__(160, tc_min_ctas<DT, MAXM, TB>()) prune_tc_ker
             const float pv[8] = {__uint_as_float(y0.x), __uint_as_float(y0.y), __uint_as_float(y0.z),
                                  __uint_as_float(y0.w), __uint_as_float(y1.x), __uint_as_float(y1.y),
                                  __uint_as_float(y1.z), __uint_as_float(y1.w)};
-            store_split8_centred(opnd, orow, c, xv, pv, a.scale);
+            store_split8_centred(opnd, g * MAXM + t, c, xv, pv, a.scale);
+          }
+          fence_async_smem();
+          tc_fence_before();
+          named_sync(kBarProd, 128);
+          tc_fence_after();
+          if (r == 0) {
+            issue_gram_slice<true>(tmem, opnd, kd, sl > 0);
+            umma_commit(mbar);
           }
         }
-        const bool last = sl == nslices - 1;
-        fence_async_smem();
-        tc_fence_before();
-        named_sync(kBarProd, 128);
-        tc_fence_after();
-        if (r == 0) {
-          issue_gram_slice<DT == kF32>(tmem, opnd, kd, sl > 0);
-          umma_commit(mbar);
-        }
-        if (last) {
-          // while the MMA runs: the thresholds of column `rank` for every target
-          // (uint8) or every distinct alpha (float) (a6)
-          if (live_row) {
-#pragma unroll
-            for (int u = 0; u < TB; ++u) {
-              if (u >= (DT == kF32 ? a.TA : T)) break;
-              const int32_t Au = DT == kF32 ? a.Ad[u] : a.A[u];
-              const unsigned long long A2 = static_cast<unsigned long long>(Au) * Au;
-              if constexpr (DT == kU8) {
-                // v is removed by row u'  <=>  A2 d2(u', v) <= 1e6 d2(p, v)
-                //   <=>  2 G(u', v) - |u'|^2 >= |v|^2 - floor(1e6 d2(p, v) / A2)
-                // (every quantity an integer below 2^24, exact in f32)
-                const unsigned thr = exact_threshold(kacc, A2, a.inv_A2[u]);
-                qlo[u * MAXM + rank] = float(int(nacc) - int(thr));
-              } else {
-                // float thresholds per column, distinct alphas contiguous.  The
-                // last factor of each (1 -+ 1e-6) covers the roundings of the
-                // pair's d2 - err and d2 + err, compared against them directly.
-                const float A2f = float(A2);
-                qlo[rank * L::TB4 + u] =
-                    1.0e6f * (kacc * (1.0f - E_rel) - E_abs) * 0.9999995f / A2f * 0.9999995f * 0.999999f;
-                qhi[rank * L::TB4 + u] =
-                    1.0e6f * (kacc * (1.0f + E_rel) + E_abs) * 1.0000005f / A2f * 1.0000005f * 1.000001f;
-              }
-            }
-            if constexpr (DT == kF32) {
-              // padding past the last alpha never counts (hi < -inf, lo > -inf)
-              for (int u = a.TA; u < L::TB4; ++u) qlo[rank * L::TB4 + u] = qhi[rank * L::TB4 + u] = -INFINITY;
-              cq[rank] = make_float4(kacc, sqrtf(kacc), 0.f, 0.f);  // the column's centred norm^2 and its root
-            }
-          }
-        }
-        if (last && next_id >= 0) {
-          const char* nrow = reinterpret_cast<const char*>(a.X + int64_t(next_id) * a.row_bytes);
-          for (int64_t off = 0; off < a.row_bytes; off += 128) asm volatile("prefetch.global.L2 [%0];" ::"l"(nrow + off));
-        }
-        const bool ok = mbar_wait(mbar, phase, 1 << 24);
-        if (prod_sync_or(!ok)) {  // the MMA never completed: report, stop after this slot (uniform)
-          if (r == 0) raise_status(a.status, kDevOverflow, -2);
-          dead = true;
-        }
-        phase ^= 1u;
-        tc_fence_after();
-      }
-
-      // ---- a6: thread t turns Gram row t (TMEM lane t: the candidate of rank
-      // t) into one mask per target of the ranks it would remove.
-      // tcgen05.ld is warp-collective: every lane issues it, live rows use it.
-      if (!dead) {
-        unsigned long long mk[TB][MW];
-#pragma unroll
-        for (int u = 0; u < TB; ++u)
-#pragma unroll
-          for (int w = 0; w < MW; ++w) mk[u][w] = 0;
-        const float nt = live_row ? float(norm[t]) : 0.f;
-        const float st = DT == kF32 && live_row ? sn[t] : 0.f;
-        // A row only removes candidates after it in the processing order (the
-        // scan has decided every earlier one), so a warp whose rows all come
-        // after a 32-column chunk skips it (a uniform choice: the TMEM read is
-        // warp-collective).  Bits set for earlier columns are harmless too.
-        const int first_col = 32 * (warp % (MAXM / 32));
-        if constexpr (DT == kU8) {
-          // Columns at or past the degree hold no candidate: the bits set there
-          // can never meet a live bit in the scan, so they are not tested for.
-#pragma unroll
-          for (int c0 = 0; c0 < MAXM; c0 += 32) {
-            if (c0 < first_col) continue;
-            uint32_t v[32];
-            tmem_ld32(tmem + (uint32_t(32 * warp) << 16) + uint32_t(g * MAXM + c0), v);
-            tmem_ld_wait();
-            if (live_row) {
-              // x = 2 G - |t|^2 lies in [-|t|^2, |c|^2], an integer below 2^24,
-              // exact; q too.  x - q keeps its sign when rounded and is +0 when
-              // x = q, so its sign bit is exactly "x < q": not removed.  Columns
-              // go in last to first, so column c0 + j ends at bit j.
-              uint32_t nb[TB];
-#pragma unroll
-              for (int u = 0; u < TB; ++u) nb[u] = 0u;
-#pragma unroll
-              for (int j4 = 28; j4 >= 0; j4 -= 4) {
-                float x[4];
-#pragma unroll
-                for (int q = 0; q < 4; ++q) x[q] = fmaf(2.f, __uint_as_float(v[j4 + q]), -nt);
-#pragma unroll
-                for (int u = 0; u < TB; ++u) {
-                  if (u >= T) break;
-                  const float4 q4 = *reinterpret_cast<const float4*>(qlo + u * MAXM + c0 + j4);
-                  nb[u] = __funnelshift_l(__float_as_uint(x[3] - q4.w), nb[u], 1);
-                  nb[u] = __funnelshift_l(__float_as_uint(x[2] - q4.z), nb[u], 1);
-                  nb[u] = __funnelshift_l(__float_as_uint(x[1] - q4.y), nb[u], 1);
-                  nb[u] = __funnelshift_l(__float_as_uint(x[0] - q4.x), nb[u], 1);
-                }
-              }
-#pragma unroll
-              for (int u = 0; u < TB; ++u) mk[u][c0 >> 6] |= static_cast<unsigned long long>(~nb[u]) << (c0 & 63);
-            }
-          }
-        } else {
-          // Float rows: for every column c after row t, ts = how many distinct
-          // alphas surely remove c and tp = how many may (both prefixes: the
-          // alphas ascend and the thresholds fall with them).  ts is kept as NB
-          // bit planes over the columns; pairs with ts < tp go to the recheck
-          // queue.  The code is branch-free per column, so the sixteen columns
-          // of a TMEM read overlap; each column's bits go first into 16-bit
-          // chunk words at constant positions.
-          constexpr int NB = TB <= 1 ? 1 : TB <= 3 ? 2 : TB <= 7 ? 3 : TB <= 15 ? 4 : 5;
-          unsigned long long pl[NB][MW];
-#pragma unroll
-          for (int b = 0; b < NB; ++b)
-#pragma unroll
-            for (int w = 0; w < MW; ++w) pl[b][w] = 0;
-          unsigned long long und[MW];
-#pragma unroll
-          for (int w = 0; w < MW; ++w) und[w] = 0;
-          const int TA = a.TA;
-          // the d2 error bound as two multiply-adds: err = |c| At + |c|^2 eps_n + Bt
-          const float At = 2.f * eps_ip * st * 1.0009765625f + sub_abs;
-          const float Bt = sub_abs * st + eps_n * nt + err_abs;
-          const float4* ql4 = reinterpret_cast<const float4*>(qlo);
-          const float4* qh4 = reinterpret_cast<const float4*>(qhi);
-          const int cend = (m + 15) & ~15;  // the same for every lane of the warp (one node)
-#pragma unroll 1
-          for (int c0 = first_col; c0 < cend; c0 += 16) {
-            uint32_t v[16], v2[16];
-            tmem_ld8(tmem + (uint32_t(32 * warp) << 16) + uint32_t(g * MAXM + c0), *reinterpret_cast<uint32_t(*)[8]>(v));
-            tmem_ld8(tmem + (uint32_t(32 * warp) << 16) + uint32_t(g * MAXM + c0 + 8),
-                     *reinterpret_cast<uint32_t(*)[8]>(v + 8));
-            tmem_ld8(tmem + (uint32_t(32 * warp) << 16) + uint32_t(128 + g * MAXM + c0),
-                     *reinterpret_cast<uint32_t(*)[8]>(v2));
-            tmem_ld8(tmem + (uint32_t(32 * warp) << 16) + uint32_t(128 + g * MAXM + c0 + 8),
-                     *reinterpret_cast<uint32_t(*)[8]>(v2 + 8));
-            tmem_ld_wait();
-            uint32_t cp[NB], cu = 0;
-#pragma unroll
-            for (int b = 0; b < NB; ++b) cp[b] = 0;
-#pragma unroll
-            for (int j = 0; j < 16; ++j) {
-              const int c = c0 + j;
-              const float4 q = cq[c];
-              // hi hi^T + 2^-11 (cross terms), back in the rows' units (powers of two: exact scalings)
-              const float G = split_gram_value(v[j], v2[j], a.inv_s2);
-              const float dv = (nt + q.x) - 2.f * G;
-              const float err = fmaf(q.y, At, fmaf(q.x, eps_n, Bt));
-              const float lo = dv - err, hi = dv + err;
-              int ts = 0, tp = 0;
-#pragma unroll
-              for (int u4 = 0; u4 < L::TB4; u4 += 4) {
-                if (u4 < TA) {  // uniform
-                  const float4 l4 = ql4[(c * L::TB4 + u4) / 4];
-                  const float4 h4 = qh4[(c * L::TB4 + u4) / 4];
-                  ts += int(hi < l4.x) + int(hi < l4.y) + int(hi < l4.z) + int(hi < l4.w);
-                  tp += int(!(lo > h4.x)) + int(!(lo > h4.y)) + int(!(lo > h4.z)) + int(!(lo > h4.w));
-                }
-              }
-              const bool valid = live_row && c > t && c < m;
-              ts = valid ? ts : 0;
-              tp = valid ? tp : 0;
-#pragma unroll
-              for (int b = 0; b < NB; ++b) cp[b] |= ((uint32_t(ts) >> b) & 1u) << j;
-              cu |= uint32_t(tp > ts) << j;
-            }
-            const int sh = c0 & 63;
-            const bool w1 = MW > 1 && c0 >= 64;
-#pragma unroll
-            for (int b = 0; b < NB; ++b) {
-              const unsigned long long x = static_cast<unsigned long long>(cp[b]) << sh;
-              pl[b][0] |= w1 ? 0ull : x;
-              pl[b][MW - 1] |= w1 ? x : 0ull;
-            }
-            const unsigned long long xu = static_cast<unsigned long long>(cu) << sh;
-            und[0] |= w1 ? 0ull : xu;
-            und[MW - 1] |= w1 ? xu : 0ull;
-          }
-          // open pairs (rare): the alphas from ts on go to the recheck, one entry
-          // per pair, which decides them in ascending order from one distance
-          // (those that in fact keep the pair say so)
-#pragma unroll
-          for (int w = 0; w < MW; ++w) {
-            while (und[w]) {
-              const int cb = __ffsll(static_cast<long long>(und[w])) - 1;
-              und[w] &= und[w] - 1;
-              const int c = 64 * w + cb;
-              int u0 = 0;
-#pragma unroll
-              for (int b = 0; b < NB; ++b) u0 |= int((pl[b][w] >> cb) & 1ull) << b;
-              // queued and resolved after this pass by all producer threads at
-              // once; decided here if the queue is full
-              const int qi = atomicAdd(rq_count + s, 1);
-              if (qi < L::rq_cap) {
-                rq[qi] = (unsigned(g * MAXM + t) << 16) | (unsigned(c) << 5) | unsigned(u0);
-              } else {
-                // the binary64 decision is monotone in alpha: kept at u means kept
-                // at every larger alpha, removed at u means removed at every
-                // smaller one, so ts for this column becomes the first u that keeps
-                const int u1 = recheck_prefix_cold(a, ids, key, key64, t, c, u0, TA, ppt, E_rel, E_abs);
-                n_rechecks += recheck_tests(u0, u1, TA);
-                const unsigned long long bit = 1ull << cb;
-#pragma unroll
-                for (int b = 0; b < NB; ++b) {
-                  const unsigned long long m_b = ((u1 >> b) & 1) ? bit : 0ull;
-                  pl[b][w] = (pl[b][w] & ~bit) | m_b;
-                }
-              }
-            }
-          }
-          // planes -> one row mask per distinct alpha: bit c of mask u is [ts(t, c) > u]
-          if (live_row) {
-#pragma unroll
-            for (int u = 0; u < TB; ++u) {
-              if (u >= TA) break;
-#pragma unroll
-              for (int w = 0; w < MW; ++w) {
-                unsigned long long gt = 0, eq = ~0ull;
-#pragma unroll
-                for (int b = NB - 1; b >= 0; --b) {
-                  if ((u >> b) & 1) {
-                    eq &= pl[b][w];
-                  } else {
-                    gt |= eq & pl[b][w];
-                    eq &= ~pl[b][w];
-                  }
-                }
-                mk[u][w] |= gt;
-              }
-            }
-          }
-        }
+        // while the MMA runs: the thresholds of column `rank` for every distinct
+        // alpha (a6).  The last factor of each (1 -+ 1e-6) covers the roundings
+        // of the pair's d2 - err and d2 + err, compared against them directly.
         if (live_row) {
 #pragma unroll
           for (int u = 0; u < TB; ++u) {
-            if (u >= (DT == kF32 ? a.TA : T)) break;
+            if (u >= a.TA) break;
+            const float A2f = float(static_cast<unsigned long long>(a.Ad[u]) * a.Ad[u]);
+            qlo[rank * L::TB4 + u] = 1.0e6f * (kacc * (1.0f - E_rel) - E_abs) * 0.9999995f / A2f * 0.9999995f * 0.999999f;
+            qhi[rank * L::TB4 + u] = 1.0e6f * (kacc * (1.0f + E_rel) + E_abs) * 1.0000005f / A2f * 1.0000005f * 1.000001f;
+          }
+          // padding past the last alpha never counts (hi < -inf, lo > -inf)
+          for (int u = a.TA; u < L::TB4; ++u) qlo[rank * L::TB4 + u] = qhi[rank * L::TB4 + u] = -INFINITY;
+          cq[rank] = make_float4(kacc, sqrtf(kacc), 0.f, 0.f);  // the column's centred norm^2 and its root
+        }
+        if (next_id >= 0) {
+          const char* nrow = reinterpret_cast<const char*>(a.X + int64_t(next_id) * a.row_bytes);
+          for (int64_t off = 0; off < a.row_bytes; off += 128) asm volatile("prefetch.global.L2 [%0];" ::"l"(nrow + off));
+        }
+        named_sync(kBarProd, 128);  // every rank-indexed array is complete
+        if (!dead) {
+          const bool ok = mbar_wait(mbar, phase, 1 << 24);
+          if (prod_sync_or(!ok)) {  // the MMA never completed: report, stop after this slot (uniform)
+            if (r == 0) raise_status(a.status, kDevOverflow, -2);
+            dead = true;
+          }
+          phase ^= 1u;
+          tc_fence_after();
+        }
+        // The group's Gram, MAXM x MAXM in stored order over the operands (read
+        // by now), row t rotated by t: G~(t, c) at [t * MAXM + (c + t) % MAXM].
+        // tcgen05.ld is warp-collective: every lane issues it, live rows store.
+        float* Gs = reinterpret_cast<float*>(opnd) + size_t(g) * MAXM * MAXM;
+        if (!dead) {
+          const int cend = (m + 15) & ~15;  // the same for every lane of the warp (one node)
+          const uint32_t lane_base = tmem + (uint32_t(32 * warp) << 16) + uint32_t(g * MAXM);
+          float* grow = Gs + size_t(t) * MAXM;
+#pragma unroll 1
+          for (int c0 = 0; c0 < cend; c0 += 16) {
+            uint32_t v[16], v2[16];
+            tmem_ld8(lane_base + uint32_t(c0), *reinterpret_cast<uint32_t(*)[8]>(v));
+            tmem_ld8(lane_base + uint32_t(c0 + 8), *reinterpret_cast<uint32_t(*)[8]>(v + 8));
+            tmem_ld8(lane_base + uint32_t(128 + c0), *reinterpret_cast<uint32_t(*)[8]>(v2));
+            tmem_ld8(lane_base + uint32_t(128 + c0 + 8), *reinterpret_cast<uint32_t(*)[8]>(v2 + 8));
+            tmem_ld_wait();
+            if (live_row) {
 #pragma unroll
-            for (int w = 0; w < MW; ++w) masks[(u * MAXM + t) * MW + w] = mk[u][w];
+              for (int j = 0; j < 16; ++j) grow[(c0 + j + t) & (MAXM - 1)] = split_gram_value(v[j], v2[j], a.inv_s2);
+            }
+          }
+          // rank row t's masks start empty (the rows of the group, one per thread)
+#pragma unroll
+          for (int u = 0; u < TB; ++u) {
+            if (u >= a.TA) break;
+#pragma unroll
+            for (int w = 0; w < MW; ++w) masks[(u * MAXM + t) * MW + w] = 0ull;
           }
         }
-      }
-      if (dead && t == 0) misc[s * 2 + g] = -1;  // nothing valid in this slot
-      tc_fence_before();
-      named_sync(kBarProd, 128);  // every producer's masks and TMEM reads are done
-      tc_fence_after();
-      if constexpr (DT == kF32) {
-        // the queued pairs, one per thread: each alpha that removes the column
-        // sets its bit in the row's mask for that alpha
-        const int nq = min(rq_count[s], L::rq_cap);  // the same for every producer
-        if (nq > 0) {
-          for (int i = r; i < nq; i += 128) {
-            const uint32_t e = rq[i];
-            const int tr = int(e >> 16), c = int((e >> 5) & 0x7ffu), u0 = int(e & 31u);
-            const int gq = tr / MAXM, tq = tr % MAXM;
-            unsigned char* sbq = slot_base(s, gq);
-            const int u1 = recheck_prefix(a, reinterpret_cast<const int32_t*>(sbq + L::s_ids),
-                                          reinterpret_cast<const float*>(sbq + L::s_key),
-                                          reinterpret_cast<double*>(sbq + L::s_key64), tq, c, u0, a.TA,
-                                          point_of_row(a, misc[s * 2 + gq]), E_rel, E_abs);
-            n_rechecks += recheck_tests(u0, u1, a.TA);
-            unsigned long long* mrow = reinterpret_cast<unsigned long long*>(sbq + L::s_masks) + tq * MW + (c >> 6);
-            for (int u = u0; u < u1; ++u) atomicOr(mrow + u * MAXM * MW, 1ull << (c & 63));
+        tc_fence_before();
+        named_sync(kBarProd, 128);  // the staged Gram, the cleared masks; TMEM read
+        tc_fence_after();
+        if (!dead) {
+          // Rows pair up as (q, MAXM - 1 - q): row q has MAXM - 1 - q later
+          // columns and row MAXM - 1 - q has q, MAXM - 1 in all, and the two
+          // threads of a pair take half each.  Thread h = 0 takes row q's first
+          // Q columns; thread h = 1 the rest of row q, then row MAXM - 1 - q.
+          // Item k of a thread is one (row, column) pair; for every item it counts
+          // the distinct alphas that surely remove the column (ts) and those that
+          // may (tp), both prefixes since the alphas ascend.  ts goes into NB bit
+          // planes over the items; pairs with ts < tp are open (queued).
+          constexpr int Q = MAXM / 2;
+          constexpr int NB = TB <= 1 ? 1 : TB <= 3 ? 2 : TB <= 7 ? 3 : TB <= 15 ? 4 : 5;
+          const int q = t % Q, h = t / Q;
+          const int rA = q, rB = MAXM - 1 - q;
+          const int nItems = h == 0 ? Q : Q - 1;
+          const int nA = h == 0 ? Q : Q - 1 - q;        // items on row rA, the rest on row rB
+          const int cA = h == 0 ? rA + 1 : rA + Q + 1;  // row rA's first column
+          const int cB = rB + 1;                         // row rB's first column
+          const int sA = rA < m ? st_of[rA] : 0, sB = rB < m ? st_of[rB] : 0;
+          // the d2 error bound as two multiply-adds: err = |c| At + |c|^2 eps_n + Bt
+          const float ntA = rA < m ? float(norm[rA]) : 0.f, stA = rA < m ? sn[rA] : 0.f;
+          const float ntB = rB < m ? float(norm[rB]) : 0.f, stB = rB < m ? sn[rB] : 0.f;
+          const float AtA = 2.f * eps_ip * stA * 1.0009765625f + sub_abs, BtA = sub_abs * stA + eps_n * ntA + err_abs;
+          const float AtB = 2.f * eps_ip * stB * 1.0009765625f + sub_abs, BtB = sub_abs * stB + eps_n * ntB + err_abs;
+          const int TA = a.TA;
+          const float4* ql4 = reinterpret_cast<const float4*>(qlo);
+          const float4* qh4 = reinterpret_cast<const float4*>(qhi);
+          unsigned long long ip[NB];
+#pragma unroll
+          for (int b = 0; b < NB; ++b) ip[b] = 0;
+#pragma unroll 4
+          for (int k = 0; k < Q; ++k) {
+            const bool onA = k < nA;
+            const int c = onA ? cA + k : cB + (k - nA);
+            const bool valid = k < nItems && c < m;  // c > its row, so the row is live too
+            const int cc = valid ? c : 0;
+            const int sR = valid ? (onA ? sA : sB) : 0;
+            const int sc = valid ? st_of[cc] : 0;
+            const float G = Gs[sR * MAXM + ((sc + sR) & (MAXM - 1))];
+            const float4 qc = cq[cc];
+            const float dv = ((onA ? ntA : ntB) + qc.x) - 2.f * G;
+            const float err = fmaf(qc.y, onA ? AtA : AtB, fmaf(qc.x, eps_n, onA ? BtA : BtB));
+            const float lo = dv - err, hi = dv + err;
+            int ts = 0, tp = 0;
+#pragma unroll
+            for (int u4 = 0; u4 < L::TB4; u4 += 4) {
+              if (u4 < TA) {  // uniform
+                const float4 l4 = ql4[(cc * L::TB4 + u4) / 4];
+                const float4 h4 = qh4[(cc * L::TB4 + u4) / 4];
+                ts += int(hi < l4.x) + int(hi < l4.y) + int(hi < l4.z) + int(hi < l4.w);
+                tp += int(!(lo > h4.x)) + int(!(lo > h4.y)) + int(!(lo > h4.z)) + int(!(lo > h4.w));
+              }
+            }
+            ts = valid ? ts : 0;
+            tp = valid ? tp : 0;
+            if (tp > ts) {
+              // an open pair (rare): the alphas from ts on are decided exactly by
+              // the consumer warp before its scan; here if the slot's queue is full
+              const int R = onA ? rA : rB;
+              const int qi = atomicAdd(rq_count + s, 1);
+              if (qi < L::rq_cap) {
+                rq[s * L::rq_cap + qi] = (unsigned(g * MAXM + R) << 16) | (unsigned(c) << 5) | unsigned(ts);
+              } else {
+                // removal is monotone in alpha: ts becomes the first alpha that keeps the pair
+                const int u1 = recheck_prefix_cold(a, ids, key, key64, R, c, ts, TA, ppt, E_rel, E_abs);
+                n_rechecks += recheck_tests(ts, u1, TA);
+                ts = u1;
+              }
+            }
+#pragma unroll
+            for (int b = 0; b < NB; ++b) ip[b] |= static_cast<unsigned long long>((ts >> b) & 1) << k;
           }
-          named_sync(kBarProd, 128);
+          // item planes -> one row mask per distinct alpha: bit c of row R's mask u
+          // is [ts(R, c) > u]; row rA's items are [0, nA) from column cA, row rB's
+          // [nA, nItems) from column cB
+          auto or_run = [&](unsigned long long* row, unsigned long long bits, int col) {
+            const int w0 = col >> 6, sh = col & 63;
+            if (bits << sh) atomicOr(row + w0, bits << sh);
+            if (MW > 1 && sh && w0 + 1 < MW && (bits >> (64 - sh))) atomicOr(row + w0 + 1, bits >> (64 - sh));
+          };
+#pragma unroll
+          for (int u = 0; u < TB; ++u) {
+            if (u >= TA) break;
+            unsigned long long gt = 0, eq = ~0ull;
+#pragma unroll
+            for (int b = NB - 1; b >= 0; --b) {
+              if ((u >> b) & 1) {
+                eq &= ip[b];
+              } else {
+                gt |= eq & ip[b];
+                eq &= ~ip[b];
+              }
+            }
+            const unsigned long long mA = nA >= 64 ? gt : (gt & ((1ull << nA) - 1));
+            const unsigned long long mB = nA >= 64 ? 0ull : (gt >> nA);
+            if (mA) or_run(masks + (u * MAXM + rA) * MW, mA, cA);
+            if (mB) or_run(masks + (u * MAXM + rB) * MW, mB, cB);
+          }
         }
+        if (dead && t == 0) misc[s * 2 + g] = -1;  // nothing valid in this slot
       }
       bar_arrive(kBarFull + s, 160);
     }
@@ -1019,6 +1251,7 @@ __global__ void __launch_bounds__(160, tc_min_ctas<DT, MAXM, TB>()) prune_tc_ker
     bar_arrive(kBarFree + 0, 160);  // both slots start free
     bar_arrive(kBarFree + 1, 160);
     long long done = 0;
+    unsigned long long n_rechecks = 0;  // single-precision rechecks of the queued pairs
     for (int k = 0;; ++k) {
       const int s = k & 1;
       named_sync(kBarFull + s, 160);
@@ -1029,6 +1262,25 @@ __global__ void __launch_bounds__(160, tc_min_ctas<DT, MAXM, TB>()) prune_tc_ker
         done += misc[s * 2 + q] >= 0;
       }
       if (!any) break;
+      if constexpr (DT == kF32) {
+        // the slot's open pairs, one per lane: each alpha that removes the
+        // column sets its bit in the row's mask for that alpha
+        const int nq = min(rq_count[s], L::rq_cap);
+        for (int i = lane; i < nq; i += 32) {
+          const uint32_t e = rq[s * L::rq_cap + i];
+          const int tr = int(e >> 16), c = int((e >> 5) & 0x7ffu), u0 = int(e & 31u);
+          const int gq = tr / MAXM, tq = tr % MAXM;
+          unsigned char* sbq = slot_base(s, gq);
+          const int u1 = recheck_prefix(a, reinterpret_cast<const int32_t*>(sbq + L::s_ids),
+                                        reinterpret_cast<const float*>(sbq + L::s_key),
+                                        reinterpret_cast<double*>(sbq + L::s_key64), tq, c, u0, a.TA,
+                                        point_of_row(a, misc[s * 2 + gq]), E_rel, E_abs);
+          n_rechecks += recheck_tests(u0, u1, a.TA);
+          unsigned long long* mrow = reinterpret_cast<unsigned long long*>(sbq + L::s_masks) + tq * MW + (c >> 6);
+          for (int u = u0; u < u1; ++u) atomicOr(mrow + u * MAXM * MW, 1ull << (c & 63));
+        }
+        __syncwarp();
+      }
       // ---- a7 greedy scan: lane (g * 16 + u) runs Algorithm 1's loop for node
       // g and target u.  Candidates are laid out by rank, so the next argmin of
       // the live set is its lowest set bit.
@@ -1072,6 +1324,11 @@ __global__ void __launch_bounds__(160, tc_min_ctas<DT, MAXM, TB>()) prune_tc_ker
       bar_arrive(kBarFree + s, 160);
     }
     if (lane == 0 && done) atomicAdd(&a.status->nodes_pruned, static_cast<unsigned long long>(done) * T);
+    if constexpr (DT == kF32) {
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) n_rechecks += __shfl_xor_sync(0xffffffffu, n_rechecks, o);
+      if (lane == 0 && n_rechecks) atomicAdd(&a.status->spare[2], n_rechecks);
+    }
   }
   // the TMEM columns go back once the producers are finished with them
   if (warp < 4) {
