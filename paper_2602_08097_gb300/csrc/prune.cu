@@ -305,9 +305,10 @@ struct TcLayout {
   static constexpr size_t p_k64 = p_sk + size_t(MAXM) * 8;       // [MAXM] binary64 keys in stored order
   static constexpr size_t p_cq = p_k64 + size_t(MAXM) * 8;        // [MAXM] float4 per column (float rows)
   static constexpr size_t p_srt = p_cq + size_t(MAXM) * 16;       // [MAXM] float keys by rank (float rows)
-  static constexpr size_t p_st = p_srt + size_t(MAXM) * 4;        // [MAXM] stored position of each rank (float rows)
-  static constexpr size_t p_bytes = p_st + size_t(MAXM) * 4;
-  static_assert(p_qlo % 16 == 0 && p_qhi % 16 == 0 && p_cq % 16 == 0 && p_bytes % 16 == 0, "16-byte reads");
+  static constexpr size_t p_rk = p_srt + size_t(MAXM) * 4;        // [MAXM] rank of each stored position (float rows)
+  static constexpr size_t p_bytes = p_rk + size_t(MAXM) * 4;
+  static_assert(p_qlo % 16 == 0 && p_qhi % 16 == 0 && p_cq % 16 == 0 && p_rk % 16 == 0 && p_bytes % 16 == 0,
+                "16-byte reads");
   static constexpr size_t off_prod = off_slots + 2 * NG * s_bytes;
   // small words: node/degree/row start per (slot, group), the claim queue's
   // head, mbarrier, TMEM address; then the claim queue (node, degree, row start)
@@ -320,7 +321,7 @@ struct TcLayout {
   static constexpr size_t off_rq = off_misc + misc_bytes;
   static constexpr size_t bytes = (off_rq + 2 * size_t(rq_cap) * 4 + 127) & ~size_t(127);
   // float rows: a group's Gram staged in shared memory over the operands (which
-  // the MMA has read by then), MAXM x MAXM floats in stored order, each row
+  // the MMA has read by then), MAXM x MAXM floats in rank order, each row
   // rotated by its index so that a warp's accesses spread over the banks
   static_assert(NOP == 1 || size_t(NG) * MAXM * MAXM * 4 <= off_slots, "staged Gram fits over the operands");
 };
@@ -551,7 +552,7 @@ __global__ void __launch_bounds__(160, tc_min_ctas<DT, MAXM, TB>()) prune_tc_ker
         const bool one_slice = nslices == 1;
         if (live_row || one_slice) {
           float part = 0.f;  // the key is summed per 32-dimension slice (slice_rel_bound)
-#pragma unroll 2
+#pragma unroll 4
           for (int c = 0; c < int(elems / 8); ++c) {
             uint4 x0 = make_uint4(0, 0, 0, 0), x1 = x0, y0 = x0, y1 = x0;
             if (live_row) {
@@ -1030,11 +1031,11 @@ __global__ void __launch_bounds__(160, tc_min_ctas<DT, MAXM, TB>()) prune_tc_ker
         }
       } else {
         // ---- float rows: the operands stay at the stored position, so the
-        // Gram is in stored order; it is staged in shared memory and every pair
-        // (row before column in rank order) is decided from there, the pairs
+        // Gram is in stored order; it is staged in shared memory in rank order
+        // and every pair (row before column) is decided from there, the pairs
         // spread evenly over the 128 producer threads.
-        int* st_of = reinterpret_cast<int*>(pb + L::p_st);  // stored position of each rank
-        if (live_row) st_of[rank] = t;
+        int* rank_of = reinterpret_cast<int*>(pb + L::p_rk);  // rank of each stored position
+        if (live_row) rank_of[t] = rank;
         // rows of several 128-dimension slices: one MMA chain per slice, a
         // slice's operands written once the previous MMA has read its own
         for (int sl = 0; !early_mma && sl < nslices; ++sl) {
@@ -1107,14 +1108,16 @@ __global__ void __launch_bounds__(160, tc_min_ctas<DT, MAXM, TB>()) prune_tc_ker
           phase ^= 1u;
           tc_fence_after();
         }
-        // The group's Gram, MAXM x MAXM in stored order over the operands (read
-        // by now), row t rotated by t: G~(t, c) at [t * MAXM + (c + t) % MAXM].
-        // tcgen05.ld is warp-collective: every lane issues it, live rows store.
+        // The group's Gram, MAXM x MAXM in rank order over the operands (read by
+        // now), row R rotated by R: G~(R, c) at [R * MAXM + (c + R) % MAXM], the
+        // entries with R < c.  tcgen05.ld is warp-collective: every lane issues
+        // it, live rows store.
         float* Gs = reinterpret_cast<float*>(opnd) + size_t(g) * MAXM * MAXM;
         if (!dead) {
           const int cend = (m + 15) & ~15;  // the same for every lane of the warp (one node)
           const uint32_t lane_base = tmem + (uint32_t(32 * warp) << 16) + uint32_t(g * MAXM);
-          float* grow = Gs + size_t(t) * MAXM;
+          float* grow = Gs + size_t(rank) * MAXM;
+          const int4* rk4 = reinterpret_cast<const int4*>(rank_of);
 #pragma unroll 1
           for (int c0 = 0; c0 < cend; c0 += 16) {
             uint32_t v[16], v2[16];
@@ -1125,7 +1128,14 @@ __global__ void __launch_bounds__(160, tc_min_ctas<DT, MAXM, TB>()) prune_tc_ker
             tmem_ld_wait();
             if (live_row) {
 #pragma unroll
-              for (int j = 0; j < 16; ++j) grow[(c0 + j + t) & (MAXM - 1)] = split_gram_value(v[j], v2[j], a.inv_s2);
+              for (int j4 = 0; j4 < 16; j4 += 4) {
+                const int4 r4 = rk4[(c0 + j4) / 4];  // ranks of four stored columns (past m: not used)
+                const int rc[4] = {r4.x, r4.y, r4.z, r4.w};
+#pragma unroll
+                for (int j = 0; j < 4; ++j)
+                  if (c0 + j4 + j < m && rc[j] > rank)
+                    grow[(rc[j] + rank) & (MAXM - 1)] = split_gram_value(v[j4 + j], v2[j4 + j], a.inv_s2);
+              }
             }
           }
           // rank row t's masks start empty (the rows of the group, one per thread)
@@ -1156,7 +1166,6 @@ __global__ void __launch_bounds__(160, tc_min_ctas<DT, MAXM, TB>()) prune_tc_ker
           const int nA = h == 0 ? Q : Q - 1 - q;        // items on row rA, the rest on row rB
           const int cA = h == 0 ? rA + 1 : rA + Q + 1;  // row rA's first column
           const int cB = rB + 1;                         // row rB's first column
-          const int sA = rA < m ? st_of[rA] : 0, sB = rB < m ? st_of[rB] : 0;
           // the d2 error bound as two multiply-adds: err = |c| At + |c|^2 eps_n + Bt
           const float ntA = rA < m ? float(norm[rA]) : 0.f, stA = rA < m ? sn[rA] : 0.f;
           const float ntB = rB < m ? float(norm[rB]) : 0.f, stB = rB < m ? sn[rB] : 0.f;
@@ -1165,19 +1174,20 @@ __global__ void __launch_bounds__(160, tc_min_ctas<DT, MAXM, TB>()) prune_tc_ker
           const int TA = a.TA;
           const float4* ql4 = reinterpret_cast<const float4*>(qlo);
           const float4* qh4 = reinterpret_cast<const float4*>(qhi);
-          unsigned long long ip[NB];
+          unsigned long long ip[NB], open = 0;
 #pragma unroll
           for (int b = 0; b < NB; ++b) ip[b] = 0;
+          // straight-line items (the open ones are only marked), so that the
+          // reads of several items overlap
 #pragma unroll 4
           for (int k = 0; k < Q; ++k) {
             const bool onA = k < nA;
+            const int R = onA ? rA : rB;
             const int c = onA ? cA + k : cB + (k - nA);
-            const bool valid = k < nItems && c < m;  // c > its row, so the row is live too
-            const int cc = valid ? c : 0;
-            const int sR = valid ? (onA ? sA : sB) : 0;
-            const int sc = valid ? st_of[cc] : 0;
-            const float G = Gs[sR * MAXM + ((sc + sR) & (MAXM - 1))];
-            const float4 qc = cq[cc];
+            const bool valid = k < nItems && c < m;  // c > R, so the row is live too
+            const int ci = valid ? c : 0;            // the reads stay in range for every k
+            const float G = Gs[R * MAXM + ((ci + R) & (MAXM - 1))];
+            const float4 qc = cq[ci];
             const float dv = ((onA ? ntA : ntB) + qc.x) - 2.f * G;
             const float err = fmaf(qc.y, onA ? AtA : AtB, fmaf(qc.x, eps_n, onA ? BtA : BtB));
             const float lo = dv - err, hi = dv + err;
@@ -1185,30 +1195,39 @@ __global__ void __launch_bounds__(160, tc_min_ctas<DT, MAXM, TB>()) prune_tc_ker
 #pragma unroll
             for (int u4 = 0; u4 < L::TB4; u4 += 4) {
               if (u4 < TA) {  // uniform
-                const float4 l4 = ql4[(cc * L::TB4 + u4) / 4];
-                const float4 h4 = qh4[(cc * L::TB4 + u4) / 4];
+                const float4 l4 = ql4[(ci * L::TB4 + u4) / 4];
+                const float4 h4 = qh4[(ci * L::TB4 + u4) / 4];
                 ts += int(hi < l4.x) + int(hi < l4.y) + int(hi < l4.z) + int(hi < l4.w);
                 tp += int(!(lo > h4.x)) + int(!(lo > h4.y)) + int(!(lo > h4.z)) + int(!(lo > h4.w));
               }
             }
             ts = valid ? ts : 0;
-            tp = valid ? tp : 0;
-            if (tp > ts) {
-              // an open pair (rare): the alphas from ts on are decided exactly by
-              // the consumer warp before its scan; here if the slot's queue is full
-              const int R = onA ? rA : rB;
-              const int qi = atomicAdd(rq_count + s, 1);
-              if (qi < L::rq_cap) {
-                rq[s * L::rq_cap + qi] = (unsigned(g * MAXM + R) << 16) | (unsigned(c) << 5) | unsigned(ts);
-              } else {
-                // removal is monotone in alpha: ts becomes the first alpha that keeps the pair
-                const int u1 = recheck_prefix_cold(a, ids, key, key64, R, c, ts, TA, ppt, E_rel, E_abs);
-                n_rechecks += recheck_tests(ts, u1, TA);
-                ts = u1;
-              }
-            }
+            open |= static_cast<unsigned long long>(valid && tp > ts) << k;
 #pragma unroll
             for (int b = 0; b < NB; ++b) ip[b] |= static_cast<unsigned long long>((ts >> b) & 1) << k;
+          }
+          // open pairs (rare): the alphas from ts on are decided exactly by the
+          // consumer warp before its scan; here if the slot's queue is full
+          while (open) {
+            const int k = __ffsll(static_cast<long long>(open)) - 1;
+            open &= open - 1;
+            const bool onA = k < nA;
+            const int R = onA ? rA : rB;
+            const int c = onA ? cA + k : cB + (k - nA);
+            int ts = 0;
+#pragma unroll
+            for (int b = 0; b < NB; ++b) ts |= int((ip[b] >> k) & 1ull) << b;
+            const int qi = atomicAdd(rq_count + s, 1);
+            if (qi < L::rq_cap) {
+              rq[s * L::rq_cap + qi] = (unsigned(g * MAXM + R) << 16) | (unsigned(c) << 5) | unsigned(ts);
+            } else {
+              // removal is monotone in alpha: ts becomes the first alpha that keeps the pair
+              const int u1 = recheck_prefix_cold(a, ids, key, key64, R, c, ts, TA, ppt, E_rel, E_abs);
+              n_rechecks += recheck_tests(ts, u1, TA);
+#pragma unroll
+              for (int b = 0; b < NB; ++b)
+                ip[b] = (ip[b] & ~(1ull << k)) | (static_cast<unsigned long long>((u1 >> b) & 1) << k);
+            }
           }
           // item planes -> one row mask per distinct alpha: bit c of row R's mask u
           // is [ts(R, c) > u]; row rA's items are [0, nA) from column cA, row rB's
