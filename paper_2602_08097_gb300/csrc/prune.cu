@@ -27,6 +27,7 @@
 // path (one node per 256-thread CTA, lazy CUDA-core distances).
 #include <algorithm>
 #include <cmath>
+#include <type_traits>
 
 #include "internal.h"
 #include "tc.cuh"
@@ -712,51 +713,29 @@ __global__ void __launch_bounds__(160, tc_min_ctas<DT, MAXM, TB>()) prune_tc_ker
         for (int sl = 0; sl < nslices; ++sl) {
           const int64_t rem = elems - int64_t(sl) * 128;
           const int kd = int(rem < 128 ? rem : 128);  // a multiple of 16 here
-          if constexpr (DT == kU8) {
-            if (nslices > 1) {
-#pragma unroll
-              for (int c = 0; c < 8; ++c) {
-                xs[c] = make_uint4(0, 0, 0, 0);
-                if (live_row && c < kd / 16) xs[c] = __ldg(reinterpret_cast<const uint4*>(xrow + sl * 128) + c);
-              }
-            }
+          if (nslices > 1) {
 #pragma unroll
             for (int c = 0; c < 8; ++c) {
-              if (c >= kd / 16) break;
-              const uint4 x = xs[c];
-              const unsigned w4[4] = {x.x, x.y, x.z, x.w};
-              uint32_t o[8];
+              xs[c] = make_uint4(0, 0, 0, 0);
+              if (live_row && c < kd / 16) xs[c] = __ldg(reinterpret_cast<const uint4*>(xrow + sl * 128) + c);
+            }
+          }
 #pragma unroll
-              for (int q = 0; q < 4; ++q) {
-                o[2 * q] = u8x2_f16x2(w4[q], 0x4140u);      // bytes 0, 1
-                o[2 * q + 1] = u8x2_f16x2(w4[q], 0x4342u);  // bytes 2, 3
-              }
-              const int kc0 = 2 * c;
-              *reinterpret_cast<uint4*>(opnd + (kc0 * 16 + orow / 8) * 128 + (orow % 8) * 16) =
-                  make_uint4(o[0], o[1], o[2], o[3]);
-              *reinterpret_cast<uint4*>(opnd + ((kc0 + 1) * 16 + orow / 8) * 128 + (orow % 8) * 16) =
-                  make_uint4(o[4], o[5], o[6], o[7]);
+          for (int c = 0; c < 8; ++c) {
+            if (c >= kd / 16) break;
+            const uint4 x = xs[c];
+            const unsigned w4[4] = {x.x, x.y, x.z, x.w};
+            uint32_t o[8];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+              o[2 * q] = u8x2_f16x2(w4[q], 0x4140u);      // bytes 0, 1
+              o[2 * q + 1] = u8x2_f16x2(w4[q], 0x4342u);  // bytes 2, 3
             }
-          } else if (!(nslices == 1 && in_order)) {  // else written with the keys
-#pragma unroll 4
-            for (int c = 0; c < kd / 8; ++c) {
-              uint4 x0 = make_uint4(0, 0, 0, 0), x1 = x0, y0 = x0, y1 = x0;
-              if (live_row) {  // rows past the degree stay zero
-                const uint4* xq = reinterpret_cast<const uint4*>(xrow + int64_t(sl) * 512) + 2 * c;
-                const uint4* pq = reinterpret_cast<const uint4*>(prow + int64_t(sl) * 512) + 2 * c;
-                x0 = __ldg(xq);
-                x1 = __ldg(xq + 1);
-                y0 = __ldg(pq);
-                y1 = __ldg(pq + 1);
-              }
-              const float xv[8] = {__uint_as_float(x0.x), __uint_as_float(x0.y), __uint_as_float(x0.z),
-                                   __uint_as_float(x0.w), __uint_as_float(x1.x), __uint_as_float(x1.y),
-                                   __uint_as_float(x1.z), __uint_as_float(x1.w)};
-              const float pv[8] = {__uint_as_float(y0.x), __uint_as_float(y0.y), __uint_as_float(y0.z),
-                                   __uint_as_float(y0.w), __uint_as_float(y1.x), __uint_as_float(y1.y),
-                                   __uint_as_float(y1.z), __uint_as_float(y1.w)};
-              store_split8_centred(opnd, orow, c, xv, pv, a.scale);
-            }
+            const int kc0 = 2 * c;
+            *reinterpret_cast<uint4*>(opnd + (kc0 * 16 + orow / 8) * 128 + (orow % 8) * 16) =
+                make_uint4(o[0], o[1], o[2], o[3]);
+            *reinterpret_cast<uint4*>(opnd + ((kc0 + 1) * 16 + orow / 8) * 128 + (orow % 8) * 16) =
+                make_uint4(o[4], o[5], o[6], o[7]);
           }
           const bool last = sl == nslices - 1;
           fence_async_smem();
@@ -764,40 +743,20 @@ __global__ void __launch_bounds__(160, tc_min_ctas<DT, MAXM, TB>()) prune_tc_ker
           named_sync(kBarProd, 128);
           tc_fence_after();
           if (r == 0) {
-            issue_gram_slice<DT == kF32>(tmem, opnd, kd, sl > 0);
+            issue_gram_slice<false>(tmem, opnd, kd, sl > 0);
             umma_commit(mbar);
           }
-          if (last) {
-            // while the MMA runs: the thresholds of column `rank` for every target
-            // (uint8) or every distinct alpha (float) (a6)
-            if (live_row) {
+          if (last && live_row) {
+            // while the MMA runs: the thresholds of column `rank` for every target (a6)
 #pragma unroll
-              for (int u = 0; u < TB; ++u) {
-                if (u >= (DT == kF32 ? a.TA : T)) break;
-                const int32_t Au = DT == kF32 ? a.Ad[u] : a.A[u];
-                const unsigned long long A2 = static_cast<unsigned long long>(Au) * Au;
-                if constexpr (DT == kU8) {
-                  // v is removed by row u'  <=>  A2 d2(u', v) <= 1e6 d2(p, v)
-                  //   <=>  2 G(u', v) - |u'|^2 >= |v|^2 - floor(1e6 d2(p, v) / A2)
-                  // (every quantity an integer below 2^24, exact in f32)
-                  const unsigned thr = exact_threshold(kacc, A2, a.inv_A2[u]);
-                  qlo[u * MAXM + rank] = float(int(nacc) - int(thr));
-                } else {
-                  // float thresholds per column, distinct alphas contiguous.  The
-                  // last factor of each (1 -+ 1e-6) covers the roundings of the
-                  // pair's d2 - err and d2 + err, compared against them directly.
-                  const float A2f = float(A2);
-                  qlo[rank * L::TB4 + u] =
-                      1.0e6f * (kacc * (1.0f - E_rel) - E_abs) * 0.9999995f / A2f * 0.9999995f * 0.999999f;
-                  qhi[rank * L::TB4 + u] =
-                      1.0e6f * (kacc * (1.0f + E_rel) + E_abs) * 1.0000005f / A2f * 1.0000005f * 1.000001f;
-                }
-              }
-              if constexpr (DT == kF32) {
-                // padding past the last alpha never counts (hi < -inf, lo > -inf)
-                for (int u = a.TA; u < L::TB4; ++u) qlo[rank * L::TB4 + u] = qhi[rank * L::TB4 + u] = -INFINITY;
-                cq[rank] = make_float4(kacc, sqrtf(kacc), 0.f, 0.f);  // the column's centred norm^2 and its root
-              }
+            for (int u = 0; u < TB; ++u) {
+              if (u >= T) break;
+              const unsigned long long A2 = static_cast<unsigned long long>(a.A[u]) * a.A[u];
+              // v is removed by row u'  <=>  A2 d2(u', v) <= 1e6 d2(p, v)
+              //   <=>  2 G(u', v) - |u'|^2 >= |v|^2 - floor(1e6 d2(p, v) / A2)
+              // (every quantity an integer below 2^24, exact in f32)
+              const unsigned thr = exact_threshold(kacc, A2, a.inv_A2[u]);
+              qlo[u * MAXM + rank] = float(int(nacc) - int(thr));
             }
           }
           if (last && next_id >= 0) {
@@ -823,182 +782,50 @@ __global__ void __launch_bounds__(160, tc_min_ctas<DT, MAXM, TB>()) prune_tc_ker
 #pragma unroll
             for (int w = 0; w < MW; ++w) mk[u][w] = 0;
           const float nt = live_row ? float(norm[t]) : 0.f;
-          const float st = DT == kF32 && live_row ? sn[t] : 0.f;
           // A row only removes candidates after it in the processing order (the
           // scan has decided every earlier one), so a warp whose rows all come
           // after a 32-column chunk skips it (a uniform choice: the TMEM read is
           // warp-collective).  Bits set for earlier columns are harmless too.
           const int first_col = 32 * (warp % (MAXM / 32));
-          if constexpr (DT == kU8) {
-            // Columns at or past the degree hold no candidate: the bits set there
-            // can never meet a live bit in the scan, so they are not tested for.
+          // Columns at or past the degree hold no candidate: the bits set there
+          // can never meet a live bit in the scan, so they are not tested for.
 #pragma unroll
-            for (int c0 = 0; c0 < MAXM; c0 += 32) {
-              if (c0 < first_col) continue;
-              uint32_t v[32];
-              tmem_ld32(tmem + (uint32_t(32 * warp) << 16) + uint32_t(g * MAXM + c0), v);
-              tmem_ld_wait();
-              if (live_row) {
-                // x = 2 G - |t|^2 lies in [-|t|^2, |c|^2], an integer below 2^24,
-                // exact; q too.  x - q keeps its sign when rounded and is +0 when
-                // x = q, so its sign bit is exactly "x < q": not removed.  Columns
-                // go in last to first, so column c0 + j ends at bit j.
-                uint32_t nb[TB];
-#pragma unroll
-                for (int u = 0; u < TB; ++u) nb[u] = 0u;
-#pragma unroll
-                for (int j4 = 28; j4 >= 0; j4 -= 4) {
-                  float x[4];
-#pragma unroll
-                  for (int q = 0; q < 4; ++q) x[q] = fmaf(2.f, __uint_as_float(v[j4 + q]), -nt);
-#pragma unroll
-                  for (int u = 0; u < TB; ++u) {
-                    if (u >= T) break;
-                    const float4 q4 = *reinterpret_cast<const float4*>(qlo + u * MAXM + c0 + j4);
-                    nb[u] = __funnelshift_l(__float_as_uint(x[3] - q4.w), nb[u], 1);
-                    nb[u] = __funnelshift_l(__float_as_uint(x[2] - q4.z), nb[u], 1);
-                    nb[u] = __funnelshift_l(__float_as_uint(x[1] - q4.y), nb[u], 1);
-                    nb[u] = __funnelshift_l(__float_as_uint(x[0] - q4.x), nb[u], 1);
-                  }
-                }
-#pragma unroll
-                for (int u = 0; u < TB; ++u) mk[u][c0 >> 6] |= static_cast<unsigned long long>(~nb[u]) << (c0 & 63);
-              }
-            }
-          } else {
-            // Float rows: for every column c after row t, ts = how many distinct
-            // alphas surely remove c and tp = how many may (both prefixes: the
-            // alphas ascend and the thresholds fall with them).  ts is kept as NB
-            // bit planes over the columns; pairs with ts < tp go to the recheck
-            // queue.  The code is branch-free per column, so the sixteen columns
-            // of a TMEM read overlap; each column's bits go first into 16-bit
-            // chunk words at constant positions.
-            constexpr int NB = TB <= 1 ? 1 : TB <= 3 ? 2 : TB <= 7 ? 3 : TB <= 15 ? 4 : 5;
-            unsigned long long pl[NB][MW];
-#pragma unroll
-            for (int b = 0; b < NB; ++b)
-#pragma unroll
-              for (int w = 0; w < MW; ++w) pl[b][w] = 0;
-            unsigned long long und[MW];
-#pragma unroll
-            for (int w = 0; w < MW; ++w) und[w] = 0;
-            const int TA = a.TA;
-            // the d2 error bound as two multiply-adds: err = |c| At + |c|^2 eps_n + Bt
-            const float At = 2.f * eps_ip * st * 1.0009765625f + sub_abs;
-            const float Bt = sub_abs * st + eps_n * nt + err_abs;
-            const float4* ql4 = reinterpret_cast<const float4*>(qlo);
-            const float4* qh4 = reinterpret_cast<const float4*>(qhi);
-            const int cend = (m + 15) & ~15;  // the same for every lane of the warp (one node)
-#pragma unroll 1
-            for (int c0 = first_col; c0 < cend; c0 += 16) {
-              uint32_t v[16], v2[16];
-              tmem_ld8(tmem + (uint32_t(32 * warp) << 16) + uint32_t(g * MAXM + c0), *reinterpret_cast<uint32_t(*)[8]>(v));
-              tmem_ld8(tmem + (uint32_t(32 * warp) << 16) + uint32_t(g * MAXM + c0 + 8),
-                       *reinterpret_cast<uint32_t(*)[8]>(v + 8));
-              tmem_ld8(tmem + (uint32_t(32 * warp) << 16) + uint32_t(128 + g * MAXM + c0),
-                       *reinterpret_cast<uint32_t(*)[8]>(v2));
-              tmem_ld8(tmem + (uint32_t(32 * warp) << 16) + uint32_t(128 + g * MAXM + c0 + 8),
-                       *reinterpret_cast<uint32_t(*)[8]>(v2 + 8));
-              tmem_ld_wait();
-              uint32_t cp[NB], cu = 0;
-#pragma unroll
-              for (int b = 0; b < NB; ++b) cp[b] = 0;
-#pragma unroll
-              for (int j = 0; j < 16; ++j) {
-                const int c = c0 + j;
-                const float4 q = cq[c];
-                // hi hi^T + 2^-11 (cross terms), back in the rows' units (powers of two: exact scalings)
-                const float G = split_gram_value(v[j], v2[j], a.inv_s2);
-                const float dv = (nt + q.x) - 2.f * G;
-                const float err = fmaf(q.y, At, fmaf(q.x, eps_n, Bt));
-                const float lo = dv - err, hi = dv + err;
-                int ts = 0, tp = 0;
-#pragma unroll
-                for (int u4 = 0; u4 < L::TB4; u4 += 4) {
-                  if (u4 < TA) {  // uniform
-                    const float4 l4 = ql4[(c * L::TB4 + u4) / 4];
-                    const float4 h4 = qh4[(c * L::TB4 + u4) / 4];
-                    ts += int(hi < l4.x) + int(hi < l4.y) + int(hi < l4.z) + int(hi < l4.w);
-                    tp += int(!(lo > h4.x)) + int(!(lo > h4.y)) + int(!(lo > h4.z)) + int(!(lo > h4.w));
-                  }
-                }
-                const bool valid = live_row && c > t && c < m;
-                ts = valid ? ts : 0;
-                tp = valid ? tp : 0;
-#pragma unroll
-                for (int b = 0; b < NB; ++b) cp[b] |= ((uint32_t(ts) >> b) & 1u) << j;
-                cu |= uint32_t(tp > ts) << j;
-              }
-              const int sh = c0 & 63;
-              const bool w1 = MW > 1 && c0 >= 64;
-#pragma unroll
-              for (int b = 0; b < NB; ++b) {
-                const unsigned long long x = static_cast<unsigned long long>(cp[b]) << sh;
-                pl[b][0] |= w1 ? 0ull : x;
-                pl[b][MW - 1] |= w1 ? x : 0ull;
-              }
-              const unsigned long long xu = static_cast<unsigned long long>(cu) << sh;
-              und[0] |= w1 ? 0ull : xu;
-              und[MW - 1] |= w1 ? xu : 0ull;
-            }
-            // open pairs (rare): the alphas from ts on go to the recheck, one entry
-            // per pair, which decides them in ascending order from one distance
-            // (those that in fact keep the pair say so)
-#pragma unroll
-            for (int w = 0; w < MW; ++w) {
-              while (und[w]) {
-                const int cb = __ffsll(static_cast<long long>(und[w])) - 1;
-                und[w] &= und[w] - 1;
-                const int c = 64 * w + cb;
-                int u0 = 0;
-#pragma unroll
-                for (int b = 0; b < NB; ++b) u0 |= int((pl[b][w] >> cb) & 1ull) << b;
-                // queued and resolved after this pass by all producer threads at
-                // once; decided here if the queue is full
-                const int qi = atomicAdd(rq_count + s, 1);
-                if (qi < L::rq_cap) {
-                  rq[qi] = (unsigned(g * MAXM + t) << 16) | (unsigned(c) << 5) | unsigned(u0);
-                } else {
-                  // the binary64 decision is monotone in alpha: kept at u means kept
-                  // at every larger alpha, removed at u means removed at every
-                  // smaller one, so ts for this column becomes the first u that keeps
-                  const int u1 = recheck_prefix_cold(a, ids, key, key64, t, c, u0, TA, ppt, E_rel, E_abs);
-                  n_rechecks += recheck_tests(u0, u1, TA);
-                  const unsigned long long bit = 1ull << cb;
-#pragma unroll
-                  for (int b = 0; b < NB; ++b) {
-                    const unsigned long long m_b = ((u1 >> b) & 1) ? bit : 0ull;
-                    pl[b][w] = (pl[b][w] & ~bit) | m_b;
-                  }
-                }
-              }
-            }
-            // planes -> one row mask per distinct alpha: bit c of mask u is [ts(t, c) > u]
+          for (int c0 = 0; c0 < MAXM; c0 += 32) {
+            if (c0 < first_col) continue;
+            uint32_t v[32];
+            tmem_ld32(tmem + (uint32_t(32 * warp) << 16) + uint32_t(g * MAXM + c0), v);
+            tmem_ld_wait();
             if (live_row) {
+              // x = 2 G - |t|^2 lies in [-|t|^2, |c|^2], an integer below 2^24,
+              // exact; q too.  x - q keeps its sign when rounded and is +0 when
+              // x = q, so its sign bit is exactly "x < q": not removed.  Columns
+              // go in last to first, so column c0 + j ends at bit j.
+              uint32_t nb[TB];
 #pragma unroll
-              for (int u = 0; u < TB; ++u) {
-                if (u >= TA) break;
+              for (int u = 0; u < TB; ++u) nb[u] = 0u;
 #pragma unroll
-                for (int w = 0; w < MW; ++w) {
-                  unsigned long long gt = 0, eq = ~0ull;
+              for (int j4 = 28; j4 >= 0; j4 -= 4) {
+                float x[4];
 #pragma unroll
-                  for (int b = NB - 1; b >= 0; --b) {
-                    if ((u >> b) & 1) {
-                      eq &= pl[b][w];
-                    } else {
-                      gt |= eq & pl[b][w];
-                      eq &= ~pl[b][w];
-                    }
-                  }
-                  mk[u][w] |= gt;
+                for (int q = 0; q < 4; ++q) x[q] = fmaf(2.f, __uint_as_float(v[j4 + q]), -nt);
+#pragma unroll
+                for (int u = 0; u < TB; ++u) {
+                  if (u >= T) break;
+                  const float4 q4 = *reinterpret_cast<const float4*>(qlo + u * MAXM + c0 + j4);
+                  nb[u] = __funnelshift_l(__float_as_uint(x[3] - q4.w), nb[u], 1);
+                  nb[u] = __funnelshift_l(__float_as_uint(x[2] - q4.z), nb[u], 1);
+                  nb[u] = __funnelshift_l(__float_as_uint(x[1] - q4.y), nb[u], 1);
+                  nb[u] = __funnelshift_l(__float_as_uint(x[0] - q4.x), nb[u], 1);
                 }
               }
+#pragma unroll
+              for (int u = 0; u < TB; ++u) mk[u][c0 >> 6] |= static_cast<unsigned long long>(~nb[u]) << (c0 & 63);
             }
           }
           if (live_row) {
 #pragma unroll
             for (int u = 0; u < TB; ++u) {
-              if (u >= (DT == kF32 ? a.TA : T)) break;
+              if (u >= T) break;
 #pragma unroll
               for (int w = 0; w < MW; ++w) masks[(u * MAXM + t) * MW + w] = mk[u][w];
             }
@@ -1008,27 +835,6 @@ __global__ void __launch_bounds__(160, tc_min_ctas<DT, MAXM, TB>()) prune_tc_ker
         tc_fence_before();
         named_sync(kBarProd, 128);  // every producer's masks and TMEM reads are done
         tc_fence_after();
-        if constexpr (DT == kF32) {
-          // the queued pairs, one per thread: each alpha that removes the column
-          // sets its bit in the row's mask for that alpha
-          const int nq = min(rq_count[s], L::rq_cap);  // the same for every producer
-          if (nq > 0) {
-            for (int i = r; i < nq; i += 128) {
-              const uint32_t e = rq[i];
-              const int tr = int(e >> 16), c = int((e >> 5) & 0x7ffu), u0 = int(e & 31u);
-              const int gq = tr / MAXM, tq = tr % MAXM;
-              unsigned char* sbq = slot_base(s, gq);
-              const int u1 = recheck_prefix(a, reinterpret_cast<const int32_t*>(sbq + L::s_ids),
-                                            reinterpret_cast<const float*>(sbq + L::s_key),
-                                            reinterpret_cast<double*>(sbq + L::s_key64), tq, c, u0, a.TA,
-                                            point_of_row(a, misc[s * 2 + gq]), E_rel, E_abs);
-              n_rechecks += recheck_tests(u0, u1, a.TA);
-              unsigned long long* mrow = reinterpret_cast<unsigned long long*>(sbq + L::s_masks) + tq * MW + (c >> 6);
-              for (int u = u0; u < u1; ++u) atomicOr(mrow + u * MAXM * MW, 1ull << (c & 63));
-            }
-            named_sync(kBarProd, 128);
-          }
-        }
       } else {
         // ---- float rows: the operands stay at the stored position, so the
         // Gram is in stored order; it is staged in shared memory in rank order
@@ -1082,16 +888,19 @@ __global__ void __launch_bounds__(160, tc_min_ctas<DT, MAXM, TB>()) prune_tc_ker
         // while the MMA runs: the thresholds of column `rank` for every distinct
         // alpha (a6).  The last factor of each (1 -+ 1e-6) covers the roundings
         // of the pair's d2 - err and d2 + err, compared against them directly.
+        // a column's thresholds are TA4 = TA rounded up to 4 floats apart, so
+        // that consecutive columns' 16-byte reads are consecutive
+        const int TA4 = (a.TA + 3) & ~3;
         if (live_row) {
 #pragma unroll
           for (int u = 0; u < TB; ++u) {
             if (u >= a.TA) break;
             const float A2f = float(static_cast<unsigned long long>(a.Ad[u]) * a.Ad[u]);
-            qlo[rank * L::TB4 + u] = 1.0e6f * (kacc * (1.0f - E_rel) - E_abs) * 0.9999995f / A2f * 0.9999995f * 0.999999f;
-            qhi[rank * L::TB4 + u] = 1.0e6f * (kacc * (1.0f + E_rel) + E_abs) * 1.0000005f / A2f * 1.0000005f * 1.000001f;
+            qlo[rank * TA4 + u] = 1.0e6f * (kacc * (1.0f - E_rel) - E_abs) * 0.9999995f / A2f * 0.9999995f * 0.999999f;
+            qhi[rank * TA4 + u] = 1.0e6f * (kacc * (1.0f + E_rel) + E_abs) * 1.0000005f / A2f * 1.0000005f * 1.000001f;
           }
           // padding past the last alpha never counts (hi < -inf, lo > -inf)
-          for (int u = a.TA; u < L::TB4; ++u) qlo[rank * L::TB4 + u] = qhi[rank * L::TB4 + u] = -INFINITY;
+          for (int u = a.TA; u < TA4; ++u) qlo[rank * TA4 + u] = qhi[rank * TA4 + u] = -INFINITY;
           cq[rank] = make_float4(kacc, sqrtf(kacc), 0.f, 0.f);  // the column's centred norm^2 and its root
         }
         if (next_id >= 0) {
@@ -1154,12 +963,8 @@ __global__ void __launch_bounds__(160, tc_min_ctas<DT, MAXM, TB>()) prune_tc_ker
           // columns and row MAXM - 1 - q has q, MAXM - 1 in all, and the two
           // threads of a pair take half each.  Thread h = 0 takes row q's first
           // Q columns; thread h = 1 the rest of row q, then row MAXM - 1 - q.
-          // Item k of a thread is one (row, column) pair; for every item it counts
-          // the distinct alphas that surely remove the column (ts) and those that
-          // may (tp), both prefixes since the alphas ascend.  ts goes into NB bit
-          // planes over the items; pairs with ts < tp are open (queued).
+          // Item k of a thread is one (row, column) pair.
           constexpr int Q = MAXM / 2;
-          constexpr int NB = TB <= 1 ? 1 : TB <= 3 ? 2 : TB <= 7 ? 3 : TB <= 15 ? 4 : 5;
           const int q = t % Q, h = t / Q;
           const int rA = q, rB = MAXM - 1 - q;
           const int nItems = h == 0 ? Q : Q - 1;
@@ -1174,12 +979,19 @@ __global__ void __launch_bounds__(160, tc_min_ctas<DT, MAXM, TB>()) prune_tc_ker
           const int TA = a.TA;
           const float4* ql4 = reinterpret_cast<const float4*>(qlo);
           const float4* qh4 = reinterpret_cast<const float4*>(qhi);
-          unsigned long long ip[NB], open = 0;
+          // Per distinct alpha u, bit k of mk[u] says that item k's column is
+          // surely removed at alpha u: hi < qlo(column, u).  Those tests are a
+          // prefix over u (the alphas ascend, the thresholds fall), so they are
+          // the row masks' bits as they stand.  "May be removed", !(lo >
+          // qhi(column, u)), is a prefix too; an item is open when some alpha may
+          // remove its column without surely doing so.
+          using IW = typename std::conditional<(Q <= 32), unsigned, unsigned long long>::type;
+          IW mk[TB], open = 0;
 #pragma unroll
-          for (int b = 0; b < NB; ++b) ip[b] = 0;
+          for (int u = 0; u < TB; ++u) mk[u] = 0;
           // straight-line items (the open ones are only marked), so that the
           // reads of several items overlap
-#pragma unroll 4
+#pragma unroll 2
           for (int k = 0; k < Q; ++k) {
             const bool onA = k < nA;
             const int R = onA ? rA : rB;
@@ -1191,47 +1003,50 @@ __global__ void __launch_bounds__(160, tc_min_ctas<DT, MAXM, TB>()) prune_tc_ker
             const float dv = ((onA ? ntA : ntB) + qc.x) - 2.f * G;
             const float err = fmaf(qc.y, onA ? AtA : AtB, fmaf(qc.x, eps_n, onA ? BtA : BtB));
             const float lo = dv - err, hi = dv + err;
-            int ts = 0, tp = 0;
+            bool op = false;
 #pragma unroll
             for (int u4 = 0; u4 < L::TB4; u4 += 4) {
               if (u4 < TA) {  // uniform
-                const float4 l4 = ql4[(ci * L::TB4 + u4) / 4];
-                const float4 h4 = qh4[(ci * L::TB4 + u4) / 4];
-                ts += int(hi < l4.x) + int(hi < l4.y) + int(hi < l4.z) + int(hi < l4.w);
-                tp += int(!(lo > h4.x)) + int(!(lo > h4.y)) + int(!(lo > h4.z)) + int(!(lo > h4.w));
+                const float4 l4 = ql4[(ci * TA4 + u4) / 4];
+                const float4 h4 = qh4[(ci * TA4 + u4) / 4];
+                const float lv[4] = {l4.x, l4.y, l4.z, l4.w}, hv[4] = {h4.x, h4.y, h4.z, h4.w};
+#pragma unroll
+                for (int e = 0; e < 4; ++e) {
+                  if (u4 + e >= TB) break;
+                  const bool sure = valid && hi < lv[e];  // padding past TA: -inf, never
+                  if (sure) mk[u4 + e] |= IW(1) << k;
+                  op |= valid && !sure && !(lo > hv[e]);
+                }
               }
             }
-            ts = valid ? ts : 0;
-            open |= static_cast<unsigned long long>(valid && tp > ts) << k;
-#pragma unroll
-            for (int b = 0; b < NB; ++b) ip[b] |= static_cast<unsigned long long>((ts >> b) & 1) << k;
+            if (op) open |= IW(1) << k;
           }
-          // open pairs (rare): the alphas from ts on are decided exactly by the
-          // consumer warp before its scan; here if the slot's queue is full
+          // open pairs (rare): the alphas from ts (the surely-removing count) on
+          // are decided exactly by the consumer warp before its scan; here if the
+          // slot's queue is full
           while (open) {
-            const int k = __ffsll(static_cast<long long>(open)) - 1;
+            const int k = int(__ffsll(static_cast<long long>(open))) - 1;
             open &= open - 1;
             const bool onA = k < nA;
             const int R = onA ? rA : rB;
             const int c = onA ? cA + k : cB + (k - nA);
             int ts = 0;
 #pragma unroll
-            for (int b = 0; b < NB; ++b) ts |= int((ip[b] >> k) & 1ull) << b;
+            for (int u = 0; u < TB; ++u) ts += int((mk[u] >> k) & 1u);
             const int qi = atomicAdd(rq_count + s, 1);
             if (qi < L::rq_cap) {
               rq[s * L::rq_cap + qi] = (unsigned(g * MAXM + R) << 16) | (unsigned(c) << 5) | unsigned(ts);
             } else {
-              // removal is monotone in alpha: ts becomes the first alpha that keeps the pair
+              // removal is monotone in alpha: the alphas before the first that keeps the pair remove it
               const int u1 = recheck_prefix_cold(a, ids, key, key64, R, c, ts, TA, ppt, E_rel, E_abs);
               n_rechecks += recheck_tests(ts, u1, TA);
 #pragma unroll
-              for (int b = 0; b < NB; ++b)
-                ip[b] = (ip[b] & ~(1ull << k)) | (static_cast<unsigned long long>((u1 >> b) & 1) << k);
+              for (int u = 0; u < TB; ++u)
+                if (u >= ts && u < u1) mk[u] |= IW(1) << k;
             }
           }
-          // item planes -> one row mask per distinct alpha: bit c of row R's mask u
-          // is [ts(R, c) > u]; row rA's items are [0, nA) from column cA, row rB's
-          // [nA, nItems) from column cB
+          // item masks -> row masks: row rA's items are [0, nA) from column cA,
+          // row rB's [nA, nItems) from column cB
           auto or_run = [&](unsigned long long* row, unsigned long long bits, int col) {
             const int w0 = col >> 6, sh = col & 63;
             if (bits << sh) atomicOr(row + w0, bits << sh);
@@ -1240,16 +1055,7 @@ __global__ void __launch_bounds__(160, tc_min_ctas<DT, MAXM, TB>()) prune_tc_ker
 #pragma unroll
           for (int u = 0; u < TB; ++u) {
             if (u >= TA) break;
-            unsigned long long gt = 0, eq = ~0ull;
-#pragma unroll
-            for (int b = NB - 1; b >= 0; --b) {
-              if ((u >> b) & 1) {
-                eq &= ip[b];
-              } else {
-                gt |= eq & ip[b];
-                eq &= ~ip[b];
-              }
-            }
+            const unsigned long long gt = mk[u];
             const unsigned long long mA = nA >= 64 ? gt : (gt & ((1ull << nA) - 1));
             const unsigned long long mB = nA >= 64 ? 0ull : (gt >> nA);
             if (mA) or_run(masks + (u * MAXM + rA) * MW, mA, cA);
