@@ -622,13 +622,14 @@ __global__ void __launch_bounds__(160, tc_min_ctas<DT, MAXM, TB>()) prune_tc_ker
       if (!in_order && live_row) {
         // entries past the degree hold ~0 and never count
         const ulonglong2* sk2 = reinterpret_cast<const ulonglong2*>(sk);
-        int cnt = 0;
+        int cnt0 = 0, cnt1 = 0;  // two sums, so the adds of successive entries overlap
 #pragma unroll 4
         for (int j2 = 0; j2 < (m + 1) / 2; ++j2) {
           const ulonglong2 v = sk2[j2];
-          cnt += int(v.x < my_sk) + int(v.y < my_sk);
+          cnt0 += int(v.x < my_sk);
+          cnt1 += int(v.y < my_sk);
         }
-        rank = cnt;
+        rank = cnt0 + cnt1;
       }
       double my64 = __longlong_as_double(0x7ff8000000000000ll);
       if constexpr (DT == kF32) {
