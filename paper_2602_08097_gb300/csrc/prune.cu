@@ -57,6 +57,7 @@ struct PruneArgs {
   int TA;
   int32_t Ad[kMaxTargets];
   int32_t amap[kMaxTargets];
+  float kappa[kMaxTargets];   // 1e6 / Ad^2 rounded to nearest (float thresholds)
   float scale;                // float rows enter the f16 Gram as scale * x (a power of two: exact)
   float inv_s;                // 1 / scale
   float inv_s2;               // 1 / scale^2: the Gram back in the rows' units (exact)
@@ -896,9 +897,12 @@ __global__ void __launch_bounds__(160, tc_min_ctas<DT, MAXM, TB>()) prune_tc_ker
 #pragma unroll
           for (int u = 0; u < TB; ++u) {
             if (u >= a.TA) break;
-            const float A2f = float(static_cast<unsigned long long>(a.Ad[u]) * a.Ad[u]);
-            qlo[rank * TA4 + u] = 1.0e6f * (kacc * (1.0f - E_rel) - E_abs) * 0.9999995f / A2f * 0.9999995f * 0.999999f;
-            qhi[rank * TA4 + u] = 1.0e6f * (kacc * (1.0f + E_rel) + E_abs) * 1.0000005f / A2f * 1.0000005f * 1.000001f;
+            // kappa = 1e6 / A^2 carries one rounding and the product two more; the
+            // last factor (1 -+ 2e-6) covers them with room to spare, and the
+            // roundings of the pair's d2 - err and d2 + err, compared against
+            // these thresholds directly
+            qlo[rank * TA4 + u] = (kacc * (1.0f - E_rel) - E_abs) * a.kappa[u] * 0.999998f;
+            qhi[rank * TA4 + u] = (kacc * (1.0f + E_rel) + E_abs) * a.kappa[u] * 1.000002f;
           }
           // padding past the last alpha never counts (hi < -inf, lo > -inf)
           for (int u = a.TA; u < TA4; ++u) qlo[rank * TA4 + u] = qhi[rank * TA4 + u] = -INFINITY;
@@ -920,8 +924,8 @@ __global__ void __launch_bounds__(160, tc_min_ctas<DT, MAXM, TB>()) prune_tc_ker
         }
         // The group's Gram, MAXM x MAXM in rank order over the operands (read by
         // now), row R rotated by R: G~(R, c) at [R * MAXM + (c + R) % MAXM], the
-        // entries with R < c.  tcgen05.ld is warp-collective: every lane issues
-        // it, live rows store.
+        // entries with R < c, in the operands' scaled units (G~ / inv_s2).
+        // tcgen05.ld is warp-collective: every lane issues it, live rows store.
         float* Gs = reinterpret_cast<float*>(opnd) + size_t(g) * MAXM * MAXM;
         if (!dead) {
           const int cend = (m + 15) & ~15;  // the same for every lane of the warp (one node)
@@ -943,8 +947,9 @@ __global__ void __launch_bounds__(160, tc_min_ctas<DT, MAXM, TB>()) prune_tc_ker
                 const int rc[4] = {r4.x, r4.y, r4.z, r4.w};
 #pragma unroll
                 for (int j = 0; j < 4; ++j)
-                  if (c0 + j4 + j < m && rc[j] > rank)
-                    grow[(rc[j] + rank) & (MAXM - 1)] = split_gram_value(v[j4 + j], v2[j4 + j], a.inv_s2);
+                  if (c0 + j4 + j < m && rc[j] > rank)  // in the scaled units (inv_s2 goes into the decision)
+                    grow[(rc[j] + rank) & (MAXM - 1)] = fmaf(__uint_as_float(v2[j4 + j]), 4.8828125e-04f,
+                                                             __uint_as_float(v[j4 + j]));
               }
             }
           }
@@ -978,6 +983,7 @@ __global__ void __launch_bounds__(160, tc_min_ctas<DT, MAXM, TB>()) prune_tc_ker
           const float AtA = 2.f * eps_ip * stA * 1.0009765625f + sub_abs, BtA = sub_abs * stA + eps_n * ntA + err_abs;
           const float AtB = 2.f * eps_ip * stB * 1.0009765625f + sub_abs, BtB = sub_abs * stB + eps_n * ntB + err_abs;
           const int TA = a.TA;
+          const float m2inv_s2 = -2.f * a.inv_s2;
           const float4* ql4 = reinterpret_cast<const float4*>(qlo);
           const float4* qh4 = reinterpret_cast<const float4*>(qhi);
           // Per distinct alpha u, bit k of mk[u] says that item k's column is
@@ -1001,7 +1007,7 @@ __global__ void __launch_bounds__(160, tc_min_ctas<DT, MAXM, TB>()) prune_tc_ker
             const int ci = valid ? c : 0;            // the reads stay in range for every k
             const float G = Gs[R * MAXM + ((ci + R) & (MAXM - 1))];
             const float4 qc = cq[ci];
-            const float dv = ((onA ? ntA : ntB) + qc.x) - 2.f * G;
+            const float dv = fmaf(G, m2inv_s2, (onA ? ntA : ntB) + qc.x);  // G~ = G * inv_s2: exact scaling
             const float err = fmaf(qc.y, onA ? AtA : AtB, fmaf(qc.x, eps_n, onA ? BtA : BtB));
             const float lo = dv - err, hi = dv + err;
             bool op = false;
@@ -1737,7 +1743,10 @@ cudaError_t launch_prune(const PruneLaunch& L, cudaStream_t s) {
   // distinct alphas (ascending, as the targets now are) and each target's index among them
   a.TA = 0;
   for (int t = 0; t < L.T; ++t) {
-    if (a.TA == 0 || a.Ad[a.TA - 1] != a.A[t]) a.Ad[a.TA++] = a.A[t];
+    if (a.TA == 0 || a.Ad[a.TA - 1] != a.A[t]) {
+      a.kappa[a.TA] = float(1.0e6 / (double(a.A[t]) * double(a.A[t])));
+      a.Ad[a.TA++] = a.A[t];
+    }
     a.amap[t] = a.TA - 1;
   }
   cudaError_t err = cudaSuccess;
