@@ -548,12 +548,14 @@ __global__ void __launch_bounds__(160, tc_min_ctas<DT, MAXM, TB>()) prune_tc_ker
         kacc = pacc + nacc - 2u * dacc;
       } else {
         // Rows of one 128-dimension slice also write their split f16 operand
-        // here, at the stored position: when the ranks turn out to be the
-        // stored positions (lists in Algorithm 1's order), the operand pass
-        // below has nothing left to do and the row is read once.
+        // here, at the stored position, so the row is read once.
         const bool one_slice = nslices == 1;
         if (live_row || one_slice) {
-          float part = 0.f;  // the key is summed per 32-dimension slice (slice_rel_bound)
+          // The key is summed per 32-dimension slice (slice_rel_bound), each
+          // slice as two interleaved running sums of 16 squares added at its
+          // end: a bound of 17 roundings per slice, within the 32 allowed, and
+          // half the dependent chain.
+          float part = 0.f, part1 = 0.f;
 #pragma unroll 4
           for (int c = 0; c < int(elems / 8); ++c) {
             uint4 x0 = make_uint4(0, 0, 0, 0), x1 = x0, y0 = x0, y1 = x0;
@@ -566,10 +568,10 @@ __global__ void __launch_bounds__(160, tc_min_ctas<DT, MAXM, TB>()) prune_tc_ker
               y1 = __ldg(pq + 1);
             }
             part = Acc<kF32>::step4(x0, y0, part);
-            part = Acc<kF32>::step4(x1, y1, part);
+            part1 = Acc<kF32>::step4(x1, y1, part1);
             if ((c & 3) == 3 || c == int(elems / 8) - 1) {
-              kacc += part;
-              part = 0.f;
+              kacc += part + part1;
+              part = part1 = 0.f;
             }
             if (one_slice) {  // rows past the degree: zeros
               const float xv[8] = {__uint_as_float(x0.x), __uint_as_float(x0.y), __uint_as_float(x0.z),
@@ -912,16 +914,17 @@ __global__ void __launch_bounds__(160, tc_min_ctas<DT, MAXM, TB>()) prune_tc_ker
           const char* nrow = reinterpret_cast<const char*>(a.X + int64_t(next_id) * a.row_bytes);
           for (int64_t off = 0; off < a.row_bytes; off += 128) asm volatile("prefetch.global.L2 [%0];" ::"l"(nrow + off));
         }
-        named_sync(kBarProd, 128);  // every rank-indexed array is complete
-        if (!dead) {
-          const bool ok = mbar_wait(mbar, phase, 1 << 24);
-          if (prod_sync_or(!ok)) {  // the MMA never completed: report, stop after this slot (uniform)
-            if (r == 0) raise_status(a.status, kDevOverflow, -2);
-            dead = true;
-          }
-          phase ^= 1u;
-          tc_fence_after();
+        // the Gram's MMA (dead is uniform; a slot that is already dead has none
+        // outstanding)
+        const bool waited = !dead;
+        const bool ok = waited ? mbar_wait(mbar, phase, 1 << 24) : true;
+        // one barrier: every rank-indexed array is complete, and the wait's outcome is known to all
+        if (prod_sync_or(!ok)) {  // the MMA never completed: report, stop after this slot (uniform)
+          if (r == 0) raise_status(a.status, kDevOverflow, -2);
+          dead = true;
         }
+        if (waited) phase ^= 1u;
+        tc_fence_after();
         // The group's Gram, MAXM x MAXM in rank order over the operands (read by
         // now), row R rotated by R: G~(R, c) at [R * MAXM + (c + R) % MAXM], the
         // entries with R < c, in the operands' scaled units (G~ / inv_s2).

@@ -99,21 +99,30 @@ def test_equal_subnormal_and_long_rows():
 # sums then added in order; its bound (slice_rel_bound, abs_bound in
 # csrc/common.cuh) is (min(d, 32) + ceil(d / 32) + 8) 2^-24 d2 + (d + 1) 2^-149 4.
 
-def _sliced_d2(a, b):
+def _sliced_d2(a, b, interleaved=False):
+    # interleaved: the prune kernel's pivot keys, where each slice keeps two
+    # running sums (dimensions 8c .. 8c+3 and 8c+4 .. 8c+7 of each group of
+    # eight) added together at the slice's end
     acc = f32(0)
     with np.errstate(over="ignore", under="ignore"):
         for c0 in range(0, a.shape[0], 32):
-            part = f32(0)
-            for x, y in zip(a[c0:c0 + 32], b[c0:c0 + 32]):
+            part = [f32(0), f32(0)]
+            for i, (x, y) in enumerate(zip(a[c0:c0 + 32], b[c0:c0 + 32])):
                 t = f32(x - y)
-                part = _fma(t, t, part)
-            acc = f32(acc + part)
+                j = ((i // 4) & 1) if interleaved else 0
+                part[j] = _fma(t, t, part[j])
+            acc = f32(acc + f32(part[0] + part[1]))
     return acc
 
 
 def _check_sliced(a, b):
+    for interleaved in (False, True):
+        _check_sliced_order(a, b, interleaved)
+
+
+def _check_sliced_order(a, b, interleaved):
     d = a.shape[0]
-    got = Fraction(float(_sliced_d2(a, b)))
+    got = Fraction(float(_sliced_d2(a, b, interleaved)))
     exact = sum((Fraction(float(x)) - Fraction(float(y))) ** 2 for x, y in zip(a, b))
     rel = Fraction(min(d, 32) + (d + 31) // 32 + 8, 2 ** 24)
     bound = rel * exact + Fraction(4 * (d + 1), 2 ** 149)
