@@ -1139,7 +1139,26 @@ __global__ void __launch_bounds__(160, tc_min_ctas<DT, MAXM, TB>()) prune_tc_ker
           const int mu = DT == kF32 ? a.amap[u] : u;  // the target's domination mask
           int32_t* out = a.out_col[u] + e0;
           int kept = 0;
-          while (kept < R) {
+          if constexpr (MW == 1) {
+            // Two steps per round: the mask of the next live candidate is read
+            // together with that of the one after it, which is the next argmin
+            // too unless the first removes it (then the round takes one step).
+            unsigned long long live = al[0];
+            const unsigned long long* mrow = masks + mu * MAXM;
+            while (kept < R && live) {
+              const int p1 = __ffsll(static_cast<long long>(live)) - 1;
+              const unsigned long long rest = live & (live - 1);  // live without p1
+              const int p2 = rest ? __ffsll(static_cast<long long>(rest)) - 1 : p1;
+              const unsigned long long m1 = mrow[p1], m2 = mrow[p2];
+              out[kept++] = ids[p1];
+              live = rest & ~m1;
+              if (kept < R && ((live >> p2) & 1ull)) {  // p2 outlived p1: the next argmin
+                out[kept++] = ids[p2];
+                live &= ~(m2 | (1ull << p2));
+              }
+            }
+          }
+          while (MW > 1 && kept < R) {
             int pos = -1;
 #pragma unroll
             for (int w = MW - 1; w >= 0; --w)
