@@ -612,7 +612,8 @@ def run_ours(args):
             "config": {"workload": workload_name(n, nq, args.workload), "n": n, "d": W["d"], "targets": TARGETS_W,
                        "queries": nq, "L": L_W, "k": k, "l2": "flushed (512 MB write) before every timed step",
                        "parallelism": f"node ranges x{ws} (all-gather of tuned slices)" if ws > 1 else "1 GPU"},
-            "roofline": {"bound": "hbm", "kernel": f"prune_tc_kernel<{W['dtype']}, 64, {T}> (tcgen05 Gram)",
+            "roofline": {"bound": "hbm", "kernel": f"prune_tc_kernel<{W['dtype']}, 64, {kernel_tb(W['dtype'], TARGETS_W)}> "
+                                                   "(tcgen05 Gram)",
                          "achieved": achieved,
                          "peak": hbm_peak, "unit": "GB/s", "frac": achieved / hbm_peak, "traffic": traffic,
                          "peak_kind": peak_kind, "algorithmic_bytes_per_launch": alg_bytes,
@@ -690,6 +691,16 @@ def serve_bench(rp, ctx, base, Q, gt, args):
         out["loads"][f"{load:g}x"] = entry
     out["stream_span_s_at_1x"] = span_s / cap_rps
     return out
+
+
+def kernel_tb(dtype, targets):
+    """The prune kernel's TB for a sweep: the power of two at or above the number of
+    targets (uint8) or of distinct alphas (float), at most 16."""
+    k = len({a for a, _ in targets}) if dtype == "f32" else len(targets)
+    tb = 1
+    while tb < k:
+        tb *= 2
+    return min(tb, 16)
 
 
 def kernel_hash():

@@ -1611,10 +1611,14 @@ static cudaError_t run_fast_t(const PruneArgs& args, int num_sms, int64_t host_c
 template <int DT, int MAXM>
 static cudaError_t run_fast(const PruneArgs& args, int num_sms, int64_t host_count, int ctas_cap, cudaStream_t s) {
   if (host_count <= 0) return cudaSuccess;
-  if (args.T <= 1) return run_fast_t<DT, MAXM, 1>(args, num_sms, host_count, ctas_cap, s);
-  if (args.T <= 2) return run_fast_t<DT, MAXM, 2>(args, num_sms, host_count, ctas_cap, s);
-  if (args.T <= 4) return run_fast_t<DT, MAXM, 4>(args, num_sms, host_count, ctas_cap, s);
-  if (args.T <= 8) return run_fast_t<DT, MAXM, 8>(args, num_sms, host_count, ctas_cap, s);
+  // TB bounds what the kernel keeps per target: one mask and threshold set per
+  // target for uint8 rows, per distinct alpha for float rows (targets sharing
+  // alpha share them; the consumer's lanes cover every target either way)
+  const int nb = DT == kF32 ? args.TA : args.T;
+  if (nb <= 1) return run_fast_t<DT, MAXM, 1>(args, num_sms, host_count, ctas_cap, s);
+  if (nb <= 2) return run_fast_t<DT, MAXM, 2>(args, num_sms, host_count, ctas_cap, s);
+  if (nb <= 4) return run_fast_t<DT, MAXM, 4>(args, num_sms, host_count, ctas_cap, s);
+  if (nb <= 8) return run_fast_t<DT, MAXM, 8>(args, num_sms, host_count, ctas_cap, s);
   return run_fast_t<DT, MAXM, kMaxTargets>(args, num_sms, host_count, ctas_cap, s);
 }
 
