@@ -364,14 +364,19 @@ __device__ __forceinline__ bool prod_sync_or(bool flag) {
 // One CTA = 4 producer warps + 1 consumer warp.  The producers handle NG =
 // 128 / MAXM nodes at a time, one candidate per thread: gather, pivot keys and
 // norms, the rank of each candidate in the processing order (a4), its f16
-// operand row placed at CTA row (group, rank) = TMEM lane, the tcgen05 Gram,
-// per-column thresholds and, from the Gram rows read back from TMEM, one
-// domination mask per target for every rank.  They hand ids and masks over
-// through one of two slots; the consumer warp runs the greedy loop per node and
-// target (a7) while the producers already work on the next nodes.
-// 4 CTAs per SM (the TMEM limit) need at most 96 registers per thread; the
-// kernels with more targets per launch, or one 128-candidate node per MMA
-// (more shared memory per CTA), trade that for registers.
+// operand row, the tcgen05 Gram, per-column thresholds and one domination mask
+// per target (uint8) or distinct alpha (float) for every rank.  uint8 operand
+// rows sit at CTA row (group, rank) = TMEM lane, and each lane turns its Gram row
+// into mask bits straight from TMEM.  Float operand rows stay at the stored
+// position, so the MMA starts before the ranks are known; the Gram is then
+// staged in shared memory in rank order and decided with the pairs spread
+// evenly over the producers.  They hand ids and masks over through one of two
+// slots; the consumer warp resolves the slot's open float pairs and runs the
+// greedy loop per node and target (a7) while the producers work on the next
+// nodes.  4 CTAs per SM (the TMEM limit) need at most 96 registers per thread;
+// the kernels with more targets per launch, float rows (256 TMEM columns), or
+// one 128-candidate node per MMA (more shared memory per CTA) trade that for
+// registers.
 template <int DT, int MAXM, int TB>
 constexpr int tc_min_ctas() { return (DT == kU8 && MAXM == 64 && TB <= 4) ? 4 : 2; }
 
