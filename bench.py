@@ -558,9 +558,11 @@ def run_ours(args):
         out_col = [torch.empty(base_col.shape[0], dtype=torch.int32).pin_memory() for _ in range(T)]
         lib = rp.load_library()
         import ctypes
+        # a stored index is its vectors, its adjacency and its start vertex
+        base_start = rp.rp_graph_info(ctx, base)["start"]
 
         def e2e_step():
-            g = rp.rp_load_graph(ctx, Xh, rph, colh)
+            g = rp.rp_load_graph(ctx, Xh, rph, colh, start=base_start)
             outs = rp.rp_tune_batch(ctx, g, alphas, Rs)
             h2d = X.nbytes + base_rp.nbytes + base_col.nbytes
             d2h = 0

@@ -232,25 +232,58 @@ __global__ void mean_u8_finish_kernel(const unsigned long long* __restrict__ sum
     mean[j] = __ddiv_rn(double(sums[j]), double(n));
 }
 
-// float32: one thread per column adds the rows in index order in binary64;
-// loads are issued eight rows ahead of the dependent additions.
-__global__ void mean_f32_kernel(const uint8_t* __restrict__ X, int64_t n, int64_t row_bytes, int d,
-                                double* __restrict__ mean) {
-  const float* F = reinterpret_cast<const float*>(X);
+// float32: each column's rows are added in index order in binary64, one
+// dependent chain per column. A chain runs on lane 0 of its own CTA, so the
+// chains of different columns do not share an SM's few binary64 units. Rows
+// arrive kMeanRows at a time in registers, the next group loaded while the
+// current one is added; the CTA of the first column of each 128-byte line
+// prefetches that line into L2 kMeanAhead rows before it is loaded.
+constexpr int kMeanRows = 64;
+constexpr int kMeanAhead = 1024;
+
+__global__ void __launch_bounds__(32) mean_f32_kernel(const uint8_t* __restrict__ X, int64_t n,
+                                                      int64_t row_bytes, int d, double* __restrict__ mean) {
+  const int j = blockIdx.x;  // grid = d
+  const int lane = threadIdx.x;
+  const bool lead = (j & 31) == 0;                // j * 4 is then a multiple of 128
+  const uint8_t* line = X + int64_t(j) * 4;       // rows are 128-byte multiples
+  const float* F = reinterpret_cast<const float*>(X) + j;
   const int64_t stride = row_bytes / 4;
-  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < d; j += gridDim.x * blockDim.x) {
-    double s = 0.0;
-    int64_t i = 0;
-    for (; i + 8 <= n; i += 8) {
-      float v[8];
+  const int64_t nfull = n / kMeanRows * kMeanRows;
+  double s = 0.0;
+  int64_t i = 0;
+  if (nfull > 0) {
+    float cur[kMeanRows], nxt[kMeanRows];
+    if (lane == 0) {
 #pragma unroll
-      for (int u = 0; u < 8; ++u) v[u] = __ldg(F + (i + u) * stride + j);
-#pragma unroll
-      for (int u = 0; u < 8; ++u) s = __dadd_rn(s, double(v[u]));
+      for (int u = 0; u < kMeanRows; ++u) cur[u] = __ldg(F + int64_t(u) * stride);
     }
-    for (; i < n; ++i) s = __dadd_rn(s, double(F[i * stride + j]));
-    mean[j] = __ddiv_rn(s, double(n));
+    // a next full group exists while i + kMeanRows < nfull (both multiples of kMeanRows)
+    for (; i + kMeanRows < nfull; i += kMeanRows) {
+      if (lead) {
+        for (int r = lane; r < kMeanRows; r += 32) {
+          const int64_t q = i + kMeanAhead + r;
+          if (q < n) asm volatile("prefetch.global.L2 [%0];" ::"l"(line + q * row_bytes));
+        }
+      }
+      if (lane == 0) {
+#pragma unroll
+        for (int u = 0; u < kMeanRows; ++u) nxt[u] = __ldg(F + (i + kMeanRows + u) * stride);
+#pragma unroll
+        for (int u = 0; u < kMeanRows; ++u) s = __dadd_rn(s, double(cur[u]));
+#pragma unroll
+        for (int u = 0; u < kMeanRows; ++u) cur[u] = nxt[u];
+      }
+    }
+    if (lane == 0) {
+#pragma unroll
+      for (int u = 0; u < kMeanRows; ++u) s = __dadd_rn(s, double(cur[u]));
+    }
+    i = nfull;
   }
+  if (lane != 0) return;
+  for (; i < n; ++i) s = __dadd_rn(s, double(F[i * stride]));
+  mean[j] = __ddiv_rn(s, double(n));
 }
 
 __global__ void nearest_mean_kernel(const uint8_t* __restrict__ X, int64_t n, int64_t row_bytes, int d,
@@ -424,7 +457,7 @@ cudaError_t launch_medoid(const DevData& D, double* mean, double* block_best, in
     mean_u8_sum_kernel<<<grid, 128, 0, s>>>(D.X, D.n, D.row_bytes, D.d, sums);
     mean_u8_finish_kernel<<<unsigned((D.d + 127) / 128), 128, 0, s>>>(sums, D.n, D.d, mean);
   } else {
-    mean_f32_kernel<<<unsigned((D.d + 31) / 32), 32, 0, s>>>(D.X, D.n, D.row_bytes, D.d, mean);
+    mean_f32_kernel<<<unsigned(D.d), 32, 0, s>>>(D.X, D.n, D.row_bytes, D.d, mean);
   }
   const int64_t nb = medoid_blocks(D.n);
   nearest_mean_kernel<<<unsigned(nb), 256, 0, s>>>(D.X, D.n, D.row_bytes, D.d, D.dtype, mean, block_best);

@@ -322,10 +322,14 @@ void rp_server::round(std::vector<Req*>& batch, int32_t round_no) {
     }
   }
   run_searches(rest);
+  {
+    // counted before the last requests complete, so that a caller who has seen
+    // them complete also sees the round in the statistics
+    std::lock_guard<std::mutex> lk(mu);
+    stats.rounds += 1;
+    stats.busy_ns += now_ns(t0) - t_start;
+  }
   publish(rest);
-  std::lock_guard<std::mutex> lk(mu);
-  stats.rounds += 1;
-  stats.busy_ns += now_ns(t0) - t_start;
 }
 
 // One step of the scheduler with an asynchronous executor: take in the tuning

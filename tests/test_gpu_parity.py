@@ -327,6 +327,32 @@ def test_float_knn_candidate_base_matches_oracle(ctx):
     _same_csr(rp.rp_graph_export(ctx, b), oracle.knn_base(X, 128, 1.2, 64), "deep kNN-128 base")
 
 
+# ------------------------------------------------------------------ start vertex
+
+@pytest.mark.parametrize("n", [1, 2, 63, 64, 65, 129, 1151, 4097])
+def test_float_medoid_of_a_ramp(ctx, n):
+    """The float mean adds rows in index order, 64 rows a group plus a ragged tail.
+    Rows on a ramp (x = i in three columns, one of them in each 32-column group)
+    put the mean at (n-1)/2, so the medoid (§4.1, ties to the smaller id) is row
+    (n-1)//2; a skipped or repeated group moves it."""
+    X = np.zeros((n, 96), dtype=np.float32)
+    for c in (0, 40, 95):
+        X[:, c] = np.arange(n, dtype=np.float32)
+    g = rp.rp_load_graph(ctx, X)
+    assert rp.rp_graph_info(ctx, g)["start"] == (n - 1) // 2
+    rp.rp_graph_free(ctx, g)
+
+
+@pytest.mark.parametrize("n,d", [(4097, 96), (20011, 100), (3001, 17)])
+def test_float_medoid_matches_oracle(ctx, n, d):
+    rng = np.random.default_rng(n + d)
+    X = rng.standard_normal((n, d)).astype(np.float32)
+    X[rng.integers(0, n, 8)] *= 40.0  # a few far rows pull the mean off the origin
+    g = rp.rp_load_graph(ctx, X)
+    assert rp.rp_graph_info(ctx, g)["start"] == oracle.medoid(X)
+    rp.rp_graph_free(ctx, g)
+
+
 # ------------------------------------------------------------------ search
 
 @pytest.mark.parametrize("L,k", [(64, 10), (32, 32), (100, 7)])
