@@ -232,58 +232,152 @@ __global__ void mean_u8_finish_kernel(const unsigned long long* __restrict__ sum
     mean[j] = __ddiv_rn(double(sums[j]), double(n));
 }
 
-// float32: each column's rows are added in index order in binary64, one
-// dependent chain per column. A chain runs on lane 0 of its own CTA, so the
-// chains of different columns do not share an SM's few binary64 units. Rows
-// arrive kMeanRows at a time in registers, the next group loaded while the
-// current one is added; the CTA of the first column of each 128-byte line
-// prefetches that line into L2 kMeanAhead rows before it is loaded.
-constexpr int kMeanRows = 64;
-constexpr int kMeanAhead = 1024;
+// float32: each column's rows are added in index order in binary64, exactly as
+// the sequential loop s <- fl(s + x_i) rounds them, but 64 rows per warp step.
+//
+// While s stays in one binade [2^E, 2^(E+1)) every addition rounds to the grid
+// u = 2^(E-52): fl(s + x) = s + u * rne(x / u), unless x / u is exactly halfway
+// (the tie then goes by the parity of the result). So with s = S * u (S the
+// 53-bit significand) the step converts each x to integer units q = rne(x/u),
+// takes the warp's inclusive prefix sum T = S + (q_0 + ... + q_e), and keeps
+// every leading element for which T stays in [2^52 + 1, 2^53] and x was no tie.
+// An element with T in that range had an exact sum in binade E (or rounding to
+// 2^(E+1)), where this rounding is the IEEE one. The first element outside it is
+// added with a real binary64 addition and the next step starts after it; a T of
+// exactly 2^53 ends the step (s moves up a binade). s = +0 stays +0 over zeros
+// and takes the first nonzero value exactly; a subnormal s takes real additions.
+// Every step consumes at least one row, so the loop ends.
+//
+// One warp per column (grid = d). Rows arrive in blocks of kMeanBlock through
+// shared memory, the next block loaded into registers while this one is summed.
+constexpr int kMeanBlock = 1024;
+
+// q = rne(x / 2^e52) in the sign frame of s (neg), or false when x / 2^e52 is a
+// tie or too large to be kept anyway (the caller then adds x in binary64).
+__device__ __forceinline__ bool mean_units(float x, int e52, unsigned neg, long long& q) {
+  const unsigned xb = __float_as_uint(x);
+  const int ex = int((xb >> 23) & 0xff);
+  const unsigned m = (xb & 0x7fffffu) | (ex ? 0x800000u : 0u);  // x = m * 2^((ex ? ex : 1) - 150)
+  const int k = (ex ? ex : 1) - 150 - e52;
+  long long v = 0;
+  bool ok = true;
+  if (m != 0) {
+    if (k >= 0) {
+      ok = k <= 30;  // |x| >= 2^30 u: past the top of the binade before the sum could keep it
+      v = ok ? (long long)m << k : 0;
+    } else if (-k < 26) {  // -k >= 26: x / u < 1/4 rounds to 0, no tie
+      const int sh = -k;
+      const unsigned rem = m & ((1u << sh) - 1u), half = 1u << (sh - 1);
+      v = (long long)(m >> sh) + (rem > half ? 1 : 0);
+      ok = rem != half;
+    }
+  }
+  q = (xb >> 31) != neg ? -v : v;
+  return ok;
+}
 
 __global__ void __launch_bounds__(32) mean_f32_kernel(const uint8_t* __restrict__ X, int64_t n,
                                                       int64_t row_bytes, int d, double* __restrict__ mean) {
-  const int j = blockIdx.x;  // grid = d
+  __shared__ float buf[kMeanBlock];
+  const int j = blockIdx.x;
   const int lane = threadIdx.x;
-  const bool lead = (j & 31) == 0;                // j * 4 is then a multiple of 128
-  const uint8_t* line = X + int64_t(j) * 4;       // rows are 128-byte multiples
   const float* F = reinterpret_cast<const float*>(X) + j;
   const int64_t stride = row_bytes / 4;
-  const int64_t nfull = n / kMeanRows * kMeanRows;
-  double s = 0.0;
-  int64_t i = 0;
-  if (nfull > 0) {
-    float cur[kMeanRows], nxt[kMeanRows];
-    if (lane == 0) {
+  const long long kLo = (1ll << 52) + 1, kHi = 1ll << 53;
+  float nxt[kMeanBlock / 32];
 #pragma unroll
-      for (int u = 0; u < kMeanRows; ++u) cur[u] = __ldg(F + int64_t(u) * stride);
-    }
-    // a next full group exists while i + kMeanRows < nfull (both multiples of kMeanRows)
-    for (; i + kMeanRows < nfull; i += kMeanRows) {
-      if (lead) {
-        for (int r = lane; r < kMeanRows; r += 32) {
-          const int64_t q = i + kMeanAhead + r;
-          if (q < n) asm volatile("prefetch.global.L2 [%0];" ::"l"(line + q * row_bytes));
-        }
-      }
-      if (lane == 0) {
-#pragma unroll
-        for (int u = 0; u < kMeanRows; ++u) nxt[u] = __ldg(F + (i + kMeanRows + u) * stride);
-#pragma unroll
-        for (int u = 0; u < kMeanRows; ++u) s = __dadd_rn(s, double(cur[u]));
-#pragma unroll
-        for (int u = 0; u < kMeanRows; ++u) cur[u] = nxt[u];
-      }
-    }
-    if (lane == 0) {
-#pragma unroll
-      for (int u = 0; u < kMeanRows; ++u) s = __dadd_rn(s, double(cur[u]));
-    }
-    i = nfull;
+  for (int t = 0; t < kMeanBlock / 32; ++t) {
+    const int64_t r = int64_t(32 * t + lane);
+    nxt[t] = r < n ? __ldg(F + r * stride) : 0.f;
   }
-  if (lane != 0) return;
-  for (; i < n; ++i) s = __dadd_rn(s, double(F[i * stride]));
-  mean[j] = __ddiv_rn(s, double(n));
+  double s = 0.0;
+  for (int64_t base = 0; base < n; base += kMeanBlock) {
+    __syncwarp();
+#pragma unroll
+    for (int t = 0; t < kMeanBlock / 32; ++t) buf[32 * t + lane] = nxt[t];
+    __syncwarp();
+    if (base + kMeanBlock < n) {
+#pragma unroll
+      for (int t = 0; t < kMeanBlock / 32; ++t) {
+        const int64_t r = base + kMeanBlock + 32 * t + lane;
+        nxt[t] = r < n ? __ldg(F + r * stride) : 0.f;
+      }
+    }
+    const int64_t bend = n < base + kMeanBlock ? n : base + kMeanBlock;
+    int64_t i = base;
+    while (i < bend) {  // s, i and every branch below are uniform over the warp
+      const int avail = bend - i < 64 ? int(bend - i) : 64;
+      const int off = int(i - base);
+      const bool ha = 2 * lane < avail, hb = 2 * lane + 1 < avail;
+      const float xa = ha ? buf[off + 2 * lane] : 0.f;
+      const float xb = hb ? buf[off + 2 * lane + 1] : 0.f;
+      const unsigned long long sb = (unsigned long long)__double_as_longlong(s);
+      const int eb = int((sb >> 52) & 0x7ff);
+      if (sb == 0) {  // s = +0
+        const unsigned nza = __ballot_sync(0xffffffffu, ha && (__float_as_uint(xa) & 0x7fffffffu) != 0);
+        const unsigned nzb = __ballot_sync(0xffffffffu, hb && (__float_as_uint(xb) & 0x7fffffffu) != 0);
+        if ((nza | nzb) == 0) {
+          i += avail;
+          continue;
+        }
+        const int l = __ffs(int(nza | nzb)) - 1;
+        const bool at_a = (nza >> l) & 1u;
+        s = double(__shfl_sync(0xffffffffu, at_a ? xa : xb, l));  // 0 + x = x exactly
+        i += 2 * l + (at_a ? 0 : 1) + 1;
+        continue;
+      }
+      if (eb == 0 || eb == 0x7ff) {  // subnormal s (or a non-finite one): a real addition
+        s = __dadd_rn(s, double(__shfl_sync(0xffffffffu, xa, 0)));
+        i += 1;
+        continue;
+      }
+      const int e52 = eb - 1075;
+      const unsigned neg = unsigned(sb >> 63);
+      const long long S = (long long)((sb & ((1ull << 52) - 1)) | (1ull << 52));
+      long long qa, qb;
+      const bool oka = mean_units(xa, e52, neg, qa) && ha;
+      const bool okb = mean_units(xb, e52, neg, qb) && hb;
+      if (!ha) qa = 0;
+      if (!hb) qb = 0;
+      long long pre = qa + qb;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const long long v = __shfl_up_sync(0xffffffffu, pre, o);
+        if (lane >= o) pre += v;
+      }
+      const long long Tb = S + pre, Ta = Tb - qb;
+      const bool va = oka && Ta >= kLo && Ta <= kHi;
+      const bool vb = okb && Tb >= kLo && Tb <= kHi;
+      const unsigned inva = __ballot_sync(0xffffffffu, !va), invb = __ballot_sync(0xffffffffu, !vb);
+      const unsigned enda = __ballot_sync(0xffffffffu, va && Ta == kHi);
+      const unsigned endb = __ballot_sync(0xffffffffu, vb && Tb == kHi);
+      int fi = 64, fe = 64;  // first element kept by no T, first element at 2^53
+      if (inva | invb) {
+        const int l = __ffs(int(inva | invb)) - 1;
+        fi = 2 * l + (((inva >> l) & 1u) ? 0 : 1);
+      }
+      if (enda | endb) {
+        const int l = __ffs(int(enda | endb)) - 1;
+        fe = 2 * l + (((enda >> l) & 1u) ? 0 : 1);
+      }
+      const int c = fi < fe + 1 ? fi : fe + 1;  // elements kept, c <= fi <= avail
+      if (c > 0) {
+        const int e = c - 1;
+        const long long T = __shfl_sync(0xffffffffu, (e & 1) ? Tb : Ta, e >> 1);
+        const unsigned long long sign = (unsigned long long)neg << 63;
+        s = __longlong_as_double((long long)(T == kHi ? sign | ((unsigned long long)(eb + 1) << 52)
+                                                     : sign | ((unsigned long long)eb << 52) |
+                                                           (unsigned long long)(T - (1ll << 52))));
+      }
+      int used = c;
+      if (c < avail && c == fi) {
+        s = __dadd_rn(s, double(__shfl_sync(0xffffffffu, (c & 1) ? xb : xa, c >> 1)));
+        used = c + 1;
+      }
+      i += used;
+    }
+  }
+  if (lane == 0) mean[j] = __ddiv_rn(s, double(n));
 }
 
 __global__ void nearest_mean_kernel(const uint8_t* __restrict__ X, int64_t n, int64_t row_bytes, int d,

@@ -6,6 +6,7 @@ import numpy as np
 import pytest
 
 import datagen
+import medoid_cases
 import oracle
 
 rp = pytest.importorskip("paper_2602_08097_gb300")
@@ -343,11 +344,37 @@ def test_float_medoid_of_a_ramp(ctx, n):
     rp.rp_graph_free(ctx, g)
 
 
-@pytest.mark.parametrize("n,d", [(4097, 96), (20011, 100), (3001, 17)])
-def test_float_medoid_matches_oracle(ctx, n, d):
-    rng = np.random.default_rng(n + d)
+@pytest.mark.parametrize("col", [0, 40, 95])
+@pytest.mark.parametrize("k", [-1, 0, 1])
+def test_float_medoid_to_the_last_bit(ctx, col, k):
+    """The mean is on, or one ulp either side of, the midpoint of rows 0 and 1
+    (the sum rounds thousands of times on the way): a mean one ulp off in
+    either direction changes one of these answers."""
+    X, expect = medoid_cases.tie_case(col, k)
+    g = rp.rp_load_graph(ctx, X)
+    assert rp.rp_graph_info(ctx, g)["start"] == expect
+    rp.rp_graph_free(ctx, g)
+
+
+def _medoid_data(kind, n, d, rng):
     X = rng.standard_normal((n, d)).astype(np.float32)
-    X[rng.integers(0, n, 8)] *= 40.0  # a few far rows pull the mean off the origin
+    if kind == "far rows":
+        X[rng.integers(0, n, 8)] *= 40.0  # pull the mean off the origin
+    elif kind == "wide range":
+        X *= (2.0 ** rng.integers(-100, 44, (n, d))).astype(np.float32)  # loads take |x| <= 2^50
+    elif kind == "zero and subnormal columns":
+        X[:, ::3] = 0.0
+        X[:, 1::3] *= np.float32(1e-40)  # subnormal float32 values
+    elif kind == "alternating":
+        X[:, 0] = np.where(np.arange(n) % 2 == 0, 1.0, -1.0)
+    return X
+
+
+@pytest.mark.parametrize("kind,n,d", [("far rows", 4097, 96), ("far rows", 20011, 100), ("far rows", 3001, 17),
+                                      ("wide range", 5000, 96), ("zero and subnormal columns", 3003, 40),
+                                      ("alternating", 2500, 8)])
+def test_float_medoid_matches_oracle(ctx, kind, n, d):
+    X = _medoid_data(kind, n, d, np.random.default_rng(n + d))
     g = rp.rp_load_graph(ctx, X)
     assert rp.rp_graph_info(ctx, g)["start"] == oracle.medoid(X)
     rp.rp_graph_free(ctx, g)

@@ -22,6 +22,7 @@ import pytest
 
 import datagen
 import oracle
+import medoid_cases
 from closed_forms import (appendix_a_points, beta_euc, sorted_euclid_bound,
                           sorted_general_bound, unsorted_bound,
                           unsorted_bound_as_printed)
@@ -364,6 +365,37 @@ def test_medoid_is_nearest_to_mean():
     mu = U.astype(np.float64).mean(0)
     du = ((U.astype(np.float64) - mu) ** 2).sum(1)
     assert oracle.medoid(U) == int(np.argmin(du))
+
+
+@pytest.mark.parametrize("col", [0, 40, 95])
+@pytest.mark.parametrize("k", [-1, 0, 1])
+def test_medoid_follows_the_index_order_mean_to_the_last_bit(col, k):
+    """§4.1's start vertex under the binary64 index-order reading of the mean:
+    the constructed mean sits on, or one ulp either side of, the midpoint of
+    rows 0 and 1, so only the exact sequential rounding gives the answer."""
+    X, expect = medoid_cases.tie_case(col, k)
+    assert oracle.medoid(X) == expect
+
+
+def test_medoid_tie_cases_see_one_ulp():
+    """The construction is sensitive: a mean one ulp up breaks the k = 0 tie
+    towards row 1, and one ulp down turns the k = 1 case to row 0; the exactly
+    rounded sum (another reading of the mean) changes some answer too."""
+    def nearest(X, mean):
+        return int(np.argmin(((X.astype(np.float64) - mean) ** 2).sum(1)))
+
+    n_changed = 0
+    for col in (0, 40, 95):
+        for k, nudge, flipped in ((0, +1, 1), (1, -1, 0)):
+            X, _ = medoid_cases.tie_case(col, k)
+            m = np.array([medoid_cases.sequential_sum(X[:, j]) for j in range(X.shape[1])]) / X.shape[0]
+            m[col] = np.nextafter(m[col], nudge * np.inf)
+            assert nearest(X, m) == flipped
+        for k in (-1, 0, 1):
+            X, expect = medoid_cases.tie_case(col, k)
+            exact = np.array([math.fsum(X[:, j].astype(np.float64).tolist()) for j in range(X.shape[1])]) / X.shape[0]
+            n_changed += nearest(X, exact) != expect
+    assert n_changed > 0
 
 
 def test_reachability_small_line():
