@@ -111,7 +111,9 @@ rp_status rp_sync(rp_ctx *ctx);
  *   start: the GreedySearch start vertex, or -1 for the medoid, read as the
  *     data point nearest (binary64, index-order sums) to the binary64 mean
  *     vector, ties to the smaller id (§4.1 names the medoid; this reading
- *     keeps it computable at n = 10^7).
+ *     keeps it computable at n = 10^7).  The medoid takes two more passes
+ *     over the vectors; a stored index passes the start vertex it was built
+ *     with and skips them.
  * Cleaning: self loops are dropped and repeated ids keep their first
  * occurrence; the cleaned graph is what every later call sees.  Counts of
  * dropped entries are available through rp_stats.
