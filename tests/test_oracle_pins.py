@@ -398,6 +398,70 @@ def test_medoid_tie_cases_see_one_ulp():
     assert n_changed > 0
 
 
+def test_canonical_distances_are_exact_or_within_the_sum_bound():
+    """d2_pairs / d2_query: uint8 distances are exact integers; float32 ones are
+    index-order binary64 sums of exactly formed squares' roundings, within
+    (d + 1) 2^-53 of the exact rational value; id -1 gives +inf."""
+    from fractions import Fraction
+    rng = np.random.default_rng(31)
+    n, d = 60, 37
+    a = rng.integers(0, n, 150)
+    b = rng.integers(0, n, 150)
+    U = rng.integers(0, 256, (n, d), dtype=np.uint8)
+    want = ((U[a].astype(np.int64) - U[b].astype(np.int64)) ** 2).sum(1)
+    assert np.array_equal(oracle.d2_pairs(U, a, b), want.astype(np.float64))
+    F = rng.standard_normal((n, d)).astype(np.float32)
+
+    def exact(x, y):
+        return sum((Fraction(float(u)) - Fraction(float(v))) ** 2 for u, v in zip(x, y))
+
+    got = oracle.d2_pairs(F, a, b)
+    for i in range(a.size):
+        e = exact(F[a[i]], F[b[i]])
+        assert abs(Fraction(got[i]) - e) <= Fraction(d + 1, 2 ** 53) * e
+    assert (oracle.d2_pairs(F, a, a) == 0).all()
+    Q = rng.standard_normal((5, d)).astype(np.float32)
+    ids = rng.integers(-1, n, (5, 7)).astype(np.int32)
+    ids[0, 0] = -1
+    dq = oracle.d2_query(F, Q, ids)
+    for i in range(5):
+        for j in range(7):
+            if ids[i, j] < 0:
+                assert dq[i, j] == np.inf
+            else:
+                e = exact(Q[i], F[ids[i, j]])
+                assert abs(Fraction(dq[i, j]) - e) <= Fraction(d + 1, 2 ** 53) * e
+    dqu = oracle.d2_query(U, U[:3], np.array([[0, 1], [2, -1], [5, 2]], np.int32))
+    assert dqu[0, 0] == 0 and dqu[1, 1] == np.inf
+    assert dqu[2, 0] == float(((U[2].astype(np.int64) - U[5].astype(np.int64)) ** 2).sum())
+
+
+def test_knn_base_reduces_to_the_knn_lists():
+    """The kNN-candidate base, RobustPrune(p, kNN_k(p), alpha, R):
+    - alpha so large that no candidate dominates another keeps every list whole
+      and in distance order, i.e. exactly the kNN lists;
+    - R = 1 keeps each point's nearest neighbour (Algorithm 1 keeps the argmin
+      first), i.e. the 1-NN graph;
+    - any alpha gives lists that start with the nearest neighbour and hold
+      only kNN candidates."""
+    rng = np.random.default_rng(32)
+    n, k = 300, 12
+    X = rng.standard_normal((n, 8)).astype(np.float32)
+    ids, _ = oracle.knn(X, k, qid=np.arange(n))
+    rp_, col = oracle.knn_base(X, k, 1000.0, k)
+    assert np.array_equal(np.diff(rp_), np.full(n, k))
+    assert np.array_equal(col.reshape(n, k), ids)
+    rp1, col1 = oracle.knn_base(X, k, 1.2, 1)
+    assert np.array_equal(np.diff(rp1), np.ones(n, np.int64)) and np.array_equal(col1, ids[:, 0])
+    rpa, cola = oracle.knn_base(X, k, 1.2, k)
+    for p in range(n):
+        row = cola[rpa[p]:rpa[p + 1]]
+        assert row[0] == ids[p, 0] and set(row.tolist()) <= set(ids[p].tolist())
+    assert np.diff(rpa).mean() < k  # alpha = 1.2 does prune
+    rows = oracle.knn_base(X, k, 1.2, k, nodes=np.array([7, 3]))
+    assert [r.tolist() for r in rows] == [cola[rpa[7]:rpa[8]].tolist(), cola[rpa[3]:rpa[4]].tolist()]
+
+
 def test_reachability_small_line():
     # points 0, 1, 3 on a line; edges 0->1, 1->2, 2->1
     X = np.array([[0], [1], [3]], dtype=np.uint8)
