@@ -595,7 +595,9 @@ def run_ours(args):
             et.append(time.perf_counter() - t1)
         e2e_s = statistics.mean(et)
         e2e = {"value": n * T / e2e_s, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
-               "d2h_bytes_per_step": int(d2h), "ms_per_step": 1000 * e2e_s}
+               "d2h_bytes_per_step": int(d2h), "ms_per_step": 1000 * e2e_s,
+               "step": "load the stored index (vectors, CSR, start vertex) from pinned host memory, tune, "
+                       "search with host queries and results, recall, export every tuned graph to host memory"}
 
     serving = None
     if not args.quick and not args.no_serve and args.workload in SERVE_BUDGET_GB:
