@@ -145,3 +145,32 @@ def test_recheck_tier_never_contradicts_the_canonical_test(seed):
                     assert not canonical_remove, (A, d, d2a, d2b, fa, fb)
                 decided += r >= 0
     assert decided > 1000
+
+
+def _sure_less(a, b, E, Eabs):
+    return F(F(a * F(F(1) + E)) + Eabs) < F(F(b * F(F(1) - E)) - Eabs)
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_sure_less_never_misorders_keys(seed):
+    """sure_less(a, b) orders two pivot keys in single precision only when their
+    binary64 values are strictly ordered the same way; equal values (which the
+    id orders) are never claimed. Keys carry the distances' own error, as above."""
+    rng = np.random.default_rng(300 + seed)
+    claimed = 0
+    for _ in range(6000):
+        d = int(rng.choice([8, 32, 96, 128, 960]))
+        E, Eabs = _bounds(d)
+        rel = float(E) - 6 * 2.0 ** -24
+        ab = (d + 1) * 2.0 ** -149
+        tb = float(2.0 ** (rng.uniform(-149, -118) if rng.random() < 0.3 else rng.uniform(-118, 100)))
+        r = rng.random()
+        ta = tb if r < 0.2 else tb * (1.0 + (rng.uniform(-1e-5, 1e-5) if r < 0.8 else rng.uniform(-0.5, 0.5)))
+        a_lo, a_hi = _inward(ta - rel * ta - ab, ta + rel * ta + ab)
+        b_lo, b_hi = _inward(tb - rel * tb - ab, tb + rel * tb + ab)
+        for fa in (a_lo, a_hi, F(ta)):
+            for fb in (b_lo, b_hi, F(tb)):
+                if _sure_less(fa, fb, E, Eabs):
+                    assert ta < tb, (d, ta, tb, fa, fb)
+                    claimed += 1
+    assert claimed > 1000
