@@ -101,3 +101,10 @@ def test_search_matches_oracle_at_full_size(float_full):
     rel = (min(d, 32) + -(-d // 32) + 8) * 2.0**-24
     ok = ref_ids >= 0
     assert np.all(np.abs(dists[ok].astype(np.float64) - ref_d2[ok]) <= rel * ref_d2[ok] + 1e-30)
+
+
+def test_start_vertex_matches_the_oracle(float_full):
+    """The start vertex (§4.1) at full size: the data point nearest to the
+    index-order binary64 mean, over every row, equals the oracle's."""
+    name, W, ctx, X, base, outs, stats = float_full
+    assert rp.rp_graph_info(ctx, base)["start"] == oracle.medoid(X), name
